@@ -1,0 +1,185 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the method: it draws populations (ages,
+households, occupation groups, initial cases) with numpy's seeded generator and
+lists parameter sets.  Both the CUDA path and the CPU oracle consume what it
+returns; neither is imported here.
+
+The paper's populations come from King County census and mobility data
+(Sec. 3 "Agent State Definition"), which is not available; these generators
+stand in for it with the shapes the paper describes:
+  * ages: 9 ten-year bins (Sec. 3 "Infection Transmission"), uniform;
+  * households: complete graphs (Sec. 3 "Interaction Networks"), sizes 1-6 with
+    probabilities (.28, .35, .15, .13, .06, .03), members given consecutive ids;
+  * occupation: groups of 20 drawn from a random permutation of the agents,
+    each agent receiving in-links from 10 distinct members of its group;
+  * random network: regenerated every day by the method itself (not here).
+The disease parameters are placeholders: the paper cites other work for them
+(Sec. 3 "Disease Progression") and prints none.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+HOUSEHOLD_SIZE_P = (0.28, 0.35, 0.15, 0.13, 0.06, 0.03)
+N_AGE = 9
+N_REP_PARAMS = 14  # R, B_household, B_occupation, B_random, S_age[9], second-dose delay
+
+
+def household_sizes(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Household sizes covering exactly n agents (the last household is truncated)."""
+    mean = sum((i + 1) * p for i, p in enumerate(HOUSEHOLD_SIZE_P))
+    sizes = rng.choice(np.arange(1, 7), size=int(n / mean * 1.2) + 16, p=HOUSEHOLD_SIZE_P)
+    cs = np.cumsum(sizes)
+    while cs[-1] < n:
+        sizes = np.concatenate([sizes, rng.choice(np.arange(1, 7), size=64, p=HOUSEHOLD_SIZE_P)])
+        cs = np.cumsum(sizes)
+    k = int(np.searchsorted(cs, n))
+    sizes = sizes[: k + 1].copy()
+    sizes[-1] -= int(cs[k] - n)
+    return sizes[sizes > 0].astype(np.int64)
+
+
+def household_csr(sizes: np.ndarray):
+    """Complete graph inside each household; destination-sorted CSR, sources ascending."""
+    n = int(sizes.sum())
+    start = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    deg = np.repeat(sizes - 1, sizes)
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(deg, out=row_ptr[1:])
+    col = np.zeros(int(row_ptr[-1]), np.uint32)
+    for s in range(2, int(sizes.max(initial=1)) + 1):
+        st = start[sizes == s]
+        if st.size == 0:
+            continue
+        members = st[:, None] + np.arange(s)[None, :]
+        for p in range(s):
+            src = np.delete(members, p, axis=1)
+            dst = members[:, p]
+            col[row_ptr[dst][:, None] + np.arange(s - 1)[None, :]] = src
+    return row_ptr.astype(np.uint32), col
+
+
+def occupation_csr(n: int, rng: np.random.Generator, group: int = 20, links: int = 10):
+    """Groups of `group` agents from a random permutation; each agent gets `links`
+    distinct in-links from its group-mates (all of them if the group is smaller)."""
+    perm = rng.permutation(n).astype(np.int64)
+    deg = np.zeros(n, np.int64)
+    parts = []  # (dst ids, src matrix)
+    G = n // group
+    if G:
+        members = perm[: G * group].reshape(G, group)
+        others = np.array([[q for q in range(group) if q != p] for p in range(group)])  # (group, group-1)
+        k = min(links, group - 1)
+        keys = rng.random((G, group, group - 1), dtype=np.float32)
+        pick = np.argsort(keys, axis=2, kind="stable")[:, :, :k]          # (G, group, k)
+        pos = np.take_along_axis(np.broadcast_to(others, (G, group, group - 1)), pick, axis=2)
+        src = np.take_along_axis(members[:, None, :].repeat(group, axis=1), pos, axis=2)
+        src = np.sort(src, axis=2)
+        parts.append((members.reshape(-1), src.reshape(-1, k)))
+        deg[members.reshape(-1)] = k
+    rest = perm[G * group:]
+    r = rest.size
+    if r >= 2:
+        k = min(links, r - 1)
+        rows = []
+        for p in range(r):
+            cand = np.delete(rest, p)
+            rows.append(np.sort(rng.choice(cand, size=k, replace=False)))
+        parts.append((rest, np.array(rows, np.int64)))
+        deg[rest] = k
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(deg, out=row_ptr[1:])
+    col = np.zeros(int(row_ptr[-1]), np.uint32)
+    for dst, src in parts:
+        kk = src.shape[1]
+        col[row_ptr[dst][:, None] + np.arange(kk)[None, :]] = src
+    return row_ptr.astype(np.uint32), col
+
+
+def population(n: int, seed: int = 0, n_seed_infections: int = 10) -> dict:
+    """Ages, household and occupation CSRs and the initial cases for n agents."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x5EED]))
+    age = rng.integers(0, N_AGE, size=n, dtype=np.uint8)
+    sizes = household_sizes(n, rng)
+    hh_rp, hh_col = household_csr(sizes)
+    oc_rp, oc_col = occupation_csr(n, rng)
+    k = min(int(n_seed_infections), n)
+    seeds = np.sort(rng.choice(n, size=k, replace=False)).astype(np.uint32)
+    return dict(n=n, age=age, row_ptr=[hh_rp, oc_rp], col=[hh_col, oc_col], seed_ids=seeds,
+                household_sizes=sizes)
+
+
+# --------------------------------------------------------------------------- parameters
+def default_params() -> dict:
+    """Placeholder disease parameters.  Names follow Eq. 1: R, S_age (S_a),
+    A_class (A_s for asymptomatic / mild / severe infectors), B_net (B_n per
+    static network: household, occupation), B_rand (random network), inv_Ibar (1/I)."""
+    dur_lo = [[0] * N_AGE for _ in range(8)]
+    dur_hi = [[0] * N_AGE for _ in range(8)]
+    # stage index: 1 asym, 2 presym-mild, 3 presym-severe, 4 mild, 5 severe, 6 hospital, 7 ICU
+    for st, (lo, hi) in {1: (5, 10), 2: (2, 4), 3: (2, 4), 4: (5, 10), 5: (3, 7), 6: (5, 15), 7: (5, 15)}.items():
+        dur_lo[st] = [lo] * N_AGE
+        dur_hi[st] = [hi] * N_AGE
+    return dict(
+        R=3.0, inv_Ibar=1.0 / 14.0, dt=1.0,   # 1/I: I = mean daily interactions (about 14 here)
+        B_net=[2.0, 1.0], B_rand=1.0, rand_mean=2.0,
+        S_age=[1.0] * N_AGE,
+        A_class=[0.5, 1.0, 1.0],
+        inf_shape=[4.0, 4.0, 4.0], inf_scale=[1.25, 1.25, 1.25], inf_len=30,
+        p_asym=[0.45, 0.40, 0.35, 0.30, 0.30, 0.25, 0.20, 0.20, 0.20],
+        p_sev=[0.02, 0.03, 0.05, 0.08, 0.12, 0.18, 0.28, 0.38, 0.50],
+        p_hosp=[0.20, 0.20, 0.25, 0.30, 0.35, 0.40, 0.50, 0.60, 0.70],
+        p_icu=[0.10, 0.10, 0.15, 0.20, 0.25, 0.30, 0.35, 0.40, 0.45],
+        p_death=[0.05, 0.05, 0.10, 0.15, 0.20, 0.30, 0.40, 0.50, 0.60],
+        dur_lo=dur_lo, dur_hi=dur_hi,
+        test_on=0, test_sens=0.95, test_lo=3, test_hi=5,          # RT-PCR (Sec. 4.3)
+        quar_on=0, quar_days=14, q_dropout=0.0,                     # Sec. 4.1
+        vax_on=0, vax_start=30, vax_onset=12, dose2_delay=21,       # Sec. 5
+        vax_rate=0.01, vax_eff1=0.8, vax_eff2=0.95,
+        seed=0, net_seed=0,
+    )
+
+
+def params_with(**kw) -> dict:
+    p = copy.deepcopy(default_params())
+    for k, v in kw.items():
+        if k not in p:
+            raise KeyError(k)
+        p[k] = v
+    return p
+
+
+# --------------------------------------------------------------------------- workloads
+def plain_small():
+    """N=10,000 agents, 60 days, 10 initial cases, seed 0, no interventions."""
+    return dict(name="plain N=1e4 T=60", n=10_000, T=60, n_seed=10, params=params_with())
+
+
+def plain_large():
+    """N=2,000,000 agents, 180 days, 0.5% initial cases, testing + 14-day quarantine
+    of symptomatic agents, vaccination of 1% of agents a day from day 30."""
+    return dict(name="plain N=2e6 T=180", n=2_000_000, T=180, n_seed=10_000,
+                params=params_with(test_on=1, quar_on=1, vax_on=1, vax_start=30, vax_rate=0.01))
+
+
+def batch_params(B: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Per-replicate parameter rows [B, 14] (R ~ U[2,6]; household, occupation and
+    random weights ~ U[0.5,2]; S_age = 1; second-dose delay ~ U{21..84}) and seeds."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0xBA7C]))
+    rp = np.zeros((B, N_REP_PARAMS), np.float32)
+    rp[:, 0] = rng.uniform(2.0, 6.0, B)
+    rp[:, 1:4] = rng.uniform(0.5, 2.0, (B, 3))
+    rp[:, 4:13] = 1.0
+    rp[:, 13] = rng.integers(21, 85, B)
+    seeds = rng.integers(0, 2**63 - 1, B, dtype=np.int64).astype(np.uint64)
+    return rp, seeds
+
+
+def batched():
+    """One N=100,000 graph shared by B=256 replicates, 180 days, vaccination at
+    0.3%/day from day 20 with a per-replicate second-dose delay."""
+    return dict(name="batched N=1e5 B=256 T=180", n=100_000, B=256, T=180, n_seed=10,
+                params=params_with(vax_on=1, vax_start=20, vax_rate=0.003))
