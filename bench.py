@@ -1,0 +1,366 @@
+"""Benchmark: agent interactions per second of the DeepABM-COVID day on GB300.
+
+Default workload (one GPU): the plain simulation at scale, N = 2,000,000 agents,
+household + occupation networks and a Poisson(2) random network regenerated
+each day (about 14.2 messages per agent per day), 0.5% initial cases, testing
+with 14-day quarantine, vaccination of 1%/day from day 30.  A step is one
+simulated day (one launch of the day kernel).  Also reported: the batched
+ensemble (one N = 100,000 graph shared by B = 256 replicates) against a loop of
+plain per-replicate runs.
+
+  python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--gpus N]
+
+Interactions = messages processed (static in-edges + that day's random
+in-contacts, before masking), summed over days and replicates.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2**20
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def step_bytes_plain(n: int, static_edges: int, n_nets: int, vax: bool) -> int:
+    """Algorithmic HBM bytes of one day of the plain kernel: each array once.
+    CSR row pointers 4(N+1) per network, columns 4 per stored edge; state read
+    and written (stage 1, timer 2, tinf 2, flags 1, qt 1 = 7 B each way); age
+    1 B; first-dose day 2 B (vaccination on); emitted infectiousness read once
+    and written once (4 + 4 B).  Random edges are generated, not stored: 0 B."""
+    return 4 * (n + 1) * n_nets + 4 * static_edges + n * (7 + 7 + 1 + (2 if vax else 0) + 4 + 4)
+
+
+def step_bytes_batch(n: int, B: int, static_edges: int, n_nets: int, vax: bool) -> int:
+    """Same for the [N][B] panel: per (agent, replicate) 7 + 7 + 4 + 4 B; per agent
+    age and first-dose day; the CSR once for all replicates."""
+    return 4 * (n + 1) * n_nets + 4 * static_edges + n * (1 + (2 if vax else 0)) + n * B * (7 + 7 + 4 + 4)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_from_profile(kernel_src: str, profile: str, units_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (its sha256 prefix is recorded there); else None."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+        src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if f"source_sha256_16: {src_hash}" not in txt:
+            return None
+        m = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+-]+)", txt)
+        return float(m.group(1)) * units_per_launch if m else None
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Simulation
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = W.plain_large()
+    n, K, Wm = w["n"], args.steps, args.warmup
+    params = dict(w["params"], seed=w["params"]["seed"] + rank, net_seed=w["params"]["net_seed"] + rank)
+    pop = W.population(n, rank, w["n_seed"])
+    static_edges = int(sum(int(rp[-1]) for rp in pop["row_ptr"]))
+    stream = torch.cuda.Stream()
+
+    # ---- device-resident timing: inputs uploaded before the timed region
+    sim = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=Wm + K, stream=stream.cuda_stream)
+    sim.step(Wm)
+    sim.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for d in range(K):
+            sim.step(1)
+            ev[d + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    per_day_ms = [ev[d].elapsed_time(ev[d + 1]) for d in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    _, _, msgs = sim.counters(Wm + K)
+    messages = int(msgs[Wm:].astype(np.int64).sum())
+    sim.close()
+
+    # ---- end to end through the C-ABI with host buffers (create + run + readback)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim2 = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=K, stream=stream.cuda_stream)
+    ni, hist = sim2.run(K)
+    st = sim2.state()
+    _, _, msgs2 = sim2.counters(K)
+    sim2.close()
+    e2e_s = time.perf_counter() - t0
+    e2e_messages = int(msgs2.astype(np.int64).sum())
+    h2d = 4 * (n + 1) * len(pop["row_ptr"]) + 4 * static_edges + n + 4 * len(pop["seed_ids"])
+    d2h = ni.nbytes + hist.nbytes + sum(v.nbytes for v in st.values()) + msgs2.nbytes
+
+    # ---- max over ranks
+    tt = torch.tensor([total_ms, e2e_s, float(messages), float(e2e_messages)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms, e2e_s = float(mx[0]), float(mx[1])
+        messages, e2e_messages = int(sm[2]), int(sm[3])
+
+    # ---- batched ensemble vs plain per-replicate loop (rank 0, a short window)
+    batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
+
+    if rank == 0:
+        value = messages / (total_ms / 1e3)
+        avg_ms = statistics.mean(per_day_ms)
+        alg = step_bytes_plain(n, static_edges, len(pop["row_ptr"]), bool(params["vax_on"]))
+        peak, peak_kind = measured_peak_hbm()
+        achieved = alg / (avg_ms / 1e3) / 1e9
+        kernel_src = os.path.join(ROOT, "paper_2110_04421_gb300", "csrc", "step_kernels.cu")
+        traffic = traffic_from_profile(kernel_src, "step_plain_n2e6.md", n)
+        cpu = None if args.no_cpu_baseline else cpu_baseline(pop, params, args.cpu_seconds)
+        line = {
+            "metric": "agent interactions/s on 1 GB300 (plain day kernel; batched B=256 in 'batched')",
+            "value": value, "unit": "interactions/s", "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded generators shaped like the paper's population)",
+            "config": {"workload": "plain N=2e6 T=180 (households 1-6, occupation groups of 20 x 10 links, "
+                                   "Poisson(2) random network, testing + 14-day quarantine, vaccination 1%/day "
+                                   "from day 30)",
+                       "n_agents": n, "messages_per_day": messages / K / world,
+                       "static_edges": static_edges, "days_timed": f"{Wm}..{Wm + K - 1}",
+                       "l2": f"inputs larger than L2: {alg / 1e6:.0f} MB algorithmic per day vs "
+                             f"{L2_BYTES / 1e6:.0f} MB L2, no flush",
+                       "parallelism": f"{world} independent population(s), one per GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "step_plain_kernel", "alg_bytes_per_launch": alg,
+                         "launch_ms_mean": avg_ms, "launch_ms_min": min(per_day_ms)},
+            "e2e": {"value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / K,
+                    "d2h_bytes_per_step": d2h / K, "seconds": e2e_s},
+            "gpu_launches": K,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        if batched:
+            line["batched"] = batched
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_batched(args):
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Simulation
+
+    w = W.batched()
+    n, B = w["n"], w["B"]
+    Kb = max(3, min(args.batched_steps, args.steps))
+    pop = W.population(n, 0, w["n_seed"])
+    rp, seeds = W.batch_params(B, 0)
+    static_edges = int(sum(int(r[-1]) for r in pop["row_ptr"]))
+    stream = torch.cuda.Stream()
+    sim = Simulation(pop, w["params"], pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds,
+                     max_steps=args.warmup + Kb, stream=stream.cuda_stream)
+    sim.step(args.warmup)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(Kb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, _, msgs = sim.counters()
+    sim.close()
+    msg_b = int(msgs[args.warmup:].astype(np.int64).sum()) * B
+    # plain loop: the same B replicates one after another, same days
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sims = []
+    for r in range(B):
+        pr = dict(w["params"], R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
+                  S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r]))
+        s = Simulation(pop, pr, pop["age"], pop["seed_ids"], max_steps=args.warmup + Kb, stream=stream.cuda_stream)
+        s.step(args.warmup)
+        sims.append(s)
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for s in sims:
+        s.step(Kb)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e2.elapsed_time(e3)
+    for s in sims:
+        s.close()
+    alg = step_bytes_batch(n, B, static_edges, len(pop["row_ptr"]), True)
+    peak, _ = measured_peak_hbm()
+    achieved = alg / (ms / Kb / 1e3) / 1e9
+    value = msg_b / (ms / 1e3)
+    return {"workload": "batched N=1e5 B=256 (R~U[2,6], weights~U[0.5,2], dose-2 delay~U{21..84}, own seeds)",
+            "value": value, "unit": "interactions/s", "ms_per_step": ms / Kb, "steps": Kb,
+            "plain_loop_value": msg_b / (ms_loop / 1e3), "multiple_of_plain_loop": ms_loop / ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "step_batch_kernel", "alg_bytes_per_launch": alg}}
+
+
+# ---------------------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(pop, params, seconds: float):
+    """The oracle, as it stands (single-threaded C), on the same population: whole
+    days from day 0 until about `seconds` of CPU time."""
+    import oracle
+    sim = oracle.Sim(pop, params, pop["age"], pop["seed_ids"])
+    msgs, days = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        d = sim.step(diag=False)
+        msgs += d["messages"]
+        days += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": msgs / el, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"{days} whole days (days 0..{days - 1}) of the same N={pop['n']} population, "
+                      f"{el:.1f} s, single thread", "cpu": cpu_model()}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if "model name" in line:
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_reference(args, rank, world, local):
+    """The oracle arm: each step is one whole oracle day of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2110_04421_gb300 import workloads as W
+    w = W.plain_large()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    sim = oracle.Sim(pop, w["params"], pop["age"], pop["seed_ids"])
+    for _ in range(args.warmup):
+        sim.step(diag=False)
+    msgs = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        msgs += sim.step(diag=False)["messages"]
+    el = time.perf_counter() - t0
+    value = msgs / el
+    line = {"impl": "reference", "metric": "agent interactions/s on 1 GB300 (plain day kernel; batched B=256 in "
+            "'batched')", "value": value, "unit": "interactions/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generators shaped like the paper's population)",
+            "config": {"workload": "plain N=2e6 T=180", "n_agents": w["n"]},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} whole oracle days after {args.warmup} warm-up days",
+                             "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=177)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        import __graft_entry__
+        if local == 0:
+            __graft_entry__.build()
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

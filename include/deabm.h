@@ -1,0 +1,205 @@
+/*
+ * deabm.h -- C ABI of the GB300 (sm_103a) DeepABM-COVID step library, libdeabm.so.
+ *
+ * The library runs the per-day simulation step of DeepABM-COVID (Chopra et al.,
+ * "DeepABM: Scalable, efficient and differentiable agent-based simulations via
+ * graph neural networks", arXiv 2110.04421) on one GPU:
+ *   - Sec. 2.1 / Sec. 3 "Infection Transmission", Eq. 1-2: each interaction i->j
+ *     carries R S_{a_j} A_{s_i} B_n / I * (integral over the day of the gamma
+ *     infectiousness density); messages are summed per destination into lambda_j
+ *     and p_j = 1 - exp(-lambda_j dt) (message passing over the interaction graph);
+ *   - Sec. 3 "Interaction Networks": static household / occupation networks given
+ *     as destination-sorted CSR, plus a random network regenerated every day on
+ *     the device from a counter-based generator (Philox4x32-10);
+ *   - Sec. 3 "Agent State Definition" / "Disease Progression": eleven disease
+ *     stages, integer day timers, Bernoulli infection draw;
+ *   - Sec. 4.1 self-quarantine, Sec. 4.3 testing, Sec. 4.4 / Sec. 5 two-dose
+ *     vaccination.
+ * Points the paper leaves open (stage durations, branch probabilities, random
+ * stream layout, reduction order) follow one written reading; every random
+ * decision is a function of (seed, agent, step, stream), so runs are exactly
+ * reproducible and comparable with an independent implementation.
+ *
+ * Conventions for every entry point
+ *   - Return DEABM_OK (0) or a negative DEABM_E* code; deabm_last_error() gives
+ *     the message.  No entry point aborts the process.
+ *   - Host pointers passed to create are read during the call only (the library
+ *     copies everything it needs to device memory it owns).  Output pointers are
+ *     caller-owned host buffers of the stated size.
+ *   - The CUDA stream is borrowed (cudaStream_t passed as void*; NULL = the
+ *     legacy default stream).  Work is queued on it; deabm_step returns without
+ *     waiting; calls that return host data synchronise the stream.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef DEABM_H
+#define DEABM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DEABM_OK 0
+#define DEABM_EINVAL (-1)   /* invalid argument, graph, state or parameter */
+#define DEABM_ENOMEM (-2)   /* device or host allocation failed */
+#define DEABM_ECUDA (-3)    /* a CUDA call failed (message has the CUDA error) */
+#define DEABM_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define DEABM_ESTATE (-5)   /* call not valid in the context's current state */
+
+#define DEABM_MAX_NETS 4
+#define DEABM_N_AGE 9       /* age bins 0-10, 11-20, ..., 80+ (Sec. 3) */
+#define DEABM_N_STAGE 11    /* disease stages (Sec. 3 "Agent State Definition") */
+#define DEABM_N_CLASS 3     /* infector class: asymptomatic, mild, severe (Eq. 1, s_i) */
+#define DEABM_MAX_INF_LEN 64
+#define DEABM_POIS_CAP 15   /* random in-contacts per agent per day are capped here */
+#define DEABM_N_REP_PARAMS 14
+
+/* stage codes (int8) */
+enum {
+    DEABM_S = 0, DEABM_ASYM = 1, DEABM_PRE_MILD = 2, DEABM_PRE_SEV = 3, DEABM_MILD = 4,
+    DEABM_SEV = 5, DEABM_HOSP = 6, DEABM_ICU = 7, DEABM_REC = 8, DEABM_VAX = 9, DEABM_DEAD = 10
+};
+/* flags byte: dose 1 given, dose 2 given, pending test is positive */
+#define DEABM_FL_DOSE1 0x01u
+#define DEABM_FL_DOSE2 0x02u
+#define DEABM_FL_POS 0x04u
+/* qt byte: bits 0..3 quarantine days left (0 = not quarantined),
+ *          bits 4..6 days until a pending test result (0 = none) */
+
+typedef struct deabm_ctx deabm_ctx;
+
+/* Interaction graph (Sec. 3 "Interaction Networks").
+ * n_nets static networks, each a destination-sorted CSR over n_agents rows:
+ * row_ptr[k] has n_agents+1 entries with row_ptr[k][0] = 0 and non-decreasing
+ * values; col[k] has row_ptr[k][n_agents] entries, each a source agent id
+ * < n_agents and != its row (no self-loops).  Edge j <- col[e] for
+ * e in [row_ptr[j], row_ptr[j+1]).  The in-edges of a row are summed in the
+ * order listed.  rand_mean > 0 adds the daily random network: each agent j
+ * receives K_j ~ Poisson(rand_mean) (capped at DEABM_POIS_CAP) in-contacts
+ * drawn uniformly from the other agents, regenerated every day. */
+typedef struct {
+    uint32_t n_agents;
+    uint32_t n_nets;
+    const uint32_t *row_ptr[DEABM_MAX_NETS];
+    const uint32_t *col[DEABM_MAX_NETS];
+    float rand_mean;
+} deabm_graph;
+
+/* Agents (Sec. 3 "Agent State Definition"); all host arrays of n_agents entries.
+ * age_bin is required (0..8).  The dynamic state arrays may be NULL, meaning all
+ * susceptible with zero timers.  seed_ids lists agents infected before day 0
+ * (ignored for agents that are not susceptible). */
+typedef struct {
+    const uint8_t *age_bin;
+    const int8_t *stage;
+    const int16_t *timer;
+    const int16_t *tinf;
+    const uint8_t *flags;
+    const uint8_t *qt;
+    const uint32_t *seed_ids;
+    uint32_t n_seed;
+} deabm_agents;
+
+/* Model parameters.  Eq. 1 names: R, S_age (S_a), A_class (A_s), B_net (B_n),
+ * inv_Ibar (1/I).  The infectiousness curve of class c is a gamma density of
+ * shape inf_shape[c] and scale inf_scale[c], integrated over each day since
+ * infection t = 1..inf_len-1 (day 0 and days >= inf_len contribute 0).
+ * Probabilities are doubles in [0,1]; an event of probability p happens when
+ * its 32-bit random word is < floor(p * 2^32).  dur_lo/dur_hi[stage][age]
+ * bound the integer stage duration in days (stages 1..7; uniform on the range).
+ * Test result delays are uniform on test_lo..test_hi days (1 <= lo <= hi <= 7);
+ * quar_days <= 15.  Vaccination: from day vax_start, floor(vax_rate * N) first
+ * doses a day in priority order (age bin descending, then id ascending) to
+ * agents not in hospital, ICU or dead; the second dose dose2_delay days later;
+ * a susceptible agent becomes immune (stage VAX) vax_onset days after a dose
+ * when its per-agent vaccine word is below floor(eff * 2^32) of that dose.
+ * seed keys the per-agent draws, net_seed the daily random network. */
+typedef struct {
+    float R, inv_Ibar, dt;
+    float B_net[DEABM_MAX_NETS];
+    float B_rand;
+    float S_age[DEABM_N_AGE];
+    float A_class[DEABM_N_CLASS];
+    double inf_shape[DEABM_N_CLASS], inf_scale[DEABM_N_CLASS];
+    uint32_t inf_len;
+    double p_asym[DEABM_N_AGE], p_sev[DEABM_N_AGE], p_hosp[DEABM_N_AGE];
+    double p_icu[DEABM_N_AGE], p_death[DEABM_N_AGE];
+    uint8_t dur_lo[8][DEABM_N_AGE], dur_hi[8][DEABM_N_AGE];
+    uint32_t test_on;
+    double test_sens;
+    uint32_t test_lo, test_hi;
+    uint32_t quar_on, quar_days;
+    double q_dropout;
+    uint32_t vax_on, vax_start, vax_onset, dose2_delay;
+    double vax_rate, vax_eff1, vax_eff2;
+    uint64_t seed, net_seed;
+    uint32_t max_steps;   /* capacity of the per-day counters (0 = 1024) */
+    uint32_t keep_lambda; /* 1: keep lambda_j and p_j of the last day for deabm_get_state */
+} deabm_params;
+
+/* Create a plain (one replicate) simulation.  Validates the graph (monotone
+ * row_ptr, col < n_agents, no self-loops, < 2^32 edges), the agents (age bins,
+ * stage codes) and the parameters, copies everything to the device on `stream`,
+ * builds the infectiousness table and the vaccination schedule there, and
+ * infects seed_ids.  On success *out owns all device memory it allocated.
+ * Errors: DEABM_EINVAL, DEABM_ENOMEM, DEABM_ECUDA. */
+int deabm_create(const deabm_graph *graph, const deabm_agents *agents, const deabm_params *params,
+                 void *cuda_stream, deabm_ctx **out);
+
+/* Create a batch of n_rep replicates sharing one graph (state laid out [N][n_rep],
+ * replicate fastest).  rep_params is a host [n_rep][14] float array:
+ * R, B_net[0], B_net[1], B_rand, S_age[0..8], dose2_delay (whole days); the
+ * other parameters come from `base`.  rep_seeds [n_rep] keys each replicate's
+ * per-agent draws; all replicates share the day's random network (base->net_seed).
+ * Replicate r reproduces deabm_create with those parameters and seed exactly.
+ * 1 <= n_rep <= 1024. */
+int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, const deabm_params *base,
+                       uint32_t n_rep, const float *rep_params, const uint64_t *rep_seeds,
+                       void *cuda_stream, deabm_ctx **out);
+
+/* Queue n_steps days on the context's stream and return without waiting.
+ * DEABM_ESTATE if the day counter would pass max_steps. */
+int deabm_step(deabm_ctx *ctx, uint32_t n_steps);
+
+/* Run T days, then copy the per-day counters of those days to the host and
+ * synchronise.  new_inf: host int32 [T][n_rep] new infections per day;
+ * hist: host int32 [T][n_rep][11] stage counts after each day, or NULL. */
+int deabm_run(deabm_ctx *ctx, uint32_t T, int32_t *new_inf, int32_t *hist);
+
+/* Copy the current state (host arrays of n_agents * n_rep entries; any may be
+ * NULL) and, if params.keep_lambda was set, lambda and p of the last day.
+ * Synchronises the stream. */
+int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags,
+                    uint8_t *qt, float *lambda, float *p);
+
+/* Per-day counters already run: days [0, day_count) of new infections
+ * [day][n_rep], stage histogram [day][n_rep][11] and messages processed
+ * [day] (static in-edges + that day's random in-contacts, per replicate).
+ * Any output may be NULL.  Synchronises. */
+int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *new_inf, int32_t *hist,
+                       uint64_t *messages);
+
+/* Tables the device built: infectiousness [3][inf_len] (FP32), Poisson CDF
+ * thresholds [15], first-dose day per agent [n_agents] (0x7FFF = never).
+ * Any output may be NULL.  Synchronises. */
+int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *poisson_thr, int16_t *dose1_day);
+
+/* Days run so far, agents, replicates. */
+int deabm_info(const deabm_ctx *ctx, uint32_t *day, uint32_t *n_agents, uint32_t *n_rep);
+
+/* Wait for all queued work on the context's stream. */
+int deabm_sync(deabm_ctx *ctx);
+
+/* Message of the last error on ctx (or of the calling thread when ctx is NULL).
+ * The string stays valid until the next call on the same ctx / thread. */
+const char *deabm_last_error(const deabm_ctx *ctx);
+
+/* Free all device memory of ctx.  NULL-safe. */
+void deabm_destroy(deabm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEABM_H */

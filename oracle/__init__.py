@@ -40,6 +40,13 @@ STAGES = ("S", "ASYM", "PRE_MILD", "PRE_SEV", "MILD", "SEV", "HOSP", "ICU", "REC
 def build(force: bool = False) -> str:
     """Compile the oracle's C into ``oracle/_build/liboracle.so`` (gcc, -O2, no FMA contraction)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
+    import fcntl
+    with open(os.path.join(_OUT_DIR, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        return _build_locked(force)
+
+
+def _build_locked(force: bool) -> str:
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH

@@ -1,0 +1,464 @@
+// deabm_api.cu -- the C ABI of libdeabm (declared in include/deabm.h): context
+// creation and validation, device memory ownership, the day loop, readback.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "deabm.h"
+#include "deabm_device.cuh"
+#include "kernels.h"
+
+using namespace deabm;
+
+struct deabm_ctx {
+    cudaStream_t stream = nullptr;
+    uint32_t n = 0, n_nets = 0, n_rep = 1, max_steps = 0, day = 0;
+    uint64_t static_edges = 0;
+    bool keep_lambda = false;
+    std::vector<void *> allocs;
+    uint32_t *row_ptr[DEABM_MAX_NETS] = {};
+    uint32_t *col[DEABM_MAX_NETS] = {};
+    uint8_t *age = nullptr;
+    int16_t *dose1 = nullptr;
+    StateRef S{};
+    float *inf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *lam = nullptr, *p = nullptr;
+    Tables *tab = nullptr;
+    Rep *rep = nullptr;
+    Counters C{};
+    KParams kp{};
+    std::string err;
+};
+
+static thread_local std::string g_err;
+
+static int fail(deabm_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    g_err = buf;
+    return code;
+}
+
+#define CU(ctx, call)                                                                                    \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? DEABM_ENOMEM : DEABM_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                             \
+    } while (0)
+
+template <class T>
+static int dalloc(deabm_ctx *ctx, T **out, size_t count)
+{
+    void *ptr = nullptr;
+    const size_t bytes = count ? count * sizeof(T) : sizeof(T);
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(ptr);
+    *out = (T *)ptr;
+    return DEABM_OK;
+}
+
+static uint64_t threshold(double p)
+{
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+static bool prob_ok(double p) { return p >= 0.0 && p <= 1.0; }
+
+// ---------------------------------------------------------------- validation
+static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a, const deabm_params *p,
+                    uint32_t n_rep, const float *rep_params)
+{
+    if (!g || !a || !p) return fail(ctx, DEABM_EINVAL, "graph, agents and params are required");
+    const uint32_t n = g->n_agents;
+    if (n == 0 || n >= (1u << 31)) return fail(ctx, DEABM_EINVAL, "n_agents must be in [1, 2^31)");
+    if (g->n_nets > DEABM_MAX_NETS) return fail(ctx, DEABM_EINVAL, "n_nets > %d", DEABM_MAX_NETS);
+    if (!(g->rand_mean >= 0.0f) || g->rand_mean > 1e3f) return fail(ctx, DEABM_EINVAL, "rand_mean out of range");
+    if (g->rand_mean > 0.0f && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
+    if ((uint64_t)n * n_rep >= (1ull << 40)) return fail(ctx, DEABM_EINVAL, "n_agents * n_rep too large");
+    for (uint32_t k = 0; k < g->n_nets; ++k) {
+        const uint32_t *rp = g->row_ptr[k], *col = g->col[k];
+        if (!rp) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] is NULL", k);
+        if (rp[0] != 0) return fail(ctx, DEABM_EINVAL, "row_ptr[%u][0] != 0", k);
+        for (uint32_t j = 0; j < n; ++j)
+            if (rp[j + 1] < rp[j]) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] decreases at row %u", k, j);
+        if (rp[n] > 0 && !col) return fail(ctx, DEABM_EINVAL, "col[%u] is NULL", k);
+        for (uint32_t j = 0; j < n; ++j)
+            for (uint32_t e = rp[j]; e < rp[j + 1]; ++e) {
+                if (col[e] >= n) return fail(ctx, DEABM_EINVAL, "col[%u][%u] = %u >= n_agents", k, e, col[e]);
+                if (col[e] == j) return fail(ctx, DEABM_EINVAL, "self-loop at row %u of network %u", j, k);
+            }
+    }
+    if (!a->age_bin) return fail(ctx, DEABM_EINVAL, "age_bin is required");
+    for (uint32_t j = 0; j < n; ++j)
+        if (a->age_bin[j] >= DEABM_N_AGE) return fail(ctx, DEABM_EINVAL, "age_bin[%u] = %u > 8", j, a->age_bin[j]);
+    if (a->stage)
+        for (uint32_t j = 0; j < n; ++j)
+            if (a->stage[j] < 0 || a->stage[j] >= DEABM_N_STAGE)
+                return fail(ctx, DEABM_EINVAL, "stage[%u] = %d is not a stage code", j, a->stage[j]);
+    if (a->qt)
+        for (uint32_t j = 0; j < n; ++j)
+            if (a->qt[j] & 0x80u) return fail(ctx, DEABM_EINVAL, "qt[%u] has bit 7 set", j);
+    if (a->n_seed && !a->seed_ids) return fail(ctx, DEABM_EINVAL, "seed_ids is NULL");
+    for (uint32_t q = 0; q < a->n_seed; ++q)
+        if (a->seed_ids[q] >= n) return fail(ctx, DEABM_EINVAL, "seed_ids[%u] >= n_agents", q);
+    if (p->inf_len == 0 || p->inf_len > DEABM_MAX_INF_LEN) return fail(ctx, DEABM_EINVAL, "inf_len must be 1..64");
+    for (int c = 0; c < DEABM_N_CLASS; ++c)
+        if (!(p->inf_shape[c] > 0.0) || !(p->inf_scale[c] > 0.0))
+            return fail(ctx, DEABM_EINVAL, "gamma shape and scale must be > 0");
+    if (!(p->dt >= 0.0f)) return fail(ctx, DEABM_EINVAL, "dt must be >= 0");
+    for (int q = 0; q < DEABM_N_AGE; ++q)
+        if (!prob_ok(p->p_asym[q]) || !prob_ok(p->p_sev[q]) || !prob_ok(p->p_hosp[q]) || !prob_ok(p->p_icu[q]) ||
+            !prob_ok(p->p_death[q]))
+            return fail(ctx, DEABM_EINVAL, "branch probabilities must be in [0,1]");
+    for (int st = DEABM_ASYM; st <= DEABM_ICU; ++st)
+        for (int q = 0; q < DEABM_N_AGE; ++q)
+            if (p->dur_lo[st][q] < 1 || p->dur_hi[st][q] < p->dur_lo[st][q])
+                return fail(ctx, DEABM_EINVAL, "stage %d durations need 1 <= lo <= hi", st);
+    if (p->test_lo < 1 || p->test_hi > 7 || p->test_lo > p->test_hi)
+        return fail(ctx, DEABM_EINVAL, "test delays need 1 <= test_lo <= test_hi <= 7");
+    if (p->quar_days > 15) return fail(ctx, DEABM_EINVAL, "quar_days must be <= 15");
+    if (!prob_ok(p->test_sens) || !prob_ok(p->q_dropout) || !prob_ok(p->vax_eff1) || !prob_ok(p->vax_eff2) ||
+        !(p->vax_rate >= 0.0 && p->vax_rate <= 1.0))
+        return fail(ctx, DEABM_EINVAL, "probabilities and rates must be in [0,1]");
+    if (p->vax_on && (p->vax_onset < 1 || p->dose2_delay < 1))
+        return fail(ctx, DEABM_EINVAL, "vax_onset and dose2_delay must be >= 1");
+    if (n_rep < 1 || n_rep > 1024) return fail(ctx, DEABM_EINVAL, "n_rep must be in 1..1024");
+    if (rep_params)
+        for (uint32_t b = 0; b < n_rep; ++b) {
+            const float d = rep_params[b * DEABM_N_REP_PARAMS + 13];
+            if (!(d >= 1.0f && d <= 30000.0f) || d != std::floor(d))
+                return fail(ctx, DEABM_EINVAL, "replicate %u: dose2_delay must be a whole number of days >= 1", b);
+        }
+    return DEABM_OK;
+}
+
+// ---------------------------------------------------------------- creation
+static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_params *p, uint32_t n_rep,
+                       const float *rep_params, const uint64_t *rep_seeds, void *stream, deabm_ctx **out)
+{
+    if (!out) return fail(nullptr, DEABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    deabm_ctx *ctx = new (std::nothrow) deabm_ctx();
+    if (!ctx) return fail(nullptr, DEABM_ENOMEM, "host allocation failed");
+    int rc = validate(ctx, g, a, p, n_rep, rep_params);
+    if (rc == DEABM_OK) {
+        rc = [&]() -> int {
+            ctx->stream = (cudaStream_t)stream;
+            const uint32_t n = g->n_agents;
+            const size_t nb = (size_t)n * n_rep;
+            ctx->n = n;
+            ctx->n_nets = g->n_nets;
+            ctx->n_rep = n_rep;
+            ctx->max_steps = p->max_steps ? p->max_steps : 1024u;
+            ctx->keep_lambda = p->keep_lambda != 0;
+            cudaStream_t s = ctx->stream;
+            int r;
+            for (uint32_t k = 0; k < g->n_nets; ++k) {
+                const uint32_t E = g->row_ptr[k][n];
+                ctx->static_edges += E;
+                if ((r = dalloc(ctx, &ctx->row_ptr[k], (size_t)n + 1))) return r;
+                if ((r = dalloc(ctx, &ctx->col[k], E))) return r;
+                CU(ctx, cudaMemcpyAsync(ctx->row_ptr[k], g->row_ptr[k], sizeof(uint32_t) * ((size_t)n + 1),
+                                        cudaMemcpyHostToDevice, s));
+                if (E) CU(ctx, cudaMemcpyAsync(ctx->col[k], g->col[k], sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
+            }
+            if ((r = dalloc(ctx, &ctx->age, n))) return r;
+            if ((r = dalloc(ctx, &ctx->dose1, n))) return r;
+            if ((r = dalloc(ctx, &ctx->S.stage, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S.timer, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S.tinf, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S.flags, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S.qt, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
+            if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
+            if (ctx->keep_lambda) {
+                if ((r = dalloc(ctx, &ctx->lam, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->p, nb))) return r;
+                CU(ctx, cudaMemsetAsync(ctx->lam, 0, sizeof(float) * nb, s));
+                CU(ctx, cudaMemsetAsync(ctx->p, 0, sizeof(float) * nb, s));
+            }
+            if ((r = dalloc(ctx, &ctx->tab, 1))) return r;
+            if ((r = dalloc(ctx, &ctx->rep, n_rep))) return r;
+            const size_t days = ctx->max_steps;
+            if ((r = dalloc(ctx, &ctx->C.new_inf, days * n_rep))) return r;
+            if ((r = dalloc(ctx, &ctx->C.hist, days * n_rep * DEABM_N_STAGE))) return r;
+            if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
+            CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * n_rep, s));
+            CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
+            CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+
+            // agents: [N] -> [N][n_rep] by repeating each agent's initial state per replicate
+            CU(ctx, cudaMemcpyAsync(ctx->age, a->age_bin, n, cudaMemcpyHostToDevice, s));
+            std::vector<int8_t> st(nb, 0);
+            std::vector<int16_t> tm(nb, 0), ti(nb, 0);
+            std::vector<uint8_t> fl(nb, 0), qt(nb, 0);
+            for (uint32_t j = 0; j < n; ++j)
+                for (uint32_t b = 0; b < n_rep; ++b) {
+                    const size_t i = (size_t)j * n_rep + b;
+                    if (a->stage) st[i] = a->stage[j];
+                    if (a->timer) tm[i] = a->timer[j];
+                    if (a->tinf) ti[i] = a->tinf[j];
+                    if (a->flags) fl[i] = a->flags[j];
+                    if (a->qt) qt[i] = a->qt[j];
+                }
+            CU(ctx, cudaMemcpyAsync(ctx->S.stage, st.data(), nb, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S.timer, tm.data(), nb * 2, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S.tinf, ti.data(), nb * 2, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S.flags, fl.data(), nb, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S.qt, qt.data(), nb, cudaMemcpyHostToDevice, s));
+
+            // per-replicate parameters
+            std::vector<Rep> reps(n_rep);
+            for (uint32_t b = 0; b < n_rep; ++b) {
+                Rep &R = reps[b];
+                float Rv = p->R, Bn[DEABM_MAX_NETS], Br = p->B_rand, Sa[DEABM_N_AGE];
+                uint32_t delay = p->dose2_delay;
+                for (int k = 0; k < DEABM_MAX_NETS; ++k) Bn[k] = p->B_net[k];
+                for (int q = 0; q < DEABM_N_AGE; ++q) Sa[q] = p->S_age[q];
+                if (rep_params) {
+                    const float *rp = rep_params + (size_t)b * DEABM_N_REP_PARAMS;
+                    Rv = rp[0]; Bn[0] = rp[1]; Bn[1] = rp[2]; Br = rp[3];
+                    for (int q = 0; q < DEABM_N_AGE; ++q) Sa[q] = rp[4 + q];
+                    delay = (uint32_t)rp[13];
+                }
+                volatile float rv = Rv, ib = p->inv_Ibar;  // one FP32 product, no contraction
+                R.cR = rv * ib;
+                for (int k = 0; k < DEABM_MAX_NETS; ++k) R.B_net[k] = Bn[k];
+                R.B_rand = Br;
+                for (int q = 0; q < DEABM_N_AGE; ++q) R.S_age[q] = Sa[q];
+                R.dose2_delay = delay;
+                R.seed = rep_seeds ? rep_seeds[b] : p->seed;
+            }
+            CU(ctx, cudaMemcpyAsync(ctx->rep, reps.data(), sizeof(Rep) * n_rep, cudaMemcpyHostToDevice, s));
+
+            // host-side integer tables (thresholds are exact: p * 2^32 then floor)
+            Tables T;
+            std::memset(&T, 0, sizeof T);
+            {
+                // Poisson CDF: t_0 = exp(-m), t_k = (t_{k-1} * m) / k, c_k = c_{k-1} + t_k
+                const double m = (double)g->rand_mean;
+                volatile double t = std::exp(-m), c = t;
+                T.pois[0] = threshold(c);
+                for (int k = 1; k < DEABM_POIS_CAP; ++k) {
+                    t = (t * m) / (double)k;
+                    c = c + t;
+                    T.pois[k] = threshold(c);
+                }
+            }
+            for (int q = 0; q < DEABM_N_AGE; ++q) {
+                T.thr_asym[q] = threshold(p->p_asym[q]);
+                T.thr_sev[q] = threshold(p->p_sev[q]);
+                T.thr_branch[DEABM_SEV][q] = threshold(p->p_hosp[q]);
+                T.thr_branch[DEABM_HOSP][q] = threshold(p->p_icu[q]);
+                T.thr_branch[DEABM_ICU][q] = threshold(p->p_death[q]);
+            }
+            std::memcpy(T.dur_lo, p->dur_lo, sizeof T.dur_lo);
+            std::memcpy(T.dur_hi, p->dur_hi, sizeof T.dur_hi);
+            CU(ctx, cudaMemcpyAsync(ctx->tab, &T, sizeof T, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaStreamSynchronize(s));  // host staging buffers above go out of scope
+
+            // device-built tables: infectiousness (FP64 integrals), vaccination days
+            double *d_gamma;
+            float *d_A;
+            uint32_t *d_scratch, *d_ids = nullptr;
+            if ((r = dalloc(ctx, &d_gamma, 6))) return r;
+            if ((r = dalloc(ctx, &d_A, 3))) return r;
+            if ((r = dalloc(ctx, &d_scratch, dose1_scratch_words(n)))) return r;
+            const double gs[6] = {p->inf_shape[0], p->inf_shape[1], p->inf_shape[2],
+                                  p->inf_scale[0], p->inf_scale[1], p->inf_scale[2]};
+            CU(ctx, cudaMemcpyAsync(d_gamma, gs, sizeof gs, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(d_A, p->A_class, sizeof(float) * 3, cudaMemcpyHostToDevice, s));
+            CU(ctx, launch_inf_table(ctx->tab, d_gamma, d_A, p->inf_len, s));
+            const uint32_t per_day = p->vax_on ? (uint32_t)std::floor(p->vax_rate * (double)n) : 0u;
+            CU(ctx, launch_dose1_days(ctx->age, n, p->vax_start, per_day, ctx->dose1, d_scratch, s));
+
+            KParams &K = ctx->kp;
+            K.n = n;
+            K.n_nets = g->n_nets;
+            K.n_rep = n_rep;
+            K.inf_len = p->inf_len;
+            K.dt = p->dt;
+            K.rand_on = g->rand_mean > 0.0f ? 1u : 0u;
+            for (uint32_t k = 0; k < DEABM_MAX_NETS; ++k) {
+                K.row_ptr[k] = ctx->row_ptr[k];
+                K.col[k] = ctx->col[k];
+            }
+            K.net_seed = p->net_seed;
+            K.test_on = p->test_on;
+            K.test_lo = p->test_lo;
+            K.test_hi = p->test_hi;
+            K.quar_on = p->quar_on;
+            K.quar_days = p->quar_days;
+            K.thr_sens = threshold(p->test_sens);
+            K.thr_qdrop = threshold(p->q_dropout);
+            K.vax_on = p->vax_on;
+            K.vax_onset = p->vax_onset;
+            K.thr_eff1 = threshold(p->vax_eff1);
+            K.thr_eff2 = threshold(p->vax_eff2);
+            K.tab = ctx->tab;
+            K.rep = ctx->rep;
+            K.age = ctx->age;
+            K.dose1_day = ctx->dose1;
+
+            if (a->n_seed) {
+                if ((r = dalloc(ctx, &d_ids, a->n_seed))) return r;
+                CU(ctx, cudaMemcpyAsync(d_ids, a->seed_ids, sizeof(uint32_t) * a->n_seed, cudaMemcpyHostToDevice, s));
+                CU(ctx, launch_seed(K, d_ids, a->n_seed, ctx->S, s));
+            }
+            CU(ctx, launch_emit(K, ctx->S, ctx->inf[0], s));
+            CU(ctx, cudaStreamSynchronize(s));
+            return DEABM_OK;
+        }();
+    }
+    if (rc != DEABM_OK) {
+        std::string msg = ctx->err;
+        deabm_destroy(ctx);
+        g_err = msg;
+        return rc;
+    }
+    *out = ctx;
+    return DEABM_OK;
+}
+
+extern "C" int deabm_create(const deabm_graph *graph, const deabm_agents *agents, const deabm_params *params,
+                            void *cuda_stream, deabm_ctx **out)
+{
+    return create_impl(graph, agents, params, 1u, nullptr, nullptr, cuda_stream, out);
+}
+
+extern "C" int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, const deabm_params *base,
+                                  uint32_t n_rep, const float *rep_params, const uint64_t *rep_seeds,
+                                  void *cuda_stream, deabm_ctx **out)
+{
+    if (!rep_params || !rep_seeds) return fail(nullptr, DEABM_EINVAL, "rep_params and rep_seeds are required");
+    return create_impl(graph, agents, base, n_rep, rep_params, rep_seeds, cuda_stream, out);
+}
+
+// ---------------------------------------------------------------- the day loop
+extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if ((uint64_t)ctx->day + n_steps > ctx->max_steps)
+        return fail(ctx, DEABM_ESTATE, "day %u + %u steps exceeds max_steps %u", ctx->day, n_steps, ctx->max_steps);
+    for (uint32_t s = 0; s < n_steps; ++s) {
+        CU(ctx, launch_step(ctx->kp, ctx->day, ctx->inf[ctx->cur], ctx->inf[ctx->cur ^ 1], ctx->S, ctx->C,
+                            ctx->keep_lambda ? ctx->lam : nullptr, ctx->p, ctx->stream));
+        ctx->cur ^= 1;
+        ctx->day += 1;
+    }
+    return DEABM_OK;
+}
+
+extern "C" int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *new_inf, int32_t *hist,
+                                  uint64_t *messages)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (day_count > ctx->day) return fail(ctx, DEABM_EINVAL, "only %u days have run", ctx->day);
+    const size_t B = ctx->n_rep;
+    if (new_inf && day_count)
+        CU(ctx, cudaMemcpyAsync(new_inf, ctx->C.new_inf, sizeof(int32_t) * day_count * B, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+    if (hist && day_count)
+        CU(ctx, cudaMemcpyAsync(hist, ctx->C.hist, sizeof(int32_t) * day_count * B * DEABM_N_STAGE,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    if (messages && day_count)
+        CU(ctx, cudaMemcpyAsync(messages, ctx->C.msgs, sizeof(uint64_t) * day_count, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (messages)
+        for (uint32_t d = 0; d < day_count; ++d) messages[d] += ctx->static_edges;
+    return DEABM_OK;
+}
+
+extern "C" int deabm_run(deabm_ctx *ctx, uint32_t T, int32_t *new_inf, int32_t *hist)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    const uint32_t d0 = ctx->day;
+    int rc = deabm_step(ctx, T);
+    if (rc) return rc;
+    const size_t B = ctx->n_rep;
+    if (new_inf && T)
+        CU(ctx, cudaMemcpyAsync(new_inf, ctx->C.new_inf + (size_t)d0 * B, sizeof(int32_t) * T * B,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    if (hist && T)
+        CU(ctx, cudaMemcpyAsync(hist, ctx->C.hist + (size_t)d0 * B * DEABM_N_STAGE,
+                                sizeof(int32_t) * T * B * DEABM_N_STAGE, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags,
+                               uint8_t *qt, float *lambda, float *p)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if ((lambda || p) && !ctx->keep_lambda) return fail(ctx, DEABM_ESTATE, "created without keep_lambda");
+    const size_t nb = (size_t)ctx->n * ctx->n_rep;
+    cudaStream_t s = ctx->stream;
+    if (stage) CU(ctx, cudaMemcpyAsync(stage, ctx->S.stage, nb, cudaMemcpyDeviceToHost, s));
+    if (timer) CU(ctx, cudaMemcpyAsync(timer, ctx->S.timer, nb * 2, cudaMemcpyDeviceToHost, s));
+    if (tinf) CU(ctx, cudaMemcpyAsync(tinf, ctx->S.tinf, nb * 2, cudaMemcpyDeviceToHost, s));
+    if (flags) CU(ctx, cudaMemcpyAsync(flags, ctx->S.flags, nb, cudaMemcpyDeviceToHost, s));
+    if (qt) CU(ctx, cudaMemcpyAsync(qt, ctx->S.qt, nb, cudaMemcpyDeviceToHost, s));
+    if (lambda) CU(ctx, cudaMemcpyAsync(lambda, ctx->lam, nb * 4, cudaMemcpyDeviceToHost, s));
+    if (p) CU(ctx, cudaMemcpyAsync(p, ctx->p, nb * 4, cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *poisson_thr, int16_t *dose1_day)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    Tables T;
+    CU(ctx, cudaMemcpyAsync(&T, ctx->tab, sizeof T, cudaMemcpyDeviceToHost, ctx->stream));
+    if (dose1_day) CU(ctx, cudaMemcpyAsync(dose1_day, ctx->dose1, 2ull * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (inf_table)
+        for (int c = 0; c < DEABM_N_CLASS; ++c)
+            std::memcpy(inf_table + (size_t)c * ctx->kp.inf_len, T.infT[c], sizeof(float) * ctx->kp.inf_len);
+    if (poisson_thr) std::memcpy(poisson_thr, T.pois, sizeof T.pois);
+    return DEABM_OK;
+}
+
+extern "C" int deabm_info(const deabm_ctx *ctx, uint32_t *day, uint32_t *n_agents, uint32_t *n_rep)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (day) *day = ctx->day;
+    if (n_agents) *n_agents = ctx->n;
+    if (n_rep) *n_rep = ctx->n_rep;
+    return DEABM_OK;
+}
+
+extern "C" int deabm_sync(deabm_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return DEABM_OK;
+}
+
+extern "C" const char *deabm_last_error(const deabm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+extern "C" void deabm_destroy(deabm_ctx *ctx)
+{
+    if (!ctx) return;
+    if (!ctx->allocs.empty()) (void)cudaStreamSynchronize(ctx->stream);
+    for (void *ptr : ctx->allocs) (void)cudaFree(ptr);
+    delete ctx;
+}

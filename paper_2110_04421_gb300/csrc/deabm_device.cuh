@@ -1,0 +1,196 @@
+// deabm_device.cuh -- device-side pieces shared by the step kernels of libdeabm.
+//
+// Philox4x32-10, the per-context parameter block, and the per-agent state
+// machine (Sec. 3 "Disease Progression", Sec. 4 interventions) of DeepABM-COVID.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "deabm.h"
+
+namespace deabm {
+
+// Philox counter word 2 ("stream") layout; counter = (agent, day, stream, block)
+enum : uint32_t {
+    kStreamInf = 0,    // x: infection uniform, y: quarantine dropout
+    kStreamProg = 1,   // x: asymptomatic?, y: stage duration, z: severe?, w: secondary branch
+    kStreamRnet = 3,   // random network: word 0 = contact count, words 1.. = contacts
+    kStreamTest = 5,   // x: test positive?, y: result delay
+    kStreamVax = 7,    // x: vaccine response (day word fixed at 0)
+    kStreamGumbel = 8, // relaxed draw noise
+};
+constexpr uint32_t kSeedDay = 0xFFFFFFFFu;  // day word of the infections before day 0
+constexpr int16_t kNever = 0x7FFF;
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+__device__ __forceinline__ uint2 seed_key(uint64_t s) { return make_uint2((uint32_t)s, (uint32_t)(s >> 32)); }
+__device__ __forceinline__ uint4 draw(uint2 key, uint32_t agent, uint32_t day, uint32_t stream, uint32_t blk = 0)
+{
+    return philox(make_uint4(agent, day, stream, blk), key);
+}
+// 24-bit uniform in [0,1), exact in FP32
+__device__ __forceinline__ float unit_float(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ uint32_t uniform_int(uint32_t w, uint32_t lo, uint32_t hi)
+{
+    return lo + (uint32_t)(((uint64_t)w * (uint64_t)(hi - lo + 1u)) >> 32);
+}
+
+// ---------------------------------------------------------------- parameter blocks
+// Tables with per-thread dynamic indices live in device global memory (L1-resident).
+struct Tables {
+    float infT[DEABM_N_CLASS][DEABM_MAX_INF_LEN];  // A_class folded in: A_c * infT_c[t]
+    uint64_t pois[DEABM_POIS_CAP];
+    uint64_t thr_asym[DEABM_N_AGE], thr_sev[DEABM_N_AGE];
+    uint64_t thr_branch[8][DEABM_N_AGE];   // by stage: SEV->HOSP, HOSP->ICU, ICU->DEAD
+    uint8_t dur_lo[8][DEABM_N_AGE], dur_hi[8][DEABM_N_AGE];
+};
+
+// per replicate (n_rep entries; plain runs have one)
+struct Rep {
+    float cR;                    // R * inv_Ibar (FP32 product)
+    float B_net[DEABM_MAX_NETS];
+    float B_rand;
+    float S_age[DEABM_N_AGE];
+    uint32_t dose2_delay;
+    uint64_t seed;
+};
+
+// by-value kernel argument
+struct KParams {
+    uint32_t n, n_nets, n_rep, inf_len;
+    float dt;
+    uint32_t rand_on;
+    const uint32_t *row_ptr[DEABM_MAX_NETS];
+    const uint32_t *col[DEABM_MAX_NETS];
+    uint64_t net_seed;
+    uint32_t test_on, test_lo, test_hi, quar_on, quar_days;
+    uint64_t thr_sens, thr_qdrop;
+    uint32_t vax_on, vax_onset;
+    uint64_t thr_eff1, thr_eff2;
+    const Tables *tab;
+    const Rep *rep;
+    const uint8_t *age;
+    const int16_t *dose1_day;
+};
+
+struct StateRef {
+    int8_t *stage;
+    int16_t *timer, *tinf;
+    uint8_t *flags, *qt;
+};
+
+struct Counters {
+    int32_t *new_inf;          // [day][n_rep]
+    int32_t *hist;             // [day][n_rep][11]
+    unsigned long long *msgs;  // [day] random in-contacts (static edges added on the host)
+};
+
+// ---------------------------------------------------------------- state machine
+struct AgentState {
+    int st, tm, ti;
+    uint32_t fl, qd, cd;
+};
+
+__device__ __forceinline__ int infector_class(int st)
+{
+    // asymptomatic -> 0; presymptomatic/symptomatic mild -> 1; severe -> 2; others none
+    return st == DEABM_ASYM ? 0
+         : (st == DEABM_PRE_MILD || st == DEABM_MILD) ? 1
+         : (st == DEABM_PRE_SEV || st == DEABM_SEV) ? 2 : -1;
+}
+
+// infectiousness an agent emits on a day: A_c * infT_c[tinf], zero when quarantined
+__device__ __forceinline__ float emitted(const Tables *tab, uint32_t L, int st, int ti, uint32_t qd)
+{
+    const int c = infector_class(st);
+    if (c < 0 || qd != 0u || ti < 0 || (uint32_t)ti >= L) return 0.0f;
+    return __ldg(&tab->infT[c][ti]);
+}
+
+__device__ __forceinline__ void new_infection(const Tables *tab, int age, uint4 w, AgentState &a)
+{
+    if ((uint64_t)w.x < __ldg(&tab->thr_asym[age])) a.st = DEABM_ASYM;
+    else if ((uint64_t)w.z < __ldg(&tab->thr_sev[age])) a.st = DEABM_PRE_SEV;
+    else a.st = DEABM_PRE_MILD;
+    a.tm = (int)uniform_int(w.y, __ldg(&tab->dur_lo[a.st][age]), __ldg(&tab->dur_hi[a.st][age]));
+    a.ti = 1;
+}
+
+// One day's update of one agent (everything after the infection draw).
+// `infected` = the draw succeeded this day; `day` is the day index.
+__device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 key, uint32_t j, uint32_t day,
+                                        int age, int16_t d1, bool infected, AgentState &a, uint32_t inf_y)
+{
+    bool onset = false;
+    if (infected) {
+        new_infection(P.tab, age, draw(key, j, day, kStreamProg), a);
+    } else if (a.st >= DEABM_ASYM && a.st <= DEABM_ICU) {
+        a.ti = a.ti < 32767 ? a.ti + 1 : 32767;
+        a.tm -= 1;
+        if (a.tm <= 0) {
+            const uint4 w = draw(key, j, day, kStreamProg);
+            int nx;
+            switch (a.st) {
+            case DEABM_PRE_MILD: nx = DEABM_MILD; onset = true; break;
+            case DEABM_PRE_SEV: nx = DEABM_SEV; onset = true; break;
+            case DEABM_SEV: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_SEV][age]) ? DEABM_HOSP : DEABM_REC; break;
+            case DEABM_HOSP: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_HOSP][age]) ? DEABM_ICU : DEABM_REC; break;
+            case DEABM_ICU: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_ICU][age]) ? DEABM_DEAD : DEABM_REC; break;
+            default: nx = DEABM_REC; break;  // asymptomatic, mild
+            }
+            a.st = nx;
+            a.tm = (nx >= DEABM_ASYM && nx <= DEABM_ICU)
+                       ? (int)uniform_int(w.y, __ldg(&P.tab->dur_lo[nx][age]), __ldg(&P.tab->dur_hi[nx][age]))
+                       : 0;
+        }
+    }
+    // quarantine in progress: daily dropout, else one day served (Sec. 4.1)
+    if (a.qd > 0u) {
+        if ((uint64_t)inf_y < P.thr_qdrop) a.qd = 0u;
+        else a.qd -= 1u;
+    }
+    // pending test result, or a test at symptom onset (Sec. 4.3)
+    if (a.cd > 0u) {
+        a.cd -= 1u;
+        if (a.cd == 0u) {
+            if ((a.fl & DEABM_FL_POS) && P.quar_on) a.qd = P.quar_days;
+            a.fl &= ~DEABM_FL_POS;
+        }
+    } else if (onset && P.test_on && a.qd == 0u) {
+        const uint4 w = draw(key, j, day, kStreamTest);
+        if ((uint64_t)w.x < P.thr_sens) a.fl |= DEABM_FL_POS;
+        else a.fl &= ~DEABM_FL_POS;
+        a.cd = uniform_int(w.y, P.test_lo, P.test_hi);
+    }
+    // two-dose vaccination (Sec. 4.4, Sec. 5)
+    if (P.vax_on && d1 != kNever) {
+        const int64_t t = day, D1 = d1, D2 = D1 + (int64_t)rp.dose2_delay;
+        const bool elig = !(a.st == DEABM_HOSP || a.st == DEABM_ICU || a.st == DEABM_DEAD);
+        if (t == D1 && elig) a.fl |= DEABM_FL_DOSE1;
+        if ((a.fl & DEABM_FL_DOSE1) && t == D2 && elig) a.fl |= DEABM_FL_DOSE2;
+        if (a.st == DEABM_S && !infected) {
+            const bool on1 = (a.fl & DEABM_FL_DOSE1) && t == D1 + (int64_t)P.vax_onset;
+            const bool on2 = (a.fl & DEABM_FL_DOSE2) && t == D2 + (int64_t)P.vax_onset;
+            if (on1 || on2) {
+                const uint32_t v = draw(key, j, 0u, kStreamVax).x;
+                if (on1 && (uint64_t)v < P.thr_eff1) a.st = DEABM_VAX;
+                else if (on2 && (uint64_t)v < P.thr_eff2) a.st = DEABM_VAX;
+            }
+        }
+    }
+}
+
+}  // namespace deabm

@@ -1,0 +1,25 @@
+// kernels.h -- host-side launchers of libdeabm's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "deabm_device.cuh"
+
+namespace deabm {
+
+// one simulated day: reads inf_cur and the state, writes the state, inf_next and the day's counters
+cudaError_t launch_step(const KParams &P, uint32_t day, const float *inf_cur, float *inf_next, const StateRef &S,
+                        const Counters &C, float *lam_out, float *p_out, cudaStream_t stream);
+
+// set-up: infectiousness table (FP64 gamma integrals, rounded once, times A_class)
+cudaError_t launch_inf_table(Tables *tab, const double *shape_scale /*device [6]*/, const float *A_class /*device [3]*/,
+                             uint32_t len, cudaStream_t stream);
+// set-up: first-dose day of every agent from the age-priority order
+cudaError_t launch_dose1_days(const uint8_t *age, uint32_t n, uint32_t start, uint32_t per_day, int16_t *out,
+                              uint32_t *scratch /*device, 9 * (blocks + 1) + 9 words*/, cudaStream_t stream);
+size_t dose1_scratch_words(uint32_t n);
+// set-up: infections before day 0 for every replicate
+cudaError_t launch_seed(const KParams &P, const uint32_t *ids, uint32_t n_ids, const StateRef &S, cudaStream_t stream);
+// set-up: emitted infectiousness of the current state
+cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, cudaStream_t stream);
+
+}  // namespace deabm

@@ -1,0 +1,247 @@
+// step_kernels.cu -- one simulated day of DeepABM-COVID on the GPU.
+//
+// A day (Sec. 3 "Infection Transmission", Eq. 1-2) is one kernel launch:
+//   for every destination agent j (and replicate b in batched runs)
+//     H_{n,j}  = sum of inf_src over the CSR in-edges of j in static network n,
+//                in CSR order (left to right from +0.0f, no FMA contraction)
+//     Rn_j     = sum of inf_src over the K_j ~ Poisson random in-contacts of
+//                the day, generated here from Philox (never stored)
+//     lambda_j = (R/I * S_{age_j}) * (B_0 H_0 + B_1 H_1 + ... + B_r Rn_j)
+//     p_j      = 1 - exp(-lambda_j dt), infected iff susceptible and u_j < p_j
+//   then the agent's stage/timer machine and interventions, the agent's emitted
+//   infectiousness for the next day (written to the other half of a double
+//   buffer), and the day's counters (block-aggregated atomics).
+// The emitted-infectiousness vector of the day being read (4 B per agent per
+// replicate) stays L2-resident; the CSR column stream is the HBM traffic.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "deabm_device.cuh"
+#include "kernels.h"
+
+namespace deabm {
+
+// fl32(1 - exp(-x)) correctly rounded: the decision u < p uses this value.
+// expm1f (<= 2 ulp) decides every draw whose u is more than 2^-21 away from
+// p; the rest take the FP64 value rounded once to FP32.
+__device__ __forceinline__ bool infection_decision(float lam_dt, float u, float *p_out)
+{
+    const float p = -expm1f(-lam_dt);
+    if (fabsf(u - p) > 4.76837158203125e-07f) {  // 2^-21
+        *p_out = p;
+        return u < p;
+    }
+    const float pe = (float)(-expm1(-(double)lam_dt));
+    *p_out = pe;
+    return u < pe;
+}
+
+__device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                                         const float *__restrict__ inf, uint32_t j, uint32_t stride, uint32_t b)
+{
+    uint32_t e = __ldg(rp + j);
+    const uint32_t end = __ldg(rp + j + 1);
+    float h = 0.0f;
+    for (; e + 4u <= end; e += 4u) {
+        const uint32_t c0 = __ldg(col + e), c1 = __ldg(col + e + 1), c2 = __ldg(col + e + 2), c3 = __ldg(col + e + 3);
+        const float v0 = __ldg(inf + (size_t)c0 * stride + b), v1 = __ldg(inf + (size_t)c1 * stride + b);
+        const float v2 = __ldg(inf + (size_t)c2 * stride + b), v3 = __ldg(inf + (size_t)c3 * stride + b);
+        h = __fadd_rn(h, v0);
+        h = __fadd_rn(h, v1);
+        h = __fadd_rn(h, v2);
+        h = __fadd_rn(h, v3);
+    }
+    for (; e < end; ++e) h = __fadd_rn(h, __ldg(inf + (size_t)__ldg(col + e) * stride + b));
+    return h;
+}
+
+// Random in-contacts of agent j on `day`: count from word 0 of block 0, contact e
+// from word e+1 (block (e+1)/4, lane (e+1)%4); v uniform on the other n-1 agents.
+__device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
+                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out)
+{
+    const uint2 nk = seed_key(P.net_seed);
+    uint4 w = draw(nk, j, day, kStreamRnet, 0u);
+    uint32_t k = 0;
+    while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
+    float r = 0.0f;
+    const uint64_t nm1 = (uint64_t)(P.n - 1u);
+    for (uint32_t e = 0; e < k; ++e) {
+        const uint32_t idx = e + 1u;
+        if ((idx & 3u) == 0u) w = draw(nk, j, day, kStreamRnet, idx >> 2);
+        const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+        uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
+        v += (v >= j) ? 1u : 0u;
+        r = __fadd_rn(r, __ldg(inf + (size_t)v * stride + b));
+    }
+    *k_out = k;
+    return r;
+}
+
+// lambda_j of one (agent, replicate) from the state of the day
+__device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const float *__restrict__ inf, uint32_t j,
+                                           uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out)
+{
+    float s = 0.0f;
+    for (uint32_t net = 0; net < P.n_nets; ++net) {
+        const float h = csr_sum(P.row_ptr[net], P.col[net], inf, j, stride, b);
+        const float term = __fmul_rn(rp.B_net[net], h);
+        s = net == 0 ? term : __fadd_rn(s, term);
+    }
+    *k_out = 0;
+    if (P.rand_on) {
+        const float r = random_sum(P, inf, j, day, stride, b, k_out);
+        const float term = __fmul_rn(rp.B_rand, r);
+        s = P.n_nets == 0 ? term : __fadd_rn(s, term);
+    }
+    return __fmul_rn(__fmul_rn(rp.cR, rp.S_age[age]), s);
+}
+
+// Full day for one (agent j, replicate b) at flat index i = j*stride + b.
+__device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const float *__restrict__ inf_cur,
+                                          float *__restrict__ inf_next, const StateRef &S, uint32_t j, uint32_t stride,
+                                          uint32_t b, float *lam_out, float *p_out, int *new_stage, bool *infected,
+                                          uint32_t *k_out)
+{
+    const size_t i = (size_t)j * stride + b;
+    const int age = __ldg(P.age + j);
+    const float lam = lambda_of(P, rp, inf_cur, j, day, stride, b, age, k_out);
+    AgentState a;
+    a.st = S.stage[i];
+    a.tm = S.timer[i];
+    a.ti = S.tinf[i];
+    a.fl = S.flags[i];
+    const uint32_t q = S.qt[i];
+    a.qd = q & 0x0Fu;
+    a.cd = (q >> 4) & 0x07u;
+    const uint2 key = seed_key(rp.seed);
+    bool inf_now = false;
+    uint32_t inf_y = 0;
+    float p = 0.0f;
+    if (a.st == DEABM_S || a.qd > 0u || lam_out != nullptr) {
+        const uint4 w = draw(key, j, day, kStreamInf);
+        inf_y = w.y;
+        const bool hit = infection_decision(__fmul_rn(lam, P.dt), unit_float(w.x), &p);
+        inf_now = (a.st == DEABM_S) && hit;
+    }
+    const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
+    advance(P, rp, key, j, day, age, d1, inf_now, a, inf_y);
+    S.stage[i] = (int8_t)a.st;
+    S.timer[i] = (int16_t)a.tm;
+    S.tinf[i] = (int16_t)a.ti;
+    S.flags[i] = (uint8_t)a.fl;
+    S.qt[i] = (uint8_t)((a.qd & 0x0Fu) | ((a.cd & 0x07u) << 4));
+    inf_next[i] = emitted(P.tab, P.inf_len, a.st, a.ti, a.qd);
+    if (lam_out) {
+        lam_out[i] = lam;
+        p_out[i] = p;
+    }
+    *new_stage = a.st;
+    *infected = inf_now;
+}
+
+// block-level aggregation of the day's counters; every thread of the block calls it
+__device__ __forceinline__ void count_day(bool active, int st, bool infected, uint32_t k, int *s_hist, int *s_new,
+                                          unsigned long long *s_msgs)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    const unsigned act = __ballot_sync(full, active);
+    const int lane = threadIdx.x & 31;
+    if (active) {
+        const unsigned m = __match_any_sync(act, st);
+        if (lane == __ffs(m) - 1) atomicAdd(&s_hist[st], __popc(m));
+    }
+    const unsigned nb = __ballot_sync(full, infected);
+    if (lane == 0 && nb) atomicAdd(s_new, __popc(nb));
+    const unsigned ks = __reduce_add_sync(full, active ? k : 0u);
+    if (lane == 0 && ks) atomicAdd(s_msgs, (unsigned long long)ks);
+}
+
+template <bool KEEP>
+__global__ void __launch_bounds__(256) step_plain_kernel(const KParams P, uint32_t day, const float *__restrict__ inf_cur,
+                                                         float *__restrict__ inf_next, StateRef S, Counters C,
+                                                         float *lam_out, float *p_out)
+{
+    __shared__ int s_hist[DEABM_N_STAGE];
+    __shared__ int s_new;
+    __shared__ unsigned long long s_msgs;
+    if (threadIdx.x < DEABM_N_STAGE) s_hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; }
+    __syncthreads();
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = j < P.n;
+    int st = 0;
+    bool infected = false;
+    uint32_t k = 0;
+    if (active) {
+        const Rep &rp = P.rep[0];
+        agent_day(P, rp, day, inf_cur, inf_next, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+    }
+    count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
+    __syncthreads();
+    if (threadIdx.x < DEABM_N_STAGE && s_hist[threadIdx.x])
+        atomicAdd(&C.hist[(size_t)day * DEABM_N_STAGE + threadIdx.x], s_hist[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        if (s_new) atomicAdd(&C.new_inf[day], s_new);
+        if (s_msgs) atomicAdd(&C.msgs[day], s_msgs);
+    }
+}
+
+// Batched panel: block (32 x 8) covers 8 agents x 32 replicates; lane = replicate.
+// The 32 lanes of a warp read the same CSR entries (one broadcast load) and
+// gather one contiguous 128 B run of the [N][B] infectiousness panel per edge.
+template <bool KEEP>
+__global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32_t day, const float *__restrict__ inf_cur,
+                                                         float *__restrict__ inf_next, StateRef S, Counters C,
+                                                         float *lam_out, float *p_out)
+{
+    // per (stage or new-infection, replicate lane) counts of the block's 8 agent rows
+    __shared__ int s_cnt[DEABM_N_STAGE + 1][32];
+    __shared__ unsigned long long s_msgs;
+    const uint32_t lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32u + lane;
+    const uint32_t j = blockIdx.x * 8u + wy;
+    const uint32_t b = blockIdx.y * 32u + lane;
+    for (uint32_t q = tid; q < (DEABM_N_STAGE + 1) * 32u; q += 256u) (&s_cnt[0][0])[q] = 0;
+    if (tid == 0) s_msgs = 0ull;
+    __syncthreads();
+    const bool active = (j < P.n) && (b < P.n_rep);
+    int st = 0;
+    bool infected = false;
+    uint32_t k = 0;
+    if (active) {
+        const Rep &rp = P.rep[b];
+        agent_day(P, rp, day, inf_cur, inf_next, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        atomicAdd(&s_cnt[st][lane], 1);
+        if (infected) atomicAdd(&s_cnt[DEABM_N_STAGE][lane], 1);
+    }
+    // messages are counted once per agent row (lane 0 of the first replicate panel)
+    if (lane == 0 && blockIdx.y == 0 && j < P.n && k) atomicAdd(&s_msgs, (unsigned long long)k);
+    __syncthreads();
+    for (uint32_t q = tid; q < (DEABM_N_STAGE + 1) * 32u; q += 256u) {
+        const uint32_t s = q / 32u, l = q % 32u, bb = blockIdx.y * 32u + l;
+        const int v = s_cnt[s][l];
+        if (v && bb < P.n_rep) {
+            if (s < DEABM_N_STAGE) atomicAdd(&C.hist[((size_t)day * P.n_rep + bb) * DEABM_N_STAGE + s], v);
+            else atomicAdd(&C.new_inf[(size_t)day * P.n_rep + bb], v);
+        }
+    }
+    if (tid == 0 && s_msgs) atomicAdd(&C.msgs[day], s_msgs);
+}
+
+cudaError_t launch_step(const KParams &P, uint32_t day, const float *inf_cur, float *inf_next, const StateRef &S,
+                        const Counters &C, float *lam_out, float *p_out, cudaStream_t stream)
+{
+    if (P.n_rep == 1) {
+        const dim3 grid((P.n + 255u) / 256u);
+        if (lam_out) step_plain_kernel<true><<<grid, 256, 0, stream>>>(P, day, inf_cur, inf_next, S, C, lam_out, p_out);
+        else step_plain_kernel<false><<<grid, 256, 0, stream>>>(P, day, inf_cur, inf_next, S, C, nullptr, nullptr);
+    } else {
+        const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
+        const dim3 block(32, 8);
+        if (lam_out) step_batch_kernel<true><<<grid, block, 0, stream>>>(P, day, inf_cur, inf_next, S, C, lam_out, p_out);
+        else step_batch_kernel<false><<<grid, block, 0, stream>>>(P, day, inf_cur, inf_next, S, C, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace deabm

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libdeabm.so (include/deabm.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library is missing, loading
+it raises.  PyTorch, when present, supplies the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdeabm.so")
+
+MAX_NETS, N_AGE, N_STAGE, N_CLASS, POIS_CAP, N_REP_PARAMS = 4, 9, 11, 3, 15, 14
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+STAGES = ("S", "ASYM", "PRE_MILD", "PRE_SEV", "MILD", "SEV", "HOSP", "ICU", "REC", "VAX", "DEAD")
+
+EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "deabm_get_state",
+           "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_last_error",
+           "deabm_destroy")
+
+
+class DeabmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"deabm error {code}: {msg}")
+        self.code = code
+
+
+class Graph(C.Structure):
+    _fields_ = [("n_agents", C.c_uint32), ("n_nets", C.c_uint32),
+                ("row_ptr", C.c_void_p * MAX_NETS), ("col", C.c_void_p * MAX_NETS),
+                ("rand_mean", C.c_float)]
+
+
+class Agents(C.Structure):
+    _fields_ = [("age_bin", C.c_void_p), ("stage", C.c_void_p), ("timer", C.c_void_p), ("tinf", C.c_void_p),
+                ("flags", C.c_void_p), ("qt", C.c_void_p), ("seed_ids", C.c_void_p), ("n_seed", C.c_uint32)]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("R", C.c_float), ("inv_Ibar", C.c_float), ("dt", C.c_float),
+        ("B_net", C.c_float * MAX_NETS), ("B_rand", C.c_float),
+        ("S_age", C.c_float * N_AGE), ("A_class", C.c_float * N_CLASS),
+        ("inf_shape", C.c_double * N_CLASS), ("inf_scale", C.c_double * N_CLASS), ("inf_len", C.c_uint32),
+        ("p_asym", C.c_double * N_AGE), ("p_sev", C.c_double * N_AGE), ("p_hosp", C.c_double * N_AGE),
+        ("p_icu", C.c_double * N_AGE), ("p_death", C.c_double * N_AGE),
+        ("dur_lo", (C.c_uint8 * N_AGE) * 8), ("dur_hi", (C.c_uint8 * N_AGE) * 8),
+        ("test_on", C.c_uint32), ("test_sens", C.c_double), ("test_lo", C.c_uint32), ("test_hi", C.c_uint32),
+        ("quar_on", C.c_uint32), ("quar_days", C.c_uint32), ("q_dropout", C.c_double),
+        ("vax_on", C.c_uint32), ("vax_start", C.c_uint32), ("vax_onset", C.c_uint32), ("dose2_delay", C.c_uint32),
+        ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
+        ("seed", C.c_uint64), ("net_seed", C.c_uint64),
+        ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdeabm.so (build it with ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        vp, u32 = C.c_void_p, C.c_uint32
+        L.deabm_create.argtypes = [C.POINTER(Graph), C.POINTER(Agents), C.POINTER(Params), vp, C.POINTER(vp)]
+        L.deabm_create_batch.argtypes = [C.POINTER(Graph), C.POINTER(Agents), C.POINTER(Params), u32, vp, vp, vp,
+                                         C.POINTER(vp)]
+        L.deabm_step.argtypes = [vp, u32]
+        L.deabm_run.argtypes = [vp, u32, vp, vp]
+        L.deabm_get_state.argtypes = [vp] + [vp] * 7
+        L.deabm_get_counters.argtypes = [vp, u32, vp, vp, vp]
+        L.deabm_get_tables.argtypes = [vp, vp, vp, vp]
+        L.deabm_info.argtypes = [vp, vp, vp, vp]
+        L.deabm_sync.argtypes = [vp]
+        L.deabm_last_error.argtypes = [vp]
+        L.deabm_last_error.restype = C.c_char_p
+        L.deabm_destroy.argtypes = [vp]
+        L.deabm_destroy.restype = None
+        for name in ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "deabm_get_state",
+                     "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(rc, ctx=None):
+    if rc != OK:
+        msg = lib().deabm_last_error(ctx).decode(errors="replace")
+        raise DeabmError(rc, msg)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(0)
+
+
+def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False) -> Params:
+    p = Params()
+    p.R, p.inv_Ibar, p.dt = P["R"], P["inv_Ibar"], P["dt"]
+    for i in range(MAX_NETS):
+        p.B_net[i] = P["B_net"][i] if i < len(P["B_net"]) else 0.0
+    p.B_rand = P["B_rand"]
+    for i in range(N_AGE):
+        p.S_age[i] = P["S_age"][i]
+    for c in range(N_CLASS):
+        p.A_class[c] = P["A_class"][c]
+        p.inf_shape[c] = P["inf_shape"][c]
+        p.inf_scale[c] = P["inf_scale"][c]
+    p.inf_len = P["inf_len"]
+    for name in ("p_asym", "p_sev", "p_hosp", "p_icu", "p_death"):
+        arr = getattr(p, name)
+        for i in range(N_AGE):
+            arr[i] = P[name][i]
+    for st in range(8):
+        for a in range(N_AGE):
+            p.dur_lo[st][a] = P["dur_lo"][st][a]
+            p.dur_hi[st][a] = P["dur_hi"][st][a]
+    for name in ("test_on", "test_sens", "test_lo", "test_hi", "quar_on", "quar_days", "q_dropout", "vax_on",
+                 "vax_start", "vax_onset", "dose2_delay", "vax_rate", "vax_eff1", "vax_eff2", "seed", "net_seed"):
+        setattr(p, name, P[name])
+    p.max_steps = max_steps
+    p.keep_lambda = 1 if keep_lambda else 0
+    return p
+
+
+class Simulation:
+    """A DeepABM-COVID simulation living on the GPU (one context of libdeabm).
+
+    ``graph``: dict with ``n``, ``row_ptr`` and ``col`` (lists of u32 arrays, one
+    per static network) and the parameters' ``rand_mean``; ``age``: u8 [n];
+    ``seed_ids``: initial cases.  ``n_rep > 1`` with ``rep_params [n_rep, 14]``
+    and ``rep_seeds [n_rep]`` creates a batch of replicates sharing the graph.
+    """
+
+    def __init__(self, graph: dict, params: dict, age, seed_ids=None, state: dict | None = None,
+                 n_rep: int = 1, rep_params=None, rep_seeds=None, keep_lambda: bool = False,
+                 max_steps: int = 1024, stream=None):
+        L = lib()
+        self.n = int(graph["n"])
+        self.n_rep = int(n_rep)
+        keep = []
+        g = Graph()
+        g.n_agents = self.n
+        g.n_nets = len(graph["row_ptr"])
+        for i, (rp, cl) in enumerate(zip(graph["row_ptr"], graph["col"])):
+            rp = np.ascontiguousarray(rp, dtype=np.uint32)
+            cl = np.ascontiguousarray(cl, dtype=np.uint32)
+            keep += [rp, cl]
+            g.row_ptr[i] = rp.ctypes.data
+            g.col[i] = cl.ctypes.data if cl.size else None
+        g.rand_mean = params["rand_mean"]
+        a = Agents()
+        age = np.ascontiguousarray(age, dtype=np.uint8)
+        keep.append(age)
+        a.age_bin = age.ctypes.data
+        if state is not None:
+            for k, dt in (("stage", np.int8), ("timer", np.int16), ("tinf", np.int16), ("flags", np.uint8),
+                          ("qt", np.uint8)):
+                arr = np.ascontiguousarray(state[k], dtype=dt)
+                keep.append(arr)
+                setattr(a, k, arr.ctypes.data)
+        if seed_ids is not None and len(seed_ids):
+            ids = np.ascontiguousarray(seed_ids, dtype=np.uint32)
+            keep.append(ids)
+            a.seed_ids = ids.ctypes.data
+            a.n_seed = ids.size
+        p = make_params(params, max_steps=max_steps, keep_lambda=keep_lambda)
+        self._stream = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
+        ctx = C.c_void_p()
+        if self.n_rep == 1 and rep_params is None:
+            rc = L.deabm_create(C.byref(g), C.byref(a), C.byref(p), self._stream, C.byref(ctx))
+        else:
+            rp = np.ascontiguousarray(rep_params, dtype=np.float32).reshape(self.n_rep, N_REP_PARAMS)
+            rs = np.ascontiguousarray(rep_seeds, dtype=np.uint64).reshape(self.n_rep)
+            keep += [rp, rs]
+            rc = L.deabm_create_batch(C.byref(g), C.byref(a), C.byref(p), self.n_rep, _p(rp), _p(rs),
+                                      self._stream, C.byref(ctx))
+        _check(rc)
+        self.ctx = ctx
+        self.keep_lambda = keep_lambda
+
+    # -- the day loop
+    def step(self, n_steps: int = 1):
+        _check(lib().deabm_step(self.ctx, n_steps), self.ctx)
+
+    def run(self, T: int, hist: bool = True):
+        B = self.n_rep
+        ni = np.zeros((T, B), np.int32)
+        h = np.zeros((T, B, N_STAGE), np.int32) if hist else None
+        _check(lib().deabm_run(self.ctx, T, _p(ni), _p(h)), self.ctx)
+        return ni, h
+
+    def sync(self):
+        _check(lib().deabm_sync(self.ctx), self.ctx)
+
+    # -- readback
+    @property
+    def day(self) -> int:
+        d = C.c_uint32()
+        _check(lib().deabm_info(self.ctx, C.byref(d), None, None), self.ctx)
+        return d.value
+
+    def state(self, with_lambda: bool = False) -> dict:
+        nb = self.n * self.n_rep
+        out = dict(stage=np.zeros(nb, np.int8), timer=np.zeros(nb, np.int16), tinf=np.zeros(nb, np.int16),
+                   flags=np.zeros(nb, np.uint8), qt=np.zeros(nb, np.uint8))
+        lam = p = None
+        if with_lambda:
+            lam, p = np.zeros(nb, np.float32), np.zeros(nb, np.float32)
+            out["lambda"], out["p"] = lam, p
+        _check(lib().deabm_get_state(self.ctx, _p(out["stage"]), _p(out["timer"]), _p(out["tinf"]),
+                                     _p(out["flags"]), _p(out["qt"]), _p(lam), _p(p)), self.ctx)
+        if self.n_rep > 1:
+            out = {k: v.reshape(self.n, self.n_rep) for k, v in out.items()}
+        return out
+
+    def counters(self, days: int | None = None):
+        days = self.day if days is None else days
+        B = self.n_rep
+        ni = np.zeros((days, B), np.int32)
+        h = np.zeros((days, B, N_STAGE), np.int32)
+        m = np.zeros(days, np.uint64)
+        _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
+        return ni, h, m
+
+    def tables(self, inf_len: int):
+        t = np.zeros((N_CLASS, inf_len), np.float32)
+        pois = np.zeros(POIS_CAP, np.uint64)
+        d1 = np.zeros(self.n, np.int16)
+        _check(lib().deabm_get_tables(self.ctx, _p(t), _p(pois), _p(d1)), self.ctx)
+        return t, pois, d1
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().deabm_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every entry point include/deabm.h declares, and create() rejects invalid
+inputs during host validation, before any CUDA call."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_04421_gb300 import build, deabm
+    build.build()
+    return deabm.lib()
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(deabm_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert {"deabm_create", "deabm_step", "deabm_run", "deabm_destroy"} <= names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def _graph(n, rp, col, rand_mean=2.0):
+    from paper_2110_04421_gb300.deabm import Graph
+    g = Graph()
+    g.n_agents, g.n_nets, g.rand_mean = n, 1, rand_mean
+    g.row_ptr[0] = rp.ctypes.data
+    g.col[0] = col.ctypes.data
+    return g
+
+
+def _create(lib, n, rp, col, age, params=None, rand_mean=2.0, stage=None):
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Agents, make_params
+    g = _graph(n, rp, col, rand_mean)
+    a = Agents()
+    a.age_bin = age.ctypes.data
+    if stage is not None:
+        a.stage = stage.ctypes.data
+    p = make_params(params or W.params_with())
+    ctx = C.c_void_p()
+    rc = lib.deabm_create(C.byref(g), C.byref(a), C.byref(p), None, C.byref(ctx))
+    return rc, ctx, lib.deabm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case", ["self_loop", "col_out_of_range", "row_ptr_decreases", "row_ptr_start",
+                                  "bad_age", "bad_stage", "bad_test_delay", "bad_quarantine", "bad_prob",
+                                  "random_net_single_agent"])
+def test_create_rejects_invalid_input(lib, case):
+    from paper_2110_04421_gb300 import workloads as W
+    n = 4
+    rp = np.array([0, 1, 2, 3, 4], np.uint32)
+    col = np.array([1, 2, 3, 0], np.uint32)
+    age = np.zeros(n, np.uint8)
+    params, stage, rand_mean = None, None, 2.0
+    if case == "self_loop":
+        col[2] = 2
+    elif case == "col_out_of_range":
+        col[1] = 4
+    elif case == "row_ptr_decreases":
+        rp = np.array([0, 2, 1, 3, 4], np.uint32)
+    elif case == "row_ptr_start":
+        rp = np.array([1, 1, 2, 3, 4], np.uint32)
+    elif case == "bad_age":
+        age[3] = 9
+    elif case == "bad_stage":
+        stage = np.array([0, 11, 0, 0], np.int8)
+    elif case == "bad_test_delay":
+        params = W.params_with(test_lo=0)
+    elif case == "bad_quarantine":
+        params = W.params_with(quar_days=16)
+    elif case == "bad_prob":
+        params = W.params_with(p_sev=[1.5] * 9)
+    elif case == "random_net_single_agent":
+        n, rp, col, age = 1, np.array([0, 0], np.uint32), np.zeros(1, np.uint32), np.zeros(1, np.uint8)
+    rc, ctx, msg = _create(lib, n, rp, col, age, params, rand_mean, stage)
+    assert rc == -1, (case, rc, msg)
+    assert ctx.value is None and msg
+
+
+def test_null_arguments(lib):
+    ctx = C.c_void_p()
+    assert lib.deabm_create(None, None, None, None, C.byref(ctx)) == -1
+    assert lib.deabm_step(None, 1) == -1
+    assert lib.deabm_run(None, 1, None, None) == -1
+    lib.deabm_destroy(None)  # NULL-safe
+    assert b"NULL" in lib.deabm_last_error(None)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2110_04421_gb300 import deabm
+    monkeypatch.setattr(deabm, "_lib", None)
+    monkeypatch.setattr(deabm, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        deabm.lib()

@@ -1,0 +1,149 @@
+"""CUDA path (through the C-ABI) against the CPU oracle, element by element.
+
+Bar: stages, timers, flags and counters bit-exact; lambda bit-exact against the
+oracle's FP32 path (same CSR order, no FMA) and within 1e-5 relative of its FP64
+path; the only tolerated infection-draw difference is |u - p| < 1e-6 (counted,
+and it ends the comparison)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_04421_gb300 import workloads as W
+from tests.helpers import compare_days, gpu_available, gpu_sim, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+if not gpu_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_device_tables_match_oracle():
+    pop = W.population(5000, 1, 10)
+    for p in (W.params_with(vax_on=1, vax_start=7, vax_rate=0.013),
+              W.params_with(inf_shape=[2.5, 4.0, 6.7], inf_scale=[2.0, 1.25, 0.9], A_class=[0.3, 1.0, 1.7],
+                            inf_len=40, rand_mean=3.7, vax_on=1, vax_rate=0.002)):
+        g = gpu_sim(pop, p)
+        try:
+            t, pois, d1 = g.tables(p["inf_len"])
+        finally:
+            g.close()
+        _, t32 = oracle.Model(pop, p).inf_table()
+        want = np.float32(p["A_class"])[:, None] * t32          # A_c * infT_c[t] in FP32
+        assert np.array_equal(t.view(np.uint32), want.view(np.uint32)), np.nonzero(t != want)
+        assert np.array_equal(pois, oracle.poisson_thresholds(float(np.float32(p["rand_mean"]))))  # FP32 parameter
+        assert np.array_equal(d1, oracle.vax_days(pop["age"], p["vax_start"], p["vax_rate"]))
+
+
+def test_plain_small_workload_60_days():
+    """N=10,000, 60 days, 10 initial cases, seed 0 (the small plain workload)."""
+    w = W.plain_small()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    rep = compare_days(pop, w["params"], w["T"])
+    assert rep["flips"] == 0 and rep["days"] == w["T"], rep
+    assert rep["max_rel_lambda64"] <= 1e-5
+    assert sum(rep["new_inf"]) > 1000
+
+
+def test_interventions_all_on():
+    pop = W.population(6001, 2, 40)
+    p = W.params_with(test_on=1, quar_on=1, q_dropout=0.07, vax_on=1, vax_start=10, vax_rate=0.02,
+                      dose2_delay=17, R=4.5, seed=77, net_seed=78, S_age=[0.5, 0.7, 0.9, 1.0, 1.1, 1.2, 1.3, 1.4, 1.6])
+    rep = compare_days(pop, p, 100)
+    assert rep["flips"] == 0 and rep["days"] == 100, rep
+    assert rep["max_rel_lambda64"] <= 1e-5
+
+
+@pytest.mark.parametrize("n", [2, 3, 31, 257, 1001])
+def test_ragged_and_tiny_populations(n):
+    pop = W.population(n, 5, max(1, n // 10))
+    p = W.params_with(R=6.0, rand_mean=2.5, test_on=1, quar_on=1)
+    rep = compare_days(pop, p, 30)
+    assert rep["flips"] == 0 and rep["days"] == 30
+
+
+def test_no_networks_and_no_random_network():
+    pop = W.population(700, 6, 20)
+    empty = dict(pop, row_ptr=[], col=[])
+    rep = compare_days(empty, W.params_with(rand_mean=3.0), 20)
+    assert rep["days"] == 20
+    rep = compare_days(pop, W.params_with(rand_mean=0.0, R=8.0), 25)
+    assert rep["days"] == 25
+    one = dict(n=1, age=np.array([4], np.uint8), row_ptr=[np.zeros(2, np.uint32)], col=[np.zeros(0, np.uint32)],
+               seed_ids=np.array([0], np.uint32))
+    rep = compare_days(one, W.params_with(rand_mean=0.0), 15)
+    assert rep["days"] == 15
+
+
+def test_high_degree_rows_and_many_nets():
+    """One household of 300 (in-degree 299) plus four networks."""
+    rng = np.random.default_rng(3)
+    n = 1200
+    sizes = np.array([300] + [4] * 225)
+    hh_rp, hh_col = W.household_csr(sizes)
+    oc_rp, oc_col = W.occupation_csr(n, rng, group=50, links=40)
+    x_rp, x_col = W.occupation_csr(n, rng, group=7, links=3)
+    pop = dict(n=n, age=rng.integers(0, 9, n).astype(np.uint8), row_ptr=[hh_rp, oc_rp, x_rp, hh_rp],
+               col=[hh_col, oc_col, x_col, hh_col], seed_ids=np.arange(0, n, 97, dtype=np.uint32))
+    p = W.params_with(B_net=[0.5, 0.2, 1.3, 0.1], R=2.0, dt=0.75)
+    rep = compare_days(pop, p, 30)
+    assert rep["flips"] == 0 and rep["days"] == 30
+
+
+def test_full_size_plain_workload_first_days():
+    """N=2,000,000 with 10,000 initial cases and all interventions, launched as the
+    benchmark launches it; the oracle runs the same first days in full."""
+    w = W.plain_large()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    p = dict(w["params"], vax_start=1)   # vaccination events inside the compared window
+    rep = compare_days(pop, p, 4)
+    assert rep["flips"] == 0 and rep["days"] == 4
+    assert rep["max_rel_lambda64"] <= 1e-5
+
+
+def test_batched_columns_equal_plain_runs_and_oracle():
+    n, B, T = 3001, 37, 40
+    pop = W.population(n, 8, 30)
+    base = W.params_with(vax_on=1, vax_start=5, vax_rate=0.01, test_on=1, quar_on=1, net_seed=5)
+    rp, seeds = W.batch_params(B, 1)
+    rp[:, 4:13] = np.random.default_rng(2).uniform(0.5, 1.5, (B, 9))
+    from paper_2110_04421_gb300.deabm import Simulation
+    gb = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds,
+                    max_steps=T)
+    ni_b, h_b = gb.run(T)
+    sb = gb.state()
+    gb.close()
+    for r in (0, 1, 17, 31, 32, 36):
+        pr = dict(base, R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
+                  S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r]))
+        g = gpu_sim(pop, pr, keep_lambda=False, max_steps=T)
+        ni, h = g.run(T)
+        s = g.state()
+        g.close()
+        assert np.array_equal(ni[:, 0], ni_b[:, r]) and np.array_equal(h[:, 0], h_b[:, r])
+        for k in ("stage", "timer", "tinf", "flags", "qt"):
+            assert np.array_equal(s[k], sb[k][:, r]), (r, k)
+        if r in (0, 36):
+            o = oracle_sim(pop, pr)
+            ni_o, h_o, _ = o.run(T)
+            assert np.array_equal(ni_o, ni_b[:, r]) and np.array_equal(h_o, h_b[:, r])
+            assert np.array_equal(o.state.stage, sb["stage"][:, r])
+
+
+def test_counters_and_run_agree():
+    pop = W.population(4000, 9, 20)
+    p = W.params_with()
+    g = gpu_sim(pop, p, keep_lambda=False, max_steps=50)
+    ni, h = g.run(50)
+    ni2, h2, m = g.counters()
+    g.close()
+    assert np.array_equal(ni, ni2) and np.array_equal(h, h2)
+    assert np.all(h.sum(axis=2) == 4000)
+    o = oracle_sim(pop, p)
+    ni_o, h_o, m_o = o.run(50)
+    assert np.array_equal(ni_o, ni[:, 0]) and np.array_equal(m_o, m.astype(np.int64))
