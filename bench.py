@@ -160,17 +160,19 @@ def run_ours(args, rank, world, local):
     sim.close()
 
     # ---- end to end through the C-ABI with host buffers (create + run + readback)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sim2 = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=K, stream=stream.cuda_stream)
-    ni, hist = sim2.run(K)
-    st = sim2.state()
-    _, _, msgs2 = sim2.counters(K)
-    sim2.close()
-    e2e_s = time.perf_counter() - t0
-    e2e_messages = int(msgs2.astype(np.int64).sum())
-    h2d = 4 * (n + 1) * len(pop["row_ptr"]) + 4 * static_edges + n + 4 * len(pop["seed_ids"])
-    d2h = ni.nbytes + hist.nbytes + sum(v.nbytes for v in st.values()) + msgs2.nbytes
+    e2e_s, e2e_messages, h2d, d2h = float("nan"), 0, 0, 0
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=K, stream=stream.cuda_stream)
+        ni, hist = sim2.run(K)
+        st = sim2.state()
+        _, _, msgs2 = sim2.counters(K)
+        sim2.close()
+        e2e_s = time.perf_counter() - t0
+        e2e_messages = int(msgs2.astype(np.int64).sum())
+        h2d = 4 * (n + 1) * len(pop["row_ptr"]) + 4 * static_edges + n + 4 * len(pop["seed_ids"])
+        d2h = ni.nbytes + hist.nbytes + sum(v.nbytes for v in st.values()) + msgs2.nbytes
 
     # ---- max over ranks
     tt = torch.tensor([total_ms, e2e_s, float(messages), float(e2e_messages)], dtype=torch.float64, device="cuda")
@@ -211,8 +213,9 @@ def run_ours(args, rank, world, local):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "step_plain_kernel", "alg_bytes_per_launch": alg,
                          "launch_ms_mean": avg_ms, "launch_ms_min": min(per_day_ms)},
-            "e2e": {"value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / K,
-                    "d2h_bytes_per_step": d2h / K, "seconds": e2e_s},
+            "e2e": None if args.no_e2e else {
+                "value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K, "seconds": e2e_s},
             "gpu_launches": K,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -249,6 +252,16 @@ def run_batched(args):
     _, _, msgs = sim.counters()
     sim.close()
     msg_b = int(msgs[args.warmup:].astype(np.int64).sum()) * B
+    alg = step_bytes_batch(n, B, static_edges, len(pop["row_ptr"]), True)
+    peak, _ = measured_peak_hbm()
+    achieved = alg / (ms / Kb / 1e3) / 1e9
+    value = msg_b / (ms / 1e3)
+    out = {"workload": "batched N=1e5 B=256 (R~U[2,6], weights~U[0.5,2], dose-2 delay~U{21..84}, own seeds)",
+           "value": value, "unit": "interactions/s", "ms_per_step": ms / Kb, "steps": Kb,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "kernel": "step_batch_kernel", "alg_bytes_per_launch": alg}}
+    if args.no_loop:
+        return out
     # plain loop: the same B replicates one after another, same days
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sims = []
@@ -267,15 +280,9 @@ def run_batched(args):
     ms_loop = e2.elapsed_time(e3)
     for s in sims:
         s.close()
-    alg = step_bytes_batch(n, B, static_edges, len(pop["row_ptr"]), True)
-    peak, _ = measured_peak_hbm()
-    achieved = alg / (ms / Kb / 1e3) / 1e9
-    value = msg_b / (ms / 1e3)
-    return {"workload": "batched N=1e5 B=256 (R~U[2,6], weights~U[0.5,2], dose-2 delay~U{21..84}, own seeds)",
-            "value": value, "unit": "interactions/s", "ms_per_step": ms / Kb, "steps": Kb,
-            "plain_loop_value": msg_b / (ms_loop / 1e3), "multiple_of_plain_loop": ms_loop / ms,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "kernel": "step_batch_kernel", "alg_bytes_per_launch": alg}}
+    out["plain_loop_value"] = msg_b / (ms_loop / 1e3)
+    out["multiple_of_plain_loop"] = ms_loop / ms
+    return out
 
 
 # ---------------------------------------------------------------------------------------- CPU oracle
@@ -349,10 +356,23 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-loop", action="store_true", help="skip the plain per-replicate loop of the batched leg")
+    ap.add_argument("--only", default="all", choices=["all", "plain", "batched"],
+                    help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = dist_env()
+    if args.only == "batched":
+        import __graft_entry__
+        __graft_entry__.build()
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(run_batched(args)))
+        return
+    if args.only == "plain":
+        args.no_batched = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

@@ -137,6 +137,11 @@ typedef struct {
     uint64_t seed, net_seed;
     uint32_t max_steps;   /* capacity of the per-day counters (0 = 1024) */
     uint32_t keep_lambda; /* 1: keep lambda_j and p_j of the last day for deabm_get_state */
+    uint32_t locality_order; /* 1: number the agents internally in breadth-first order of the
+                                static network with the most edges, so that the members of a
+                                group sit next to each other in device memory; results and
+                                every array the ABI returns are unchanged (random draws and
+                                outputs use the caller's agent ids) */
 } deabm_params;
 
 /* Create a plain (one replicate) simulation.  Validates the graph (monotone

@@ -27,7 +27,11 @@ struct deabm_ctx {
     int16_t *dose1 = nullptr;
     StateRef S{};
     float *inf[2] = {nullptr, nullptr};
+    float *inf_rand[2] = {nullptr, nullptr};  // by caller id, when relabelled and the random network is on
     int cur = 0;
+    bool relabel = false;
+    std::vector<uint32_t> new2orig;           // internal id -> caller id (relabelled only)
+    uint32_t *orig_id = nullptr;
     float *lam = nullptr, *p = nullptr;
     Tables *tab = nullptr;
     Rep *rep = nullptr;
@@ -150,6 +154,39 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
     return DEABM_OK;
 }
 
+// ---------------------------------------------------------------- locality order
+// Breadth-first order over the in-edges of the static network with the most
+// edges, roots taken in id order: the members of a group (a workplace, a
+// household) end up with consecutive internal ids, so a destination's gathers
+// hit the same cache lines as its neighbours'.
+static void locality_order(const deabm_graph *g, std::vector<uint32_t> &order)
+{
+    const uint32_t n = g->n_agents;
+    uint32_t best = 0;
+    for (uint32_t k = 1; k < g->n_nets; ++k)
+        if (g->row_ptr[k][n] > g->row_ptr[best][n]) best = k;
+    const uint32_t *rp = g->row_ptr[best], *col = g->col[best];
+    std::vector<uint8_t> seen(n, 0);
+    order.clear();
+    order.reserve(n);
+    for (uint32_t root = 0; root < n; ++root) {
+        if (seen[root]) continue;
+        seen[root] = 1;
+        size_t head = order.size();
+        order.push_back(root);
+        while (head < order.size()) {
+            const uint32_t v = order[head++];
+            for (uint32_t e = rp[v]; e < rp[v + 1]; ++e) {
+                const uint32_t u = col[e];
+                if (!seen[u]) {
+                    seen[u] = 1;
+                    order.push_back(u);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- creation
 static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_params *p, uint32_t n_rep,
                        const float *rep_params, const uint64_t *rep_seeds, void *stream, deabm_ctx **out)
@@ -171,14 +208,42 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             ctx->keep_lambda = p->keep_lambda != 0;
             cudaStream_t s = ctx->stream;
             int r;
+            ctx->relabel = p->locality_order != 0 && g->n_nets > 0;
+            std::vector<uint32_t> orig2new;
+            if (ctx->relabel) {
+                locality_order(g, ctx->new2orig);
+                orig2new.resize(n);
+                for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
+            }
+            auto orig_of = [&](uint32_t q) { return ctx->relabel ? ctx->new2orig[q] : q; };
+            std::vector<uint32_t> rp_new, col_new;
             for (uint32_t k = 0; k < g->n_nets; ++k) {
                 const uint32_t E = g->row_ptr[k][n];
                 ctx->static_edges += E;
                 if ((r = dalloc(ctx, &ctx->row_ptr[k], (size_t)n + 1))) return r;
                 if ((r = dalloc(ctx, &ctx->col[k], E))) return r;
-                CU(ctx, cudaMemcpyAsync(ctx->row_ptr[k], g->row_ptr[k], sizeof(uint32_t) * ((size_t)n + 1),
+                const uint32_t *rp_src = g->row_ptr[k], *col_src = g->col[k];
+                if (ctx->relabel) {
+                    // rows in internal order, each row's edges kept in the caller's order
+                    rp_new.assign((size_t)n + 1, 0);
+                    col_new.resize(E);
+                    for (uint32_t q = 0; q < n; ++q) {
+                        const uint32_t o = ctx->new2orig[q], b0 = g->row_ptr[k][o], b1 = g->row_ptr[k][o + 1];
+                        rp_new[q + 1] = rp_new[q] + (b1 - b0);
+                        for (uint32_t e = b0; e < b1; ++e) col_new[rp_new[q] + (e - b0)] = orig2new[g->col[k][e]];
+                    }
+                    rp_src = rp_new.data();
+                    col_src = col_new.data();
+                }
+                CU(ctx, cudaMemcpyAsync(ctx->row_ptr[k], rp_src, sizeof(uint32_t) * ((size_t)n + 1),
                                         cudaMemcpyHostToDevice, s));
-                if (E) CU(ctx, cudaMemcpyAsync(ctx->col[k], g->col[k], sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
+                if (E) CU(ctx, cudaMemcpyAsync(ctx->col[k], col_src, sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaStreamSynchronize(s));  // the staging vectors are reused by the next network
+            }
+            if (ctx->relabel) {
+                if ((r = dalloc(ctx, &ctx->orig_id, n))) return r;
+                CU(ctx, cudaMemcpyAsync(ctx->orig_id, ctx->new2orig.data(), sizeof(uint32_t) * n,
+                                        cudaMemcpyHostToDevice, s));
             }
             if ((r = dalloc(ctx, &ctx->age, n))) return r;
             if ((r = dalloc(ctx, &ctx->dose1, n))) return r;
@@ -189,6 +254,10 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->S.qt, nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
+            if (ctx->relabel && g->rand_mean > 0.0f) {
+                if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
+                if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
+            }
             if (ctx->keep_lambda) {
                 if ((r = dalloc(ctx, &ctx->lam, nb))) return r;
                 if ((r = dalloc(ctx, &ctx->p, nb))) return r;
@@ -205,20 +274,24 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
             CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
 
-            // agents: [N] -> [N][n_rep] by repeating each agent's initial state per replicate
-            CU(ctx, cudaMemcpyAsync(ctx->age, a->age_bin, n, cudaMemcpyHostToDevice, s));
+            // agents: [N] -> [N][n_rep] in internal order, each agent's initial state repeated per replicate
+            std::vector<uint8_t> age_in(n);
+            for (uint32_t q = 0; q < n; ++q) age_in[q] = a->age_bin[orig_of(q)];
+            CU(ctx, cudaMemcpyAsync(ctx->age, age_in.data(), n, cudaMemcpyHostToDevice, s));
             std::vector<int8_t> st(nb, 0);
             std::vector<int16_t> tm(nb, 0), ti(nb, 0);
             std::vector<uint8_t> fl(nb, 0), qt(nb, 0);
-            for (uint32_t j = 0; j < n; ++j)
+            for (uint32_t q = 0; q < n; ++q) {
+                const uint32_t o = orig_of(q);
                 for (uint32_t b = 0; b < n_rep; ++b) {
-                    const size_t i = (size_t)j * n_rep + b;
-                    if (a->stage) st[i] = a->stage[j];
-                    if (a->timer) tm[i] = a->timer[j];
-                    if (a->tinf) ti[i] = a->tinf[j];
-                    if (a->flags) fl[i] = a->flags[j];
-                    if (a->qt) qt[i] = a->qt[j];
+                    const size_t i = (size_t)q * n_rep + b;
+                    if (a->stage) st[i] = a->stage[o];
+                    if (a->timer) tm[i] = a->timer[o];
+                    if (a->tinf) ti[i] = a->tinf[o];
+                    if (a->flags) fl[i] = a->flags[o];
+                    if (a->qt) qt[i] = a->qt[o];
                 }
+            }
             CU(ctx, cudaMemcpyAsync(ctx->S.stage, st.data(), nb, cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemcpyAsync(ctx->S.timer, tm.data(), nb * 2, cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemcpyAsync(ctx->S.tinf, ti.data(), nb * 2, cudaMemcpyHostToDevice, s));
@@ -287,8 +360,19 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaMemcpyAsync(d_gamma, gs, sizeof gs, cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemcpyAsync(d_A, p->A_class, sizeof(float) * 3, cudaMemcpyHostToDevice, s));
             CU(ctx, launch_inf_table(ctx->tab, d_gamma, d_A, p->inf_len, s));
+            // the priority order is by the caller's ids: rank in caller order, then relabel
             const uint32_t per_day = p->vax_on ? (uint32_t)std::floor(p->vax_rate * (double)n) : 0u;
-            CU(ctx, launch_dose1_days(ctx->age, n, p->vax_start, per_day, ctx->dose1, d_scratch, s));
+            if (ctx->relabel) {
+                uint8_t *d_age_orig;
+                int16_t *d_dose_orig;
+                if ((r = dalloc(ctx, &d_age_orig, n))) return r;
+                if ((r = dalloc(ctx, &d_dose_orig, n))) return r;
+                CU(ctx, cudaMemcpyAsync(d_age_orig, a->age_bin, n, cudaMemcpyHostToDevice, s));
+                CU(ctx, launch_dose1_days(d_age_orig, n, p->vax_start, per_day, d_dose_orig, d_scratch, s));
+                CU(ctx, launch_gather_i16(ctx->dose1, d_dose_orig, ctx->orig_id, n, s));
+            } else {
+                CU(ctx, launch_dose1_days(ctx->age, n, p->vax_start, per_day, ctx->dose1, d_scratch, s));
+            }
 
             KParams &K = ctx->kp;
             K.n = n;
@@ -317,13 +401,18 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.rep = ctx->rep;
             K.age = ctx->age;
             K.dose1_day = ctx->dose1;
+            K.orig_id = ctx->relabel ? ctx->orig_id : nullptr;
 
             if (a->n_seed) {
+                std::vector<uint32_t> ids(a->seed_ids, a->seed_ids + a->n_seed);
+                if (ctx->relabel)
+                    for (auto &x : ids) x = orig2new[x];
                 if ((r = dalloc(ctx, &d_ids, a->n_seed))) return r;
-                CU(ctx, cudaMemcpyAsync(d_ids, a->seed_ids, sizeof(uint32_t) * a->n_seed, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(d_ids, ids.data(), sizeof(uint32_t) * a->n_seed, cudaMemcpyHostToDevice, s));
                 CU(ctx, launch_seed(K, d_ids, a->n_seed, ctx->S, s));
+                CU(ctx, cudaStreamSynchronize(s));
             }
-            CU(ctx, launch_emit(K, ctx->S, ctx->inf[0], s));
+            CU(ctx, launch_emit(K, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
             CU(ctx, cudaStreamSynchronize(s));
             return DEABM_OK;
         }();
@@ -359,8 +448,14 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
     if ((uint64_t)ctx->day + n_steps > ctx->max_steps)
         return fail(ctx, DEABM_ESTATE, "day %u + %u steps exceeds max_steps %u", ctx->day, n_steps, ctx->max_steps);
     for (uint32_t s = 0; s < n_steps; ++s) {
-        CU(ctx, launch_step(ctx->kp, ctx->day, ctx->inf[ctx->cur], ctx->inf[ctx->cur ^ 1], ctx->S, ctx->C,
-                            ctx->keep_lambda ? ctx->lam : nullptr, ctx->p, ctx->stream));
+        const int c = ctx->cur;
+        InfBuffers I;
+        I.cur = ctx->inf[c];
+        I.next = ctx->inf[c ^ 1];
+        I.rand_cur = ctx->inf_rand[c] ? ctx->inf_rand[c] : ctx->inf[c];
+        I.rand_next = ctx->inf_rand[c ^ 1];
+        CU(ctx, launch_step(ctx->kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
+                            ctx->stream));
         ctx->cur ^= 1;
         ctx->day += 1;
     }
@@ -412,13 +507,29 @@ extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, in
     if ((lambda || p) && !ctx->keep_lambda) return fail(ctx, DEABM_ESTATE, "created without keep_lambda");
     const size_t nb = (size_t)ctx->n * ctx->n_rep;
     cudaStream_t s = ctx->stream;
-    if (stage) CU(ctx, cudaMemcpyAsync(stage, ctx->S.stage, nb, cudaMemcpyDeviceToHost, s));
-    if (timer) CU(ctx, cudaMemcpyAsync(timer, ctx->S.timer, nb * 2, cudaMemcpyDeviceToHost, s));
-    if (tinf) CU(ctx, cudaMemcpyAsync(tinf, ctx->S.tinf, nb * 2, cudaMemcpyDeviceToHost, s));
-    if (flags) CU(ctx, cudaMemcpyAsync(flags, ctx->S.flags, nb, cudaMemcpyDeviceToHost, s));
-    if (qt) CU(ctx, cudaMemcpyAsync(qt, ctx->S.qt, nb, cudaMemcpyDeviceToHost, s));
-    if (lambda) CU(ctx, cudaMemcpyAsync(lambda, ctx->lam, nb * 4, cudaMemcpyDeviceToHost, s));
-    if (p) CU(ctx, cudaMemcpyAsync(p, ctx->p, nb * 4, cudaMemcpyDeviceToHost, s));
+    // device arrays are in internal order: copy, then put each agent back at its caller id
+    auto fetch = [&](void *dst, const void *src, size_t elem) -> int {
+        if (!dst) return DEABM_OK;
+        if (!ctx->relabel) {
+            CU(ctx, cudaMemcpyAsync(dst, src, nb * elem, cudaMemcpyDeviceToHost, s));
+            return DEABM_OK;
+        }
+        std::vector<uint8_t> tmp(nb * elem);
+        CU(ctx, cudaMemcpyAsync(tmp.data(), src, nb * elem, cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+        const size_t row = (size_t)ctx->n_rep * elem;
+        for (uint32_t q = 0; q < ctx->n; ++q)
+            std::memcpy((uint8_t *)dst + (size_t)ctx->new2orig[q] * row, tmp.data() + (size_t)q * row, row);
+        return DEABM_OK;
+    };
+    int r;
+    if ((r = fetch(stage, ctx->S.stage, 1))) return r;
+    if ((r = fetch(timer, ctx->S.timer, 2))) return r;
+    if ((r = fetch(tinf, ctx->S.tinf, 2))) return r;
+    if ((r = fetch(flags, ctx->S.flags, 1))) return r;
+    if ((r = fetch(qt, ctx->S.qt, 1))) return r;
+    if ((r = fetch(lambda, ctx->lam, 4))) return r;
+    if ((r = fetch(p, ctx->p, 4))) return r;
     CU(ctx, cudaStreamSynchronize(s));
     return DEABM_OK;
 }
@@ -428,8 +539,11 @@ extern "C" int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *pois
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     Tables T;
     CU(ctx, cudaMemcpyAsync(&T, ctx->tab, sizeof T, cudaMemcpyDeviceToHost, ctx->stream));
-    if (dose1_day) CU(ctx, cudaMemcpyAsync(dose1_day, ctx->dose1, 2ull * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int16_t> d1(dose1_day ? ctx->n : 0);
+    if (dose1_day) CU(ctx, cudaMemcpyAsync(d1.data(), ctx->dose1, 2ull * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (dose1_day)
+        for (uint32_t q = 0; q < ctx->n; ++q) dose1_day[ctx->relabel ? ctx->new2orig[q] : q] = d1[q];
     if (inf_table)
         for (int c = 0; c < DEABM_N_CLASS; ++c)
             std::memcpy(inf_table + (size_t)c * ctx->kp.inf_len, T.infT[c], sizeof(float) * ctx->kp.inf_len);

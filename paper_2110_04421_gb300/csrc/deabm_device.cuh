@@ -82,8 +82,19 @@ struct KParams {
     uint64_t thr_eff1, thr_eff2;
     const Tables *tab;
     const Rep *rep;
-    const uint8_t *age;
-    const int16_t *dose1_day;
+    const uint8_t *age;        // by internal id
+    const int16_t *dose1_day;  // by internal id
+    const uint32_t *orig_id;   // internal id -> caller's agent id (nullptr: the same)
+};
+
+// Infectiousness buffers of a day.  Static-network gathers read `cur` (internal
+// ids); random-network gathers read `rand_cur`, indexed by the caller's agent ids
+// (the same array when the ids are not relabelled).
+struct InfBuffers {
+    const float *cur;
+    float *next;
+    const float *rand_cur;
+    float *rand_next;  // nullptr when not relabelled
 };
 
 struct StateRef {

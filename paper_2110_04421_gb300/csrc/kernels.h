@@ -7,8 +7,8 @@
 namespace deabm {
 
 // one simulated day: reads inf_cur and the state, writes the state, inf_next and the day's counters
-cudaError_t launch_step(const KParams &P, uint32_t day, const float *inf_cur, float *inf_next, const StateRef &S,
-                        const Counters &C, float *lam_out, float *p_out, cudaStream_t stream);
+cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, const StateRef &S, const Counters &C,
+                        float *lam_out, float *p_out, cudaStream_t stream);
 
 // set-up: infectiousness table (FP64 gamma integrals, rounded once, times A_class)
 cudaError_t launch_inf_table(Tables *tab, const double *shape_scale /*device [6]*/, const float *A_class /*device [3]*/,
@@ -19,7 +19,9 @@ cudaError_t launch_dose1_days(const uint8_t *age, uint32_t n, uint32_t start, ui
 size_t dose1_scratch_words(uint32_t n);
 // set-up: infections before day 0 for every replicate
 cudaError_t launch_seed(const KParams &P, const uint32_t *ids, uint32_t n_ids, const StateRef &S, cudaStream_t stream);
-// set-up: emitted infectiousness of the current state
-cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, cudaStream_t stream);
+// set-up: emitted infectiousness of the current state (inf_rand: copy by caller id, or nullptr)
+cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, float *inf_rand, cudaStream_t stream);
+// out[i] = in[idx[i]] for i < n
+cudaError_t launch_gather_i16(int16_t *out, const int16_t *in, const uint32_t *idx, uint32_t n, cudaStream_t stream);
 
 }  // namespace deabm

@@ -152,8 +152,9 @@ __global__ void seed_kernel(const KParams P, const uint32_t *ids, uint32_t n_ids
     const size_t i = (size_t)j * P.n_rep + b;
     if (S.stage[i] != DEABM_S) return;
     const uint2 key = seed_key(P.rep[b].seed);
+    const uint32_t jo = P.orig_id ? P.orig_id[j] : j;
     AgentState a{};
-    new_infection(P.tab, P.age[j], draw(key, j, kSeedDay, kStreamProg), a);
+    new_infection(P.tab, P.age[j], draw(key, jo, kSeedDay, kStreamProg), a);
     S.stage[i] = (int8_t)a.st;
     S.timer[i] = (int16_t)a.tm;
     S.tinf[i] = (int16_t)a.ti;
@@ -167,19 +168,37 @@ cudaError_t launch_seed(const KParams &P, const uint32_t *ids, uint32_t n_ids, c
     return cudaGetLastError();
 }
 
-__global__ void emit_kernel(const KParams P, StateRef S, float *inf)
+__global__ void emit_kernel(const KParams P, StateRef S, float *inf, float *inf_rand)
 {
     const size_t total = (size_t)P.n * P.n_rep;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
-        inf[i] = emitted(P.tab, P.inf_len, S.stage[i], S.tinf[i], S.qt[i] & 0x0Fu);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = emitted(P.tab, P.inf_len, S.stage[i], S.tinf[i], S.qt[i] & 0x0Fu);
+        inf[i] = v;
+        if (inf_rand) {
+            const size_t j = i / P.n_rep, b = i % P.n_rep;
+            inf_rand[(size_t)P.orig_id[j] * P.n_rep + b] = v;
+        }
+    }
 }
 
-cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, cudaStream_t stream)
+cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, float *inf_rand, cudaStream_t stream)
 {
     const size_t total = (size_t)P.n * P.n_rep;
     const uint32_t blocks = (uint32_t)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
     if (blocks == 0) return cudaSuccess;
-    emit_kernel<<<blocks, 256, 0, stream>>>(P, S, inf);
+    emit_kernel<<<blocks, 256, 0, stream>>>(P, S, inf, inf_rand);
+    return cudaGetLastError();
+}
+
+__global__ void gather_i16_kernel(int16_t *out, const int16_t *in, const uint32_t *idx, uint32_t n)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[idx[i]];
+}
+
+cudaError_t launch_gather_i16(int16_t *out, const int16_t *in, const uint32_t *idx, uint32_t n, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    gather_i16_kernel<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, stream>>>(out, in, idx, n);
     return cudaGetLastError();
 }
 

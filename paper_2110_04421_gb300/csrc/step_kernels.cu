@@ -36,27 +36,40 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
     return u < pe;
 }
 
-__device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                                         const float *__restrict__ inf, uint32_t j, uint32_t stride, uint32_t b)
+// Sum of inf over one CSR row, left to right from +0.0f.  The row is taken in
+// rounds of kRound edges: all column loads of a round are issued, then all
+// gathers, then the adds in order, so a row of up to kRound in-edges costs two
+// dependent memory round trips instead of one per edge.
+#ifndef DEABM_ROUND
+#define DEABM_ROUND 10
+#endif
+#ifndef DEABM_PLAIN_MINB
+#define DEABM_PLAIN_MINB 6
+#endif
+constexpr uint32_t kRound = DEABM_ROUND;
+
+__device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const float *__restrict__ inf, uint32_t e,
+                                         uint32_t end, uint32_t stride, uint32_t b)
 {
-    uint32_t e = __ldg(rp + j);
-    const uint32_t end = __ldg(rp + j + 1);
     float h = 0.0f;
-    for (; e + 4u <= end; e += 4u) {
-        const uint32_t c0 = __ldg(col + e), c1 = __ldg(col + e + 1), c2 = __ldg(col + e + 2), c3 = __ldg(col + e + 3);
-        const float v0 = __ldg(inf + (size_t)c0 * stride + b), v1 = __ldg(inf + (size_t)c1 * stride + b);
-        const float v2 = __ldg(inf + (size_t)c2 * stride + b), v3 = __ldg(inf + (size_t)c3 * stride + b);
-        h = __fadd_rn(h, v0);
-        h = __fadd_rn(h, v1);
-        h = __fadd_rn(h, v2);
-        h = __fadd_rn(h, v3);
+    while (e < end) {
+        uint32_t c[kRound];
+        float v[kRound];
+#pragma unroll
+        for (uint32_t u = 0; u < kRound; ++u) c[u] = (e + u < end) ? __ldg(col + e + u) : 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < kRound; ++u) v[u] = (e + u < end) ? __ldg(inf + (size_t)c[u] * stride + b) : 0.0f;
+#pragma unroll
+        for (uint32_t u = 0; u < kRound; ++u)
+            if (e + u < end) h = __fadd_rn(h, v[u]);
+        e += kRound;
     }
-    for (; e < end; ++e) h = __fadd_rn(h, __ldg(inf + (size_t)__ldg(col + e) * stride + b));
     return h;
 }
 
-// Random in-contacts of agent j on `day`: count from word 0 of block 0, contact e
-// from word e+1 (block (e+1)/4, lane (e+1)%4); v uniform on the other n-1 agents.
+// Random in-contacts of agent j (the caller's id) on `day`: count from word 0 of
+// block 0, contact e from word e+1 (block (e+1)/4, lane (e+1)%4); v uniform on
+// the other n-1 agents.  `inf` is indexed by the caller's ids.
 __device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
                                             uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out)
 {
@@ -78,34 +91,48 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
     return r;
 }
 
-// lambda_j of one (agent, replicate) from the state of the day
-__device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const float *__restrict__ inf, uint32_t j,
+// lambda_j of one (agent, replicate) from the state of the day; j = internal row,
+// jo = the caller's id of the same agent.  The row bounds of every network are
+// loaded first and the random contacts are generated while they are in flight.
+__device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out)
 {
-    float s = 0.0f;
-    for (uint32_t net = 0; net < P.n_nets; ++net) {
-        const float h = csr_sum(P.row_ptr[net], P.col[net], inf, j, stride, b);
-        const float term = __fmul_rn(rp.B_net[net], h);
-        s = net == 0 ? term : __fadd_rn(s, term);
+    uint32_t beg[DEABM_MAX_NETS], end[DEABM_MAX_NETS];
+#pragma unroll
+    for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
+        beg[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j) : 0u;
+        end[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j + 1) : 0u;
     }
     *k_out = 0;
+    float r = 0.0f;
+    if (P.rand_on) r = random_sum(P, I.rand_cur, jo, day, stride, b, k_out);
+    float s = 0.0f;
+#pragma unroll
+    for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
+        if (net < P.n_nets) {
+            const float h = csr_sum(P.col[net], I.cur, beg[net], end[net], stride, b);
+            const float term = __fmul_rn(rp.B_net[net], h);
+            s = net == 0 ? term : __fadd_rn(s, term);
+        }
+    }
     if (P.rand_on) {
-        const float r = random_sum(P, inf, j, day, stride, b, k_out);
         const float term = __fmul_rn(rp.B_rand, r);
         s = P.n_nets == 0 ? term : __fadd_rn(s, term);
     }
     return __fmul_rn(__fmul_rn(rp.cR, rp.S_age[age]), s);
 }
 
-// Full day for one (agent j, replicate b) at flat index i = j*stride + b.
-__device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const float *__restrict__ inf_cur,
-                                          float *__restrict__ inf_next, const StateRef &S, uint32_t j, uint32_t stride,
-                                          uint32_t b, float *lam_out, float *p_out, int *new_stage, bool *infected,
-                                          uint32_t *k_out)
+// Full day for one (agent j, replicate b) at flat index i = j*stride + b.  Every
+// random draw is keyed by the caller's agent id jo, so relabelling the agents
+// inside the library changes no result.
+__device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
+                                          const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
+                                          float *p_out, int *new_stage, bool *infected, uint32_t *k_out)
 {
     const size_t i = (size_t)j * stride + b;
+    const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
     const int age = __ldg(P.age + j);
-    const float lam = lambda_of(P, rp, inf_cur, j, day, stride, b, age, k_out);
+    const float lam = lambda_of(P, rp, I, j, jo, day, stride, b, age, k_out);
     AgentState a;
     a.st = S.stage[i];
     a.tm = S.timer[i];
@@ -119,19 +146,21 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     uint32_t inf_y = 0;
     float p = 0.0f;
     if (a.st == DEABM_S || a.qd > 0u || lam_out != nullptr) {
-        const uint4 w = draw(key, j, day, kStreamInf);
+        const uint4 w = draw(key, jo, day, kStreamInf);
         inf_y = w.y;
         const bool hit = infection_decision(__fmul_rn(lam, P.dt), unit_float(w.x), &p);
         inf_now = (a.st == DEABM_S) && hit;
     }
     const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
-    advance(P, rp, key, j, day, age, d1, inf_now, a, inf_y);
+    advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
     S.stage[i] = (int8_t)a.st;
     S.timer[i] = (int16_t)a.tm;
     S.tinf[i] = (int16_t)a.ti;
     S.flags[i] = (uint8_t)a.fl;
     S.qt[i] = (uint8_t)((a.qd & 0x0Fu) | ((a.cd & 0x07u) << 4));
-    inf_next[i] = emitted(P.tab, P.inf_len, a.st, a.ti, a.qd);
+    const float v = emitted(P.tab, P.inf_len, a.st, a.ti, a.qd);
+    I.next[i] = v;
+    if (I.rand_next) I.rand_next[(size_t)jo * stride + b] = v;
     if (lam_out) {
         lam_out[i] = lam;
         p_out[i] = p;
@@ -158,9 +187,8 @@ __device__ __forceinline__ void count_day(bool active, int st, bool infected, ui
 }
 
 template <bool KEEP>
-__global__ void __launch_bounds__(256) step_plain_kernel(const KParams P, uint32_t day, const float *__restrict__ inf_cur,
-                                                         float *__restrict__ inf_next, StateRef S, Counters C,
-                                                         float *lam_out, float *p_out)
+__global__ void __launch_bounds__(256, DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
+                                                         Counters C, float *lam_out, float *p_out)
 {
     __shared__ int s_hist[DEABM_N_STAGE];
     __shared__ int s_new;
@@ -175,7 +203,7 @@ __global__ void __launch_bounds__(256) step_plain_kernel(const KParams P, uint32
     uint32_t k = 0;
     if (active) {
         const Rep &rp = P.rep[0];
-        agent_day(P, rp, day, inf_cur, inf_next, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        agent_day(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
     }
     count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
     __syncthreads();
@@ -191,9 +219,8 @@ __global__ void __launch_bounds__(256) step_plain_kernel(const KParams P, uint32
 // The 32 lanes of a warp read the same CSR entries (one broadcast load) and
 // gather one contiguous 128 B run of the [N][B] infectiousness panel per edge.
 template <bool KEEP>
-__global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32_t day, const float *__restrict__ inf_cur,
-                                                         float *__restrict__ inf_next, StateRef S, Counters C,
-                                                         float *lam_out, float *p_out)
+__global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
+                                                         Counters C, float *lam_out, float *p_out)
 {
     // per (stage or new-infection, replicate lane) counts of the block's 8 agent rows
     __shared__ int s_cnt[DEABM_N_STAGE + 1][32];
@@ -210,7 +237,7 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     uint32_t k = 0;
     if (active) {
         const Rep &rp = P.rep[b];
-        agent_day(P, rp, day, inf_cur, inf_next, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        agent_day(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
         atomicAdd(&s_cnt[st][lane], 1);
         if (infected) atomicAdd(&s_cnt[DEABM_N_STAGE][lane], 1);
     }
@@ -228,18 +255,18 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     if (tid == 0 && s_msgs) atomicAdd(&C.msgs[day], s_msgs);
 }
 
-cudaError_t launch_step(const KParams &P, uint32_t day, const float *inf_cur, float *inf_next, const StateRef &S,
-                        const Counters &C, float *lam_out, float *p_out, cudaStream_t stream)
+cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, const StateRef &S, const Counters &C,
+                        float *lam_out, float *p_out, cudaStream_t stream)
 {
     if (P.n_rep == 1) {
         const dim3 grid((P.n + 255u) / 256u);
-        if (lam_out) step_plain_kernel<true><<<grid, 256, 0, stream>>>(P, day, inf_cur, inf_next, S, C, lam_out, p_out);
-        else step_plain_kernel<false><<<grid, 256, 0, stream>>>(P, day, inf_cur, inf_next, S, C, nullptr, nullptr);
+        if (lam_out) step_plain_kernel<true><<<grid, 256, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+        else step_plain_kernel<false><<<grid, 256, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
     } else {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
         const dim3 block(32, 8);
-        if (lam_out) step_batch_kernel<true><<<grid, block, 0, stream>>>(P, day, inf_cur, inf_next, S, C, lam_out, p_out);
-        else step_batch_kernel<false><<<grid, block, 0, stream>>>(P, day, inf_cur, inf_next, S, C, nullptr, nullptr);
+        if (lam_out) step_batch_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+        else step_batch_kernel<false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
     }
     return cudaGetLastError();
 }

@@ -54,7 +54,7 @@ class Params(C.Structure):
         ("vax_on", C.c_uint32), ("vax_start", C.c_uint32), ("vax_onset", C.c_uint32), ("dose2_delay", C.c_uint32),
         ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
-        ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32),
+        ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32), ("locality_order", C.c_uint32),
     ]
 
 
@@ -110,7 +110,7 @@ def _current_stream():
     return C.c_void_p(0)
 
 
-def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False) -> Params:
+def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False, locality_order: bool = True) -> Params:
     p = Params()
     p.R, p.inv_Ibar, p.dt = P["R"], P["inv_Ibar"], P["dt"]
     for i in range(MAX_NETS):
@@ -136,6 +136,7 @@ def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False) -> Pa
         setattr(p, name, P[name])
     p.max_steps = max_steps
     p.keep_lambda = 1 if keep_lambda else 0
+    p.locality_order = 1 if locality_order else 0
     return p
 
 
@@ -150,7 +151,7 @@ class Simulation:
 
     def __init__(self, graph: dict, params: dict, age, seed_ids=None, state: dict | None = None,
                  n_rep: int = 1, rep_params=None, rep_seeds=None, keep_lambda: bool = False,
-                 max_steps: int = 1024, stream=None):
+                 max_steps: int = 1024, stream=None, locality_order: bool = True):
         L = lib()
         self.n = int(graph["n"])
         self.n_rep = int(n_rep)
@@ -180,7 +181,7 @@ class Simulation:
             keep.append(ids)
             a.seed_ids = ids.ctypes.data
             a.n_seed = ids.size
-        p = make_params(params, max_steps=max_steps, keep_lambda=keep_lambda)
+        p = make_params(params, max_steps=max_steps, keep_lambda=keep_lambda, locality_order=locality_order)
         self._stream = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
         ctx = C.c_void_p()
         if self.n_rep == 1 and rep_params is None:

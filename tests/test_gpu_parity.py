@@ -147,3 +147,41 @@ def test_counters_and_run_agree():
     o = oracle_sim(pop, p)
     ni_o, h_o, m_o = o.run(50)
     assert np.array_equal(ni_o, ni[:, 0]) and np.array_equal(m_o, m.astype(np.int64))
+
+
+@pytest.mark.parametrize("locality_order", [False, True])
+def test_internal_numbering_changes_nothing(locality_order):
+    """The library's internal agent numbering (breadth-first order of the densest
+    network) is invisible: the same days, draws and outputs, with or without it."""
+    pop = W.population(5003, 11, 25)
+    p = W.params_with(test_on=1, quar_on=1, vax_on=1, vax_start=3, vax_rate=0.03, R=4.0, seed=5, net_seed=6)
+    rep = compare_days_kw(pop, p, 40, locality_order=locality_order)
+    assert rep["flips"] == 0 and rep["days"] == 40
+
+
+def compare_days_kw(pop, p, T, **kw):
+    from tests import helpers
+    orig = helpers.gpu_sim
+    helpers.gpu_sim = lambda *a, **k: orig(*a, **{**k, **kw})
+    try:
+        return compare_days(pop, p, T)
+    finally:
+        helpers.gpu_sim = orig
+
+
+def test_batched_without_internal_numbering():
+    n, B, T = 2000, 40, 25
+    pop = W.population(n, 12, 20)
+    base = W.params_with(test_on=1, quar_on=1, net_seed=9)
+    rp, seeds = W.batch_params(B, 3)
+    from paper_2110_04421_gb300.deabm import Simulation
+    out = []
+    for lo in (False, True):
+        g = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds, max_steps=T,
+                       locality_order=lo)
+        ni, h = g.run(T)
+        out.append((ni, h, g.state()))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for k in ("stage", "timer", "tinf", "flags", "qt"):
+        assert np.array_equal(out[0][2][k], out[1][2][k])
