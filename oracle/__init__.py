@@ -28,6 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "deabm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "deabm_relaxed.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -48,11 +49,11 @@ def build(force: bool = False) -> str:
 
 def _build_locked(force: bool) -> str:
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -88,6 +89,19 @@ class _Diag(C.Structure):
     ]
 
 
+class _RxModel(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint32), ("n_nets", C.c_uint32),
+        ("row_ptr", C.c_void_p * MAX_NETS), ("col", C.c_void_p * MAX_NETS),
+        ("B_extra", C.c_double * MAX_NETS),
+        ("rand_mean", C.c_double), ("inv_Ibar", C.c_double), ("tau", C.c_double),
+        ("A_class", C.c_double * N_CLASS),
+        ("inf_shape", C.c_double * N_CLASS), ("inf_scale", C.c_double * N_CLASS), ("inf_len", C.c_uint32),
+        ("p_asym", C.c_double * N_AGE), ("p_sev", C.c_double * N_AGE),
+        ("seed", C.c_uint64), ("net_seed", C.c_uint64),
+    ]
+
+
 def lib():
     global _lib
     with _lock:
@@ -113,6 +127,11 @@ def lib():
             L.or_run.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, C.c_uint32,
                                  vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_run.restype = C.c_int
+            L.rx_run.argtypes = [C.POINTER(_RxModel), vp, vp, C.c_uint32, C.c_uint32, vp, vp, vp, vp, vp, vp]
+            L.rx_run.restype = C.c_int
+            L.rx_classes.argtypes = [C.POINTER(_RxModel), vp, vp]
+            L.rx_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+            L.rx_noise.restype = C.c_double
             _lib = L
     return _lib
 
@@ -284,3 +303,78 @@ class Sim:
             raise ValueError("oracle rejected the model parameters")
         self.t += T
         return new_inf, hist, msgs
+
+
+# --------------------------------------------------------------------------- relaxed model
+THETA_NAMES = ("R", "B_household", "B_occupation", "B_random") + tuple(f"S_age{a}" for a in range(N_AGE))
+
+
+def theta_of(params: dict) -> np.ndarray:
+    """theta = (R, B_net[0], B_net[1], B_rand, S_age[0..8]) as FP64."""
+    B = list(params["B_net"]) + [0.0, 0.0]
+    return np.array([params["R"], B[0], B[1], params["B_rand"], *params["S_age"]], np.float64)
+
+
+class Relaxed:
+    """FP64 relaxed (Gumbel-softmax) model with full-history reverse sweep.
+    Parameters are taken as the FP32 values the CUDA path receives."""
+
+    def __init__(self, graph: dict, params: dict, age, seed_ids, tau: float = 0.5):
+        self.n = int(graph["n"])
+        self._keep = []
+        m = _RxModel()
+        m.n = self.n
+        m.n_nets = len(graph["row_ptr"])
+        for i, (rp, cl) in enumerate(zip(graph["row_ptr"], graph["col"])):
+            rp = np.ascontiguousarray(rp, dtype=np.uint32)
+            cl = np.ascontiguousarray(cl, dtype=np.uint32)
+            self._keep += [rp, cl]
+            m.row_ptr[i] = rp.ctypes.data
+            m.col[i] = cl.ctypes.data
+        f32 = lambda v: float(np.float32(v))
+        B = list(params["B_net"]) + [0.0] * MAX_NETS
+        for i in range(MAX_NETS):
+            m.B_extra[i] = f32(B[i])
+        m.rand_mean = f32(params["rand_mean"])
+        m.inv_Ibar = f32(params["inv_Ibar"])
+        m.tau = f32(tau)
+        for c in range(N_CLASS):
+            m.A_class[c] = f32(params["A_class"][c])
+            m.inf_shape[c] = params["inf_shape"][c]
+            m.inf_scale[c] = params["inf_scale"][c]
+        m.inf_len = params["inf_len"]
+        for a in range(N_AGE):
+            m.p_asym[a] = params["p_asym"][a]
+            m.p_sev[a] = params["p_sev"][a]
+        m.seed, m.net_seed = params["seed"], params["net_seed"]
+        self.m = m
+        self.age = np.ascontiguousarray(age, dtype=np.uint8)
+        self.seeds = np.ascontiguousarray(seed_ids if seed_ids is not None else [], dtype=np.uint32)
+
+    def classes(self) -> np.ndarray:
+        out = np.zeros(self.n, np.uint8)
+        lib().rx_classes(C.byref(self.m), _ptr(self.age), _ptr(out))
+        return out
+
+    def run(self, theta, T: int, target=None, grad: bool = False, want_x: bool = False, fp32_theta: bool = True):
+        """theta is rounded to FP32 first (the values the CUDA path receives) unless
+        fp32_theta=False (finite differences need the exact FP64 perturbation)."""
+        th = np.asarray(theta, np.float64)
+        th = np.ascontiguousarray(np.float32(th).astype(np.float64) if fp32_theta else th)
+        y = None if target is None else np.ascontiguousarray(target, dtype=np.float64)
+        inc = np.zeros(T, np.float64)
+        loss = C.c_double(0.0)
+        g = np.zeros(13, np.float64) if grad else None
+        x = np.zeros((T, self.n), np.float64) if want_x else None
+        rc = lib().rx_run(C.byref(self.m), _ptr(self.age), _ptr(self.seeds), self.seeds.size, T, _ptr(th), _ptr(y),
+                          _ptr(inc), C.byref(loss), _ptr(g), _ptr(x))
+        if rc != 0:
+            raise ValueError("oracle rejected the relaxed model")
+        out = dict(incidence=inc)
+        if y is not None:
+            out["loss"] = loss.value
+        if grad:
+            out["grad"] = g
+        if want_x:
+            out["x"] = x
+        return out

@@ -86,21 +86,30 @@ __global__ void age_count_kernel(const uint8_t *age, uint32_t n, uint32_t *cnt /
     if (threadIdx.x < DEABM_N_AGE) cnt[blockIdx.x * DEABM_N_AGE + threadIdx.x] = s[threadIdx.x];
 }
 
-// one thread: turns the counts into each block's first rank per bin (in place)
-__global__ void age_offsets_kernel(uint32_t *cnt, uint32_t blocks)
+// one warp per age bin: turns the per-block counts into each block's first rank
+// in the priority order (in place); launched as one block of 9 warps
+__global__ void __launch_bounds__(32 * DEABM_N_AGE) age_offsets_kernel(uint32_t *cnt, uint32_t blocks)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    uint32_t total[DEABM_N_AGE] = {0};
-    for (uint32_t q = 0; q < blocks; ++q)
-        for (int a = 0; a < DEABM_N_AGE; ++a) total[a] += cnt[q * DEABM_N_AGE + a];
-    uint32_t base[DEABM_N_AGE], acc = 0;
-    for (int a = DEABM_N_AGE - 1; a >= 0; --a) { base[a] = acc; acc += total[a]; }
-    for (uint32_t q = 0; q < blocks; ++q)
-        for (int a = 0; a < DEABM_N_AGE; ++a) {
-            const uint32_t c = cnt[q * DEABM_N_AGE + a];
-            cnt[q * DEABM_N_AGE + a] = base[a];
-            base[a] += c;
+    __shared__ uint32_t total[DEABM_N_AGE];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    uint32_t sum = 0;
+    for (uint32_t q = lane; q < blocks; q += 32u) sum += cnt[q * DEABM_N_AGE + w];
+    sum = __reduce_add_sync(0xFFFFFFFFu, sum);
+    if (lane == 0) total[w] = sum;
+    __syncthreads();
+    uint32_t running = 0;
+    for (uint32_t a = w + 1; a < DEABM_N_AGE; ++a) running += total[a];  // older bins come first
+    for (uint32_t q0 = 0; q0 < blocks; q0 += 32u) {
+        const uint32_t q = q0 + lane;
+        const uint32_t c = q < blocks ? cnt[q * DEABM_N_AGE + w] : 0u;
+        uint32_t incl = c;
+        for (uint32_t off = 1; off < 32u; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += v;
         }
+        if (q < blocks) cnt[q * DEABM_N_AGE + w] = running + incl - c;
+        running += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
 }
 
 __global__ void __launch_bounds__(kRankBlock) dose1_kernel(const uint8_t *age, uint32_t n, const uint32_t *off,
@@ -136,7 +145,7 @@ cudaError_t launch_dose1_days(const uint8_t *age, uint32_t n, uint32_t start, ui
     const uint32_t blocks = (n + kRankBlock - 1) / kRankBlock;
     if (blocks == 0) return cudaSuccess;
     age_count_kernel<<<blocks, kRankBlock, 0, stream>>>(age, n, scratch);
-    age_offsets_kernel<<<1, 32, 0, stream>>>(scratch, blocks);
+    age_offsets_kernel<<<1, 32 * DEABM_N_AGE, 0, stream>>>(scratch, blocks);
     dose1_kernel<<<blocks, kRankBlock, 0, stream>>>(age, n, scratch, start, per_day, out);
     return cudaGetLastError();
 }
