@@ -184,8 +184,9 @@ def run_ours(args, rank, world, local):
         total_ms, e2e_s = float(mx[0]), float(mx[1])
         messages, e2e_messages = int(sm[2]), int(sm[3])
 
-    # ---- batched ensemble vs plain per-replicate loop (rank 0, a short window)
+    # ---- batched ensemble vs plain per-replicate loop, relaxed gradient (rank 0)
     batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
+    relaxed = run_relaxed(args) if (rank == 0 and not args.no_relaxed) else None
 
     if rank == 0:
         value = messages / (total_ms / 1e3)
@@ -222,9 +223,42 @@ def run_ours(args, rank, world, local):
         }
         if batched:
             line["batched"] = batched
+        if relaxed:
+            line["relaxed"] = relaxed
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def run_relaxed(args):
+    """Differentiable inverse run: one gradient (forward with checkpoints + reverse
+    sweep) and an on-device Adam calibration, N = 1e5, 90 days."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Relaxed
+
+    w = W.relaxed_workload()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    stream = torch.cuda.Stream()
+    rx = Relaxed(pop, w["params"], pop["age"], pop["seed_ids"], tau=w["tau"], max_days=w["T"], ckpt_every=10,
+                 stream=stream.cuda_stream)
+    y = np.log(rx.forward(w["hidden"], w["T"]).astype(np.float64) + 1.0).astype(np.float32)
+    for _ in range(args.warmup):
+        rx.grad(w["start"], y)
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        loss0, g0, _ = rx.grad(w["start"], y)
+    ms_grad = (time.perf_counter() - t0) / reps * 1e3
+    t1 = time.perf_counter()
+    theta, trace = rx.calibrate(w["start"], y, steps=args.calib_steps, lr=w["lr"])
+    cal_s = time.perf_counter() - t1
+    loss1, _, _ = rx.grad(theta, y)
+    rx.close()
+    return {"workload": w["name"], "ms_per_gradient": ms_grad, "days": w["T"], "checkpoint_every": 10,
+            "calibration": {"steps": args.calib_steps, "seconds": cal_s, "loss_start": float(trace[0]),
+                            "loss_end": float(loss1), "theta_hidden": [float(x) for x in w["hidden"][:4]],
+                            "theta_found": [float(x) for x in theta[:4]]}}
 
 
 def run_batched(args):
@@ -358,7 +392,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-loop", action="store_true", help="skip the plain per-replicate loop of the batched leg")
-    ap.add_argument("--only", default="all", choices=["all", "plain", "batched"],
+    ap.add_argument("--no-relaxed", action="store_true")
+    ap.add_argument("--calib-steps", type=int, default=200)
+    ap.add_argument("--only", default="all", choices=["all", "plain", "batched", "relaxed"],
                     help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -371,8 +407,16 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps(run_batched(args)))
         return
+    if args.only == "relaxed":
+        import __graft_entry__
+        __graft_entry__.build()
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(run_relaxed(args)))
+        return
     if args.only == "plain":
         args.no_batched = True
+        args.no_relaxed = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

@@ -204,6 +204,58 @@ const char *deabm_last_error(const deabm_ctx *ctx);
 /* Free all device memory of ctx.  NULL-safe. */
 void deabm_destroy(deabm_ctx *ctx);
 
+/* ------------------------------------------------------------------------------------------
+ * Relaxed (differentiable) simulation for gradient-based calibration.
+ * The paper proposes learning the simulator's parameters by gradient descent
+ * against aggregate data ("inverse" simulation: Abstract, Sec. 1, Sec. 6) but
+ * defines no relaxation.  The model here (one reading, stated in full):
+ *   each agent's symptom class is drawn once before day 0 (asymptomatic with
+ *   p_asym[age], else severe with p_sev[age], else mild);  x_j(t), s_j(t) are the
+ *   infected / susceptible mass of agent j (initial cases: x(-1) = 1, s(0) = 0);
+ *   inf_i(t) = sum_{d=1}^{inf_len-1} A_c infT_c[d] x_i(t-d);  lambda_j(t) as in Eq. 1
+ *   over the static networks and the day's random network;
+ *   g_j(t) = sigmoid((log(expm1(lambda_j)) + l_j(t)) / tau) with logistic noise
+ *   l = log(u) - log(1-u), u = ((w >> 8) + 0.5) 2^-24, w = Philox(seed; j, t, 8, 0).x
+ *   (a binary Gumbel-softmax relaxation of the Eq. 2 draw);
+ *   x_j(t) = s_j(t) g_j(t);  s_j(t+1) = s_j(t) - x_j(t);  I(t) = sum_j x_j(t);
+ *   loss = (1/T) sum_t (log(I(t) + 1) - target_t)^2.
+ * theta (host float[13]) = R, B_net[0], B_net[1], B_rand, S_age[0..8]; B_net[2..3],
+ * inv_Ibar, A_class, the infectiousness curve, seed and net_seed come from params.
+ * Error messages of these calls: deabm_relaxed_last_error() (per thread).
+ * ------------------------------------------------------------------------------------------ */
+#define DEABM_N_THETA 13
+typedef struct deabm_relaxed deabm_relaxed;
+
+/* Validate and copy the graph (and build its transpose), age bins and initial
+ * cases (agents->seed_ids; the dynamic state arrays are ignored).  max_days
+ * bounds T of later calls; the reverse sweep keeps a checkpoint every
+ * ckpt_every days and recomputes the days in between.  tau > 0.
+ * Errors: DEABM_EINVAL, DEABM_ENOMEM, DEABM_ECUDA. */
+int deabm_relaxed_create(const deabm_graph *graph, const deabm_agents *agents, const deabm_params *params,
+                         float tau, uint32_t max_days, uint32_t ckpt_every, void *cuda_stream,
+                         deabm_relaxed **out);
+
+/* Forward T days at theta; incidence (host float[T], may be NULL) = I(t).  Synchronises. */
+int deabm_relaxed_forward(deabm_relaxed *ctx, uint32_t T, const float *theta, float *incidence);
+
+/* Loss and its gradient d loss / d theta (host float[13]) at theta against
+ * target (host float[T], log(I*(t) + 1)); incidence (float[T]) may be NULL.
+ * Forward with checkpoints, then the reverse sweep along the transpose of every
+ * network (the day's random contacts regenerated).  Synchronises. */
+int deabm_grad(deabm_relaxed *ctx, uint32_t T, const float *theta, const float *target, float *loss, float *grad,
+               float *incidence);
+
+/* `steps` Adam steps (lr; beta 0.9 / 0.999; eps 1e-8; parameters kept >= 0)
+ * from theta0 against target, entirely on the device.  theta_out (float[13])
+ * and loss_trace (float[steps], the loss before each step) may be NULL. */
+int deabm_calibrate(deabm_relaxed *ctx, uint32_t T, const float *theta0, const float *target, uint32_t steps,
+                    float lr, float *theta_out, float *loss_trace);
+
+const char *deabm_relaxed_last_error(void);
+
+/* Free all device memory of ctx.  NULL-safe. */
+void deabm_relaxed_destroy(deabm_relaxed *ctx);
+
 #ifdef __cplusplus
 }
 #endif

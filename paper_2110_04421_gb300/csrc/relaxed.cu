@@ -1,0 +1,658 @@
+// relaxed.cu -- the relaxed (differentiable) day step, its reverse sweep and
+// on-device Adam calibration (include/deabm.h: deabm_relaxed_*, deabm_grad,
+// deabm_calibrate).
+//
+// The paper names gradient-based calibration of the simulator ("inverse ABM",
+// Abstract, Sec. 1, Sec. 6) without defining a relaxation.  The model run here:
+//   x_j(t) = s_j(t) * g_j(t),  s_j(t+1) = s_j(t) - x_j(t),  I(t) = sum_j x_j(t)
+//   g_j(t) = sigmoid((log expm1(lambda_j(t)) + l_j(t)) / tau)   (binary Gumbel-softmax
+//            relaxation of the Eq. 2 draw; l = logistic noise from Philox stream 8)
+//   lambda_j(t) = R/I * S_{a_j} * (sum_n B_n sum_{i->j} inf_i(t) + B_r sum_rand inf_i(t))   (Eq. 1)
+//   inf_i(t) = sum_{d=1}^{L-1} A_{c_i} infT_{c_i}[d] * x_i(t-d)
+//   loss = (1/T) sum_t (log(I(t)+1) - y_t)^2
+// The reverse sweep carries d loss / d x back through the susceptible mass and,
+// along the transpose of every network, to the infectiousness of the sources;
+// the days are recomputed segment by segment from checkpoints (Philox noise and
+// random contacts are regenerated, never stored).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "deabm.h"
+#include "deabm_device.cuh"
+#include "kernels.h"
+
+namespace deabm {
+
+constexpr uint32_t kRxBlock = 256;
+constexpr int kTheta = DEABM_N_THETA;
+
+struct RxParams {
+    uint32_t n, n_nets, L, rand_on, T, nblk;
+    float tau, inv_Ibar;
+    float B_extra[DEABM_MAX_NETS];
+    uint64_t seed, net_seed;
+    const uint32_t *row_ptr[DEABM_MAX_NETS], *col[DEABM_MAX_NETS];
+    const uint32_t *tr_ptr[DEABM_MAX_NETS], *tr_col[DEABM_MAX_NETS];
+    const Tables *tab;
+    const uint8_t *age, *cls;
+    const float *theta;  // R, B_0, B_1, B_r, S_0..S_8 (device)
+};
+
+__device__ __forceinline__ float rx_weight(const RxParams &P, uint32_t net)
+{
+    return net < 2 ? P.theta[1 + net] : P.B_extra[net];
+}
+
+__device__ __forceinline__ float sigmoidf_(float z)
+{
+    if (z >= 0.0f) return 1.0f / (1.0f + expf(-z));
+    const float e = expf(z);
+    return e / (1.0f + e);
+}
+
+__device__ __forceinline__ float logit_p(float lam)
+{
+    return lam > 20.0f ? lam + log1pf(-expf(-lam)) : logf(expm1f(lam));
+}
+
+__device__ __forceinline__ float logistic_noise(uint64_t seed, uint32_t j, uint32_t t)
+{
+    const uint32_t w = draw(seed_key(seed), j, t, kStreamGumbel).x;
+    const float u = ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    return logf(u) - log1pf(-u);
+}
+
+// slot of day `day` (>= -L) in a ring of L days; day -1 -> slot 0.  Days before -1
+// map to slots not yet written this run, which hold zeros.
+__device__ __forceinline__ uint32_t ring_slot(int day, uint32_t L)
+{
+    const int m = (day + 1) % (int)L;
+    return (uint32_t)(m < 0 ? m + (int)L : m);
+}
+
+// symptom class fixed before day 0: asymptomatic (0), else severe (2), else mild (1)
+__global__ void rx_class_kernel(const RxParams P, uint8_t *cls)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const uint4 w = draw(seed_key(P.seed), i, 0xFFFFFFFEu, kStreamProg);
+    const int a = P.age[i];
+    cls[i] = (uint64_t)w.x < __ldg(&P.tab->thr_asym[a]) ? 0 : ((uint64_t)w.z < __ldg(&P.tab->thr_sev[a]) ? 2 : 1);
+}
+
+// inf_i(t) from the ring of the last L days of x
+__global__ void rx_inf_kernel(const RxParams P, int t, const float *__restrict__ xring, float *__restrict__ inf)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int c = P.cls[i];
+    float v = 0.0f;
+    for (uint32_t d = 1; d < P.L; ++d)
+        v += __ldg(&P.tab->infT[c][d]) * xring[(size_t)ring_slot(t - (int)d, P.L) * P.n + i];
+    inf[i] = v;
+}
+
+struct RxSeg {  // per-day records of one checkpoint segment (k = t - t0)
+    float *x, *g, *s, *lam, *H;  // H: [K][n_nets + 1][N]
+};
+
+template <bool REC>
+__global__ void __launch_bounds__(kRxBlock) rx_day_kernel(const RxParams P, int t, int k, const float *__restrict__ inf,
+                                                          float *__restrict__ s, float *__restrict__ xring, RxSeg seg,
+                                                          float *__restrict__ Ipart)
+{
+    __shared__ float warp_sum[kRxBlock / 32];
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    float x = 0.0f;
+    if (j < P.n) {
+        const float R = P.theta[0];
+        float ssum = 0.0f;
+        for (uint32_t net = 0; net < P.n_nets; ++net) {
+            float h = 0.0f;
+            for (uint32_t e = __ldg(P.row_ptr[net] + j); e < __ldg(P.row_ptr[net] + j + 1); ++e)
+                h = __fadd_rn(h, __ldg(inf + __ldg(P.col[net] + e)));
+            ssum = __fadd_rn(ssum, __fmul_rn(rx_weight(P, net), h));
+            if (REC) seg.H[((size_t)k * (P.n_nets + 1) + net) * P.n + j] = h;
+        }
+        float r = 0.0f;
+        if (P.rand_on) {
+            const uint2 nk = seed_key(P.net_seed);
+            uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+            uint32_t kk = 0;
+            while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+            for (uint32_t e = 0; e < kk; ++e) {
+                const uint32_t idx = e + 1u;
+                if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
+                const uint32_t xw = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+                uint32_t v = (uint32_t)(((uint64_t)xw * (uint64_t)(P.n - 1u)) >> 32);
+                v += (v >= j) ? 1u : 0u;
+                r = __fadd_rn(r, __ldg(inf + v));
+            }
+            ssum = __fadd_rn(ssum, __fmul_rn(P.theta[3], r));
+        }
+        if (REC) seg.H[((size_t)k * (P.n_nets + 1) + P.n_nets) * P.n + j] = r;
+        const float lam = R * P.inv_Ibar * P.theta[4 + P.age[j]] * ssum;
+        const float g = lam > 0.0f ? sigmoidf_((logit_p(lam) + logistic_noise(P.seed, j, (uint32_t)t)) / P.tau) : 0.0f;
+        const float sj = s[j];
+        x = sj * g;
+        s[j] = sj - x;
+        xring[(size_t)ring_slot(t, P.L) * P.n + j] = x;
+        if (REC) {
+            seg.x[(size_t)k * P.n + j] = x;
+            seg.g[(size_t)k * P.n + j] = g;
+            seg.s[(size_t)k * P.n + j] = sj;
+            seg.lam[(size_t)k * P.n + j] = lam;
+        }
+    }
+    // block partial of I(t) in a fixed order (deterministic)
+    float v = x;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.0f;
+        for (uint32_t w = 0; w < kRxBlock / 32; ++w) b += warp_sum[w];
+        Ipart[(size_t)t * P.nblk + blockIdx.x] = b;
+    }
+}
+
+// I(t), the loss and d loss / d I(t); one block
+__global__ void rx_loss_kernel(const RxParams P, uint32_t T, const float *Ipart, const float *y, float *I, float *Ibar,
+                               float *loss, float *loss_trace)
+{
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
+        double s = 0.0;
+        for (uint32_t b = 0; b < P.nblk; ++b) s += Ipart[(size_t)t * P.nblk + b];
+        I[t] = (float)s;
+        if (y) {
+            const double d = log(s + 1.0) - (double)y[t];
+            acc += d * d;
+            Ibar[t] = (float)(2.0 / T * d / (s + 1.0));
+        }
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0 && y) {
+        double L = 0.0;
+        for (uint32_t q = 0; q < blockDim.x; ++q) L += part[q];
+        *loss = (float)(L / T);
+        if (loss_trace) *loss_trace = (float)(L / T);
+    }
+}
+
+// reverse of day t: d loss / d x, d loss / d lambda, the susceptible-mass adjoint,
+// each agent's coefficient for the transpose scatter and the parameter partials
+__global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int t, int k, const float *__restrict__ Ibar,
+                                                          const float *__restrict__ ibring, float *__restrict__ sbar,
+                                                          float *__restrict__ coef, RxSeg seg, double *gpart)
+{
+    __shared__ float red[kTheta][kRxBlock / 32];
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    float contrib[kTheta];
+#pragma unroll
+    for (int q = 0; q < kTheta; ++q) contrib[q] = 0.0f;
+    if (j < P.n) {
+        const int c = P.cls[j], a = P.age[j];
+        float xbar = Ibar[t] - sbar[j];
+        for (uint32_t d = 1; d < P.L && (uint32_t)t + d < P.T; ++d)
+            xbar += __ldg(&P.tab->infT[c][d]) * ibring[(size_t)(((uint32_t)t + d) % P.L) * P.n + j];
+        const size_t q = (size_t)k * P.n + j;
+        const float g = seg.g[q], lam = seg.lam[q], sj = seg.s[q];
+        const float gbar = xbar * sj;
+        // d g / d lambda = g (1 - g) / (tau (1 - e^-lambda)); it is 0 wherever g is 0
+        // (also when lambda is so small that 1 - e^-lambda underflows in FP32)
+        const float lbar = (lam > 0.0f && g > 0.0f) ? gbar * g * (1.0f - g) / (P.tau * (-expm1f(-lam))) : 0.0f;
+        sbar[j] = xbar * g + sbar[j];
+        const float R = P.theta[0], Sa = P.theta[4 + a], cR = R * P.inv_Ibar;
+        const float cf = lbar * cR * Sa;
+        coef[j] = cf;
+        float ssum = 0.0f;
+        for (uint32_t net = 0; net <= P.n_nets; ++net) {
+            const float h = seg.H[((size_t)k * (P.n_nets + 1) + net) * P.n + j];
+            const float w = net < P.n_nets ? rx_weight(P, net) : P.theta[3];
+            ssum += w * h;
+            if (net < 2 && net < P.n_nets) contrib[1 + net] = cf * h;
+            if (net == P.n_nets && P.rand_on) contrib[3] = cf * h;
+        }
+        contrib[0] = lbar * P.inv_Ibar * Sa * ssum;
+#pragma unroll
+        for (int q2 = 0; q2 < DEABM_N_AGE; ++q2) contrib[4 + q2] = (q2 == a) ? lbar * cR * ssum : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < kTheta; ++q) {
+        float v = contrib[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kTheta) {
+        double b = 0.0;
+        for (uint32_t w = 0; w < kRxBlock / 32; ++w) b += red[threadIdx.x][w];
+        gpart[(size_t)blockIdx.x * kTheta + threadIdx.x] += b;
+    }
+}
+
+// d loss / d inf_i(t) over the static networks: gather along the transpose CSR
+__global__ void rx_scatter_static_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    float v = 0.0f;
+    for (uint32_t net = 0; net < P.n_nets; ++net) {
+        float h = 0.0f;
+        for (uint32_t e = __ldg(P.tr_ptr[net] + i); e < __ldg(P.tr_ptr[net] + i + 1); ++e)
+            h += __ldg(coef + __ldg(P.tr_col[net] + e));
+        v += rx_weight(P, net) * h;
+    }
+    ibring[(size_t)((uint32_t)t % P.L) * P.n + i] = v;
+}
+
+// ... and over the day's random network: each destination regenerates its contacts
+// and adds to theirs (atomics: the day's transpose is never stored)
+__global__ void rx_scatter_random_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n) return;
+    const float cf = coef[j] * P.theta[3];
+    if (cf == 0.0f) return;
+    const uint2 nk = seed_key(P.net_seed);
+    uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+    uint32_t kk = 0;
+    while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+    float *dst = ibring + (size_t)((uint32_t)t % P.L) * P.n;
+    for (uint32_t e = 0; e < kk; ++e) {
+        const uint32_t idx = e + 1u;
+        if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
+        const uint32_t xw = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+        uint32_t v = (uint32_t)(((uint64_t)xw * (uint64_t)(P.n - 1u)) >> 32);
+        v += (v >= j) ? 1u : 0u;
+        atomicAdd(dst + v, cf);
+    }
+}
+
+__global__ void rx_grad_reduce_kernel(const RxParams P, const double *gpart, float *grad)
+{
+    const int q = threadIdx.x;
+    if (q >= kTheta) return;
+    double s = 0.0;
+    for (uint32_t b = 0; b < P.nblk; ++b) s += gpart[(size_t)b * kTheta + q];
+    grad[q] = (float)s;
+}
+
+// projected Adam on theta (parameters stay >= 0)
+__global__ void adam_kernel(float *theta, float *m, float *v, const float *grad, float lr, float b1, float b2, float eps,
+                            int step)
+{
+    const int q = threadIdx.x;
+    if (q >= kTheta) return;
+    const float g = grad[q];
+    m[q] = b1 * m[q] + (1.0f - b1) * g;
+    v[q] = b2 * v[q] + (1.0f - b2) * g * g;
+    const float mh = m[q] / (1.0f - powf(b1, (float)step)), vh = v[q] / (1.0f - powf(b2, (float)step));
+    theta[q] = fmaxf(theta[q] - lr * mh / (sqrtf(vh) + eps), 0.0f);
+}
+
+__global__ void rx_init_kernel(const RxParams P, const uint32_t *seeds, uint32_t n_seeds, float *s, float *xring)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) s[i] = 1.0f;
+    for (size_t q = i; q < (size_t)P.L * P.n; q += (size_t)gridDim.x * blockDim.x) xring[q] = 0.0f;
+}
+
+__global__ void rx_seed_kernel(const RxParams P, const uint32_t *seeds, uint32_t n_seeds, float *s, float *xring)
+{
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_seeds) return;
+    s[seeds[q]] = 0.0f;
+    xring[seeds[q]] = 1.0f;  // slot 0 = day -1
+}
+
+}  // namespace deabm
+
+using namespace deabm;
+
+// ------------------------------------------------------------------------------------ host side
+struct deabm_relaxed {
+    cudaStream_t stream = nullptr;
+    uint32_t n = 0, L = 0, max_days = 0, K = 10, nseg = 0, n_nets = 0, n_seeds = 0;
+    std::vector<void *> allocs;
+    RxParams P{};
+    float *theta = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+    float *s = nullptr, *xring = nullptr, *inf = nullptr, *ckpt = nullptr;
+    RxSeg seg{};
+    float *Ipart = nullptr, *I = nullptr, *y = nullptr, *Ibar = nullptr, *loss = nullptr, *loss_trace = nullptr;
+    float *ibring = nullptr, *sbar = nullptr, *coef = nullptr;
+    double *gpart = nullptr;
+    uint32_t *seeds = nullptr;
+    uint32_t trace_cap = 0;
+};
+
+static thread_local std::string g_rx_err;
+
+static int rx_fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_rx_err = buf;
+    return code;
+}
+
+#define RCU(call)                                                                                                  \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess)                                                                                     \
+            return rx_fail(e_ == cudaErrorMemoryAllocation ? DEABM_ENOMEM : DEABM_ECUDA, "%s: %s (%s:%d)", #call, \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
+    } while (0)
+
+template <class T>
+static int rx_alloc(deabm_relaxed *c, T **out, size_t count)
+{
+    void *p = nullptr;
+    const size_t bytes = count ? count * sizeof(T) : sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return rx_fail(DEABM_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    c->allocs.push_back(p);
+    *out = (T *)p;
+    return DEABM_OK;
+}
+
+static uint64_t rx_threshold(double p)
+{
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+extern "C" void deabm_relaxed_destroy(deabm_relaxed *c)
+{
+    if (!c) return;
+    if (!c->allocs.empty()) (void)cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs) (void)cudaFree(p);
+    delete c;
+}
+
+extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a, const deabm_params *p, float tau,
+                                    uint32_t max_days, uint32_t ckpt_every, void *stream, deabm_relaxed **out)
+{
+    if (!out) return rx_fail(DEABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g || !a || !p || !a->age_bin) return rx_fail(DEABM_EINVAL, "graph, agents (age_bin) and params are required");
+    const uint32_t n = g->n_agents;
+    if (n == 0 || n >= (1u << 31) || g->n_nets > DEABM_MAX_NETS) return rx_fail(DEABM_EINVAL, "bad graph size");
+    if (!(tau > 0.0f)) return rx_fail(DEABM_EINVAL, "tau must be > 0");
+    if (max_days == 0 || ckpt_every == 0) return rx_fail(DEABM_EINVAL, "max_days and ckpt_every must be >= 1");
+    if (p->inf_len < 2 || p->inf_len > DEABM_MAX_INF_LEN) return rx_fail(DEABM_EINVAL, "inf_len must be 2..64");
+    if (g->rand_mean > 0.0f && n < 2) return rx_fail(DEABM_EINVAL, "the random network needs >= 2 agents");
+    for (uint32_t k = 0; k < g->n_nets; ++k) {
+        const uint32_t *rp = g->row_ptr[k];
+        if (!rp || rp[0] != 0 || (rp[n] && !g->col[k])) return rx_fail(DEABM_EINVAL, "bad CSR %u", k);
+        for (uint32_t j = 0; j < n; ++j) {
+            if (rp[j + 1] < rp[j]) return rx_fail(DEABM_EINVAL, "row_ptr[%u] decreases at %u", k, j);
+            for (uint32_t e = rp[j]; e < rp[j + 1]; ++e)
+                if (g->col[k][e] >= n || g->col[k][e] == j) return rx_fail(DEABM_EINVAL, "bad column in network %u", k);
+        }
+    }
+    for (uint32_t j = 0; j < n; ++j)
+        if (a->age_bin[j] >= DEABM_N_AGE) return rx_fail(DEABM_EINVAL, "age_bin out of range");
+    for (uint32_t q = 0; q < a->n_seed; ++q)
+        if (!a->seed_ids || a->seed_ids[q] >= n) return rx_fail(DEABM_EINVAL, "bad seed id");
+
+    deabm_relaxed *c = new (std::nothrow) deabm_relaxed();
+    if (!c) return rx_fail(DEABM_ENOMEM, "host allocation failed");
+    int rc = [&]() -> int {
+        c->stream = (cudaStream_t)stream;
+        cudaStream_t s = c->stream;
+        c->n = n;
+        c->L = p->inf_len;
+        c->max_days = max_days;
+        c->K = ckpt_every;
+        c->nseg = (max_days + ckpt_every - 1) / ckpt_every;
+        c->n_nets = g->n_nets;
+        const uint32_t nblk = (n + kRxBlock - 1) / kRxBlock;
+        RxParams &P = c->P;
+        P.n = n;
+        P.n_nets = g->n_nets;
+        P.L = p->inf_len;
+        P.rand_on = g->rand_mean > 0.0f;
+        P.nblk = nblk;
+        P.tau = tau;
+        P.inv_Ibar = p->inv_Ibar;
+        for (int k = 0; k < DEABM_MAX_NETS; ++k) P.B_extra[k] = p->B_net[k];
+        P.seed = p->seed;
+        P.net_seed = p->net_seed;
+        int r;
+        std::vector<uint32_t> tptr, tcol, fill;
+        for (uint32_t k = 0; k < g->n_nets; ++k) {
+            const uint32_t E = g->row_ptr[k][n];
+            uint32_t *rp, *cl, *trp, *tcl;
+            if ((r = rx_alloc(c, &rp, (size_t)n + 1))) return r;
+            if ((r = rx_alloc(c, &cl, E))) return r;
+            if ((r = rx_alloc(c, &trp, (size_t)n + 1))) return r;
+            if ((r = rx_alloc(c, &tcl, E))) return r;
+            // transpose (out-edges of each source, destinations ascending) by counting sort
+            tptr.assign((size_t)n + 1, 0);
+            for (uint32_t e = 0; e < E; ++e) tptr[g->col[k][e] + 1]++;
+            for (uint32_t i = 0; i < n; ++i) tptr[i + 1] += tptr[i];
+            fill.assign(tptr.begin(), tptr.end() - 1);
+            tcol.resize(E);
+            for (uint32_t j = 0; j < n; ++j)
+                for (uint32_t e = g->row_ptr[k][j]; e < g->row_ptr[k][j + 1]; ++e) tcol[fill[g->col[k][e]]++] = j;
+            RCU(cudaMemcpyAsync(rp, g->row_ptr[k], 4ull * (n + 1), cudaMemcpyHostToDevice, s));
+            if (E) RCU(cudaMemcpyAsync(cl, g->col[k], 4ull * E, cudaMemcpyHostToDevice, s));
+            RCU(cudaMemcpyAsync(trp, tptr.data(), 4ull * (n + 1), cudaMemcpyHostToDevice, s));
+            if (E) RCU(cudaMemcpyAsync(tcl, tcol.data(), 4ull * E, cudaMemcpyHostToDevice, s));
+            RCU(cudaStreamSynchronize(s));
+            P.row_ptr[k] = rp;
+            P.col[k] = cl;
+            P.tr_ptr[k] = trp;
+            P.tr_col[k] = tcl;
+        }
+        uint8_t *age, *cls;
+        if ((r = rx_alloc(c, &age, n))) return r;
+        if ((r = rx_alloc(c, &cls, n))) return r;
+        RCU(cudaMemcpyAsync(age, a->age_bin, n, cudaMemcpyHostToDevice, s));
+        P.age = age;
+        P.cls = cls;
+        Tables T;
+        std::memset(&T, 0, sizeof T);
+        {
+            const double m = (double)g->rand_mean;
+            volatile double t = std::exp(-m), cdf = t;
+            T.pois[0] = rx_threshold(cdf);
+            for (int k = 1; k < DEABM_POIS_CAP; ++k) {
+                t = (t * m) / (double)k;
+                cdf = cdf + t;
+                T.pois[k] = rx_threshold(cdf);
+            }
+        }
+        for (int q = 0; q < DEABM_N_AGE; ++q) {
+            T.thr_asym[q] = rx_threshold(p->p_asym[q]);
+            T.thr_sev[q] = rx_threshold(p->p_sev[q]);
+        }
+        Tables *tab;
+        if ((r = rx_alloc(c, &tab, 1))) return r;
+        RCU(cudaMemcpyAsync(tab, &T, sizeof T, cudaMemcpyHostToDevice, s));
+        double *d_gamma;
+        float *d_A;
+        if ((r = rx_alloc(c, &d_gamma, 6))) return r;
+        if ((r = rx_alloc(c, &d_A, 3))) return r;
+        const double gs[6] = {p->inf_shape[0], p->inf_shape[1], p->inf_shape[2],
+                              p->inf_scale[0], p->inf_scale[1], p->inf_scale[2]};
+        RCU(cudaMemcpyAsync(d_gamma, gs, sizeof gs, cudaMemcpyHostToDevice, s));
+        RCU(cudaMemcpyAsync(d_A, p->A_class, sizeof(float) * 3, cudaMemcpyHostToDevice, s));
+        RCU(launch_inf_table(tab, d_gamma, d_A, p->inf_len, s));
+        P.tab = tab;
+        if ((r = rx_alloc(c, &c->theta, kTheta))) return r;
+        if ((r = rx_alloc(c, &c->adam_m, kTheta))) return r;
+        if ((r = rx_alloc(c, &c->adam_v, kTheta))) return r;
+        if ((r = rx_alloc(c, &c->grad, kTheta))) return r;
+        P.theta = c->theta;
+        rx_class_kernel<<<(n + 255) / 256, 256, 0, s>>>(P, cls);
+        RCU(cudaGetLastError());
+        const size_t L = c->L, K = c->K, NN = (size_t)g->n_nets + 1;
+        if ((r = rx_alloc(c, &c->s, n))) return r;
+        if ((r = rx_alloc(c, &c->xring, L * n))) return r;
+        if ((r = rx_alloc(c, &c->inf, n))) return r;
+        if ((r = rx_alloc(c, &c->ckpt, (size_t)c->nseg * (L + 1) * n))) return r;
+        if ((r = rx_alloc(c, &c->seg.x, K * n))) return r;
+        if ((r = rx_alloc(c, &c->seg.g, K * n))) return r;
+        if ((r = rx_alloc(c, &c->seg.s, K * n))) return r;
+        if ((r = rx_alloc(c, &c->seg.lam, K * n))) return r;
+        if ((r = rx_alloc(c, &c->seg.H, K * NN * n))) return r;
+        if ((r = rx_alloc(c, &c->Ipart, (size_t)max_days * nblk))) return r;
+        if ((r = rx_alloc(c, &c->I, max_days))) return r;
+        if ((r = rx_alloc(c, &c->y, max_days))) return r;
+        if ((r = rx_alloc(c, &c->Ibar, max_days))) return r;
+        if ((r = rx_alloc(c, &c->loss, 1))) return r;
+        if ((r = rx_alloc(c, &c->ibring, L * n))) return r;
+        if ((r = rx_alloc(c, &c->sbar, n))) return r;
+        if ((r = rx_alloc(c, &c->coef, n))) return r;
+        if ((r = rx_alloc(c, &c->gpart, (size_t)nblk * kTheta))) return r;
+        c->n_seeds = a->n_seed;
+        if ((r = rx_alloc(c, &c->seeds, a->n_seed))) return r;
+        if (a->n_seed) RCU(cudaMemcpyAsync(c->seeds, a->seed_ids, 4ull * a->n_seed, cudaMemcpyHostToDevice, s));
+        RCU(cudaStreamSynchronize(s));
+        return DEABM_OK;
+    }();
+    if (rc != DEABM_OK) {
+        deabm_relaxed_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return DEABM_OK;
+}
+
+// forward days [0, T): checkpoints every K days; records nothing else
+static int rx_forward_device(deabm_relaxed *c, uint32_t T, const float *y_dev, float *loss_trace_slot)
+{
+    cudaStream_t s = c->stream;
+    RxParams P = c->P;
+    P.T = T;
+    const uint32_t n = c->n, L = c->L, nb = (n + kRxBlock - 1) / kRxBlock;
+    rx_init_kernel<<<nb, kRxBlock, 0, s>>>(P, c->seeds, c->n_seeds, c->s, c->xring);
+    if (c->n_seeds) rx_seed_kernel<<<(c->n_seeds + 255) / 256, 256, 0, s>>>(P, c->seeds, c->n_seeds, c->s, c->xring);
+    RCU(cudaGetLastError());
+    for (uint32_t t = 0; t < T; ++t) {
+        if (t % c->K == 0) {
+            float *ck = c->ckpt + (size_t)(t / c->K) * (L + 1) * n;
+            RCU(cudaMemcpyAsync(ck, c->s, 4ull * n, cudaMemcpyDeviceToDevice, s));
+            RCU(cudaMemcpyAsync(ck + n, c->xring, 4ull * L * n, cudaMemcpyDeviceToDevice, s));
+        }
+        rx_inf_kernel<<<nb, kRxBlock, 0, s>>>(P, (int)t, c->xring, c->inf);
+        rx_day_kernel<false><<<nb, kRxBlock, 0, s>>>(P, (int)t, 0, c->inf, c->s, c->xring, c->seg, c->Ipart);
+    }
+    rx_loss_kernel<<<1, 256, 0, s>>>(P, T, c->Ipart, y_dev, c->I, c->Ibar, c->loss, loss_trace_slot);
+    RCU(cudaGetLastError());
+    return DEABM_OK;
+}
+
+static int rx_backward_device(deabm_relaxed *c, uint32_t T)
+{
+    cudaStream_t s = c->stream;
+    RxParams P = c->P;
+    P.T = T;
+    const uint32_t n = c->n, L = c->L, nb = (n + kRxBlock - 1) / kRxBlock;
+    RCU(cudaMemsetAsync(c->sbar, 0, 4ull * n, s));
+    RCU(cudaMemsetAsync(c->ibring, 0, 4ull * L * n, s));
+    RCU(cudaMemsetAsync(c->gpart, 0, sizeof(double) * nb * kTheta, s));
+    const uint32_t nseg = (T + c->K - 1) / c->K;
+    for (int sg = (int)nseg - 1; sg >= 0; --sg) {
+        const uint32_t t0 = (uint32_t)sg * c->K, t1 = t0 + c->K < T ? t0 + c->K : T;
+        const float *ck = c->ckpt + (size_t)sg * (L + 1) * n;
+        RCU(cudaMemcpyAsync(c->s, ck, 4ull * n, cudaMemcpyDeviceToDevice, s));
+        RCU(cudaMemcpyAsync(c->xring, ck + n, 4ull * L * n, cudaMemcpyDeviceToDevice, s));
+        for (uint32_t t = t0; t < t1; ++t) {  // recompute the segment, recording it
+            rx_inf_kernel<<<nb, kRxBlock, 0, s>>>(P, (int)t, c->xring, c->inf);
+            rx_day_kernel<true><<<nb, kRxBlock, 0, s>>>(P, (int)t, (int)(t - t0), c->inf, c->s, c->xring, c->seg, c->Ipart);
+        }
+        for (int t = (int)t1 - 1; t >= (int)t0; --t) {
+            rx_adj_kernel<<<nb, kRxBlock, 0, s>>>(P, t, t - (int)t0, c->Ibar, c->ibring, c->sbar, c->coef, c->seg, c->gpart);
+            rx_scatter_static_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
+            if (P.rand_on) rx_scatter_random_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
+        }
+    }
+    rx_grad_reduce_kernel<<<1, 32, 0, s>>>(P, c->gpart, c->grad);
+    RCU(cudaGetLastError());
+    return DEABM_OK;
+}
+
+static int rx_check(deabm_relaxed *c, uint32_t T)
+{
+    if (!c) return rx_fail(DEABM_EINVAL, "ctx is NULL");
+    if (T == 0 || T > c->max_days) return rx_fail(DEABM_EINVAL, "T must be in 1..max_days (%u)", c->max_days);
+    return DEABM_OK;
+}
+
+extern "C" int deabm_relaxed_forward(deabm_relaxed *c, uint32_t T, const float *theta, float *incidence)
+{
+    int r;
+    if ((r = rx_check(c, T))) return r;
+    if (!theta) return rx_fail(DEABM_EINVAL, "theta is NULL");
+    RCU(cudaMemcpyAsync(c->theta, theta, 4 * kTheta, cudaMemcpyHostToDevice, c->stream));
+    if ((r = rx_forward_device(c, T, nullptr, nullptr))) return r;
+    if (incidence) RCU(cudaMemcpyAsync(incidence, c->I, 4ull * T, cudaMemcpyDeviceToHost, c->stream));
+    RCU(cudaStreamSynchronize(c->stream));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_grad(deabm_relaxed *c, uint32_t T, const float *theta, const float *target, float *loss,
+                          float *grad, float *incidence)
+{
+    int r;
+    if ((r = rx_check(c, T))) return r;
+    if (!theta || !target) return rx_fail(DEABM_EINVAL, "theta and target are required");
+    RCU(cudaMemcpyAsync(c->theta, theta, 4 * kTheta, cudaMemcpyHostToDevice, c->stream));
+    RCU(cudaMemcpyAsync(c->y, target, 4ull * T, cudaMemcpyHostToDevice, c->stream));
+    if ((r = rx_forward_device(c, T, c->y, nullptr))) return r;
+    if ((r = rx_backward_device(c, T))) return r;
+    if (loss) RCU(cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
+    if (grad) RCU(cudaMemcpyAsync(grad, c->grad, 4 * kTheta, cudaMemcpyDeviceToHost, c->stream));
+    if (incidence) RCU(cudaMemcpyAsync(incidence, c->I, 4ull * T, cudaMemcpyDeviceToHost, c->stream));
+    RCU(cudaStreamSynchronize(c->stream));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_calibrate(deabm_relaxed *c, uint32_t T, const float *theta0, const float *target, uint32_t steps,
+                               float lr, float *theta_out, float *loss_trace)
+{
+    int r;
+    if ((r = rx_check(c, T))) return r;
+    if (!theta0 || !target || !(lr > 0.0f)) return rx_fail(DEABM_EINVAL, "theta0, target and lr > 0 are required");
+    if (steps > c->trace_cap) {
+        float *tr;
+        if ((r = rx_alloc(c, &tr, steps))) return r;
+        c->loss_trace = tr;
+        c->trace_cap = steps;
+    }
+    RCU(cudaMemcpyAsync(c->theta, theta0, 4 * kTheta, cudaMemcpyHostToDevice, c->stream));
+    RCU(cudaMemcpyAsync(c->y, target, 4ull * T, cudaMemcpyHostToDevice, c->stream));
+    RCU(cudaMemsetAsync(c->adam_m, 0, 4 * kTheta, c->stream));
+    RCU(cudaMemsetAsync(c->adam_v, 0, 4 * kTheta, c->stream));
+    for (uint32_t it = 0; it < steps; ++it) {
+        if ((r = rx_forward_device(c, T, c->y, c->loss_trace + it))) return r;
+        if ((r = rx_backward_device(c, T))) return r;
+        adam_kernel<<<1, 32, 0, c->stream>>>(c->theta, c->adam_m, c->adam_v, c->grad, lr, 0.9f, 0.999f, 1e-8f, (int)it + 1);
+        RCU(cudaGetLastError());
+    }
+    if (theta_out) RCU(cudaMemcpyAsync(theta_out, c->theta, 4 * kTheta, cudaMemcpyDeviceToHost, c->stream));
+    if (loss_trace && steps) RCU(cudaMemcpyAsync(loss_trace, c->loss_trace, 4ull * steps, cudaMemcpyDeviceToHost, c->stream));
+    RCU(cudaStreamSynchronize(c->stream));
+    return DEABM_OK;
+}
+
+extern "C" const char *deabm_relaxed_last_error(void) { return g_rx_err.c_str(); }

@@ -20,7 +20,9 @@ STAGES = ("S", "ASYM", "PRE_MILD", "PRE_SEV", "MILD", "SEV", "HOSP", "ICU", "REC
 
 EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "deabm_get_state",
            "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_last_error",
-           "deabm_destroy")
+           "deabm_destroy", "deabm_relaxed_create", "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate",
+           "deabm_relaxed_last_error", "deabm_relaxed_destroy")
+N_THETA = 13
 
 
 class DeabmError(RuntimeError):
@@ -83,8 +85,18 @@ def lib():
         L.deabm_last_error.restype = C.c_char_p
         L.deabm_destroy.argtypes = [vp]
         L.deabm_destroy.restype = None
+        L.deabm_relaxed_create.argtypes = [C.POINTER(Graph), C.POINTER(Agents), C.POINTER(Params), C.c_float, u32,
+                                           u32, vp, C.POINTER(vp)]
+        L.deabm_relaxed_forward.argtypes = [vp, u32, vp, vp]
+        L.deabm_grad.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+        L.deabm_calibrate.argtypes = [vp, u32, vp, vp, u32, C.c_float, vp, vp]
+        L.deabm_relaxed_last_error.argtypes = []
+        L.deabm_relaxed_last_error.restype = C.c_char_p
+        L.deabm_relaxed_destroy.argtypes = [vp]
+        L.deabm_relaxed_destroy.restype = None
         for name in ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "deabm_get_state",
-                     "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync"):
+                     "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_relaxed_create",
+                     "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -138,6 +150,112 @@ def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False, local
     p.keep_lambda = 1 if keep_lambda else 0
     p.locality_order = 1 if locality_order else 0
     return p
+
+
+def _graph_struct(graph: dict, rand_mean: float, keep: list) -> Graph:
+    g = Graph()
+    g.n_agents = int(graph["n"])
+    g.n_nets = len(graph["row_ptr"])
+    for i, (rp, cl) in enumerate(zip(graph["row_ptr"], graph["col"])):
+        rp = np.ascontiguousarray(rp, dtype=np.uint32)
+        cl = np.ascontiguousarray(cl, dtype=np.uint32)
+        keep += [rp, cl]
+        g.row_ptr[i] = rp.ctypes.data
+        g.col[i] = cl.ctypes.data if cl.size else None
+    g.rand_mean = rand_mean
+    return g
+
+
+def theta_of(params: dict) -> np.ndarray:
+    """theta = (R, B_net[0], B_net[1], B_rand, S_age[0..8]) as float32."""
+    B = list(params["B_net"]) + [0.0, 0.0]
+    return np.array([params["R"], B[0], B[1], params["B_rand"], *params["S_age"]], np.float32)
+
+
+def _rx_check(rc):
+    if rc != OK:
+        raise DeabmError(rc, lib().deabm_relaxed_last_error().decode(errors="replace"))
+
+
+class Relaxed:
+    """The relaxed (Gumbel-softmax) simulation on the GPU: forward, loss gradient
+    by the library's reverse sweep, and on-device Adam calibration."""
+
+    def __init__(self, graph: dict, params: dict, age, seed_ids=None, tau: float = 0.5, max_days: int = 90,
+                 ckpt_every: int = 10, stream=None):
+        L = lib()
+        keep = []
+        g = _graph_struct(graph, params["rand_mean"], keep)
+        a = Agents()
+        age = np.ascontiguousarray(age, dtype=np.uint8)
+        keep.append(age)
+        a.age_bin = age.ctypes.data
+        if seed_ids is not None and len(seed_ids):
+            ids = np.ascontiguousarray(seed_ids, dtype=np.uint32)
+            keep.append(ids)
+            a.seed_ids = ids.ctypes.data
+            a.n_seed = ids.size
+        p = make_params(params)
+        self._stream = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
+        ctx = C.c_void_p()
+        _rx_check(L.deabm_relaxed_create(C.byref(g), C.byref(a), C.byref(p), tau, max_days, ckpt_every,
+                                         self._stream, C.byref(ctx)))
+        self.ctx = ctx
+        self.max_days = max_days
+
+    def forward(self, theta, T: int) -> np.ndarray:
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        inc = np.zeros(T, np.float32)
+        _rx_check(lib().deabm_relaxed_forward(self.ctx, T, _p(th), _p(inc)))
+        return inc
+
+    def grad(self, theta, target):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        y = np.ascontiguousarray(target, dtype=np.float32)
+        T = y.size
+        loss = np.zeros(1, np.float32)
+        g = np.zeros(N_THETA, np.float32)
+        inc = np.zeros(T, np.float32)
+        _rx_check(lib().deabm_grad(self.ctx, T, _p(th), _p(y), _p(loss), _p(g), _p(inc)))
+        return float(loss[0]), g, inc
+
+    def calibrate(self, theta0, target, steps: int, lr: float):
+        th0 = np.ascontiguousarray(theta0, dtype=np.float32)
+        y = np.ascontiguousarray(target, dtype=np.float32)
+        out = np.zeros(N_THETA, np.float32)
+        trace = np.zeros(steps, np.float32)
+        _rx_check(lib().deabm_calibrate(self.ctx, y.size, _p(th0), _p(y), steps, lr, _p(out), _p(trace)))
+        return out, trace
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().deabm_relaxed_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def relaxed_loss(sim: "Relaxed", theta, target):
+    """torch autograd entry: loss(theta) whose backward is the library's reverse sweep."""
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th, y):
+            loss, g, _ = sim.grad(th.detach().cpu().numpy(), y.detach().cpu().numpy())
+            ctx.save_for_backward(torch.from_numpy(g).to(th.device))
+            return torch.tensor(loss, dtype=th.dtype, device=th.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g.to(gout.dtype), None
+
+    return _Fn.apply(theta, target)
 
 
 class Simulation:

@@ -183,3 +183,14 @@ def batched():
     0.3%/day from day 20 with a per-replicate second-dose delay."""
     return dict(name="batched N=1e5 B=256 T=180", n=100_000, B=256, T=180, n_seed=10,
                 params=params_with(vax_on=1, vax_start=20, vax_rate=0.003))
+
+
+def relaxed_workload():
+    """Differentiable inverse run: N = 100,000, 90 days, tau = 0.5; the target curve
+    comes from hidden parameters R = 3.5, weights 2.0 / 1.0 / 0.7 (household,
+    occupation, random); calibration starts from R = 2.5, weights 1.0 / 1.0 / 1.0."""
+    p = params_with(seed=0, net_seed=0)
+    hidden = np.array([3.5, 2.0, 1.0, 0.7] + [1.0] * N_AGE, np.float32)
+    start = np.array([2.5, 1.0, 1.0, 1.0] + [1.0] * N_AGE, np.float32)
+    return dict(name="relaxed N=1e5 T=90 tau=0.5", n=100_000, T=90, tau=0.5, n_seed=10, params=p,
+                hidden=hidden, start=start, steps=200, lr=0.02)

@@ -1,0 +1,129 @@
+"""Relaxed (Gumbel-softmax) path on the GPU against the FP64 oracle.
+
+Bars: incidence within 1e-4 relative of the FP64 forward (FP32 sums over 90
+days); gradient within 1e-3 relative of central finite differences (h = 1e-3)
+of the FP64 oracle and within 1e-4 (relative to the gradient's norm) of the
+oracle's own reverse sweep; the checkpoint interval changes nothing but
+rounding."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_04421_gb300 import workloads as W
+from tests.helpers import gpu_available
+
+pytestmark = pytest.mark.gpu
+
+if not gpu_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def case():
+    pop = W.population(4000, 7, 12)
+    p = W.params_with(R=3.3, seed=31, net_seed=32, S_age=[0.6, 0.8, 1.0, 1.1, 1.2, 0.9, 1.3, 1.0, 0.7])
+    T = 60
+    rx = oracle.Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=0.5)
+    th = oracle.theta_of(p)
+    hidden = th.copy()
+    hidden[0], hidden[1], hidden[2], hidden[3] = 3.8, 2.2, 0.9, 0.8
+    y = np.log(rx.run(hidden, T)["incidence"] + 1.0).astype(np.float32)
+    return pop, p, T, rx, th, y
+
+
+def gpu(pop, p, **kw):
+    from paper_2110_04421_gb300.deabm import Relaxed
+    return Relaxed(pop, p, pop["age"], pop["seed_ids"], **kw)
+
+
+def test_forward_matches_oracle(case):
+    pop, p, T, rx, th, y = case
+    g = gpu(pop, p, max_days=T)
+    inc = g.forward(th, T)
+    g.close()
+    ref = rx.run(th, T)["incidence"]
+    assert np.all(np.abs(inc - ref) <= 1e-4 * np.maximum(ref, 1.0)), np.max(np.abs(inc - ref) / np.maximum(ref, 1))
+
+
+def test_gradient_matches_oracle_adjoint_and_fd(case):
+    pop, p, T, rx, th, y = case
+    g = gpu(pop, p, max_days=T, ckpt_every=10)
+    loss, grad, inc = g.grad(th, y)
+    g.close()
+    o = rx.run(th, T, target=y.astype(np.float64), grad=True)
+    assert abs(loss - o["loss"]) <= 1e-4 * o["loss"]
+    scale = np.linalg.norm(o["grad"])
+    assert np.max(np.abs(grad - o["grad"])) <= 1e-4 * scale, (grad, o["grad"])
+    th64 = np.float32(th).astype(np.float64)
+    for i in range(13):
+        h = 1e-3
+        tp, tm = th64.copy(), th64.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (rx.run(tp, T, target=y, fp32_theta=False)["loss"] - rx.run(tm, T, target=y, fp32_theta=False)["loss"]) / (2 * h)
+        assert abs(grad[i] - fd) <= 1e-3 * max(abs(fd), 1e-2 * scale), (i, grad[i], fd)
+
+
+def test_checkpoint_interval_changes_only_rounding(case):
+    pop, p, T, rx, th, y = case
+    grads = []
+    for k in (1, 7, 10, T):
+        g = gpu(pop, p, max_days=T, ckpt_every=k)
+        grads.append(g.grad(th, y)[1])
+        g.close()
+    for gr in grads[1:]:
+        assert np.max(np.abs(gr - grads[0])) <= 1e-5 * np.linalg.norm(grads[0])
+
+
+def test_autograd_function(case):
+    import torch
+    from paper_2110_04421_gb300.deabm import relaxed_loss
+    pop, p, T, rx, th, y = case
+    g = gpu(pop, p, max_days=T)
+    theta = torch.tensor(np.float32(th), requires_grad=True)
+    loss = relaxed_loss(g, theta, torch.tensor(y))
+    (3.0 * loss).backward()
+    _, grad, _ = g.grad(th, y)
+    g.close()
+    assert torch.allclose(theta.grad, torch.tensor(3.0 * grad), rtol=1e-5, atol=1e-7)
+
+
+def test_calibration_reduces_loss(case):
+    pop, p, T, rx, th, y = case
+    g = gpu(pop, p, max_days=T)
+    out, trace = g.calibrate(th, y, steps=40, lr=0.02)
+    loss_after, _, _ = g.grad(out, y)
+    g.close()
+    assert trace[0] > 0 and loss_after < 0.5 * trace[0], (trace[0], loss_after)
+    assert np.all(out >= 0)
+
+
+def test_full_size_gradient():
+    """N = 100,000, 90 days, tau = 0.5, checkpoint every 10 days; target simulated
+    at hidden parameters R = 3.5, weights 2.0 / 1.0 / 0.7."""
+    w = W.relaxed_workload()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    p, T = w["params"], w["T"]
+    rx = oracle.Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=w["tau"])
+    y = np.log(rx.run(w["hidden"], T)["incidence"] + 1.0).astype(np.float32)
+    th = w["start"]
+    g = gpu(pop, p, max_days=T, ckpt_every=10, tau=w["tau"])
+    loss, grad, _ = g.grad(th, y)
+    g.close()
+    o = rx.run(th, T, target=y, grad=True)
+    scale = np.linalg.norm(o["grad"])
+    assert abs(loss - o["loss"]) <= 1e-4 * o["loss"]
+    assert np.max(np.abs(grad - o["grad"])) <= 1e-4 * scale
+    th64 = np.float32(th).astype(np.float64)
+    for i in (0, 1, 3, 4):
+        tp, tm = th64.copy(), th64.copy()
+        tp[i] += 1e-3
+        tm[i] -= 1e-3
+        fd = (rx.run(tp, T, target=y, fp32_theta=False)["loss"] - rx.run(tm, T, target=y, fp32_theta=False)["loss"]) / 2e-3
+        assert abs(grad[i] - fd) <= 1e-3 * max(abs(fd), 1e-2 * scale), (i, grad[i], fd)
