@@ -191,6 +191,13 @@ int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *new_inf, int
  * Any output may be NULL.  Synchronises. */
 int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *poisson_thr, int16_t *dose1_day);
 
+/* Restart a context at day 0 with new per-replicate parameters and seeds (same
+ * layout as deabm_create_batch; both NULL keeps the current ones): the initial
+ * state given at create is restored, the initial cases are infected again with
+ * the new seeds, the per-day counters are cleared.  Lets one context generate
+ * many ensembles without re-uploading the graph.  Asynchronous. */
+int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_seeds);
+
 /* Days run so far, agents, replicates. */
 int deabm_info(const deabm_ctx *ctx, uint32_t *day, uint32_t *n_agents, uint32_t *n_rep);
 
@@ -255,6 +262,39 @@ const char *deabm_relaxed_last_error(void);
 
 /* Free all device memory of ctx.  NULL-safe. */
 void deabm_relaxed_destroy(deabm_relaxed *ctx);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned surrogate: an MLP from the 14 simulation parameters to the daily
+ * log incidence (not in the paper, which only hopes to bring agent-based models
+ * and learning closer, Sec. 6).  n_in -> hidden x depth (erf-GELU) -> n_out,
+ * BF16 operands with FP32 accumulation on the tensor cores, FP32 master weights.
+ * Parameter layout (FP32, host): for each layer l, W_l [fan_in x fan_out]
+ * row-major, then b_l [fan_out].  Data pointers x / y are DEVICE FP32 arrays
+ * [batch x n_in] / [batch x n_out] (the caller's allocation).  Errors:
+ * deabm_mlp_last_error() (per thread).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct deabm_mlp deabm_mlp;
+
+/* hidden % 8 == 0, n_out even, 1 <= depth <= 16, batch <= max_batch <= 2^22. */
+int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, uint32_t n_out, uint32_t max_batch,
+                     void *cuda_stream, deabm_mlp **out);
+int deabm_mlp_param_count(const deabm_mlp *mlp, uint64_t *count);
+/* Load FP32 parameters (host, layout above) and reset the Adam state.  Synchronises. */
+int deabm_mlp_set_params(deabm_mlp *mlp, const float *params);
+/* Copy the FP32 parameters and / or the last computed gradients (host; either may be NULL). */
+int deabm_mlp_get_params(deabm_mlp *mlp, float *params, float *grads);
+/* y = MLP(x) for `batch` rows (device pointers).  Asynchronous. */
+int deabm_mlp_forward(deabm_mlp *mlp, const float *x, uint32_t batch, float *y);
+/* Loss (1/(batch n_out)) sum (MLP(x) - y)^2 and its gradients (kept in the
+ * context, read with deabm_mlp_get_params); loss -> host float, may be NULL. */
+int deabm_mlp_grad(deabm_mlp *mlp, const float *x, const float *y, uint32_t batch, float *loss);
+/* deabm_mlp_grad, then one Adam step (beta 0.9 / 0.999, eps 1e-8) with rate lr.
+ * loss (host, may be NULL: no synchronisation) is the loss before the step. */
+int deabm_mlp_train_step(deabm_mlp *mlp, const float *x, const float *y, uint32_t batch, float lr, float *loss);
+int deabm_mlp_sync(deabm_mlp *mlp);
+const char *deabm_mlp_last_error(void);
+/* NULL-safe. */
+void deabm_mlp_destroy(deabm_mlp *mlp);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,10 @@ struct deabm_ctx {
     Rep *rep = nullptr;
     Counters C{};
     KParams kp{};
+    StateRef S0{};                 // initial state as given at create (before the initial cases)
+    uint32_t *seed_ids = nullptr;  // initial cases, internal ids
+    uint32_t n_seed = 0;
+    deabm_params base{};
     std::string err;
 };
 
@@ -187,6 +191,33 @@ static void locality_order(const deabm_graph *g, std::vector<uint32_t> &order)
     }
 }
 
+// per-replicate parameter blocks: rep_params rows override the base parameters
+static void build_reps(const deabm_params *p, uint32_t n_rep, const float *rep_params, const uint64_t *rep_seeds,
+                       std::vector<Rep> &reps)
+{
+    reps.assign(n_rep, Rep{});
+    for (uint32_t b = 0; b < n_rep; ++b) {
+        Rep &R = reps[b];
+        float Rv = p->R, Bn[DEABM_MAX_NETS], Br = p->B_rand, Sa[DEABM_N_AGE];
+        uint32_t delay = p->dose2_delay;
+        for (int k = 0; k < DEABM_MAX_NETS; ++k) Bn[k] = p->B_net[k];
+        for (int q = 0; q < DEABM_N_AGE; ++q) Sa[q] = p->S_age[q];
+        if (rep_params) {
+            const float *rp = rep_params + (size_t)b * DEABM_N_REP_PARAMS;
+            Rv = rp[0]; Bn[0] = rp[1]; Bn[1] = rp[2]; Br = rp[3];
+            for (int q = 0; q < DEABM_N_AGE; ++q) Sa[q] = rp[4 + q];
+            delay = (uint32_t)rp[13];
+        }
+        volatile float rv = Rv, ib = p->inv_Ibar;  // one FP32 product, no contraction
+        R.cR = rv * ib;
+        for (int k = 0; k < DEABM_MAX_NETS; ++k) R.B_net[k] = Bn[k];
+        R.B_rand = Br;
+        for (int q = 0; q < DEABM_N_AGE; ++q) R.S_age[q] = Sa[q];
+        R.dose2_delay = delay;
+        R.seed = rep_seeds ? rep_seeds[b] : p->seed;
+    }
+}
+
 // ---------------------------------------------------------------- creation
 static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_params *p, uint32_t n_rep,
                        const float *rep_params, const uint64_t *rep_seeds, void *stream, deabm_ctx **out)
@@ -297,29 +328,22 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaMemcpyAsync(ctx->S.tinf, ti.data(), nb * 2, cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemcpyAsync(ctx->S.flags, fl.data(), nb, cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemcpyAsync(ctx->S.qt, qt.data(), nb, cudaMemcpyHostToDevice, s));
+            // keep the initial state for deabm_reset
+            if ((r = dalloc(ctx, &ctx->S0.stage, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S0.timer, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S0.tinf, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S0.flags, nb))) return r;
+            if ((r = dalloc(ctx, &ctx->S0.qt, nb))) return r;
+            CU(ctx, cudaMemcpyAsync(ctx->S0.stage, ctx->S.stage, nb, cudaMemcpyDeviceToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.timer, ctx->S.timer, nb * 2, cudaMemcpyDeviceToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.tinf, ctx->S.tinf, nb * 2, cudaMemcpyDeviceToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.flags, ctx->S.flags, nb, cudaMemcpyDeviceToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.qt, ctx->S.qt, nb, cudaMemcpyDeviceToDevice, s));
+            ctx->base = *p;
 
             // per-replicate parameters
-            std::vector<Rep> reps(n_rep);
-            for (uint32_t b = 0; b < n_rep; ++b) {
-                Rep &R = reps[b];
-                float Rv = p->R, Bn[DEABM_MAX_NETS], Br = p->B_rand, Sa[DEABM_N_AGE];
-                uint32_t delay = p->dose2_delay;
-                for (int k = 0; k < DEABM_MAX_NETS; ++k) Bn[k] = p->B_net[k];
-                for (int q = 0; q < DEABM_N_AGE; ++q) Sa[q] = p->S_age[q];
-                if (rep_params) {
-                    const float *rp = rep_params + (size_t)b * DEABM_N_REP_PARAMS;
-                    Rv = rp[0]; Bn[0] = rp[1]; Bn[1] = rp[2]; Br = rp[3];
-                    for (int q = 0; q < DEABM_N_AGE; ++q) Sa[q] = rp[4 + q];
-                    delay = (uint32_t)rp[13];
-                }
-                volatile float rv = Rv, ib = p->inv_Ibar;  // one FP32 product, no contraction
-                R.cR = rv * ib;
-                for (int k = 0; k < DEABM_MAX_NETS; ++k) R.B_net[k] = Bn[k];
-                R.B_rand = Br;
-                for (int q = 0; q < DEABM_N_AGE; ++q) R.S_age[q] = Sa[q];
-                R.dose2_delay = delay;
-                R.seed = rep_seeds ? rep_seeds[b] : p->seed;
-            }
+            std::vector<Rep> reps;
+            build_reps(p, n_rep, rep_params, rep_seeds, reps);
             CU(ctx, cudaMemcpyAsync(ctx->rep, reps.data(), sizeof(Rep) * n_rep, cudaMemcpyHostToDevice, s));
 
             // host-side integer tables (thresholds are exact: p * 2^32 then floor)
@@ -411,6 +435,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 CU(ctx, cudaMemcpyAsync(d_ids, ids.data(), sizeof(uint32_t) * a->n_seed, cudaMemcpyHostToDevice, s));
                 CU(ctx, launch_seed(K, d_ids, a->n_seed, ctx->S, s));
                 CU(ctx, cudaStreamSynchronize(s));
+                ctx->seed_ids = d_ids;
+                ctx->n_seed = a->n_seed;
             }
             CU(ctx, launch_emit(K, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
             CU(ctx, cudaStreamSynchronize(s));
@@ -548,6 +574,40 @@ extern "C" int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *pois
         for (int c = 0; c < DEABM_N_CLASS; ++c)
             std::memcpy(inf_table + (size_t)c * ctx->kp.inf_len, T.infT[c], sizeof(float) * ctx->kp.inf_len);
     if (poisson_thr) std::memcpy(poisson_thr, T.pois, sizeof T.pois);
+    return DEABM_OK;
+}
+
+extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_seeds)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if ((rep_params == nullptr) != (rep_seeds == nullptr))
+        return fail(ctx, DEABM_EINVAL, "rep_params and rep_seeds go together");
+    cudaStream_t s = ctx->stream;
+    const size_t nb = (size_t)ctx->n * ctx->n_rep;
+    if (rep_params) {
+        for (uint32_t b = 0; b < ctx->n_rep; ++b) {
+            const float d = rep_params[b * DEABM_N_REP_PARAMS + 13];
+            if (!(d >= 1.0f && d <= 30000.0f) || d != std::floor(d))
+                return fail(ctx, DEABM_EINVAL, "replicate %u: dose2_delay must be a whole number of days >= 1", b);
+        }
+        std::vector<Rep> reps;
+        build_reps(&ctx->base, ctx->n_rep, rep_params, rep_seeds, reps);
+        CU(ctx, cudaMemcpyAsync(ctx->rep, reps.data(), sizeof(Rep) * ctx->n_rep, cudaMemcpyHostToDevice, s));
+        CU(ctx, cudaStreamSynchronize(s));  // the staging vector goes out of scope
+    }
+    CU(ctx, cudaMemcpyAsync(ctx->S.stage, ctx->S0.stage, nb, cudaMemcpyDeviceToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->S.timer, ctx->S0.timer, nb * 2, cudaMemcpyDeviceToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->S.tinf, ctx->S0.tinf, nb * 2, cudaMemcpyDeviceToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->S.flags, ctx->S0.flags, nb, cudaMemcpyDeviceToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->S.qt, ctx->S0.qt, nb, cudaMemcpyDeviceToDevice, s));
+    if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
+    ctx->cur = 0;
+    CU(ctx, launch_emit(ctx->kp, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
+    const size_t days = ctx->max_steps;
+    CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * ctx->n_rep, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+    ctx->day = 0;
     return DEABM_OK;
 }
 

@@ -1,0 +1,589 @@
+// mlp.cu -- surrogate MLP (simulation parameters -> daily log incidence) trained
+// and evaluated on the GPU: BF16 operands, FP32 accumulation on the tensor cores.
+//
+// Layers: n_in -> H -> ... -> H (depth hidden layers, erf-GELU) -> n_out (linear).
+// Forward of layer l:  z_l = a_{l-1} W_l + b_l  (FP32 accumulate of BF16 products),
+// a_l = bf16(gelu(z_l)) for hidden layers, the output z_L in FP32.
+// Backward (MSE loss (1/(B n_out)) sum (y_hat - y)^2):
+//   dz_L = 2 (y_hat - y) / (B n_out);  dW_l = a_{l-1}^T bf16(dz_l);  db_l = sum_rows dz_l;
+//   dz_{l-1} = (bf16(dz_l) W_l^T) * gelu'(z_{l-1}).
+// Adam keeps FP32 master weights and refreshes the BF16 copies after each step.
+// The input layer's K is padded to a multiple of 16 with zero columns / rows.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "deabm.h"
+
+namespace mlpk {
+
+// ------------------------------------------------------------------ tensor-core GEMM
+// C[M x N] = A[M x K] * B[K x N] with A(i, r) = A[i*sAi + r*sAr], B(r, j) = B[r*sBr + j*sBj]
+// (BF16), FP32 accumulate, fused epilogue.  Tile 128 x 64 x 32, 4 warps of 64 x 32,
+// mma.sync m16n8k16 with ldmatrix fragments.
+constexpr int BM = 128, BN = 64, BK = 32, PAD = 8;
+
+enum Epi : int {
+    EPI_HIDDEN = 0,   // z = acc + bias -> zf (FP32), a = bf16(gelu(z))
+    EPI_OUTPUT = 1,   // y = acc + bias (FP32)
+    EPI_DGRAD = 2,    // dz = acc * gelu'(zf) -> out (FP32) and bf16 copy
+    EPI_WGRAD = 3,    // plain FP32 store
+};
+
+struct GemmArgs {
+    const __nv_bfloat16 *A, *B;
+    long sAi, sAr, sBr, sBj;
+    int M, N, K;
+    const float *bias;    // EPI_HIDDEN / EPI_OUTPUT
+    const float *zin;     // EPI_DGRAD: pre-activation of the layer below [M x N]
+    float *outf;          // FP32 output [M x ldo]
+    __nv_bfloat16 *outb;  // BF16 output [M x ldo] (hidden, dgrad)
+    int ldo;
+    int epi;
+};
+
+__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_erf_grad(float z)
+{
+    // d/dz [z Phi(z)] = Phi(z) + z phi(z)
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 sA[BM][BK + PAD];  // [i][r]
+    __shared__ __align__(16) __nv_bfloat16 sB[BN][BK + PAD];  // [j][r]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, each 64 x 32
+    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    float acc[4][4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    for (int r0 = 0; r0 < g.K; r0 += BK) {
+        // A tile: walk the contiguous dimension with consecutive threads
+        if (g.sAr == 1) {
+            for (int q = tid; q < BM * BK; q += 128) {
+                const int i = q / BK, r = q % BK, gi = i0 + i, gr = r0 + r;
+                sA[i][r] = (gi < g.M && gr < g.K) ? g.A[(long)gi * g.sAi + gr] : zero;
+            }
+        } else {
+            for (int q = tid; q < BM * BK; q += 128) {
+                const int r = q / BM, i = q % BM, gi = i0 + i, gr = r0 + r;
+                sA[i][r] = (gi < g.M && gr < g.K) ? g.A[(long)gi * g.sAi + (long)gr * g.sAr] : zero;
+            }
+        }
+        if (g.sBj == 1) {
+            for (int q = tid; q < BN * BK; q += 128) {
+                const int r = q / BN, j = q % BN, gj = j0 + j, gr = r0 + r;
+                sB[j][r] = (gj < g.N && gr < g.K) ? g.B[(long)gr * g.sBr + gj] : zero;
+            }
+        } else {
+            for (int q = tid; q < BN * BK; q += 128) {
+                const int j = q / BK, r = q % BK, gj = j0 + j, gr = r0 + r;
+                sB[j][r] = (gj < g.N && gr < g.K) ? g.B[(long)gr * g.sBr + (long)gj * g.sBj] : zero;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[4][4];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                const int row = wm * 64 + mt * 16 + (lane & 15), col = kk + (lane >> 4) * 8;
+                ldmatrix_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], &sA[row][col]);
+            }
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {  // pairs of 8-wide n tiles
+                uint32_t b0, b1, b2, b3;
+                // matrices: (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+                const int nrow = wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3);
+                const int kcol = kk + ((lane >> 3) & 1) * 8;
+                ldmatrix_x4(b0, b1, b2, b3, &sB[nrow][kcol]);
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) {
+                    mma_bf16(acc[mt][np * 2 + 0], af[mt], b0, b1);
+                    mma_bf16(acc[mt][np * 2 + 1], af[mt], b2, b3);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue: thread owns rows (g, g+8) and columns (2t, 2t+1) of each 16 x 8 tile
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int i = i0 + wm * 64 + mt * 16 + gid + h * 8;
+                    const int j = j0 + wn * 32 + nt * 8 + tig * 2 + e;
+                    if (i >= g.M || j >= g.N) continue;
+                    const float v = acc[mt][nt][h * 2 + e];
+                    const long o = (long)i * g.ldo + j;
+                    if (g.epi == EPI_HIDDEN) {
+                        const float z = v + g.bias[j];
+                        if (g.outf) g.outf[o] = z;
+                        g.outb[o] = __float2bfloat16(gelu_erf(z));
+                    } else if (g.epi == EPI_OUTPUT) {
+                        g.outf[o] = v + g.bias[j];
+                    } else if (g.epi == EPI_DGRAD) {
+                        const float d = v * gelu_erf_grad(g.zin[o]);
+                        g.outf[o] = d;
+                        g.outb[o] = __float2bfloat16(d);
+                    } else {
+                        g.outf[o] = v;
+                    }
+                }
+}
+
+// ------------------------------------------------------------------ small kernels
+__global__ void to_bf16_pad_kernel(const float *x, int rows, int cols, int ld, __nv_bfloat16 *out)
+{
+    const long n = (long)rows * ld;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / ld), c = (int)(q % ld);
+        out[q] = __float2bfloat16(c < cols ? x[(long)r * cols + c] : 0.0f);
+    }
+}
+
+// dz_L = 2 (y_hat - y) / (B n_out), its bf16 copy, and the loss (block partials)
+__global__ void mse_grad_kernel(const float *yhat, const float *y, long n, float scale, float *dz, __nv_bfloat16 *dzb,
+                                double *loss_part)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const float d = yhat[q] - y[q];
+        acc += (double)d * d;
+        const float gq = 2.0f * d * scale;
+        dz[q] = gq;
+        dzb[q] = __float2bfloat16(gq);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_reduce_kernel(const double *part, int nparts, float scale, float *loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < nparts; ++q) s += part[q];
+        *loss = (float)(s * scale);
+    }
+}
+
+// db[j] = sum_i dz[i][j] (fixed order per column)
+__global__ void colsum_kernel(const float *dz, int rows, int cols, float *db)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    double s = 0.0;
+    for (int i = 0; i < rows; ++i) s += dz[(long)i * cols + j];
+    db[j] = (float)s;
+}
+
+__global__ void adam_update_kernel(float *w, float *m, float *v, const float *g, long n, float lr, float b1, float b2,
+                                   float eps, float c1, float c2, __nv_bfloat16 *wb, int rows, int cols, int ldb)
+{
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const float gq = g[q];
+        const float mq = b1 * m[q] + (1.0f - b1) * gq, vq = b2 * v[q] + (1.0f - b2) * gq * gq;
+        m[q] = mq;
+        v[q] = vq;
+        const float wq = w[q] - lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+        w[q] = wq;
+        if (wb) {
+            const int r = (int)(q / cols), c = (int)(q % cols);
+            if (r < rows) wb[(long)r * ldb + c] = __float2bfloat16(wq);
+        }
+    }
+}
+
+__global__ void weights_to_bf16_kernel(const float *w, int rows, int cols, int rows_pad, __nv_bfloat16 *wb)
+{
+    const long n = (long)rows_pad * cols;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / cols);
+        wb[q] = __float2bfloat16(r < rows ? w[q] : 0.0f);
+    }
+}
+
+}  // namespace mlpk
+
+using namespace mlpk;
+
+// ------------------------------------------------------------------------------------ host side
+struct deabm_mlp {
+    cudaStream_t stream = nullptr;
+    int n_in = 0, k_in = 0, H = 0, depth = 0, n_out = 0, L = 0, max_batch = 0;
+    std::vector<void *> allocs;
+    std::vector<int> fin, fout, kpad;  // per layer: fan-in, fan-out, padded fan-in
+    std::vector<float *> W, b, gW, gb, mW, vW, mb, vb;   // FP32 master, grads, Adam moments
+    std::vector<__nv_bfloat16 *> Wb;                      // BF16 copies [kpad x fout]
+    std::vector<__nv_bfloat16 *> act;                     // a_l, l = 0..L-1 (a_0 = input) [B x ld]
+    std::vector<float *> z;                               // pre-activations of hidden layers [B x H]
+    float *yhat = nullptr, *dz = nullptr, *dz2 = nullptr, *loss = nullptr;
+    __nv_bfloat16 *dzb = nullptr, *dzb2 = nullptr;
+    double *loss_part = nullptr;
+    int step = 0;
+};
+
+static thread_local std::string g_mlp_err;
+
+static int mlp_fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_mlp_err = buf;
+    return code;
+}
+
+#define MCU(call)                                                                                                   \
+    do {                                                                                                            \
+        cudaError_t e_ = (call);                                                                                    \
+        if (e_ != cudaSuccess)                                                                                      \
+            return mlp_fail(e_ == cudaErrorMemoryAllocation ? DEABM_ENOMEM : DEABM_ECUDA, "%s: %s (%s:%d)", #call, \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
+    } while (0)
+
+template <class T>
+static int m_alloc(deabm_mlp *m, T **out, size_t count)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (count ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return mlp_fail(DEABM_ENOMEM, "cudaMalloc failed (%zu bytes)", count * sizeof(T));
+    }
+    m->allocs.push_back(p);
+    *out = (T *)p;
+    return DEABM_OK;
+}
+
+static int gemm(cudaStream_t s, const GemmArgs &g)
+{
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    if (grid.y > 65535) return mlp_fail(DEABM_EINVAL, "GEMM with M = %d is too tall", g.M);
+    gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
+    MCU(cudaGetLastError());
+    return DEABM_OK;
+}
+
+extern "C" void deabm_mlp_destroy(deabm_mlp *m)
+{
+    if (!m) return;
+    if (!m->allocs.empty()) (void)cudaStreamSynchronize(m->stream);
+    for (void *p : m->allocs) (void)cudaFree(p);
+    delete m;
+}
+
+extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, uint32_t n_out, uint32_t max_batch,
+                                void *stream, deabm_mlp **out)
+{
+    if (!out) return mlp_fail(DEABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_in == 0 || n_in > 4096 || hidden == 0 || hidden > 4096 || depth == 0 || depth > 16 || n_out == 0 ||
+        n_out > 4096 || max_batch == 0 || max_batch > (1u << 22))
+        return mlp_fail(DEABM_EINVAL, "sizes out of range");
+    if (hidden % 8 || n_out % 2) return mlp_fail(DEABM_EINVAL, "hidden must be a multiple of 8 and n_out even");
+    deabm_mlp *m = new (std::nothrow) deabm_mlp();
+    if (!m) return mlp_fail(DEABM_ENOMEM, "host allocation failed");
+    int rc = [&]() -> int {
+        m->stream = (cudaStream_t)stream;
+        m->n_in = (int)n_in;
+        m->k_in = (int)((n_in + 15) / 16 * 16);
+        m->H = (int)hidden;
+        m->depth = (int)depth;
+        m->n_out = (int)n_out;
+        m->L = (int)depth + 1;
+        m->max_batch = (int)max_batch;
+        int r;
+        for (int l = 0; l < m->L; ++l) {
+            const int fi = l == 0 ? m->n_in : m->H, fo = l == m->L - 1 ? m->n_out : m->H;
+            const int kp = l == 0 ? m->k_in : m->H;
+            m->fin.push_back(fi);
+            m->fout.push_back(fo);
+            m->kpad.push_back(kp);
+            float *W, *b, *gW, *gb, *mW, *vW, *mb, *vb;
+            __nv_bfloat16 *Wb;
+            if ((r = m_alloc(m, &W, (size_t)fi * fo))) return r;
+            if ((r = m_alloc(m, &b, fo))) return r;
+            if ((r = m_alloc(m, &gW, (size_t)fi * fo))) return r;
+            if ((r = m_alloc(m, &gb, fo))) return r;
+            if ((r = m_alloc(m, &mW, (size_t)fi * fo))) return r;
+            if ((r = m_alloc(m, &vW, (size_t)fi * fo))) return r;
+            if ((r = m_alloc(m, &mb, fo))) return r;
+            if ((r = m_alloc(m, &vb, fo))) return r;
+            if ((r = m_alloc(m, &Wb, (size_t)kp * fo))) return r;
+            MCU(cudaMemsetAsync(W, 0, 4ull * fi * fo, m->stream));
+            MCU(cudaMemsetAsync(b, 0, 4ull * fo, m->stream));
+            MCU(cudaMemsetAsync(Wb, 0, 2ull * kp * fo, m->stream));
+            m->W.push_back(W); m->b.push_back(b); m->gW.push_back(gW); m->gb.push_back(gb);
+            m->mW.push_back(mW); m->vW.push_back(vW); m->mb.push_back(mb); m->vb.push_back(vb); m->Wb.push_back(Wb);
+        }
+        const size_t B = max_batch;
+        for (int l = 0; l < m->L; ++l) {  // a_0 .. a_{L-1}: inputs of each layer
+            __nv_bfloat16 *a;
+            if ((r = m_alloc(m, &a, B * m->kpad[l]))) return r;
+            m->act.push_back(a);
+        }
+        for (int l = 0; l < m->L - 1; ++l) {
+            float *zz;
+            if ((r = m_alloc(m, &zz, B * m->H))) return r;
+            m->z.push_back(zz);
+        }
+        const int wmax = m->H > m->n_out ? m->H : m->n_out;
+        if ((r = m_alloc(m, &m->yhat, B * m->n_out))) return r;
+        if ((r = m_alloc(m, &m->dz, B * wmax))) return r;
+        if ((r = m_alloc(m, &m->dz2, B * wmax))) return r;
+        if ((r = m_alloc(m, &m->dzb, B * wmax))) return r;
+        if ((r = m_alloc(m, &m->dzb2, B * wmax))) return r;
+        if ((r = m_alloc(m, &m->loss, 1))) return r;
+        if ((r = m_alloc(m, &m->loss_part, 1024))) return r;
+        MCU(cudaStreamSynchronize(m->stream));
+        return DEABM_OK;
+    }();
+    if (rc != DEABM_OK) {
+        deabm_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return DEABM_OK;
+}
+
+size_t mlp_param_count(const deabm_mlp *m)
+{
+    size_t n = 0;
+    for (int l = 0; l < m->L; ++l) n += (size_t)m->fin[l] * m->fout[l] + m->fout[l];
+    return n;
+}
+
+extern "C" int deabm_mlp_param_count(const deabm_mlp *m, uint64_t *count)
+{
+    if (!m || !count) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    *count = mlp_param_count(m);
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_set_params(deabm_mlp *m, const float *params)
+{
+    if (!m || !params) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    size_t off = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const size_t nw = (size_t)m->fin[l] * m->fout[l];
+        MCU(cudaMemcpyAsync(m->W[l], params + off, 4 * nw, cudaMemcpyHostToDevice, m->stream));
+        off += nw;
+        MCU(cudaMemcpyAsync(m->b[l], params + off, 4ull * m->fout[l], cudaMemcpyHostToDevice, m->stream));
+        off += m->fout[l];
+        weights_to_bf16_kernel<<<256, 256, 0, m->stream>>>(m->W[l], m->fin[l], m->fout[l], m->kpad[l], m->Wb[l]);
+        MCU(cudaMemsetAsync(m->mW[l], 0, 4 * nw, m->stream));
+        MCU(cudaMemsetAsync(m->vW[l], 0, 4 * nw, m->stream));
+        MCU(cudaMemsetAsync(m->mb[l], 0, 4ull * m->fout[l], m->stream));
+        MCU(cudaMemsetAsync(m->vb[l], 0, 4ull * m->fout[l], m->stream));
+    }
+    m->step = 0;
+    MCU(cudaGetLastError());
+    MCU(cudaStreamSynchronize(m->stream));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_get_params(deabm_mlp *m, float *params, float *grads)
+{
+    if (!m || (!params && !grads)) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    size_t off = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const size_t nw = (size_t)m->fin[l] * m->fout[l];
+        if (params) MCU(cudaMemcpyAsync(params + off, m->W[l], 4 * nw, cudaMemcpyDeviceToHost, m->stream));
+        if (grads) MCU(cudaMemcpyAsync(grads + off, m->gW[l], 4 * nw, cudaMemcpyDeviceToHost, m->stream));
+        off += nw;
+        if (params) MCU(cudaMemcpyAsync(params + off, m->b[l], 4ull * m->fout[l], cudaMemcpyDeviceToHost, m->stream));
+        if (grads) MCU(cudaMemcpyAsync(grads + off, m->gb[l], 4ull * m->fout[l], cudaMemcpyDeviceToHost, m->stream));
+        off += m->fout[l];
+    }
+    MCU(cudaStreamSynchronize(m->stream));
+    return DEABM_OK;
+}
+
+// forward over `batch` rows of x (device FP32 [batch x n_in]) into yhat (device FP32);
+// `keep` stores the pre-activations for a backward pass
+static int mlp_forward_dev(deabm_mlp *m, const float *x, int batch, float *yhat, bool keep)
+{
+    cudaStream_t s = m->stream;
+    to_bf16_pad_kernel<<<512, 256, 0, s>>>(x, batch, m->n_in, m->k_in, m->act[0]);
+    MCU(cudaGetLastError());
+    int r;
+    for (int l = 0; l < m->L; ++l) {
+        GemmArgs g{};
+        g.A = m->act[l];
+        g.sAi = m->kpad[l];
+        g.sAr = 1;
+        g.B = m->Wb[l];
+        g.sBr = m->fout[l];
+        g.sBj = 1;
+        g.M = batch;
+        g.N = m->fout[l];
+        g.K = m->kpad[l];
+        g.bias = m->b[l];
+        if (l < m->L - 1) {
+            g.epi = EPI_HIDDEN;
+            g.outf = keep ? m->z[l] : nullptr;
+            g.outb = m->act[l + 1];
+            g.ldo = m->H;
+        } else {
+            g.epi = EPI_OUTPUT;
+            g.outf = yhat;
+            g.ldo = m->n_out;
+        }
+        if ((r = gemm(s, g))) return r;
+    }
+    return DEABM_OK;
+}
+
+static int mlp_backward_dev(deabm_mlp *m, const float *y, int batch, float *loss_host)
+{
+    cudaStream_t s = m->stream;
+    const long n = (long)batch * m->n_out;
+    const int nparts = 256;
+    mse_grad_kernel<<<nparts, 256, 0, s>>>(m->yhat, y, n, 1.0f / (float)n, m->dz, m->dzb, m->loss_part);
+    loss_reduce_kernel<<<1, 32, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
+    MCU(cudaGetLastError());
+    float *dz = m->dz, *dzo = m->dz2;
+    __nv_bfloat16 *dzb = m->dzb, *dzbo = m->dzb2;
+    int r;
+    for (int l = m->L - 1; l >= 0; --l) {
+        const int fo = m->fout[l], fi = m->fin[l];
+        // dW_l = a_{l-1}^T dz_l : [fi x fo], reduction over the batch
+        GemmArgs gw{};
+        gw.A = m->act[l];
+        gw.sAi = 1;
+        gw.sAr = m->kpad[l];
+        gw.B = dzb;
+        gw.sBr = fo;
+        gw.sBj = 1;
+        gw.M = fi;
+        gw.N = fo;
+        gw.K = batch;
+        gw.outf = m->gW[l];
+        gw.ldo = fo;
+        gw.epi = EPI_WGRAD;
+        if ((r = gemm(s, gw))) return r;
+        colsum_kernel<<<(fo + 127) / 128, 128, 0, s>>>(dz, batch, fo, m->gb[l]);
+        MCU(cudaGetLastError());
+        if (l > 0) {
+            // dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})
+            GemmArgs gd{};
+            gd.A = dzb;
+            gd.sAi = fo;
+            gd.sAr = 1;
+            gd.B = m->Wb[l];
+            gd.sBr = 1;
+            gd.sBj = fo;
+            gd.M = batch;
+            gd.N = m->H;
+            gd.K = fo;
+            gd.zin = m->z[l - 1];
+            gd.outf = dzo;
+            gd.outb = dzbo;
+            gd.ldo = m->H;
+            gd.epi = EPI_DGRAD;
+            if ((r = gemm(s, gd))) return r;
+            float *tf = dz;
+            dz = dzo;
+            dzo = tf;
+            __nv_bfloat16 *tb = dzb;
+            dzb = dzbo;
+            dzbo = tb;
+        }
+    }
+    if (loss_host) {
+        MCU(cudaMemcpyAsync(loss_host, m->loss, 4, cudaMemcpyDeviceToHost, s));
+        MCU(cudaStreamSynchronize(s));
+    }
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_forward(deabm_mlp *m, const float *x, uint32_t batch, float *y)
+{
+    if (!m || !x || !y) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    if (batch == 0) return DEABM_OK;
+    if ((int)batch > m->max_batch) return mlp_fail(DEABM_EINVAL, "batch %u > max_batch %d", batch, m->max_batch);
+    return mlp_forward_dev(m, x, (int)batch, y, false);
+}
+
+extern "C" int deabm_mlp_grad(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float *loss)
+{
+    if (!m || !x || !y) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    if (batch == 0 || (int)batch > m->max_batch) return mlp_fail(DEABM_EINVAL, "batch must be in 1..max_batch");
+    int r;
+    if ((r = mlp_forward_dev(m, x, (int)batch, m->yhat, true))) return r;
+    return mlp_backward_dev(m, y, (int)batch, loss);
+}
+
+extern "C" int deabm_mlp_train_step(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float lr, float *loss)
+{
+    int r;
+    if ((r = deabm_mlp_grad(m, x, y, batch, nullptr))) return r;
+    m->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
+    for (int l = 0; l < m->L; ++l) {
+        const long nw = (long)m->fin[l] * m->fout[l];
+        adam_update_kernel<<<256, 256, 0, m->stream>>>(m->W[l], m->mW[l], m->vW[l], m->gW[l], nw, lr, b1, b2, 1e-8f, c1,
+                                                       c2, m->Wb[l], m->fin[l], m->fout[l], m->fout[l]);
+        adam_update_kernel<<<4, 256, 0, m->stream>>>(m->b[l], m->mb[l], m->vb[l], m->gb[l], m->fout[l], lr, b1, b2,
+                                                     1e-8f, c1, c2, nullptr, 0, 0, 0);
+    }
+    MCU(cudaGetLastError());
+    if (loss) {
+        MCU(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
+        MCU(cudaStreamSynchronize(m->stream));
+    }
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_sync(deabm_mlp *m)
+{
+    if (!m) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    MCU(cudaStreamSynchronize(m->stream));
+    return DEABM_OK;
+}
+
+extern "C" const char *deabm_mlp_last_error(void) { return g_mlp_err.c_str(); }

@@ -21,7 +21,9 @@ STAGES = ("S", "ASYM", "PRE_MILD", "PRE_SEV", "MILD", "SEV", "HOSP", "ICU", "REC
 EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "deabm_get_state",
            "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_last_error",
            "deabm_destroy", "deabm_relaxed_create", "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate",
-           "deabm_relaxed_last_error", "deabm_relaxed_destroy")
+           "deabm_relaxed_last_error", "deabm_relaxed_destroy", "deabm_reset", "deabm_mlp_create",
+           "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
+           "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy")
 N_THETA = 13
 
 
@@ -94,9 +96,24 @@ def lib():
         L.deabm_relaxed_last_error.restype = C.c_char_p
         L.deabm_relaxed_destroy.argtypes = [vp]
         L.deabm_relaxed_destroy.restype = None
+        L.deabm_reset.argtypes = [vp, vp, vp]
+        L.deabm_mlp_create.argtypes = [u32, u32, u32, u32, u32, vp, C.POINTER(vp)]
+        L.deabm_mlp_param_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.deabm_mlp_set_params.argtypes = [vp, vp]
+        L.deabm_mlp_get_params.argtypes = [vp, vp, vp]
+        L.deabm_mlp_forward.argtypes = [vp, vp, u32, vp]
+        L.deabm_mlp_grad.argtypes = [vp, vp, vp, u32, vp]
+        L.deabm_mlp_train_step.argtypes = [vp, vp, vp, u32, C.c_float, vp]
+        L.deabm_mlp_sync.argtypes = [vp]
+        L.deabm_mlp_last_error.argtypes = []
+        L.deabm_mlp_last_error.restype = C.c_char_p
+        L.deabm_mlp_destroy.argtypes = [vp]
+        L.deabm_mlp_destroy.restype = None
         for name in ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "deabm_get_state",
                      "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_relaxed_create",
-                     "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate"):
+                     "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate", "deabm_reset", "deabm_mlp_create",
+                     "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
+                     "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -328,6 +345,15 @@ class Simulation:
     def sync(self):
         _check(lib().deabm_sync(self.ctx), self.ctx)
 
+    def reset(self, rep_params=None, rep_seeds=None):
+        """Back to day 0 (initial state and cases re-applied), optionally with new
+        per-replicate parameters [n_rep, 14] and seeds."""
+        rp = rs = None
+        if rep_params is not None:
+            rp = np.ascontiguousarray(rep_params, dtype=np.float32).reshape(self.n_rep, N_REP_PARAMS)
+            rs = np.ascontiguousarray(rep_seeds, dtype=np.uint64).reshape(self.n_rep)
+        _check(lib().deabm_reset(self.ctx, _p(rp), _p(rs)), self.ctx)
+
     # -- readback
     @property
     def day(self) -> int:
@@ -381,3 +407,78 @@ class Simulation:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _mlp_check(rc):
+    if rc != OK:
+        raise DeabmError(rc, lib().deabm_mlp_last_error().decode(errors="replace"))
+
+
+class MLP:
+    """The surrogate MLP in libdeabm: BF16 tensor-core forward / backward, FP32
+    master weights, Adam.  Data are torch CUDA float32 tensors (device pointers)."""
+
+    def __init__(self, n_in=14, hidden=256, depth=3, n_out=180, max_batch=65536, stream=None):
+        L = lib()
+        self.sizes = [n_in] + [hidden] * depth + [n_out]
+        self.n_in, self.n_out, self.max_batch = n_in, n_out, max_batch
+        self._stream = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
+        ctx = C.c_void_p()
+        _mlp_check(L.deabm_mlp_create(n_in, hidden, depth, n_out, max_batch, self._stream, C.byref(ctx)))
+        self.ctx = ctx
+        cnt = C.c_uint64()
+        _mlp_check(L.deabm_mlp_param_count(ctx, C.byref(cnt)))
+        self.n_params = cnt.value
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.n_params
+        _mlp_check(lib().deabm_mlp_set_params(self.ctx, _p(p)))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        _mlp_check(lib().deabm_mlp_get_params(self.ctx, _p(p), None))
+        return p
+
+    def get_grads(self):
+        g = np.zeros(self.n_params, np.float32)
+        _mlp_check(lib().deabm_mlp_get_params(self.ctx, None, _p(g)))
+        return g
+
+    @staticmethod
+    def _dev(t, cols):
+        assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous() and t.shape[-1] == cols
+        return C.c_void_p(t.data_ptr())
+
+    def forward(self, x, out=None):
+        import torch
+        B = x.shape[0]
+        y = out if out is not None else torch.empty((B, self.n_out), dtype=torch.float32, device=x.device)
+        _mlp_check(lib().deabm_mlp_forward(self.ctx, self._dev(x, self.n_in), B, self._dev(y, self.n_out)))
+        return y
+
+    def grad(self, x, y):
+        loss = np.zeros(1, np.float32)
+        _mlp_check(lib().deabm_mlp_grad(self.ctx, self._dev(x, self.n_in), self._dev(y, self.n_out), x.shape[0],
+                                        _p(loss)))
+        return float(loss[0])
+
+    def train_step(self, x, y, lr, sync=False):
+        loss = np.zeros(1, np.float32) if sync else None
+        _mlp_check(lib().deabm_mlp_train_step(self.ctx, self._dev(x, self.n_in), self._dev(y, self.n_out), x.shape[0],
+                                              lr, _p(loss)))
+        return float(loss[0]) if sync else None
+
+    def sync(self):
+        _mlp_check(lib().deabm_mlp_sync(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().deabm_mlp_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -194,3 +194,26 @@ def relaxed_workload():
     start = np.array([2.5, 1.0, 1.0, 1.0] + [1.0] * N_AGE, np.float32)
     return dict(name="relaxed N=1e5 T=90 tau=0.5", n=100_000, T=90, tau=0.5, n_seed=10, params=p,
                 hidden=hidden, start=start, steps=200, lr=0.02)
+
+
+# parameter box of the surrogate's inputs: R, three network weights, nine age
+# susceptibilities, second-dose delay (days)
+SURROGATE_LO = np.array([2.0, 0.5, 0.5, 0.5] + [0.5] * N_AGE + [21.0], np.float32)
+SURROGATE_HI = np.array([6.0, 2.0, 2.0, 2.0] + [1.5] * N_AGE + [84.0], np.float32)
+
+
+def surrogate_params(n: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """[n, 14] parameter rows drawn uniformly in the surrogate's box (delay whole
+    days) and a Philox seed per row."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x5A77]))
+    rp = rng.uniform(SURROGATE_LO, SURROGATE_HI, (n, N_REP_PARAMS)).astype(np.float32)
+    rp[:, 13] = rng.integers(21, 85, n)
+    seeds = rng.integers(0, 2**63 - 1, n, dtype=np.int64).astype(np.uint64)
+    return rp, seeds
+
+
+def surrogate_workload():
+    """Surrogate: MLP 14 -> 3 x 256 (GELU) -> 180 trained on 50,000 batched runs of
+    the N = 100,000 ensemble workload (80/20 split), inference batch 65,536."""
+    return dict(name="surrogate MLP 14-256x3-180", n_runs=50_000, n=100_000, T=180, B=256, hidden=256, depth=3,
+                batch=65_536, params=batched()["params"])
