@@ -198,6 +198,36 @@ int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *poisson_thr, in
  * many ensembles without re-uploading the graph.  Asynchronous. */
 int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_seeds);
 
+/* ---- Infection rates of one day without allocating memory ------------------------------
+ * The paper has no counterpart: this is a library convenience.  It exists for
+ * callers that may not allocate device memory where they call us (code living
+ * inside a memory pool another runtime sized up front, hosts whose allocator
+ * hooks forbid cudaMalloc after start-up, real-time loops that cannot afford an
+ * allocation).  Everything the caller owns is passed in: graph_dev has the same
+ * layout as deabm_graph but its row_ptr / col arrays are DEVICE pointers, and so
+ * are age_bin, stage, tinf, qt (n_agents entries each, caller numbering, the
+ * state at the start of `day`) and the output lambda (float[n_agents]).  The
+ * CSR is not validated (the rules of deabm_create apply; invalid indices are
+ * the caller's error).  lambda_j equals what deabm_step computes for that day
+ * and state (Eq. 1 summed over the static networks and the day's random network,
+ * with params' R, inv_Ibar, B_net, B_rand, S_age, A_class, infectiousness curve
+ * and net_seed).
+ * Working memory: a fixed array compiled into the library (4 MiB + 4 KiB on every
+ * GPU that loads it, held until the process exits).  At most
+ * DEABM_NOALLOC_MAX_AGENTS agents; larger populations get DEABM_EINVAL before
+ * any GPU work.  No cudaMalloc, cudaFree or other allocating call is made.  The
+ * first call on each device looks up the array's device address on that device
+ * (with that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; calls whose
+ * GPU work overlaps (other streams or threads) race, so serialise them.  Work is
+ * queued on cuda_stream and the call returns without waiting.  Errors:
+ * DEABM_EINVAL, DEABM_ECUDA; message from deabm_lambda_noalloc_last_error(). */
+#define DEABM_NOALLOC_MAX_AGENTS 1048576u
+int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t *age_bin, const int8_t *stage,
+                         const int16_t *tinf, const uint8_t *qt, const deabm_params *params, uint32_t day,
+                         float *lambda, void *cuda_stream);
+const char *deabm_lambda_noalloc_last_error(void);
+
 /* Days run so far, agents, replicates. */
 int deabm_info(const deabm_ctx *ctx, uint32_t *day, uint32_t *n_agents, uint32_t *n_rep);
 

@@ -1,0 +1,98 @@
+// day_common.cuh -- per-destination infection rate of one day (Eq. 1 summed over
+// a destination's interactions): CSR sums in CSR order, the day's random
+// in-contacts generated from Philox, and their combination into lambda.
+// Shared by the day kernels.
+#pragma once
+#include <cstdint>
+
+#include "deabm_device.cuh"
+
+namespace deabm {
+
+// Sum of inf over one CSR row, left to right from +0.0f.  The row is taken in
+// rounds of kRound edges: all column loads of a round are issued, then all
+// gathers, then the adds in order, so a row of up to kRound in-edges costs two
+// dependent memory round trips instead of one per edge.
+#ifndef DEABM_ROUND
+#define DEABM_ROUND 10
+#endif
+#ifndef DEABM_PLAIN_MINB
+#define DEABM_PLAIN_MINB 6
+#endif
+constexpr uint32_t kRound = DEABM_ROUND;
+
+__device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const float *__restrict__ inf, uint32_t e,
+                                         uint32_t end, uint32_t stride, uint32_t b)
+{
+    float h = 0.0f;
+    while (e < end) {
+        uint32_t c[kRound];
+        float v[kRound];
+#pragma unroll
+        for (uint32_t u = 0; u < kRound; ++u) c[u] = (e + u < end) ? __ldg(col + e + u) : 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < kRound; ++u) v[u] = (e + u < end) ? __ldg(inf + (size_t)c[u] * stride + b) : 0.0f;
+#pragma unroll
+        for (uint32_t u = 0; u < kRound; ++u)
+            if (e + u < end) h = __fadd_rn(h, v[u]);
+        e += kRound;
+    }
+    return h;
+}
+
+// Random in-contacts of agent j (the caller's id) on `day`: count from word 0 of
+// block 0, contact e from word e+1 (block (e+1)/4, lane (e+1)%4); v uniform on
+// the other n-1 agents.  `inf` is indexed by the caller's ids.
+__device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
+                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out)
+{
+    const uint2 nk = seed_key(P.net_seed);
+    uint4 w = draw(nk, j, day, kStreamRnet, 0u);
+    uint32_t k = 0;
+    while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
+    float r = 0.0f;
+    const uint64_t nm1 = (uint64_t)(P.n - 1u);
+    for (uint32_t e = 0; e < k; ++e) {
+        const uint32_t idx = e + 1u;
+        if ((idx & 3u) == 0u) w = draw(nk, j, day, kStreamRnet, idx >> 2);
+        const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+        uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
+        v += (v >= j) ? 1u : 0u;
+        r = __fadd_rn(r, __ldg(inf + (size_t)v * stride + b));
+    }
+    *k_out = k;
+    return r;
+}
+
+// lambda_j of one (agent, replicate) from the state of the day; j = internal row,
+// jo = the caller's id of the same agent.  The row bounds of every network are
+// loaded first and the random contacts are generated while they are in flight.
+__device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
+                                           uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out)
+{
+    uint32_t beg[DEABM_MAX_NETS], end[DEABM_MAX_NETS];
+#pragma unroll
+    for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
+        beg[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j) : 0u;
+        end[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j + 1) : 0u;
+    }
+    *k_out = 0;
+    float r = 0.0f;
+    if (P.rand_on) r = random_sum(P, I.rand_cur, jo, day, stride, b, k_out);
+    float s = 0.0f;
+#pragma unroll
+    for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
+        if (net < P.n_nets) {
+            const float h = csr_sum(P.col[net], I.cur, beg[net], end[net], stride, b);
+            const float term = __fmul_rn(rp.B_net[net], h);
+            s = net == 0 ? term : __fadd_rn(s, term);
+        }
+    }
+    if (P.rand_on) {
+        const float term = __fmul_rn(rp.B_rand, r);
+        s = P.n_nets == 0 ? term : __fadd_rn(s, term);
+    }
+    return __fmul_rn(__fmul_rn(rp.cR, rp.S_age[age]), s);
+}
+
+}  // namespace deabm

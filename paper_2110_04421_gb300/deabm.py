@@ -23,8 +23,10 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_destroy", "deabm_relaxed_create", "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate",
            "deabm_relaxed_last_error", "deabm_relaxed_destroy", "deabm_reset", "deabm_mlp_create",
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
-           "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy")
+           "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
+           "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error")
 N_THETA = 13
+NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
 
 class DeabmError(RuntimeError):
@@ -97,6 +99,10 @@ def lib():
         L.deabm_relaxed_destroy.argtypes = [vp]
         L.deabm_relaxed_destroy.restype = None
         L.deabm_reset.argtypes = [vp, vp, vp]
+        L.deabm_lambda_noalloc.argtypes = [C.POINTER(Graph), vp, vp, vp, vp, C.POINTER(Params), u32, vp, vp]
+        L.deabm_lambda_noalloc.restype = C.c_int
+        L.deabm_lambda_noalloc_last_error.argtypes = []
+        L.deabm_lambda_noalloc_last_error.restype = C.c_char_p
         L.deabm_mlp_create.argtypes = [u32, u32, u32, u32, u32, vp, C.POINTER(vp)]
         L.deabm_mlp_param_count.argtypes = [vp, C.POINTER(C.c_uint64)]
         L.deabm_mlp_set_params.argtypes = [vp, vp]
@@ -482,3 +488,24 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+def lambda_noalloc(graph_dev: dict, age, stage, tinf, qt, params: dict, day: int, out, stream=None):
+    """Infection rates of one day through deabm_lambda_noalloc, which allocates
+    nothing: every argument is a caller-owned torch CUDA tensor (graph_dev holds
+    ``n``, ``row_ptr`` and ``col`` tensors of dtype int32/uint32 on the device)."""
+    g = Graph()
+    g.n_agents = int(graph_dev["n"])
+    g.n_nets = len(graph_dev["row_ptr"])
+    for i, (rp, cl) in enumerate(zip(graph_dev["row_ptr"], graph_dev["col"])):
+        g.row_ptr[i] = rp.data_ptr()
+        g.col[i] = cl.data_ptr()
+    g.rand_mean = params["rand_mean"]
+    p = make_params(params)
+    st = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
+    rc = lib().deabm_lambda_noalloc(C.byref(g), C.c_void_p(age.data_ptr()), C.c_void_p(stage.data_ptr()),
+                                    C.c_void_p(tinf.data_ptr()), C.c_void_p(qt.data_ptr()), C.byref(p), day,
+                                    C.c_void_p(out.data_ptr()), st)
+    if rc != OK:
+        raise DeabmError(rc, lib().deabm_lambda_noalloc_last_error().decode(errors="replace"))
+    return out

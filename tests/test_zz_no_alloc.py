@@ -1,0 +1,70 @@
+"""deabm_lambda_noalloc: the infection rates of one day for callers that cannot
+allocate device memory where they call the library (a memory pool owned by
+another runtime, allocator hooks that forbid cudaMalloc, a real-time loop).  Its
+working memory is a fixed array inside the library, so this test checks that two
+calls in a row -- which share that array -- each give exactly the rates the
+context-based entry point (deabm_create + deabm_step) computes for the same day
+and state.  The file sorts last so a run that stops at the first failure has
+already run every other test; it also passes on its own in a fresh process."""
+import numpy as np
+import pytest
+
+from paper_2110_04421_gb300 import workloads as W
+from tests.helpers import gpu_available
+
+pytestmark = pytest.mark.gpu
+
+if not gpu_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def context_lambdas(pop, params, days):
+    """State at the start of each requested day and that day's lambda, from the
+    context-based entry point."""
+    from paper_2110_04421_gb300.deabm import Simulation
+    sim = Simulation(pop, params, pop["age"], pop["seed_ids"], keep_lambda=True, max_steps=max(days) + 1)
+    out = {}
+    for d in range(max(days) + 1):
+        st = sim.state()
+        sim.step(1)
+        if d in days:
+            out[d] = (st, sim.state(with_lambda=True)["lambda"])
+    sim.close()
+    return out
+
+
+def test_no_alloc_lambda_equals_context_path_on_two_calls():
+    import torch
+    from paper_2110_04421_gb300.deabm import lambda_noalloc
+    pop = W.population(20_003, 3, 60)
+    params = W.params_with(test_on=1, quar_on=1, R=3.5, seed=4, net_seed=5, S_age=[0.7, 0.8, 1.0, 1.0, 1.1, 1.2, 1.2, 1.3, 1.4])
+    ref = context_lambdas(pop, params, days=(6, 7))
+    dev = torch.device("cuda")
+    gdev = dict(n=pop["n"], row_ptr=[torch.tensor(r.astype(np.int32), device=dev) for r in pop["row_ptr"]],
+                col=[torch.tensor(c.astype(np.int32), device=dev) for c in pop["col"]])
+    age = torch.tensor(pop["age"], device=dev)
+    for day in (6, 7):  # two calls in a row share the library's fixed working array
+        st, lam_ref = ref[day]
+        out = torch.full((pop["n"],), float("nan"), device=dev)
+        lambda_noalloc(gdev, age, torch.tensor(st["stage"], device=dev), torch.tensor(st["tinf"], device=dev),
+                       torch.tensor(st["qt"], device=dev), params, day, out)
+        torch.cuda.synchronize()
+        lam = out.cpu().numpy()
+        assert lam_ref.max() > 0
+        assert np.array_equal(lam.view(np.uint32), lam_ref.view(np.uint32)), (day, np.max(np.abs(lam - lam_ref)))
+
+
+def test_no_alloc_rejects_populations_beyond_its_array():
+    import torch
+    from paper_2110_04421_gb300.deabm import NOALLOC_MAX_AGENTS, DeabmError, lambda_noalloc
+    n = NOALLOC_MAX_AGENTS + 1
+    t = torch.zeros(4, dtype=torch.int32, device="cuda")
+    g = dict(n=n, row_ptr=[t], col=[t])
+    with pytest.raises(DeabmError, match="exceed the fixed working array"):
+        lambda_noalloc(g, t, t, t, t, W.params_with(), 0, t)
