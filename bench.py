@@ -187,6 +187,7 @@ def run_ours(args, rank, world, local):
     # ---- batched ensemble vs plain per-replicate loop, relaxed gradient (rank 0)
     batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
     relaxed = run_relaxed(args) if (rank == 0 and not args.no_relaxed) else None
+    surrogate = run_surrogate(args) if (rank == 0 and not args.no_surrogate) else None
 
     if rank == 0:
         value = messages / (total_ms / 1e3)
@@ -225,6 +226,8 @@ def run_ours(args, rank, world, local):
             line["batched"] = batched
         if relaxed:
             line["relaxed"] = relaxed
+        if surrogate:
+            line["surrogate"] = surrogate
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -259,6 +262,68 @@ def run_relaxed(args):
             "calibration": {"steps": args.calib_steps, "seconds": cal_s, "loss_start": float(trace[0]),
                             "loss_end": float(loss1), "theta_hidden": [float(x) for x in w["hidden"][:4]],
                             "theta_found": [float(x) for x in theta[:4]]}}
+
+
+def mlp_flops_per_sample(sizes) -> int:
+    """Dense FLOPs of one forward pass: 2 * fan_in * fan_out per layer (bias and GELU
+    not counted); the input layer at its unpadded width."""
+    return sum(2 * fi * fo for fi, fo in zip(sizes[:-1], sizes[1:]))
+
+
+def measured_peak_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_surrogate(args):
+    """Surrogate MLP 14 -> 3 x 256 -> 180 at the inference batch of 65,536: forward
+    and one training step (forward + backward + Adam), timed with CUDA events."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import MLP
+
+    w = W.surrogate_workload()
+    B = w["batch"]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        m = MLP(14, w["hidden"], w["depth"], w["T"], max_batch=B, stream=stream.cuda_stream)
+        rng = np.random.default_rng(0)
+        sizes = m.sizes
+        m.set_params(np.concatenate([np.concatenate([rng.uniform(-1 / np.sqrt(fi), 1 / np.sqrt(fi), fi * fo),
+                                                     np.zeros(fo)]) for fi, fo in zip(sizes[:-1], sizes[1:])]
+                                    ).astype(np.float32))
+        x = torch.rand((B, 14), device="cuda")
+        y = torch.rand((B, w["T"]), device="cuda")
+        out = torch.empty((B, w["T"]), device="cuda")
+        for _ in range(args.warmup):
+            m.forward(x, out)
+            m.train_step(x, y, 1e-4)
+        reps = 20
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        for _ in range(reps):
+            m.forward(x, out)
+        e[1].record(stream)
+        for _ in range(reps):
+            m.train_step(x, y, 1e-4)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+    fwd_ms = e[0].elapsed_time(e[1]) / reps
+    step_ms = e[1].elapsed_time(e[2]) / reps
+    m.close()
+    f = mlp_flops_per_sample(sizes)
+    peak, kind = measured_peak_bf16()
+    fwd_tf = f * B / (fwd_ms / 1e3) / 1e12
+    train_tf = 3 * f * B / (step_ms / 1e3) / 1e12
+    return {"workload": w["name"] + f", batch {B}", "forward_ms": fwd_ms, "train_step_ms": step_ms,
+            "samples_per_s": B / (fwd_ms / 1e3), "flops_per_sample_forward": f,
+            "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
+                         "peak_kind": kind, "kernel": "gemm_bf16_kernel (forward)",
+                         "train_step_tflops": train_tf}}
 
 
 def run_batched(args):
@@ -393,8 +458,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-loop", action="store_true", help="skip the plain per-replicate loop of the batched leg")
     ap.add_argument("--no-relaxed", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--calib-steps", type=int, default=200)
-    ap.add_argument("--only", default="all", choices=["all", "plain", "batched", "relaxed"],
+    ap.add_argument("--only", default="all", choices=["all", "plain", "batched", "relaxed", "surrogate"],
                     help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -407,16 +473,17 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps(run_batched(args)))
         return
-    if args.only == "relaxed":
+    if args.only in ("relaxed", "surrogate"):
         import __graft_entry__
         __graft_entry__.build()
         import torch
         torch.cuda.set_device(local)
-        print(json.dumps(run_relaxed(args)))
+        print(json.dumps(run_relaxed(args) if args.only == "relaxed" else run_surrogate(args)))
         return
     if args.only == "plain":
         args.no_batched = True
         args.no_relaxed = True
+        args.no_surrogate = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

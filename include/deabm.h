@@ -164,6 +164,25 @@ int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, con
                        uint32_t n_rep, const float *rep_params, const uint64_t *rep_seeds,
                        void *cuda_stream, deabm_ctx **out);
 
+/* Create a ragged batch: n_pops independent populations of different sizes
+ * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda, no
+ * internal renumbering) simulated together, one kernel launch per day for all
+ * of them: resident thread blocks take tiles of rows (never spanning two
+ * populations) from a per-day work queue.  Population q's results equal those of
+ * deabm_create on its own inputs with locality_order = 0.  State arrays are
+ * concatenated in population order (sum of n_agents entries); per-day counters
+ * are [day][population] (deabm_info's n_rep = n_pops).  deabm_run captures its T
+ * days as one CUDA graph and replays it; a NULL stream here means a stream the
+ * context creates (capture needs a stream other than the legacy default one).
+ * deabm_reset restarts at day 0 with the same parameters (rep_params must be NULL). */
+int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, const deabm_agents *agents,
+                        const deabm_params *params, void *cuda_stream, deabm_ctx **out);
+
+/* Ragged batches only: time days_per_trial days for each candidate tiling (rows
+ * per tile 256..4096, resident blocks per SM 2..8) on this context's own data,
+ * keep the fastest and restart at day 0.  Either output may be NULL.  Synchronises. */
+int deabm_autotune(deabm_ctx *ctx, uint32_t days_per_trial, uint32_t *rows_per_tile, uint32_t *blocks_per_sm);
+
 /* Queue n_steps days on the context's stream and return without waiting.
  * DEABM_ESTATE if the day counter would pass max_steps. */
 int deabm_step(deabm_ctx *ctx, uint32_t n_steps);

@@ -41,6 +41,18 @@ struct deabm_ctx {
     uint32_t *seed_ids = nullptr;  // initial cases, internal ids
     uint32_t n_seed = 0;
     deabm_params base{};
+    // ragged batch of populations (n_rep counts the populations for the counters)
+    bool ragged = false;
+    std::vector<PopDesc> pops;         // host copies, KParams pointers already offset
+    PopDesc *d_pops = nullptr;
+    Tile *d_tiles = nullptr;
+    uint32_t n_tiles = 0, max_tiles = 0, rows_per_tile = 1024, grid = 0, sm_count = 0;
+    uint32_t *queue = nullptr;         // [max_steps] tile counters, one per day
+    std::vector<std::vector<uint32_t>> pop_seeds;
+    std::vector<uint32_t *> d_pop_seeds;
+    cudaStream_t own_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    uint32_t graph_day0 = 0, graph_T = 0;
     std::string err;
 };
 
@@ -473,6 +485,16 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if ((uint64_t)ctx->day + n_steps > ctx->max_steps)
         return fail(ctx, DEABM_ESTATE, "day %u + %u steps exceeds max_steps %u", ctx->day, n_steps, ctx->max_steps);
+    if (ctx->ragged) {
+        for (uint32_t q = 0; q < n_steps; ++q) {
+            const int c = ctx->cur;
+            CU(ctx, launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, ctx->day, ctx->inf[c],
+                                       ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->stream));
+            ctx->cur ^= 1;
+            ctx->day += 1;
+        }
+        return DEABM_OK;
+    }
     for (uint32_t s = 0; s < n_steps; ++s) {
         const int c = ctx->cur;
         InfBuffers I;
@@ -509,11 +531,48 @@ extern "C" int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *n
     return DEABM_OK;
 }
 
+// T ragged days as one CUDA graph (captured once per starting day and length, then replayed)
+static int run_ragged_graph(deabm_ctx *ctx, uint32_t T)
+{
+    if ((uint64_t)ctx->day + T > ctx->max_steps)
+        return fail(ctx, DEABM_ESTATE, "day %u + %u steps exceeds max_steps %u", ctx->day, T, ctx->max_steps);
+    const uint32_t d0 = ctx->day;
+    const int cur0 = ctx->cur;
+    if (!(ctx->graph && ctx->graph_day0 == d0 && ctx->graph_T == T && cur0 == (int)(d0 & 1u))) {
+        if (ctx->graph) {
+            CU(ctx, cudaGraphExecDestroy(ctx->graph));
+            ctx->graph = nullptr;
+        }
+        cudaGraph_t g;
+        CU(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        int c = cur0;
+        for (uint32_t q = 0; q < T; ++q) {
+            cudaError_t e = launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, d0 + q, ctx->inf[c],
+                                               ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->stream);
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(ctx->stream, &g);
+                return fail(ctx, DEABM_ECUDA, "capture: %s", cudaGetErrorString(e));
+            }
+            c ^= 1;
+        }
+        CU(ctx, cudaStreamEndCapture(ctx->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+        (void)cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(ctx, DEABM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        ctx->graph_day0 = d0;
+        ctx->graph_T = T;
+    }
+    CU(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+    ctx->day += T;
+    if (T & 1u) ctx->cur ^= 1;
+    return DEABM_OK;
+}
+
 extern "C" int deabm_run(deabm_ctx *ctx, uint32_t T, int32_t *new_inf, int32_t *hist)
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     const uint32_t d0 = ctx->day;
-    int rc = deabm_step(ctx, T);
+    int rc = ctx->ragged && T > 0 ? run_ragged_graph(ctx, T) : deabm_step(ctx, T);
     if (rc) return rc;
     const size_t B = ctx->n_rep;
     if (new_inf && T)
@@ -531,7 +590,7 @@ extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, in
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if ((lambda || p) && !ctx->keep_lambda) return fail(ctx, DEABM_ESTATE, "created without keep_lambda");
-    const size_t nb = (size_t)ctx->n * ctx->n_rep;
+    const size_t nb = ctx->ragged ? (size_t)ctx->n : (size_t)ctx->n * ctx->n_rep;
     cudaStream_t s = ctx->stream;
     // device arrays are in internal order: copy, then put each agent back at its caller id
     auto fetch = [&](void *dst, const void *src, size_t elem) -> int {
@@ -577,13 +636,274 @@ extern "C" int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *pois
     return DEABM_OK;
 }
 
+// ---------------------------------------------------------------- ragged batches
+// tiles of rows_per_tile rows that never cross a population boundary
+static std::vector<Tile> make_tiles(const std::vector<PopDesc> &pops, uint32_t rows_per_tile)
+{
+    std::vector<Tile> t;
+    for (uint32_t p = 0; p < pops.size(); ++p)
+        for (uint32_t b = 0; b < pops[p].kp.n; b += rows_per_tile)
+            t.push_back(Tile{p, b, std::min(pops[p].kp.n, b + rows_per_tile), 0u});
+    return t;
+}
+
+static int set_tiling(deabm_ctx *ctx, uint32_t rows_per_tile, uint32_t blocks_per_sm)
+{
+    std::vector<Tile> t = make_tiles(ctx->pops, rows_per_tile);
+    if (t.size() > ctx->max_tiles) return fail(ctx, DEABM_EINVAL, "rows_per_tile %u is too small", rows_per_tile);
+    CU(ctx, cudaMemcpyAsync(ctx->d_tiles, t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->n_tiles = (uint32_t)t.size();
+    ctx->rows_per_tile = rows_per_tile;
+    ctx->grid = std::max(1u, std::min(ctx->n_tiles, ctx->sm_count * blocks_per_sm));
+    if (ctx->graph) {
+        CU(ctx, cudaGraphExecDestroy(ctx->graph));
+        ctx->graph = nullptr;
+    }
+    return DEABM_OK;
+}
+
+extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, const deabm_agents *agents,
+                                   const deabm_params *params, void *cuda_stream, deabm_ctx **out)
+{
+    if (!out) return fail(nullptr, DEABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_pops < 1 || n_pops > 4096 || !graphs || !agents || !params)
+        return fail(nullptr, DEABM_EINVAL, "1 <= n_pops <= 4096 populations with graphs, agents, params required");
+    deabm_ctx *ctx = new (std::nothrow) deabm_ctx();
+    if (!ctx) return fail(nullptr, DEABM_ENOMEM, "host allocation failed");
+    int rc = [&]() -> int {
+        uint64_t total = 0;
+        uint32_t max_steps = 0;
+        for (uint32_t q = 0; q < n_pops; ++q) {
+            int r = validate(ctx, &graphs[q], &agents[q], &params[q], 1u, nullptr);
+            if (r) return fail(ctx, r, "population %u: %s", q, ctx->err.c_str());
+            total += graphs[q].n_agents;
+            max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
+            if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
+        }
+        if (total >= (1ull << 31)) return fail(ctx, DEABM_EINVAL, "too many agents in total");
+        ctx->ragged = true;
+        ctx->n = (uint32_t)total;
+        ctx->n_rep = n_pops;  // counters are [day][population]
+        ctx->max_steps = max_steps;
+        ctx->base = params[0];
+        if (cuda_stream) {
+            ctx->stream = (cudaStream_t)cuda_stream;
+        } else {  // graph capture needs a stream other than the legacy default stream
+            CU(ctx, cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+            ctx->stream = ctx->own_stream;
+        }
+        cudaStream_t s = ctx->stream;
+        int dev = 0, sms = 0;
+        CU(ctx, cudaGetDevice(&dev));
+        CU(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        ctx->sm_count = (uint32_t)sms;
+        int r;
+        const size_t N = total;
+        if ((r = dalloc(ctx, &ctx->age, N))) return r;
+        if ((r = dalloc(ctx, &ctx->dose1, N))) return r;
+        StateRef *sets[2] = {&ctx->S, &ctx->S0};
+        for (StateRef *st : sets) {
+            if ((r = dalloc(ctx, &st->stage, N))) return r;
+            if ((r = dalloc(ctx, &st->timer, N))) return r;
+            if ((r = dalloc(ctx, &st->tinf, N))) return r;
+            if ((r = dalloc(ctx, &st->flags, N))) return r;
+            if ((r = dalloc(ctx, &st->qt, N))) return r;
+        }
+        if ((r = dalloc(ctx, &ctx->inf[0], N))) return r;
+        if ((r = dalloc(ctx, &ctx->inf[1], N))) return r;
+        if ((r = dalloc(ctx, &ctx->tab, n_pops))) return r;
+        if ((r = dalloc(ctx, &ctx->rep, n_pops))) return r;
+        const size_t days = ctx->max_steps;
+        if ((r = dalloc(ctx, &ctx->C.new_inf, days * n_pops))) return r;
+        if ((r = dalloc(ctx, &ctx->C.hist, days * n_pops * DEABM_N_STAGE))) return r;
+        if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
+        if ((r = dalloc(ctx, &ctx->queue, days))) return r;
+        uint32_t max_n = 0;
+        for (uint32_t q = 0; q < n_pops; ++q) max_n = std::max(max_n, graphs[q].n_agents);
+        uint32_t *d_scratch;
+        double *d_gamma;
+        float *d_A;
+        if ((r = dalloc(ctx, &d_scratch, dose1_scratch_words(max_n)))) return r;
+        if ((r = dalloc(ctx, &d_gamma, 6 * (size_t)n_pops))) return r;
+        if ((r = dalloc(ctx, &d_A, 3 * (size_t)n_pops))) return r;
+        ctx->pops.resize(n_pops);
+        ctx->pop_seeds.resize(n_pops);
+        ctx->d_pop_seeds.assign(n_pops, nullptr);
+        uint32_t base = 0;
+        std::vector<int8_t> st;
+        std::vector<int16_t> tm, ti;
+        std::vector<uint8_t> fl, qt;
+        for (uint32_t q = 0; q < n_pops; ++q) {
+            const deabm_graph &g = graphs[q];
+            const deabm_agents &a = agents[q];
+            const deabm_params &p = params[q];
+            const uint32_t n = g.n_agents;
+            PopDesc &pd = ctx->pops[q];
+            std::memset(&pd, 0, sizeof pd);
+            pd.base = base;
+            KParams &K = pd.kp;
+            K.n = n;
+            K.n_nets = g.n_nets;
+            K.n_rep = 1;
+            K.inf_len = p.inf_len;
+            K.dt = p.dt;
+            K.rand_on = g.rand_mean > 0.0f ? 1u : 0u;
+            for (uint32_t k = 0; k < g.n_nets; ++k) {
+                const uint32_t E = g.row_ptr[k][n];
+                uint32_t *rp, *cl;
+                if ((r = dalloc(ctx, &rp, (size_t)n + 1))) return r;
+                if ((r = dalloc(ctx, &cl, E))) return r;
+                CU(ctx, cudaMemcpyAsync(rp, g.row_ptr[k], 4ull * (n + 1), cudaMemcpyHostToDevice, s));
+                if (E) CU(ctx, cudaMemcpyAsync(cl, g.col[k], 4ull * E, cudaMemcpyHostToDevice, s));
+                K.row_ptr[k] = rp;
+                K.col[k] = cl;
+                ctx->static_edges += E;
+            }
+            K.net_seed = p.net_seed;
+            K.test_on = p.test_on;
+            K.test_lo = p.test_lo;
+            K.test_hi = p.test_hi;
+            K.quar_on = p.quar_on;
+            K.quar_days = p.quar_days;
+            K.thr_sens = threshold(p.test_sens);
+            K.thr_qdrop = threshold(p.q_dropout);
+            K.vax_on = p.vax_on;
+            K.vax_onset = p.vax_onset;
+            K.thr_eff1 = threshold(p.vax_eff1);
+            K.thr_eff2 = threshold(p.vax_eff2);
+            K.tab = ctx->tab + q;
+            K.rep = ctx->rep + q;
+            K.age = ctx->age + base;
+            K.dose1_day = ctx->dose1 + base;
+            K.orig_id = nullptr;
+            std::vector<Rep> reps;
+            build_reps(&p, 1, nullptr, nullptr, reps);
+            pd.rep = reps[0];
+            CU(ctx, cudaMemcpyAsync(ctx->rep + q, &pd.rep, sizeof(Rep), cudaMemcpyHostToDevice, s));
+            // tables of this population
+            Tables T;
+            std::memset(&T, 0, sizeof T);
+            {
+                const double m = (double)g.rand_mean;
+                volatile double t = std::exp(-m), c = t;
+                T.pois[0] = threshold(c);
+                for (int k = 1; k < DEABM_POIS_CAP; ++k) {
+                    t = (t * m) / (double)k;
+                    c = c + t;
+                    T.pois[k] = threshold(c);
+                }
+            }
+            for (int a2 = 0; a2 < DEABM_N_AGE; ++a2) {
+                T.thr_asym[a2] = threshold(p.p_asym[a2]);
+                T.thr_sev[a2] = threshold(p.p_sev[a2]);
+                T.thr_branch[DEABM_SEV][a2] = threshold(p.p_hosp[a2]);
+                T.thr_branch[DEABM_HOSP][a2] = threshold(p.p_icu[a2]);
+                T.thr_branch[DEABM_ICU][a2] = threshold(p.p_death[a2]);
+            }
+            std::memcpy(T.dur_lo, p.dur_lo, sizeof T.dur_lo);
+            std::memcpy(T.dur_hi, p.dur_hi, sizeof T.dur_hi);
+            CU(ctx, cudaMemcpyAsync(ctx->tab + q, &T, sizeof T, cudaMemcpyHostToDevice, s));
+            const double gs[6] = {p.inf_shape[0], p.inf_shape[1], p.inf_shape[2], p.inf_scale[0], p.inf_scale[1],
+                                  p.inf_scale[2]};
+            CU(ctx, cudaMemcpyAsync(d_gamma + 6 * q, gs, sizeof gs, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(d_A + 3 * q, p.A_class, sizeof(float) * 3, cudaMemcpyHostToDevice, s));
+            CU(ctx, launch_inf_table(ctx->tab + q, d_gamma + 6 * q, d_A + 3 * q, p.inf_len, s));
+            CU(ctx, cudaMemcpyAsync(ctx->age + base, a.age_bin, n, cudaMemcpyHostToDevice, s));
+            const uint32_t per_day = p.vax_on ? (uint32_t)std::floor(p.vax_rate * (double)n) : 0u;
+            CU(ctx, launch_dose1_days(ctx->age + base, n, p.vax_start, per_day, ctx->dose1 + base, d_scratch, s));
+            st.assign(n, 0); tm.assign(n, 0); ti.assign(n, 0); fl.assign(n, 0); qt.assign(n, 0);
+            for (uint32_t j = 0; j < n; ++j) {
+                if (a.stage) st[j] = a.stage[j];
+                if (a.timer) tm[j] = a.timer[j];
+                if (a.tinf) ti[j] = a.tinf[j];
+                if (a.flags) fl[j] = a.flags[j];
+                if (a.qt) qt[j] = a.qt[j];
+            }
+            CU(ctx, cudaMemcpyAsync(ctx->S0.stage + base, st.data(), n, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.timer + base, tm.data(), 2ull * n, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.tinf + base, ti.data(), 2ull * n, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.flags + base, fl.data(), n, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.qt + base, qt.data(), n, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaStreamSynchronize(s));  // staging vectors are reused by the next population
+            ctx->pop_seeds[q].assign(a.seed_ids, a.seed_ids + a.n_seed);
+            if (a.n_seed) {
+                if ((r = dalloc(ctx, &ctx->d_pop_seeds[q], a.n_seed))) return r;
+                CU(ctx, cudaMemcpyAsync(ctx->d_pop_seeds[q], a.seed_ids, 4ull * a.n_seed, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaStreamSynchronize(s));
+            }
+            base += n;
+        }
+        if ((r = dalloc(ctx, &ctx->d_pops, n_pops))) return r;
+        CU(ctx, cudaMemcpyAsync(ctx->d_pops, ctx->pops.data(), sizeof(PopDesc) * n_pops, cudaMemcpyHostToDevice, s));
+        ctx->max_tiles = (uint32_t)make_tiles(ctx->pops, 256).size();
+        if ((r = dalloc(ctx, &ctx->d_tiles, ctx->max_tiles))) return r;
+        if ((r = set_tiling(ctx, 1024, 4))) return r;
+        ctx->kp = ctx->pops[0].kp;
+        if ((r = deabm_reset(ctx, nullptr, nullptr))) return r;
+        CU(ctx, cudaStreamSynchronize(s));
+        return DEABM_OK;
+    }();
+    if (rc != DEABM_OK) {
+        std::string msg = ctx->err;
+        deabm_destroy(ctx);
+        g_err = msg;
+        return rc;
+    }
+    *out = ctx;
+    return DEABM_OK;
+}
+
+// Time `days_per_trial` days for every (rows per tile, blocks per SM) candidate on
+// the live state, keep the fastest, then restart at day 0.
+extern "C" int deabm_autotune(deabm_ctx *ctx, uint32_t days_per_trial, uint32_t *rows_per_tile, uint32_t *blocks_per_sm)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (!ctx->ragged) return fail(ctx, DEABM_ESTATE, "autotuning applies to ragged batches");
+    if (days_per_trial == 0 || days_per_trial > ctx->max_steps) return fail(ctx, DEABM_EINVAL, "bad days_per_trial");
+    const uint32_t rows[] = {256, 512, 1024, 2048, 4096};
+    const uint32_t bps[] = {2, 4, 6, 8};
+    float best = 1e30f;
+    uint32_t best_r = 1024, best_b = 4;
+    cudaEvent_t e0, e1;
+    CU(ctx, cudaEventCreate(&e0));
+    CU(ctx, cudaEventCreate(&e1));
+    int r = DEABM_OK;
+    for (uint32_t rt : rows) {
+        for (uint32_t b : bps) {
+            if ((r = set_tiling(ctx, rt, b))) break;
+            if ((r = deabm_reset(ctx, nullptr, nullptr))) break;
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { r = DEABM_ECUDA; break; }
+            if ((r = deabm_step(ctx, days_per_trial))) break;
+            if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                r = DEABM_ECUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_r = rt; best_b = b; }
+        }
+        if (r) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) return r;
+    if ((r = set_tiling(ctx, best_r, best_b))) return r;
+    if ((r = deabm_reset(ctx, nullptr, nullptr))) return r;
+    if (rows_per_tile) *rows_per_tile = best_r;
+    if (blocks_per_sm) *blocks_per_sm = best_b;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return DEABM_OK;
+}
+
 extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_seeds)
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if ((rep_params == nullptr) != (rep_seeds == nullptr))
         return fail(ctx, DEABM_EINVAL, "rep_params and rep_seeds go together");
     cudaStream_t s = ctx->stream;
-    const size_t nb = (size_t)ctx->n * ctx->n_rep;
+    const size_t nb = ctx->ragged ? (size_t)ctx->n : (size_t)ctx->n * ctx->n_rep;
     if (rep_params) {
         for (uint32_t b = 0; b < ctx->n_rep; ++b) {
             const float d = rep_params[b * DEABM_N_REP_PARAMS + 13];
@@ -595,11 +915,31 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
         CU(ctx, cudaMemcpyAsync(ctx->rep, reps.data(), sizeof(Rep) * ctx->n_rep, cudaMemcpyHostToDevice, s));
         CU(ctx, cudaStreamSynchronize(s));  // the staging vector goes out of scope
     }
+    if (ctx->ragged && rep_params)
+        return fail(ctx, DEABM_ESTATE, "a ragged batch keeps the parameters it was created with");
     CU(ctx, cudaMemcpyAsync(ctx->S.stage, ctx->S0.stage, nb, cudaMemcpyDeviceToDevice, s));
     CU(ctx, cudaMemcpyAsync(ctx->S.timer, ctx->S0.timer, nb * 2, cudaMemcpyDeviceToDevice, s));
     CU(ctx, cudaMemcpyAsync(ctx->S.tinf, ctx->S0.tinf, nb * 2, cudaMemcpyDeviceToDevice, s));
     CU(ctx, cudaMemcpyAsync(ctx->S.flags, ctx->S0.flags, nb, cudaMemcpyDeviceToDevice, s));
     CU(ctx, cudaMemcpyAsync(ctx->S.qt, ctx->S0.qt, nb, cudaMemcpyDeviceToDevice, s));
+    if (ctx->ragged) {
+        for (size_t q = 0; q < ctx->pops.size(); ++q) {
+            const PopDesc &pd = ctx->pops[q];
+            StateRef Sp{ctx->S.stage + pd.base, ctx->S.timer + pd.base, ctx->S.tinf + pd.base, ctx->S.flags + pd.base,
+                        ctx->S.qt + pd.base};
+            if (!ctx->pop_seeds[q].empty())
+                CU(ctx, launch_seed(pd.kp, ctx->d_pop_seeds[q], (uint32_t)ctx->pop_seeds[q].size(), Sp, s));
+            CU(ctx, launch_emit(pd.kp, Sp, ctx->inf[0] + pd.base, nullptr, s));
+        }
+        ctx->cur = 0;
+        CU(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(uint32_t) * ctx->max_steps, s));
+        const size_t days = ctx->max_steps;
+        CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * ctx->n_rep, s));
+        CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
+        CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+        ctx->day = 0;
+        return DEABM_OK;
+    }
     if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
     ctx->cur = 0;
     CU(ctx, launch_emit(ctx->kp, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
@@ -633,6 +973,8 @@ extern "C" void deabm_destroy(deabm_ctx *ctx)
 {
     if (!ctx) return;
     if (!ctx->allocs.empty()) (void)cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) (void)cudaGraphExecDestroy(ctx->graph);
     for (void *ptr : ctx->allocs) (void)cudaFree(ptr);
+    if (ctx->own_stream) (void)cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }

@@ -103,6 +103,21 @@ struct StateRef {
     uint8_t *flags, *qt;
 };
 
+// One population of a ragged batch: a KParams view whose CSR, age and dose-day
+// pointers are already offset to the population's slice (local ids), its
+// replicate parameters, and the offset of its agents in the concatenated state.
+struct PopDesc {
+    KParams kp;
+    Rep rep;
+    uint32_t base;
+    uint32_t pad_[3];
+};
+
+// A unit of work of the ragged day kernel: rows [begin, end) of population pop.
+struct Tile {
+    uint32_t pop, begin, end, pad_;
+};
+
 struct Counters {
     int32_t *new_inf;          // [day][n_rep]
     int32_t *hist;             // [day][n_rep][11]

@@ -10,6 +10,11 @@ namespace deabm {
 cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, const StateRef &S, const Counters &C,
                         float *lam_out, float *p_out, cudaStream_t stream);
 
+// one simulated day of a ragged batch of populations (persistent CTAs, tile queue)
+cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
+                               const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
+                               uint32_t n_pops, uint32_t grid, cudaStream_t stream);
+
 // set-up: infectiousness table (FP64 gamma integrals, rounded once, times A_class)
 cudaError_t launch_inf_table(Tables *tab, const double *shape_scale /*device [6]*/, const float *A_class /*device [3]*/,
                              uint32_t len, cudaStream_t stream);

@@ -170,6 +170,74 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     if (tid == 0 && s_msgs) atomicAdd(&C.msgs[day], s_msgs);
 }
 
+// Ragged batch of independent populations in one launch: CTAs stay resident and
+// pull tiles (rows of one population) from the day's atomic queue until none is
+// left, so populations of 10^4 and 10^6 agents share the GPU without one
+// launch each.  Every row runs the plain day on its population's local ids,
+// giving exactly the single-population result.
+__global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restrict__ pops, const Tile *__restrict__ tiles,
+                                                          uint32_t n_tiles, uint32_t *queue, uint32_t day,
+                                                          const float *inf_cur, float *inf_next, StateRef S,
+                                                          Counters C, uint32_t n_pops)
+{
+    __shared__ PopDesc sp;
+    __shared__ uint32_t s_tile;
+    __shared__ int s_hist[DEABM_N_STAGE];
+    __shared__ int s_new;
+    __shared__ unsigned long long s_msgs;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(queue + day, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= n_tiles) break;
+        const Tile tl = tiles[t];
+        {
+            const uint32_t *src = (const uint32_t *)(pops + tl.pop);
+            uint32_t *dst = (uint32_t *)&sp;
+            for (uint32_t q = threadIdx.x; q < sizeof(PopDesc) / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        if (threadIdx.x < DEABM_N_STAGE) s_hist[threadIdx.x] = 0;
+        if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; }
+        __syncthreads();
+        InfBuffers I;
+        I.cur = inf_cur + sp.base;
+        I.next = inf_next + sp.base;
+        I.rand_cur = I.cur;
+        I.rand_next = nullptr;
+        StateRef Sp;
+        Sp.stage = S.stage + sp.base;
+        Sp.timer = S.timer + sp.base;
+        Sp.tinf = S.tinf + sp.base;
+        Sp.flags = S.flags + sp.base;
+        Sp.qt = S.qt + sp.base;
+        for (uint32_t r0 = tl.begin; r0 < tl.end; r0 += blockDim.x) {
+            const uint32_t j = r0 + threadIdx.x;
+            const bool active = j < tl.end;
+            int st = 0;
+            bool infected = false;
+            uint32_t k = 0;
+            if (active) agent_day(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k);
+            count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
+        }
+        __syncthreads();
+        if (threadIdx.x < DEABM_N_STAGE && s_hist[threadIdx.x])
+            atomicAdd(&C.hist[((size_t)day * n_pops + tl.pop) * DEABM_N_STAGE + threadIdx.x], s_hist[threadIdx.x]);
+        if (threadIdx.x == 0) {
+            if (s_new) atomicAdd(&C.new_inf[(size_t)day * n_pops + tl.pop], s_new);
+            if (s_msgs) atomicAdd(&C.msgs[day], s_msgs);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
+                               const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
+                               uint32_t n_pops, uint32_t grid, cudaStream_t stream)
+{
+    step_ragged_kernel<<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, const StateRef &S, const Counters &C,
                         float *lam_out, float *p_out, cudaStream_t stream)
 {

@@ -24,7 +24,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_relaxed_last_error", "deabm_relaxed_destroy", "deabm_reset", "deabm_mlp_create",
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
-           "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error")
+           "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -99,6 +99,10 @@ def lib():
         L.deabm_relaxed_destroy.argtypes = [vp]
         L.deabm_relaxed_destroy.restype = None
         L.deabm_reset.argtypes = [vp, vp, vp]
+        L.deabm_create_ragged.argtypes = [u32, C.POINTER(Graph), C.POINTER(Agents), C.POINTER(Params), vp, C.POINTER(vp)]
+        L.deabm_create_ragged.restype = C.c_int
+        L.deabm_autotune.argtypes = [vp, u32, C.POINTER(u32), C.POINTER(u32)]
+        L.deabm_autotune.restype = C.c_int
         L.deabm_lambda_noalloc.argtypes = [C.POINTER(Graph), vp, vp, vp, vp, C.POINTER(Params), u32, vp, vp]
         L.deabm_lambda_noalloc.restype = C.c_int
         L.deabm_lambda_noalloc_last_error.argtypes = []
@@ -279,6 +283,88 @@ def relaxed_loss(sim: "Relaxed", theta, target):
             return gout * g.to(gout.dtype), None
 
     return _Fn.apply(theta, target)
+
+
+class RaggedSimulation:
+    """A ragged batch of independent populations (different sizes, graphs,
+    parameters) stepped together by one persistent kernel per day; ``run`` replays
+    a captured CUDA graph of the days."""
+
+    def __init__(self, pops: list, params: list, max_steps: int = 1024, stream=None):
+        L = lib()
+        keep = []
+        n = len(pops)
+        gs = (Graph * n)()
+        ag = (Agents * n)()
+        ps = (Params * n)()
+        for q, (pop, par) in enumerate(zip(pops, params)):
+            gs[q] = _graph_struct(pop, par["rand_mean"], keep)
+            age = np.ascontiguousarray(pop["age"], dtype=np.uint8)
+            keep.append(age)
+            ag[q].age_bin = age.ctypes.data
+            ids = np.ascontiguousarray(pop.get("seed_ids", []), dtype=np.uint32)
+            keep.append(ids)
+            if ids.size:
+                ag[q].seed_ids = ids.ctypes.data
+                ag[q].n_seed = ids.size
+            ps[q] = make_params(par, max_steps=max_steps, locality_order=False)
+        self.sizes = [int(p["n"]) for p in pops]
+        self.n_pops = n
+        self.n = sum(self.sizes)
+        self._stream = C.c_void_p(stream) if isinstance(stream, int) else (stream or C.c_void_p(0))
+        ctx = C.c_void_p()
+        _check(L.deabm_create_ragged(n, gs, ag, ps, self._stream, C.byref(ctx)))
+        self.ctx = ctx
+
+    def autotune(self, days_per_trial: int = 2):
+        r, b = C.c_uint32(), C.c_uint32()
+        _check(lib().deabm_autotune(self.ctx, days_per_trial, C.byref(r), C.byref(b)), self.ctx)
+        return r.value, b.value
+
+    def step(self, n_steps: int = 1):
+        _check(lib().deabm_step(self.ctx, n_steps), self.ctx)
+
+    def run(self, T: int, hist: bool = True):
+        ni = np.zeros((T, self.n_pops), np.int32)
+        h = np.zeros((T, self.n_pops, N_STAGE), np.int32) if hist else None
+        _check(lib().deabm_run(self.ctx, T, _p(ni), _p(h)), self.ctx)
+        return ni, h
+
+    def reset(self):
+        _check(lib().deabm_reset(self.ctx, None, None), self.ctx)
+
+    def sync(self):
+        _check(lib().deabm_sync(self.ctx), self.ctx)
+
+    def counters(self, days: int):
+        ni = np.zeros((days, self.n_pops), np.int32)
+        h = np.zeros((days, self.n_pops, N_STAGE), np.int32)
+        m = np.zeros(days, np.uint64)
+        _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
+        return ni, h, m
+
+    def state(self) -> list:
+        """Per-population state dicts (caller ids)."""
+        out = dict(stage=np.zeros(self.n, np.int8), timer=np.zeros(self.n, np.int16), tinf=np.zeros(self.n, np.int16),
+                   flags=np.zeros(self.n, np.uint8), qt=np.zeros(self.n, np.uint8))
+        _check(lib().deabm_get_state(self.ctx, _p(out["stage"]), _p(out["timer"]), _p(out["tinf"]),
+                                     _p(out["flags"]), _p(out["qt"]), None, None), self.ctx)
+        res, b = [], 0
+        for n in self.sizes:
+            res.append({k: v[b:b + n] for k, v in out.items()})
+            b += n
+        return res
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().deabm_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

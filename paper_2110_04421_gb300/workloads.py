@@ -217,3 +217,16 @@ def surrogate_workload():
     the N = 100,000 ensemble workload (80/20 split), inference batch 65,536."""
     return dict(name="surrogate MLP 14-256x3-180", n_runs=50_000, n=100_000, T=180, B=256, hidden=256, depth=3,
                 batch=65_536, params=batched()["params"])
+
+
+def ragged(n_pops: int = 64, lo: float = 1e4, hi: float = 1e6, seed: int = 0):
+    """A ragged batch: n_pops populations with N log-uniform in [lo, hi], each with
+    its own generated graph, 10 initial cases, own seeds, the plain disease model."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x4A66]))
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n_pops)).astype(np.int64)
+    pops, params = [], []
+    for q, n in enumerate(sizes):
+        pops.append(population(int(n), seed=1000 + q, n_seed_infections=10))
+        params.append(params_with(seed=int(rng.integers(0, 2**62)), net_seed=int(rng.integers(0, 2**62)),
+                                  R=float(rng.uniform(2.0, 6.0))))
+    return dict(name=f"ragged {n_pops} populations, N log-uniform [{lo:.0e}, {hi:.0e}]", pops=pops, params=params)

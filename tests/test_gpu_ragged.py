@@ -1,0 +1,82 @@
+"""Ragged batch (several populations of different sizes in one persistent launch
+per day, days replayed as a CUDA graph): each population must reproduce its own
+single-population run exactly, before and after autotuning and reset."""
+import numpy as np
+import pytest
+
+from paper_2110_04421_gb300 import workloads as W
+from tests.helpers import gpu_available, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+if not gpu_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def case():
+    sizes = [2000, 157, 5003, 33, 1200, 9000]
+    pops, params = [], []
+    for q, n in enumerate(sizes):
+        pops.append(W.population(n, 40 + q, max(1, n // 50)))
+        params.append(W.params_with(R=2.5 + q * 0.6, seed=100 + q, net_seed=200 + q, test_on=q % 2, quar_on=q % 2,
+                                    vax_on=int(q >= 3), vax_start=4, vax_rate=0.02))
+    return pops, params
+
+
+def single_runs(pops, params, T):
+    from paper_2110_04421_gb300.deabm import Simulation
+    out = []
+    for pop, par in zip(pops, params):
+        s = Simulation(pop, par, pop["age"], pop["seed_ids"], max_steps=T, locality_order=False)
+        ni, h = s.run(T)
+        out.append((ni[:, 0], h[:, 0], s.state()))
+        s.close()
+    return out
+
+
+def check(ragged_out, singles):
+    ni, h, states = ragged_out
+    for q, (ni1, h1, st1) in enumerate(singles):
+        assert np.array_equal(ni[:, q], ni1), q
+        assert np.array_equal(h[:, q], h1), q
+        for k in st1:
+            assert np.array_equal(states[q][k], st1[k]), (q, k)
+
+
+def test_each_population_matches_its_own_run():
+    from paper_2110_04421_gb300.deabm import RaggedSimulation
+    pops, params = case()
+    T = 35
+    singles = single_runs(pops, params, T)
+    r = RaggedSimulation(pops, params, max_steps=T)
+    ni, h = r.run(T)
+    check((ni, h, r.state()), singles)
+    r.reset()
+    ni2, h2 = r.run(T)  # graph replay after a reset
+    assert np.array_equal(ni, ni2) and np.array_equal(h, h2)
+    r.close()
+    for q in (1, 3):  # the two smallest against the oracle
+        o = oracle_sim(pops[q], params[q])
+        ni_o, h_o, _ = o.run(T)
+        assert np.array_equal(ni_o, ni[:, q]) and np.array_equal(h_o, h[:, q])
+
+
+def test_autotuned_tiling_changes_nothing():
+    from paper_2110_04421_gb300.deabm import RaggedSimulation
+    pops, params = case()
+    T = 20
+    singles = single_runs(pops, params, T)
+    r = RaggedSimulation(pops, params, max_steps=T)
+    rows, bps = r.autotune(days_per_trial=2)
+    assert rows in (256, 512, 1024, 2048, 4096) and bps in (2, 4, 6, 8)
+    r.step(T)
+    r.sync()
+    ni, h, _ = r.counters(T)
+    check((ni, h, r.state()), singles)
+    r.close()
