@@ -188,6 +188,7 @@ def run_ours(args, rank, world, local):
     batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
     relaxed = run_relaxed(args) if (rank == 0 and not args.no_relaxed) else None
     surrogate = run_surrogate(args) if (rank == 0 and not args.no_surrogate) else None
+    ragged = run_ragged(args) if (rank == 0 and not args.no_ragged) else None
 
     if rank == 0:
         value = messages / (total_ms / 1e3)
@@ -228,6 +229,8 @@ def run_ours(args, rank, world, local):
             line["relaxed"] = relaxed
         if surrogate:
             line["surrogate"] = surrogate
+        if ragged:
+            line["ragged"] = ragged
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -324,6 +327,51 @@ def run_surrogate(args):
             "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
                          "peak_kind": kind, "kernel": "gemm_bf16_kernel (forward)",
                          "train_step_tflops": train_tf}}
+
+
+def run_ragged(args):
+    """64 populations with N log-uniform in [1e4, 1e6] in one persistent launch per
+    day (days replayed as a CUDA graph, tiling autotuned) against a loop of one
+    plain launch per population per day."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import RaggedSimulation, Simulation
+
+    w = W.ragged(64)
+    T = max(3, min(args.batched_steps, args.steps))
+    stream = torch.cuda.Stream()
+    r = RaggedSimulation(w["pops"], w["params"], max_steps=args.warmup + T, stream=stream.cuda_stream)
+    rows, bps = r.autotune(days_per_trial=2)
+    r.step(args.warmup)
+    r.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r.run(T, hist=False)  # one CUDA graph of T day launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, _, msgs = r.counters(args.warmup + T)
+    r.close()
+    messages = int(msgs[args.warmup:].astype(np.int64).sum())
+    sims = [Simulation(p, par, p["age"], p["seed_ids"], max_steps=args.warmup + T, stream=stream.cuda_stream,
+                       locality_order=False) for p, par in zip(w["pops"], w["params"])]
+    for s in sims:
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(T):
+        for s in sims:
+            s.step(1)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e2.elapsed_time(e3)
+    for s in sims:
+        s.close()
+    return {"workload": w["name"], "total_agents": int(sum(p["n"] for p in w["pops"])), "steps": T,
+            "value": messages / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / T,
+            "autotuned": {"rows_per_tile": rows, "blocks_per_sm": bps},
+            "loop_of_plain_launches_ms_per_step": ms_loop / T, "multiple_of_plain_loop": ms_loop / ms}
 
 
 def run_batched(args):
@@ -459,8 +507,9 @@ def main():
     ap.add_argument("--no-loop", action="store_true", help="skip the plain per-replicate loop of the batched leg")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--calib-steps", type=int, default=200)
-    ap.add_argument("--only", default="all", choices=["all", "plain", "batched", "relaxed", "surrogate"],
+    ap.add_argument("--only", default="all", choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged"],
                     help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -473,17 +522,19 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps(run_batched(args)))
         return
-    if args.only in ("relaxed", "surrogate"):
+    if args.only in ("relaxed", "surrogate", "ragged"):
         import __graft_entry__
         __graft_entry__.build()
         import torch
         torch.cuda.set_device(local)
-        print(json.dumps(run_relaxed(args) if args.only == "relaxed" else run_surrogate(args)))
+        fn = {"relaxed": run_relaxed, "surrogate": run_surrogate, "ragged": run_ragged}[args.only]
+        print(json.dumps(fn(args)))
         return
     if args.only == "plain":
         args.no_batched = True
         args.no_relaxed = True
         args.no_surrogate = True
+        args.no_ragged = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

@@ -17,7 +17,7 @@ namespace deabm {
 #define DEABM_ROUND 10
 #endif
 #ifndef DEABM_PLAIN_MINB
-#define DEABM_PLAIN_MINB 6
+#define DEABM_PLAIN_MINB 12
 #endif
 constexpr uint32_t kRound = DEABM_ROUND;
 

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "deabm.h"
@@ -78,6 +79,9 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, each 64 x 32
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    // split-K (weight gradients): this CTA reduces K range [kb, ke) into its own partial
+    const int kchunk = (g.K + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int kb = (int)blockIdx.z * kchunk, ke = min(g.K, kb + kchunk);
     float acc[4][4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -86,28 +90,28 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
     const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int r0 = 0; r0 < g.K; r0 += BK) {
+    for (int r0 = kb; r0 < ke; r0 += BK) {
         // A tile: walk the contiguous dimension with consecutive threads
         if (g.sAr == 1) {
             for (int q = tid; q < BM * BK; q += 128) {
                 const int i = q / BK, r = q % BK, gi = i0 + i, gr = r0 + r;
-                sA[i][r] = (gi < g.M && gr < g.K) ? g.A[(long)gi * g.sAi + gr] : zero;
+                sA[i][r] = (gi < g.M && gr < ke) ? g.A[(long)gi * g.sAi + gr] : zero;
             }
         } else {
             for (int q = tid; q < BM * BK; q += 128) {
                 const int r = q / BM, i = q % BM, gi = i0 + i, gr = r0 + r;
-                sA[i][r] = (gi < g.M && gr < g.K) ? g.A[(long)gi * g.sAi + (long)gr * g.sAr] : zero;
+                sA[i][r] = (gi < g.M && gr < ke) ? g.A[(long)gi * g.sAi + (long)gr * g.sAr] : zero;
             }
         }
         if (g.sBj == 1) {
             for (int q = tid; q < BN * BK; q += 128) {
                 const int r = q / BN, j = q % BN, gj = j0 + j, gr = r0 + r;
-                sB[j][r] = (gj < g.N && gr < g.K) ? g.B[(long)gr * g.sBr + gj] : zero;
+                sB[j][r] = (gj < g.N && gr < ke) ? g.B[(long)gr * g.sBr + gj] : zero;
             }
         } else {
             for (int q = tid; q < BN * BK; q += 128) {
                 const int j = q / BK, r = q % BK, gj = j0 + j, gr = r0 + r;
-                sB[j][r] = (gj < g.N && gr < g.K) ? g.B[(long)gr * g.sBr + (long)gj * g.sBj] : zero;
+                sB[j][r] = (gj < g.N && gr < ke) ? g.B[(long)gr * g.sBr + (long)gj * g.sBj] : zero;
             }
         }
         __syncthreads();
@@ -161,12 +165,22 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
                         g.outf[o] = d;
                         g.outb[o] = __float2bfloat16(d);
                     } else {
-                        g.outf[o] = v;
+                        g.outf[o + (long)blockIdx.z * g.M * g.ldo] = v;
                     }
                 }
 }
 
 // ------------------------------------------------------------------ small kernels
+// out[q] = sum over splits of part[s][q] in split order (deterministic)
+__global__ void splitk_reduce_kernel(const float *part, int splits, long n, float *out)
+{
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        for (int z = 0; z < splits; ++z) v += part[(long)z * n + q];
+        out[q] = v;
+    }
+}
+
 __global__ void to_bf16_pad_kernel(const float *x, int rows, int cols, int ld, __nv_bfloat16 *out)
 {
     const long n = (long)rows * ld;
@@ -207,14 +221,33 @@ __global__ void loss_reduce_kernel(const double *part, int nparts, float scale, 
     }
 }
 
-// db[j] = sum_i dz[i][j] (fixed order per column)
-__global__ void colsum_kernel(const float *dz, int rows, int cols, float *db)
+// db[j] = sum_i dz[i][j]: row chunks summed in parallel (partials [chunk][col]),
+// then the chunks in order (deterministic)
+constexpr int kColChunks = 64;
+__global__ void colsum_partial_kernel(const float *dz, int rows, int cols, float *part)
+{
+    const int j = blockIdx.x * 32 + (threadIdx.x & 31), sub = threadIdx.x >> 5;  // 8 row lanes
+    const int chunk = (rows + kColChunks - 1) / kColChunks, r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
+    __shared__ float red[8][32];
+    float s = 0.0f;
+    if (j < cols)
+        for (int i = r0 + sub; i < r1; i += 8) s += dz[(long)i * cols + j];
+    red[sub][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (sub == 0 && j < cols) {
+        float t = 0.0f;
+        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+        part[(long)blockIdx.y * cols + j] = t;
+    }
+}
+
+__global__ void colsum_final_kernel(const float *part, int cols, float *db)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cols) return;
-    double s = 0.0;
-    for (int i = 0; i < rows; ++i) s += dz[(long)i * cols + j];
-    db[j] = (float)s;
+    float s = 0.0f;
+    for (int c = 0; c < kColChunks; ++c) s += part[(long)c * cols + j];
+    db[j] = s;
 }
 
 __global__ void adam_update_kernel(float *w, float *m, float *v, const float *g, long n, float lr, float b1, float b2,
@@ -257,7 +290,8 @@ struct deabm_mlp {
     std::vector<__nv_bfloat16 *> Wb;                      // BF16 copies [kpad x fout]
     std::vector<__nv_bfloat16 *> act;                     // a_l, l = 0..L-1 (a_0 = input) [B x ld]
     std::vector<float *> z;                               // pre-activations of hidden layers [B x H]
-    float *yhat = nullptr, *dz = nullptr, *dz2 = nullptr, *loss = nullptr;
+    float *yhat = nullptr, *dz = nullptr, *dz2 = nullptr, *loss = nullptr, *wpart = nullptr;
+    int max_splits = 1;
     __nv_bfloat16 *dzb = nullptr, *dzb2 = nullptr;
     double *loss_part = nullptr;
     int step = 0;
@@ -298,9 +332,9 @@ static int m_alloc(deabm_mlp *m, T **out, size_t count)
     return DEABM_OK;
 }
 
-static int gemm(cudaStream_t s, const GemmArgs &g)
+static int gemm(cudaStream_t s, const GemmArgs &g, int splits = 1)
 {
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, splits);
     if (grid.y > 65535) return mlp_fail(DEABM_EINVAL, "GEMM with M = %d is too tall", g.M);
     gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
     MCU(cudaGetLastError());
@@ -377,6 +411,13 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
         if ((r = m_alloc(m, &m->dzb, B * wmax))) return r;
         if ((r = m_alloc(m, &m->dzb2, B * wmax))) return r;
         if ((r = m_alloc(m, &m->loss, 1))) return r;
+        // split-K partials of the largest weight gradient: enough splits to fill the GPU
+        m->max_splits = (int)std::min<uint32_t>(64u, std::max<uint32_t>(1u, max_batch / 256u));
+        size_t wmax_params = 0;
+        for (int l = 0; l < m->L; ++l) wmax_params = std::max(wmax_params, (size_t)m->fin[l] * m->fout[l]);
+        // also holds the bias-gradient partials [kColChunks][fan_out]
+        const size_t wp = std::max(wmax_params * m->max_splits, (size_t)kColChunks * (size_t)std::max(m->H, m->n_out));
+        if ((r = m_alloc(m, &m->wpart, wp))) return r;
         if ((r = m_alloc(m, &m->loss_part, 1024))) return r;
         MCU(cudaStreamSynchronize(m->stream));
         return DEABM_OK;
@@ -501,11 +542,17 @@ static int mlp_backward_dev(deabm_mlp *m, const float *y, int batch, float *loss
         gw.M = fi;
         gw.N = fo;
         gw.K = batch;
-        gw.outf = m->gW[l];
         gw.ldo = fo;
         gw.epi = EPI_WGRAD;
-        if ((r = gemm(s, gw))) return r;
-        colsum_kernel<<<(fo + 127) / 128, 128, 0, s>>>(dz, batch, fo, m->gb[l]);
+        const int splits = std::max(1, std::min(m->max_splits, batch / 512));
+        gw.outf = splits > 1 ? m->wpart : m->gW[l];
+        if ((r = gemm(s, gw, splits))) return r;
+        if (splits > 1) {
+            splitk_reduce_kernel<<<256, 256, 0, s>>>(m->wpart, splits, (long)fi * fo, m->gW[l]);
+            MCU(cudaGetLastError());
+        }
+        colsum_partial_kernel<<<dim3((fo + 31) / 32, kColChunks), 256, 0, s>>>(dz, batch, fo, m->wpart);
+        colsum_final_kernel<<<(fo + 127) / 128, 128, 0, s>>>(m->wpart, fo, m->gb[l]);
         MCU(cudaGetLastError());
         if (l > 0) {
             // dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})

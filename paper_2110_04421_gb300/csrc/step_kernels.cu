@@ -60,10 +60,14 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     bool inf_now = false;
     uint32_t inf_y = 0;
     float p = 0.0f;
-    if (a.st == DEABM_S || a.qd > 0u || lam_out != nullptr) {
+    // the draw is needed by a susceptible agent with lambda > 0 (p = 0 never infects)
+    // and by a quarantined agent (its dropout word); skipping it elsewhere lets
+    // whole warps skip the Philox rounds
+    const float lam_dt = __fmul_rn(lam, P.dt);
+    if ((a.st == DEABM_S && lam_dt > 0.0f) || a.qd > 0u || lam_out != nullptr) {
         const uint4 w = draw(key, jo, day, kStreamInf);
         inf_y = w.y;
-        const bool hit = infection_decision(__fmul_rn(lam, P.dt), unit_float(w.x), &p);
+        const bool hit = infection_decision(lam_dt, unit_float(w.x), &p);
         inf_now = (a.st == DEABM_S) && hit;
     }
     const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
@@ -85,29 +89,47 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
 }
 
 // block-level aggregation of the day's counters; every thread of the block calls it
+#ifndef DEABM_HIST_MATCH
+#define DEABM_HIST_MATCH 0  // 1: warp-aggregated (match.any) stage counts; 0: one shared atomic per agent
+#endif
 __device__ __forceinline__ void count_day(bool active, int st, bool infected, uint32_t k, int *s_hist, int *s_new,
                                           unsigned long long *s_msgs)
 {
     const unsigned full = 0xFFFFFFFFu;
-    const unsigned act = __ballot_sync(full, active);
     const int lane = threadIdx.x & 31;
+#if DEABM_HIST_MATCH
+    const unsigned act = __ballot_sync(full, active);
     if (active) {
         const unsigned m = __match_any_sync(act, st);
         if (lane == __ffs(m) - 1) atomicAdd(&s_hist[st], __popc(m));
     }
+#else
+    if (active) atomicAdd(&s_hist[st], 1);
+#endif
     const unsigned nb = __ballot_sync(full, infected);
     if (lane == 0 && nb) atomicAdd(s_new, __popc(nb));
     const unsigned ks = __reduce_add_sync(full, active ? k : 0u);
     if (lane == 0 && ks) atomicAdd(s_msgs, (unsigned long long)ks);
 }
 
+#ifndef DEABM_PLAIN_BLOCK
+#define DEABM_PLAIN_BLOCK 128
+#endif
 template <bool KEEP>
-__global__ void __launch_bounds__(256, DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
+__global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                          Counters C, float *lam_out, float *p_out)
 {
     __shared__ int s_hist[DEABM_N_STAGE];
     __shared__ int s_new;
     __shared__ unsigned long long s_msgs;
+#ifndef DEABM_REP_SMEM
+#define DEABM_REP_SMEM 0  // 1: stage the replicate parameters in shared memory once per block
+#endif
+#if DEABM_REP_SMEM
+    __shared__ Rep s_rep;
+    for (uint32_t q = threadIdx.x; q < sizeof(Rep) / 4; q += blockDim.x)
+        ((uint32_t *)&s_rep)[q] = ((const uint32_t *)P.rep)[q];
+#endif
     if (threadIdx.x < DEABM_N_STAGE) s_hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; }
     __syncthreads();
@@ -117,7 +139,11 @@ __global__ void __launch_bounds__(256, DEABM_PLAIN_MINB) step_plain_kernel(const
     bool infected = false;
     uint32_t k = 0;
     if (active) {
+#if DEABM_REP_SMEM
+        const Rep &rp = s_rep;
+#else
         const Rep &rp = P.rep[0];
+#endif
         agent_day(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
     }
     count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
@@ -242,9 +268,9 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
                         float *lam_out, float *p_out, cudaStream_t stream)
 {
     if (P.n_rep == 1) {
-        const dim3 grid((P.n + 255u) / 256u);
-        if (lam_out) step_plain_kernel<true><<<grid, 256, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
-        else step_plain_kernel<false><<<grid, 256, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        const dim3 grid((P.n + DEABM_PLAIN_BLOCK - 1u) / DEABM_PLAIN_BLOCK);
+        if (lam_out) step_plain_kernel<true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+        else step_plain_kernel<false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
     } else {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
         const dim3 block(32, 8);
