@@ -264,6 +264,153 @@ cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t 
     return cudaGetLastError();
 }
 
+// Batched panel, four replicates per thread (n_rep a multiple of 4): a warp owns
+// one agent row and 128 consecutive replicates, so each in-edge costs one
+// broadcast column load and one 16-byte gather per lane, and the row's random
+// contacts are generated once for 128 replicates.  Each replicate's sums are
+// still left to right in CSR order, so results equal the one-replicate kernels.
+constexpr uint32_t kRepPerThread = 4;
+#ifndef DEABM_B4_UNROLL
+#define DEABM_B4_UNROLL 2   // unroll factor of the per-replicate state update
+#endif
+constexpr int kB4Unroll = DEABM_B4_UNROLL;
+
+__device__ __forceinline__ void add4(float4 &h, const float4 v)
+{
+    h.x = __fadd_rn(h.x, v.x);
+    h.y = __fadd_rn(h.y, v.y);
+    h.z = __fadd_rn(h.z, v.z);
+    h.w = __fadd_rn(h.w, v.w);
+}
+
+template <bool KEEP>
+__global__ void __launch_bounds__(256) step_batch4_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
+                                                          Counters C, float *lam_out, float *p_out)
+{
+    __shared__ int s_cnt[DEABM_N_STAGE + 1][32 * kRepPerThread];
+    __shared__ unsigned long long s_msgs;
+    const uint32_t lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32u + lane;
+    const uint32_t j = blockIdx.x * 8u + wy;
+    const uint32_t B = P.n_rep;
+    const uint32_t b0 = blockIdx.y * (32u * kRepPerThread) + lane * kRepPerThread;
+    for (uint32_t q = tid; q < (DEABM_N_STAGE + 1) * 32u * kRepPerThread; q += 256u) (&s_cnt[0][0])[q] = 0;
+    if (tid == 0) s_msgs = 0ull;
+    __syncthreads();
+    uint32_t k = 0;
+    if (j < P.n && b0 < B) {
+        const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
+        const int age = __ldg(P.age + j);
+        // static networks: per replicate sums in CSR order
+        float s4[kRepPerThread] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (uint32_t net = 0; net < P.n_nets; ++net) {
+            float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const uint32_t e1 = __ldg(P.row_ptr[net] + j + 1);
+            for (uint32_t e = __ldg(P.row_ptr[net] + j); e < e1; ++e) {
+                const uint32_t c = __ldg(P.col[net] + e);
+                add4(h, __ldg((const float4 *)(I.cur + (size_t)c * B + b0)));
+            }
+            const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+            for (uint32_t v = 0; v < kRepPerThread; ++v) {
+                const float term = __fmul_rn(P.rep[b0 + v].B_net[net], hv[v]);
+                s4[v] = net == 0 ? term : __fadd_rn(s4[v], term);
+            }
+        }
+        if (P.rand_on) {
+            const uint2 nk = seed_key(P.net_seed);
+            uint4 w = draw(nk, jo, day, kStreamRnet, 0u);
+            while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
+            float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const uint64_t nm1 = (uint64_t)(P.n - 1u);
+            for (uint32_t e = 0; e < k; ++e) {
+                const uint32_t idx = e + 1u;
+                if ((idx & 3u) == 0u) w = draw(nk, jo, day, kStreamRnet, idx >> 2);
+                const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+                uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
+                v += (v >= jo) ? 1u : 0u;
+                add4(r, __ldg((const float4 *)(I.rand_cur + (size_t)v * B + b0)));
+            }
+            const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (uint32_t v = 0; v < kRepPerThread; ++v) {
+                const float term = __fmul_rn(P.rep[b0 + v].B_rand, rv[v]);
+                s4[v] = P.n_nets == 0 ? term : __fadd_rn(s4[v], term);
+            }
+        }
+        // state of the four replicates (vector loads)
+        const size_t i0 = (size_t)j * B + b0;
+        const char4 st4 = *(const char4 *)(S.stage + i0);
+        const short4 tm4 = *(const short4 *)(S.timer + i0);
+        const short4 ti4 = *(const short4 *)(S.tinf + i0);
+        const uchar4 fl4 = *(const uchar4 *)(S.flags + i0);
+        const uchar4 qt4 = *(const uchar4 *)(S.qt + i0);
+        const int8_t st_in[4] = {st4.x, st4.y, st4.z, st4.w};
+        const int16_t tm_in[4] = {tm4.x, tm4.y, tm4.z, tm4.w}, ti_in[4] = {ti4.x, ti4.y, ti4.z, ti4.w};
+        const uint8_t fl_in[4] = {fl4.x, fl4.y, fl4.z, fl4.w}, qt_in[4] = {qt4.x, qt4.y, qt4.z, qt4.w};
+        int8_t st_out[4];
+        int16_t tm_out[4], ti_out[4];
+        uint8_t fl_out[4], qt_out[4];
+        float inf_out[4];
+        const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
+#pragma unroll kB4Unroll
+        for (uint32_t v = 0; v < kRepPerThread; ++v) {
+            const Rep &rp = P.rep[b0 + v];
+            const float lam = __fmul_rn(__fmul_rn(rp.cR, rp.S_age[age]), s4[v]);
+            AgentState a;
+            a.st = st_in[v];
+            a.tm = tm_in[v];
+            a.ti = ti_in[v];
+            a.fl = fl_in[v];
+            a.qd = qt_in[v] & 0x0Fu;
+            a.cd = (qt_in[v] >> 4) & 0x07u;
+            const uint2 key = seed_key(rp.seed);
+            bool inf_now = false;
+            uint32_t inf_y = 0;
+            float p = 0.0f;
+            const float lam_dt = __fmul_rn(lam, P.dt);
+            if ((a.st == DEABM_S && lam_dt > 0.0f) || a.qd > 0u || KEEP) {
+                const uint4 w = draw(key, jo, day, kStreamInf);
+                inf_y = w.y;
+                const bool hit = infection_decision(lam_dt, unit_float(w.x), &p);
+                inf_now = (a.st == DEABM_S) && hit;
+            }
+            advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
+            st_out[v] = (int8_t)a.st;
+            tm_out[v] = (int16_t)a.tm;
+            ti_out[v] = (int16_t)a.ti;
+            fl_out[v] = (uint8_t)a.fl;
+            qt_out[v] = (uint8_t)((a.qd & 0x0Fu) | ((a.cd & 0x07u) << 4));
+            inf_out[v] = emitted(P.tab, P.inf_len, a.st, a.ti, a.qd);
+            if (KEEP) {
+                lam_out[i0 + v] = lam;
+                p_out[i0 + v] = p;
+            }
+            atomicAdd(&s_cnt[a.st][lane * kRepPerThread + v], 1);
+            if (inf_now) atomicAdd(&s_cnt[DEABM_N_STAGE][lane * kRepPerThread + v], 1);
+        }
+        *(char4 *)(S.stage + i0) = make_char4(st_out[0], st_out[1], st_out[2], st_out[3]);
+        *(short4 *)(S.timer + i0) = make_short4(tm_out[0], tm_out[1], tm_out[2], tm_out[3]);
+        *(short4 *)(S.tinf + i0) = make_short4(ti_out[0], ti_out[1], ti_out[2], ti_out[3]);
+        *(uchar4 *)(S.flags + i0) = make_uchar4(fl_out[0], fl_out[1], fl_out[2], fl_out[3]);
+        *(uchar4 *)(S.qt + i0) = make_uchar4(qt_out[0], qt_out[1], qt_out[2], qt_out[3]);
+        const float4 iv = make_float4(inf_out[0], inf_out[1], inf_out[2], inf_out[3]);
+        *(float4 *)(I.next + i0) = iv;
+        if (I.rand_next) *(float4 *)(I.rand_next + (size_t)jo * B + b0) = iv;
+    }
+    if (lane == 0 && blockIdx.y == 0 && j < P.n && k) atomicAdd(&s_msgs, (unsigned long long)k);
+    __syncthreads();
+    for (uint32_t q = tid; q < (DEABM_N_STAGE + 1) * 32u * kRepPerThread; q += 256u) {
+        const uint32_t s = q / (32u * kRepPerThread), l = q % (32u * kRepPerThread);
+        const uint32_t bb = blockIdx.y * (32u * kRepPerThread) + l;
+        const int v = s_cnt[s][l];
+        if (v && bb < B) {
+            if (s < DEABM_N_STAGE) atomicAdd(&C.hist[((size_t)day * B + bb) * DEABM_N_STAGE + s], v);
+            else atomicAdd(&C.new_inf[(size_t)day * B + bb], v);
+        }
+    }
+    if (tid == 0 && s_msgs) atomicAdd(&C.msgs[day], s_msgs);
+}
+
 cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, const StateRef &S, const Counters &C,
                         float *lam_out, float *p_out, cudaStream_t stream)
 {
@@ -271,6 +418,11 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
         const dim3 grid((P.n + DEABM_PLAIN_BLOCK - 1u) / DEABM_PLAIN_BLOCK);
         if (lam_out) step_plain_kernel<true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
         else step_plain_kernel<false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+    } else if (P.n_rep % kRepPerThread == 0) {
+        const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 32u * kRepPerThread - 1u) / (32u * kRepPerThread));
+        const dim3 block(32, 8);
+        if (lam_out) step_batch4_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+        else step_batch4_kernel<false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
     } else {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
         const dim3 block(32, 8);

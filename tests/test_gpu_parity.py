@@ -106,8 +106,11 @@ def test_full_size_plain_workload_first_days():
     assert rep["max_rel_lambda64"] <= 1e-5
 
 
-def test_batched_columns_equal_plain_runs_and_oracle():
-    n, B, T = 3001, 37, 40
+@pytest.mark.parametrize("B", [37, 36, 132])
+def test_batched_columns_equal_plain_runs_and_oracle(B):
+    """B = 37 runs the one-replicate-per-thread panel kernel; B = 36 and 132 (a
+    partly filled second panel of 128) the four-replicates-per-thread kernel."""
+    n, T = 3001, 40
     pop = W.population(n, 8, 30)
     base = W.params_with(vax_on=1, vax_start=5, vax_rate=0.01, test_on=1, quar_on=1, net_seed=5)
     rp, seeds = W.batch_params(B, 1)
@@ -118,7 +121,7 @@ def test_batched_columns_equal_plain_runs_and_oracle():
     ni_b, h_b = gb.run(T)
     sb = gb.state()
     gb.close()
-    for r in (0, 1, 17, 31, 32, 36):
+    for r in sorted({0, 1, 17, 31, 32, B - 4, B - 1}):
         pr = dict(base, R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
                   S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r]))
         g = gpu_sim(pop, pr, keep_lambda=False, max_steps=T)
@@ -128,7 +131,7 @@ def test_batched_columns_equal_plain_runs_and_oracle():
         assert np.array_equal(ni[:, 0], ni_b[:, r]) and np.array_equal(h[:, 0], h_b[:, r])
         for k in ("stage", "timer", "tinf", "flags", "qt"):
             assert np.array_equal(s[k], sb[k][:, r]), (r, k)
-        if r in (0, 36):
+        if r in (0, B - 1):
             o = oracle_sim(pop, pr)
             ni_o, h_o, _ = o.run(T)
             assert np.array_equal(ni_o, ni_b[:, r]) and np.array_equal(h_o, h_b[:, r])
