@@ -332,14 +332,23 @@ int deabm_mlp_param_count(const deabm_mlp *mlp, uint64_t *count);
 int deabm_mlp_set_params(deabm_mlp *mlp, const float *params);
 /* Copy the FP32 parameters and / or the last computed gradients (host; either may be NULL). */
 int deabm_mlp_get_params(deabm_mlp *mlp, float *params, float *grads);
-/* y = MLP(x) for `batch` rows (device pointers).  Asynchronous. */
+/* y = MLP(x) for `batch` rows (device pointers).  Asynchronous.  When the shape
+ * allows (n_in <= 64, hidden a multiple of 64 up to 256, n_out <= 256) this is one
+ * fused kernel on the tcgen05 tensor cores with the accumulator in TMEM;
+ * otherwise, or after deabm_mlp_use_tcgen05(mlp, 0, ...), the per-layer
+ * mma.sync GEMMs run.  A bounded wait that gave up inside the fused kernel is
+ * reported by the next deabm_mlp_sync as DEABM_ETIMEOUT. */
 int deabm_mlp_forward(deabm_mlp *mlp, const float *x, uint32_t batch, float *y);
+/* Choose the forward path (1: fused tcgen05 when eligible, 0: per-layer GEMMs);
+ * *available (may be NULL) tells whether the fused path applies to this shape. */
+int deabm_mlp_use_tcgen05(deabm_mlp *mlp, int enable, int *available);
 /* Loss (1/(batch n_out)) sum (MLP(x) - y)^2 and its gradients (kept in the
  * context, read with deabm_mlp_get_params); loss -> host float, may be NULL. */
 int deabm_mlp_grad(deabm_mlp *mlp, const float *x, const float *y, uint32_t batch, float *loss);
 /* deabm_mlp_grad, then one Adam step (beta 0.9 / 0.999, eps 1e-8) with rate lr.
  * loss (host, may be NULL: no synchronisation) is the loss before the step. */
 int deabm_mlp_train_step(deabm_mlp *mlp, const float *x, const float *y, uint32_t batch, float lr, float *loss);
+/* Wait for the MLP's queued work; DEABM_ETIMEOUT if a bounded device wait gave up. */
 int deabm_mlp_sync(deabm_mlp *mlp);
 const char *deabm_mlp_last_error(void);
 /* NULL-safe. */

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "deabm.h"
+#include "mlp_tc.h"
 
 namespace mlpk {
 
@@ -295,6 +296,11 @@ struct deabm_mlp {
     __nv_bfloat16 *dzb = nullptr, *dzb2 = nullptr;
     double *loss_part = nullptr;
     int step = 0;
+    // fused tcgen05 forward (inference): eligible shapes, K-major BF16 weight copies
+    bool tc_ok = false, tc_on = true, wt_dirty = true;
+    std::vector<__nv_bfloat16 *> Wt;
+    std::vector<int> tcK, tcN;
+    int *tc_err = nullptr;
 };
 
 static thread_local std::string g_mlp_err;
@@ -419,6 +425,20 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
         const size_t wp = std::max(wmax_params * m->max_splits, (size_t)kColChunks * (size_t)std::max(m->H, m->n_out));
         if ((r = m_alloc(m, &m->wpart, wp))) return r;
         if ((r = m_alloc(m, &m->loss_part, 1024))) return r;
+        m->tc_ok = m->n_in <= 64 && m->H % 64 == 0 && m->H <= 256 && m->n_out <= 256 && m->L <= kMaxTcLayers;
+        if (m->tc_ok) {
+            for (int l = 0; l < m->L; ++l) {
+                const int kp = l == 0 ? 64 : m->H;
+                const int np = l < m->L - 1 ? m->H : (m->n_out + 63) / 64 * 64;
+                __nv_bfloat16 *w;
+                if ((r = m_alloc(m, &w, (size_t)kp * np))) return r;
+                m->Wt.push_back(w);
+                m->tcK.push_back(kp);
+                m->tcN.push_back(np);
+            }
+            if ((r = m_alloc(m, &m->tc_err, 1))) return r;
+            MCU(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
+        }
         MCU(cudaStreamSynchronize(m->stream));
         return DEABM_OK;
     }();
@@ -461,6 +481,7 @@ extern "C" int deabm_mlp_set_params(deabm_mlp *m, const float *params)
         MCU(cudaMemsetAsync(m->vb[l], 0, 4ull * m->fout[l], m->stream));
     }
     m->step = 0;
+    m->wt_dirty = true;
     MCU(cudaGetLastError());
     MCU(cudaStreamSynchronize(m->stream));
     return DEABM_OK;
@@ -592,7 +613,36 @@ extern "C" int deabm_mlp_forward(deabm_mlp *m, const float *x, uint32_t batch, f
     if (!m || !x || !y) return mlp_fail(DEABM_EINVAL, "NULL argument");
     if (batch == 0) return DEABM_OK;
     if ((int)batch > m->max_batch) return mlp_fail(DEABM_EINVAL, "batch %u > max_batch %d", batch, m->max_batch);
-    return mlp_forward_dev(m, x, (int)batch, y, false);
+    if (!(m->tc_ok && m->tc_on)) return mlp_forward_dev(m, x, (int)batch, y, false);
+    if (m->wt_dirty) {
+        for (int l = 0; l < m->L; ++l)
+            MCU(mlptc_prepare_weights(m->W[l], m->fin[l], m->fout[l], m->tcK[l], m->tcN[l], m->Wt[l], m->stream));
+        m->wt_dirty = false;
+    }
+    FusedArgs g{};
+    g.x = x;
+    g.y = y;
+    g.M = (int)batch;
+    g.n_in = m->n_in;
+    g.n_out = m->n_out;
+    g.L = m->L;
+    for (int l = 0; l < m->L; ++l) {
+        g.Wt[l] = m->Wt[l];
+        g.bias[l] = m->b[l];
+        g.K[l] = m->tcK[l];
+        g.N[l] = m->tcN[l];
+    }
+    g.err = m->tc_err;
+    MCU(mlptc_forward(g, m->stream));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_use_tcgen05(deabm_mlp *m, int enable, int *available)
+{
+    if (!m) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    m->tc_on = enable != 0;
+    if (available) *available = m->tc_ok ? 1 : 0;
+    return DEABM_OK;
 }
 
 extern "C" int deabm_mlp_grad(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float *loss)
@@ -609,6 +659,7 @@ extern "C" int deabm_mlp_train_step(deabm_mlp *m, const float *x, const float *y
     int r;
     if ((r = deabm_mlp_grad(m, x, y, batch, nullptr))) return r;
     m->step += 1;
+    m->wt_dirty = true;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     for (int l = 0; l < m->L; ++l) {
@@ -630,6 +681,14 @@ extern "C" int deabm_mlp_sync(deabm_mlp *m)
 {
     if (!m) return mlp_fail(DEABM_EINVAL, "NULL argument");
     MCU(cudaStreamSynchronize(m->stream));
+    if (m->tc_err) {
+        int err = 0;
+        MCU(cudaMemcpy(&err, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            MCU(cudaMemset(m->tc_err, 0, sizeof(int)));
+            return mlp_fail(DEABM_ETIMEOUT, "a bounded wait of the tensor-core forward gave up");
+        }
+    }
     return DEABM_OK;
 }
 

@@ -24,7 +24,8 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_relaxed_last_error", "deabm_relaxed_destroy", "deabm_reset", "deabm_mlp_create",
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
-           "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune")
+           "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
+           "deabm_mlp_use_tcgen05")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -115,6 +116,8 @@ def lib():
         L.deabm_mlp_grad.argtypes = [vp, vp, vp, u32, vp]
         L.deabm_mlp_train_step.argtypes = [vp, vp, vp, u32, C.c_float, vp]
         L.deabm_mlp_sync.argtypes = [vp]
+        L.deabm_mlp_use_tcgen05.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.deabm_mlp_use_tcgen05.restype = C.c_int
         L.deabm_mlp_last_error.argtypes = []
         L.deabm_mlp_last_error.restype = C.c_char_p
         L.deabm_mlp_destroy.argtypes = [vp]
@@ -521,6 +524,13 @@ class MLP:
         cnt = C.c_uint64()
         _mlp_check(L.deabm_mlp_param_count(ctx, C.byref(cnt)))
         self.n_params = cnt.value
+
+    def use_tcgen05(self, enable: bool = True) -> bool:
+        """Select the fused tcgen05 forward (True) or the per-layer mma.sync GEMMs;
+        returns whether the fused path applies to this shape."""
+        avail = C.c_int()
+        _mlp_check(lib().deabm_mlp_use_tcgen05(self.ctx, 1 if enable else 0, C.byref(avail)))
+        return bool(avail.value)
 
     def set_params(self, params):
         p = np.ascontiguousarray(params, dtype=np.float32)

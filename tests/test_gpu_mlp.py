@@ -42,15 +42,20 @@ def layer_slices(sizes):
     return out
 
 
+@pytest.mark.parametrize("tcgen05", [True, False])
 @pytest.mark.parametrize("batch", [1, 131, 300])
-def test_forward_matches_bf16_oracle(batch):
+def test_forward_matches_bf16_oracle(batch, tcgen05):
+    """Both forward paths: the fused tcgen05 kernel (TMEM accumulator) and the
+    per-layer mma.sync GEMMs."""
     import torch
     from paper_2110_04421_gb300.deabm import MLP
     p = M.init_params(SIZES, 7)
     x, _ = make(batch, 1)
     m = MLP(max_batch=512)
+    assert m.use_tcgen05(tcgen05)
     m.set_params(p)
     y = m.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    m.sync()
     m.close()
     ref, _, _ = M.forward(p, SIZES, x)
     assert np.max(np.abs(y - ref)) <= 1e-2 * np.max(np.abs(ref)), np.max(np.abs(y - ref))
