@@ -427,14 +427,19 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
         if ((r = m_alloc(m, &m->loss_part, 1024))) return r;
         m->tc_ok = m->n_in <= 64 && m->H % 64 == 0 && m->H <= 256 && m->n_out <= 256 && m->L <= kMaxTcLayers;
         if (m->tc_ok) {
+            size_t total = 0;
             for (int l = 0; l < m->L; ++l) {
                 const int kp = l == 0 ? 64 : m->H;
                 const int np = l < m->L - 1 ? m->H : (m->n_out + 63) / 64 * 64;
-                __nv_bfloat16 *w;
-                if ((r = m_alloc(m, &w, (size_t)kp * np))) return r;
-                m->Wt.push_back(w);
                 m->tcK.push_back(kp);
                 m->tcN.push_back(np);
+                total += (size_t)kp * np;
+            }
+            __nv_bfloat16 *img;
+            if ((r = m_alloc(m, &img, total))) return r;
+            for (int l = 0, off = 0; l < m->L; ++l) {
+                m->Wt.push_back(img + off);  // this layer's chunk images
+                off += m->tcK[l] * m->tcN[l];
             }
             if ((r = m_alloc(m, &m->tc_err, 1))) return r;
             MCU(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
@@ -626,8 +631,8 @@ extern "C" int deabm_mlp_forward(deabm_mlp *m, const float *x, uint32_t batch, f
     g.n_in = m->n_in;
     g.n_out = m->n_out;
     g.L = m->L;
+    g.wimg = m->Wt[0];
     for (int l = 0; l < m->L; ++l) {
-        g.Wt[l] = m->Wt[l];
         g.bias[l] = m->b[l];
         g.K[l] = m->tcK[l];
         g.N[l] = m->tcN[l];

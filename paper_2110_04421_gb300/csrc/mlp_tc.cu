@@ -5,11 +5,13 @@
 //   * the layer input a_{l-1} [128 x K] (BF16) lives in shared memory in the
 //     K-major 128-byte-swizzled layout the tensor core reads (8-row atoms of
 //     1024 B, 16-byte chunk c of row r stored at chunk c ^ (r % 8));
-//   * the layer's weights W_l^T [N x K] (BF16, K-major) stream through two
-//     32 KB shared buffers, 64 K-columns at a time;
+//   * the layer's weights W_l^T [N x K] (BF16, K-major) arrive 64 K-columns at a
+//     time in a 32 KB shared buffer, each chunk one cp.async.bulk copy of an
+//     image prepared in the swizzled layout (mbarrier transaction count);
 //   * one thread issues tcgen05.mma (M = 128, N <= 256, K = 16, BF16 inputs,
 //     FP32 accumulate) into a TMEM accumulator of 128 lanes x 256 columns and
-//     commits each 64-column chunk to an mbarrier;
+//     commits each chunk to an mbarrier; two CTAs share an SM so one's epilogue
+//     overlaps the other's MMAs;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w: TMEM lanes
 //     32 (w % 4) .. +31, half w / 4 of the columns), adds the bias, applies the
 //     erf-GELU and writes the BF16 activations back to shared memory as the next
@@ -107,17 +109,30 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *(const uint32_t *)&h;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc_kernel(const FusedArgs g)
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst_smem),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// Two CTAs per SM (97 KB of shared memory, 256 TMEM columns each): while one
+// runs its GELU epilogue on the CUDA cores the other's MMAs use the tensor core.
+// Weight chunks arrive by one bulk copy each, already in the swizzled layout;
+// the next layer's first chunk is copied while the epilogue runs.
+__global__ void __launch_bounds__(kThreads, 2) mlp_forward_tc_kernel(const FusedArgs g)
 {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar_w, mbar_mma;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023u) & ~(uintptr_t)1023u);
-    unsigned char *sA = smem;                          // kMaxKChunks x 16 KB
-    unsigned char *sB = smem + kMaxKChunks * kAChunkBytes;  // 2 x 32 KB
+    unsigned char *sA = smem;                               // kMaxKChunks x 16 KB
+    unsigned char *sB = smem + kMaxKChunks * kAChunkBytes;  // one 32 KB weight chunk
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t row0 = blockIdx.x * kRows;
+    const uint32_t mw = smem_u32(&mbar_w), mm = smem_u32(&mbar_mma), sB_addr = smem_u32(sB);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
@@ -125,10 +140,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc_kernel(const Fused
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mw));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mm));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
+        bulk_load(sB_addr, g.wimg, (uint32_t)g.N[0] * 128u, mw);  // first chunk of layer 0
     }
     // the input tile: x rows (FP32, n_in columns) -> BF16, zero-padded to 64 columns
     for (uint32_t q = tid; q < kRows * 8u; q += kThreads) {
@@ -148,41 +164,31 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc_kernel(const Fused
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    uint32_t gchunk = 0;  // chunks issued so far (alternating buffers)
     bool ok = true;
+    uint32_t gchunk = 0;  // weight chunks consumed so far
+    size_t woff = 0;      // byte offset of the next chunk image
 
     for (int l = 0; l < g.L && ok; ++l) {
-        const uint32_t K = (uint32_t)g.K[l], N = (uint32_t)g.N[l];
-        const __nv_bfloat16 *Wt = g.Wt[l];
-        const uint32_t idesc = idesc_bf16(kRows, N);
-        for (uint32_t c = 0; c < K / 64u; ++c, ++gchunk) {
-            const uint32_t buf = gchunk & 1u;
-            if (gchunk >= 2) {  // the MMAs that read this buffer two chunks ago are done
-                if (tid == 0 && !mbar_wait(smem_u32(&mbar[buf]), ((gchunk - 2u) >> 1) & 1u)) s_abort = 1;
-                __syncthreads();
-                if (s_abort) { ok = false; break; }
-            }
-            unsigned char *dstB = sB + buf * kBBufBytes;
-            for (uint32_t q = tid; q < N * 8u; q += kThreads) {
-                const uint32_t n = q >> 3, cc = q & 7u;
-                const uint4 w = __ldg((const uint4 *)(Wt + (size_t)n * K + c * 64u + cc * 8u));
-                *(uint4 *)(dstB + sw128(n, cc)) = w;
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
+        const uint32_t K = (uint32_t)g.K[l], N = (uint32_t)g.N[l], nch = K / 64u;
+        if (tid == 0) {
+            const uint32_t idesc = idesc_bf16(kRows, N);
+            const uint32_t a_base0 = smem_u32(sA);
+            for (uint32_t c = 0; c < nch; ++c, ++gchunk) {
+                if (!mbar_wait(mw, gchunk & 1u)) { s_abort = 1; break; }  // chunk in shared memory
                 tc_fence_after();
-                const uint32_t a_base = smem_u32(sA + c * kAChunkBytes), b_base = smem_u32(dstB);
 #pragma unroll
                 for (uint32_t kk = 0; kk < 4; ++kk)
-                    mma_bf16(tmem, sw128_desc(a_base + kk * 32u), sw128_desc(b_base + kk * 32u), idesc,
-                             (c > 0 || kk > 0) ? 1u : 0u);
-                mma_commit(smem_u32(&mbar[buf]));
+                    mma_bf16(tmem, sw128_desc(a_base0 + c * kAChunkBytes + kk * 32u), sw128_desc(sB_addr + kk * 32u),
+                             idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(mm);
+                if (!mbar_wait(mm, gchunk & 1u)) { s_abort = 1; break; }  // buffer free again
+                woff += (size_t)N * 128u;
+                // next chunk: this layer's, or the first of the next layer (overlaps the epilogue)
+                if (c + 1 < nch) bulk_load(sB_addr, (const unsigned char *)g.wimg + woff, N * 128u, mw);
+                else if (l + 1 < g.L)
+                    bulk_load(sB_addr, (const unsigned char *)g.wimg + woff, (uint32_t)g.N[l + 1] * 128u, mw);
             }
         }
-        if (!ok) break;
-        // all MMAs of this layer are done once its last commit lands
-        if (tid == 0 && !mbar_wait(smem_u32(&mbar[(gchunk - 1u) & 1u]), ((gchunk - 1u) >> 1) & 1u)) s_abort = 1;
         __syncthreads();
         if (s_abort) { ok = false; break; }
         tc_fence_after();
@@ -215,7 +221,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc_kernel(const Fused
         __syncthreads();
         tc_fence_after();
     }
-    if (!ok && tid == 0) atomicExch(g.err, 1);
+    if (!ok && tid == 0) {
+        atomicExch(g.err, 1);
+        (void)mbar_wait(mw, gchunk & 1u);  // a copy may still be in flight: give it a bounded chance to land
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -224,29 +233,32 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc_kernel(const Fused
     }
 }
 
-// W [fan_in x fan_out] FP32 (row-major) -> W^T [n_pad x k_pad] BF16, zero padding
-__global__ void transpose_to_bf16_kernel(const float *W, int fin, int fout, int k_pad, int n_pad, __nv_bfloat16 *Wt)
+// weight images: for every layer l and 64-column chunk c, W_l^T[0:N_l, 64c:64c+64] in
+// the K-major 128-byte-swizzled layout (one contiguous N_l x 128 B block each)
+__global__ void weight_image_kernel(const float *W, int fin, int fout, int k_pad, int n_pad, __nv_bfloat16 *img)
 {
     const long total = (long)n_pad * k_pad;
     for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long)gridDim.x * blockDim.x) {
         const int n = (int)(q / k_pad), k = (int)(q % k_pad);
-        Wt[q] = __float2bfloat16(n < fout && k < fin ? W[(long)k * fout + n] : 0.0f);
+        const int c = k >> 6, cc = (k & 63) >> 3, e = k & 7;
+        const size_t off = (size_t)c * n_pad * 128u + sw128((uint32_t)n, (uint32_t)cc) + (size_t)e * 2u;
+        *(__nv_bfloat16 *)((unsigned char *)img + off) = __float2bfloat16(n < fout && k < fin ? W[(long)k * fout + n] : 0.0f);
     }
 }
 
 }  // namespace mlptc
 
-cudaError_t mlptc_prepare_weights(const float *W, int fin, int fout, int k_pad, int n_pad, __nv_bfloat16 *Wt,
+cudaError_t mlptc_prepare_weights(const float *W, int fin, int fout, int k_pad, int n_pad, __nv_bfloat16 *img,
                                   cudaStream_t s)
 {
-    mlptc::transpose_to_bf16_kernel<<<256, 256, 0, s>>>(W, fin, fout, k_pad, n_pad, Wt);
+    mlptc::weight_image_kernel<<<256, 256, 0, s>>>(W, fin, fout, k_pad, n_pad, img);
     return cudaGetLastError();
 }
 
 cudaError_t mlptc_forward(const FusedArgs &g, cudaStream_t s)
 {
     static bool attr_set = false;
-    const size_t smem = kMaxKChunks * mlptc::kAChunkBytes + 2 * mlptc::kBBufBytes + 1024;
+    const size_t smem = kMaxKChunks * mlptc::kAChunkBytes + mlptc::kBBufBytes + 1024;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(mlptc::mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
