@@ -78,6 +78,7 @@ class _Model(C.Structure):
         ("dose2_delay", C.c_uint32),
         ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
+        ("vax_strategy", C.c_uint32), ("elderly_bin", C.c_uint32),
     ]
 
 
@@ -120,12 +121,12 @@ def lib():
             L.or_random_contacts.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, vp]
             L.or_random_contacts.restype = C.c_uint32
             L.or_vax_days.argtypes = [C.c_uint32, vp, C.c_uint32, C.c_double, vp]
-            L.or_step.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, vp, vp, vp, vp, vp, C.POINTER(_Diag)]
+            L.or_step.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(_Diag)]
             L.or_step.restype = C.c_int
             L.or_seed_infections.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, vp, vp, vp]
             L.or_seed_infections.restype = C.c_int
             L.or_run.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, C.c_uint32,
-                                 vp, vp, vp, vp, vp, vp, vp, vp]
+                                 vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_run.restype = C.c_int
             L.rx_run.argtypes = [C.POINTER(_RxModel), vp, vp, C.c_uint32, C.c_uint32, vp, vp, vp, vp, vp, vp]
             L.rx_run.restype = C.c_int
@@ -220,6 +221,8 @@ class Model:
                      "vax_on", "vax_start", "vax_onset", "dose2_delay", "vax_rate", "vax_eff1", "vax_eff2",
                      "seed", "net_seed"):
             setattr(m, name, P[name])
+        m.vax_strategy = P.get("vax_strategy", 0)
+        m.elderly_bin = P.get("elderly_bin", 6)
         self.m = m
         self.params = P
 
@@ -232,7 +235,8 @@ class Model:
 
 
 class State:
-    """Per-agent state arrays (SoA): stage int8, timer int16, tinf int16, flags u8, qt u8."""
+    """Per-agent state arrays (SoA): stage int8, timer int16, tinf int16, flags u8, qt u8,
+    and the days of dose 1 / dose 2 under a priority strategy (int16, 0x7FFF = none)."""
 
     def __init__(self, n: int):
         self.stage = np.zeros(n, np.int8)
@@ -240,15 +244,18 @@ class State:
         self.tinf = np.zeros(n, np.int16)
         self.flags = np.zeros(n, np.uint8)
         self.qt = np.zeros(n, np.uint8)
+        self.vd1 = np.full(n, 0x7FFF, np.int16)
+        self.vd2 = np.full(n, 0x7FFF, np.int16)
 
     def copy(self):
         s = State(0)
-        for k in ("stage", "timer", "tinf", "flags", "qt"):
+        for k in ("stage", "timer", "tinf", "flags", "qt", "vd1", "vd2"):
             setattr(s, k, getattr(self, k).copy())
         return s
 
     def ptrs(self):
-        return [_ptr(self.stage), _ptr(self.timer), _ptr(self.tinf), _ptr(self.flags), _ptr(self.qt)]
+        return [_ptr(self.stage), _ptr(self.timer), _ptr(self.tinf), _ptr(self.flags), _ptr(self.qt),
+                _ptr(self.vd1), _ptr(self.vd2)]
 
 
 class Sim:

@@ -75,6 +75,8 @@ typedef struct {
     uint32_t vax_on, vax_start, vax_onset, dose2_delay;
     double vax_rate, vax_eff1, vax_eff2;
     uint64_t seed, net_seed;
+    uint32_t vax_strategy;  /* 0 static schedule; 1 standard, 2 delayed second dose, 3 delayed except elderly */
+    uint32_t elderly_bin;   /* first age bin counted as "65+" by strategy 3 */
 } or_model;
 
 /* ------------------------------------------------------------------------- */
@@ -332,6 +334,7 @@ static int check_model(const or_model *m)
     if (m->inf_len == 0 || m->inf_len > OR_MAX_INF_LEN || m->n_nets > OR_MAX_NETS) return -1;
     if (m->quar_days > 15 || m->test_hi > 7 || m->test_lo < 1 || m->test_lo > m->test_hi) return -1;
     if (m->rand_mean > 0.0f && m->n < 2) return -1;
+    if (m->vax_strategy > 3 || m->elderly_bin > 9) return -1;
     return 0;
 }
 
@@ -341,9 +344,62 @@ static void make_tables(const or_model *m, or_tables *tb)
     or_poisson_thresholds((double)m->rand_mean, tb->pois);
 }
 
+/* Daily dose selection of the priority strategies (Sec. 5, Table 1): a shared
+ * supply of floor(rate * N) doses a day goes to the eligible agents with the
+ * smallest (key, id); first-dose eligible = no dose yet, second-dose eligible =
+ * first dose at least dose2_delay days ago; agents in hospital, ICU or dead are
+ * not eligible.  Keys (age bin descending inside each group):
+ *   standard:            second doses, then first doses;
+ *   delayed second dose: first doses, then second doses;
+ *   delayed except 65+:  agents of the elderly bins by age with a first dose
+ *                        before a second dose of the same bin, then the others'
+ *                        first doses, then their second doses. */
+typedef struct { uint32_t key, id, type; } vcand;
+
+static int cmp_vcand(const void *a, const void *b)
+{
+    const vcand *x = (const vcand *)a, *y = (const vcand *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->id < y->id ? -1 : (x->id > y->id ? 1 : 0);
+}
+
+static uint32_t vax_key(uint32_t strategy, uint32_t elderly_bin, int age, uint32_t type)
+{
+    const uint32_t older = (uint32_t)(8 - age);
+    if (strategy == 1) return (type == 2 ? 0u : 1u) * 16u + older;
+    if (strategy == 2) return (type == 1 ? 0u : 1u) * 16u + older;
+    if ((uint32_t)age >= elderly_bin) return older * 2u + (type - 1u);
+    return (type == 1 ? 1u : 2u) * 64u + older * 2u;
+}
+
+static void select_doses(const or_model *m, const uint8_t *age, uint32_t t, const int8_t *stage, const uint8_t *flags,
+                         const int16_t *vd1, uint8_t *dose_today)
+{
+    const uint32_t n = m->n;
+    const uint32_t q = (uint32_t)floor(m->vax_rate * (double)n);
+    vcand *c = (vcand *)malloc(sizeof(vcand) * (n ? n : 1));
+    uint32_t k = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        dose_today[j] = 0;
+        const int st = stage[j];
+        if (st == ST_HOSP || st == ST_ICU || st == ST_DEAD) continue;
+        uint32_t type = 0;
+        if (!(flags[j] & FL_DOSE1)) type = 1;
+        else if (!(flags[j] & FL_DOSE2) && (int64_t)t - (int64_t)vd1[j] >= (int64_t)m->dose2_delay) type = 2;
+        if (!type) continue;
+        c[k].key = vax_key(m->vax_strategy, m->elderly_bin, age[j], type);
+        c[k].id = j;
+        c[k].type = type;
+        ++k;
+    }
+    qsort(c, k, sizeof(vcand), cmp_vcand);
+    for (uint32_t r = 0; r < k && r < q; ++r) dose_today[c[r].id] = (uint8_t)c[r].type;
+    free(c);
+}
+
 static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age, const int16_t *vday1,
                      uint32_t t, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt,
-                     or_diag *dg)
+                     int16_t *vd1, int16_t *vd2, or_diag *dg)
 {
     const uint32_t n = m->n, L = m->inf_len;
     const double *t64 = tb->t64;
@@ -414,6 +470,13 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         }
     }
 
+    /* dose selection of the priority strategies, from the state at the start of the day */
+    uint8_t *dose_today = NULL;
+    if (m->vax_on && m->vax_strategy != 0 && t >= m->vax_start) {
+        dose_today = (uint8_t *)malloc(n ? n : 1);
+        select_doses(m, age, t, stage, flags, vd1, dose_today);
+    }
+
     /* a6-a7: state machine and interventions, agent by agent */
     for (uint32_t j = 0; j < n; ++j) {
         int st = stage[j], a = age[j];
@@ -472,7 +535,18 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         }
 
         /* vaccination (Sec. 4.4 and Sec. 5) */
-        if (m->vax_on && vday1[j] != 0x7FFF) {
+        if (m->vax_on && m->vax_strategy != 0) {
+            if (dose_today && dose_today[j] == 1) { fl |= FL_DOSE1; vd1[j] = (int16_t)t; }
+            if (dose_today && dose_today[j] == 2) { fl |= FL_DOSE2; vd2[j] = (int16_t)t; }
+            if (st == ST_S && !newinf[j]) {
+                uint32_t w[4];
+                draw4(m->seed, j, 0, SM_VAX, 0, w);
+                if ((fl & FL_DOSE1) && (int64_t)t == (int64_t)vd1[j] + m->vax_onset && happens(w[0], m->vax_eff1))
+                    st = ST_VAX;
+                else if ((fl & FL_DOSE2) && (int64_t)t == (int64_t)vd2[j] + m->vax_onset && happens(w[0], m->vax_eff2))
+                    st = ST_VAX;
+            }
+        } else if (m->vax_on && vday1[j] != 0x7FFF) {
             int64_t d1 = vday1[j];
             int elig = !(st == ST_HOSP || st == ST_ICU || st == ST_DEAD);
             if ((int64_t)t == d1 && elig) fl |= FL_DOSE1;
@@ -499,17 +573,18 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         for (int s = 0; s < OR_N_STAGE; ++s) dg->hist[s] = 0;
         for (uint32_t j = 0; j < n; ++j) dg->hist[(int)stage[j]]++;
     }
-    free(inf32); free(inf64); free(newinf);
+    free(inf32); free(inf64); free(newinf); free(dose_today);
     return 0;
 }
 
 int or_step(const or_model *m, const uint8_t *age, const int16_t *vday1, uint32_t t,
-            int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt, or_diag *dg)
+            int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt, int16_t *vd1, int16_t *vd2,
+            or_diag *dg)
 {
     if (check_model(m)) return -1;
     or_tables tb;
     make_tables(m, &tb);
-    return step_impl(m, &tb, age, vday1, t, stage, timer, tinf, flags, qt, dg);
+    return step_impl(m, &tb, age, vday1, t, stage, timer, tinf, flags, qt, vd1, vd2, dg);
 }
 
 /* infection of the initial cases before step 0: the same branch and duration
@@ -535,7 +610,7 @@ int or_seed_infections(const or_model *m, const uint8_t *age, const uint32_t *id
 
 /* T steps from t0; new_inf[T], hist[T][11], messages[T] (NULL to skip) */
 int or_run(const or_model *m, const uint8_t *age, const int16_t *vday1, uint32_t t0, uint32_t T,
-           int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt,
+           int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt, int16_t *vd1, int16_t *vd2,
            int32_t *new_inf, int32_t *hist, int64_t *messages)
 {
     if (check_model(m)) return -1;
@@ -544,7 +619,7 @@ int or_run(const or_model *m, const uint8_t *age, const int16_t *vday1, uint32_t
     or_diag dg;
     memset(&dg, 0, sizeof dg);
     for (uint32_t s = 0; s < T; ++s) {
-        int rc = step_impl(m, &tb, age, vday1, t0 + s, stage, timer, tinf, flags, qt, &dg);
+        int rc = step_impl(m, &tb, age, vday1, t0 + s, stage, timer, tinf, flags, qt, vd1, vd2, &dg);
         if (rc) return rc;
         if (new_inf) new_inf[s] = dg.new_inf;
         if (hist) memcpy(hist + (size_t)s * OR_N_STAGE, dg.hist, sizeof dg.hist);

@@ -139,6 +139,8 @@ def default_params() -> dict:
         quar_on=0, quar_days=14, q_dropout=0.0,                     # Sec. 4.1
         vax_on=0, vax_start=30, vax_onset=12, dose2_delay=21,       # Sec. 5
         vax_rate=0.01, vax_eff1=0.8, vax_eff2=0.95,
+        vax_strategy=0,   # 0 static age-priority schedule; 1 standard, 2 delayed second dose, 3 delayed except 65+
+        elderly_bin=6,    # first age bin treated as "65+" (the 61-70 bin holds Table 1's 68-year-olds)
         seed=0, net_seed=0,
     )
 

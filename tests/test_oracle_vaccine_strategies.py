@@ -1,0 +1,86 @@
+"""Pins for the vaccination priority strategies (Sec. 5) against the paper's worked
+example (Table 1, tests/golden/table1_vaccine_priority.txt) and invariants of the
+shared daily dose supply."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_04421_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_vaccine_priority.txt")
+STRATEGY = {"standard": 1, "delayed_second_dose": 2, "delayed_second_dose_except_65": 3}
+
+
+def age_bin(years):
+    """The paper's nine bins 0-10, 11-20, ..., 71-80, 80+ (Sec. 3)."""
+    return min(8, max(0, (years - 1) // 10))
+
+
+def load_golden():
+    people, orders = [], {}
+    for line in open(GOLDEN):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "person":
+            people.append((f[1], int(f[2]), f[3]))
+        elif f[0] == "order":
+            orders[f[1]] = f[2:]
+    return people, orders
+
+
+def empty_graph(n):
+    return dict(n=n, row_ptr=[], col=[])
+
+
+@pytest.mark.parametrize("name", list(STRATEGY))
+def test_table1_order(name):
+    people, orders = load_golden()
+    n = len(people)
+    age = np.array([age_bin(a) for _, a, _ in people], np.uint8)
+    st = oracle.State(n)
+    for j, (_, _, elig) in enumerate(people):
+        if elig == "second":
+            st.flags[j] = 0x01
+            st.vd1[j] = -30          # first dose a month ago: due for the second
+    p = W.params_with(rand_mean=0.0, vax_on=1, vax_start=0, vax_rate=1.0 / n, dose2_delay=21,
+                      vax_strategy=STRATEGY[name])
+    sim = oracle.Sim(empty_graph(n), p, age, None, state=st)
+    got = []
+    for t in range(n):
+        before = sim.state.flags.copy()
+        sim.step(diag=False)
+        changed = np.nonzero(sim.state.flags != before)[0]
+        assert changed.size == 1, (t, changed)   # one dose a day
+        got.append(people[int(changed[0])][0])
+    assert got == orders[name], (name, got)
+
+
+def test_shared_supply_invariants():
+    """Each day exactly min(supply, eligible) doses; second doses only after the delay."""
+    pop = W.population(4000, 6, 30)
+    for strat in (1, 2, 3):
+        p = W.params_with(vax_on=1, vax_start=2, vax_rate=0.01, dose2_delay=10, vax_strategy=strat, R=3.0)
+        sim = oracle.Sim(pop, p, pop["age"], pop["seed_ids"])
+        q = int(np.floor(0.01 * 4000))
+        for t in range(40):
+            prev = sim.state.copy()
+            sim.step(diag=False)
+            s = sim.state
+            d1 = np.nonzero((s.flags & 1) & ~(prev.flags & 1))[0]
+            d2 = np.nonzero((s.flags & 2) & ~(prev.flags & 2))[0]
+            if t < 2:
+                assert d1.size == 0 and d2.size == 0
+                continue
+            elig1 = ((prev.flags & 1) == 0) & ~np.isin(prev.stage, [6, 7, 10])
+            elig2 = ((prev.flags & 1) != 0) & ((prev.flags & 2) == 0) & (t - prev.vd1.astype(int) >= 10) & \
+                ~np.isin(prev.stage, [6, 7, 10])
+            assert d1.size + d2.size == min(q, int(elig1.sum() + elig2.sum()))
+            assert np.all(s.vd1[d1] == t) and np.all(s.vd2[d2] == t)
+            assert np.all(t - prev.vd1[d2].astype(int) >= 10)
+            if strat == 1 and elig2.sum() >= q:
+                assert d1.size == 0          # standard: second doses come first
+            if strat == 2 and elig1.sum() >= q:
+                assert d2.size == 0          # delayed: first doses come first
