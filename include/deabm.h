@@ -100,6 +100,8 @@ typedef struct {
     const uint8_t *qt;
     const uint32_t *seed_ids;
     uint32_t n_seed;
+    const int16_t *dose1_day;  /* [N] or NULL: day of a first dose given before the run (priority strategies) */
+    const int16_t *dose2_day;  /* [N] or NULL: day of a second dose given before the run; 0x7FFF = none */
 } deabm_agents;
 
 /* Model parameters.  Eq. 1 names: R, S_age (S_a), A_class (A_s), B_net (B_n),
@@ -137,6 +139,15 @@ typedef struct {
     uint64_t seed, net_seed;
     uint32_t max_steps;   /* capacity of the per-day counters (0 = 1024) */
     uint32_t keep_lambda; /* 1: keep lambda_j and p_j of the last day for deabm_get_state */
+    uint32_t vax_strategy;   /* 0: static schedule above.  1, 2, 3: a shared supply of floor(vax_rate * N)
+                                doses a day from vax_start, given by priority (Sec. 5, Table 1) to agents
+                                due a first dose or due a second dose (first dose >= dose2_delay days ago),
+                                none in hospital, ICU or dead; age bin descending inside each group:
+                                1 standard (second doses first), 2 delayed second dose (first doses first),
+                                3 delayed except the elderly (bins >= elderly_bin interleaved by age with a
+                                first dose before a second, then the others' first doses, then their second
+                                doses); ties by agent id.  Plain contexts only. */
+    uint32_t elderly_bin;    /* first age bin counted as "65+" by strategy 3 */
     uint32_t locality_order; /* 1: number the agents internally in breadth-first order of the
                                 static network with the most edges, so that the members of a
                                 group sit next to each other in device memory; results and
@@ -197,6 +208,10 @@ int deabm_run(deabm_ctx *ctx, uint32_t T, int32_t *new_inf, int32_t *hist);
  * Synchronises the stream. */
 int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags,
                     uint8_t *qt, float *lambda, float *p);
+
+/* Days of each agent's first and second dose under a priority strategy
+ * (host int16 [N], 0x7FFF = none; either may be NULL).  Synchronises. */
+int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day);
 
 /* Per-day counters already run: days [0, day_count) of new infections
  * [day][n_rep], stage histogram [day][n_rep][11] and messages processed

@@ -53,6 +53,10 @@ struct deabm_ctx {
     cudaStream_t own_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     uint32_t graph_day0 = 0, graph_T = 0;
+    // vaccination priority strategies: today's classes and doses by caller id, selection scratch
+    uint8_t *vax_cls = nullptr, *vax_dose = nullptr;
+    uint32_t *vax_scratch = nullptr;
+    uint32_t vax_supply = 0;
     std::string err;
 };
 
@@ -160,6 +164,10 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         return fail(ctx, DEABM_EINVAL, "probabilities and rates must be in [0,1]");
     if (p->vax_on && (p->vax_onset < 1 || p->dose2_delay < 1))
         return fail(ctx, DEABM_EINVAL, "vax_onset and dose2_delay must be >= 1");
+    if (p->vax_strategy > 3 || p->elderly_bin > 9)
+        return fail(ctx, DEABM_EINVAL, "vax_strategy must be 0..3 and elderly_bin 0..9");
+    if (p->vax_strategy != 0 && n_rep != 1)
+        return fail(ctx, DEABM_EINVAL, "vaccination priority strategies need a plain (one replicate) context");
     if (n_rep < 1 || n_rep > 1024) return fail(ctx, DEABM_EINVAL, "n_rep must be in 1..1024");
     if (rep_params)
         for (uint32_t b = 0; b < n_rep; ++b) {
@@ -352,6 +360,26 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaMemcpyAsync(ctx->S0.flags, ctx->S.flags, nb, cudaMemcpyDeviceToDevice, s));
             CU(ctx, cudaMemcpyAsync(ctx->S0.qt, ctx->S.qt, nb, cudaMemcpyDeviceToDevice, s));
             ctx->base = *p;
+            if (p->vax_strategy != 0) {
+                std::vector<int16_t> d1(nb, kNever), d2(nb, kNever);
+                for (uint32_t q = 0; q < n; ++q) {
+                    if (a->dose1_day) d1[q] = a->dose1_day[orig_of(q)];
+                    if (a->dose2_day) d2[q] = a->dose2_day[orig_of(q)];
+                }
+                if ((r = dalloc(ctx, &ctx->S.vd1, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->S.vd2, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->S0.vd1, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->S0.vd2, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->vax_cls, n))) return r;
+                if ((r = dalloc(ctx, &ctx->vax_dose, n))) return r;
+                if ((r = dalloc(ctx, &ctx->vax_scratch, vax_select_scratch_words(n)))) return r;
+                CU(ctx, cudaMemcpyAsync(ctx->S0.vd1, d1.data(), nb * 2, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->S0.vd2, d2.data(), nb * 2, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->S.vd1, d1.data(), nb * 2, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->S.vd2, d2.data(), nb * 2, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaStreamSynchronize(s));
+                ctx->vax_supply = (uint32_t)std::floor(p->vax_rate * (double)n);
+            }
 
             // per-replicate parameters
             std::vector<Rep> reps;
@@ -438,6 +466,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.age = ctx->age;
             K.dose1_day = ctx->dose1;
             K.orig_id = ctx->relabel ? ctx->orig_id : nullptr;
+            K.vax_strategy = p->vax_strategy;
+            K.dose_today = nullptr;
 
             if (a->n_seed) {
                 std::vector<uint32_t> ids(a->seed_ids, a->seed_ids + a->n_seed);
@@ -497,12 +527,18 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
     }
     for (uint32_t s = 0; s < n_steps; ++s) {
         const int c = ctx->cur;
+        KParams kp = ctx->kp;
+        if (kp.vax_strategy != 0 && kp.vax_on && ctx->day >= ctx->base.vax_start) {
+            CU(ctx, launch_vax_select(kp, ctx->day, ctx->base.dose2_delay, ctx->base.elderly_bin, ctx->vax_supply,
+                                      ctx->S, ctx->vax_cls, ctx->vax_dose, ctx->vax_scratch, ctx->stream));
+            kp.dose_today = ctx->vax_dose;
+        }
         InfBuffers I;
         I.cur = ctx->inf[c];
         I.next = ctx->inf[c ^ 1];
         I.rand_cur = ctx->inf_rand[c] ? ctx->inf_rand[c] : ctx->inf[c];
         I.rand_next = ctx->inf_rand[c ^ 1];
-        CU(ctx, launch_step(ctx->kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
+        CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
                             ctx->stream));
         ctx->cur ^= 1;
         ctx->day += 1;
@@ -619,6 +655,23 @@ extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, in
     return DEABM_OK;
 }
 
+extern "C" int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (!ctx->S.vd1) return fail(ctx, DEABM_ESTATE, "no vaccination priority strategy in this context");
+    const size_t nb = (size_t)ctx->n;
+    std::vector<int16_t> t1(nb), t2(nb);
+    CU(ctx, cudaMemcpyAsync(t1.data(), ctx->S.vd1, nb * 2, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(t2.data(), ctx->S.vd2, nb * 2, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (uint32_t q = 0; q < ctx->n; ++q) {
+        const uint32_t o = ctx->relabel ? ctx->new2orig[q] : q;
+        if (dose1_day) dose1_day[o] = t1[q];
+        if (dose2_day) dose2_day[o] = t2[q];
+    }
+    return DEABM_OK;
+}
+
 extern "C" int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *poisson_thr, int16_t *dose1_day)
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
@@ -681,6 +734,8 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
+            if (params[q].vax_strategy)
+                return fail(ctx, DEABM_EINVAL, "vaccination priority strategies are not available for ragged batches");
         }
         if (total >= (1ull << 31)) return fail(ctx, DEABM_EINVAL, "too many agents in total");
         ctx->ragged = true;
@@ -939,6 +994,10 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
         CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
         ctx->day = 0;
         return DEABM_OK;
+    }
+    if (ctx->S.vd1) {
+        CU(ctx, cudaMemcpyAsync(ctx->S.vd1, ctx->S0.vd1, nb * 2, cudaMemcpyDeviceToDevice, s));
+        CU(ctx, cudaMemcpyAsync(ctx->S.vd2, ctx->S0.vd2, nb * 2, cudaMemcpyDeviceToDevice, s));
     }
     if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
     ctx->cur = 0;

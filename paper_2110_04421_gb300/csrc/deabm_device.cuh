@@ -85,6 +85,8 @@ struct KParams {
     const uint8_t *age;        // by internal id
     const int16_t *dose1_day;  // by internal id
     const uint32_t *orig_id;   // internal id -> caller's agent id (nullptr: the same)
+    uint32_t vax_strategy;     // 0 static schedule; 1..3 priority strategies with a shared supply
+    const uint8_t *dose_today; // priority strategies: 1 = dosed today, by caller id (nullptr: none)
 };
 
 // Infectiousness buffers of a day.  Static-network gathers read `cur` (internal
@@ -101,6 +103,7 @@ struct StateRef {
     int8_t *stage;
     int16_t *timer, *tinf;
     uint8_t *flags, *qt;
+    int16_t *vd1, *vd2;  // dose days under a priority strategy (nullptr otherwise)
 };
 
 // One population of a ragged batch: a KParams view whose CSR, age and dose-day
@@ -128,6 +131,7 @@ struct Counters {
 struct AgentState {
     int st, tm, ti;
     uint32_t fl, qd, cd;
+    int vd1 = kNever, vd2 = kNever;
 };
 
 __device__ __forceinline__ int infector_class(int st)
@@ -202,7 +206,22 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
         a.cd = uniform_int(w.y, P.test_lo, P.test_hi);
     }
     // two-dose vaccination (Sec. 4.4, Sec. 5)
-    if (P.vax_on && d1 != kNever) {
+    if (P.vax_on && P.vax_strategy != 0) {
+        // priority strategies: today's doses were selected before the day from its starting state
+        if (P.dose_today && P.dose_today[j]) {
+            if (!(a.fl & DEABM_FL_DOSE1)) { a.fl |= DEABM_FL_DOSE1; a.vd1 = (int)day; }
+            else { a.fl |= DEABM_FL_DOSE2; a.vd2 = (int)day; }
+        }
+        if (a.st == DEABM_S && !infected) {
+            const bool on1 = (a.fl & DEABM_FL_DOSE1) && (int64_t)day == (int64_t)a.vd1 + (int64_t)P.vax_onset;
+            const bool on2 = (a.fl & DEABM_FL_DOSE2) && (int64_t)day == (int64_t)a.vd2 + (int64_t)P.vax_onset;
+            if (on1 || on2) {
+                const uint32_t v = draw(key, j, 0u, kStreamVax).x;
+                if (on1 && (uint64_t)v < P.thr_eff1) a.st = DEABM_VAX;
+                else if (on2 && (uint64_t)v < P.thr_eff2) a.st = DEABM_VAX;
+            }
+        }
+    } else if (P.vax_on && d1 != kNever) {
         const int64_t t = day, D1 = d1, D2 = D1 + (int64_t)rp.dose2_delay;
         const bool elig = !(a.st == DEABM_HOSP || a.st == DEABM_ICU || a.st == DEABM_DEAD);
         if (t == D1 && elig) a.fl |= DEABM_FL_DOSE1;

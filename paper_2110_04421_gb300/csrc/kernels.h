@@ -15,6 +15,13 @@ cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t 
                                const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
                                uint32_t n_pops, uint32_t grid, cudaStream_t stream);
 
+// daily dose selection of the vaccination priority strategies: dose_caller[o] = 1
+// for the agents (caller ids) dosed today; scratch of vax_select_scratch_words(n)
+cudaError_t launch_vax_select(const KParams &P, uint32_t day, uint32_t dose2_delay, uint32_t elderly_bin,
+                              uint32_t supply, const StateRef &S, uint8_t *cls_caller, uint8_t *dose_caller,
+                              uint32_t *scratch, cudaStream_t stream);
+size_t vax_select_scratch_words(uint32_t n);
+
 // set-up: infectiousness table (FP64 gamma integrals, rounded once, times A_class)
 cudaError_t launch_inf_table(Tables *tab, const double *shape_scale /*device [6]*/, const float *A_class /*device [3]*/,
                              uint32_t len, cudaStream_t stream);

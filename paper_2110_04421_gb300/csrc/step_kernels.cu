@@ -56,6 +56,10 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     const uint32_t q = S.qt[i];
     a.qd = q & 0x0Fu;
     a.cd = (q >> 4) & 0x07u;
+    if (S.vd1) {
+        a.vd1 = S.vd1[i];
+        a.vd2 = S.vd2[i];
+    }
     const uint2 key = seed_key(rp.seed);
     bool inf_now = false;
     uint32_t inf_y = 0;
@@ -77,6 +81,10 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     S.tinf[i] = (int16_t)a.ti;
     S.flags[i] = (uint8_t)a.fl;
     S.qt[i] = (uint8_t)((a.qd & 0x0Fu) | ((a.cd & 0x07u) << 4));
+    if (S.vd1) {
+        S.vd1[i] = (int16_t)a.vd1;
+        S.vd2[i] = (int16_t)a.vd2;
+    }
     const float v = emitted(P.tab, P.inf_len, a.st, a.ti, a.qd);
     I.next[i] = v;
     if (I.rand_next) I.rand_next[(size_t)jo * stride + b] = v;
@@ -236,6 +244,8 @@ __global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restr
         Sp.tinf = S.tinf + sp.base;
         Sp.flags = S.flags + sp.base;
         Sp.qt = S.qt + sp.base;
+        Sp.vd1 = nullptr;  // priority strategies are not available in ragged batches
+        Sp.vd2 = nullptr;
         for (uint32_t r0 = tl.begin; r0 < tl.end; r0 += blockDim.x) {
             const uint32_t j = r0 + threadIdx.x;
             const bool active = j < tl.end;

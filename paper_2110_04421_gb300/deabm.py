@@ -25,7 +25,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
-           "deabm_mlp_use_tcgen05")
+           "deabm_mlp_use_tcgen05", "deabm_get_dose_days")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -44,7 +44,8 @@ class Graph(C.Structure):
 
 class Agents(C.Structure):
     _fields_ = [("age_bin", C.c_void_p), ("stage", C.c_void_p), ("timer", C.c_void_p), ("tinf", C.c_void_p),
-                ("flags", C.c_void_p), ("qt", C.c_void_p), ("seed_ids", C.c_void_p), ("n_seed", C.c_uint32)]
+                ("flags", C.c_void_p), ("qt", C.c_void_p), ("seed_ids", C.c_void_p), ("n_seed", C.c_uint32),
+                ("dose1_day", C.c_void_p), ("dose2_day", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -61,7 +62,8 @@ class Params(C.Structure):
         ("vax_on", C.c_uint32), ("vax_start", C.c_uint32), ("vax_onset", C.c_uint32), ("dose2_delay", C.c_uint32),
         ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
-        ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32), ("locality_order", C.c_uint32),
+        ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32), ("vax_strategy", C.c_uint32),
+        ("elderly_bin", C.c_uint32), ("locality_order", C.c_uint32),
     ]
 
 
@@ -100,6 +102,8 @@ def lib():
         L.deabm_relaxed_destroy.argtypes = [vp]
         L.deabm_relaxed_destroy.restype = None
         L.deabm_reset.argtypes = [vp, vp, vp]
+        L.deabm_get_dose_days.argtypes = [vp, vp, vp]
+        L.deabm_get_dose_days.restype = C.c_int
         L.deabm_create_ragged.argtypes = [u32, C.POINTER(Graph), C.POINTER(Agents), C.POINTER(Params), vp, C.POINTER(vp)]
         L.deabm_create_ragged.restype = C.c_int
         L.deabm_autotune.argtypes = [vp, u32, C.POINTER(u32), C.POINTER(u32)]
@@ -178,6 +182,8 @@ def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False, local
         setattr(p, name, P[name])
     p.max_steps = max_steps
     p.keep_lambda = 1 if keep_lambda else 0
+    p.vax_strategy = P.get("vax_strategy", 0)
+    p.elderly_bin = P.get("elderly_bin", 6)
     p.locality_order = 1 if locality_order else 0
     return p
 
@@ -402,7 +408,9 @@ class Simulation:
         a.age_bin = age.ctypes.data
         if state is not None:
             for k, dt in (("stage", np.int8), ("timer", np.int16), ("tinf", np.int16), ("flags", np.uint8),
-                          ("qt", np.uint8)):
+                          ("qt", np.uint8), ("dose1_day", np.int16), ("dose2_day", np.int16)):
+                if k not in state:
+                    continue
                 arr = np.ascontiguousarray(state[k], dtype=dt)
                 keep.append(arr)
                 setattr(a, k, arr.ctypes.data)
@@ -469,6 +477,12 @@ class Simulation:
         if self.n_rep > 1:
             out = {k: v.reshape(self.n, self.n_rep) for k, v in out.items()}
         return out
+
+    def dose_days(self):
+        d1 = np.zeros(self.n * self.n_rep, np.int16)
+        d2 = np.zeros(self.n * self.n_rep, np.int16)
+        _check(lib().deabm_get_dose_days(self.ctx, _p(d1), _p(d2)), self.ctx)
+        return d1, d2
 
     def counters(self, days: int | None = None):
         days = self.day if days is None else days
