@@ -78,7 +78,7 @@ class _Model(C.Structure):
         ("dose2_delay", C.c_uint32),
         ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
-        ("vax_strategy", C.c_uint32), ("elderly_bin", C.c_uint32),
+        ("vax_strategy", C.c_uint32), ("elderly_bin", C.c_uint32), ("vax_nonsterile", C.c_uint32),
     ]
 
 
@@ -223,6 +223,7 @@ class Model:
             setattr(m, name, P[name])
         m.vax_strategy = P.get("vax_strategy", 0)
         m.elderly_bin = P.get("elderly_bin", 6)
+        m.vax_nonsterile = P.get("vax_nonsterile", 0)
         self.m = m
         self.params = P
 

@@ -44,6 +44,7 @@ enum {
 #define FL_DOSE1 0x01u
 #define FL_DOSE2 0x02u
 #define FL_POS 0x04u
+#define FL_IMMUNE 0x08u  /* non-sterilising vaccine immunity: infections are asymptomatic (Sec. 5) */
 /* qt byte: low nibble = quarantine days left, bits 4..6 = days until the test result */
 #define QT_QDAYS(q) ((q) & 0x0Fu)
 #define QT_TCD(q) (((q) >> 4) & 0x07u)
@@ -77,6 +78,7 @@ typedef struct {
     uint64_t seed, net_seed;
     uint32_t vax_strategy;  /* 0 static schedule; 1 standard, 2 delayed second dose, 3 delayed except elderly */
     uint32_t elderly_bin;   /* first age bin counted as "65+" by strategy 3 */
+    uint32_t vax_nonsterile; /* 1: immunity is non-sterilising (Sec. 5, second version) */
 } or_model;
 
 /* ------------------------------------------------------------------------- */
@@ -489,7 +491,8 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         if (newinf[j]) {
             uint32_t w[4];
             draw4(m->seed, j, t, SM_PROG, 0, w);
-            if (happens(w[0], m->p_asym[a])) st = ST_ASYM;
+            if (fl & FL_IMMUNE) st = ST_ASYM;  /* vaccinated, non-sterilising: asymptomatic infection */
+            else if (happens(w[0], m->p_asym[a])) st = ST_ASYM;
             else if (happens(w[2], m->p_sev[a])) st = ST_PRE_SEV;
             else st = ST_PRE_MILD;
             tm = (int)duration(m, st, a, w[1]);
@@ -541,10 +544,10 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             if (st == ST_S && !newinf[j]) {
                 uint32_t w[4];
                 draw4(m->seed, j, 0, SM_VAX, 0, w);
-                if ((fl & FL_DOSE1) && (int64_t)t == (int64_t)vd1[j] + m->vax_onset && happens(w[0], m->vax_eff1))
-                    st = ST_VAX;
-                else if ((fl & FL_DOSE2) && (int64_t)t == (int64_t)vd2[j] + m->vax_onset && happens(w[0], m->vax_eff2))
-                    st = ST_VAX;
+                if (((fl & FL_DOSE1) && (int64_t)t == (int64_t)vd1[j] + m->vax_onset && happens(w[0], m->vax_eff1)) ||
+                    ((fl & FL_DOSE2) && (int64_t)t == (int64_t)vd2[j] + m->vax_onset && happens(w[0], m->vax_eff2))) {
+                    if (m->vax_nonsterile) fl |= FL_IMMUNE; else st = ST_VAX;
+                }
             }
         } else if (m->vax_on && vday1[j] != 0x7FFF) {
             int64_t d1 = vday1[j];
@@ -554,9 +557,11 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             if (st == ST_S && !newinf[j]) {
                 uint32_t w[4];
                 draw4(m->seed, j, 0, SM_VAX, 0, w);
-                if ((fl & FL_DOSE1) && (int64_t)t == d1 + m->vax_onset && happens(w[0], m->vax_eff1)) st = ST_VAX;
-                else if ((fl & FL_DOSE2) && (int64_t)t == d1 + m->dose2_delay + m->vax_onset &&
-                         happens(w[0], m->vax_eff2)) st = ST_VAX;
+                if (((fl & FL_DOSE1) && (int64_t)t == d1 + m->vax_onset && happens(w[0], m->vax_eff1)) ||
+                    ((fl & FL_DOSE2) && (int64_t)t == d1 + m->dose2_delay + m->vax_onset &&
+                     happens(w[0], m->vax_eff2))) {
+                    if (m->vax_nonsterile) fl |= FL_IMMUNE; else st = ST_VAX;
+                }
             }
         }
 

@@ -141,6 +141,7 @@ def default_params() -> dict:
         vax_rate=0.01, vax_eff1=0.8, vax_eff2=0.95,
         vax_strategy=0,   # 0 static age-priority schedule; 1 standard, 2 delayed second dose, 3 delayed except 65+
         elderly_bin=6,    # first age bin treated as "65+" (the 61-70 bin holds Table 1's 68-year-olds)
+        vax_nonsterile=0, # 1: vaccine immunity is non-sterilising (infections become asymptomatic)
         seed=0, net_seed=0,
     )
 

@@ -84,3 +84,31 @@ def test_shared_supply_invariants():
                 assert d1.size == 0          # standard: second doses come first
             if strat == 2 and elig1.sum() >= q:
                 assert d2.size == 0          # delayed: first doses come first
+
+
+def test_nonsterilising_immunity_makes_infections_asymptomatic():
+    """Second immunity version of Sec. 5: immune agents stay susceptible but every
+    later infection is asymptomatic; sterilising immunity moves them to VAX."""
+    pop = W.population(5000, 9, 50)
+    base = dict(vax_on=1, vax_start=0, vax_rate=0.2, vax_eff1=0.9, dose2_delay=60, R=5.0, seed=17)
+    ster = oracle.Sim(pop, W.params_with(**base), pop["age"], pop["seed_ids"])
+    non = oracle.Sim(pop, W.params_with(vax_nonsterile=1, **base), pop["age"], pop["seed_ids"])
+    asym_immune, infected_immune = 0, 0
+    for t in range(70):
+        prev = non.state.copy()
+        ster.step(diag=False)
+        non.step(diag=False)
+        s = non.state
+        newly = (prev.stage == 0) & (s.stage != 0) & (s.stage != 9)
+        imm = (prev.flags & 0x08) != 0
+        infected_immune += int((newly & imm).sum())
+        asym_immune += int((newly & imm & (s.stage == 1)).sum())
+        assert not np.any(s.stage == 9)                      # no VAX stage without sterilising immunity
+    assert infected_immune > 50 and asym_immune == infected_immune
+    assert np.any(ster.state.stage == 9)
+    # every immune flag replays from the agent's vaccine word (dose 1 only: dose 2 comes after day 60 + 12)
+    imm = np.nonzero(non.state.flags & 0x08)[0]
+    assert imm.size > 100
+    for j in imm[:300]:
+        w = oracle.philox([int(j), 0, 7, 0], [17, 0])[0]
+        assert (non.state.flags[j] & 1) and w < oracle.threshold(0.9)
