@@ -65,6 +65,7 @@ enum {
 #define DEABM_FL_DOSE1 0x01u
 #define DEABM_FL_DOSE2 0x02u
 #define DEABM_FL_POS 0x04u
+#define DEABM_FL_IMMUNE 0x08u  /* non-sterilising vaccine immunity (vax_nonsterile) */
 /* qt byte: bits 0..3 quarantine days left (0 = not quarantined),
  *          bits 4..6 days until a pending test result (0 = none) */
 
@@ -148,6 +149,9 @@ typedef struct {
                                 first dose before a second, then the others' first doses, then their second
                                 doses); ties by agent id.  Plain contexts only. */
     uint32_t elderly_bin;    /* first age bin counted as "65+" by strategy 3 */
+    uint32_t vax_nonsterile; /* 0: immunity is sterilising (stage VAX); 1: non-sterilising (Sec. 5, second
+                                version): the agent stays susceptible with flag DEABM_FL_IMMUNE and any
+                                later infection is asymptomatic */
     uint32_t locality_order; /* 1: number the agents internally in breadth-first order of the
                                 static network with the most edges, so that the members of a
                                 group sit next to each other in device memory; results and

@@ -467,6 +467,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.dose1_day = ctx->dose1;
             K.orig_id = ctx->relabel ? ctx->orig_id : nullptr;
             K.vax_strategy = p->vax_strategy;
+            K.vax_nonsterile = p->vax_nonsterile ? 1u : 0u;
             K.dose_today = nullptr;
 
             if (a->n_seed) {
@@ -828,6 +829,7 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.vax_onset = p.vax_onset;
             K.thr_eff1 = threshold(p.vax_eff1);
             K.thr_eff2 = threshold(p.vax_eff2);
+            K.vax_nonsterile = p.vax_nonsterile ? 1u : 0u;
             K.tab = ctx->tab + q;
             K.rep = ctx->rep + q;
             K.age = ctx->age + base;

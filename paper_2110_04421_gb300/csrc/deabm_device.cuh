@@ -86,6 +86,7 @@ struct KParams {
     const int16_t *dose1_day;  // by internal id
     const uint32_t *orig_id;   // internal id -> caller's agent id (nullptr: the same)
     uint32_t vax_strategy;     // 0 static schedule; 1..3 priority strategies with a shared supply
+    uint32_t vax_nonsterile;   // 1: immunity leaves the agent susceptible (flag), infections asymptomatic
     const uint8_t *dose_today; // priority strategies: 1 = dosed today, by caller id (nullptr: none)
 };
 
@@ -152,7 +153,8 @@ __device__ __forceinline__ float emitted(const Tables *tab, uint32_t L, int st, 
 
 __device__ __forceinline__ void new_infection(const Tables *tab, int age, uint4 w, AgentState &a)
 {
-    if ((uint64_t)w.x < __ldg(&tab->thr_asym[age])) a.st = DEABM_ASYM;
+    if (a.fl & DEABM_FL_IMMUNE) a.st = DEABM_ASYM;  // vaccinated, non-sterilising: asymptomatic infection
+    else if ((uint64_t)w.x < __ldg(&tab->thr_asym[age])) a.st = DEABM_ASYM;
     else if ((uint64_t)w.z < __ldg(&tab->thr_sev[age])) a.st = DEABM_PRE_SEV;
     else a.st = DEABM_PRE_MILD;
     a.tm = (int)uniform_int(w.y, __ldg(&tab->dur_lo[a.st][age]), __ldg(&tab->dur_hi[a.st][age]));
@@ -217,8 +219,10 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
             const bool on2 = (a.fl & DEABM_FL_DOSE2) && (int64_t)day == (int64_t)a.vd2 + (int64_t)P.vax_onset;
             if (on1 || on2) {
                 const uint32_t v = draw(key, j, 0u, kStreamVax).x;
-                if (on1 && (uint64_t)v < P.thr_eff1) a.st = DEABM_VAX;
-                else if (on2 && (uint64_t)v < P.thr_eff2) a.st = DEABM_VAX;
+                if ((on1 && (uint64_t)v < P.thr_eff1) || (on2 && (uint64_t)v < P.thr_eff2)) {
+                    if (P.vax_nonsterile) a.fl |= DEABM_FL_IMMUNE;
+                    else a.st = DEABM_VAX;
+                }
             }
         }
     } else if (P.vax_on && d1 != kNever) {
@@ -231,8 +235,10 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
             const bool on2 = (a.fl & DEABM_FL_DOSE2) && t == D2 + (int64_t)P.vax_onset;
             if (on1 || on2) {
                 const uint32_t v = draw(key, j, 0u, kStreamVax).x;
-                if (on1 && (uint64_t)v < P.thr_eff1) a.st = DEABM_VAX;
-                else if (on2 && (uint64_t)v < P.thr_eff2) a.st = DEABM_VAX;
+                if ((on1 && (uint64_t)v < P.thr_eff1) || (on2 && (uint64_t)v < P.thr_eff2)) {
+                    if (P.vax_nonsterile) a.fl |= DEABM_FL_IMMUNE;
+                    else a.st = DEABM_VAX;
+                }
             }
         }
     }

@@ -63,7 +63,7 @@ class Params(C.Structure):
         ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
         ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32), ("vax_strategy", C.c_uint32),
-        ("elderly_bin", C.c_uint32), ("locality_order", C.c_uint32),
+        ("elderly_bin", C.c_uint32), ("vax_nonsterile", C.c_uint32), ("locality_order", C.c_uint32),
     ]
 
 
@@ -184,6 +184,7 @@ def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False, local
     p.keep_lambda = 1 if keep_lambda else 0
     p.vax_strategy = P.get("vax_strategy", 0)
     p.elderly_bin = P.get("elderly_bin", 6)
+    p.vax_nonsterile = P.get("vax_nonsterile", 0)
     p.locality_order = 1 if locality_order else 0
     return p
 

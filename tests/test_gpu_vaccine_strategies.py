@@ -62,3 +62,12 @@ def test_strategy_runs_match_oracle(strategy):
     o.run(70)
     assert np.array_equal(d1, o.state.vd1) and np.array_equal(d2, o.state.vd2)
     assert (d1 != 0x7FFF).sum() > 1000
+
+
+@pytest.mark.parametrize("strategy", [0, 2])
+def test_nonsterilising_immunity_matches_oracle(strategy):
+    pop = W.population(5003, 13, 40)
+    p = W.params_with(vax_on=1, vax_start=2, vax_rate=0.05, vax_eff1=0.85, dose2_delay=15, vax_strategy=strategy,
+                      vax_nonsterile=1, R=4.5, seed=91, net_seed=92)
+    rep = compare_days(pop, p, 60)
+    assert rep["flips"] == 0 and rep["days"] == 60
