@@ -103,12 +103,24 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def traffic_from_profile(kernel_src: str, profile: str, units_per_launch: float):
+DAY_KERNEL_SOURCES = ("step_kernels.cu", "day_common.cuh", "deabm_device.cuh")
+MLP_KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc.h")
+
+
+def sources_hash(names) -> str:
+    """sha256 prefix over the concatenated sources a kernel is compiled from."""
+    h = hashlib.sha256()
+    for nm in names:
+        h.update(open(os.path.join(ROOT, "paper_2110_04421_gb300", "csrc", nm), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(sources, profile: str, units_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (its sha256 prefix is recorded there); else None."""
+    current kernel sources (their sha256 prefix is recorded there); else None."""
     try:
         txt = open(os.path.join(ROOT, "profiles", profile)).read()
-        src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        src_hash = sources_hash(sources)
         if f"source_sha256_16: {src_hash}" not in txt:
             return None
         m = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+-]+)", txt)
@@ -196,8 +208,7 @@ def run_ours(args, rank, world, local):
         alg = step_bytes_plain(n, static_edges, len(pop["row_ptr"]), bool(params["vax_on"]))
         peak, peak_kind = measured_peak_hbm()
         achieved = alg / (avg_ms / 1e3) / 1e9
-        kernel_src = os.path.join(ROOT, "paper_2110_04421_gb300", "csrc", "step_kernels.cu")
-        traffic = traffic_from_profile(kernel_src, "step_plain_n2e6.md", n)
+        traffic = traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_n2e6.md", n)
         cpu = None if args.no_cpu_baseline else cpu_baseline(pop, params, args.cpu_seconds)
         line = {
             "metric": "agent interactions/s on 1 GB300 (plain day kernel; batched B=256 in 'batched')",
@@ -252,16 +263,21 @@ def run_relaxed(args):
     for _ in range(args.warmup):
         rx.grad(w["start"], y)
     reps = 5
-    t0 = time.perf_counter()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    ms_grad = 0.0
     for _ in range(reps):
-        loss0, g0, _ = rx.grad(w["start"], y)
-    ms_grad = (time.perf_counter() - t0) / reps * 1e3
+        flush.fill_(1.0)  # L2 flushed between gradients
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rx.grad(w["start"], y)  # returns host values: the call ends synchronised
+        ms_grad += (time.perf_counter() - t0) * 1e3 / reps
     t1 = time.perf_counter()
     theta, trace = rx.calibrate(w["start"], y, steps=args.calib_steps, lr=w["lr"])
     cal_s = time.perf_counter() - t1
     loss1, _, _ = rx.grad(theta, y)
     rx.close()
     return {"workload": w["name"], "ms_per_gradient": ms_grad, "days": w["T"], "checkpoint_every": 10,
+            "l2": "flushed before every timed gradient (write of twice its size)",
             "calibration": {"steps": args.calib_steps, "seconds": cal_s, "loss_start": float(trace[0]),
                             "loss_end": float(loss1), "theta_hidden": [float(x) for x in w["hidden"][:4]],
                             "theta_found": [float(x) for x in theta[:4]]}}
@@ -307,24 +323,26 @@ def run_surrogate(args):
             m.forward(x, out)
             m.train_step(x, y, 1e-4)
         reps = 20
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+        def timed(fn):
+            # L2 flushed (a write of twice its size) before every call; each call
+            # bracketed by its own events on the MLP's stream
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for e0, e1 in ev:
+                flush.fill_(1.0)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            m.sync()
+            torch.cuda.synchronize()
+            return sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
+
         m.forward(x, out)  # refresh the K-major weight copies outside the timed region
-        e[0].record(stream)
-        for _ in range(reps):
-            m.forward(x, out)
-        e[1].record(stream)
-        for _ in range(reps):
-            m.train_step(x, y, 1e-4)
-        e[2].record(stream)
+        fwd_ms = timed(lambda: m.forward(x, out))
+        step_ms = timed(lambda: m.train_step(x, y, 1e-4))
         m.use_tcgen05(False)
-        for _ in range(reps):
-            m.forward(x, out)
-        e[3].record(stream)
-        m.sync()
-        torch.cuda.synchronize()
-    fwd_ms = e[0].elapsed_time(e[1]) / reps
-    step_ms = e[1].elapsed_time(e[2]) / reps
-    fwd_mma_ms = e[2].elapsed_time(e[3]) / reps
+        fwd_mma_ms = timed(lambda: m.forward(x, out))
     m.close()
     f = mlp_flops_per_sample(sizes)
     peak, kind = measured_peak_bf16()
@@ -332,9 +350,11 @@ def run_surrogate(args):
     train_tf = 3 * f * B / (step_ms / 1e3) / 1e12
     return {"workload": w["name"] + f", batch {B}", "forward_ms": fwd_ms, "train_step_ms": step_ms,
             "forward_ms_mma_sync_path": fwd_mma_ms, "samples_per_s": B / (fwd_ms / 1e3), "flops_per_sample_forward": f,
+            "l2": "flushed before every timed call (write of twice its size)",
             "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
                          "peak_kind": kind,
                          "kernel": "mlp_forward_tc_kernel (fused tcgen05)" if tc else "gemm_bf16_kernel (mma.sync)",
+                         "traffic": traffic_from_profile(MLP_KERNEL_SOURCES, "mlp_forward_tc_b65536.md", B) if tc else None,
                          "train_step_tflops": train_tf}}
 
 
@@ -415,7 +435,8 @@ def run_batched(args):
     out = {"workload": "batched N=1e5 B=256 (R~U[2,6], weights~U[0.5,2], dose-2 delay~U{21..84}, own seeds)",
            "value": value, "unit": "interactions/s", "ms_per_step": ms / Kb, "steps": Kb,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "kernel": "step_batch_kernel", "alg_bytes_per_launch": alg}}
+                        "kernel": "step_batch4_kernel", "alg_bytes_per_launch": alg,
+                        "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_batch_n1e5_b256.md", n * B)}}
     if args.no_loop:
         return out
     # plain loop: the same B replicates one after another, same days

@@ -79,6 +79,7 @@ class _Model(C.Structure):
         ("vax_rate", C.c_double), ("vax_eff1", C.c_double), ("vax_eff2", C.c_double),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
         ("vax_strategy", C.c_uint32), ("elderly_bin", C.c_uint32), ("vax_nonsterile", C.c_uint32),
+        ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
     ]
 
 
@@ -120,6 +121,8 @@ def lib():
             L.or_poisson_thresholds.argtypes = [C.c_double, vp]
             L.or_random_contacts.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double, vp]
             L.or_random_contacts.restype = C.c_uint32
+            L.or_occ_contacts.argtypes = [C.POINTER(_Model), C.c_uint32, C.c_uint32, vp]
+            L.or_occ_contacts.restype = C.c_uint32
             L.or_vax_days.argtypes = [C.c_uint32, vp, C.c_uint32, C.c_double, vp]
             L.or_step.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(_Diag)]
             L.or_step.restype = C.c_int
@@ -181,7 +184,9 @@ def vax_days(age: np.ndarray, start: int, rate: float) -> np.ndarray:
 # --------------------------------------------------------------------------- the model
 class Model:
     """Graph + parameters packed for the C oracle.  ``graph`` holds ``row_ptr`` and
-    ``col`` lists (u32 CSR, destination rows) and ``n``; ``params`` is a plain dict."""
+    ``col`` lists (u32 CSR, destination rows) and ``n``, and optionally the daily
+    occupation networks: ``occ_group`` (u32 per agent) and ``occ_k`` (u8 per
+    occupation, in-contacts a day); ``params`` is a plain dict."""
 
     def __init__(self, graph: dict, params: dict):
         self.n = int(graph["n"])
@@ -224,8 +229,21 @@ class Model:
         m.vax_strategy = P.get("vax_strategy", 0)
         m.elderly_bin = P.get("elderly_bin", 6)
         m.vax_nonsterile = P.get("vax_nonsterile", 0)
+        if graph.get("occ_group") is not None:
+            og = np.ascontiguousarray(graph["occ_group"], dtype=np.uint32)
+            ok = np.ascontiguousarray(graph["occ_k"], dtype=np.uint8)
+            self._keep += [og, ok]
+            m.n_occ = ok.size
+            m.occ_group = og.ctypes.data
+            m.occ_k = ok.ctypes.data
         self.m = m
         self.params = P
+
+    def occ_contacts(self, j: int, step: int) -> np.ndarray:
+        """The daily occupation network's in-contacts of agent j on `step`."""
+        buf = np.zeros(POIS_CAP, np.uint32)
+        k = lib().or_occ_contacts(C.byref(self.m), j, step, _ptr(buf))
+        return buf[:k].copy()
 
     def inf_table(self):
         L = self.m.inf_len

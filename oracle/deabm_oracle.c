@@ -12,8 +12,10 @@
  *   inf_i      = A_{c(i)} * infT[c(i)][tinf_i]   if i is infectious and not quarantined, else 0
  *   infT[c][t] = integral_{t-1}^{t} gamma_pdf(u; shape_c, scale_c) du           (Eq. 1)
  *   H_{n,j}    = sum over the in-edges of j in static network n of inf_src, in CSR order
+ *   O_j        = sum over the day's occupation in-contacts of j of inf_src, in draw order
+ *                (optional: occupation membership fixed, contacts drawn anew each step)
  *   Rn_j       = sum over the k_j daily random in-contacts of j of inf_src, in draw order
- *   lambda_j   = (R*inv_Ibar) * S_{age_j} * (sum_n B_n H_{n,j} + B_r Rn_j)         (Eq. 1 summed)
+ *   lambda_j   = (R*inv_Ibar) * S_{age_j} * (sum_n B_n H_{n,j} + B_o O_j + B_r Rn_j)  (Eq. 1 summed)
  *   p_j        = 1 - exp(-lambda_j dt)                                             (Eq. 2, aggregated)
  *   infected   = stage_j == S  and  u_j < p_j
  * followed by the integer stage/timer machine, testing, quarantine and vaccination.
@@ -54,6 +56,7 @@ enum {
 #define SM_INF 0u     /* x: infection uniform, y: quarantine dropout */
 #define SM_PROG 1u    /* x: asymptomatic?, y: duration, z: severe?, w: secondary branch */
 #define SM_RNET 3u    /* random network: word 0 = contact count, words 1.. = contacts */
+#define SM_OCC 4u     /* daily occupation network: word e = contact e */
 #define SM_TEST 5u    /* x: test positive?, y: result delay */
 #define SM_VAX 7u     /* x: vaccine response (step word fixed at 0) */
 #define SM_GUMBEL 8u  /* relaxed draw noise */
@@ -79,6 +82,12 @@ typedef struct {
     uint32_t vax_strategy;  /* 0 static schedule; 1 standard, 2 delayed second dose, 3 delayed except elderly */
     uint32_t elderly_bin;   /* first age bin counted as "65+" by strategy 3 */
     uint32_t vax_nonsterile; /* 1: immunity is non-sterilising (Sec. 5, second version) */
+    /* daily occupation networks (Sec. 3, Interaction Networks: fixed membership,
+     * contacts drawn anew every step); n_occ = 0: none.  Its weight is
+     * B_net[n_nets], after the stored networks. */
+    uint32_t n_occ;
+    const uint32_t *occ_group; /* [n] occupation of each agent, < n_occ */
+    const uint8_t *occ_k;      /* [n_occ] in-contacts per agent per step, <= 15 */
 } or_model;
 
 /* ------------------------------------------------------------------------- */
@@ -337,6 +346,13 @@ static int check_model(const or_model *m)
     if (m->quar_days > 15 || m->test_hi > 7 || m->test_lo < 1 || m->test_lo > m->test_hi) return -1;
     if (m->rand_mean > 0.0f && m->n < 2) return -1;
     if (m->vax_strategy > 3 || m->elderly_bin > 9) return -1;
+    if (m->n_occ) {
+        if (m->n_nets >= OR_MAX_NETS || !m->occ_group || !m->occ_k) return -1;
+        for (uint32_t g = 0; g < m->n_occ; ++g)
+            if (m->occ_k[g] > OR_POIS_CAP) return -1;
+        for (uint32_t j = 0; j < m->n; ++j)
+            if (m->occ_group[j] >= m->n_occ) return -1;
+    }
     return 0;
 }
 
@@ -399,6 +415,60 @@ static void select_doses(const or_model *m, const uint8_t *age, uint32_t t, cons
     free(c);
 }
 
+/* Members of every occupation in ascending agent id: members[start[g] ..
+ * start[g+1]) are the agents of occupation g, pos[j] is j's place among them. */
+typedef struct {
+    uint32_t *start, *members, *pos;
+} or_occ;
+
+static void occ_build(const or_model *m, or_occ *o)
+{
+    const uint32_t n = m->n, G = m->n_occ;
+    o->start = (uint32_t *)calloc(G + 1u, sizeof(uint32_t));
+    o->members = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    o->pos = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *fill = (uint32_t *)calloc(G + 1u, sizeof(uint32_t));
+    for (uint32_t j = 0; j < n; ++j) o->start[m->occ_group[j] + 1u]++;
+    for (uint32_t g = 0; g < G; ++g) o->start[g + 1u] += o->start[g];
+    for (uint32_t j = 0; j < n; ++j) { /* j ascending: members stay sorted */
+        const uint32_t g = m->occ_group[j];
+        o->pos[j] = fill[g];
+        o->members[o->start[g] + fill[g]++] = j;
+    }
+    free(fill);
+}
+
+static void occ_free(or_occ *o) { free(o->start); free(o->members); free(o->pos); }
+
+/* the day's occupation in-contacts of agent j: occ_k[g] of them (none for a
+ * lone member), each uniform over the other members of j's occupation, from
+ * word e of the SM_OCC stream (block e/4, lane e%4). */
+static uint32_t occ_contacts(const or_model *m, const or_occ *o, uint32_t j, uint32_t step, uint32_t *contacts)
+{
+    const uint32_t g = m->occ_group[j];
+    const uint32_t beg = o->start[g], size = o->start[g + 1u] - beg;
+    if (size < 2u) return 0;
+    const uint32_t k = m->occ_k[g];
+    for (uint32_t e = 0; e < k; ++e) {
+        uint32_t blk[4];
+        draw4(m->net_seed, j, step, SM_OCC, e / 4u, blk);
+        uint32_t r = (uint32_t)(((uint64_t)blk[e % 4u] * (uint64_t)(size - 1u)) >> 32);
+        if (r >= o->pos[j]) r += 1u;
+        contacts[e] = o->members[beg + r];
+    }
+    return k;
+}
+
+uint32_t or_occ_contacts(const or_model *m, uint32_t j, uint32_t step, uint32_t *contacts)
+{
+    if (check_model(m) || !m->n_occ || j >= m->n) return 0;
+    or_occ o;
+    occ_build(m, &o);
+    uint32_t k = occ_contacts(m, &o, j, step, contacts);
+    occ_free(&o);
+    return k;
+}
+
 static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age, const int16_t *vday1,
                      uint32_t t, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt,
                      int16_t *vd1, int16_t *vd2, or_diag *dg)
@@ -426,6 +496,8 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
     int64_t messages = 0;
     int32_t n_new = 0;
     uint32_t contacts[OR_POIS_CAP];
+    or_occ occ = {NULL, NULL, NULL};
+    if (m->n_occ) occ_build(m, &occ);
     for (uint32_t j = 0; j < n; ++j) {
         float s32 = 0.0f;
         double s64 = 0.0;
@@ -442,6 +514,16 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             s32 = (net == 0) ? term : s32 + term;
             s64 += (double)m->B_net[net] * h64;
         }
+        if (m->n_occ) {
+            const uint32_t ko = occ_contacts(m, &occ, j, t, contacts);
+            float h32 = 0.0f;
+            double h64 = 0.0;
+            for (uint32_t e = 0; e < ko; ++e) { h32 = h32 + inf32[contacts[e]]; h64 = h64 + inf64[contacts[e]]; }
+            float term = m->B_net[m->n_nets] * h32;
+            s32 = (m->n_nets == 0) ? term : s32 + term;
+            s64 += (double)m->B_net[m->n_nets] * h64;
+            messages += ko;
+        }
         uint32_t k = 0;
         if (m->rand_mean > 0.0f) {
             k = random_contacts(m->net_seed, n, j, t, tb->pois, contacts);
@@ -449,7 +531,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             double r64 = 0.0;
             for (uint32_t e = 0; e < k; ++e) { r32 = r32 + inf32[contacts[e]]; r64 = r64 + inf64[contacts[e]]; }
             float term = m->B_rand * r32;
-            s32 = (m->n_nets == 0) ? term : s32 + term;
+            s32 = (m->n_nets == 0 && m->n_occ == 0) ? term : s32 + term;
             s64 += (double)m->B_rand * r64;
             messages += k;
         }
@@ -578,6 +660,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         for (int s = 0; s < OR_N_STAGE; ++s) dg->hist[s] = 0;
         for (uint32_t j = 0; j < n; ++j) dg->hist[(int)stage[j]]++;
     }
+    if (m->n_occ) occ_free(&occ);
     free(inf32); free(inf64); free(newinf); free(dose_today);
     return 0;
 }

@@ -13,7 +13,11 @@ stand in for it with the shapes the paper describes:
     probabilities (.28, .35, .15, .13, .06, .03), members given consecutive ids;
   * occupation: groups of 20 drawn from a random permutation of the agents,
     each agent receiving in-links from 10 distinct members of its group;
-  * random network: regenerated every day by the method itself (not here).
+  * random network: regenerated every day by the method itself (not here);
+  * daily occupation networks (optional): 23 occupations (Sec. 3 "Agent State
+    Definition") with Dirichlet(2) shares of the agents, each with its own number
+    of in-contacts a member has a day, uniform on {5..15}; the contacts
+    themselves are drawn every day by the method (not here).
 The disease parameters are placeholders: the paper cites other work for them
 (Sec. 3 "Disease Progression") and prints none.
 """
@@ -99,6 +103,31 @@ def occupation_csr(n: int, rng: np.random.Generator, group: int = 20, links: int
     return row_ptr.astype(np.uint32), col
 
 
+N_OCCUPATION = 23
+
+
+def occupations(n: int, seed: int = 0, n_occ: int = N_OCCUPATION, k_lo: int = 5, k_hi: int = 15):
+    """Occupation of every agent (u32, fixed for the run) and the number of daily
+    in-contacts of a member of each occupation (u8)."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x0CC]))
+    share = rng.dirichlet(np.full(n_occ, 2.0))
+    group = rng.choice(n_occ, size=n, p=share).astype(np.uint32)
+    k = rng.integers(k_lo, k_hi + 1, size=n_occ, dtype=np.uint8)
+    return group, k
+
+
+def workplaces(n: int, seed: int = 0, size: int = 20, k: int = 10):
+    """Occupation groups of `size` agents from a random permutation (the last one
+    ragged), each member meeting k of them a day: the static occupation network's
+    groups with their contacts redrawn daily."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x0CD]))
+    perm = rng.permutation(n)
+    group = np.empty(n, np.uint32)
+    group[perm] = (np.arange(n) // size).astype(np.uint32)
+    n_occ = (n + size - 1) // size
+    return group, np.full(n_occ, k, np.uint8)
+
+
 def population(n: int, seed: int = 0, n_seed_infections: int = 10) -> dict:
     """Ages, household and occupation CSRs and the initial cases for n agents."""
     rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x5EED]))
@@ -166,6 +195,21 @@ def plain_large():
     of symptomatic agents, vaccination of 1% of agents a day from day 30."""
     return dict(name="plain N=2e6 T=180", n=2_000_000, T=180, n_seed=10_000,
                 params=params_with(test_on=1, quar_on=1, vax_on=1, vax_start=30, vax_rate=0.01))
+
+
+def population_daily_occupation(n: int, seed: int = 0, n_seed_infections: int = 10) -> dict:
+    """Households as a stored network and the 23 occupations as daily networks."""
+    pop = population(n, seed, n_seed_infections)
+    pop["row_ptr"], pop["col"] = pop["row_ptr"][:1], pop["col"][:1]
+    pop["occ_group"], pop["occ_k"] = occupations(n, seed)
+    return pop
+
+
+def plain_daily_occupation():
+    """The N=2e6 plain workload with its occupation network redrawn every day:
+    23 occupations, 5-15 daily in-contacts per member by occupation."""
+    w = plain_large()
+    return dict(w, name="plain N=2e6 T=180, daily occupation networks (23 occupations)")
 
 
 def batch_params(B: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
