@@ -80,6 +80,8 @@ class _Model(C.Structure):
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
         ("vax_strategy", C.c_uint32), ("elderly_bin", C.c_uint32), ("vax_nonsterile", C.c_uint32),
         ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
+        ("den_on", C.c_uint32), ("den_adoption", C.c_double), ("den_compliance", C.c_double),
+        ("den_window", C.c_uint32),
     ]
 
 
@@ -88,6 +90,7 @@ class _Diag(C.Structure):
         ("lambda32", C.c_void_p), ("lambda64", C.c_void_p), ("p32", C.c_void_p), ("u32", C.c_void_p),
         ("inf32", C.c_void_p), ("near", C.c_void_p), ("rand_k", C.c_void_p),
         ("new_inf", C.c_int32), ("messages", C.c_int64), ("hist", C.c_int32 * N_STAGE),
+        ("den_notified", C.c_int32),
     ]
 
 
@@ -129,7 +132,8 @@ def lib():
             L.or_seed_infections.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, vp, vp, vp]
             L.or_seed_infections.restype = C.c_int
             L.or_run.argtypes = [C.POINTER(_Model), vp, vp, C.c_uint32, C.c_uint32,
-                                 vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+                                 vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.or_den_apps.argtypes = [C.POINTER(_Model), vp]
             L.or_run.restype = C.c_int
             L.rx_run.argtypes = [C.POINTER(_RxModel), vp, vp, C.c_uint32, C.c_uint32, vp, vp, vp, vp, vp, vp]
             L.rx_run.restype = C.c_int
@@ -229,6 +233,10 @@ class Model:
         m.vax_strategy = P.get("vax_strategy", 0)
         m.elderly_bin = P.get("elderly_bin", 6)
         m.vax_nonsterile = P.get("vax_nonsterile", 0)
+        m.den_on = P.get("den_on", 0)
+        m.den_adoption = P.get("den_adoption", 0.3)
+        m.den_compliance = P.get("den_compliance", 0.8)
+        m.den_window = P.get("den_window", 7)
         if graph.get("occ_group") is not None:
             og = np.ascontiguousarray(graph["occ_group"], dtype=np.uint32)
             ok = np.ascontiguousarray(graph["occ_k"], dtype=np.uint8)
@@ -291,6 +299,9 @@ class Sim:
             self.vday1 = np.full(self.n, 0x7FFF, np.int16)
         self.state = state.copy() if state is not None else State(self.n)
         self.t = 0
+        self.den_notified = []  # per step: app holders notified (Sec. 4.2)
+        if params.get("den_on", 0):
+            lib().or_den_apps(C.byref(self.model.m), _ptr(self.state.flags))
         if seed_ids is not None and len(seed_ids):
             ids = np.ascontiguousarray(seed_ids, dtype=np.uint32)
             s = self.state
@@ -315,6 +326,8 @@ class Sim:
         out["new_inf"] = int(d.new_inf)
         out["messages"] = int(d.messages)
         out["hist"] = np.array(list(d.hist), np.int32)
+        out["den_notified"] = int(d.den_notified)
+        self.den_notified.append(out["den_notified"])
         out["t"] = self.t
         self.t += 1
         return out
@@ -323,10 +336,12 @@ class Sim:
         new_inf = np.zeros(T, np.int32)
         hist = np.zeros((T, N_STAGE), np.int32)
         msgs = np.zeros(T, np.int64)
+        den = np.zeros(T, np.int32)
         rc = lib().or_run(C.byref(self.model.m), _ptr(self.age), _ptr(self.vday1), self.t, T,
-                          *self.state.ptrs(), _ptr(new_inf), _ptr(hist), _ptr(msgs))
+                          *self.state.ptrs(), _ptr(new_inf), _ptr(hist), _ptr(msgs), _ptr(den))
         if rc != 0:
             raise ValueError("oracle rejected the model parameters")
+        self.den_notified += den.tolist()
         self.t += T
         return new_inf, hist, msgs
 

@@ -47,6 +47,8 @@ enum {
 #define FL_DOSE2 0x02u
 #define FL_POS 0x04u
 #define FL_IMMUNE 0x08u  /* non-sterilising vaccine immunity: infections are asymptomatic (Sec. 5) */
+#define FL_DEN 0x10u     /* exposure notification received: test on the next step (Sec. 4.2) */
+#define FL_APP 0x20u     /* holds the exposure-notification app (Sec. 4.2) */
 /* qt byte: low nibble = quarantine days left, bits 4..6 = days until the test result */
 #define QT_QDAYS(q) ((q) & 0x0Fu)
 #define QT_TCD(q) (((q) >> 4) & 0x07u)
@@ -58,6 +60,7 @@ enum {
 #define SM_RNET 3u    /* random network: word 0 = contact count, words 1.. = contacts */
 #define SM_OCC 4u     /* daily occupation network: word e = contact e */
 #define SM_TEST 5u    /* x: test positive?, y: result delay */
+#define SM_DEN 6u     /* x: complies with a notification; step word 0xFFFFFFFD: x = holds the app */
 #define SM_VAX 7u     /* x: vaccine response (step word fixed at 0) */
 #define SM_GUMBEL 8u  /* relaxed draw noise */
 
@@ -88,6 +91,10 @@ typedef struct {
     uint32_t n_occ;
     const uint32_t *occ_group; /* [n] occupation of each agent, < n_occ */
     const uint8_t *occ_k;      /* [n_occ] in-contacts per agent per step, <= 15 */
+    /* digital exposure notification (Sec. 4.2) */
+    uint32_t den_on;
+    double den_adoption, den_compliance;
+    uint32_t den_window;       /* steps of contacts looked back over, >= 1 */
 } or_model;
 
 /* ------------------------------------------------------------------------- */
@@ -328,6 +335,7 @@ typedef struct {
     int32_t new_inf;
     int64_t messages;  /* household+occupation+random in-edges processed */
     int32_t hist[OR_N_STAGE];
+    int32_t den_notified;  /* app holders notified at the end of this step */
 } or_diag;
 
 /*
@@ -346,6 +354,7 @@ static int check_model(const or_model *m)
     if (m->quar_days > 15 || m->test_hi > 7 || m->test_lo < 1 || m->test_lo > m->test_hi) return -1;
     if (m->rand_mean > 0.0f && m->n < 2) return -1;
     if (m->vax_strategy > 3 || m->elderly_bin > 9) return -1;
+    if (m->den_on && (!m->test_on || m->den_window < 1 || m->den_window > 64)) return -1;
     if (m->n_occ) {
         if (m->n_nets >= OR_MAX_NETS || !m->occ_group || !m->occ_k) return -1;
         for (uint32_t g = 0; g < m->n_occ; ++g)
@@ -556,6 +565,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
 
     /* dose selection of the priority strategies, from the state at the start of the day */
     uint8_t *dose_today = NULL;
+    uint8_t *den_src = m->den_on ? (uint8_t *)calloc(n ? n : 1, 1) : NULL; /* positive app holders of the step */
     if (m->vax_on && m->vax_strategy != 0 && t >= m->vax_start) {
         dose_today = (uint8_t *)malloc(n ? n : 1);
         select_doses(m, age, t, stage, flags, vd1, dose_today);
@@ -608,16 +618,21 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         if (cd > 0) {
             cd -= 1;
             if (cd == 0) {
-                if ((fl & FL_POS) && m->quar_on) qd = m->quar_days;
+                if (fl & FL_POS) {
+                    if (m->quar_on) qd = m->quar_days;
+                    if (den_src && (fl & FL_APP)) den_src[j] = 1; /* notifies its contacts (Sec. 4.2) */
+                }
                 fl &= ~FL_POS;
             }
-        } else if (onset && m->test_on && qd == 0) {
-            /* symptom onset: take a test */
+        } else if ((onset || (fl & FL_DEN)) && m->test_on && qd == 0) {
+            /* symptom onset, or yesterday's exposure notification: take a test.
+             * Only an infected agent in the community can test positive. */
             uint32_t w[4];
             draw4(m->seed, j, t, SM_TEST, 0, w);
-            if (happens(w[0], m->test_sens)) fl |= FL_POS; else fl &= ~FL_POS;
+            if (st >= ST_ASYM && st <= ST_SEV && happens(w[0], m->test_sens)) fl |= FL_POS; else fl &= ~FL_POS;
             cd = uniform_int(w[1], m->test_lo, m->test_hi);
         }
+        fl &= ~FL_DEN; /* a notification is acted on the next step or not at all */
 
         /* vaccination (Sec. 4.4 and Sec. 5) */
         if (m->vax_on && m->vax_strategy != 0) {
@@ -654,7 +669,44 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         qt[j] = QT_MAKE(qd, cd);
     }
 
+    /* digital exposure notification (Sec. 4.2), after every agent's update: an app
+     * holder in the community and out of quarantine is notified when one of its
+     * in-contacts of the last den_window steps (this one included) had a positive
+     * result this step and holds the app; it complies with probability
+     * den_compliance and is then tested on the next step. */
+    int32_t n_notified = 0;
+    if (den_src) {
+        for (uint32_t j = 0; j < n; ++j) {
+            const int st = stage[j];
+            if (!(flags[j] & FL_APP) || QT_QDAYS(qt[j]) > 0 || st == ST_HOSP || st == ST_ICU || st == ST_DEAD)
+                continue;
+            int hit = 0;
+            for (uint32_t net = 0; net < m->n_nets && !hit; ++net)
+                for (uint32_t e = m->row_ptr[net][j]; e < m->row_ptr[net][j + 1] && !hit; ++e)
+                    hit = den_src[m->col[net][e]];
+            const uint32_t d0 = t + 1u > m->den_window ? t + 1u - m->den_window : 0u;
+            for (uint32_t d = d0; d <= t && !hit; ++d) {
+                uint32_t k;
+                if (m->n_occ) {
+                    k = occ_contacts(m, &occ, j, d, contacts);
+                    for (uint32_t e = 0; e < k && !hit; ++e) hit = den_src[contacts[e]];
+                }
+                if (m->rand_mean > 0.0f) {
+                    k = random_contacts(m->net_seed, n, j, d, tb->pois, contacts);
+                    for (uint32_t e = 0; e < k && !hit; ++e) hit = den_src[contacts[e]];
+                }
+            }
+            if (!hit) continue;
+            ++n_notified;
+            uint32_t w[4];
+            draw4(m->seed, j, t, SM_DEN, 0, w);
+            if (happens(w[0], m->den_compliance)) flags[j] |= FL_DEN;
+        }
+        free(den_src);
+    }
+
     if (dg) {
+        dg->den_notified = n_notified;
         dg->new_inf = n_new;
         dg->messages = messages;
         for (int s = 0; s < OR_N_STAGE; ++s) dg->hist[s] = 0;
@@ -699,7 +751,7 @@ int or_seed_infections(const or_model *m, const uint8_t *age, const uint32_t *id
 /* T steps from t0; new_inf[T], hist[T][11], messages[T] (NULL to skip) */
 int or_run(const or_model *m, const uint8_t *age, const int16_t *vday1, uint32_t t0, uint32_t T,
            int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt, int16_t *vd1, int16_t *vd2,
-           int32_t *new_inf, int32_t *hist, int64_t *messages)
+           int32_t *new_inf, int32_t *hist, int64_t *messages, int32_t *den_notified)
 {
     if (check_model(m)) return -1;
     or_tables tb;
@@ -712,6 +764,20 @@ int or_run(const or_model *m, const uint8_t *age, const int16_t *vday1, uint32_t
         if (new_inf) new_inf[s] = dg.new_inf;
         if (hist) memcpy(hist + (size_t)s * OR_N_STAGE, dg.hist, sizeof dg.hist);
         if (messages) messages[s] = dg.messages;
+        if (den_notified) den_notified[s] = dg.den_notified;
     }
     return 0;
+}
+
+/* exposure-notification app holders (Sec. 4.2), drawn once at initialisation:
+ * agent j holds the app when word x of (seed, j, step word 0xFFFFFFFD, SM_DEN)
+ * falls under den_adoption; sets or clears FL_APP in flags */
+void or_den_apps(const or_model *m, uint8_t *flags)
+{
+    for (uint32_t j = 0; j < m->n; ++j) {
+        uint32_t w[4];
+        draw4(m->seed, j, 0xFFFFFFFDu, SM_DEN, 0, w);
+        if (happens(w[0], m->den_adoption)) flags[j] |= FL_APP;
+        else flags[j] &= (uint8_t)~FL_APP;
+    }
 }

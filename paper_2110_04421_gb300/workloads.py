@@ -171,6 +171,7 @@ def default_params() -> dict:
         vax_strategy=0,   # 0 static age-priority schedule; 1 standard, 2 delayed second dose, 3 delayed except 65+
         elderly_bin=6,    # first age bin treated as "65+" (the 61-70 bin holds Table 1's 68-year-olds)
         vax_nonsterile=0, # 1: vaccine immunity is non-sterilising (infections become asymptomatic)
+        den_on=0, den_adoption=0.3, den_compliance=0.8, den_window=7,  # exposure notification (Sec. 4.2, 4.5)
         seed=0, net_seed=0,
     )
 
