@@ -56,6 +56,13 @@ def step_bytes_batch(n: int, B: int, static_edges: int, n_nets: int, vax: bool) 
     return 4 * (n + 1) * n_nets + 4 * static_edges + n * (1 + (2 if vax else 0)) + n * B * (7 + 7 + 4 + 4)
 
 
+def step_bytes_occ(n: int, static_edges: int, n_nets: int, n_occ: int, vax: bool) -> int:
+    """The plain day with its occupation network drawn daily: the stored networks'
+    bytes as above, plus each agent's occupation (4 B) and each occupation's
+    first row and daily count (4 + 1 B).  The day's contacts are generated: 0 B."""
+    return step_bytes_plain(n, static_edges, n_nets, vax) + 4 * n + 5 * n_occ + 4
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -201,6 +208,7 @@ def run_ours(args, rank, world, local):
     relaxed = run_relaxed(args) if (rank == 0 and not args.no_relaxed) else None
     surrogate = run_surrogate(args) if (rank == 0 and not args.no_surrogate) else None
     ragged = run_ragged(args) if (rank == 0 and not args.no_ragged) else None
+    occupation = run_occupation(args) if (rank == 0 and not args.no_occupation) else None
 
     if rank == 0:
         value = messages / (total_ms / 1e3)
@@ -242,6 +250,8 @@ def run_ours(args, rank, world, local):
             line["surrogate"] = surrogate
         if ragged:
             line["ragged"] = ragged
+        if occupation:
+            line["daily_occupation"] = occupation
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -403,6 +413,47 @@ def run_ragged(args):
             "loop_of_plain_launches_ms_per_step": ms_loop / T, "multiple_of_plain_loop": ms_loop / ms}
 
 
+def run_occupation(args):
+    """The N=2e6 plain workload with its occupation network redrawn every day
+    (23 occupations, 5-15 contacts a member): households stored, occupations and
+    random network generated in the day kernel."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Simulation
+
+    w = W.plain_daily_occupation()
+    n = w["n"]
+    K = max(3, min(args.occupation_steps, args.steps))
+    pop = W.population_daily_occupation(n, 0, w["n_seed"])
+    static_edges = int(sum(int(r[-1]) for r in pop["row_ptr"]))
+    stream = torch.cuda.Stream()
+    sim = Simulation(pop, w["params"], pop["age"], pop["seed_ids"], max_steps=args.warmup + K,
+                     stream=stream.cuda_stream)
+    sim.step(args.warmup)
+    sim.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        sim.step(1)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    per_day = [e0.elapsed_time(e1) for e0, e1 in ev]
+    _, _, msgs = sim.counters()
+    sim.close()
+    ms = sum(per_day)
+    msg = int(msgs[args.warmup:args.warmup + K].astype(np.int64).sum())
+    alg = step_bytes_occ(n, static_edges, len(pop["row_ptr"]), int(pop["occ_k"].size), True)
+    peak, _ = measured_peak_hbm()
+    avg = ms / K
+    achieved = alg / (avg / 1e3) / 1e9
+    return {"workload": w["name"], "value": msg / (ms / 1e3), "unit": "interactions/s", "ms_per_step": avg,
+            "steps": K, "messages_per_day": msg / K,
+            "l2": f"inputs larger than L2: {alg / 1e6:.0f} MB algorithmic per day, no flush",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "step_plain_kernel (daily occupation networks)", "alg_bytes_per_launch": alg,
+                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_occ_n2e6.md", n)}}
+
+
 def run_batched(args):
     import torch
     from paper_2110_04421_gb300 import workloads as W
@@ -538,8 +589,11 @@ def main():
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--no-occupation", action="store_true")
+    ap.add_argument("--occupation-steps", type=int, default=20)
     ap.add_argument("--calib-steps", type=int, default=200)
-    ap.add_argument("--only", default="all", choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged"],
+    ap.add_argument("--only", default="all",
+                    choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged", "occupation"],
                     help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -552,12 +606,13 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps(run_batched(args)))
         return
-    if args.only in ("relaxed", "surrogate", "ragged"):
+    if args.only in ("relaxed", "surrogate", "ragged", "occupation"):
         import __graft_entry__
         __graft_entry__.build()
         import torch
         torch.cuda.set_device(local)
-        fn = {"relaxed": run_relaxed, "surrogate": run_surrogate, "ragged": run_ragged}[args.only]
+        fn = {"relaxed": run_relaxed, "surrogate": run_surrogate, "ragged": run_ragged,
+              "occupation": run_occupation}[args.only]
         print(json.dumps(fn(args)))
         return
     if args.only == "plain":
@@ -565,6 +620,7 @@ def main():
         args.no_relaxed = True
         args.no_surrogate = True
         args.no_ragged = True
+        args.no_occupation = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

@@ -66,6 +66,8 @@ enum {
 #define DEABM_FL_DOSE2 0x02u
 #define DEABM_FL_POS 0x04u
 #define DEABM_FL_IMMUNE 0x08u  /* non-sterilising vaccine immunity (vax_nonsterile) */
+#define DEABM_FL_DEN 0x10u     /* exposure notification received: tested on the next day (den_on) */
+#define DEABM_FL_APP 0x20u     /* holds the exposure-notification app (den_on; drawn by the library) */
 /* qt byte: bits 0..3 quarantine days left (0 = not quarantined),
  *          bits 4..6 days until a pending test result (0 = none) */
 
@@ -79,13 +81,30 @@ typedef struct deabm_ctx deabm_ctx;
  * e in [row_ptr[j], row_ptr[j+1]).  The in-edges of a row are summed in the
  * order listed.  rand_mean > 0 adds the daily random network: each agent j
  * receives K_j ~ Poisson(rand_mean) (capped at DEABM_POIS_CAP) in-contacts
- * drawn uniformly from the other agents, regenerated every day. */
+ * drawn uniformly from the other agents, regenerated every day.
+ *
+ * n_occ > 0 adds the daily occupation networks (Sec. 3 "Interaction Networks":
+ * an agent's occupation is fixed, whom it meets there changes every day).
+ * occ_group[j] < n_occ is agent j's occupation (host array of n_agents); every
+ * day a member of occupation g receives occ_k[g] <= DEABM_POIS_CAP in-contacts
+ * (host array of n_occ), each uniform over the other members of g (none for a
+ * lone member), contact e from word e of Philox stream 4 keyed by (net_seed,
+ * day, agent) -- block e/4, lane e%4 -- mapped to the member in place
+ * floor(word * (size-1) / 2^32), skipping the agent itself, members ranked by
+ * ascending id.  Their sum enters Eq. 1 with weight B_net[n_nets], after the
+ * stored networks and before the random network, so n_nets must be <= 3.
+ * Only plain and batched contexts take them (deabm_create, deabm_create_batch);
+ * the other constructors reject n_occ > 0.  n_occ = 0: occ_group and occ_k are
+ * ignored. */
 typedef struct {
     uint32_t n_agents;
     uint32_t n_nets;
     const uint32_t *row_ptr[DEABM_MAX_NETS];
     const uint32_t *col[DEABM_MAX_NETS];
     float rand_mean;
+    uint32_t n_occ;
+    const uint32_t *occ_group;
+    const uint8_t *occ_k;
 } deabm_graph;
 
 /* Agents (Sec. 3 "Agent State Definition"); all host arrays of n_agents entries.
@@ -157,6 +176,21 @@ typedef struct {
                                 group sit next to each other in device memory; results and
                                 every array the ABI returns are unchanged (random draws and
                                 outputs use the caller's agent ids) */
+    /* Digital exposure notification (Sec. 4.2); plain contexts with test_on only.
+     * At create (and reset) agent j gets DEABM_FL_APP when word x of Philox
+     * stream 6 keyed (seed, j, day word 0xFFFFFFFD) is below floor(den_adoption
+     * 2^32).  An app holder whose positive test result lands on day t notifies,
+     * after every agent's update of day t, each app holder that is out of
+     * quarantine, not in hospital, ICU or dead, and had it as an in-contact on one
+     * of the days max(0, t-den_window+1) .. t (stored networks, daily occupation
+     * and random networks); a notified agent sets DEABM_FL_DEN when word x of
+     * stream 6 keyed (seed, j, t) is below floor(den_compliance 2^32) and takes a
+     * test on day t+1 unless a result is pending or it is quarantined.  Any test
+     * is positive only for an agent in stages 1..5 (with probability test_sens).
+     * den_window: 1..64 days (7 in Sec. 4.2). */
+    uint32_t den_on;
+    double den_adoption, den_compliance;
+    uint32_t den_window;
 } deabm_params;
 
 /* Create a plain (one replicate) simulation.  Validates the graph (monotone
@@ -246,7 +280,8 @@ int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_see
  * are age_bin, stage, tinf, qt (n_agents entries each, caller numbering, the
  * state at the start of `day`) and the output lambda (float[n_agents]).  The
  * CSR is not validated (the rules of deabm_create apply; invalid indices are
- * the caller's error).  lambda_j equals what deabm_step computes for that day
+ * the caller's error); graph_dev->n_occ must be 0 (daily occupation networks
+ * need a context, DEABM_EINVAL otherwise).  lambda_j equals what deabm_step computes for that day
  * and state (Eq. 1 summed over the static networks and the day's random network,
  * with params' R, inv_Ibar, B_net, B_rand, S_age, A_class, infectiousness curve
  * and net_seed).
@@ -265,6 +300,11 @@ int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t *age_bin, c
                          const int16_t *tinf, const uint8_t *qt, const deabm_params *params, uint32_t day,
                          float *lambda, void *cuda_stream);
 const char *deabm_lambda_noalloc_last_error(void);
+
+/* Exposure notification (den_on): notified[d] = agents notified at the end of
+ * day d, for d < day_count (day_count <= days run; host array).  Zeros when
+ * den_on = 0.  Returns DEABM_OK, DEABM_EINVAL, DEABM_ECUDA. */
+int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *notified);
 
 /* Days run so far, agents, replicates. */
 int deabm_info(const deabm_ctx *ctx, uint32_t *day, uint32_t *n_agents, uint32_t *n_rep);

@@ -1,6 +1,6 @@
 // day_common.cuh -- per-destination infection rate of one day (Eq. 1 summed over
-// a destination's interactions): CSR sums in CSR order, the day's random
-// in-contacts generated from Philox, and their combination into lambda.
+// a destination's interactions): CSR sums in CSR order, the day's occupation
+// and random in-contacts generated from Philox, and their combination into lambda.
 // Shared by the day kernels.
 #pragma once
 #include <cstdint>
@@ -64,9 +64,47 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
     return r;
 }
 
+// Place of the member an occupation contact lands on: word x mapped to
+// [0, size-1), the agent's own place skipped.
+__device__ __forceinline__ uint32_t occ_place(uint32_t x, uint32_t size_m1, uint32_t own)
+{
+    uint32_t r = (uint32_t)(((uint64_t)x * size_m1) >> 32);
+    return r + ((r >= own) ? 1u : 0u);
+}
+
+// The day's occupation in-contacts of internal row j (caller id jo): occ_k[g]
+// of them (none for a lone member), contact e from word e of stream 4 (block
+// e/4, lane e%4).  Taken four at a time: one Philox block gives four rows whose
+// gathers are issued together, then added in draw order from +0.0f.
+__device__ __forceinline__ float occ_sum(const KParams &P, const float *__restrict__ inf, uint32_t j, uint32_t jo,
+                                         uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out)
+{
+    const uint32_t g = __ldg(P.occ_gid + j);
+    const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
+    const uint32_t k = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
+    const uint2 nk = seed_key(P.net_seed);
+    const uint32_t own = j - beg;
+    float h = 0.0f;
+    for (uint32_t e = 0; e < k; e += 4u) {
+        const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+        float v[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u)
+            v[u] = (e + u < k) ? __ldg(inf + (size_t)(beg + occ_place(x[u], size - 1u, own)) * stride + b) : 0.0f;
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u)
+            if (e + u < k) h = __fadd_rn(h, v[u]);
+    }
+    *k_out = k;
+    return h;
+}
+
 // lambda_j of one (agent, replicate) from the state of the day; j = internal row,
-// jo = the caller's id of the same agent.  The row bounds of every network are
+// jo = the caller's id of the same agent.  OCC = false compiles the daily
+// occupation networks out (for contexts that have none).  The row bounds of every network are
 // loaded first and the random contacts are generated while they are in flight.
+template <bool OCC = true>
 __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out)
 {
@@ -88,9 +126,15 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
             s = net == 0 ? term : __fadd_rn(s, term);
         }
     }
+    if (OCC && P.n_occ) {
+        uint32_t ko;
+        const float term = __fmul_rn(rp.B_net[P.n_nets], occ_sum(P, I.cur, j, jo, day, stride, b, &ko));
+        s = P.n_nets == 0 ? term : __fadd_rn(s, term);
+        *k_out += ko;
+    }
     if (P.rand_on) {
         const float term = __fmul_rn(rp.B_rand, r);
-        s = P.n_nets == 0 ? term : __fadd_rn(s, term);
+        s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
     }
     return __fmul_rn(__fmul_rn(rp.cR, rp.S_age[age]), s);
 }

@@ -32,6 +32,13 @@ struct deabm_ctx {
     bool relabel = false;
     std::vector<uint32_t> new2orig;           // internal id -> caller id (relabelled only)
     uint32_t *orig_id = nullptr;
+    // daily occupation networks (internal rows in occupation order)
+    uint32_t n_occ = 0;
+    uint32_t *occ_gid = nullptr, *occ_start = nullptr;
+    uint8_t *occ_k = nullptr;
+    // exposure notification: today's positive app holders (internal rows, caller ids), per-day counts
+    uint8_t *den_src = nullptr, *den_src_orig = nullptr;
+    int32_t *den_pos = nullptr;
     float *lam = nullptr, *p = nullptr;
     Tables *tab = nullptr;
     Rep *rep = nullptr;
@@ -130,6 +137,19 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
                 if (col[e] == j) return fail(ctx, DEABM_EINVAL, "self-loop at row %u of network %u", j, k);
             }
     }
+    if (g->n_occ) {
+        if (g->n_nets >= DEABM_MAX_NETS)
+            return fail(ctx, DEABM_EINVAL, "daily occupation networks take weight B_net[n_nets]: n_nets must be <= %d",
+                        DEABM_MAX_NETS - 1);
+        if (!g->occ_group || !g->occ_k) return fail(ctx, DEABM_EINVAL, "occ_group and occ_k are required when n_occ > 0");
+        if (g->n_occ >= (1u << 31)) return fail(ctx, DEABM_EINVAL, "n_occ too large");
+        for (uint32_t q = 0; q < g->n_occ; ++q)
+            if (g->occ_k[q] > DEABM_POIS_CAP)
+                return fail(ctx, DEABM_EINVAL, "occ_k[%u] = %u > %d", q, g->occ_k[q], DEABM_POIS_CAP);
+        for (uint32_t j = 0; j < n; ++j)
+            if (g->occ_group[j] >= g->n_occ)
+                return fail(ctx, DEABM_EINVAL, "occ_group[%u] = %u >= n_occ", j, g->occ_group[j]);
+    }
     if (!a->age_bin) return fail(ctx, DEABM_EINVAL, "age_bin is required");
     for (uint32_t j = 0; j < n; ++j)
         if (a->age_bin[j] >= DEABM_N_AGE) return fail(ctx, DEABM_EINVAL, "age_bin[%u] = %u > 8", j, a->age_bin[j]);
@@ -168,6 +188,13 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         return fail(ctx, DEABM_EINVAL, "vax_strategy must be 0..3 and elderly_bin 0..9");
     if (p->vax_strategy != 0 && n_rep != 1)
         return fail(ctx, DEABM_EINVAL, "vaccination priority strategies need a plain (one replicate) context");
+    if (p->den_on) {
+        if (n_rep != 1) return fail(ctx, DEABM_EINVAL, "exposure notification needs a plain (one replicate) context");
+        if (!p->test_on) return fail(ctx, DEABM_EINVAL, "exposure notification needs test_on");
+        if (p->den_window < 1 || p->den_window > 64) return fail(ctx, DEABM_EINVAL, "den_window must be 1..64");
+        if (!prob_ok(p->den_adoption) || !prob_ok(p->den_compliance))
+            return fail(ctx, DEABM_EINVAL, "den_adoption and den_compliance must be in [0,1]");
+    }
     if (n_rep < 1 || n_rep > 1024) return fail(ctx, DEABM_EINVAL, "n_rep must be in 1..1024");
     if (rep_params)
         for (uint32_t b = 0; b < n_rep; ++b) {
@@ -209,6 +236,21 @@ static void locality_order(const deabm_graph *g, std::vector<uint32_t> &order)
             }
         }
     }
+}
+
+// ---------------------------------------------------------------- occupation order
+// Occupations in id order, the members of each in ascending caller id: the
+// member in place r of occupation g is internal row start[g] + r, which is how
+// the day kernels map a drawn place to a row.
+static void occupation_order(const deabm_graph *g, std::vector<uint32_t> &order, std::vector<uint32_t> &start)
+{
+    const uint32_t n = g->n_agents, G = g->n_occ;
+    start.assign((size_t)G + 1, 0);
+    for (uint32_t j = 0; j < n; ++j) start[g->occ_group[j] + 1]++;
+    for (uint32_t q = 0; q < G; ++q) start[q + 1] += start[q];
+    std::vector<uint32_t> fill(start.begin(), start.end() - 1);
+    order.resize(n);
+    for (uint32_t j = 0; j < n; ++j) order[fill[g->occ_group[j]]++] = j;
 }
 
 // per-replicate parameter blocks: rep_params rows override the base parameters
@@ -259,9 +301,13 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             ctx->keep_lambda = p->keep_lambda != 0;
             cudaStream_t s = ctx->stream;
             int r;
-            ctx->relabel = p->locality_order != 0 && g->n_nets > 0;
-            std::vector<uint32_t> orig2new;
-            if (ctx->relabel) {
+            ctx->relabel = (p->locality_order != 0 && g->n_nets > 0) || g->n_occ > 0;
+            std::vector<uint32_t> orig2new, occ_start;
+            if (g->n_occ) {
+                occupation_order(g, ctx->new2orig, occ_start);
+                orig2new.resize(n);
+                for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
+            } else if (ctx->relabel) {
                 locality_order(g, ctx->new2orig);
                 orig2new.resize(n);
                 for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
@@ -296,6 +342,19 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 CU(ctx, cudaMemcpyAsync(ctx->orig_id, ctx->new2orig.data(), sizeof(uint32_t) * n,
                                         cudaMemcpyHostToDevice, s));
             }
+            if (g->n_occ) {
+                ctx->n_occ = g->n_occ;
+                std::vector<uint32_t> gid(n);
+                for (uint32_t q = 0; q < n; ++q) gid[q] = g->occ_group[ctx->new2orig[q]];
+                if ((r = dalloc(ctx, &ctx->occ_gid, n))) return r;
+                if ((r = dalloc(ctx, &ctx->occ_start, (size_t)g->n_occ + 1))) return r;
+                if ((r = dalloc(ctx, &ctx->occ_k, g->n_occ))) return r;
+                CU(ctx, cudaMemcpyAsync(ctx->occ_gid, gid.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->occ_start, occ_start.data(), sizeof(uint32_t) * ((size_t)g->n_occ + 1),
+                                        cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->occ_k, g->occ_k, g->n_occ, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaStreamSynchronize(s));  // gid is a local staging vector
+            }
             if ((r = dalloc(ctx, &ctx->age, n))) return r;
             if ((r = dalloc(ctx, &ctx->dose1, n))) return r;
             if ((r = dalloc(ctx, &ctx->S.stage, nb))) return r;
@@ -321,6 +380,14 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->C.new_inf, days * n_rep))) return r;
             if ((r = dalloc(ctx, &ctx->C.hist, days * n_rep * DEABM_N_STAGE))) return r;
             if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
+            if ((r = dalloc(ctx, &ctx->C.den, days))) return r;
+            CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
+            if (p->den_on) {
+                if ((r = dalloc(ctx, &ctx->den_src, n))) return r;
+                if (ctx->relabel && (r = dalloc(ctx, &ctx->den_src_orig, n))) return r;
+                if ((r = dalloc(ctx, &ctx->den_pos, days))) return r;
+                CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * days, s));
+            }
             CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * n_rep, s));
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
             CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
@@ -469,6 +536,21 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.vax_strategy = p->vax_strategy;
             K.vax_nonsterile = p->vax_nonsterile ? 1u : 0u;
             K.dose_today = nullptr;
+            K.n_occ = ctx->n_occ;
+            K.occ_gid = ctx->occ_gid;
+            K.occ_start = ctx->occ_start;
+            K.occ_k = ctx->occ_k;
+            K.den_on = p->den_on ? 1u : 0u;
+            K.den_window = p->den_window;
+            K.thr_comp = threshold(p->den_compliance);
+            K.thr_adopt = threshold(p->den_adoption);
+            K.den_src = ctx->den_src;
+            K.den_src_orig = ctx->den_src_orig;
+            K.den_pos = ctx->den_pos;
+            if (K.den_on) {  // app holders, part of the initial state kept for deabm_reset
+                CU(ctx, launch_den_apps(K, ctx->S, s));
+                CU(ctx, cudaMemcpyAsync(ctx->S0.flags, ctx->S.flags, nb, cudaMemcpyDeviceToDevice, s));
+            }
 
             if (a->n_seed) {
                 std::vector<uint32_t> ids(a->seed_ids, a->seed_ids + a->n_seed);
@@ -541,6 +623,7 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         I.rand_next = ctx->inf_rand[c ^ 1];
         CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
                             ctx->stream));
+        if (kp.den_on) CU(ctx, launch_den(kp, ctx->day, ctx->S, ctx->C, ctx->stream));
         ctx->cur ^= 1;
         ctx->day += 1;
     }
@@ -735,6 +818,10 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
+            if (graphs[q].n_occ)
+                return fail(ctx, DEABM_EINVAL, "daily occupation networks are not available for ragged batches");
+            if (params[q].den_on)
+                return fail(ctx, DEABM_EINVAL, "exposure notification is not available for ragged batches");
             if (params[q].vax_strategy)
                 return fail(ctx, DEABM_EINVAL, "vaccination priority strategies are not available for ragged batches");
         }
@@ -1001,6 +1088,10 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
         CU(ctx, cudaMemcpyAsync(ctx->S.vd1, ctx->S0.vd1, nb * 2, cudaMemcpyDeviceToDevice, s));
         CU(ctx, cudaMemcpyAsync(ctx->S.vd2, ctx->S0.vd2, nb * 2, cudaMemcpyDeviceToDevice, s));
     }
+    if (ctx->kp.den_on) {  // the app draw follows the (possibly new) seed
+        CU(ctx, launch_den_apps(ctx->kp, ctx->S, s));
+        CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * ctx->max_steps, s));
+    }
     if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
     ctx->cur = 0;
     CU(ctx, launch_emit(ctx->kp, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
@@ -1008,7 +1099,22 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * ctx->n_rep, s));
     CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
     CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
     ctx->day = 0;
+    return DEABM_OK;
+}
+
+extern "C" int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *notified)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (day_count > ctx->day) return fail(ctx, DEABM_EINVAL, "only %u days have run", ctx->day);
+    if (!notified || !day_count) return DEABM_OK;
+    if (ctx->ragged) {
+        std::memset(notified, 0, sizeof(int32_t) * day_count);
+        return DEABM_OK;
+    }
+    CU(ctx, cudaMemcpyAsync(notified, ctx->C.den, sizeof(int32_t) * day_count, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
     return DEABM_OK;
 }
 

@@ -15,7 +15,9 @@ enum : uint32_t {
     kStreamInf = 0,    // x: infection uniform, y: quarantine dropout
     kStreamProg = 1,   // x: asymptomatic?, y: stage duration, z: severe?, w: secondary branch
     kStreamRnet = 3,   // random network: word 0 = contact count, words 1.. = contacts
+    kStreamOcc = 4,    // daily occupation network: word e = contact e
     kStreamTest = 5,   // x: test positive?, y: result delay
+    kStreamDen = 6,    // x: complies with a notification; day word 0xFFFFFFFD: x = holds the app
     kStreamVax = 7,    // x: vaccine response (day word fixed at 0)
     kStreamGumbel = 8, // relaxed draw noise
 };
@@ -88,6 +90,20 @@ struct KParams {
     uint32_t vax_strategy;     // 0 static schedule; 1..3 priority strategies with a shared supply
     uint32_t vax_nonsterile;   // 1: immunity leaves the agent susceptible (flag), infections asymptomatic
     const uint8_t *dose_today; // priority strategies: 1 = dosed today, by caller id (nullptr: none)
+    // daily occupation networks (n_occ = 0: none).  Internal rows are in
+    // occupation order, members of one occupation consecutive and in ascending
+    // caller id, so the member in place r of occupation g is row occ_start[g] + r.
+    uint32_t n_occ;
+    const uint32_t *occ_gid;    // [n] occupation of each internal row
+    const uint32_t *occ_start;  // [n_occ + 1] first internal row of each occupation
+    const uint8_t *occ_k;       // [n_occ] daily in-contacts of a member
+    // digital exposure notification (den_on = 0: none).  den_src[row] = 1 when
+    // the agent is an app holder whose positive result landed today; the same
+    // by caller id in den_src_orig (nullptr when the ids are not relabelled).
+    uint32_t den_on, den_window;
+    uint64_t thr_comp, thr_adopt;
+    uint8_t *den_src, *den_src_orig;
+    int32_t *den_pos;           // [day] positive app holders of the day
 };
 
 // Infectiousness buffers of a day.  Static-network gathers read `cur` (internal
@@ -126,6 +142,7 @@ struct Counters {
     int32_t *new_inf;          // [day][n_rep]
     int32_t *hist;             // [day][n_rep][11]
     unsigned long long *msgs;  // [day] random in-contacts (static edges added on the host)
+    int32_t *den;              // [day] agents notified (exposure notification)
 };
 
 // ---------------------------------------------------------------- state machine
@@ -133,6 +150,7 @@ struct AgentState {
     int st, tm, ti;
     uint32_t fl, qd, cd;
     int vd1 = kNever, vd2 = kNever;
+    bool pos_result = false;  // a positive test result landed in this update
 };
 
 __device__ __forceinline__ int infector_class(int st)
@@ -194,19 +212,25 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
         if ((uint64_t)inf_y < P.thr_qdrop) a.qd = 0u;
         else a.qd -= 1u;
     }
-    // pending test result, or a test at symptom onset (Sec. 4.3)
+    // pending test result, or a test at symptom onset or after yesterday's
+    // exposure notification (Sec. 4.3, 4.2); only an infected agent in the
+    // community (stages 1..5) can test positive
     if (a.cd > 0u) {
         a.cd -= 1u;
         if (a.cd == 0u) {
-            if ((a.fl & DEABM_FL_POS) && P.quar_on) a.qd = P.quar_days;
+            if (a.fl & DEABM_FL_POS) {
+                if (P.quar_on) a.qd = P.quar_days;
+                a.pos_result = true;
+            }
             a.fl &= ~DEABM_FL_POS;
         }
-    } else if (onset && P.test_on && a.qd == 0u) {
+    } else if ((onset || (a.fl & DEABM_FL_DEN)) && P.test_on && a.qd == 0u) {
         const uint4 w = draw(key, j, day, kStreamTest);
-        if ((uint64_t)w.x < P.thr_sens) a.fl |= DEABM_FL_POS;
+        if (a.st >= DEABM_ASYM && a.st <= DEABM_SEV && (uint64_t)w.x < P.thr_sens) a.fl |= DEABM_FL_POS;
         else a.fl &= ~DEABM_FL_POS;
         a.cd = uniform_int(w.y, P.test_lo, P.test_hi);
     }
+    a.fl &= ~DEABM_FL_DEN;  // a notification is acted on the next day or not at all
     // two-dose vaccination (Sec. 4.4, Sec. 5)
     if (P.vax_on && P.vax_strategy != 0) {
         // priority strategies: today's doses were selected before the day from its starting state

@@ -33,6 +33,10 @@ size_t dose1_scratch_words(uint32_t n);
 cudaError_t launch_seed(const KParams &P, const uint32_t *ids, uint32_t n_ids, const StateRef &S, cudaStream_t stream);
 // set-up: emitted infectiousness of the current state (inf_rand: copy by caller id, or nullptr)
 cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, float *inf_rand, cudaStream_t stream);
+// exposure notification (plain contexts): app holders drawn at set-up, and the
+// notification pass that follows each day's update
+cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t stream);
+cudaError_t launch_den(const KParams &P, uint32_t day, const StateRef &S, const Counters &C, cudaStream_t stream);
 // out[i] = in[idx[i]] for i < n
 cudaError_t launch_gather_i16(int16_t *out, const int16_t *in, const uint32_t *idx, uint32_t n, cudaStream_t stream);
 

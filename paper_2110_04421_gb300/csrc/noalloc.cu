@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) na_lambda_kernel(const KParams P, const R
     I.rand_cur = inf;
     I.rand_next = nullptr;
     uint32_t k;
-    lambda[j] = lambda_of(P, rp, I, j, j, day, 1u, 0u, __ldg(P.age + j), &k);
+    lambda[j] = lambda_of<false>(P, rp, I, j, j, day, 1u, 0u, __ldg(P.age + j), &k);
 }
 
 }  // namespace deabm
@@ -153,6 +153,8 @@ extern "C" int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t 
         return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: %u agents exceed the fixed working array (%u agents max)", n,
                        (unsigned)DEABM_NOALLOC_MAX_AGENTS);
     if (graph_dev->n_nets > DEABM_MAX_NETS) return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: n_nets > 4");
+    if (graph_dev->n_occ)
+        return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: daily occupation networks need a context (n_occ must be 0)");
     for (uint32_t k = 0; k < graph_dev->n_nets; ++k)
         if (!graph_dev->row_ptr[k] || !graph_dev->col[k])
             return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: network %u has a NULL array", k);

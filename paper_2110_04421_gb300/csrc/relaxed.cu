@@ -395,6 +395,8 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
     const uint32_t n = g->n_agents;
     if (n == 0 || n >= (1u << 31) || g->n_nets > DEABM_MAX_NETS) return rx_fail(DEABM_EINVAL, "bad graph size");
     if (!(tau > 0.0f)) return rx_fail(DEABM_EINVAL, "tau must be > 0");
+    if (g->n_occ) return rx_fail(DEABM_EINVAL, "daily occupation networks are not available in the relaxed model");
+    if (p->den_on) return rx_fail(DEABM_EINVAL, "exposure notification is not available in the relaxed model");
     if (max_days == 0 || ckpt_every == 0) return rx_fail(DEABM_EINVAL, "max_days and ckpt_every must be >= 1");
     if (p->inf_len < 2 || p->inf_len > DEABM_MAX_INF_LEN) return rx_fail(DEABM_EINVAL, "inf_len must be 2..64");
     if (g->rand_mean > 0.0f && n < 2) return rx_fail(DEABM_EINVAL, "the random network needs >= 2 agents");

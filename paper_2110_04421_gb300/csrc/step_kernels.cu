@@ -4,9 +4,11 @@
 //   for every destination agent j (and replicate b in batched runs)
 //     H_{n,j}  = sum of inf_src over the CSR in-edges of j in static network n,
 //                in CSR order (left to right from +0.0f, no FMA contraction)
+//     O_j      = sum of inf_src over the day's occupation in-contacts of j
+//                (optional), generated here from Philox (never stored)
 //     Rn_j     = sum of inf_src over the K_j ~ Poisson random in-contacts of
 //                the day, generated here from Philox (never stored)
-//     lambda_j = (R/I * S_{age_j}) * (B_0 H_0 + B_1 H_1 + ... + B_r Rn_j)
+//     lambda_j = (R/I * S_{age_j}) * (B_0 H_0 + B_1 H_1 + ... + B_o O_j + B_r Rn_j)
 //     p_j      = 1 - exp(-lambda_j dt), infected iff susceptible and u_j < p_j
 //   then the agent's stage/timer machine and interventions, the agent's emitted
 //   infectiousness for the next day (written to the other half of a double
@@ -40,6 +42,7 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 // Full day for one (agent j, replicate b) at flat index i = j*stride + b.  Every
 // random draw is keyed by the caller's agent id jo, so relabelling the agents
 // inside the library changes no result.
+template <bool OCC = true>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
                                           float *p_out, int *new_stage, bool *infected, uint32_t *k_out)
@@ -47,7 +50,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     const size_t i = (size_t)j * stride + b;
     const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
     const int age = __ldg(P.age + j);
-    const float lam = lambda_of(P, rp, I, j, jo, day, stride, b, age, k_out);
+    const float lam = lambda_of<OCC>(P, rp, I, j, jo, day, stride, b, age, k_out);
     AgentState a;
     a.st = S.stage[i];
     a.tm = S.timer[i];
@@ -76,6 +79,12 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     }
     const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
     advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
+    if (P.den_on) {  // plain contexts only: a positive app holder notifies its contacts after the day
+        const uint8_t v = (a.pos_result && (a.fl & DEABM_FL_APP)) ? 1u : 0u;
+        P.den_src[j] = v;
+        if (P.den_src_orig) P.den_src_orig[jo] = v;
+        if (v) atomicAdd(P.den_pos + day, 1);
+    }
     S.stage[i] = (int8_t)a.st;
     S.timer[i] = (int16_t)a.tm;
     S.tinf[i] = (int16_t)a.ti;
@@ -123,8 +132,11 @@ __device__ __forceinline__ void count_day(bool active, int st, bool infected, ui
 #ifndef DEABM_PLAIN_BLOCK
 #define DEABM_PLAIN_BLOCK 128
 #endif
-template <bool KEEP>
-__global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
+#ifndef DEABM_OCC_MINB
+#define DEABM_OCC_MINB 10  // resident blocks per SM asked of the daily-occupation variant (swept: 8, 10, 12)
+#endif
+template <bool KEEP, bool OCC>
+__global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                          Counters C, float *lam_out, float *p_out)
 {
     __shared__ int s_hist[DEABM_N_STAGE];
@@ -152,7 +164,7 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, DEABM_PLAIN_MINB) step_plai
 #else
         const Rep &rp = P.rep[0];
 #endif
-        agent_day(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        agent_day<OCC>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
     }
     count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
     __syncthreads();
@@ -204,7 +216,8 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     if (tid == 0 && s_msgs) atomicAdd(&C.msgs[day], s_msgs);
 }
 
-// Ragged batch of independent populations in one launch: CTAs stay resident and
+// Ragged batch of independent populations in one launch (no daily occupation
+// networks): CTAs stay resident and
 // pull tiles (rows of one population) from the day's atomic queue until none is
 // left, so populations of 10^4 and 10^6 agents share the GPU without one
 // launch each.  Every row runs the plain day on its population's local ids,
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restr
             int st = 0;
             bool infected = false;
             uint32_t k = 0;
-            if (active) agent_day(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k);
+            if (active) agent_day<false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k);
             count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
         }
         __syncthreads();
@@ -326,13 +339,41 @@ __global__ void __launch_bounds__(256) step_batch4_kernel(const KParams P, uint3
                 s4[v] = net == 0 ? term : __fadd_rn(s4[v], term);
             }
         }
+        if (P.n_occ) {
+            // the day's occupation contacts, drawn once for the warp's 128 replicates
+            const uint32_t g = __ldg(P.occ_gid + j);
+            const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
+            const uint32_t ko = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
+            const uint2 nk = seed_key(P.net_seed);
+            float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (uint32_t e = 0; e < ko; e += 4u) {
+                const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
+                const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+                float4 v[4];
+#pragma unroll
+                for (uint32_t u = 0; u < 4u; ++u)
+                    v[u] = (e + u < ko) ? __ldg((const float4 *)(I.cur + (size_t)(beg + occ_place(x[u], size - 1u, j - beg)) * B + b0))
+                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (uint32_t u = 0; u < 4u; ++u)
+                    if (e + u < ko) add4(h, v[u]);
+            }
+            const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+            for (uint32_t v = 0; v < kRepPerThread; ++v) {
+                const float term = __fmul_rn(P.rep[b0 + v].B_net[P.n_nets], hv[v]);
+                s4[v] = P.n_nets == 0 ? term : __fadd_rn(s4[v], term);
+            }
+            k = ko;
+        }
         if (P.rand_on) {
             const uint2 nk = seed_key(P.net_seed);
             uint4 w = draw(nk, jo, day, kStreamRnet, 0u);
-            while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
+            uint32_t kr = 0;
+            while (kr < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kr])) ++kr;
             float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const uint64_t nm1 = (uint64_t)(P.n - 1u);
-            for (uint32_t e = 0; e < k; ++e) {
+            for (uint32_t e = 0; e < kr; ++e) {
                 const uint32_t idx = e + 1u;
                 if ((idx & 3u) == 0u) w = draw(nk, jo, day, kStreamRnet, idx >> 2);
                 const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
@@ -344,8 +385,9 @@ __global__ void __launch_bounds__(256) step_batch4_kernel(const KParams P, uint3
 #pragma unroll
             for (uint32_t v = 0; v < kRepPerThread; ++v) {
                 const float term = __fmul_rn(P.rep[b0 + v].B_rand, rv[v]);
-                s4[v] = P.n_nets == 0 ? term : __fadd_rn(s4[v], term);
+                s4[v] = (P.n_nets == 0 && P.n_occ == 0) ? term : __fadd_rn(s4[v], term);
             }
+            k += kr;
         }
         // state of the four replicates (vector loads)
         const size_t i0 = (size_t)j * B + b0;
@@ -426,8 +468,13 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
 {
     if (P.n_rep == 1) {
         const dim3 grid((P.n + DEABM_PLAIN_BLOCK - 1u) / DEABM_PLAIN_BLOCK);
-        if (lam_out) step_plain_kernel<true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
-        else step_plain_kernel<false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        if (P.n_occ) {
+            if (lam_out) step_plain_kernel<true, true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_plain_kernel<false, true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        } else {
+            if (lam_out) step_plain_kernel<true, false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_plain_kernel<false, false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        }
     } else if (P.n_rep % kRepPerThread == 0) {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 32u * kRepPerThread - 1u) / (32u * kRepPerThread));
         const dim3 block(32, 8);

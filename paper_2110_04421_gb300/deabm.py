@@ -25,7 +25,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
-           "deabm_mlp_use_tcgen05", "deabm_get_dose_days")
+           "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -39,7 +39,8 @@ class DeabmError(RuntimeError):
 class Graph(C.Structure):
     _fields_ = [("n_agents", C.c_uint32), ("n_nets", C.c_uint32),
                 ("row_ptr", C.c_void_p * MAX_NETS), ("col", C.c_void_p * MAX_NETS),
-                ("rand_mean", C.c_float)]
+                ("rand_mean", C.c_float),
+                ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p)]
 
 
 class Agents(C.Structure):
@@ -64,6 +65,8 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
         ("max_steps", C.c_uint32), ("keep_lambda", C.c_uint32), ("vax_strategy", C.c_uint32),
         ("elderly_bin", C.c_uint32), ("vax_nonsterile", C.c_uint32), ("locality_order", C.c_uint32),
+        ("den_on", C.c_uint32), ("den_adoption", C.c_double), ("den_compliance", C.c_double),
+        ("den_window", C.c_uint32),
     ]
 
 
@@ -85,6 +88,8 @@ def lib():
         L.deabm_run.argtypes = [vp, u32, vp, vp]
         L.deabm_get_state.argtypes = [vp] + [vp] * 7
         L.deabm_get_counters.argtypes = [vp, u32, vp, vp, vp]
+        L.deabm_get_notified.argtypes = [vp, u32, vp]
+        L.deabm_get_notified.restype = C.c_int
         L.deabm_get_tables.argtypes = [vp, vp, vp, vp]
         L.deabm_info.argtypes = [vp, vp, vp, vp]
         L.deabm_sync.argtypes = [vp]
@@ -186,6 +191,10 @@ def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False, local
     p.elderly_bin = P.get("elderly_bin", 6)
     p.vax_nonsterile = P.get("vax_nonsterile", 0)
     p.locality_order = 1 if locality_order else 0
+    p.den_on = P.get("den_on", 0)
+    p.den_adoption = P.get("den_adoption", 0.3)
+    p.den_compliance = P.get("den_compliance", 0.8)
+    p.den_window = P.get("den_window", 7)
     return p
 
 
@@ -200,6 +209,13 @@ def _graph_struct(graph: dict, rand_mean: float, keep: list) -> Graph:
         g.row_ptr[i] = rp.ctypes.data
         g.col[i] = cl.ctypes.data if cl.size else None
     g.rand_mean = rand_mean
+    if graph.get("occ_group") is not None:  # daily occupation networks
+        og = np.ascontiguousarray(graph["occ_group"], dtype=np.uint32)
+        ok = np.ascontiguousarray(graph["occ_k"], dtype=np.uint8)
+        keep += [og, ok]
+        g.n_occ = ok.size
+        g.occ_group = og.ctypes.data
+        g.occ_k = ok.ctypes.data
     return g
 
 
@@ -393,16 +409,7 @@ class Simulation:
         self.n = int(graph["n"])
         self.n_rep = int(n_rep)
         keep = []
-        g = Graph()
-        g.n_agents = self.n
-        g.n_nets = len(graph["row_ptr"])
-        for i, (rp, cl) in enumerate(zip(graph["row_ptr"], graph["col"])):
-            rp = np.ascontiguousarray(rp, dtype=np.uint32)
-            cl = np.ascontiguousarray(cl, dtype=np.uint32)
-            keep += [rp, cl]
-            g.row_ptr[i] = rp.ctypes.data
-            g.col[i] = cl.ctypes.data if cl.size else None
-        g.rand_mean = params["rand_mean"]
+        g = _graph_struct(graph, params["rand_mean"], keep)
         a = Agents()
         age = np.ascontiguousarray(age, dtype=np.uint8)
         keep.append(age)
@@ -493,6 +500,13 @@ class Simulation:
         m = np.zeros(days, np.uint64)
         _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
         return ni, h, m
+
+    def notified(self, days: int | None = None) -> np.ndarray:
+        """Agents notified by exposure notification at the end of each day."""
+        days = self.day if days is None else days
+        out = np.zeros(days, np.int32)
+        _check(lib().deabm_get_notified(self.ctx, days, _p(out)), self.ctx)
+        return out
 
     def tables(self, inf_len: int):
         t = np.zeros((N_CLASS, inf_len), np.float32)

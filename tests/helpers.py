@@ -77,6 +77,9 @@ def compare_days(pop, params, T, state=None, seed_ids="pop", check_lambda=True):
         ni, h, m = g.counters(T)
         assert ni[:, 0].tolist() == report["new_inf"]
         assert m.astype(np.int64).tolist() == report["messages"]
+        if params.get("den_on"):
+            assert g.notified(T).tolist() == osim.den_notified[:T]
+            report["notified"] = osim.den_notified[:T]
         return report
     finally:
         g.close()

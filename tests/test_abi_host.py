@@ -43,10 +43,15 @@ def _graph(n, rp, col, rand_mean=2.0):
     return g
 
 
-def _create(lib, n, rp, col, age, params=None, rand_mean=2.0, stage=None):
+def _create(lib, n, rp, col, age, params=None, rand_mean=2.0, stage=None, occ=None):
     from paper_2110_04421_gb300 import workloads as W
     from paper_2110_04421_gb300.deabm import Agents, make_params
     g = _graph(n, rp, col, rand_mean)
+    if occ is not None:  # (occ_group, occ_k, n_nets)
+        g.n_occ, g.occ_group, g.occ_k = occ[1].size, occ[0].ctypes.data, occ[1].ctypes.data
+        g.n_nets = occ[2]
+        for q in range(1, occ[2]):
+            g.row_ptr[q], g.col[q] = rp.ctypes.data, col.ctypes.data
     a = Agents()
     a.age_bin = age.ctypes.data
     if stage is not None:
@@ -59,15 +64,32 @@ def _create(lib, n, rp, col, age, params=None, rand_mean=2.0, stage=None):
 
 @pytest.mark.parametrize("case", ["self_loop", "col_out_of_range", "row_ptr_decreases", "row_ptr_start",
                                   "bad_age", "bad_stage", "bad_test_delay", "bad_quarantine", "bad_prob",
-                                  "random_net_single_agent"])
+                                  "random_net_single_agent", "occ_group_out_of_range", "occ_k_too_large",
+                                  "occ_without_weight_slot", "den_without_testing", "den_bad_window",
+                                  "den_bad_adoption"])
 def test_create_rejects_invalid_input(lib, case):
     from paper_2110_04421_gb300 import workloads as W
     n = 4
     rp = np.array([0, 1, 2, 3, 4], np.uint32)
     col = np.array([1, 2, 3, 0], np.uint32)
     age = np.zeros(n, np.uint8)
-    params, stage, rand_mean = None, None, 2.0
-    if case == "self_loop":
+    params, stage, rand_mean, occ = None, None, 2.0, None
+    occ_group, occ_k = np.array([0, 1, 1, 0], np.uint32), np.array([3, 15], np.uint8)
+    if case == "occ_group_out_of_range":
+        occ_group[2] = 2
+        occ = (occ_group, occ_k, 1)
+    elif case == "occ_k_too_large":
+        occ_k[1] = 16
+        occ = (occ_group, occ_k, 1)
+    elif case == "occ_without_weight_slot":  # four stored networks leave no B_net entry for it
+        occ = (occ_group, occ_k, 4)
+    elif case == "den_without_testing":
+        params = W.params_with(den_on=1, test_on=0)
+    elif case == "den_bad_window":
+        params = W.params_with(den_on=1, test_on=1, den_window=0)
+    elif case == "den_bad_adoption":
+        params = W.params_with(den_on=1, test_on=1, den_adoption=1.5)
+    elif case == "self_loop":
         col[2] = 2
     elif case == "col_out_of_range":
         col[1] = 4
@@ -87,7 +109,7 @@ def test_create_rejects_invalid_input(lib, case):
         params = W.params_with(p_sev=[1.5] * 9)
     elif case == "random_net_single_agent":
         n, rp, col, age = 1, np.array([0, 0], np.uint32), np.zeros(1, np.uint32), np.zeros(1, np.uint8)
-    rc, ctx, msg = _create(lib, n, rp, col, age, params, rand_mean, stage)
+    rc, ctx, msg = _create(lib, n, rp, col, age, params, rand_mean, stage, occ)
     assert rc == -1, (case, rc, msg)
     assert ctx.value is None and msg
 
@@ -107,3 +129,20 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(deabm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         deabm.lib()
+
+
+def test_binding_passes_daily_occupations(lib):
+    """The Python binding hands the occupation arrays to the library: an invalid
+    daily count is rejected by the library's host validation, before any CUDA call."""
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import DeabmError, Simulation
+    pop = W.population_daily_occupation(60, 1, 3)
+    pop["occ_k"] = pop["occ_k"].copy()
+    pop["occ_k"][0] = 16
+    with pytest.raises(DeabmError, match="occ_k"):
+        Simulation(pop, W.params_with(), pop["age"], pop["seed_ids"])
+    pop["occ_k"][0] = 5
+    pop["occ_group"] = pop["occ_group"].copy()
+    pop["occ_group"][7] = pop["occ_k"].size
+    with pytest.raises(DeabmError, match="occ_group"):
+        Simulation(pop, W.params_with(), pop["age"], pop["seed_ids"])

@@ -1,0 +1,96 @@
+"""Digital exposure notification (Sec. 4.2) on the GPU against the CPU oracle,
+through the C-ABI: app holders, notifications, the tests they trigger and the
+per-day notification counts, bit-exact."""
+import numpy as np
+import pytest
+
+from paper_2110_04421_gb300 import workloads as W
+from tests.helpers import compare_days, gpu_available, gpu_sim, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+if not gpu_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def den_params(**kw):
+    base = dict(test_on=1, quar_on=1, den_on=1, den_adoption=0.3, den_compliance=0.8, R=3.5, seed=11, net_seed=12)
+    base.update(kw)
+    return W.params_with(**base)
+
+
+@pytest.mark.parametrize("locality_order", [True, False])
+def test_stored_networks(locality_order):
+    pop = W.population(10_000, 4, 30)
+    rep = compare_days(pop, den_params(), 60) if locality_order else None
+    if not locality_order:
+        from tests.helpers import STATE_KEYS
+        p = den_params()
+        o = oracle_sim(pop, p)
+        g = gpu_sim(pop, p, keep_lambda=False, max_steps=60, locality_order=False)
+        ni, h = g.run(60)
+        s = g.state()
+        den = g.notified()
+        g.close()
+        ni_o, h_o, _ = o.run(60)
+        assert np.array_equal(ni[:, 0], ni_o) and np.array_equal(h[:, 0], h_o)
+        for k in STATE_KEYS:
+            assert np.array_equal(s[k], getattr(o.state, k)), k
+        assert den.tolist() == o.den_notified
+        rep = dict(flips=0, days=60, notified=o.den_notified)
+    assert rep["flips"] == 0 and rep["days"] == 60, rep
+    assert sum(rep["notified"]) > 100
+
+
+def test_daily_occupations_and_full_adoption():
+    pop = W.population_daily_occupation(8_000, 5, 25)
+    p = den_params(den_adoption=1.0, den_compliance=1.0, vax_on=1, vax_start=20, vax_rate=0.01, q_dropout=0.05)
+    rep = compare_days(pop, p, 50)
+    assert rep["flips"] == 0 and rep["days"] == 50, rep
+    assert sum(rep["notified"]) > 100
+
+
+def test_short_window_random_network_only():
+    n = 6_001
+    pop = W.population(n, 6, 40)
+    g = dict(pop, row_ptr=[], col=[])
+    p = den_params(B_net=[], rand_mean=6.0, R=9.0, den_window=2, den_adoption=0.9)
+    rep = compare_days(g, p, 40)
+    assert rep["flips"] == 0 and rep["days"] == 40, rep
+    assert sum(rep["notified"]) > 50
+
+
+def test_reset_redraws_app_holders():
+    pop = W.population(5_000, 7, 20)
+    p = den_params()
+    g = gpu_sim(pop, p, keep_lambda=False, max_steps=40)
+    g.run(40)
+    rp = np.array([[p["R"], 2.0, 1.0, 1.0, *p["S_age"], p["dose2_delay"]]], np.float32)
+    g.reset(rp, np.array([99], np.uint64))
+    g.run(40)
+    s = g.state()
+    den = g.notified()
+    g.close()
+    o = oracle_sim(pop, dict(p, seed=99))
+    o.run(40)
+    assert np.array_equal(s["flags"], o.state.flags) and np.array_equal(s["stage"], o.state.stage)
+    assert den.tolist() == o.den_notified
+
+
+def test_other_contexts_reject_notification():
+    from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation, Relaxed, Simulation
+    pop = W.population(500, 1, 5)
+    p = den_params()
+    rp, seeds = W.batch_params(4, 0)
+    with pytest.raises(DeabmError):
+        Simulation(pop, p, pop["age"], pop["seed_ids"], n_rep=4, rep_params=rp, rep_seeds=seeds)
+    with pytest.raises(DeabmError):
+        RaggedSimulation([pop], [p], max_steps=5)
+    with pytest.raises(DeabmError):
+        Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=0.5, max_days=5, ckpt_every=5)
