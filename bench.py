@@ -137,6 +137,27 @@ def traffic_from_profile(sources, profile: str, units_per_launch: float):
 
 
 # ---------------------------------------------------------------------------------------- ours
+def rank_inputs(w: dict, rank: int):
+    """Rank r's own problem: an independent population (seeded by r) with its own
+    simulation and network seeds.  Ranks exchange no data on the simulation path."""
+    from paper_2110_04421_gb300 import workloads as W
+    params = dict(w["params"], seed=w["params"]["seed"] + rank, net_seed=w["params"]["net_seed"] + rank)
+    pop = W.population(w["n"], rank, w["n_seed"])
+    return params, pop
+
+
+def reduce_over_ranks(dist, maxed, summed, device):
+    """Whole-job figures: the slowest rank's times (max) and the work of all ranks
+    (sum).  dist is torch.distributed (None on one rank)."""
+    import torch
+    mx = torch.tensor([float(v) for v in maxed], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(v) for v in summed], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist(), sm.tolist()
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2110_04421_gb300 import workloads as W
@@ -149,8 +170,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = W.plain_large()
     n, K, Wm = w["n"], args.steps, args.warmup
-    params = dict(w["params"], seed=w["params"]["seed"] + rank, net_seed=w["params"]["net_seed"] + rank)
-    pop = W.population(n, rank, w["n_seed"])
+    params, pop = rank_inputs(w, rank)
     static_edges = int(sum(int(rp[-1]) for rp in pop["row_ptr"]))
     stream = torch.cuda.Stream()
 
@@ -194,14 +214,9 @@ def run_ours(args, rank, world, local):
         d2h = ni.nbytes + hist.nbytes + sum(v.nbytes for v in st.values()) + msgs2.nbytes
 
     # ---- max over ranks
-    tt = torch.tensor([total_ms, e2e_s, float(messages), float(e2e_messages)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms, e2e_s = float(mx[0]), float(mx[1])
-        messages, e2e_messages = int(sm[2]), int(sm[3])
+    (total_ms, e2e_s), (messages, e2e_messages) = reduce_over_ranks(dist, [total_ms, e2e_s],
+                                                                    [messages, e2e_messages], "cuda")
+    messages, e2e_messages = int(messages), int(e2e_messages)
 
     # ---- batched ensemble vs plain per-replicate loop, relaxed gradient (rank 0)
     batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
@@ -209,6 +224,7 @@ def run_ours(args, rank, world, local):
     surrogate = run_surrogate(args) if (rank == 0 and not args.no_surrogate) else None
     ragged = run_ragged(args) if (rank == 0 and not args.no_ragged) else None
     occupation = run_occupation(args) if (rank == 0 and not args.no_occupation) else None
+    den = run_den(args) if (rank == 0 and not args.no_den) else None
 
     if rank == 0:
         value = messages / (total_ms / 1e3)
@@ -252,6 +268,8 @@ def run_ours(args, rank, world, local):
             line["ragged"] = ragged
         if occupation:
             line["daily_occupation"] = occupation
+        if den:
+            line["exposure_notification"] = den
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -454,6 +472,40 @@ def run_occupation(args):
                          "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_occ_n2e6.md", n)}}
 
 
+def run_den(args):
+    """The N=2e6 plain workload with digital exposure notification (adoption 0.3,
+    compliance 0.8, 7-day look-back): day kernel plus notification pass, timed
+    from day 30 on, once test results are coming in."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Simulation
+
+    w = W.plain_large()
+    n = w["n"]
+    K = max(3, min(args.den_steps, args.steps))
+    W0 = max(args.warmup, 30)
+    pop = W.population(n, 0, w["n_seed"])
+    params = dict(w["params"], den_on=1)
+    stream = torch.cuda.Stream()
+    sim = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=W0 + K, stream=stream.cuda_stream)
+    sim.step(W0)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, _, msgs = sim.counters()
+    den = sim.notified()
+    sim.close()
+    msg = int(msgs[W0:W0 + K].astype(np.int64).sum())
+    return {"workload": "plain N=2e6 with exposure notification (adoption 0.3, compliance 0.8, 7-day look-back)",
+            "value": msg / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / K, "steps": K,
+            "days_timed": f"{W0}..{W0 + K - 1}", "notified_per_day": float(den[W0:W0 + K].mean()),
+            "launches_per_day": 2}
+
+
 def run_batched(args):
     import torch
     from paper_2110_04421_gb300 import workloads as W
@@ -488,6 +540,8 @@ def run_batched(args):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "kernel": "step_batch4_kernel", "alg_bytes_per_launch": alg,
                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_batch_n1e5_b256.md", n * B)}}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_columns(pop, w["params"], rp, seeds, args.cpu_seconds / 2)
     if args.no_loop:
         return out
     # plain loop: the same B replicates one after another, same days
@@ -531,6 +585,33 @@ def cpu_baseline(pop, params, seconds: float):
     return {"value": msgs / el, "unit": "interactions/s", "cores": 1, "kind": "oracle",
             "sample": f"{days} whole days (days 0..{days - 1}) of the same N={pop['n']} population, "
                       f"{el:.1f} s, single thread", "cpu": cpu_model()}
+
+
+def cpu_baseline_columns(pop, base, rp, seeds, seconds: float):
+    """The oracle on replicate columns of the batched workload, one after another
+    (each column is an independent run on the shared graph), 8 columns of whole
+    days from day 0, stopping after about `seconds`."""
+    import oracle
+    msgs, days, cols = 0, 0, 0
+    t0 = time.perf_counter()
+    el = 0.0
+    for r in range(min(8, len(seeds))):
+        pr = dict(base, R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
+                  S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r]))
+        sim = oracle.Sim(pop, pr, pop["age"], pop["seed_ids"])
+        cols += 1
+        for _ in range(180):
+            msgs += sim.step(diag=False)["messages"]
+            days += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+        if el >= seconds:
+            break
+    return {"value": msgs / el, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"{days} replicate-days over {cols} of the {len(seeds)} columns (from day 0), {el:.1f} s, "
+                      "single thread; the columns are independent, so this per-column rate is the whole "
+                      "batch's rate on one core (extrapolated, not run for all columns)", "cpu": cpu_model()}
 
 
 def cpu_model():
@@ -591,9 +672,11 @@ def main():
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-occupation", action="store_true")
     ap.add_argument("--occupation-steps", type=int, default=20)
+    ap.add_argument("--no-den", action="store_true")
+    ap.add_argument("--den-steps", type=int, default=20)
     ap.add_argument("--calib-steps", type=int, default=200)
     ap.add_argument("--only", default="all",
-                    choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged", "occupation"],
+                    choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged", "occupation", "den"],
                     help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -606,13 +689,13 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps(run_batched(args)))
         return
-    if args.only in ("relaxed", "surrogate", "ragged", "occupation"):
+    if args.only in ("relaxed", "surrogate", "ragged", "occupation", "den"):
         import __graft_entry__
         __graft_entry__.build()
         import torch
         torch.cuda.set_device(local)
         fn = {"relaxed": run_relaxed, "surrogate": run_surrogate, "ragged": run_ragged,
-              "occupation": run_occupation}[args.only]
+              "occupation": run_occupation, "den": run_den}[args.only]
         print(json.dumps(fn(args)))
         return
     if args.only == "plain":
@@ -621,6 +704,7 @@ def main():
         args.no_surrogate = True
         args.no_ragged = True
         args.no_occupation = True
+        args.no_den = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

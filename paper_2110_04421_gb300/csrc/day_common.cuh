@@ -40,11 +40,20 @@ __device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const
     return h;
 }
 
+// Exposure-notification record of one (day, agent), kept for the last
+// den_window days: word 0 = random count | occupation count << 8, the random
+// contacts (caller ids) from word 1, the occupation contacts (internal rows)
+// from word kDenOccAt.
+constexpr uint32_t kDenOccAt = 16;
+
 // Random in-contacts of agent j (the caller's id) on `day`: count from word 0 of
 // block 0, contact e from word e+1 (block (e+1)/4, lane (e+1)%4); v uniform on
-// the other n-1 agents.  `inf` is indexed by the caller's ids.
+// the other n-1 agents.  `inf` is indexed by the caller's ids.  REC: also write
+// the contacts to rec[1..] when rec is not null.
+template <bool REC = false>
 __device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
-                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out)
+                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
+                                            uint32_t *rec = nullptr)
 {
     const uint2 nk = seed_key(P.net_seed);
     uint4 w = draw(nk, j, day, kStreamRnet, 0u);
@@ -58,6 +67,7 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
         const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
         uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
         v += (v >= j) ? 1u : 0u;
+        if (REC && rec) rec[1u + e] = v;
         r = __fadd_rn(r, __ldg(inf + (size_t)v * stride + b));
     }
     *k_out = k;
@@ -76,8 +86,10 @@ __device__ __forceinline__ uint32_t occ_place(uint32_t x, uint32_t size_m1, uint
 // of them (none for a lone member), contact e from word e of stream 4 (block
 // e/4, lane e%4).  Taken four at a time: one Philox block gives four rows whose
 // gathers are issued together, then added in draw order from +0.0f.
+template <bool REC = false>
 __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restrict__ inf, uint32_t j, uint32_t jo,
-                                         uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out)
+                                         uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
+                                         uint32_t *rec = nullptr)
 {
     const uint32_t g = __ldg(P.occ_gid + j);
     const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
@@ -90,8 +102,11 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
         const uint32_t x[4] = {w.x, w.y, w.z, w.w};
         float v[4];
 #pragma unroll
-        for (uint32_t u = 0; u < 4u; ++u)
-            v[u] = (e + u < k) ? __ldg(inf + (size_t)(beg + occ_place(x[u], size - 1u, own)) * stride + b) : 0.0f;
+        for (uint32_t u = 0; u < 4u; ++u) {
+            const uint32_t row = beg + occ_place(x[u], size - 1u, own);
+            if (REC && rec && e + u < k) rec[kDenOccAt + e + u] = row;
+            v[u] = (e + u < k) ? __ldg(inf + (size_t)row * stride + b) : 0.0f;
+        }
 #pragma unroll
         for (uint32_t u = 0; u < 4u; ++u)
             if (e + u < k) h = __fadd_rn(h, v[u]);
@@ -104,9 +119,12 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 // jo = the caller's id of the same agent.  OCC = false compiles the daily
 // occupation networks out (for contexts that have none).  The row bounds of every network are
 // loaded first and the random contacts are generated while they are in flight.
-template <bool OCC = true>
+// REC: the agent's exposure-notification record of the day goes to rec (when
+// not null).
+template <bool OCC = true, bool REC = false>
 __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
-                                           uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out)
+                                           uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out,
+                                           uint32_t *rec = nullptr)
 {
     uint32_t beg[DEABM_MAX_NETS], end[DEABM_MAX_NETS];
 #pragma unroll
@@ -116,7 +134,9 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
     }
     *k_out = 0;
     float r = 0.0f;
-    if (P.rand_on) r = random_sum(P, I.rand_cur, jo, day, stride, b, k_out);
+    if (P.rand_on) r = random_sum<REC>(P, I.rand_cur, jo, day, stride, b, k_out, rec);
+    const uint32_t k_rand = *k_out;
+    uint32_t k_occ = 0;
     float s = 0.0f;
 #pragma unroll
     for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
@@ -127,11 +147,11 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
         }
     }
     if (OCC && P.n_occ) {
-        uint32_t ko;
-        const float term = __fmul_rn(rp.B_net[P.n_nets], occ_sum(P, I.cur, j, jo, day, stride, b, &ko));
+        const float term = __fmul_rn(rp.B_net[P.n_nets], occ_sum<REC>(P, I.cur, j, jo, day, stride, b, &k_occ, rec));
         s = P.n_nets == 0 ? term : __fadd_rn(s, term);
-        *k_out += ko;
+        *k_out += k_occ;
     }
+    if (REC && rec) rec[0] = k_rand | (k_occ << 8);
     if (P.rand_on) {
         const float term = __fmul_rn(rp.B_rand, r);
         s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);

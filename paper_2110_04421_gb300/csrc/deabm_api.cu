@@ -39,6 +39,7 @@ struct deabm_ctx {
     // exposure notification: today's positive app holders (internal rows, caller ids), per-day counts
     uint8_t *den_src = nullptr, *den_src_orig = nullptr;
     int32_t *den_pos = nullptr;
+    uint32_t *den_ring = nullptr;  // [den_window][n][slots] contact records of the app holders
     float *lam = nullptr, *p = nullptr;
     Tables *tab = nullptr;
     Rep *rep = nullptr;
@@ -387,6 +388,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 if (ctx->relabel && (r = dalloc(ctx, &ctx->den_src_orig, n))) return r;
                 if ((r = dalloc(ctx, &ctx->den_pos, days))) return r;
                 CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * days, s));
+                const size_t slots = g->n_occ ? 32 : 16;
+                if ((r = dalloc(ctx, &ctx->den_ring, (size_t)p->den_window * n * slots))) return r;
             }
             CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * n_rep, s));
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
@@ -547,6 +550,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.den_src = ctx->den_src;
             K.den_src_orig = ctx->den_src_orig;
             K.den_pos = ctx->den_pos;
+            K.den_ring = ctx->den_ring;
+            K.den_slots = g->n_occ ? 32u : 16u;
             if (K.den_on) {  // app holders, part of the initial state kept for deabm_reset
                 CU(ctx, launch_den_apps(K, ctx->S, s));
                 CU(ctx, cudaMemcpyAsync(ctx->S0.flags, ctx->S.flags, nb, cudaMemcpyDeviceToDevice, s));

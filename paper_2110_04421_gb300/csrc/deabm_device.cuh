@@ -104,6 +104,10 @@ struct KParams {
     uint64_t thr_comp, thr_adopt;
     uint8_t *den_src, *den_src_orig;
     int32_t *den_pos;           // [day] positive app holders of the day
+    // each app holder's in-contacts of the last den_window days: record of
+    // (day d, row j) at den_ring + ((d % den_window) * n + j) * den_slots
+    uint32_t *den_ring;
+    uint32_t den_slots;
 };
 
 // Infectiousness buffers of a day.  Static-network gathers read `cur` (internal

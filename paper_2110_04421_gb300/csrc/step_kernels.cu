@@ -42,7 +42,9 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 // Full day for one (agent j, replicate b) at flat index i = j*stride + b.  Every
 // random draw is keyed by the caller's agent id jo, so relabelling the agents
 // inside the library changes no result.
-template <bool OCC = true>
+// DEN: exposure notification on (plain contexts): an app holder records the day's
+// contacts, a positive app holder is marked for the notification pass.
+template <bool OCC = true, bool DEN = false>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
                                           float *p_out, int *new_stage, bool *infected, uint32_t *k_out)
@@ -50,7 +52,10 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     const size_t i = (size_t)j * stride + b;
     const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
     const int age = __ldg(P.age + j);
-    const float lam = lambda_of<OCC>(P, rp, I, j, jo, day, stride, b, age, k_out);
+    uint32_t *rec = nullptr;
+    if (DEN && (S.flags[i] & DEABM_FL_APP))
+        rec = P.den_ring + ((size_t)(day % P.den_window) * P.n + j) * P.den_slots;
+    const float lam = lambda_of<OCC, DEN>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
     AgentState a;
     a.st = S.stage[i];
     a.tm = S.timer[i];
@@ -79,7 +84,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     }
     const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
     advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
-    if (P.den_on) {  // plain contexts only: a positive app holder notifies its contacts after the day
+    if (DEN) {  // a positive app holder notifies its contacts after the day
         const uint8_t v = (a.pos_result && (a.fl & DEABM_FL_APP)) ? 1u : 0u;
         P.den_src[j] = v;
         if (P.den_src_orig) P.den_src_orig[jo] = v;
@@ -135,7 +140,7 @@ __device__ __forceinline__ void count_day(bool active, int st, bool infected, ui
 #ifndef DEABM_OCC_MINB
 #define DEABM_OCC_MINB 10  // resident blocks per SM asked of the daily-occupation variant (swept: 8, 10, 12)
 #endif
-template <bool KEEP, bool OCC>
+template <bool KEEP, bool OCC, bool DEN>
 __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                          Counters C, float *lam_out, float *p_out)
 {
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
 #else
         const Rep &rp = P.rep[0];
 #endif
-        agent_day<OCC>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
     }
     count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
     __syncthreads();
@@ -468,12 +473,19 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
 {
     if (P.n_rep == 1) {
         const dim3 grid((P.n + DEABM_PLAIN_BLOCK - 1u) / DEABM_PLAIN_BLOCK);
-        if (P.n_occ) {
-            if (lam_out) step_plain_kernel<true, true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
-            else step_plain_kernel<false, true><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
-        } else {
-            if (lam_out) step_plain_kernel<true, false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
-            else step_plain_kernel<false, false><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        const int v = (lam_out ? 4 : 0) | (P.n_occ ? 2 : 0) | (P.den_on ? 1 : 0);
+        switch (v) {
+#define DEABM_PLAIN_CASE(c, K, O, D)                                                                      \
+    case c: step_plain_kernel<K, O, D><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out); break;
+            DEABM_PLAIN_CASE(0, false, false, false)
+            DEABM_PLAIN_CASE(1, false, false, true)
+            DEABM_PLAIN_CASE(2, false, true, false)
+            DEABM_PLAIN_CASE(3, false, true, true)
+            DEABM_PLAIN_CASE(4, true, false, false)
+            DEABM_PLAIN_CASE(5, true, false, true)
+            DEABM_PLAIN_CASE(6, true, true, false)
+            DEABM_PLAIN_CASE(7, true, true, true)
+#undef DEABM_PLAIN_CASE
         }
     } else if (P.n_rep % kRepPerThread == 0) {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 32u * kRepPerThread - 1u) / (32u * kRepPerThread));

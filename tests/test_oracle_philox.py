@@ -118,3 +118,37 @@ def test_random_contacts_distribution():
     assert chi2 < 30, chi2
     assert abs(counts.mean() - mean) < 5 * np.sqrt(mean / counts.size)
     assert hits.min() > 0.6 * hits.mean() and hits.max() < 1.4 * hits.mean()
+
+
+@pytest.mark.gpu
+def test_philox_matches_curand(tmp_path):
+    """The oracle's Philox4x32-10 against cuRAND's device implementation (a
+    library, compiled and run on the GPU by this test) on 10^5 random
+    (key, counter) pairs, including the day words the method uses (0xFFFFFFFF
+    and 0xFFFFFFFE are out of cuRAND's offset range here, so c1 < 2^30)."""
+    import shutil
+    import subprocess
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            pytest.skip("needs a CUDA GPU")
+    except ImportError:
+        pytest.skip("needs torch")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = tmp_path / "curand_philox_ref"
+    src = os.path.join(os.path.dirname(__file__), "curand_philox_ref.cu")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-o", str(exe), src], check=True)
+    rng = np.random.default_rng(2024)
+    n = 100_000
+    rec = rng.integers(0, 2**32, size=(n, 6), dtype=np.uint64).astype(np.uint32)
+    rec[:, 3] &= (1 << 30) - 1
+    inp = tmp_path / "in.bin"
+    with open(inp, "wb") as f:
+        f.write(np.uint32(n).tobytes())
+        f.write(rec.tobytes())
+    out = tmp_path / "out.bin"
+    subprocess.run([str(exe), str(inp), str(out)], check=True, timeout=120)
+    ref = np.fromfile(out, dtype=np.uint32).reshape(n, 4)
+    for i in range(n):
+        got = oracle.philox(rec[i, 2:6], rec[i, 0:2])
+        assert np.array_equal(got, ref[i]), (i, rec[i], got, ref[i])
