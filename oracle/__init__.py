@@ -80,6 +80,7 @@ class _Model(C.Structure):
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
         ("vax_strategy", C.c_uint32), ("elderly_bin", C.c_uint32), ("vax_nonsterile", C.c_uint32),
         ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
+        ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_float),
         ("den_on", C.c_uint32), ("den_adoption", C.c_double), ("den_compliance", C.c_double),
         ("den_window", C.c_uint32),
     ]
@@ -190,7 +191,8 @@ class Model:
     """Graph + parameters packed for the C oracle.  ``graph`` holds ``row_ptr`` and
     ``col`` lists (u32 CSR, destination rows) and ``n``, and optionally the daily
     occupation networks: ``occ_group`` (u32 per agent) and ``occ_k`` (u8 per
-    occupation, in-contacts a day); ``params`` is a plain dict."""
+    occupation, in-contacts a day), with ``occ_lattice`` = 1 and ``occ_rewire``
+    for Watts-Strogatz contacts; ``params`` is a plain dict."""
 
     def __init__(self, graph: dict, params: dict):
         self.n = int(graph["n"])
@@ -244,6 +246,8 @@ class Model:
             m.n_occ = ok.size
             m.occ_group = og.ctypes.data
             m.occ_k = ok.ctypes.data
+            m.occ_lattice = int(graph.get("occ_lattice", 0))
+            m.occ_rewire = float(graph.get("occ_rewire", 0.0))
         self.m = m
         self.params = P
 

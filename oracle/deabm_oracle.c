@@ -63,6 +63,7 @@ enum {
 #define SM_DEN 6u     /* x: complies with a notification; step word 0xFFFFFFFD: x = holds the app */
 #define SM_VAX 7u     /* x: vaccine response (step word fixed at 0) */
 #define SM_GUMBEL 8u  /* relaxed draw noise */
+#define SM_WS 9u      /* Watts-Strogatz occupation contacts: block e/2, lanes 2(e%2), 2(e%2)+1 = rewire coin, place */
 
 typedef struct {
     uint32_t n, n_nets;
@@ -91,6 +92,8 @@ typedef struct {
     uint32_t n_occ;
     const uint32_t *occ_group; /* [n] occupation of each agent, < n_occ */
     const uint8_t *occ_k;      /* [n_occ] in-contacts per agent per step, <= 15 */
+    uint32_t occ_lattice;      /* 0: contacts uniform over the occupation; 1: Watts-Strogatz ring lattice */
+    float occ_rewire;          /* lattice in-edges rewired each step with this probability */
     /* digital exposure notification (Sec. 4.2) */
     uint32_t den_on;
     double den_adoption, den_compliance;
@@ -361,6 +364,7 @@ static int check_model(const or_model *m)
             if (m->occ_k[g] > OR_POIS_CAP) return -1;
         for (uint32_t j = 0; j < m->n; ++j)
             if (m->occ_group[j] >= m->n_occ) return -1;
+        if (m->occ_lattice > 1 || !(m->occ_rewire >= 0.0f && m->occ_rewire <= 1.0f)) return -1;
     }
     return 0;
 }
@@ -449,11 +453,43 @@ static void occ_build(const or_model *m, or_occ *o)
 
 static void occ_free(or_occ *o) { free(o->start); free(o->members); free(o->pos); }
 
+/* Watts-Strogatz contacts (Sec. 3, Interaction Networks; Watts and Strogatz
+ * 1998), drawn anew every step: the members of an occupation sit on a ring in
+ * ascending id; in-edge e of the member at place q comes from the lattice place
+ * q + (e/2 + 1) for even e, q - (e/2 + 1) for odd e (mod size), unless its coin
+ * falls under occ_rewire (or the lattice offset is a multiple of the size), in
+ * which case it comes from a uniform other member. */
+static uint32_t occ_ws_contacts(const or_model *m, const or_occ *o, uint32_t j, uint32_t step, uint32_t *contacts)
+{
+    const uint32_t g = m->occ_group[j];
+    const uint32_t beg = o->start[g], size = o->start[g + 1u] - beg;
+    if (size < 2u) return 0;
+    const uint32_t k = m->occ_k[g], q = o->pos[j];
+    for (uint32_t e = 0; e < k; ++e) {
+        uint32_t blk[4];
+        draw4(m->net_seed, j, step, SM_WS, e / 2u, blk);
+        const uint32_t coin = blk[2u * (e % 2u)], word = blk[2u * (e % 2u) + 1u];
+        const uint32_t hop = (e / 2u + 1u) % size;
+        const uint32_t off = (e % 2u == 0u) ? hop : (size - hop) % size;
+        uint32_t r;
+        if (off == 0u || happens(coin, (double)m->occ_rewire)) {
+            r = (uint32_t)(((uint64_t)word * (uint64_t)(size - 1u)) >> 32);
+            if (r >= q) r += 1u;
+        } else {
+            r = (q + off) % size;
+        }
+        contacts[e] = o->members[beg + r];
+    }
+    return k;
+}
+
 /* the day's occupation in-contacts of agent j: occ_k[g] of them (none for a
  * lone member), each uniform over the other members of j's occupation, from
- * word e of the SM_OCC stream (block e/4, lane e%4). */
+ * word e of the SM_OCC stream (block e/4, lane e%4); Watts-Strogatz contacts
+ * when occ_lattice is set. */
 static uint32_t occ_contacts(const or_model *m, const or_occ *o, uint32_t j, uint32_t step, uint32_t *contacts)
 {
+    if (m->occ_lattice) return occ_ws_contacts(m, o, j, step, contacts);
     const uint32_t g = m->occ_group[j];
     const uint32_t beg = o->start[g], size = o->start[g + 1u] - beg;
     if (size < 2u) return 0;
