@@ -445,21 +445,24 @@ def run_occupation(args):
     pop = W.population_daily_occupation(n, 0, w["n_seed"])
     static_edges = int(sum(int(r[-1]) for r in pop["row_ptr"]))
     stream = torch.cuda.Stream()
-    sim = Simulation(pop, w["params"], pop["age"], pop["seed_ids"], max_steps=args.warmup + K,
-                     stream=stream.cuda_stream)
-    sim.step(args.warmup)
-    sim.sync()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    for e0, e1 in ev:
-        e0.record(stream)
-        sim.step(1)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    per_day = [e0.elapsed_time(e1) for e0, e1 in ev]
-    _, _, msgs = sim.counters()
-    sim.close()
-    ms = sum(per_day)
-    msg = int(msgs[args.warmup:args.warmup + K].astype(np.int64).sum())
+
+    def timed_days(graph):
+        sim = Simulation(graph, w["params"], pop["age"], pop["seed_ids"], max_steps=args.warmup + K,
+                         stream=stream.cuda_stream)
+        sim.step(args.warmup)
+        sim.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            sim.step(1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        _, _, msgs = sim.counters()
+        sim.close()
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev), int(msgs[args.warmup:args.warmup + K].astype(np.int64).sum())
+
+    ms, msg = timed_days(pop)
+    ms_ws, msg_ws = timed_days(dict(pop, occ_lattice=1, occ_rewire=0.1))
     alg = step_bytes_occ(n, static_edges, len(pop["row_ptr"]), int(pop["occ_k"].size), True)
     peak, _ = measured_peak_hbm()
     avg = ms / K
@@ -469,7 +472,11 @@ def run_occupation(args):
             "l2": f"inputs larger than L2: {alg / 1e6:.0f} MB algorithmic per day, no flush",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "kernel": "step_plain_kernel (daily occupation networks)", "alg_bytes_per_launch": alg,
-                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_occ_n2e6.md", n)}}
+                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_occ_n2e6.md", n)},
+            "watts_strogatz": {"workload": "the same with Watts-Strogatz occupations (ring lattice, rewiring 0.1)",
+                               "value": msg_ws / (ms_ws / 1e3), "unit": "interactions/s", "ms_per_step": ms_ws / K,
+                               "roofline": {"bound": "hbm", "achieved": alg / (ms_ws / K / 1e3) / 1e9, "peak": peak,
+                                            "unit": "GB/s", "frac": alg / (ms_ws / K / 1e3) / 1e9 / peak}}}
 
 
 def run_den(args):

@@ -91,7 +91,15 @@ typedef struct deabm_ctx deabm_ctx;
  * lone member), contact e from word e of Philox stream 4 keyed by (net_seed,
  * day, agent) -- block e/4, lane e%4 -- mapped to the member in place
  * floor(word * (size-1) / 2^32), skipping the agent itself, members ranked by
- * ascending id.  Their sum enters Eq. 1 with weight B_net[n_nets], after the
+ * ascending id.  occ_lattice = 1 makes each occupation a Watts-Strogatz small
+ * world rewired every day instead: the members sit on a ring in ascending id;
+ * in-edge e of the member at place q comes from the lattice place
+ * q + (e/2 + 1) (e even) or q - (e/2 + 1) (e odd), mod the occupation's size,
+ * unless word 2(e%2) of block e/2 of Philox stream 9 (same key and counter
+ * words) is below floor(occ_rewire 2^32), or the lattice offset is a multiple
+ * of the size: then it comes from the member in place floor(word' (size-1) /
+ * 2^32), skipping the agent itself, word' = word 2(e%2)+1 of that block.
+ * Their sum enters Eq. 1 with weight B_net[n_nets], after the
  * stored networks and before the random network, so n_nets must be <= 3.
  * Only plain and batched contexts take them (deabm_create, deabm_create_batch);
  * the other constructors reject n_occ > 0.  n_occ = 0: occ_group and occ_k are
@@ -105,6 +113,8 @@ typedef struct {
     uint32_t n_occ;
     const uint32_t *occ_group;
     const uint8_t *occ_k;
+    uint32_t occ_lattice; /* 0: as above; 1: Watts-Strogatz (see below) */
+    float occ_rewire;     /* occ_lattice = 1: rewiring probability, 0..1 */
 } deabm_graph;
 
 /* Agents (Sec. 3 "Agent State Definition"); all host arrays of n_agents entries.

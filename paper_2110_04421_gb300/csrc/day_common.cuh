@@ -86,6 +86,43 @@ __device__ __forceinline__ uint32_t occ_place(uint32_t x, uint32_t size_m1, uint
 // of them (none for a lone member), contact e from word e of stream 4 (block
 // e/4, lane e%4).  Taken four at a time: one Philox block gives four rows whose
 // gathers are issued together, then added in draw order from +0.0f.
+// Watts-Strogatz variant: the member at place `own` of a ring of `size`
+// receives in-edge e from the lattice place own + (e/2+1) (e even) or
+// own - (e/2+1) (e odd), unless the edge is rewired (coin below the threshold,
+// or a lattice offset that is a multiple of the size): then from a uniform
+// other member.  Two contacts per Philox block.
+template <bool REC = false>
+__device__ __forceinline__ float occ_ws_sum(const KParams &P, const float *__restrict__ inf, uint32_t jo, uint32_t day,
+                                            uint32_t stride, uint32_t b, uint32_t beg, uint32_t size, uint32_t own,
+                                            uint32_t k, uint32_t *rec)
+{
+    const uint2 nk = seed_key(P.net_seed);
+    float h = 0.0f;
+    for (uint32_t e = 0; e < k; e += 2u) {
+        const uint4 w = draw(nk, jo, day, kStreamWs, e >> 1);
+        const uint32_t m = (e >> 1) + 1u;
+        const uint32_t hop = m < size ? m : m % size;
+        const uint32_t coin[2] = {w.x, w.z}, word[2] = {w.y, w.w};
+        float v[2];
+#pragma unroll
+        for (uint32_t u = 0; u < 2u; ++u) {
+            const uint32_t off = u == 0u ? hop : (hop == 0u ? 0u : size - hop);
+            uint32_t r;
+            if (off == 0u || (uint64_t)coin[u] < P.thr_rewire) {
+                r = occ_place(word[u], size - 1u, own);
+            } else {
+                r = own + off;
+                r = r >= size ? r - size : r;
+            }
+            if (REC && rec && e + u < k) rec[kDenOccAt + e + u] = beg + r;
+            v[u] = (e + u < k) ? __ldg(inf + (size_t)(beg + r) * stride + b) : 0.0f;
+        }
+        h = __fadd_rn(h, v[0]);
+        if (e + 1u < k) h = __fadd_rn(h, v[1]);
+    }
+    return h;
+}
+
 template <bool REC = false>
 __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restrict__ inf, uint32_t j, uint32_t jo,
                                          uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
@@ -94,8 +131,10 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
     const uint32_t g = __ldg(P.occ_gid + j);
     const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
     const uint32_t k = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
-    const uint2 nk = seed_key(P.net_seed);
     const uint32_t own = j - beg;
+    *k_out = k;
+    if (P.occ_lattice) return occ_ws_sum<REC>(P, inf, jo, day, stride, b, beg, size, own, k, rec);
+    const uint2 nk = seed_key(P.net_seed);
     float h = 0.0f;
     for (uint32_t e = 0; e < k; e += 4u) {
         const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);

@@ -37,9 +37,10 @@ struct deabm_ctx {
     uint32_t *occ_gid = nullptr, *occ_start = nullptr;
     uint8_t *occ_k = nullptr;
     // exposure notification: today's positive app holders (internal rows, caller ids), per-day counts
-    uint8_t *den_src = nullptr, *den_src_orig = nullptr;
+    uint32_t *den_bits = nullptr, *den_bits_orig = nullptr;
     int32_t *den_pos = nullptr;
-    uint32_t *den_ring = nullptr;  // [den_window][n][slots] contact records of the app holders
+    uint32_t *den_ring = nullptr;  // [den_window][n_app][slots] contact records of the app holders
+    uint32_t *app_rows = nullptr, *app_rank = nullptr;
     float *lam = nullptr, *p = nullptr;
     Tables *tab = nullptr;
     Rep *rep = nullptr;
@@ -144,6 +145,9 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
                         DEABM_MAX_NETS - 1);
         if (!g->occ_group || !g->occ_k) return fail(ctx, DEABM_EINVAL, "occ_group and occ_k are required when n_occ > 0");
         if (g->n_occ >= (1u << 31)) return fail(ctx, DEABM_EINVAL, "n_occ too large");
+        if (g->occ_lattice > 1) return fail(ctx, DEABM_EINVAL, "occ_lattice must be 0 or 1");
+        if (!(g->occ_rewire >= 0.0f && g->occ_rewire <= 1.0f))
+            return fail(ctx, DEABM_EINVAL, "occ_rewire must be in [0,1]");
         for (uint32_t q = 0; q < g->n_occ; ++q)
             if (g->occ_k[q] > DEABM_POIS_CAP)
                 return fail(ctx, DEABM_EINVAL, "occ_k[%u] = %u > %d", q, g->occ_k[q], DEABM_POIS_CAP);
@@ -281,6 +285,31 @@ static void build_reps(const deabm_params *p, uint32_t n_rep, const float *rep_p
     }
 }
 
+// ---------------------------------------------------------------- exposure notification
+// The app holders drawn on the device, listed in row order with each row's rank
+// (for the notification pass and the contact ring); sets K.n_app.
+static int den_list_apps(deabm_ctx *ctx, KParams &K)
+{
+    const uint32_t n = ctx->n;
+    std::vector<uint8_t> fl(n);
+    CU(ctx, cudaMemcpyAsync(fl.data(), ctx->S.flags, n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<uint32_t> rows, rank(n, 0xFFFFFFFFu);
+    rows.reserve(n);
+    for (uint32_t j = 0; j < n; ++j)
+        if (fl[j] & DEABM_FL_APP) {
+            rank[j] = (uint32_t)rows.size();
+            rows.push_back(j);
+        }
+    K.n_app = (uint32_t)rows.size();
+    if (K.n_app)
+        CU(ctx, cudaMemcpyAsync(ctx->app_rows, rows.data(), sizeof(uint32_t) * K.n_app, cudaMemcpyHostToDevice,
+                                ctx->stream));
+    CU(ctx, cudaMemcpyAsync(ctx->app_rank, rank.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));  // the staging vectors go out of scope
+    return DEABM_OK;
+}
+
 // ---------------------------------------------------------------- creation
 static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_params *p, uint32_t n_rep,
                        const float *rep_params, const uint64_t *rep_seeds, void *stream, deabm_ctx **out)
@@ -384,12 +413,14 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->C.den, days))) return r;
             CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
             if (p->den_on) {
-                if ((r = dalloc(ctx, &ctx->den_src, n))) return r;
-                if (ctx->relabel && (r = dalloc(ctx, &ctx->den_src_orig, n))) return r;
+                if ((r = dalloc(ctx, &ctx->den_bits, ((size_t)n + 31) / 32))) return r;
+                if (ctx->relabel && (r = dalloc(ctx, &ctx->den_bits_orig, ((size_t)n + 31) / 32))) return r;
                 if ((r = dalloc(ctx, &ctx->den_pos, days))) return r;
                 CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * days, s));
                 const size_t slots = g->n_occ ? 32 : 16;
                 if ((r = dalloc(ctx, &ctx->den_ring, (size_t)p->den_window * n * slots))) return r;
+                if ((r = dalloc(ctx, &ctx->app_rows, n))) return r;
+                if ((r = dalloc(ctx, &ctx->app_rank, n))) return r;
             }
             CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * n_rep, s));
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
@@ -543,18 +574,23 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.occ_gid = ctx->occ_gid;
             K.occ_start = ctx->occ_start;
             K.occ_k = ctx->occ_k;
+            K.occ_lattice = g->n_occ ? g->occ_lattice : 0u;
+            K.thr_rewire = threshold((double)g->occ_rewire);
             K.den_on = p->den_on ? 1u : 0u;
             K.den_window = p->den_window;
             K.thr_comp = threshold(p->den_compliance);
             K.thr_adopt = threshold(p->den_adoption);
-            K.den_src = ctx->den_src;
-            K.den_src_orig = ctx->den_src_orig;
+            K.den_bits = ctx->den_bits;
+            K.den_bits_orig = ctx->den_bits_orig;
             K.den_pos = ctx->den_pos;
             K.den_ring = ctx->den_ring;
             K.den_slots = g->n_occ ? 32u : 16u;
+            K.app_rows = ctx->app_rows;
+            K.app_rank = ctx->app_rank;
             if (K.den_on) {  // app holders, part of the initial state kept for deabm_reset
                 CU(ctx, launch_den_apps(K, ctx->S, s));
                 CU(ctx, cudaMemcpyAsync(ctx->S0.flags, ctx->S.flags, nb, cudaMemcpyDeviceToDevice, s));
+                if ((r = den_list_apps(ctx, K))) return r;
             }
 
             if (a->n_seed) {
@@ -626,6 +662,8 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         I.next = ctx->inf[c ^ 1];
         I.rand_cur = ctx->inf_rand[c] ? ctx->inf_rand[c] : ctx->inf[c];
         I.rand_next = ctx->inf_rand[c ^ 1];
+        if (kp.den_bits_orig)
+            CU(ctx, cudaMemsetAsync(kp.den_bits_orig, 0, sizeof(uint32_t) * (((size_t)ctx->n + 31) / 32), ctx->stream));
         CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
                             ctx->stream));
         if (kp.den_on) CU(ctx, launch_den(kp, ctx->day, ctx->S, ctx->C, ctx->stream));
@@ -1096,6 +1134,8 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     if (ctx->kp.den_on) {  // the app draw follows the (possibly new) seed
         CU(ctx, launch_den_apps(ctx->kp, ctx->S, s));
         CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * ctx->max_steps, s));
+        int r = den_list_apps(ctx, ctx->kp);
+        if (r) return r;
     }
     if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
     ctx->cur = 0;

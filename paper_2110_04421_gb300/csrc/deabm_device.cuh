@@ -20,6 +20,7 @@ enum : uint32_t {
     kStreamDen = 6,    // x: complies with a notification; day word 0xFFFFFFFD: x = holds the app
     kStreamVax = 7,    // x: vaccine response (day word fixed at 0)
     kStreamGumbel = 8, // relaxed draw noise
+    kStreamWs = 9,     // Watts-Strogatz occupation contacts: block e/2, lanes 2(e%2), 2(e%2)+1 = coin, place
 };
 constexpr uint32_t kSeedDay = 0xFFFFFFFFu;  // day word of the infections before day 0
 constexpr int16_t kNever = 0x7FFF;
@@ -97,15 +98,21 @@ struct KParams {
     const uint32_t *occ_gid;    // [n] occupation of each internal row
     const uint32_t *occ_start;  // [n_occ + 1] first internal row of each occupation
     const uint8_t *occ_k;       // [n_occ] daily in-contacts of a member
-    // digital exposure notification (den_on = 0: none).  den_src[row] = 1 when
-    // the agent is an app holder whose positive result landed today; the same
-    // by caller id in den_src_orig (nullptr when the ids are not relabelled).
+    uint32_t occ_lattice;       // 1: Watts-Strogatz ring lattice, rewired daily
+    uint64_t thr_rewire;
+    // digital exposure notification (den_on = 0: none).  Bit r of den_bits is
+    // set when row r is an app holder whose positive result landed today; the
+    // same by caller id in den_bits_orig (nullptr when the ids are not
+    // relabelled; cleared before each day).
     uint32_t den_on, den_window;
     uint64_t thr_comp, thr_adopt;
-    uint8_t *den_src, *den_src_orig;
+    uint32_t *den_bits, *den_bits_orig;
     int32_t *den_pos;           // [day] positive app holders of the day
-    // each app holder's in-contacts of the last den_window days: record of
-    // (day d, row j) at den_ring + ((d % den_window) * n + j) * den_slots
+    // the app holders: their rows in ascending order, and each row's rank among
+    // them; each app holder's in-contacts of the last den_window days: record of
+    // (day d, rank a) at den_ring + ((d % den_window) * n_app + a) * den_slots
+    uint32_t n_app;
+    const uint32_t *app_rows, *app_rank;
     uint32_t *den_ring;
     uint32_t den_slots;
 };

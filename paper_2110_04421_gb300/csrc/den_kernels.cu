@@ -5,8 +5,9 @@
 // centred, as a gather: after the day's update every eligible app holder j
 // walks its own in-contacts of those days -- its stored CSR rows, and the daily
 // occupation and random contacts the day kernel recorded for app holders while
-// drawing them (a ring of den_window records per agent) -- and looks each
-// source up in the day's byte map of positive app holders.
+// drawing them (a ring of den_window records per app holder) -- and looks each
+// source up in the day's bit map of positive app holders.  One thread per app
+// holder, app holders listed in row order.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -16,29 +17,60 @@
 
 namespace deabm {
 
-// was any stored in-neighbour of row j a positive app holder today?
+__device__ __forceinline__ bool bit_of(const uint32_t *map, uint32_t x) { return (__ldg(map + (x >> 5)) >> (x & 31u)) & 1u; }
+
+// was any stored in-neighbour of row j a positive app holder today?  Each row
+// is taken in rounds of four edges: four column loads, then four bit lookups.
 __device__ __forceinline__ bool den_static_hit(const KParams &P, uint32_t j)
 {
+    bool hit = false;
     for (uint32_t net = 0; net < P.n_nets; ++net) {
         const uint32_t e1 = __ldg(P.row_ptr[net] + j + 1);
-        for (uint32_t e = __ldg(P.row_ptr[net] + j); e < e1; ++e)
-            if (P.den_src[__ldg(P.col[net] + e)]) return true;
+        for (uint32_t e = __ldg(P.row_ptr[net] + j); e < e1; e += 4u) {
+            uint32_t c[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4u; ++u) c[u] = e + u < e1 ? __ldg(P.col[net] + e + u) : 0u;
+#pragma unroll
+            for (uint32_t u = 0; u < 4u; ++u) hit |= (e + u < e1) && bit_of(P.den_bits, c[u]);
+        }
     }
-    return false;
+    return hit;
 }
 
-// the random and occupation in-contacts of row j on day d, from the record the
-// day kernel wrote while drawing them
-__device__ __forceinline__ bool den_ring_hit(const KParams &P, uint32_t j, uint32_t d)
+// the random and occupation in-contacts of row j on the days [d0, d1), from the
+// records the day kernel wrote while drawing them.  Four days at a time: their
+// first 16 bytes (header and three random contacts, which is all of most days'
+// random contacts) are loaded together, the rest on demand.
+__device__ __forceinline__ bool den_ring_hit(const KParams &P, uint32_t a, uint32_t d0, uint32_t d1)
 {
-    const uint8_t *src_rand = P.den_src_orig ? P.den_src_orig : P.den_src;
-    const uint32_t *rec = P.den_ring + ((size_t)(d % P.den_window) * P.n + j) * P.den_slots;
-    const uint32_t h = rec[0], kr = h & 0xFFu, ko = h >> 8;
-    for (uint32_t e = 0; e < kr; ++e)
-        if (src_rand[rec[1u + e]]) return true;
-    for (uint32_t e = 0; e < ko; ++e)
-        if (P.den_src[rec[kDenOccAt + e]]) return true;
-    return false;
+    const uint32_t *src_rand = P.den_bits_orig ? P.den_bits_orig : P.den_bits;
+    bool hit = false;
+    for (uint32_t c0 = d0; c0 < d1 && !hit; c0 += 4u) {
+        uint4 q[4];
+        const uint32_t *rec[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u) {
+            rec[u] = P.den_ring + ((size_t)((c0 + u) % P.den_window) * P.n_app + a) * P.den_slots;
+            q[u] = c0 + u < d1 ? __ldg((const uint4 *)rec[u]) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u) {
+            const uint32_t kr = q[u].x & 0xFFu, ko = q[u].x >> 8;
+            hit |= (kr > 0u && bit_of(src_rand, q[u].y)) | (kr > 1u && bit_of(src_rand, q[u].z)) |
+                   (kr > 2u && bit_of(src_rand, q[u].w));
+            for (uint32_t e = 4u; e <= kr; e += 4u) {
+                const uint4 v = __ldg((const uint4 *)(rec[u] + e));
+                hit |= bit_of(src_rand, v.x) | (e + 1u <= kr && bit_of(src_rand, v.y)) |
+                       (e + 2u <= kr && bit_of(src_rand, v.z)) | (e + 3u <= kr && bit_of(src_rand, v.w));
+            }
+            for (uint32_t e = 0; e < ko; e += 4u) {
+                const uint4 v = __ldg((const uint4 *)(rec[u] + kDenOccAt + e));
+                hit |= bit_of(P.den_bits, v.x) | (e + 1u < ko && bit_of(P.den_bits, v.y)) |
+                       (e + 2u < ko && bit_of(P.den_bits, v.z)) | (e + 3u < ko && bit_of(P.den_bits, v.w));
+            }
+        }
+    }
+    return hit;
 }
 
 __global__ void __launch_bounds__(256) den_kernel(const KParams P, uint32_t day, StateRef S, Counters C)
@@ -46,17 +78,16 @@ __global__ void __launch_bounds__(256) den_kernel(const KParams P, uint32_t day,
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per app holder
     bool notified = false;
     // nothing to do on a day without a positive app holder
-    if (j < P.n && __ldg(P.den_pos + day) > 0) {
+    if (a < P.n_app && __ldg(P.den_pos + day) > 0) {
+        const uint32_t j = __ldg(P.app_rows + a);
         const uint32_t fl = S.flags[j];
         const int st = S.stage[j];
-        if ((fl & DEABM_FL_APP) && (S.qt[j] & 0x0Fu) == 0u && st != DEABM_HOSP && st != DEABM_ICU &&
-            st != DEABM_DEAD) {
-            bool hit = den_static_hit(P, j);
+        if ((S.qt[j] & 0x0Fu) == 0u && st != DEABM_HOSP && st != DEABM_ICU && st != DEABM_DEAD) {
             const uint32_t d0 = day + 1u > P.den_window ? day + 1u - P.den_window : 0u;
-            for (uint32_t d = d0; d <= day && !hit; ++d) hit = den_ring_hit(P, j, d);
+            const bool hit = den_static_hit(P, j) || den_ring_hit(P, a, d0, day + 1u);
             if (hit) {
                 notified = true;
                 const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
@@ -90,7 +121,8 @@ cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t st
 
 cudaError_t launch_den(const KParams &P, uint32_t day, const StateRef &S, const Counters &C, cudaStream_t stream)
 {
-    den_kernel<<<(P.n + 255u) / 256u, 256, 0, stream>>>(P, day, S, C);
+    if (P.n_app == 0u) return cudaSuccess;
+    den_kernel<<<(P.n_app + 255u) / 256u, 256, 0, stream>>>(P, day, S, C);
     return cudaGetLastError();
 }
 

@@ -47,14 +47,15 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 template <bool OCC = true, bool DEN = false>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
-                                          float *p_out, int *new_stage, bool *infected, uint32_t *k_out)
+                                          float *p_out, int *new_stage, bool *infected, uint32_t *k_out,
+                                          bool *notify = nullptr)
 {
     const size_t i = (size_t)j * stride + b;
     const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
     const int age = __ldg(P.age + j);
     uint32_t *rec = nullptr;
     if (DEN && (S.flags[i] & DEABM_FL_APP))
-        rec = P.den_ring + ((size_t)(day % P.den_window) * P.n + j) * P.den_slots;
+        rec = P.den_ring + ((size_t)(day % P.den_window) * P.n_app + __ldg(P.app_rank + j)) * P.den_slots;
     const float lam = lambda_of<OCC, DEN>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
     AgentState a;
     a.st = S.stage[i];
@@ -85,10 +86,9 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
     advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
     if (DEN) {  // a positive app holder notifies its contacts after the day
-        const uint8_t v = (a.pos_result && (a.fl & DEABM_FL_APP)) ? 1u : 0u;
-        P.den_src[j] = v;
-        if (P.den_src_orig) P.den_src_orig[jo] = v;
-        if (v) atomicAdd(P.den_pos + day, 1);
+        const bool v = a.pos_result && (a.fl & DEABM_FL_APP);
+        *notify = v;
+        if (v && P.den_bits_orig) atomicOr(P.den_bits_orig + (jo >> 5), 1u << (jo & 31u));
     }
     S.stage[i] = (int8_t)a.st;
     S.timer[i] = (int16_t)a.tm;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = j < P.n;
     int st = 0;
-    bool infected = false;
+    bool infected = false, notify = false;
     uint32_t k = 0;
     if (active) {
 #if DEABM_REP_SMEM
@@ -169,7 +169,15 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
 #else
         const Rep &rp = P.rep[0];
 #endif
-        agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k,
+                            &notify);
+    }
+    if (DEN) {  // the day's positive app holders as a bit map over rows: one word per warp
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, notify);
+        if ((threadIdx.x & 31u) == 0u && j < P.n) {
+            P.den_bits[j >> 5] = bits;
+            if (bits) atomicAdd(P.den_pos + day, __popc(bits));
+        }
     }
     count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
     __syncthreads();
@@ -351,17 +359,43 @@ __global__ void __launch_bounds__(256) step_batch4_kernel(const KParams P, uint3
             const uint32_t ko = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
             const uint2 nk = seed_key(P.net_seed);
             float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            for (uint32_t e = 0; e < ko; e += 4u) {
-                const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
-                const uint32_t x[4] = {w.x, w.y, w.z, w.w};
-                float4 v[4];
+            if (P.occ_lattice) {  // Watts-Strogatz contacts, two per Philox block (as occ_ws_sum)
+                const uint32_t own = j - beg;
+                for (uint32_t e = 0; e < ko; e += 2u) {
+                    const uint4 w = draw(nk, jo, day, kStreamWs, e >> 1);
+                    const uint32_t m = (e >> 1) + 1u;
+                    const uint32_t hop = m < size ? m : m % size;
+                    const uint32_t coin[2] = {w.x, w.z}, word[2] = {w.y, w.w};
+                    float4 v[2];
 #pragma unroll
-                for (uint32_t u = 0; u < 4u; ++u)
-                    v[u] = (e + u < ko) ? __ldg((const float4 *)(I.cur + (size_t)(beg + occ_place(x[u], size - 1u, j - beg)) * B + b0))
-                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    for (uint32_t u = 0; u < 2u; ++u) {
+                        const uint32_t off = u == 0u ? hop : (hop == 0u ? 0u : size - hop);
+                        uint32_t r;
+                        if (off == 0u || (uint64_t)coin[u] < P.thr_rewire) {
+                            r = occ_place(word[u], size - 1u, own);
+                        } else {
+                            r = own + off;
+                            r = r >= size ? r - size : r;
+                        }
+                        v[u] = (e + u < ko) ? __ldg((const float4 *)(I.cur + (size_t)(beg + r) * B + b0))
+                                            : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+                    add4(h, v[0]);
+                    if (e + 1u < ko) add4(h, v[1]);
+                }
+            } else {
+                for (uint32_t e = 0; e < ko; e += 4u) {
+                    const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
+                    const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+                    float4 v[4];
 #pragma unroll
-                for (uint32_t u = 0; u < 4u; ++u)
-                    if (e + u < ko) add4(h, v[u]);
+                    for (uint32_t u = 0; u < 4u; ++u)
+                        v[u] = (e + u < ko) ? __ldg((const float4 *)(I.cur + (size_t)(beg + occ_place(x[u], size - 1u, j - beg)) * B + b0))
+                                            : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                    for (uint32_t u = 0; u < 4u; ++u)
+                        if (e + u < ko) add4(h, v[u]);
+                }
             }
             const float hv[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll

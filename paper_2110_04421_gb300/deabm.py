@@ -40,7 +40,8 @@ class Graph(C.Structure):
     _fields_ = [("n_agents", C.c_uint32), ("n_nets", C.c_uint32),
                 ("row_ptr", C.c_void_p * MAX_NETS), ("col", C.c_void_p * MAX_NETS),
                 ("rand_mean", C.c_float),
-                ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p)]
+                ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
+                ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_float)]
 
 
 class Agents(C.Structure):
@@ -216,6 +217,8 @@ def _graph_struct(graph: dict, rand_mean: float, keep: list) -> Graph:
         g.n_occ = ok.size
         g.occ_group = og.ctypes.data
         g.occ_k = ok.ctypes.data
+        g.occ_lattice = int(graph.get("occ_lattice", 0))
+        g.occ_rewire = float(graph.get("occ_rewire", 0.0))
     return g
 
 

@@ -47,9 +47,11 @@ def _create(lib, n, rp, col, age, params=None, rand_mean=2.0, stage=None, occ=No
     from paper_2110_04421_gb300 import workloads as W
     from paper_2110_04421_gb300.deabm import Agents, make_params
     g = _graph(n, rp, col, rand_mean)
-    if occ is not None:  # (occ_group, occ_k, n_nets)
+    if occ is not None:  # (occ_group, occ_k, n_nets[, occ_lattice, occ_rewire])
         g.n_occ, g.occ_group, g.occ_k = occ[1].size, occ[0].ctypes.data, occ[1].ctypes.data
         g.n_nets = occ[2]
+        if len(occ) > 3:
+            g.occ_lattice, g.occ_rewire = occ[3], occ[4]
         for q in range(1, occ[2]):
             g.row_ptr[q], g.col[q] = rp.ctypes.data, col.ctypes.data
     a = Agents()
@@ -66,7 +68,7 @@ def _create(lib, n, rp, col, age, params=None, rand_mean=2.0, stage=None, occ=No
                                   "bad_age", "bad_stage", "bad_test_delay", "bad_quarantine", "bad_prob",
                                   "random_net_single_agent", "occ_group_out_of_range", "occ_k_too_large",
                                   "occ_without_weight_slot", "den_without_testing", "den_bad_window",
-                                  "den_bad_adoption"])
+                                  "den_bad_adoption", "occ_bad_lattice", "occ_bad_rewire"])
 def test_create_rejects_invalid_input(lib, case):
     from paper_2110_04421_gb300 import workloads as W
     n = 4
@@ -83,6 +85,8 @@ def test_create_rejects_invalid_input(lib, case):
         occ = (occ_group, occ_k, 1)
     elif case == "occ_without_weight_slot":  # four stored networks leave no B_net entry for it
         occ = (occ_group, occ_k, 4)
+    elif case in ("occ_bad_lattice", "occ_bad_rewire"):
+        occ = (occ_group, occ_k, 1, 2 if case == "occ_bad_lattice" else 1, -0.1 if case == "occ_bad_rewire" else 0.0)
     elif case == "den_without_testing":
         params = W.params_with(den_on=1, test_on=0)
     elif case == "den_bad_window":

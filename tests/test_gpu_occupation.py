@@ -94,3 +94,48 @@ def test_other_constructors_reject_occupations():
         RaggedSimulation([pop], [p], max_steps=5)
     with pytest.raises(DeabmError):
         Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=0.5, max_days=5, ckpt_every=5)
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.1, 1.0])
+def test_watts_strogatz_occupations(beta):
+    """Watts-Strogatz contacts rewired daily: 23 occupations, households stored."""
+    pop = dict(W.population_daily_occupation(6_001, 9, 20), occ_lattice=1, occ_rewire=beta)
+    p = W.params_with(test_on=1, quar_on=1, R=2.5, seed=5, net_seed=6)
+    rep = compare_days(pop, p, 40)
+    assert rep["flips"] == 0 and rep["days"] == 40, rep
+
+
+def test_watts_strogatz_small_rings_and_notification():
+    """Workplaces of 20 with a ragged last one of 3 members (lattice offsets that
+    wrap onto the member itself are rewired), with exposure notification on, so
+    the recorded contacts of the lattice feed the notification pass."""
+    n = 20 * 250 + 3
+    pop = W.population(n, 10, 30)
+    group, k = W.workplaces(n, 10)
+    g = dict(pop, row_ptr=pop["row_ptr"][:1], col=pop["col"][:1], occ_group=group, occ_k=k, occ_lattice=1,
+             occ_rewire=0.2)
+    p = W.params_with(test_on=1, quar_on=1, R=4.0, den_on=1, den_adoption=0.6, seed=2, net_seed=3)
+    rep = compare_days(g, p, 45)
+    assert rep["flips"] == 0 and rep["days"] == 45, rep
+    assert sum(rep["notified"]) > 20
+
+
+@pytest.mark.parametrize("B", [37, 36])
+def test_watts_strogatz_batched(B):
+    n, T = 2501, 25
+    pop = dict(W.population_daily_occupation(n, 11, 25), occ_lattice=1, occ_rewire=0.15)
+    base = W.params_with(test_on=1, quar_on=1, net_seed=7)
+    rp, seeds = W.batch_params(B, 2)
+    from paper_2110_04421_gb300.deabm import Simulation
+    gb = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds, max_steps=T)
+    ni_b, h_b = gb.run(T)
+    sb = gb.state()
+    gb.close()
+    for r in (0, B - 1):
+        pr = dict(base, R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
+                  S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r]))
+        o = oracle_sim(pop, pr)
+        ni_o, h_o, _ = o.run(T)
+        assert np.array_equal(ni_o, ni_b[:, r]) and np.array_equal(h_o, h_b[:, r])
+        for k in ("stage", "timer", "tinf", "flags", "qt"):
+            assert np.array_equal(getattr(o.state, k), sb[k][:, r]), (r, k)
