@@ -48,12 +48,16 @@ constexpr uint32_t kDenOccAt = 16;
 
 // Random in-contacts of agent j (the caller's id) on `day`: count from word 0 of
 // block 0, contact e from word e+1 (block (e+1)/4, lane (e+1)%4); v uniform on
-// the other n-1 agents.  `inf` is indexed by the caller's ids.  REC: also write
-// the contacts to rec[1..] when rec is not null.
-template <bool REC = false>
+// the other n-1 agents.  `inf` is indexed by the caller's ids, or (ROWMAP) by
+// internal rows through row_of.  REC: also write the contacts to
+// rec[1..] when rec is not null.
+#ifndef DEABM_RAND_BATCH
+#define DEABM_RAND_BATCH 1  // 1: a Philox block's contacts gathered together; 0: one contact at a time
+#endif
+template <bool REC = false, bool ROWMAP = false>
 __device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
                                             uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
-                                            uint32_t *rec = nullptr)
+                                            uint32_t *rec = nullptr, const uint32_t *row_of = nullptr)
 {
     const uint2 nk = seed_key(P.net_seed);
     uint4 w = draw(nk, j, day, kStreamRnet, 0u);
@@ -61,6 +65,39 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
     while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
     float r = 0.0f;
     const uint64_t nm1 = (uint64_t)(P.n - 1u);
+#if DEABM_RAND_BATCH
+    // contacts 0..2 from words 1..3 of block 0, then four per block: the block's
+    // gathers are issued together and added in draw order
+    {
+        const uint32_t x[3] = {w.y, w.z, w.w};
+        float v[3];
+#pragma unroll
+        for (uint32_t u = 0; u < 3u; ++u) {
+            uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
+            c += (c >= j) ? 1u : 0u;
+            if (REC && rec && u < k) rec[1u + u] = c;
+            v[u] = u < k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 3u; ++u)
+            if (u < k) r = __fadd_rn(r, v[u]);
+    }
+    for (uint32_t e = 3u; e < k; e += 4u) {
+        w = draw(nk, j, day, kStreamRnet, (e + 1u) >> 2);
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+        float v[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u) {
+            uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
+            c += (c >= j) ? 1u : 0u;
+            if (REC && rec && e + u < k) rec[1u + e + u] = c;
+            v[u] = e + u < k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4u; ++u)
+            if (e + u < k) r = __fadd_rn(r, v[u]);
+    }
+#else
     for (uint32_t e = 0; e < k; ++e) {
         const uint32_t idx = e + 1u;
         if ((idx & 3u) == 0u) w = draw(nk, j, day, kStreamRnet, idx >> 2);
@@ -68,8 +105,9 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
         uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
         v += (v >= j) ? 1u : 0u;
         if (REC && rec) rec[1u + e] = v;
-        r = __fadd_rn(r, __ldg(inf + (size_t)v * stride + b));
+        r = __fadd_rn(r, __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + v) : v) * stride + b));
     }
+#endif
     *k_out = k;
     return r;
 }
@@ -160,7 +198,7 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 // loaded first and the random contacts are generated while they are in flight.
 // REC: the agent's exposure-notification record of the day goes to rec (when
 // not null).
-template <bool OCC = true, bool REC = false>
+template <bool OCC = true, bool REC = false, bool ROWMAP = false>
 __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out,
                                            uint32_t *rec = nullptr)
@@ -173,7 +211,9 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
     }
     *k_out = 0;
     float r = 0.0f;
-    if (P.rand_on) r = random_sum<REC>(P, I.rand_cur, jo, day, stride, b, k_out, rec);
+    if (P.rand_on)
+        r = ROWMAP && I.row_of ? random_sum<REC, true>(P, I.cur, jo, day, stride, b, k_out, rec, I.row_of)
+                               : random_sum<REC, false>(P, I.rand_cur, jo, day, stride, b, k_out, rec);
     const uint32_t k_rand = *k_out;
     uint32_t k_occ = 0;
     float s = 0.0f;

@@ -27,7 +27,8 @@ struct deabm_ctx {
     int16_t *dose1 = nullptr;
     StateRef S{};
     float *inf[2] = {nullptr, nullptr};
-    float *inf_rand[2] = {nullptr, nullptr};  // by caller id, when relabelled and the random network is on
+    float *inf_rand[2] = {nullptr, nullptr};  // by caller id: plain contexts, relabelled, random network on
+    uint32_t *row_of = nullptr;               // caller id -> row: batched contexts, relabelled
     int cur = 0;
     bool relabel = false;
     std::vector<uint32_t> new2orig;           // internal id -> caller id (relabelled only)
@@ -395,8 +396,15 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
             if (ctx->relabel && g->rand_mean > 0.0f) {
-                if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
-                if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
+                if (n_rep == 1) {
+                    if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
+                    if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
+                } else {
+                    if ((r = dalloc(ctx, &ctx->row_of, n))) return r;
+                    CU(ctx, cudaMemcpyAsync(ctx->row_of, orig2new.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
+                                            s));
+                    CU(ctx, cudaStreamSynchronize(s));  // orig2new is host staging
+                }
             }
             if (ctx->keep_lambda) {
                 if ((r = dalloc(ctx, &ctx->lam, nb))) return r;
@@ -662,6 +670,7 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         I.next = ctx->inf[c ^ 1];
         I.rand_cur = ctx->inf_rand[c] ? ctx->inf_rand[c] : ctx->inf[c];
         I.rand_next = ctx->inf_rand[c ^ 1];
+        I.row_of = ctx->row_of;
         if (kp.den_bits_orig)
             CU(ctx, cudaMemsetAsync(kp.den_bits_orig, 0, sizeof(uint32_t) * (((size_t)ctx->n + 31) / 32), ctx->stream));
         CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,

@@ -125,6 +125,9 @@ struct InfBuffers {
     float *next;
     const float *rand_cur;
     float *rand_next;  // nullptr when not relabelled
+    // caller id -> internal row (batched contexts when relabelled): random
+    // contacts then read `cur` through it and there is no copy by caller id
+    const uint32_t *row_of;
 };
 
 struct StateRef {

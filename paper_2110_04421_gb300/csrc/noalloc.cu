@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256) na_lambda_kernel(const KParams P, const R
     I.next = nullptr;
     I.rand_cur = inf;
     I.rand_next = nullptr;
+    I.row_of = nullptr;
     uint32_t k;
     lambda[j] = lambda_of<false>(P, rp, I, j, j, day, 1u, 0u, __ldg(P.age + j), &k);
 }

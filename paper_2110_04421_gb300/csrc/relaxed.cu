@@ -333,6 +333,10 @@ struct deabm_relaxed {
     double *gpart = nullptr;
     uint32_t *seeds = nullptr;
     uint32_t trace_cap = 0;
+    // one gradient (forward with checkpoints, reverse sweep) as a CUDA graph,
+    // captured for a horizon T and replayed while T stays the same
+    cudaGraphExec_t grad_graph = nullptr;
+    uint32_t graph_T = 0;
 };
 
 static thread_local std::string g_rx_err;
@@ -382,6 +386,7 @@ extern "C" void deabm_relaxed_destroy(deabm_relaxed *c)
 {
     if (!c) return;
     if (!c->allocs.empty()) (void)cudaStreamSynchronize(c->stream);
+    if (c->grad_graph) (void)cudaGraphExecDestroy(c->grad_graph);
     for (void *p : c->allocs) (void)cudaFree(p);
     delete c;
 }
@@ -593,6 +598,35 @@ static int rx_backward_device(deabm_relaxed *c, uint32_t T)
     return DEABM_OK;
 }
 
+// forward (loss into c->loss) and reverse sweep of horizon T, replayed from a
+// CUDA graph: the day loop launches about 6 kernels a day, which the graph
+// issues without a host round trip per launch
+static int rx_gradient(deabm_relaxed *c, uint32_t T)
+{
+    if (!(c->grad_graph && c->graph_T == T)) {
+        if (c->grad_graph) {
+            RCU(cudaGraphExecDestroy(c->grad_graph));
+            c->grad_graph = nullptr;
+        }
+        cudaGraph_t g;
+        RCU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int r = rx_forward_device(c, T, c->y, nullptr);
+        if (!r) r = rx_backward_device(c, T);
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (r) {
+            if (e == cudaSuccess) (void)cudaGraphDestroy(g);
+            return r;
+        }
+        RCU(e);
+        const cudaError_t ei = cudaGraphInstantiate(&c->grad_graph, g, 0);
+        (void)cudaGraphDestroy(g);
+        RCU(ei);
+        c->graph_T = T;
+    }
+    RCU(cudaGraphLaunch(c->grad_graph, c->stream));
+    return DEABM_OK;
+}
+
 static int rx_check(deabm_relaxed *c, uint32_t T)
 {
     if (!c) return rx_fail(DEABM_EINVAL, "ctx is NULL");
@@ -620,8 +654,7 @@ extern "C" int deabm_grad(deabm_relaxed *c, uint32_t T, const float *theta, cons
     if (!theta || !target) return rx_fail(DEABM_EINVAL, "theta and target are required");
     RCU(cudaMemcpyAsync(c->theta, theta, 4 * kTheta, cudaMemcpyHostToDevice, c->stream));
     RCU(cudaMemcpyAsync(c->y, target, 4ull * T, cudaMemcpyHostToDevice, c->stream));
-    if ((r = rx_forward_device(c, T, c->y, nullptr))) return r;
-    if ((r = rx_backward_device(c, T))) return r;
+    if ((r = rx_gradient(c, T))) return r;
     if (loss) RCU(cudaMemcpyAsync(loss, c->loss, 4, cudaMemcpyDeviceToHost, c->stream));
     if (grad) RCU(cudaMemcpyAsync(grad, c->grad, 4 * kTheta, cudaMemcpyDeviceToHost, c->stream));
     if (incidence) RCU(cudaMemcpyAsync(incidence, c->I, 4ull * T, cudaMemcpyDeviceToHost, c->stream));
@@ -646,8 +679,8 @@ extern "C" int deabm_calibrate(deabm_relaxed *c, uint32_t T, const float *theta0
     RCU(cudaMemsetAsync(c->adam_m, 0, 4 * kTheta, c->stream));
     RCU(cudaMemsetAsync(c->adam_v, 0, 4 * kTheta, c->stream));
     for (uint32_t it = 0; it < steps; ++it) {
-        if ((r = rx_forward_device(c, T, c->y, c->loss_trace + it))) return r;
-        if ((r = rx_backward_device(c, T))) return r;
+        if ((r = rx_gradient(c, T))) return r;
+        RCU(cudaMemcpyAsync(c->loss_trace + it, c->loss, 4, cudaMemcpyDeviceToDevice, c->stream));
         adam_kernel<<<1, 32, 0, c->stream>>>(c->theta, c->adam_m, c->adam_v, c->grad, lr, 0.9f, 0.999f, 1e-8f, (int)it + 1);
         RCU(cudaGetLastError());
     }

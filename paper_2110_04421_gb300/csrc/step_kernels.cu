@@ -44,7 +44,7 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 // inside the library changes no result.
 // DEN: exposure notification on (plain contexts): an app holder records the day's
 // contacts, a positive app holder is marked for the notification pass.
-template <bool OCC = true, bool DEN = false>
+template <bool OCC = true, bool DEN = false, bool ROWMAP = false>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
                                           float *p_out, int *new_stage, bool *infected, uint32_t *k_out,
@@ -56,7 +56,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     uint32_t *rec = nullptr;
     if (DEN && (S.flags[i] & DEABM_FL_APP))
         rec = P.den_ring + ((size_t)(day % P.den_window) * P.n_app + __ldg(P.app_rank + j)) * P.den_slots;
-    const float lam = lambda_of<OCC, DEN>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
+    const float lam = lambda_of<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
     AgentState a;
     a.st = S.stage[i];
     a.tm = S.timer[i];
@@ -112,18 +112,31 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
 
 // block-level aggregation of the day's counters; every thread of the block calls it
 #ifndef DEABM_HIST_MATCH
-#define DEABM_HIST_MATCH 0  // 1: warp-aggregated (match.any) stage counts; 0: one shared atomic per agent
+#define DEABM_HIST_MATCH 0  // 1: warp-aggregated (match.any) stage counts; 2: warp-reduced packed counts;
+                            // 0: one shared atomic per agent
 #endif
 __device__ __forceinline__ void count_day(bool active, int st, bool infected, uint32_t k, int *s_hist, int *s_new,
                                           unsigned long long *s_msgs)
 {
     const unsigned full = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
-#if DEABM_HIST_MATCH
+#if DEABM_HIST_MATCH == 1
     const unsigned act = __ballot_sync(full, active);
     if (active) {
         const unsigned m = __match_any_sync(act, st);
         if (lane == __ffs(m) - 1) atomicAdd(&s_hist[st], __popc(m));
+    }
+#elif DEABM_HIST_MATCH == 2
+    // the warp's 11 stage counts (each <= 32) packed 6 bits apiece into three
+    // words, summed by three warp reductions; lane s adds stage s's count
+    const uint32_t one = active ? 1u : 0u;
+    const uint32_t r0 = __reduce_add_sync(full, st < 5 ? one << (6 * st) : 0u);
+    const uint32_t r1 = __reduce_add_sync(full, (st >= 5 && st < 10) ? one << (6 * (st - 5)) : 0u);
+    const uint32_t r2 = __reduce_add_sync(full, st == 10 ? one : 0u);
+    if (lane < DEABM_N_STAGE) {
+        const uint32_t word = lane < 5 ? r0 : lane < 10 ? r1 : r2;
+        const int c = (int)((word >> (6 * (lane % 5))) & 63u);
+        if (c) atomicAdd(&s_hist[lane], c);
     }
 #else
     if (active) atomicAdd(&s_hist[st], 1);
@@ -211,7 +224,8 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     uint32_t k = 0;
     if (active) {
         const Rep &rp = P.rep[b];
-        agent_day(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k);
+        agent_day<true, false, true>(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st,
+                                     &infected, &k);
         atomicAdd(&s_cnt[st][lane], 1);
         if (infected) atomicAdd(&s_cnt[DEABM_N_STAGE][lane], 1);
     }
@@ -264,6 +278,7 @@ __global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restr
         I.next = inf_next + sp.base;
         I.rand_cur = I.cur;
         I.rand_next = nullptr;
+        I.row_of = nullptr;
         StateRef Sp;
         Sp.stage = S.stage + sp.base;
         Sp.timer = S.timer + sp.base;
@@ -412,13 +427,26 @@ __global__ void __launch_bounds__(256) step_batch4_kernel(const KParams P, uint3
             while (kr < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kr])) ++kr;
             float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const uint64_t nm1 = (uint64_t)(P.n - 1u);
-            for (uint32_t e = 0; e < kr; ++e) {
-                const uint32_t idx = e + 1u;
-                if ((idx & 3u) == 0u) w = draw(nk, jo, day, kStreamRnet, idx >> 2);
-                const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
-                uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
-                v += (v >= jo) ? 1u : 0u;
-                add4(r, __ldg((const float4 *)(I.rand_cur + (size_t)v * B + b0)));
+            const float *panel = I.row_of ? I.cur : I.rand_cur;
+            // as random_sum: contacts 0..2 from block 0, then four per block,
+            // each block's gathers issued together and added in draw order
+            for (uint32_t e = 0; e < kr; e += (e == 0u ? 3u : 4u)) {
+                if (e) w = draw(nk, jo, day, kStreamRnet, (e + 1u) >> 2);
+                const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+                const uint32_t u0 = e == 0u ? 1u : 0u;  // block 0 starts at word 1
+                float4 v[4];
+#pragma unroll
+                for (uint32_t u = 0; u < 4u; ++u) {
+                    const uint32_t c = e + u - u0;  // contact index of word u
+                    uint32_t src = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
+                    src += (src >= jo) ? 1u : 0u;
+                    const bool ok = u >= u0 && c < kr;
+                    v[u] = ok ? __ldg((const float4 *)(panel + (size_t)(I.row_of ? __ldg(I.row_of + src) : src) * B + b0))
+                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < 4u; ++u)
+                    if (u >= u0 && e + u - u0 < kr) add4(r, v[u]);
             }
             const float rv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
