@@ -51,65 +51,81 @@ constexpr uint32_t kDenOccAt = 16;
 // the other n-1 agents.  `inf` is indexed by the caller's ids, or (ROWMAP) by
 // internal rows through row_of.  REC: also write the contacts to
 // rec[1..] when rec is not null.
-#ifndef DEABM_RAND_BATCH
-#define DEABM_RAND_BATCH 1  // 1: a Philox block's contacts gathered together; 0: one contact at a time
+#ifndef DEABM_RAND_DEFER
+#define DEABM_RAND_DEFER 0  // 1: block 0's gathers are added only after the stored networks' sums (more
+                            // spills at 40 registers; measured 2 % slower at N = 2e6)
 #endif
-template <bool REC = false, bool ROWMAP = false>
-__device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
-                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
-                                            uint32_t *rec = nullptr, const uint32_t *row_of = nullptr)
+
+// The random contacts of block 0 (count word, then contacts 0..2), their
+// gathers issued but not yet added.
+struct RandHead {
+    uint32_t k;
+    float v[3];
+};
+
+template <bool REC, bool ROWMAP>
+__device__ __forceinline__ RandHead random_head(const KParams &P, const float *__restrict__ inf, uint32_t j,
+                                                uint32_t day, uint32_t stride, uint32_t b, uint32_t *rec,
+                                                const uint32_t *row_of)
 {
     const uint2 nk = seed_key(P.net_seed);
-    uint4 w = draw(nk, j, day, kStreamRnet, 0u);
-    uint32_t k = 0;
-    while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
-    float r = 0.0f;
+    const uint4 w = draw(nk, j, day, kStreamRnet, 0u);
+    RandHead h;
+    h.k = 0;
+    while (h.k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[h.k])) ++h.k;
     const uint64_t nm1 = (uint64_t)(P.n - 1u);
-#if DEABM_RAND_BATCH
-    // contacts 0..2 from words 1..3 of block 0, then four per block: the block's
-    // gathers are issued together and added in draw order
-    {
-        const uint32_t x[3] = {w.y, w.z, w.w};
-        float v[3];
+    const uint32_t x[3] = {w.y, w.z, w.w};
 #pragma unroll
-        for (uint32_t u = 0; u < 3u; ++u) {
-            uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
-            c += (c >= j) ? 1u : 0u;
-            if (REC && rec && u < k) rec[1u + u] = c;
-            v[u] = u < k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 3u; ++u)
-            if (u < k) r = __fadd_rn(r, v[u]);
+    for (uint32_t u = 0; u < 3u; ++u) {
+        uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
+        c += (c >= j) ? 1u : 0u;
+        if (REC && rec && u < h.k) rec[1u + u] = c;
+        h.v[u] = u < h.k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
     }
-    for (uint32_t e = 3u; e < k; e += 4u) {
-        w = draw(nk, j, day, kStreamRnet, (e + 1u) >> 2);
+    return h;
+}
+
+// The sum over all k random contacts in draw order: block 0's values from the
+// head, then four contacts per further block, each block's gathers together.
+template <bool REC, bool ROWMAP>
+__device__ __forceinline__ float random_tail(const KParams &P, const float *__restrict__ inf, uint32_t j,
+                                             uint32_t day, uint32_t stride, uint32_t b, const RandHead &h,
+                                             uint32_t *rec, const uint32_t *row_of)
+{
+    float r = 0.0f;
+#pragma unroll
+    for (uint32_t u = 0; u < 3u; ++u)
+        if (u < h.k) r = __fadd_rn(r, h.v[u]);
+    const uint2 nk = seed_key(P.net_seed);
+    const uint64_t nm1 = (uint64_t)(P.n - 1u);
+    for (uint32_t e = 3u; e < h.k; e += 4u) {
+        const uint4 w = draw(nk, j, day, kStreamRnet, (e + 1u) >> 2);
         const uint32_t x[4] = {w.x, w.y, w.z, w.w};
         float v[4];
 #pragma unroll
         for (uint32_t u = 0; u < 4u; ++u) {
             uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
             c += (c >= j) ? 1u : 0u;
-            if (REC && rec && e + u < k) rec[1u + e + u] = c;
-            v[u] = e + u < k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
+            if (REC && rec && e + u < h.k) rec[1u + e + u] = c;
+            v[u] = e + u < h.k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
         }
 #pragma unroll
         for (uint32_t u = 0; u < 4u; ++u)
-            if (e + u < k) r = __fadd_rn(r, v[u]);
+            if (e + u < h.k) r = __fadd_rn(r, v[u]);
     }
-#else
-    for (uint32_t e = 0; e < k; ++e) {
-        const uint32_t idx = e + 1u;
-        if ((idx & 3u) == 0u) w = draw(nk, j, day, kStreamRnet, idx >> 2);
-        const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
-        uint32_t v = (uint32_t)(((uint64_t)x * nm1) >> 32);
-        v += (v >= j) ? 1u : 0u;
-        if (REC && rec) rec[1u + e] = v;
-        r = __fadd_rn(r, __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + v) : v) * stride + b));
-    }
-#endif
-    *k_out = k;
     return r;
+}
+
+// All random in-contacts at once (head and tail back to back).  REC: also write
+// the contacts to rec[1..] when rec is not null.
+template <bool REC = false, bool ROWMAP = false>
+__device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
+                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
+                                            uint32_t *rec = nullptr, const uint32_t *row_of = nullptr)
+{
+    const RandHead h = random_head<REC, ROWMAP>(P, inf, j, day, stride, b, rec, row_of);
+    *k_out = h.k;
+    return random_tail<REC, ROWMAP>(P, inf, j, day, stride, b, h, rec, row_of);
 }
 
 // Place of the member an occupation contact lands on: word x mapped to
@@ -210,11 +226,22 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
         end[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j + 1) : 0u;
     }
     *k_out = 0;
-    float r = 0.0f;
-    if (P.rand_on)
-        r = ROWMAP && I.row_of ? random_sum<REC, true>(P, I.cur, jo, day, stride, b, k_out, rec, I.row_of)
-                               : random_sum<REC, false>(P, I.rand_cur, jo, day, stride, b, k_out, rec);
-    const uint32_t k_rand = *k_out;
+    const bool rmap = ROWMAP && I.row_of != nullptr;
+    const float *rinf = rmap ? I.cur : I.rand_cur;
+    RandHead head{0u, {0.0f, 0.0f, 0.0f}};
+#if !DEABM_RAND_DEFER
+    float r_now = 0.0f;
+#endif
+    if (P.rand_on) {  // block 0's gathers go out now and are added after the stored networks
+        head = rmap ? random_head<REC, true>(P, rinf, jo, day, stride, b, rec, I.row_of)
+                    : random_head<REC, false>(P, rinf, jo, day, stride, b, rec, nullptr);
+#if !DEABM_RAND_DEFER
+        r_now = rmap ? random_tail<REC, true>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
+                     : random_tail<REC, false>(P, rinf, jo, day, stride, b, head, rec, nullptr);
+#endif
+    }
+    const uint32_t k_rand = head.k;
+    *k_out = k_rand;
     uint32_t k_occ = 0;
     float s = 0.0f;
 #pragma unroll
@@ -232,6 +259,12 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
     }
     if (REC && rec) rec[0] = k_rand | (k_occ << 8);
     if (P.rand_on) {
+#if DEABM_RAND_DEFER
+        const float r = rmap ? random_tail<REC, true>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
+                             : random_tail<REC, false>(P, rinf, jo, day, stride, b, head, rec, nullptr);
+#else
+        const float r = r_now;
+#endif
         const float term = __fmul_rn(rp.B_rand, r);
         s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
     }

@@ -337,6 +337,7 @@ struct deabm_relaxed {
     // captured for a horizon T and replayed while T stays the same
     cudaGraphExec_t grad_graph = nullptr;
     uint32_t graph_T = 0;
+    cudaStream_t cap_stream = nullptr;  // capture happens here (the caller's stream may be the legacy one)
 };
 
 static thread_local std::string g_rx_err;
@@ -387,6 +388,7 @@ extern "C" void deabm_relaxed_destroy(deabm_relaxed *c)
     if (!c) return;
     if (!c->allocs.empty()) (void)cudaStreamSynchronize(c->stream);
     if (c->grad_graph) (void)cudaGraphExecDestroy(c->grad_graph);
+    if (c->cap_stream) (void)cudaStreamDestroy(c->cap_stream);
     for (void *p : c->allocs) (void)cudaFree(p);
     delete c;
 }
@@ -599,8 +601,10 @@ static int rx_backward_device(deabm_relaxed *c, uint32_t T)
 }
 
 // forward (loss into c->loss) and reverse sweep of horizon T, replayed from a
-// CUDA graph: the day loop launches about 6 kernels a day, which the graph
-// issues without a host round trip per launch
+// CUDA graph on the caller's stream: the day loop launches about 6 kernels a
+// day, which the graph issues without a host round trip per launch.  The graph
+// is recorded on a private stream, since the legacy default stream cannot be
+// captured.
 static int rx_gradient(deabm_relaxed *c, uint32_t T)
 {
     if (!(c->grad_graph && c->graph_T == T)) {
@@ -608,11 +612,15 @@ static int rx_gradient(deabm_relaxed *c, uint32_t T)
             RCU(cudaGraphExecDestroy(c->grad_graph));
             c->grad_graph = nullptr;
         }
+        if (!c->cap_stream) RCU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t g;
-        RCU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaStream_t user = c->stream;
+        RCU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c->stream = c->cap_stream;  // the launchers below record into the graph
         int r = rx_forward_device(c, T, c->y, nullptr);
         if (!r) r = rx_backward_device(c, T);
-        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->stream = user;
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
         if (r) {
             if (e == cudaSuccess) (void)cudaGraphDestroy(g);
             return r;
