@@ -181,11 +181,13 @@ typedef struct {
     uint32_t vax_nonsterile; /* 0: immunity is sterilising (stage VAX); 1: non-sterilising (Sec. 5, second
                                 version): the agent stays susceptible with flag DEABM_FL_IMMUNE and any
                                 later infection is asymptomatic */
-    uint32_t locality_order; /* 1: number the agents internally in breadth-first order of the
-                                static network with the most edges, so that the members of a
-                                group sit next to each other in device memory; results and
-                                every array the ABI returns are unchanged (random draws and
-                                outputs use the caller's agent ids) */
+    uint32_t locality_order; /* 1: number the agents internally so that the members of a group sit
+                                next to each other in device memory: agents grouped by the smallest
+                                id reaching them along the in-edges of the stored network with the
+                                most edges (8 rounds of min-label propagation on the device), groups
+                                in label order, ids ascending inside a group; results and every
+                                array the ABI returns are unchanged (random draws and outputs use
+                                the caller's agent ids) */
     /* Digital exposure notification (Sec. 4.2); plain contexts with test_on only.
      * At create (and reset) agent j gets DEABM_FL_APP when word x of Philox
      * stream 6 keyed (seed, j, day word 0xFFFFFFFD) is below floor(den_adoption

@@ -33,6 +33,7 @@ struct deabm_ctx {
     bool relabel = false;
     std::vector<uint32_t> new2orig;           // internal id -> caller id (relabelled only)
     uint32_t *orig_id = nullptr;
+    void *perm_scratch = nullptr;             // caller-order copies for the readbacks (relabelled only)
     // daily occupation networks (internal rows in occupation order)
     uint32_t n_occ = 0;
     uint32_t *occ_gid = nullptr, *occ_start = nullptr;
@@ -212,37 +213,32 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
 }
 
 // ---------------------------------------------------------------- locality order
-// Breadth-first order over the in-edges of the static network with the most
-// edges, roots taken in id order: the members of a group (a workplace, a
-// household) end up with consecutive internal ids, so a destination's gathers
-// hit the same cache lines as its neighbours'.
-static void locality_order(const deabm_graph *g, std::vector<uint32_t> &order)
-{
-    const uint32_t n = g->n_agents;
-    uint32_t best = 0;
-    for (uint32_t k = 1; k < g->n_nets; ++k)
-        if (g->row_ptr[k][n] > g->row_ptr[best][n]) best = k;
-    const uint32_t *rp = g->row_ptr[best], *col = g->col[best];
-    std::vector<uint8_t> seen(n, 0);
-    order.clear();
-    order.reserve(n);
-    for (uint32_t root = 0; root < n; ++root) {
-        if (seen[root]) continue;
-        seen[root] = 1;
-        size_t head = order.size();
-        order.push_back(root);
-        while (head < order.size()) {
-            const uint32_t v = order[head++];
-            for (uint32_t e = rp[v]; e < rp[v + 1]; ++e) {
-                const uint32_t u = col[e];
-                if (!seen[u]) {
-                    seen[u] = 1;
-                    order.push_back(u);
-                }
-            }
-        }
+// Device scratch freed when the creating call returns, on every path.
+struct DevScratch {
+    std::vector<void *> ptrs;
+    ~DevScratch()
+    {
+        for (void *q : ptrs) (void)cudaFree(q);
     }
+};
+
+template <class T>
+static int scratch_alloc(deabm_ctx *ctx, DevScratch &sc, T **out, size_t count)
+{
+    void *ptr = nullptr;
+    const cudaError_t e = cudaMalloc(&ptr, (count ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu scratch bytes failed: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    sc.ptrs.push_back(ptr);
+    *out = (T *)ptr;
+    return DEABM_OK;
 }
+
+// Rounds of min-label propagation that fix the locality order (even).
+constexpr uint32_t kLocalityRounds = 8;
 
 // ---------------------------------------------------------------- occupation order
 // Occupations in id order, the members of each in ascending caller id: the
@@ -333,46 +329,62 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             cudaStream_t s = ctx->stream;
             int r;
             ctx->relabel = (p->locality_order != 0 && g->n_nets > 0) || g->n_occ > 0;
-            std::vector<uint32_t> orig2new, occ_start;
-            if (g->n_occ) {
-                occupation_order(g, ctx->new2orig, occ_start);
-                orig2new.resize(n);
-                for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
-            } else if (ctx->relabel) {
-                locality_order(g, ctx->new2orig);
-                orig2new.resize(n);
-                for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
-            }
-            auto orig_of = [&](uint32_t q) { return ctx->relabel ? ctx->new2orig[q] : q; };
-            std::vector<uint32_t> rp_new, col_new;
+            // the stored networks go to the device as given: in place when the
+            // numbering stays, else into scratch to be renumbered there
+            DevScratch sc;
+            uint32_t *src_rp[DEABM_MAX_NETS] = {}, *src_col[DEABM_MAX_NETS] = {};
+            uint32_t best = 0;
             for (uint32_t k = 0; k < g->n_nets; ++k) {
                 const uint32_t E = g->row_ptr[k][n];
                 ctx->static_edges += E;
+                if (E > g->row_ptr[best][n]) best = k;
                 if ((r = dalloc(ctx, &ctx->row_ptr[k], (size_t)n + 1))) return r;
                 if ((r = dalloc(ctx, &ctx->col[k], E))) return r;
-                const uint32_t *rp_src = g->row_ptr[k], *col_src = g->col[k];
+                src_rp[k] = ctx->row_ptr[k];
+                src_col[k] = ctx->col[k];
                 if (ctx->relabel) {
-                    // rows in internal order, each row's edges kept in the caller's order
-                    rp_new.assign((size_t)n + 1, 0);
-                    col_new.resize(E);
-                    for (uint32_t q = 0; q < n; ++q) {
-                        const uint32_t o = ctx->new2orig[q], b0 = g->row_ptr[k][o], b1 = g->row_ptr[k][o + 1];
-                        rp_new[q + 1] = rp_new[q] + (b1 - b0);
-                        for (uint32_t e = b0; e < b1; ++e) col_new[rp_new[q] + (e - b0)] = orig2new[g->col[k][e]];
-                    }
-                    rp_src = rp_new.data();
-                    col_src = col_new.data();
+                    if ((r = scratch_alloc(ctx, sc, &src_rp[k], (size_t)n + 1))) return r;
+                    if ((r = scratch_alloc(ctx, sc, &src_col[k], E))) return r;
                 }
-                CU(ctx, cudaMemcpyAsync(ctx->row_ptr[k], rp_src, sizeof(uint32_t) * ((size_t)n + 1),
+                CU(ctx, cudaMemcpyAsync(src_rp[k], g->row_ptr[k], sizeof(uint32_t) * ((size_t)n + 1),
                                         cudaMemcpyHostToDevice, s));
-                if (E) CU(ctx, cudaMemcpyAsync(ctx->col[k], col_src, sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
-                CU(ctx, cudaStreamSynchronize(s));  // the staging vectors are reused by the next network
+                if (E) CU(ctx, cudaMemcpyAsync(src_col[k], g->col[k], sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
+            }
+            std::vector<uint32_t> orig2new, occ_start;
+            if (g->n_occ) {
+                occupation_order(g, ctx->new2orig, occ_start);
+            } else if (ctx->relabel) {
+                // groups by the smallest id reaching them along the densest network's
+                // in-edges (computed on the device), ids ascending inside a group
+                uint32_t *label, *tmp;
+                if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &tmp, n))) return r;
+                CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, s));
+                std::vector<uint32_t> lab(n), cnt((size_t)n + 1, 0);
+                CU(ctx, cudaMemcpyAsync(lab.data(), label, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
+                CU(ctx, cudaStreamSynchronize(s));
+                for (uint32_t v = 0; v < n; ++v) cnt[lab[v] + 1]++;
+                for (uint32_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
+                ctx->new2orig.resize(n);
+                for (uint32_t v = 0; v < n; ++v) ctx->new2orig[cnt[lab[v]]++] = v;
             }
             if (ctx->relabel) {
+                orig2new.resize(n);
+                for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
+                uint32_t *d_o2n, *d_scan;
                 if ((r = dalloc(ctx, &ctx->orig_id, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &d_o2n, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &d_scan, scan_scratch_words((size_t)n + 1)))) return r;
                 CU(ctx, cudaMemcpyAsync(ctx->orig_id, ctx->new2orig.data(), sizeof(uint32_t) * n,
                                         cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(d_o2n, orig2new.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+                // rows in internal order, each row's edges kept in the caller's order
+                for (uint32_t k = 0; k < g->n_nets; ++k)
+                    CU(ctx, launch_csr_renumber(src_rp[k], src_col[k], ctx->orig_id, d_o2n, n, ctx->row_ptr[k],
+                                                ctx->col[k], d_scan, s));
             }
+            CU(ctx, cudaStreamSynchronize(s));  // host staging and device scratch end here
+            auto orig_of = [&](uint32_t q) { return ctx->relabel ? ctx->new2orig[q] : q; };
             if (g->n_occ) {
                 ctx->n_occ = g->n_occ;
                 std::vector<uint32_t> gid(n);
@@ -757,6 +769,17 @@ extern "C" int deabm_run(deabm_ctx *ctx, uint32_t T, int32_t *new_inf, int32_t *
     return DEABM_OK;
 }
 
+// device scratch of n * n_rep * 4 bytes for caller-order readbacks (relabelled contexts)
+static int perm_scratch_ready(deabm_ctx *ctx)
+{
+    if (!ctx->relabel || ctx->perm_scratch) return DEABM_OK;
+    uint32_t *p;
+    int r = dalloc(ctx, &p, (size_t)ctx->n * ctx->n_rep);
+    if (r) return r;
+    ctx->perm_scratch = p;
+    return DEABM_OK;
+}
+
 extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags,
                                uint8_t *qt, float *lambda, float *p)
 {
@@ -764,22 +787,19 @@ extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, in
     if ((lambda || p) && !ctx->keep_lambda) return fail(ctx, DEABM_ESTATE, "created without keep_lambda");
     const size_t nb = ctx->ragged ? (size_t)ctx->n : (size_t)ctx->n * ctx->n_rep;
     cudaStream_t s = ctx->stream;
-    // device arrays are in internal order: copy, then put each agent back at its caller id
+    // device arrays are in internal order: when relabelled, a kernel puts each
+    // agent back at its caller id in device scratch, which is then copied out
+    int r;
+    if ((r = perm_scratch_ready(ctx))) return r;
     auto fetch = [&](void *dst, const void *src, size_t elem) -> int {
         if (!dst) return DEABM_OK;
-        if (!ctx->relabel) {
-            CU(ctx, cudaMemcpyAsync(dst, src, nb * elem, cudaMemcpyDeviceToHost, s));
-            return DEABM_OK;
+        if (ctx->relabel) {
+            CU(ctx, launch_to_caller(ctx->perm_scratch, src, ctx->orig_id, ctx->n, ctx->n_rep, (uint32_t)elem, s));
+            src = ctx->perm_scratch;
         }
-        std::vector<uint8_t> tmp(nb * elem);
-        CU(ctx, cudaMemcpyAsync(tmp.data(), src, nb * elem, cudaMemcpyDeviceToHost, s));
-        CU(ctx, cudaStreamSynchronize(s));
-        const size_t row = (size_t)ctx->n_rep * elem;
-        for (uint32_t q = 0; q < ctx->n; ++q)
-            std::memcpy((uint8_t *)dst + (size_t)ctx->new2orig[q] * row, tmp.data() + (size_t)q * row, row);
+        CU(ctx, cudaMemcpyAsync(dst, src, nb * elem, cudaMemcpyDeviceToHost, s));
         return DEABM_OK;
     };
-    int r;
     if ((r = fetch(stage, ctx->S.stage, 1))) return r;
     if ((r = fetch(timer, ctx->S.timer, 2))) return r;
     if ((r = fetch(tinf, ctx->S.tinf, 2))) return r;
