@@ -40,10 +40,11 @@ __device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const
     return h;
 }
 
-// Exposure-notification record of one (day, agent), kept for the last
+// Exposure-notification record of one (day, app holder), kept for the last
 // den_window days: word 0 = random count | occupation count << 8, the random
 // contacts (caller ids) from word 1, the occupation contacts (internal rows)
-// from word kDenOccAt.
+// from word kDenOccAt.  Word e of the record at rec lives at rec[e * n_app]
+// (one plane per word, app holders side by side).
 constexpr uint32_t kDenOccAt = 16;
 
 // Random in-contacts of agent j (the caller's id) on `day`: count from word 0 of
@@ -79,7 +80,7 @@ __device__ __forceinline__ RandHead random_head(const KParams &P, const float *_
     for (uint32_t u = 0; u < 3u; ++u) {
         uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
         c += (c >= j) ? 1u : 0u;
-        if (REC && rec && u < h.k) rec[1u + u] = c;
+        if (REC && rec && u < h.k) rec[(size_t)(1u + u) * P.n_app] = c;
         h.v[u] = u < h.k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
     }
     return h;
@@ -106,7 +107,7 @@ __device__ __forceinline__ float random_tail(const KParams &P, const float *__re
         for (uint32_t u = 0; u < 4u; ++u) {
             uint32_t c = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
             c += (c >= j) ? 1u : 0u;
-            if (REC && rec && e + u < h.k) rec[1u + e + u] = c;
+            if (REC && rec && e + u < h.k) rec[(size_t)(1u + e + u) * P.n_app] = c;
             v[u] = e + u < h.k ? __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b) : 0.0f;
         }
 #pragma unroll
@@ -168,7 +169,7 @@ __device__ __forceinline__ float occ_ws_sum(const KParams &P, const float *__res
                 r = own + off;
                 r = r >= size ? r - size : r;
             }
-            if (REC && rec && e + u < k) rec[kDenOccAt + e + u] = beg + r;
+            if (REC && rec && e + u < k) rec[(size_t)(kDenOccAt + e + u) * P.n_app] = beg + r;
             v[u] = (e + u < k) ? __ldg(inf + (size_t)(beg + r) * stride + b) : 0.0f;
         }
         h = __fadd_rn(h, v[0]);
@@ -197,7 +198,7 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 #pragma unroll
         for (uint32_t u = 0; u < 4u; ++u) {
             const uint32_t row = beg + occ_place(x[u], size - 1u, own);
-            if (REC && rec && e + u < k) rec[kDenOccAt + e + u] = row;
+            if (REC && rec && e + u < k) rec[(size_t)(kDenOccAt + e + u) * P.n_app] = row;
             v[u] = (e + u < k) ? __ldg(inf + (size_t)row * stride + b) : 0.0f;
         }
 #pragma unroll

@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "deabm.h"
@@ -118,6 +120,34 @@ static uint64_t threshold(double p)
 static bool prob_ok(double p) { return p >= 0.0 && p <= 1.0; }
 
 // ---------------------------------------------------------------- validation
+// The first row in [0, n) for which bad(row) holds, or n: rows split over host
+// threads (validation of a graph of tens of millions of edges is otherwise the
+// largest host cost of create).
+template <class F>
+static uint32_t first_bad_row(uint32_t n, const F &bad)
+{
+    const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const uint32_t T = n < (1u << 16) ? 1u : hw;
+    std::vector<uint32_t> found(T, n);
+    auto work = [&](uint32_t t) {
+        const uint32_t r0 = (uint32_t)((uint64_t)n * t / T), r1 = (uint32_t)((uint64_t)n * (t + 1) / T);
+        for (uint32_t j = r0; j < r1; ++j)
+            if (bad(j)) {
+                found[t] = j;
+                return;
+            }
+    };
+    if (T == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> th;
+        th.reserve(T);
+        for (uint32_t t = 0; t < T; ++t) th.emplace_back(work, t);
+        for (auto &x : th) x.join();
+    }
+    return *std::min_element(found.begin(), found.end());
+}
+
 static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a, const deabm_params *p,
                     uint32_t n_rep, const float *rep_params)
 {
@@ -132,10 +162,16 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         const uint32_t *rp = g->row_ptr[k], *col = g->col[k];
         if (!rp) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] is NULL", k);
         if (rp[0] != 0) return fail(ctx, DEABM_EINVAL, "row_ptr[%u][0] != 0", k);
-        for (uint32_t j = 0; j < n; ++j)
-            if (rp[j + 1] < rp[j]) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] decreases at row %u", k, j);
+        uint32_t j = first_bad_row(n, [&](uint32_t q) { return rp[q + 1] < rp[q]; });
+        if (j < n) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] decreases at row %u", k, j);
         if (rp[n] > 0 && !col) return fail(ctx, DEABM_EINVAL, "col[%u] is NULL", k);
-        for (uint32_t j = 0; j < n; ++j)
+        // rows are non-decreasing from here on, so every row's edges lie inside col
+        j = first_bad_row(n, [&](uint32_t q) {
+            for (uint32_t e = rp[q]; e < rp[q + 1]; ++e)
+                if (col[e] >= n || col[e] == q) return true;
+            return false;
+        });
+        if (j < n)
             for (uint32_t e = rp[j]; e < rp[j + 1]; ++e) {
                 if (col[e] >= n) return fail(ctx, DEABM_EINVAL, "col[%u][%u] = %u >= n_agents", k, e, col[e]);
                 if (col[e] == j) return fail(ctx, DEABM_EINVAL, "self-loop at row %u of network %u", j, k);

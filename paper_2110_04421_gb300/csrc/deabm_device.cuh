@@ -109,8 +109,9 @@ struct KParams {
     uint32_t *den_bits, *den_bits_orig;
     int32_t *den_pos;           // [day] positive app holders of the day
     // the app holders: their rows in ascending order, and each row's rank among
-    // them; each app holder's in-contacts of the last den_window days: record of
-    // (day d, rank a) at den_ring + ((d % den_window) * n_app + a) * den_slots
+    // them; each app holder's in-contacts of the last den_window days: word e of
+    // the record of (day d, rank a) at den_ring[((d % den_window) * den_slots + e)
+    // * n_app + a]
     uint32_t n_app;
     const uint32_t *app_rows, *app_rank;
     uint32_t *den_ring;

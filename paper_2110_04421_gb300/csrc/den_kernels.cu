@@ -5,7 +5,8 @@
 // centred, as a gather: after the day's update every eligible app holder j
 // walks its own in-contacts of those days -- its stored CSR rows, and the daily
 // occupation and random contacts the day kernel recorded for app holders while
-// drawing them (a ring of den_window records per app holder) -- and looks each
+// drawing them (a ring of den_window records per app holder, stored as word
+// planes) -- and looks each
 // source up in the day's bit map of positive app holders.  One thread per app
 // holder, app holders listed in row order.
 #include <cuda_runtime.h>
@@ -37,37 +38,35 @@ __device__ __forceinline__ bool den_static_hit(const KParams &P, uint32_t j)
     return hit;
 }
 
-// the random and occupation in-contacts of row j on the days [d0, d1), from the
-// records the day kernel wrote while drawing them.  Four days at a time: their
-// first 16 bytes (header and three random contacts, which is all of most days'
-// random contacts) are loaded together, the rest on demand.
+// the random and occupation in-contacts of app holder a on the days [d0, d1),
+// from the records the day kernel wrote while drawing them.  Records are word
+// planes over the app holders, so a warp's loads of one word are coalesced.
+// Four days at a time: their headers and first three random contacts (all of
+// most days' random contacts) are loaded together, the rest on demand.
 __device__ __forceinline__ bool den_ring_hit(const KParams &P, uint32_t a, uint32_t d0, uint32_t d1)
 {
     const uint32_t *src_rand = P.den_bits_orig ? P.den_bits_orig : P.den_bits;
+    const size_t plane = P.n_app;
     bool hit = false;
     for (uint32_t c0 = d0; c0 < d1 && !hit; c0 += 4u) {
-        uint4 q[4];
+        uint32_t h[4], w1[4], w2[4], w3[4];
         const uint32_t *rec[4];
 #pragma unroll
         for (uint32_t u = 0; u < 4u; ++u) {
-            rec[u] = P.den_ring + ((size_t)((c0 + u) % P.den_window) * P.n_app + a) * P.den_slots;
-            q[u] = c0 + u < d1 ? __ldg((const uint4 *)rec[u]) : make_uint4(0u, 0u, 0u, 0u);
+            rec[u] = P.den_ring + (size_t)((c0 + u) % P.den_window) * P.den_slots * plane + a;
+            const bool ok = c0 + u < d1;
+            h[u] = ok ? __ldg(rec[u]) : 0u;
+            w1[u] = ok ? __ldg(rec[u] + plane) : 0u;
+            w2[u] = ok ? __ldg(rec[u] + 2 * plane) : 0u;
+            w3[u] = ok ? __ldg(rec[u] + 3 * plane) : 0u;
         }
 #pragma unroll
         for (uint32_t u = 0; u < 4u; ++u) {
-            const uint32_t kr = q[u].x & 0xFFu, ko = q[u].x >> 8;
-            hit |= (kr > 0u && bit_of(src_rand, q[u].y)) | (kr > 1u && bit_of(src_rand, q[u].z)) |
-                   (kr > 2u && bit_of(src_rand, q[u].w));
-            for (uint32_t e = 4u; e <= kr; e += 4u) {
-                const uint4 v = __ldg((const uint4 *)(rec[u] + e));
-                hit |= bit_of(src_rand, v.x) | (e + 1u <= kr && bit_of(src_rand, v.y)) |
-                       (e + 2u <= kr && bit_of(src_rand, v.z)) | (e + 3u <= kr && bit_of(src_rand, v.w));
-            }
-            for (uint32_t e = 0; e < ko; e += 4u) {
-                const uint4 v = __ldg((const uint4 *)(rec[u] + kDenOccAt + e));
-                hit |= bit_of(P.den_bits, v.x) | (e + 1u < ko && bit_of(P.den_bits, v.y)) |
-                       (e + 2u < ko && bit_of(P.den_bits, v.z)) | (e + 3u < ko && bit_of(P.den_bits, v.w));
-            }
+            const uint32_t kr = h[u] & 0xFFu, ko = h[u] >> 8;
+            hit |= (kr > 0u && bit_of(src_rand, w1[u])) | (kr > 1u && bit_of(src_rand, w2[u])) |
+                   (kr > 2u && bit_of(src_rand, w3[u]));
+            for (uint32_t e = 4u; e <= kr; ++e) hit |= bit_of(src_rand, __ldg(rec[u] + e * plane));
+            for (uint32_t e = 0; e < ko; ++e) hit |= bit_of(P.den_bits, __ldg(rec[u] + (kDenOccAt + e) * plane));
         }
     }
     return hit;

@@ -55,7 +55,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     const int age = __ldg(P.age + j);
     uint32_t *rec = nullptr;
     if (DEN && (S.flags[i] & DEABM_FL_APP))
-        rec = P.den_ring + ((size_t)(day % P.den_window) * P.n_app + __ldg(P.app_rank + j)) * P.den_slots;
+        rec = P.den_ring + (size_t)(day % P.den_window) * P.den_slots * P.n_app + __ldg(P.app_rank + j);
     const float lam = lambda_of<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
     AgentState a;
     a.st = S.stage[i];
