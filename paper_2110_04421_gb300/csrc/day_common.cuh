@@ -19,8 +19,10 @@ namespace deabm {
 #ifndef DEABM_PLAIN_MINB
 #define DEABM_PLAIN_MINB 12
 #endif
-constexpr uint32_t kRound = DEABM_ROUND;
-
+#ifndef DEABM_ROUND0
+#define DEABM_ROUND0 6  // round of the first stored network (households of up to 6: one round; swept 4, 6, 10)
+#endif
+template <uint32_t kRound = DEABM_ROUND>
 __device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const float *__restrict__ inf, uint32_t e,
                                          uint32_t end, uint32_t stride, uint32_t b)
 {
@@ -248,7 +250,8 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
 #pragma unroll
     for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
         if (net < P.n_nets) {
-            const float h = csr_sum(P.col[net], I.cur, beg[net], end[net], stride, b);
+            const float h = net == 0 ? csr_sum<DEABM_ROUND0>(P.col[net], I.cur, beg[net], end[net], stride, b)
+                                     : csr_sum<DEABM_ROUND>(P.col[net], I.cur, beg[net], end[net], stride, b);
             const float term = __fmul_rn(rp.B_net[net], h);
             s = net == 0 ? term : __fadd_rn(s, term);
         }

@@ -38,35 +38,51 @@ __device__ __forceinline__ bool den_static_hit(const KParams &P, uint32_t j)
     return hit;
 }
 
-// the random and occupation in-contacts of app holder a on the days [d0, d1),
-// from the records the day kernel wrote while drawing them.  Records are word
-// planes over the app holders, so a warp's loads of one word are coalesced.
-// Four days at a time: their headers and first three random contacts (all of
-// most days' random contacts) are loaded together, the rest on demand.
-__device__ __forceinline__ bool den_ring_hit(const KParams &P, uint32_t a, uint32_t d0, uint32_t d1)
+// The records of four days [c0, c0 + 4) of app holder a (days >= d1 empty):
+// headers and first three random contacts, which cover most days' random
+// contacts.  Records are word planes over the app holders, so a warp's loads of
+// one word are coalesced.
+struct RingChunk {
+    uint32_t h[4], w1[4], w2[4], w3[4];
+};
+
+__device__ __forceinline__ const uint32_t *den_rec(const KParams &P, uint32_t a, uint32_t d)
+{
+    return P.den_ring + (size_t)(d % P.den_window) * P.den_slots * P.n_app + a;
+}
+
+__device__ __forceinline__ RingChunk den_ring_load(const KParams &P, uint32_t a, uint32_t c0, uint32_t d1)
+{
+    const size_t plane = P.n_app;
+    RingChunk c;
+#pragma unroll
+    for (uint32_t u = 0; u < 4u; ++u) {
+        const uint32_t *rec = den_rec(P, a, c0 + u);
+        const bool ok = c0 + u < d1;
+        c.h[u] = ok ? __ldg(rec) : 0u;
+        c.w1[u] = ok ? __ldg(rec + plane) : 0u;
+        c.w2[u] = ok ? __ldg(rec + 2 * plane) : 0u;
+        c.w3[u] = ok ? __ldg(rec + 3 * plane) : 0u;
+    }
+    return c;
+}
+
+// any positive app holder among the contacts of a loaded chunk (the rest of a
+// day's contacts loaded on demand)?
+__device__ __forceinline__ bool den_ring_eval(const KParams &P, uint32_t a, uint32_t c0, const RingChunk &c)
 {
     const uint32_t *src_rand = P.den_bits_orig ? P.den_bits_orig : P.den_bits;
     const size_t plane = P.n_app;
     bool hit = false;
-    for (uint32_t c0 = d0; c0 < d1 && !hit; c0 += 4u) {
-        uint32_t h[4], w1[4], w2[4], w3[4];
-        const uint32_t *rec[4];
 #pragma unroll
-        for (uint32_t u = 0; u < 4u; ++u) {
-            rec[u] = P.den_ring + (size_t)((c0 + u) % P.den_window) * P.den_slots * plane + a;
-            const bool ok = c0 + u < d1;
-            h[u] = ok ? __ldg(rec[u]) : 0u;
-            w1[u] = ok ? __ldg(rec[u] + plane) : 0u;
-            w2[u] = ok ? __ldg(rec[u] + 2 * plane) : 0u;
-            w3[u] = ok ? __ldg(rec[u] + 3 * plane) : 0u;
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 4u; ++u) {
-            const uint32_t kr = h[u] & 0xFFu, ko = h[u] >> 8;
-            hit |= (kr > 0u && bit_of(src_rand, w1[u])) | (kr > 1u && bit_of(src_rand, w2[u])) |
-                   (kr > 2u && bit_of(src_rand, w3[u]));
-            for (uint32_t e = 4u; e <= kr; ++e) hit |= bit_of(src_rand, __ldg(rec[u] + e * plane));
-            for (uint32_t e = 0; e < ko; ++e) hit |= bit_of(P.den_bits, __ldg(rec[u] + (kDenOccAt + e) * plane));
+    for (uint32_t u = 0; u < 4u; ++u) {
+        const uint32_t kr = c.h[u] & 0xFFu, ko = c.h[u] >> 8;
+        hit |= (kr > 0u && bit_of(src_rand, c.w1[u])) | (kr > 1u && bit_of(src_rand, c.w2[u])) |
+               (kr > 2u && bit_of(src_rand, c.w3[u]));
+        if (kr > 3u || ko) {
+            const uint32_t *rec = den_rec(P, a, c0 + u);
+            for (uint32_t e = 4u; e <= kr; ++e) hit |= bit_of(src_rand, __ldg(rec + e * plane));
+            for (uint32_t e = 0; e < ko; ++e) hit |= bit_of(P.den_bits, __ldg(rec + (kDenOccAt + e) * plane));
         }
     }
     return hit;
@@ -81,12 +97,17 @@ __global__ void __launch_bounds__(256) den_kernel(const KParams P, uint32_t day,
     bool notified = false;
     // nothing to do on a day without a positive app holder
     if (a < P.n_app && __ldg(P.den_pos + day) > 0) {
+        // the first four days' records are requested before the agent's own state
+        // and rows, so their latencies overlap
+        const uint32_t d0 = day + 1u > P.den_window ? day + 1u - P.den_window : 0u;
+        const RingChunk first = den_ring_load(P, a, d0, day + 1u);
         const uint32_t j = __ldg(P.app_rows + a);
         const uint32_t fl = S.flags[j];
         const int st = S.stage[j];
         if ((S.qt[j] & 0x0Fu) == 0u && st != DEABM_HOSP && st != DEABM_ICU && st != DEABM_DEAD) {
-            const uint32_t d0 = day + 1u > P.den_window ? day + 1u - P.den_window : 0u;
-            const bool hit = den_static_hit(P, j) || den_ring_hit(P, a, d0, day + 1u);
+            bool hit = den_static_hit(P, j) || den_ring_eval(P, a, d0, first);
+            for (uint32_t c0 = d0 + 4u; c0 <= day && !hit; c0 += 4u)
+                hit = den_ring_eval(P, a, c0, den_ring_load(P, a, c0, day + 1u));
             if (hit) {
                 notified = true;
                 const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;

@@ -335,7 +335,11 @@ __device__ __forceinline__ void add4(float4 &h, const float4 v)
 }
 
 template <bool KEEP>
-__global__ void __launch_bounds__(256) step_batch4_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
+#ifndef DEABM_B4_MINB
+#define DEABM_B4_MINB 4  // resident blocks per SM asked of the four-replicate kernel: 64 registers
+                         // (swept: 1 -> 105 registers, 38 % slower; 5, 6 -> spills, 8-12 % slower)
+#endif
+__global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                           Counters C, float *lam_out, float *p_out)
 {
     __shared__ int s_cnt[DEABM_N_STAGE + 1][32 * kRepPerThread];
