@@ -50,6 +50,15 @@ def step_bytes_plain(n: int, static_edges: int, n_nets: int, vax: bool) -> int:
     return 4 * (n + 1) * n_nets + 4 * static_edges + n * (7 + 7 + 1 + (2 if vax else 0) + 4 + 4)
 
 
+def step_bytes_plain_needed(n: int, static_edges: int, n_nets: int, vax: bool, n_sus: float) -> float:
+    """Bytes one plain day needs when only susceptible agents gather (Eq. 2 applies
+    to them alone): every agent's state, age, dose day and infectiousness as
+    above, but row pointers and columns only for the n_sus susceptible rows
+    (their edges counted at the mean in-degree)."""
+    return (n * (7 + 7 + 1 + (2 if vax else 0) + 4 + 4)
+            + 4.0 * n_sus * n_nets + 4.0 * static_edges * n_sus / n)
+
+
 def step_bytes_batch(n: int, B: int, static_edges: int, n_nets: int, vax: bool) -> int:
     """Same for the [N][B] panel: per (agent, replicate) 7 + 7 + 4 + 4 B; per agent
     age and first-dose day; the CSR once for all replicates."""
@@ -194,8 +203,10 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     per_day_ms = [ev[d].elapsed_time(ev[d + 1]) for d in range(K)]
     total_ms = ev[0].elapsed_time(ev[K])
-    _, _, msgs = sim.counters(Wm + K)
+    _, hist_days, msgs = sim.counters(Wm + K)
     messages = int(msgs[Wm:].astype(np.int64).sum())
+    # susceptible agents at the start of each timed day (end of the day before)
+    sus_days = [float(hist_days[d - 1, 0, 0]) for d in range(Wm, Wm + K)]
     sim.close()
 
     # ---- end to end through the C-ABI with host buffers (create + run + readback)
@@ -230,6 +241,8 @@ def run_ours(args, rank, world, local):
         value = messages / (total_ms / 1e3)
         avg_ms = statistics.mean(per_day_ms)
         alg = step_bytes_plain(n, static_edges, len(pop["row_ptr"]), bool(params["vax_on"]))
+        alg_needed = statistics.mean(
+            step_bytes_plain_needed(n, static_edges, len(pop["row_ptr"]), bool(params["vax_on"]), ns) for ns in sus_days)
         peak, peak_kind = measured_peak_hbm()
         achieved = alg / (avg_ms / 1e3) / 1e9
         traffic = traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_n2e6.md", n)
@@ -250,6 +263,11 @@ def run_ours(args, rank, world, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "step_plain_kernel", "alg_bytes_per_launch": alg,
+                         "alg_bytes_needed_mean": alg_needed,
+                         "alg_note": "achieved counts every array once (163 MB a day); only susceptible agents "
+                                     "gather (Eq. 2 applies to them alone), so a day needs alg_bytes_needed_mean "
+                                     f"on average (mean susceptible share {statistics.mean(sus_days) / n:.3f} "
+                                     "over the timed days)",
                          "launch_ms_mean": avg_ms, "launch_ms_min": min(per_day_ms)},
             "e2e": None if args.no_e2e else {
                 "value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / K,

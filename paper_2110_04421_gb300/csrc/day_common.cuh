@@ -215,6 +215,23 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 // jo = the caller's id of the same agent.  OCC = false compiles the daily
 // occupation networks out (for contexts that have none).  The row bounds of every network are
 // loaded first and the random contacts are generated while they are in flight.
+// The number of the day's in-contacts of an agent whose lambda is not needed
+// (not susceptible): the random network's count from its first Philox word and
+// the occupation's daily count.  No gathers.
+__device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t jo, uint32_t day)
+{
+    uint32_t k = 0;
+    if (P.rand_on) {
+        const uint4 w = draw(seed_key(P.net_seed), jo, day, kStreamRnet, 0u);
+        while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
+    }
+    if (P.n_occ) {
+        const uint32_t g = __ldg(P.occ_gid + j);
+        if (__ldg(P.occ_start + g + 1u) - __ldg(P.occ_start + g) > 1u) k += __ldg(P.occ_k + g);
+    }
+    return k;
+}
+
 // REC: the agent's exposure-notification record of the day goes to rec (when
 // not null).
 template <bool OCC = true, bool REC = false, bool ROWMAP = false>

@@ -39,6 +39,10 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
     return u < pe;
 }
 
+#ifndef DEABM_SUSCEPTIBLE_ONLY
+#define DEABM_SUSCEPTIBLE_ONLY 1  // 0: lambda (all gathers) for every agent, as the method is written
+#endif
+
 // Full day for one (agent j, replicate b) at flat index i = j*stride + b.  Every
 // random draw is keyed by the caller's agent id jo, so relabelling the agents
 // inside the library changes no result.
@@ -56,9 +60,16 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     uint32_t *rec = nullptr;
     if (DEN && (S.flags[i] & DEABM_FL_APP))
         rec = P.den_ring + (size_t)(day % P.den_window) * P.den_slots * P.n_app + __ldg(P.app_rank + j);
-    const float lam = lambda_of<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
     AgentState a;
     a.st = S.stage[i];
+    // Eq. 2 applies to susceptible agents only: the others skip the gathers (their
+    // in-contacts are still counted), unless lambda is kept for every agent or an
+    // app holder's contacts are being recorded
+    float lam = 0.0f;
+    if (!DEABM_SUSCEPTIBLE_ONLY || a.st == DEABM_S || lam_out != nullptr || (DEN && rec))
+        lam = lambda_of<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
+    else
+        *k_out = contact_count(P, j, jo, day);
     a.tm = S.timer[i];
     a.ti = S.tinf[i];
     a.fl = S.flags[i];
