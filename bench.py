@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_BYTES = 129 * 2**20
+PLAIN_WORKLOAD = ("plain N=2e6 T=180 (households 1-6, occupation groups of 20 x 10 links, Poisson(2) random "
+                  "network, testing + 14-day quarantine, vaccination 1%/day from day 30)")
 
 
 def dist_env():
@@ -252,9 +254,7 @@ def run_ours(args, rank, world, local):
             "value": value, "unit": "interactions/s", "n_gpus": world, "steps": K, "warmup": Wm,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded generators shaped like the paper's population)",
-            "config": {"workload": "plain N=2e6 T=180 (households 1-6, occupation groups of 20 x 10 links, "
-                                   "Poisson(2) random network, testing + 14-day quarantine, vaccination 1%/day "
-                                   "from day 30)",
+            "config": {"workload": PLAIN_WORKLOAD,
                        "n_agents": n, "messages_per_day": messages / K / world,
                        "static_edges": static_edges, "days_timed": f"{Wm}..{Wm + K - 1}",
                        "l2": f"inputs larger than L2: {alg / 1e6:.0f} MB algorithmic per day vs "
@@ -672,7 +672,8 @@ def run_reference(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded generators shaped like the paper's population)",
-            "config": {"workload": "plain N=2e6 T=180", "n_agents": w["n"]},
+            "config": {"workload": PLAIN_WORKLOAD, "n_agents": w["n"],
+                       "days_timed": f"{args.warmup}..{args.warmup + args.steps - 1}"},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} whole oracle days after {args.warmup} warm-up days",
                              "cpu": cpu_model()},
