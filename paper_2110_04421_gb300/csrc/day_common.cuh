@@ -232,68 +232,6 @@ __device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, 
     return k;
 }
 
-// The day's exposure-notification record of an app holder whose lambda is not
-// needed: the same contacts as random_head/random_tail and occ_sum draw, written
-// to rec without gathering their infectiousness; returns the contact count.
-__device__ __forceinline__ uint32_t contact_record(const KParams &P, uint32_t j, uint32_t jo, uint32_t day,
-                                                   uint32_t *rec)
-{
-    const size_t plane = P.n_app;
-    uint32_t k_rand = 0, k_occ = 0;
-    if (P.rand_on) {
-        const uint2 nk = seed_key(P.net_seed);
-        uint4 w = draw(nk, jo, day, kStreamRnet, 0u);
-        while (k_rand < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k_rand])) ++k_rand;
-        const uint64_t nm1 = (uint64_t)(P.n - 1u);
-        for (uint32_t e = 0; e < k_rand; ++e) {
-            const uint32_t idx = e + 1u;
-            if ((idx & 3u) == 0u) w = draw(nk, jo, day, kStreamRnet, idx >> 2);
-            const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
-            uint32_t c = (uint32_t)(((uint64_t)x * nm1) >> 32);
-            c += (c >= jo) ? 1u : 0u;
-            rec[(size_t)(1u + e) * plane] = c;
-        }
-    }
-    if (P.n_occ) {
-        const uint32_t g = __ldg(P.occ_gid + j);
-        const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
-        k_occ = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
-        const uint32_t own = j - beg;
-        const uint2 nk = seed_key(P.net_seed);
-        if (P.occ_lattice) {
-            for (uint32_t e = 0; e < k_occ; e += 2u) {
-                const uint4 w = draw(nk, jo, day, kStreamWs, e >> 1);
-                const uint32_t m = (e >> 1) + 1u;
-                const uint32_t hop = m < size ? m : m % size;
-                const uint32_t coin[2] = {w.x, w.z}, word[2] = {w.y, w.w};
-#pragma unroll
-                for (uint32_t u = 0; u < 2u; ++u) {
-                    if (e + u >= k_occ) break;
-                    const uint32_t off = u == 0u ? hop : (hop == 0u ? 0u : size - hop);
-                    uint32_t r;
-                    if (off == 0u || (uint64_t)coin[u] < P.thr_rewire) {
-                        r = occ_place(word[u], size - 1u, own);
-                    } else {
-                        r = own + off;
-                        r = r >= size ? r - size : r;
-                    }
-                    rec[(size_t)(kDenOccAt + e + u) * plane] = beg + r;
-                }
-            }
-        } else {
-            for (uint32_t e = 0; e < k_occ; e += 4u) {
-                const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
-                const uint32_t x[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (uint32_t u = 0; u < 4u; ++u)
-                    if (e + u < k_occ) rec[(size_t)(kDenOccAt + e + u) * plane] = beg + occ_place(x[u], size - 1u, own);
-            }
-        }
-    }
-    rec[0] = k_rand | (k_occ << 8);
-    return k_rand + k_occ;
-}
-
 // REC: the agent's exposure-notification record of the day goes to rec (when
 // not null).
 template <bool OCC = true, bool REC = false, bool ROWMAP = false>

@@ -63,13 +63,13 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     AgentState a;
     a.st = S.stage[i];
     // Eq. 2 applies to susceptible agents only: the others skip the gathers (their
-    // in-contacts are still counted, and an app holder's still recorded), unless
-    // lambda is kept for every agent
+    // in-contacts are still counted), unless lambda is kept for every agent.  With
+    // exposure notification every agent takes the full path: the app holders
+    // record their contacts anyway, and one path for all measured faster than the
+    // divergent pair there.
     float lam = 0.0f;
-    if (!DEABM_SUSCEPTIBLE_ONLY || a.st == DEABM_S || lam_out != nullptr)
+    if (!DEABM_SUSCEPTIBLE_ONLY || DEN || a.st == DEABM_S || lam_out != nullptr)
         lam = lambda_of<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
-    else if (DEN && rec)
-        *k_out = contact_record(P, j, jo, day, rec);
     else
         *k_out = contact_count(P, j, jo, day);
     a.tm = S.timer[i];
