@@ -148,6 +148,60 @@ static uint32_t first_bad_row(uint32_t n, const F &bad)
     return *std::min_element(found.begin(), found.end());
 }
 
+// fn(begin, end, t) over [0, n) split into contiguous chunks on host threads
+template <class F>
+static void parallel_chunks(uint32_t n, uint32_t T, const F &fn)
+{
+    if (T <= 1) {
+        fn(0u, n, 0u);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (uint32_t t = 0; t < T; ++t)
+        th.emplace_back(fn, (uint32_t)((uint64_t)n * t / T), (uint32_t)((uint64_t)n * (t + 1) / T), t);
+    for (auto &x : th) x.join();
+}
+
+static uint32_t host_threads(uint32_t n)
+{
+    return n < (1u << 16) ? 1u : std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+}
+
+// Stable counting sort of the agents by label on host threads: order[] lists the
+// agents by ascending label, ascending id among equal labels.  Labels are first
+// made dense (groups numbered in label order) so that each thread's counts take
+// one word per group.
+static void sort_by_label(const std::vector<uint32_t> &lab, std::vector<uint32_t> &order)
+{
+    const uint32_t n = (uint32_t)lab.size(), T = host_threads(n);
+    std::vector<uint8_t> used(n, 0);
+    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t) {
+        for (uint32_t v = b; v < e; ++v) used[lab[v]] = 1;  // every writer stores 1
+    });
+    std::vector<uint32_t> gidx(n);
+    uint32_t G = 0;
+    for (uint32_t l = 0; l < n; ++l) {
+        gidx[l] = G;
+        G += used[l];
+    }
+    std::vector<std::vector<uint32_t>> cnt(T, std::vector<uint32_t>(G, 0));
+    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t t) {
+        for (uint32_t v = b; v < e; ++v) cnt[t][gidx[lab[v]]]++;
+    });
+    uint32_t run = 0;  // offsets: group by group, thread by thread (so ids stay ascending)
+    for (uint32_t g = 0; g < G; ++g)
+        for (uint32_t t = 0; t < T; ++t) {
+            const uint32_t c = cnt[t][g];
+            cnt[t][g] = run;
+            run += c;
+        }
+    order.resize(n);
+    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t t) {
+        for (uint32_t v = b; v < e; ++v) order[cnt[t][gidx[lab[v]]]++] = v;
+    });
+}
+
 static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a, const deabm_params *p,
                     uint32_t n_rep, const float *rep_params)
 {
@@ -194,15 +248,16 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
                 return fail(ctx, DEABM_EINVAL, "occ_group[%u] = %u >= n_occ", j, g->occ_group[j]);
     }
     if (!a->age_bin) return fail(ctx, DEABM_EINVAL, "age_bin is required");
-    for (uint32_t j = 0; j < n; ++j)
-        if (a->age_bin[j] >= DEABM_N_AGE) return fail(ctx, DEABM_EINVAL, "age_bin[%u] = %u > 8", j, a->age_bin[j]);
-    if (a->stage)
-        for (uint32_t j = 0; j < n; ++j)
-            if (a->stage[j] < 0 || a->stage[j] >= DEABM_N_STAGE)
-                return fail(ctx, DEABM_EINVAL, "stage[%u] = %d is not a stage code", j, a->stage[j]);
-    if (a->qt)
-        for (uint32_t j = 0; j < n; ++j)
-            if (a->qt[j] & 0x80u) return fail(ctx, DEABM_EINVAL, "qt[%u] has bit 7 set", j);
+    uint32_t jb = first_bad_row(n, [&](uint32_t q) { return a->age_bin[q] >= DEABM_N_AGE; });
+    if (jb < n) return fail(ctx, DEABM_EINVAL, "age_bin[%u] = %u > 8", jb, a->age_bin[jb]);
+    if (a->stage) {
+        jb = first_bad_row(n, [&](uint32_t q) { return a->stage[q] < 0 || a->stage[q] >= DEABM_N_STAGE; });
+        if (jb < n) return fail(ctx, DEABM_EINVAL, "stage[%u] = %d is not a stage code", jb, a->stage[jb]);
+    }
+    if (a->qt) {
+        jb = first_bad_row(n, [&](uint32_t q) { return (a->qt[q] & 0x80u) != 0; });
+        if (jb < n) return fail(ctx, DEABM_EINVAL, "qt[%u] has bit 7 set", jb);
+    }
     if (a->n_seed && !a->seed_ids) return fail(ctx, DEABM_EINVAL, "seed_ids is NULL");
     for (uint32_t q = 0; q < a->n_seed; ++q)
         if (a->seed_ids[q] >= n) return fail(ctx, DEABM_EINVAL, "seed_ids[%u] >= n_agents", q);
@@ -396,17 +451,16 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
                 if ((r = scratch_alloc(ctx, sc, &tmp, n))) return r;
                 CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, s));
-                std::vector<uint32_t> lab(n), cnt((size_t)n + 1, 0);
+                std::vector<uint32_t> lab(n);
                 CU(ctx, cudaMemcpyAsync(lab.data(), label, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
                 CU(ctx, cudaStreamSynchronize(s));
-                for (uint32_t v = 0; v < n; ++v) cnt[lab[v] + 1]++;
-                for (uint32_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
-                ctx->new2orig.resize(n);
-                for (uint32_t v = 0; v < n; ++v) ctx->new2orig[cnt[lab[v]]++] = v;
+                sort_by_label(lab, ctx->new2orig);
             }
             if (ctx->relabel) {
                 orig2new.resize(n);
-                for (uint32_t q = 0; q < n; ++q) orig2new[ctx->new2orig[q]] = q;
+                parallel_chunks(n, host_threads(n), [&](uint32_t b, uint32_t e, uint32_t) {
+                    for (uint32_t q = b; q < e; ++q) orig2new[ctx->new2orig[q]] = q;
+                });
                 uint32_t *d_o2n, *d_scan;
                 if ((r = dalloc(ctx, &ctx->orig_id, n))) return r;
                 if ((r = scratch_alloc(ctx, sc, &d_o2n, n))) return r;
@@ -482,29 +536,29 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
             CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
 
-            // agents: [N] -> [N][n_rep] in internal order, each agent's initial state repeated per replicate
-            std::vector<uint8_t> age_in(n);
-            for (uint32_t q = 0; q < n; ++q) age_in[q] = a->age_bin[orig_of(q)];
-            CU(ctx, cudaMemcpyAsync(ctx->age, age_in.data(), n, cudaMemcpyHostToDevice, s));
-            std::vector<int8_t> st(nb, 0);
-            std::vector<int16_t> tm(nb, 0), ti(nb, 0);
-            std::vector<uint8_t> fl(nb, 0), qt(nb, 0);
-            for (uint32_t q = 0; q < n; ++q) {
-                const uint32_t o = orig_of(q);
-                for (uint32_t b = 0; b < n_rep; ++b) {
-                    const size_t i = (size_t)q * n_rep + b;
-                    if (a->stage) st[i] = a->stage[o];
-                    if (a->timer) tm[i] = a->timer[o];
-                    if (a->tinf) ti[i] = a->tinf[o];
-                    if (a->flags) fl[i] = a->flags[o];
-                    if (a->qt) qt[i] = a->qt[o];
+            // agents: [N] -> [N][n_rep] in internal order, each agent's initial state
+            // repeated per replicate.  Caller arrays go up as given and are put in
+            // place on the device; absent ones are zero.
+            uint16_t *d_in = nullptr;  // caller-order staging, n 2-byte words
+            if ((r = scratch_alloc(ctx, sc, &d_in, n))) return r;
+            const uint32_t *perm = ctx->relabel ? ctx->orig_id : nullptr;
+            auto put = [&](void *dst, const void *src, uint32_t elem, uint32_t reps) -> int {
+                if (!src) {
+                    CU(ctx, cudaMemsetAsync(dst, 0, (size_t)n * reps * elem, s));
+                } else if (!perm && reps == 1) {
+                    CU(ctx, cudaMemcpyAsync(dst, src, (size_t)n * elem, cudaMemcpyHostToDevice, s));
+                } else {
+                    CU(ctx, cudaMemcpyAsync(d_in, src, (size_t)n * elem, cudaMemcpyHostToDevice, s));
+                    CU(ctx, launch_from_caller(dst, d_in, perm, n, reps, elem, s));
                 }
-            }
-            CU(ctx, cudaMemcpyAsync(ctx->S.stage, st.data(), nb, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S.timer, tm.data(), nb * 2, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S.tinf, ti.data(), nb * 2, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S.flags, fl.data(), nb, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S.qt, qt.data(), nb, cudaMemcpyHostToDevice, s));
+                return DEABM_OK;
+            };
+            if ((r = put(ctx->age, a->age_bin, 1, 1))) return r;
+            if ((r = put(ctx->S.stage, a->stage, 1, n_rep))) return r;
+            if ((r = put(ctx->S.timer, a->timer, 2, n_rep))) return r;
+            if ((r = put(ctx->S.tinf, a->tinf, 2, n_rep))) return r;
+            if ((r = put(ctx->S.flags, a->flags, 1, n_rep))) return r;
+            if ((r = put(ctx->S.qt, a->qt, 1, n_rep))) return r;
             // keep the initial state for deabm_reset
             if ((r = dalloc(ctx, &ctx->S0.stage, nb))) return r;
             if ((r = dalloc(ctx, &ctx->S0.timer, nb))) return r;
