@@ -282,6 +282,28 @@ int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *poisson_thr, in
  * many ensembles without re-uploading the graph.  Asynchronous. */
 int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_seeds);
 
+/* Checkpoint and resume.  Draws are keyed by (seed, agent, day, stream), so the
+ * state at the start of a day plus the day index determine every later day
+ * exactly.  deabm_save writes the state at the start of the next day to run
+ * (stage, timer, tinf, flags, qt: host arrays [n_agents][n_rep] in caller order,
+ * as deabm_get_state) and, under a priority strategy, the dose days (host
+ * [n_agents], 0x7FFF = none; NULL otherwise); *day receives the day index.
+ * deabm_restore puts such a state back into a context created with the same
+ * graph and parameters (this one or another) and sets its day: the next
+ * deabm_step runs that day.  The day's emitted infectiousness is rebuilt from
+ * the state, exposure-notification records of the previous den_window - 1 days
+ * are redrawn from their Philox words, and the per-day counters of days >= day
+ * are cleared (earlier ones are kept as they are).  Plain and batched contexts;
+ * DEABM_ESTATE for ragged batches.  Any array may be NULL on save; on restore
+ * stage..qt are required and checked like deabm_create's.  Returns DEABM_OK,
+ * DEABM_EINVAL (day > max_steps, bad codes), DEABM_ESTATE, DEABM_ECUDA.
+ * Synchronises. */
+int deabm_save(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt,
+               int16_t *dose1_day, int16_t *dose2_day, uint32_t *day);
+int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t *timer, const int16_t *tinf,
+                  const uint8_t *flags, const uint8_t *qt, const int16_t *dose1_day, const int16_t *dose2_day,
+                  uint32_t day);
+
 /* ---- Infection rates of one day without allocating memory ------------------------------
  * The paper has no counterpart: this is a library convenience.  It exists for
  * callers that may not allocate device memory where they call us (code living

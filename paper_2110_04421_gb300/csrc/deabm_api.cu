@@ -549,7 +549,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                     CU(ctx, cudaMemcpyAsync(dst, src, (size_t)n * elem, cudaMemcpyHostToDevice, s));
                 } else {
                     CU(ctx, cudaMemcpyAsync(d_in, src, (size_t)n * elem, cudaMemcpyHostToDevice, s));
-                    CU(ctx, launch_from_caller(dst, d_in, perm, n, reps, elem, s));
+                    CU(ctx, launch_from_caller(dst, d_in, perm, n, reps, elem, false, s));
                 }
                 return DEABM_OK;
             };
@@ -1279,6 +1279,81 @@ extern "C" int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *n
     }
     CU(ctx, cudaMemcpyAsync(notified, ctx->C.den, sizeof(int32_t) * day_count, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return DEABM_OK;
+}
+
+extern "C" int deabm_save(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt,
+                          int16_t *dose1_day, int16_t *dose2_day, uint32_t *day)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (ctx->ragged) return fail(ctx, DEABM_ESTATE, "checkpoints are not available for ragged batches");
+    int r = deabm_get_state(ctx, stage, timer, tinf, flags, qt, nullptr, nullptr);
+    if (r) return r;
+    if ((dose1_day || dose2_day) && ctx->S.vd1 && (r = deabm_get_dose_days(ctx, dose1_day, dose2_day))) return r;
+    if (day) *day = ctx->day;
+    return DEABM_OK;
+}
+
+extern "C" int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t *timer, const int16_t *tinf,
+                             const uint8_t *flags, const uint8_t *qt, const int16_t *dose1_day,
+                             const int16_t *dose2_day, uint32_t day)
+{
+    if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
+    if (ctx->ragged) return fail(ctx, DEABM_ESTATE, "checkpoints are not available for ragged batches");
+    if (!stage || !timer || !tinf || !flags || !qt) return fail(ctx, DEABM_EINVAL, "stage, timer, tinf, flags and qt are required");
+    if (day > ctx->max_steps) return fail(ctx, DEABM_EINVAL, "day %u > max_steps %u", day, ctx->max_steps);
+    if (ctx->S.vd1 && (!dose1_day || !dose2_day))
+        return fail(ctx, DEABM_EINVAL, "dose days are required under a vaccination priority strategy");
+    const uint32_t n = ctx->n, B = ctx->n_rep;
+    const size_t nb = (size_t)n * B;
+    uint32_t jb = first_bad_row(n, [&](uint32_t q) {
+        for (uint32_t b = 0; b < B; ++b) {
+            const size_t i = (size_t)q * B + b;
+            if (stage[i] < 0 || stage[i] >= DEABM_N_STAGE || (qt[i] & 0x80u)) return true;
+        }
+        return false;
+    });
+    if (jb < n) return fail(ctx, DEABM_EINVAL, "agent %u: not a stage code or qt bit 7 set", jb);
+    cudaStream_t s = ctx->stream;
+    DevScratch sc;
+    uint16_t *d_in = nullptr;
+    int r;
+    if (ctx->relabel && (r = scratch_alloc(ctx, sc, &d_in, nb))) return r;
+    const uint32_t *perm = ctx->relabel ? ctx->orig_id : nullptr;
+    auto put = [&](void *dst, const void *src, uint32_t elem, uint32_t reps) -> int {
+        if (!perm) {
+            CU(ctx, cudaMemcpyAsync(dst, src, (size_t)n * reps * elem, cudaMemcpyHostToDevice, s));
+        } else {
+            CU(ctx, cudaMemcpyAsync(d_in, src, (size_t)n * reps * elem, cudaMemcpyHostToDevice, s));
+            CU(ctx, launch_from_caller(dst, d_in, perm, n, reps, elem, true, s));
+        }
+        return DEABM_OK;
+    };
+    if ((r = put(ctx->S.stage, stage, 1, B))) return r;
+    if ((r = put(ctx->S.timer, timer, 2, B))) return r;
+    if ((r = put(ctx->S.tinf, tinf, 2, B))) return r;
+    if ((r = put(ctx->S.flags, flags, 1, B))) return r;
+    if ((r = put(ctx->S.qt, qt, 1, B))) return r;
+    if (ctx->S.vd1) {
+        if ((r = put(ctx->S.vd1, dose1_day, 2, 1))) return r;
+        if ((r = put(ctx->S.vd2, dose2_day, 2, 1))) return r;
+    }
+    ctx->day = day;
+    ctx->cur = 0;
+    CU(ctx, launch_emit(ctx->kp, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
+    // counters of the days to come start from zero again
+    const size_t rest = ctx->max_steps - day;
+    CU(ctx, cudaMemsetAsync(ctx->C.new_inf + (size_t)day * B, 0, sizeof(int32_t) * rest * B, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.hist + (size_t)day * B * DEABM_N_STAGE, 0,
+                            sizeof(int32_t) * rest * B * DEABM_N_STAGE, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.msgs + day, 0, sizeof(unsigned long long) * rest, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.den + day, 0, sizeof(int32_t) * rest, s));
+    if (ctx->kp.den_on) {
+        CU(ctx, cudaMemsetAsync(ctx->den_pos + day, 0, sizeof(int32_t) * rest, s));
+        const uint32_t W = ctx->kp.den_window;
+        CU(ctx, launch_den_records(ctx->kp, day + 1u > W ? day + 1u - W : 0u, day, s));
+    }
+    CU(ctx, cudaStreamSynchronize(s));  // host arrays and device scratch end here
     return DEABM_OK;
 }
 

@@ -133,6 +133,70 @@ __global__ void den_apps_kernel(const KParams P, StateRef S)
     S.flags[j] = (uint8_t)((uint64_t)w < P.thr_adopt ? (fl | DEABM_FL_APP) : (fl & ~DEABM_FL_APP));
 }
 
+// One app holder's contact record of day d redrawn from Philox: the random and
+// occupation contacts the day kernel drew that day (used when a context resumes
+// from a saved state, whose previous days' records it never wrote).
+__global__ void den_record_kernel(const KParams P, uint32_t d0, uint32_t d1)
+{
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= P.n_app) return;
+    const uint32_t j = __ldg(P.app_rows + a);
+    const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
+    const size_t plane = P.n_app;
+    const uint2 nk = seed_key(P.net_seed);
+    for (uint32_t d = d0; d < d1; ++d) {
+        uint32_t *rec = P.den_ring + (size_t)(d % P.den_window) * P.den_slots * plane + a;
+        uint32_t k_rand = 0, k_occ = 0;
+        if (P.rand_on) {
+            uint4 w = draw(nk, jo, d, kStreamRnet, 0u);
+            while (k_rand < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k_rand])) ++k_rand;
+            const uint64_t nm1 = (uint64_t)(P.n - 1u);
+            for (uint32_t e = 0; e < k_rand; ++e) {
+                const uint32_t idx = e + 1u;
+                if ((idx & 3u) == 0u) w = draw(nk, jo, d, kStreamRnet, idx >> 2);
+                const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+                uint32_t c = (uint32_t)(((uint64_t)x * nm1) >> 32);
+                c += (c >= jo) ? 1u : 0u;
+                rec[(size_t)(1u + e) * plane] = c;
+            }
+        }
+        if (P.n_occ) {
+            const uint32_t g = __ldg(P.occ_gid + j);
+            const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
+            k_occ = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
+            const uint32_t own = j - beg;
+            for (uint32_t e = 0; e < k_occ; ++e) {
+                uint32_t r;
+                if (P.occ_lattice) {  // as occ_ws_sum
+                    const uint4 w = draw(nk, jo, d, kStreamWs, e >> 1);
+                    const uint32_t m = (e >> 1) + 1u, hop = m < size ? m : m % size;
+                    const uint32_t coin = (e & 1u) ? w.z : w.x, word = (e & 1u) ? w.w : w.y;
+                    const uint32_t off = (e & 1u) == 0u ? hop : (hop == 0u ? 0u : size - hop);
+                    if (off == 0u || (uint64_t)coin < P.thr_rewire) {
+                        r = occ_place(word, size - 1u, own);
+                    } else {
+                        r = own + off;
+                        r = r >= size ? r - size : r;
+                    }
+                } else {  // as occ_sum
+                    const uint4 w = draw(nk, jo, d, kStreamOcc, e >> 2);
+                    const uint32_t x = (e & 3u) == 0u ? w.x : (e & 3u) == 1u ? w.y : (e & 3u) == 2u ? w.z : w.w;
+                    r = occ_place(x, size - 1u, own);
+                }
+                rec[(size_t)(kDenOccAt + e) * plane] = beg + r;
+            }
+        }
+        rec[0] = k_rand | (k_occ << 8);
+    }
+}
+
+cudaError_t launch_den_records(const KParams &P, uint32_t d0, uint32_t d1, cudaStream_t stream)
+{
+    if (P.n_app == 0u || d0 >= d1) return cudaSuccess;
+    den_record_kernel<<<(P.n_app + 255u) / 256u, 256, 0, stream>>>(P, d0, d1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t stream)
 {
     den_apps_kernel<<<(P.n + 255u) / 256u, 256, 0, stream>>>(P, S);

@@ -49,9 +49,12 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
 size_t scan_scratch_words(size_t m);
 cudaError_t launch_to_caller(void *out, const void *in, const uint32_t *orig, uint32_t n, uint32_t n_rep,
                              uint32_t elem, cudaStream_t stream);
-// caller-order [n] array (elem = 1 or 2 bytes) to internal order [n][n_rep] (orig null: same order)
+// caller-order [n] (in_reps false) or [n][n_rep] array (elem = 1 or 2 bytes) to
+// internal order [n][n_rep] (orig null: same order)
 cudaError_t launch_from_caller(void *out, const void *in, const uint32_t *orig, uint32_t n, uint32_t n_rep,
-                               uint32_t elem, cudaStream_t stream);
+                               uint32_t elem, bool in_reps, cudaStream_t stream);
+// exposure notification: redraw the app holders' contact records of days [d0, d1)
+cudaError_t launch_den_records(const KParams &P, uint32_t d0, uint32_t d1, cudaStream_t stream);
 // out[i] = in[idx[i]] for i < n
 cudaError_t launch_gather_i16(int16_t *out, const int16_t *in, const uint32_t *idx, uint32_t n, cudaStream_t stream);
 

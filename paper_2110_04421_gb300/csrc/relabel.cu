@@ -144,27 +144,31 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
 }
 
 // ---------------------------------------------------------------- from caller order
-// out[q * n_rep + b] = in[orig[q]] (in[q] when orig is null): a caller-order
-// array of n agents put in internal order and repeated over the replicates
+// out[q * n_rep + b] = in[orig[q]] (in[q] when orig is null), or
+// in[orig[q] * n_rep + b] when the input has its replicates: a caller-order array
+// put in internal order (and repeated over the replicates when it has none)
 template <class T>
 __global__ void from_caller_kernel(T *__restrict__ out, const T *__restrict__ in, const uint32_t *__restrict__ orig,
-                                   uint32_t n, uint32_t n_rep)
+                                   uint32_t n, uint32_t n_rep, bool in_reps)
 {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (uint64_t)n * n_rep) return;
-    const uint32_t q = (uint32_t)(i / n_rep);
-    out[i] = in[orig ? orig[q] : q];
+    const uint32_t q = (uint32_t)(i / n_rep), b = (uint32_t)(i % n_rep);
+    const uint64_t o = orig ? orig[q] : q;
+    out[i] = in_reps ? in[o * n_rep + b] : in[o];
 }
 
 cudaError_t launch_from_caller(void *out, const void *in, const uint32_t *orig, uint32_t n, uint32_t n_rep,
-                               uint32_t elem, cudaStream_t stream)
+                               uint32_t elem, bool in_reps, cudaStream_t stream)
 {
     const uint64_t total = (uint64_t)n * n_rep;
     const unsigned blocks = (unsigned)((total + 255u) / 256u);
     if (elem == 1)
-        from_caller_kernel<uint8_t><<<blocks, 256, 0, stream>>>((uint8_t *)out, (const uint8_t *)in, orig, n, n_rep);
+        from_caller_kernel<uint8_t><<<blocks, 256, 0, stream>>>((uint8_t *)out, (const uint8_t *)in, orig, n, n_rep,
+                                                                 in_reps);
     else
-        from_caller_kernel<uint16_t><<<blocks, 256, 0, stream>>>((uint16_t *)out, (const uint16_t *)in, orig, n, n_rep);
+        from_caller_kernel<uint16_t><<<blocks, 256, 0, stream>>>((uint16_t *)out, (const uint16_t *)in, orig, n,
+                                                                  n_rep, in_reps);
     return cudaGetLastError();
 }
 

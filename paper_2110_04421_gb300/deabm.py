@@ -25,7 +25,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
-           "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified")
+           "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -91,6 +91,10 @@ def lib():
         L.deabm_get_counters.argtypes = [vp, u32, vp, vp, vp]
         L.deabm_get_notified.argtypes = [vp, u32, vp]
         L.deabm_get_notified.restype = C.c_int
+        L.deabm_save.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(u32)]
+        L.deabm_save.restype = C.c_int
+        L.deabm_restore.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u32]
+        L.deabm_restore.restype = C.c_int
         L.deabm_get_tables.argtypes = [vp, vp, vp, vp]
         L.deabm_info.argtypes = [vp, vp, vp, vp]
         L.deabm_sync.argtypes = [vp]
@@ -503,6 +507,31 @@ class Simulation:
         m = np.zeros(days, np.uint64)
         _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
         return ni, h, m
+
+    def save(self) -> dict:
+        """A checkpoint: the state at the start of the next day to run ([N, B] or
+        [N] arrays in caller order), dose days under a priority strategy, the day."""
+        shape = (self.n,) if self.n_rep == 1 else (self.n, self.n_rep)
+        out = dict(stage=np.zeros(shape, np.int8), timer=np.zeros(shape, np.int16), tinf=np.zeros(shape, np.int16),
+                   flags=np.zeros(shape, np.uint8), qt=np.zeros(shape, np.uint8),
+                   dose1_day=np.zeros(self.n, np.int16), dose2_day=np.zeros(self.n, np.int16))
+        day = C.c_uint32()
+        _check(lib().deabm_save(self.ctx, *(_p(out[k]) for k in ("stage", "timer", "tinf", "flags", "qt",
+                                                                 "dose1_day", "dose2_day")), C.byref(day)), self.ctx)
+        out["day"] = int(day.value)
+        return out
+
+    def restore(self, ckpt: dict):
+        """Resume from a checkpoint of save() (this context or another with the
+        same graph and parameters): the next step runs day ckpt["day"]."""
+        arrs = [np.ascontiguousarray(ckpt[k], dtype=t) for k, t in (("stage", np.int8), ("timer", np.int16),
+                                                                  ("tinf", np.int16), ("flags", np.uint8),
+                                                                  ("qt", np.uint8))]
+        d1 = ckpt.get("dose1_day")
+        d2 = ckpt.get("dose2_day")
+        d1 = None if d1 is None else np.ascontiguousarray(d1, dtype=np.int16)
+        d2 = None if d2 is None else np.ascontiguousarray(d2, dtype=np.int16)
+        _check(lib().deabm_restore(self.ctx, *(_p(a) for a in arrs), _p(d1), _p(d2), int(ckpt["day"])), self.ctx)
 
     def notified(self, days: int | None = None) -> np.ndarray:
         """Agents notified by exposure notification at the end of each day."""
