@@ -3,8 +3,8 @@
 Runs of the batched simulator (libdeabm, N agents, B replicates per launch)
 give pairs (14 parameters, log(1 + new infections per day)); the MLP of
 libdeabm is trained on them on the GPU; the simulator stays the fallback for
-parameters outside the training box and the judge of the surrogate's error in
-peak day and cumulative infections.
+parameters outside the training box and the reference against which the
+surrogate's error in peak day and cumulative infections is measured.
 
     python -m paper_2110_04421_gb300.surrogate [--runs 50000] [--steps 4000]
 """
@@ -126,7 +126,7 @@ def main():
     pred_val = mlp.forward(X[n_tr:]).cpu().numpy()
     base_mse = float(np.mean((Y[n_tr:] - Y[:n_tr].mean(0)) ** 2))
     n_test = max(1, args.runs // 100)
-    test = slice(args.runs - n_test, args.runs)  # held-out 1%, judged by the simulator
+    test = slice(args.runs - n_test, args.runs)  # held-out 1%, checked against re-simulation
     sur = Surrogate(mlp, pop, w["params"], w["T"])
     pred_test, _ = sur.predict(rp[test], seeds[test])
     resim = simulate(pop, w["params"], rp[test], seeds[test], w["T"], B=w["B"])

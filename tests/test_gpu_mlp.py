@@ -119,7 +119,7 @@ def test_reset_reproduces_a_fresh_context():
 
 
 def test_surrogate_beats_the_mean_curve_and_falls_back_outside_its_box():
-    """Trained on 2,048 runs of the N = 100,000 ensemble workload; judged on 256
+    """Trained on 2,048 runs of the N = 100,000 ensemble workload; checked on 256
     unseen runs against re-simulation."""
     import torch
     from paper_2110_04421_gb300 import surrogate as S
