@@ -106,6 +106,28 @@ def test_full_size_plain_workload_first_days():
     assert rep["max_rel_lambda64"] <= 1e-5
 
 
+def test_full_size_bench_configuration_60_days():
+    """The benchmark's launch configuration (no lambda kept, so only susceptible
+    agents gather) at its full size, N = 2,000,000, through day 59: by then about
+    half the agents are no longer susceptible.  Every day's counters and the final
+    state equal the oracle's."""
+    w = W.plain_large()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    T = 60
+    g = gpu_sim(pop, w["params"], keep_lambda=False, max_steps=T)
+    ni, h = g.run(T)
+    _, _, m = g.counters(T)
+    s = g.state()
+    g.close()
+    o = oracle_sim(pop, w["params"])
+    ni_o, h_o, m_o = o.run(T)
+    assert np.array_equal(ni[:, 0], ni_o) and np.array_equal(h[:, 0], h_o)
+    assert np.array_equal(m.astype(np.int64), m_o)
+    for k in ("stage", "timer", "tinf", "flags", "qt"):
+        assert np.array_equal(s[k], getattr(o.state, k)), k
+    assert h_o[-1, 0] < 0.8 * w["n"]  # the skip path carried most agents
+
+
 @pytest.mark.parametrize("B", [37, 36, 132])
 def test_batched_columns_equal_plain_runs_and_oracle(B):
     """B = 37 runs the one-replicate-per-thread panel kernel; B = 36 and 132 (a
