@@ -176,8 +176,9 @@ def test_counters_and_run_agree():
 
 @pytest.mark.parametrize("locality_order", [False, True])
 def test_internal_numbering_changes_nothing(locality_order):
-    """The library's internal agent numbering (breadth-first order of the densest
-    network) is invisible: the same days, draws and outputs, with or without it."""
+    """The library's internal agent numbering (agents grouped by the smallest id
+    reaching them in the densest network) is invisible: the same days, draws and
+    outputs, with or without it."""
     pop = W.population(5003, 11, 25)
     p = W.params_with(test_on=1, quar_on=1, vax_on=1, vax_start=3, vax_rate=0.03, R=4.0, seed=5, net_seed=6)
     rep = compare_days_kw(pop, p, 40, locality_order=locality_order)
