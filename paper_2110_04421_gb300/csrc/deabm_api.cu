@@ -36,6 +36,7 @@ struct deabm_ctx {
     std::vector<uint32_t> new2orig;           // internal id -> caller id (relabelled only)
     uint32_t *orig_id = nullptr;
     void *perm_scratch = nullptr;             // caller-order copies for the readbacks (relabelled only)
+    uint32_t *orig_local = nullptr, *row_local = nullptr;  // ragged: per population, local ids
     // daily occupation networks (internal rows in occupation order)
     uint32_t n_occ = 0;
     uint32_t *occ_gid = nullptr, *occ_start = nullptr;
@@ -864,7 +865,7 @@ static int perm_scratch_ready(deabm_ctx *ctx)
 {
     if (!ctx->relabel || ctx->perm_scratch) return DEABM_OK;
     uint32_t *p;
-    int r = dalloc(ctx, &p, (size_t)ctx->n * ctx->n_rep);
+    int r = dalloc(ctx, &p, (size_t)ctx->n * (ctx->ragged ? 1u : ctx->n_rep));
     if (r) return r;
     ctx->perm_scratch = p;
     return DEABM_OK;
@@ -884,7 +885,8 @@ extern "C" int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, in
     auto fetch = [&](void *dst, const void *src, size_t elem) -> int {
         if (!dst) return DEABM_OK;
         if (ctx->relabel) {
-            CU(ctx, launch_to_caller(ctx->perm_scratch, src, ctx->orig_id, ctx->n, ctx->n_rep, (uint32_t)elem, s));
+            CU(ctx, launch_to_caller(ctx->perm_scratch, src, ctx->orig_id, ctx->n, ctx->ragged ? 1u : ctx->n_rep,
+                                     (uint32_t)elem, s));
             src = ctx->perm_scratch;
         }
         CU(ctx, cudaMemcpyAsync(dst, src, nb * elem, cudaMemcpyDeviceToHost, s));
@@ -1037,9 +1039,10 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         ctx->pop_seeds.resize(n_pops);
         ctx->d_pop_seeds.assign(n_pops, nullptr);
         uint32_t base = 0;
-        std::vector<int8_t> st;
-        std::vector<int16_t> tm, ti;
-        std::vector<uint8_t> fl, qt;
+        if ((r = dalloc(ctx, &ctx->orig_local, N))) return r;
+        if ((r = dalloc(ctx, &ctx->row_local, N))) return r;
+        std::vector<uint32_t> orig_abs(N);  // internal row -> caller row of the concatenated state
+        for (size_t v = 0; v < N; ++v) orig_abs[v] = (uint32_t)v;
         for (uint32_t q = 0; q < n_pops; ++q) {
             const deabm_graph &g = graphs[q];
             const deabm_agents &a = agents[q];
@@ -1055,16 +1058,50 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.inf_len = p.inf_len;
             K.dt = p.dt;
             K.rand_on = g.rand_mean > 0.0f ? 1u : 0u;
+            // the population's stored networks; renumbered on the device like a
+            // plain context's when locality_order asks for it
+            const bool relabel_q = p.locality_order != 0 && g.n_nets > 0;
+            DevScratch sc;
+            uint32_t *src_rp[DEABM_MAX_NETS] = {}, *src_col[DEABM_MAX_NETS] = {};
+            uint32_t best = 0;
             for (uint32_t k = 0; k < g.n_nets; ++k) {
                 const uint32_t E = g.row_ptr[k][n];
+                if (E > g.row_ptr[best][n]) best = k;
                 uint32_t *rp, *cl;
                 if ((r = dalloc(ctx, &rp, (size_t)n + 1))) return r;
                 if ((r = dalloc(ctx, &cl, E))) return r;
-                CU(ctx, cudaMemcpyAsync(rp, g.row_ptr[k], 4ull * (n + 1), cudaMemcpyHostToDevice, s));
-                if (E) CU(ctx, cudaMemcpyAsync(cl, g.col[k], 4ull * E, cudaMemcpyHostToDevice, s));
+                src_rp[k] = rp;
+                src_col[k] = cl;
+                if (relabel_q) {
+                    if ((r = scratch_alloc(ctx, sc, &src_rp[k], (size_t)n + 1))) return r;
+                    if ((r = scratch_alloc(ctx, sc, &src_col[k], E))) return r;
+                }
+                CU(ctx, cudaMemcpyAsync(src_rp[k], g.row_ptr[k], 4ull * (n + 1), cudaMemcpyHostToDevice, s));
+                if (E) CU(ctx, cudaMemcpyAsync(src_col[k], g.col[k], 4ull * E, cudaMemcpyHostToDevice, s));
                 K.row_ptr[k] = rp;
                 K.col[k] = cl;
                 ctx->static_edges += E;
+            }
+            std::vector<uint32_t> n2o, o2n;  // this population's numbering (local ids)
+            if (relabel_q) {
+                uint32_t *label, *tmp, *d_scan;
+                if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &tmp, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &d_scan, scan_scratch_words((size_t)n + 1)))) return r;
+                CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, s));
+                std::vector<uint32_t> lab(n);
+                CU(ctx, cudaMemcpyAsync(lab.data(), label, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
+                CU(ctx, cudaStreamSynchronize(s));
+                sort_by_label(lab, n2o);
+                o2n.resize(n);
+                for (uint32_t v = 0; v < n; ++v) o2n[n2o[v]] = v;
+                CU(ctx, cudaMemcpyAsync(ctx->orig_local + base, n2o.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->row_local + base, o2n.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+                for (uint32_t k = 0; k < g.n_nets; ++k)
+                    CU(ctx, launch_csr_renumber(src_rp[k], src_col[k], ctx->orig_local + base, ctx->row_local + base, n,
+                                                (uint32_t *)K.row_ptr[k], (uint32_t *)K.col[k], d_scan, s));
+                for (uint32_t v = 0; v < n; ++v) orig_abs[base + v] = base + n2o[v];
+                pd.row_of = ctx->row_local + base;
             }
             K.net_seed = p.net_seed;
             K.test_on = p.test_on;
@@ -1083,7 +1120,7 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.rep = ctx->rep + q;
             K.age = ctx->age + base;
             K.dose1_day = ctx->dose1 + base;
-            K.orig_id = nullptr;
+            K.orig_id = relabel_q ? ctx->orig_local + base : nullptr;
             std::vector<Rep> reps;
             build_reps(&p, 1, nullptr, nullptr, reps);
             pd.rep = reps[0];
@@ -1116,30 +1153,59 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             CU(ctx, cudaMemcpyAsync(d_gamma + 6 * q, gs, sizeof gs, cudaMemcpyHostToDevice, s));
             CU(ctx, cudaMemcpyAsync(d_A + 3 * q, p.A_class, sizeof(float) * 3, cudaMemcpyHostToDevice, s));
             CU(ctx, launch_inf_table(ctx->tab + q, d_gamma + 6 * q, d_A + 3 * q, p.inf_len, s));
-            CU(ctx, cudaMemcpyAsync(ctx->age + base, a.age_bin, n, cudaMemcpyHostToDevice, s));
+            // per-agent arrays go up in caller order and are put in place on the device
+            uint16_t *d_in;
+            if ((r = scratch_alloc(ctx, sc, &d_in, n))) return r;
+            const uint32_t *perm = relabel_q ? ctx->orig_local + base : nullptr;
+            auto put = [&](void *dst, const void *src, uint32_t elem) -> int {
+                if (!src) {
+                    CU(ctx, cudaMemsetAsync(dst, 0, (size_t)n * elem, s));
+                } else if (!perm) {
+                    CU(ctx, cudaMemcpyAsync(dst, src, (size_t)n * elem, cudaMemcpyHostToDevice, s));
+                } else {
+                    CU(ctx, cudaMemcpyAsync(d_in, src, (size_t)n * elem, cudaMemcpyHostToDevice, s));
+                    CU(ctx, launch_from_caller(dst, d_in, perm, n, 1u, elem, false, s));
+                }
+                return DEABM_OK;
+            };
             const uint32_t per_day = p.vax_on ? (uint32_t)std::floor(p.vax_rate * (double)n) : 0u;
-            CU(ctx, launch_dose1_days(ctx->age + base, n, p.vax_start, per_day, ctx->dose1 + base, d_scratch, s));
-            st.assign(n, 0); tm.assign(n, 0); ti.assign(n, 0); fl.assign(n, 0); qt.assign(n, 0);
-            for (uint32_t j = 0; j < n; ++j) {
-                if (a.stage) st[j] = a.stage[j];
-                if (a.timer) tm[j] = a.timer[j];
-                if (a.tinf) ti[j] = a.tinf[j];
-                if (a.flags) fl[j] = a.flags[j];
-                if (a.qt) qt[j] = a.qt[j];
+            if (perm) {  // first-dose days from the caller-order ages (ties by caller id), then put in place
+                uint8_t *d_age;
+                int16_t *d_dose;
+                if ((r = scratch_alloc(ctx, sc, &d_age, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &d_dose, n))) return r;
+                CU(ctx, cudaMemcpyAsync(d_age, a.age_bin, n, cudaMemcpyHostToDevice, s));
+                CU(ctx, launch_dose1_days(d_age, n, p.vax_start, per_day, d_dose, d_scratch, s));
+                CU(ctx, launch_gather_i16(ctx->dose1 + base, d_dose, perm, n, s));
+                if ((r = put(ctx->age + base, a.age_bin, 1))) return r;
+            } else {
+                CU(ctx, cudaMemcpyAsync(ctx->age + base, a.age_bin, n, cudaMemcpyHostToDevice, s));
+                CU(ctx, launch_dose1_days(ctx->age + base, n, p.vax_start, per_day, ctx->dose1 + base, d_scratch, s));
             }
-            CU(ctx, cudaMemcpyAsync(ctx->S0.stage + base, st.data(), n, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S0.timer + base, tm.data(), 2ull * n, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S0.tinf + base, ti.data(), 2ull * n, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S0.flags + base, fl.data(), n, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaMemcpyAsync(ctx->S0.qt + base, qt.data(), n, cudaMemcpyHostToDevice, s));
-            CU(ctx, cudaStreamSynchronize(s));  // staging vectors are reused by the next population
+            if ((r = put(ctx->S0.stage + base, a.stage, 1))) return r;
+            if ((r = put(ctx->S0.timer + base, a.timer, 2))) return r;
+            if ((r = put(ctx->S0.tinf + base, a.tinf, 2))) return r;
+            if ((r = put(ctx->S0.flags + base, a.flags, 1))) return r;
+            if ((r = put(ctx->S0.qt + base, a.qt, 1))) return r;
+            CU(ctx, cudaStreamSynchronize(s));  // scratch of this population ends here
             ctx->pop_seeds[q].assign(a.seed_ids, a.seed_ids + a.n_seed);
+            if (relabel_q)
+                for (auto &x : ctx->pop_seeds[q]) x = o2n[x];
             if (a.n_seed) {
                 if ((r = dalloc(ctx, &ctx->d_pop_seeds[q], a.n_seed))) return r;
-                CU(ctx, cudaMemcpyAsync(ctx->d_pop_seeds[q], a.seed_ids, 4ull * a.n_seed, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->d_pop_seeds[q], ctx->pop_seeds[q].data(), 4ull * a.n_seed,
+                                        cudaMemcpyHostToDevice, s));
                 CU(ctx, cudaStreamSynchronize(s));
             }
             base += n;
+        }
+        bool any_relabel = false;
+        for (uint32_t q = 0; q < n_pops; ++q) any_relabel |= ctx->pops[q].row_of != nullptr;
+        if (any_relabel) {  // readbacks put every agent back at its caller position
+            ctx->relabel = true;
+            if ((r = dalloc(ctx, &ctx->orig_id, N))) return r;
+            CU(ctx, cudaMemcpyAsync(ctx->orig_id, orig_abs.data(), 4 * N, cudaMemcpyHostToDevice, s));
+            ctx->new2orig = orig_abs;
         }
         if ((r = dalloc(ctx, &ctx->d_pops, n_pops))) return r;
         CU(ctx, cudaMemcpyAsync(ctx->d_pops, ctx->pops.data(), sizeof(PopDesc) * n_pops, cudaMemcpyHostToDevice, s));

@@ -144,6 +144,7 @@ struct StateRef {
 struct PopDesc {
     KParams kp;
     Rep rep;
+    const uint32_t *row_of;  // the population's caller id -> local row (nullptr: not renumbered)
     uint32_t base;
     uint32_t pad_[3];
 };

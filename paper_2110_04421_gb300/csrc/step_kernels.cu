@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restr
         I.next = inf_next + sp.base;
         I.rand_cur = I.cur;
         I.rand_next = nullptr;
-        I.row_of = nullptr;
+        I.row_of = sp.row_of;  // random contacts (caller ids) reach rows through the map
         StateRef Sp;
         Sp.stage = S.stage + sp.base;
         Sp.timer = S.timer + sp.base;
@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restr
             int st = 0;
             bool infected = false;
             uint32_t k = 0;
-            if (active) agent_day<false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k);
+            if (active)
+                agent_day<false, false, true>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k);
             count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
         }
         __syncthreads();
