@@ -66,16 +66,31 @@ struct RandHead {
     float v[3];
 };
 
+// Block 0 of agent j's random network on `day` (caller id) and the day's
+// in-contact count it fixes: K_j = the number of Poisson thresholds at or
+// below word 0, at most DEABM_POIS_CAP.
+struct RandBlock0 {
+    uint4 w;
+    uint32_t k;
+};
+
+__device__ __forceinline__ RandBlock0 random_block0(const KParams &P, uint32_t j, uint32_t day)
+{
+    RandBlock0 r;
+    r.w = draw(seed_key(P.net_seed), j, day, kStreamRnet, 0u);
+    r.k = 0;
+    while (r.k < DEABM_POIS_CAP && (uint64_t)r.w.x >= __ldg(&P.tab->pois[r.k])) ++r.k;
+    return r;
+}
+
 template <bool REC, bool ROWMAP>
 __device__ __forceinline__ RandHead random_head(const KParams &P, const float *__restrict__ inf, uint32_t j,
-                                                uint32_t day, uint32_t stride, uint32_t b, uint32_t *rec,
+                                                const RandBlock0 &r0, uint32_t stride, uint32_t b, uint32_t *rec,
                                                 const uint32_t *row_of)
 {
-    const uint2 nk = seed_key(P.net_seed);
-    const uint4 w = draw(nk, j, day, kStreamRnet, 0u);
+    const uint4 w = r0.w;
     RandHead h;
-    h.k = 0;
-    while (h.k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[h.k])) ++h.k;
+    h.k = r0.k;
     const uint64_t nm1 = (uint64_t)(P.n - 1u);
     const uint32_t x[3] = {w.y, w.z, w.w};
 #pragma unroll
@@ -126,7 +141,7 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
                                             uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
                                             uint32_t *rec = nullptr, const uint32_t *row_of = nullptr)
 {
-    const RandHead h = random_head<REC, ROWMAP>(P, inf, j, day, stride, b, rec, row_of);
+    const RandHead h = random_head<REC, ROWMAP>(P, inf, j, random_block0(P, j, day), stride, b, rec, row_of);
     *k_out = h.k;
     return random_tail<REC, ROWMAP>(P, inf, j, day, stride, b, h, rec, row_of);
 }
@@ -211,20 +226,12 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
     return h;
 }
 
-// lambda_j of one (agent, replicate) from the state of the day; j = internal row,
-// jo = the caller's id of the same agent.  OCC = false compiles the daily
-// occupation networks out (for contexts that have none).  The row bounds of every network are
-// loaded first and the random contacts are generated while they are in flight.
 // The number of the day's in-contacts of an agent whose lambda is not needed
-// (not susceptible): the random network's count from its first Philox word and
-// the occupation's daily count.  No gathers.
-__device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t jo, uint32_t day)
+// (not susceptible): the random network's count (k_rand, from block 0) and the
+// occupation's daily count.  No gathers.
+__device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t k_rand)
 {
-    uint32_t k = 0;
-    if (P.rand_on) {
-        const uint4 w = draw(seed_key(P.net_seed), jo, day, kStreamRnet, 0u);
-        while (k < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k])) ++k;
-    }
+    uint32_t k = k_rand;
     if (P.n_occ) {
         const uint32_t g = __ldg(P.occ_gid + j);
         if (__ldg(P.occ_start + g + 1u) - __ldg(P.occ_start + g) > 1u) k += __ldg(P.occ_k + g);
@@ -232,19 +239,34 @@ __device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, 
     return k;
 }
 
-// REC: the agent's exposure-notification record of the day goes to rec (when
-// not null).
-template <bool OCC = true, bool REC = false, bool ROWMAP = false>
-__device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
-                                           uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out,
-                                           uint32_t *rec = nullptr)
-{
+// Row bounds of agent j (internal row) in every stored network.
+struct RowBounds {
     uint32_t beg[DEABM_MAX_NETS], end[DEABM_MAX_NETS];
+};
+
+__device__ __forceinline__ RowBounds row_bounds(const KParams &P, uint32_t j)
+{
+    RowBounds rb;
 #pragma unroll
     for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
-        beg[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j) : 0u;
-        end[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j + 1) : 0u;
+        rb.beg[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j) : 0u;
+        rb.end[net] = net < P.n_nets ? __ldg(P.row_ptr[net] + j + 1) : 0u;
     }
+    return rb;
+}
+
+// lambda_j of one (agent, replicate) from the state of the day; j = internal row,
+// jo = the caller's id of the same agent; rb = its row bounds, r0 = block 0 of
+// its random network (unused when the random network is off).  OCC = false
+// compiles the daily occupation networks out (for contexts that have none).
+// Callers load the row bounds and draw block 0 first, so that the bounds are in
+// flight while the Philox rounds run.  REC: the agent's exposure-notification
+// record of the day goes to rec (when not null).
+template <bool OCC = true, bool REC = false, bool ROWMAP = false>
+__device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
+                                           uint32_t day, uint32_t stride, uint32_t b, int age, const RowBounds &rb,
+                                           const RandBlock0 &r0, uint32_t *k_out, uint32_t *rec = nullptr)
+{
     *k_out = 0;
     const bool rmap = ROWMAP && I.row_of != nullptr;
     const float *rinf = rmap ? I.cur : I.rand_cur;
@@ -253,8 +275,8 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
     float r_now = 0.0f;
 #endif
     if (P.rand_on) {  // block 0's gathers go out now and are added after the stored networks
-        head = rmap ? random_head<REC, true>(P, rinf, jo, day, stride, b, rec, I.row_of)
-                    : random_head<REC, false>(P, rinf, jo, day, stride, b, rec, nullptr);
+        head = rmap ? random_head<REC, true>(P, rinf, jo, r0, stride, b, rec, I.row_of)
+                    : random_head<REC, false>(P, rinf, jo, r0, stride, b, rec, nullptr);
 #if !DEABM_RAND_DEFER
         r_now = rmap ? random_tail<REC, true>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
                      : random_tail<REC, false>(P, rinf, jo, day, stride, b, head, rec, nullptr);
@@ -267,8 +289,8 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
 #pragma unroll
     for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
         if (net < P.n_nets) {
-            const float h = net == 0 ? csr_sum<DEABM_ROUND0>(P.col[net], I.cur, beg[net], end[net], stride, b)
-                                     : csr_sum<DEABM_ROUND>(P.col[net], I.cur, beg[net], end[net], stride, b);
+            const float h = net == 0 ? csr_sum<DEABM_ROUND0>(P.col[net], I.cur, rb.beg[net], rb.end[net], stride, b)
+                                     : csr_sum<DEABM_ROUND>(P.col[net], I.cur, rb.beg[net], rb.end[net], stride, b);
             const float term = __fmul_rn(rp.B_net[net], h);
             s = net == 0 ? term : __fadd_rn(s, term);
         }
@@ -290,6 +312,18 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
         s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
     }
     return __fmul_rn(__fmul_rn(rp.cR, rp.S_age[age]), s);
+}
+
+// lambda_j with its own bounds and block 0 (see lambda_at).
+template <bool OCC = true, bool REC = false, bool ROWMAP = false>
+__device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
+                                           uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out,
+                                           uint32_t *rec = nullptr)
+{
+    const RowBounds rb = row_bounds(P, j);
+    RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
+    if (P.rand_on) r0 = random_block0(P, jo, day);
+    return lambda_at<OCC, REC, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
 }
 
 }  // namespace deabm

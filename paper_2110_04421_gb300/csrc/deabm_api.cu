@@ -169,40 +169,6 @@ static uint32_t host_threads(uint32_t n)
     return n < (1u << 16) ? 1u : std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
 }
 
-// Stable counting sort of the agents by label on host threads: order[] lists the
-// agents by ascending label, ascending id among equal labels.  Labels are first
-// made dense (groups numbered in label order) so that each thread's counts take
-// one word per group.
-static void sort_by_label(const std::vector<uint32_t> &lab, std::vector<uint32_t> &order)
-{
-    const uint32_t n = (uint32_t)lab.size(), T = host_threads(n);
-    std::vector<uint8_t> used(n, 0);
-    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t) {
-        for (uint32_t v = b; v < e; ++v) used[lab[v]] = 1;  // every writer stores 1
-    });
-    std::vector<uint32_t> gidx(n);
-    uint32_t G = 0;
-    for (uint32_t l = 0; l < n; ++l) {
-        gidx[l] = G;
-        G += used[l];
-    }
-    std::vector<std::vector<uint32_t>> cnt(T, std::vector<uint32_t>(G, 0));
-    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t t) {
-        for (uint32_t v = b; v < e; ++v) cnt[t][gidx[lab[v]]]++;
-    });
-    uint32_t run = 0;  // offsets: group by group, thread by thread (so ids stay ascending)
-    for (uint32_t g = 0; g < G; ++g)
-        for (uint32_t t = 0; t < T; ++t) {
-            const uint32_t c = cnt[t][g];
-            cnt[t][g] = run;
-            run += c;
-        }
-    order.resize(n);
-    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t t) {
-        for (uint32_t v = b; v < e; ++v) order[cnt[t][gidx[lab[v]]]++] = v;
-    });
-}
-
 static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a, const deabm_params *p,
                     uint32_t n_rep, const float *rep_params)
 {
@@ -213,19 +179,58 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
     if (!(g->rand_mean >= 0.0f) || g->rand_mean > 1e3f) return fail(ctx, DEABM_EINVAL, "rand_mean out of range");
     if (g->rand_mean > 0.0f && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
     if ((uint64_t)n * n_rep >= (1ull << 40)) return fail(ctx, DEABM_EINVAL, "n_agents * n_rep too large");
+    // Every per-row check runs in one pass over the rows on host threads (each
+    // thread a contiguous range); errors are then reported in a fixed order.  A
+    // row's edges are read only when rp[q] <= rp[q+1] <= rp[n], i.e. inside col.
+    const bool occ_arrays = g->n_occ && g->n_occ < (1u << 31) && g->occ_group && g->occ_k;
+    struct Firsts {
+        uint32_t dec[DEABM_MAX_NETS], col[DEABM_MAX_NETS], occ, age, stage, qt;
+    };
+    const uint32_t T = host_threads(n);
+    std::vector<Firsts> found(T);
+    parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t t) {
+        Firsts f;
+        for (uint32_t k = 0; k < DEABM_MAX_NETS; ++k) f.dec[k] = f.col[k] = n;
+        f.occ = f.age = f.stage = f.qt = n;
+        for (uint32_t k = 0; k < g->n_nets; ++k) {
+            const uint32_t *rp = g->row_ptr[k], *col = g->col[k];
+            if (!rp) continue;
+            const uint32_t last = rp[n];
+            const bool cols = col != nullptr || last == 0;
+            for (uint32_t q = b; q < e; ++q) {
+                const uint32_t lo = rp[q], hi = rp[q + 1];
+                if (hi < lo) {
+                    if (f.dec[k] == n) f.dec[k] = q;
+                    continue;
+                }
+                if (!cols || hi > last || f.col[k] < n) continue;
+                uint32_t bad = 0;
+                for (uint32_t x = lo; x < hi; ++x) bad |= (uint32_t)(col[x] >= n) | (uint32_t)(col[x] == q);
+                if (bad) f.col[k] = q;
+            }
+        }
+        for (uint32_t q = b; q < e; ++q) {
+            if (occ_arrays && f.occ == n && g->occ_group[q] >= g->n_occ) f.occ = q;
+            if (a->age_bin && f.age == n && a->age_bin[q] >= DEABM_N_AGE) f.age = q;
+            if (a->stage && f.stage == n && (a->stage[q] < 0 || a->stage[q] >= DEABM_N_STAGE)) f.stage = q;
+            if (a->qt && f.qt == n && (a->qt[q] & 0x80u) != 0) f.qt = q;
+        }
+        found[t] = f;
+    });
+    auto first = [&](uint32_t Firsts::*m) {
+        uint32_t v = n;
+        for (const Firsts &f : found) v = std::min(v, f.*m);
+        return v;
+    };
     for (uint32_t k = 0; k < g->n_nets; ++k) {
         const uint32_t *rp = g->row_ptr[k], *col = g->col[k];
         if (!rp) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] is NULL", k);
         if (rp[0] != 0) return fail(ctx, DEABM_EINVAL, "row_ptr[%u][0] != 0", k);
-        uint32_t j = first_bad_row(n, [&](uint32_t q) { return rp[q + 1] < rp[q]; });
+        uint32_t j = n;
+        for (const Firsts &f : found) j = std::min(j, f.dec[k]);
         if (j < n) return fail(ctx, DEABM_EINVAL, "row_ptr[%u] decreases at row %u", k, j);
         if (rp[n] > 0 && !col) return fail(ctx, DEABM_EINVAL, "col[%u] is NULL", k);
-        // rows are non-decreasing from here on, so every row's edges lie inside col
-        j = first_bad_row(n, [&](uint32_t q) {
-            for (uint32_t e = rp[q]; e < rp[q + 1]; ++e)
-                if (col[e] >= n || col[e] == q) return true;
-            return false;
-        });
+        for (const Firsts &f : found) j = std::min(j, f.col[k]);
         if (j < n)
             for (uint32_t e = rp[j]; e < rp[j + 1]; ++e) {
                 if (col[e] >= n) return fail(ctx, DEABM_EINVAL, "col[%u][%u] = %u >= n_agents", k, e, col[e]);
@@ -244,21 +249,16 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         for (uint32_t q = 0; q < g->n_occ; ++q)
             if (g->occ_k[q] > DEABM_POIS_CAP)
                 return fail(ctx, DEABM_EINVAL, "occ_k[%u] = %u > %d", q, g->occ_k[q], DEABM_POIS_CAP);
-        for (uint32_t j = 0; j < n; ++j)
-            if (g->occ_group[j] >= g->n_occ)
-                return fail(ctx, DEABM_EINVAL, "occ_group[%u] = %u >= n_occ", j, g->occ_group[j]);
+        const uint32_t j = first(&Firsts::occ);
+        if (j < n) return fail(ctx, DEABM_EINVAL, "occ_group[%u] = %u >= n_occ", j, g->occ_group[j]);
     }
     if (!a->age_bin) return fail(ctx, DEABM_EINVAL, "age_bin is required");
-    uint32_t jb = first_bad_row(n, [&](uint32_t q) { return a->age_bin[q] >= DEABM_N_AGE; });
+    uint32_t jb = first(&Firsts::age);
     if (jb < n) return fail(ctx, DEABM_EINVAL, "age_bin[%u] = %u > 8", jb, a->age_bin[jb]);
-    if (a->stage) {
-        jb = first_bad_row(n, [&](uint32_t q) { return a->stage[q] < 0 || a->stage[q] >= DEABM_N_STAGE; });
-        if (jb < n) return fail(ctx, DEABM_EINVAL, "stage[%u] = %d is not a stage code", jb, a->stage[jb]);
-    }
-    if (a->qt) {
-        jb = first_bad_row(n, [&](uint32_t q) { return (a->qt[q] & 0x80u) != 0; });
-        if (jb < n) return fail(ctx, DEABM_EINVAL, "qt[%u] has bit 7 set", jb);
-    }
+    jb = first(&Firsts::stage);
+    if (jb < n) return fail(ctx, DEABM_EINVAL, "stage[%u] = %d is not a stage code", jb, a->stage[jb]);
+    jb = first(&Firsts::qt);
+    if (jb < n) return fail(ctx, DEABM_EINVAL, "qt[%u] has bit 7 set", jb);
     if (a->n_seed && !a->seed_ids) return fail(ctx, DEABM_EINVAL, "seed_ids is NULL");
     for (uint32_t q = 0; q < a->n_seed; ++q)
         if (a->seed_ids[q] >= n) return fail(ctx, DEABM_EINVAL, "seed_ids[%u] >= n_agents", q);
@@ -326,6 +326,18 @@ static int scratch_alloc(deabm_ctx *ctx, DevScratch &sc, T **out, size_t count)
     }
     sc.ptrs.push_back(ptr);
     *out = (T *)ptr;
+    return DEABM_OK;
+}
+
+// The internal order on the host (row -> caller id), read back from the device on
+// first use: only the readbacks of host-side gathers need it.
+static int host_order(deabm_ctx *ctx)
+{
+    if (!ctx->relabel || !ctx->new2orig.empty()) return DEABM_OK;
+    std::vector<uint32_t> v(ctx->n);
+    CU(ctx, cudaMemcpyAsync(v.data(), ctx->orig_id, sizeof(uint32_t) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->new2orig.swap(v);
     return DEABM_OK;
 }
 
@@ -442,40 +454,39 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                                         cudaMemcpyHostToDevice, s));
                 if (E) CU(ctx, cudaMemcpyAsync(src_col[k], g->col[k], sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
             }
-            std::vector<uint32_t> orig2new, occ_start;
-            if (g->n_occ) {
-                occupation_order(g, ctx->new2orig, occ_start);
-            } else if (ctx->relabel) {
-                // groups by the smallest id reaching them along the densest network's
-                // in-edges (computed on the device), ids ascending inside a group
-                uint32_t *label, *tmp;
-                if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
-                if ((r = scratch_alloc(ctx, sc, &tmp, n))) return r;
-                CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, s));
-                std::vector<uint32_t> lab(n);
-                CU(ctx, cudaMemcpyAsync(lab.data(), label, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
-                CU(ctx, cudaStreamSynchronize(s));
-                sort_by_label(lab, ctx->new2orig);
-            }
+            std::vector<uint32_t> occ_start;
+            uint32_t *d_o2n = nullptr;
             if (ctx->relabel) {
-                orig2new.resize(n);
-                parallel_chunks(n, host_threads(n), [&](uint32_t b, uint32_t e, uint32_t) {
-                    for (uint32_t q = b; q < e; ++q) orig2new[ctx->new2orig[q]] = q;
-                });
-                uint32_t *d_o2n, *d_scan;
                 if ((r = dalloc(ctx, &ctx->orig_id, n))) return r;
                 if ((r = scratch_alloc(ctx, sc, &d_o2n, n))) return r;
-                if ((r = scratch_alloc(ctx, sc, &d_scan, scan_scratch_words((size_t)n + 1)))) return r;
+            }
+            if (g->n_occ) {
+                occupation_order(g, ctx->new2orig, occ_start);
                 CU(ctx, cudaMemcpyAsync(ctx->orig_id, ctx->new2orig.data(), sizeof(uint32_t) * n,
                                         cudaMemcpyHostToDevice, s));
-                CU(ctx, cudaMemcpyAsync(d_o2n, orig2new.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+            } else if (ctx->relabel) {
+                // groups by the smallest id reaching them along the densest network's
+                // in-edges, ids ascending inside a group: labels and order on the device
+                uint32_t *label, *tmp;
+                if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &tmp, std::max<size_t>(n, order_scratch_words(n))))) return r;
+                CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, s));
+                CU(ctx, launch_order_by_label(label, n, ctx->orig_id, tmp, s));
+            }
+            if (ctx->relabel) {
+                uint32_t *d_scan;
+                if ((r = scratch_alloc(ctx, sc, &d_scan, scan_scratch_words((size_t)n + 1)))) return r;
+                CU(ctx, launch_invert(ctx->orig_id, n, d_o2n, s));
                 // rows in internal order, each row's edges kept in the caller's order
                 for (uint32_t k = 0; k < g->n_nets; ++k)
                     CU(ctx, launch_csr_renumber(src_rp[k], src_col[k], ctx->orig_id, d_o2n, n, ctx->row_ptr[k],
                                                 ctx->col[k], d_scan, s));
             }
+            if (ctx->relabel && g->rand_mean > 0.0f && n_rep > 1) {  // batched: caller id -> row map
+                if ((r = dalloc(ctx, &ctx->row_of, n))) return r;
+                CU(ctx, cudaMemcpyAsync(ctx->row_of, d_o2n, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+            }
             CU(ctx, cudaStreamSynchronize(s));  // host staging and device scratch end here
-            auto orig_of = [&](uint32_t q) { return ctx->relabel ? ctx->new2orig[q] : q; };
             if (g->n_occ) {
                 ctx->n_occ = g->n_occ;
                 std::vector<uint32_t> gid(n);
@@ -498,16 +509,9 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->S.qt, nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
-            if (ctx->relabel && g->rand_mean > 0.0f) {
-                if (n_rep == 1) {
-                    if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
-                    if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
-                } else {
-                    if ((r = dalloc(ctx, &ctx->row_of, n))) return r;
-                    CU(ctx, cudaMemcpyAsync(ctx->row_of, orig2new.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
-                                            s));
-                    CU(ctx, cudaStreamSynchronize(s));  // orig2new is host staging
-                }
+            if (ctx->relabel && g->rand_mean > 0.0f && n_rep == 1) {
+                if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
+                if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
             }
             if (ctx->keep_lambda) {
                 if ((r = dalloc(ctx, &ctx->lam, nb))) return r;
@@ -574,6 +578,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             ctx->base = *p;
             if (p->vax_strategy != 0) {
                 std::vector<int16_t> d1(nb, kNever), d2(nb, kNever);
+                if ((a->dose1_day || a->dose2_day) && (r = host_order(ctx))) return r;
+                auto orig_of = [&](uint32_t q) { return ctx->relabel ? ctx->new2orig[q] : q; };
                 for (uint32_t q = 0; q < n; ++q) {
                     if (a->dose1_day) d1[q] = a->dose1_day[orig_of(q)];
                     if (a->dose2_day) d2[q] = a->dose2_day[orig_of(q)];
@@ -705,11 +711,9 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             }
 
             if (a->n_seed) {
-                std::vector<uint32_t> ids(a->seed_ids, a->seed_ids + a->n_seed);
-                if (ctx->relabel)
-                    for (auto &x : ids) x = orig2new[x];
                 if ((r = dalloc(ctx, &d_ids, a->n_seed))) return r;
-                CU(ctx, cudaMemcpyAsync(d_ids, ids.data(), sizeof(uint32_t) * a->n_seed, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(d_ids, a->seed_ids, sizeof(uint32_t) * a->n_seed, cudaMemcpyHostToDevice, s));
+                if (ctx->relabel) CU(ctx, launch_map_ids(d_ids, a->n_seed, d_o2n, s));
                 CU(ctx, launch_seed(K, d_ids, a->n_seed, ctx->S, s));
                 CU(ctx, cudaStreamSynchronize(s));
                 ctx->seed_ids = d_ids;
@@ -912,6 +916,8 @@ extern "C" int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *
     CU(ctx, cudaMemcpyAsync(t1.data(), ctx->S.vd1, nb * 2, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaMemcpyAsync(t2.data(), ctx->S.vd2, nb * 2, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    int r = host_order(ctx);
+    if (r) return r;
     for (uint32_t q = 0; q < ctx->n; ++q) {
         const uint32_t o = ctx->relabel ? ctx->new2orig[q] : q;
         if (dose1_day) dose1_day[o] = t1[q];
@@ -928,8 +934,11 @@ extern "C" int deabm_get_tables(deabm_ctx *ctx, float *inf_table, uint64_t *pois
     std::vector<int16_t> d1(dose1_day ? ctx->n : 0);
     if (dose1_day) CU(ctx, cudaMemcpyAsync(d1.data(), ctx->dose1, 2ull * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
-    if (dose1_day)
+    if (dose1_day) {
+        int r = host_order(ctx);
+        if (r) return r;
         for (uint32_t q = 0; q < ctx->n; ++q) dose1_day[ctx->relabel ? ctx->new2orig[q] : q] = d1[q];
+    }
     if (inf_table)
         for (int c = 0; c < DEABM_N_CLASS; ++c)
             std::memcpy(inf_table + (size_t)c * ctx->kp.inf_len, T.infT[c], sizeof(float) * ctx->kp.inf_len);
@@ -1041,8 +1050,6 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         uint32_t base = 0;
         if ((r = dalloc(ctx, &ctx->orig_local, N))) return r;
         if ((r = dalloc(ctx, &ctx->row_local, N))) return r;
-        std::vector<uint32_t> orig_abs(N);  // internal row -> caller row of the concatenated state
-        for (size_t v = 0; v < N; ++v) orig_abs[v] = (uint32_t)v;
         for (uint32_t q = 0; q < n_pops; ++q) {
             const deabm_graph &g = graphs[q];
             const deabm_agents &a = agents[q];
@@ -1082,25 +1089,17 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
                 K.col[k] = cl;
                 ctx->static_edges += E;
             }
-            std::vector<uint32_t> n2o, o2n;  // this population's numbering (local ids)
-            if (relabel_q) {
+            if (relabel_q) {  // this population's numbering (local ids), built on the device
                 uint32_t *label, *tmp, *d_scan;
                 if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
-                if ((r = scratch_alloc(ctx, sc, &tmp, n))) return r;
+                if ((r = scratch_alloc(ctx, sc, &tmp, std::max<size_t>(n, order_scratch_words(n))))) return r;
                 if ((r = scratch_alloc(ctx, sc, &d_scan, scan_scratch_words((size_t)n + 1)))) return r;
                 CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, s));
-                std::vector<uint32_t> lab(n);
-                CU(ctx, cudaMemcpyAsync(lab.data(), label, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
-                CU(ctx, cudaStreamSynchronize(s));
-                sort_by_label(lab, n2o);
-                o2n.resize(n);
-                for (uint32_t v = 0; v < n; ++v) o2n[n2o[v]] = v;
-                CU(ctx, cudaMemcpyAsync(ctx->orig_local + base, n2o.data(), 4ull * n, cudaMemcpyHostToDevice, s));
-                CU(ctx, cudaMemcpyAsync(ctx->row_local + base, o2n.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+                CU(ctx, launch_order_by_label(label, n, ctx->orig_local + base, tmp, s));
+                CU(ctx, launch_invert(ctx->orig_local + base, n, ctx->row_local + base, s));
                 for (uint32_t k = 0; k < g.n_nets; ++k)
                     CU(ctx, launch_csr_renumber(src_rp[k], src_col[k], ctx->orig_local + base, ctx->row_local + base, n,
                                                 (uint32_t *)K.row_ptr[k], (uint32_t *)K.col[k], d_scan, s));
-                for (uint32_t v = 0; v < n; ++v) orig_abs[base + v] = base + n2o[v];
                 pd.row_of = ctx->row_local + base;
             }
             K.net_seed = p.net_seed;
@@ -1188,13 +1187,12 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             if ((r = put(ctx->S0.flags + base, a.flags, 1))) return r;
             if ((r = put(ctx->S0.qt + base, a.qt, 1))) return r;
             CU(ctx, cudaStreamSynchronize(s));  // scratch of this population ends here
-            ctx->pop_seeds[q].assign(a.seed_ids, a.seed_ids + a.n_seed);
-            if (relabel_q)
-                for (auto &x : ctx->pop_seeds[q]) x = o2n[x];
-            if (a.n_seed) {
+            ctx->pop_seeds[q].assign(a.seed_ids, a.seed_ids + a.n_seed);  // caller ids
+            if (a.n_seed) {  // on the device: local rows
                 if ((r = dalloc(ctx, &ctx->d_pop_seeds[q], a.n_seed))) return r;
                 CU(ctx, cudaMemcpyAsync(ctx->d_pop_seeds[q], ctx->pop_seeds[q].data(), 4ull * a.n_seed,
                                         cudaMemcpyHostToDevice, s));
+                if (relabel_q) CU(ctx, launch_map_ids(ctx->d_pop_seeds[q], a.n_seed, ctx->row_local + base, s));
                 CU(ctx, cudaStreamSynchronize(s));
             }
             base += n;
@@ -1204,8 +1202,11 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         if (any_relabel) {  // readbacks put every agent back at its caller position
             ctx->relabel = true;
             if ((r = dalloc(ctx, &ctx->orig_id, N))) return r;
-            CU(ctx, cudaMemcpyAsync(ctx->orig_id, orig_abs.data(), 4 * N, cudaMemcpyHostToDevice, s));
-            ctx->new2orig = orig_abs;
+            for (uint32_t q = 0; q < n_pops; ++q) {
+                const PopDesc &pd = ctx->pops[q];
+                CU(ctx, launch_offset_ids(ctx->orig_id + pd.base, pd.row_of ? ctx->orig_local + pd.base : nullptr,
+                                          pd.kp.n, pd.base, s));
+            }
         }
         if ((r = dalloc(ctx, &ctx->d_pops, n_pops))) return r;
         CU(ctx, cudaMemcpyAsync(ctx->d_pops, ctx->pops.data(), sizeof(PopDesc) * n_pops, cudaMemcpyHostToDevice, s));

@@ -201,27 +201,32 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
                                         int age, int16_t d1, bool infected, AgentState &a, uint32_t inf_y)
 {
     bool onset = false;
-    if (infected) {
-        new_infection(P.tab, age, draw(key, j, day, kStreamProg), a);
-    } else if (a.st >= DEABM_ASYM && a.st <= DEABM_ICU) {
+    // one draw site for a new infection and for the end of a stage, so that a
+    // warp holding both runs the Philox rounds once
+    const bool in_course = !infected && a.st >= DEABM_ASYM && a.st <= DEABM_ICU;
+    if (in_course) {
         a.ti = a.ti < 32767 ? a.ti + 1 : 32767;
         a.tm -= 1;
-        if (a.tm <= 0) {
-            const uint4 w = draw(key, j, day, kStreamProg);
-            int nx;
-            switch (a.st) {
-            case DEABM_PRE_MILD: nx = DEABM_MILD; onset = true; break;
-            case DEABM_PRE_SEV: nx = DEABM_SEV; onset = true; break;
-            case DEABM_SEV: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_SEV][age]) ? DEABM_HOSP : DEABM_REC; break;
-            case DEABM_HOSP: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_HOSP][age]) ? DEABM_ICU : DEABM_REC; break;
-            case DEABM_ICU: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_ICU][age]) ? DEABM_DEAD : DEABM_REC; break;
-            default: nx = DEABM_REC; break;  // asymptomatic, mild
-            }
-            a.st = nx;
-            a.tm = (nx >= DEABM_ASYM && nx <= DEABM_ICU)
-                       ? (int)uniform_int(w.y, __ldg(&P.tab->dur_lo[nx][age]), __ldg(&P.tab->dur_hi[nx][age]))
-                       : 0;
+    }
+    const bool stage_ends = in_course && a.tm <= 0;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (infected || stage_ends) w = draw(key, j, day, kStreamProg);
+    if (infected) {
+        new_infection(P.tab, age, w, a);
+    } else if (stage_ends) {
+        int nx;
+        switch (a.st) {
+        case DEABM_PRE_MILD: nx = DEABM_MILD; onset = true; break;
+        case DEABM_PRE_SEV: nx = DEABM_SEV; onset = true; break;
+        case DEABM_SEV: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_SEV][age]) ? DEABM_HOSP : DEABM_REC; break;
+        case DEABM_HOSP: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_HOSP][age]) ? DEABM_ICU : DEABM_REC; break;
+        case DEABM_ICU: nx = (uint64_t)w.w < __ldg(&P.tab->thr_branch[DEABM_ICU][age]) ? DEABM_DEAD : DEABM_REC; break;
+        default: nx = DEABM_REC; break;  // asymptomatic, mild
         }
+        a.st = nx;
+        a.tm = (nx >= DEABM_ASYM && nx <= DEABM_ICU)
+                   ? (int)uniform_int(w.y, __ldg(&P.tab->dur_lo[nx][age]), __ldg(&P.tab->dur_hi[nx][age]))
+                   : 0;
     }
     // quarantine in progress: daily dropout, else one day served (Sec. 4.1)
     if (a.qd > 0u) {

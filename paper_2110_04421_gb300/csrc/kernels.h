@@ -47,6 +47,18 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
                                 const uint32_t *orig2new, uint32_t n, uint32_t *rp_new, uint32_t *col_new,
                                 uint32_t *scratch, cudaStream_t stream);
 size_t scan_scratch_words(size_t m);
+// new2orig[q] = the agent at internal row q: agents by ascending label (labels
+// < n), ids ascending among equal labels.  label is overwritten; scratch of
+// order_scratch_words(n) words.
+size_t order_scratch_words(uint32_t n);
+cudaError_t launch_order_by_label(uint32_t *label, uint32_t n, uint32_t *new2orig, uint32_t *scratch,
+                                  cudaStream_t stream);
+// orig2new[new2orig[q]] = q
+cudaError_t launch_invert(const uint32_t *new2orig, uint32_t n, uint32_t *orig2new, cudaStream_t stream);
+// ids[i] = orig2new[ids[i]] for i < m (every ids[i] < the population size)
+cudaError_t launch_map_ids(uint32_t *ids, uint32_t m, const uint32_t *orig2new, cudaStream_t stream);
+// out[v] = base + (local ? local[v] : v) for v < n
+cudaError_t launch_offset_ids(uint32_t *out, const uint32_t *local, uint32_t n, uint32_t base, cudaStream_t stream);
 cudaError_t launch_to_caller(void *out, const void *in, const uint32_t *orig, uint32_t n, uint32_t n_rep,
                              uint32_t elem, cudaStream_t stream);
 // caller-order [n] (in_reps false) or [n][n_rep] array (elem = 1 or 2 bytes) to

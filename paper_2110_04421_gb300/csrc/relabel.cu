@@ -9,6 +9,7 @@
 // ids); this one only decides where data sits.  Also here: the CSR rebuilt in
 // the new numbering and the copy of internal-order arrays back to caller order.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -140,6 +141,159 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
     const uint64_t threads = (uint64_t)n * 32u;
     csr_copy_kernel<<<(unsigned)((threads + 255u) / 256u), 256, 0, stream>>>(rp, col, new2orig, orig2new, rp_new, n,
                                                                              col_new);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- order by label
+// The internal order itself: (label, id) pairs sorted by label with a
+// least-significant-digit radix sort, 8 bits a pass.  Every pass is stable and
+// the ids start ascending, so ids stay ascending inside a group.  Pass: per
+// tile a 256-bin count (hist[1 + digit * tiles + tile], digit-major), one
+// inclusive scan over all counts (giving each (digit, tile) its first output
+// slot), then each tile places its pairs in order: 256 at a time, a pair's
+// slot = its (digit, tile) start + equal digits before it in this tile.
+constexpr uint32_t kRadixThreads = 256;
+
+__global__ void iota_kernel(uint32_t *v, uint32_t n)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_count_kernel(const uint32_t *__restrict__ key, uint32_t n,
+                                                                    uint32_t shift, uint32_t items,
+                                                                    uint32_t *__restrict__ hist, uint32_t tiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * items * kRadixThreads;
+    for (uint32_t r = 0; r < items; ++r) {
+        const uint64_t i = t0 + (uint64_t)r * kRadixThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[1u + (uint64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) hist[0] = 0;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_place_kernel(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, uint32_t n, uint32_t shift, uint32_t items, const uint32_t *__restrict__ start,
+    uint32_t tiles)
+{
+    constexpr uint32_t W = kRadixThreads / 32u;
+    __shared__ uint32_t next[256];     // next free slot of each digit for this tile
+    __shared__ uint32_t wcnt[W][256];  // pairs of each digit in each warp of the current 256
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    next[tid] = start[(uint64_t)tid * tiles + blockIdx.x];  // exclusive: the scan ran over hist shifted by one
+    const uint64_t t0 = (uint64_t)blockIdx.x * items * kRadixThreads;
+    for (uint32_t r = 0; r < items; ++r) {
+#pragma unroll
+        for (uint32_t w = 0; w < W; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const uint64_t i = t0 + (uint64_t)r * kRadixThreads + tid;
+        const bool valid = i < n;
+        const uint32_t k = valid ? kin[i] : 0u;
+        const uint32_t d = valid ? (k >> shift) & 255u : 256u + lane;  // past-the-end lanes match nobody
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t before = peers & ((1u << lane) - 1u);
+        if (valid && before == 0u) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t slot = next[d] + __popc(before);
+            for (uint32_t w = 0; w < warp; ++w) slot += wcnt[w][d];
+            kout[slot] = k;
+            vout[slot] = vin[i];
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+#pragma unroll
+        for (uint32_t w = 0; w < W; ++w) tot += wcnt[w][tid];
+        next[tid] += tot;
+    }
+}
+
+// pairs per thread of a tile: 8, more for very large n so that at most 16384
+// tiles (and 4 M counts) are needed
+static uint32_t radix_items(uint32_t n)
+{
+    const uint64_t per = (uint64_t)kRadixThreads * 16384u;
+    return (uint32_t)std::max<uint64_t>(8u, ((uint64_t)n + per - 1) / per);
+}
+
+static uint32_t radix_tiles(uint32_t n, uint32_t items)
+{
+    const uint64_t tile = (uint64_t)items * kRadixThreads;
+    return (uint32_t)(((uint64_t)n + tile - 1) / tile);
+}
+
+size_t order_scratch_words(uint32_t n)
+{
+    const size_t m = 256u * (size_t)radix_tiles(n, radix_items(n)) + 1u;
+    return 2u * (size_t)n + m + scan_scratch_words(m);
+}
+
+cudaError_t launch_order_by_label(uint32_t *label, uint32_t n, uint32_t *new2orig, uint32_t *scratch,
+                                  cudaStream_t stream)
+{
+    const uint32_t items = radix_items(n), tiles = radix_tiles(n, items);
+    const size_t m = 256u * (size_t)tiles + 1u;
+    uint32_t *k2 = scratch, *v2 = scratch + n, *hist = scratch + 2u * (size_t)n, *scan_tmp = hist + m;
+    const uint32_t bits = n > 1u ? 32u - (uint32_t)__builtin_clz(n - 1u) : 1u;  // labels are < n
+    const uint32_t passes = (bits + 7u) / 8u;
+    // keys alternate label <-> k2, values v2 <-> new2orig, so that the last pass
+    // writes its values to new2orig
+    uint32_t *kin = label, *kout = k2, *vin = (passes & 1u) ? v2 : new2orig, *vout = (passes & 1u) ? new2orig : v2;
+    iota_kernel<<<(n + 255u) / 256u, 256, 0, stream>>>(vin, n);
+    for (uint32_t p = 0; p < passes; ++p) {
+        radix_count_kernel<<<tiles, kRadixThreads, 0, stream>>>(kin, n, 8u * p, items, hist, tiles);
+        cudaError_t e = scan_inplace(hist, m, scan_tmp, stream);
+        if (e != cudaSuccess) return e;
+        radix_place_kernel<<<tiles, kRadixThreads, 0, stream>>>(kin, vin, kout, vout, n, 8u * p, items, hist, tiles);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    return cudaGetLastError();
+}
+
+// orig2new[new2orig[q]] = q
+__global__ void invert_kernel(const uint32_t *__restrict__ new2orig, uint32_t n, uint32_t *__restrict__ orig2new)
+{
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) orig2new[new2orig[q]] = q;
+}
+
+cudaError_t launch_invert(const uint32_t *new2orig, uint32_t n, uint32_t *orig2new, cudaStream_t stream)
+{
+    invert_kernel<<<(n + 255u) / 256u, 256, 0, stream>>>(new2orig, n, orig2new);
+    return cudaGetLastError();
+}
+
+// ids[i] = orig2new[ids[i]]: caller ids to internal rows
+__global__ void map_ids_kernel(uint32_t *ids, uint32_t m, const uint32_t *__restrict__ orig2new)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) ids[i] = orig2new[ids[i]];
+}
+
+cudaError_t launch_map_ids(uint32_t *ids, uint32_t m, const uint32_t *orig2new, cudaStream_t stream)
+{
+    map_ids_kernel<<<(m + 255u) / 256u, 256, 0, stream>>>(ids, m, orig2new);
+    return cudaGetLastError();
+}
+
+// out[v] = base + (local ? local[v] : v): a population's rows to rows of the
+// concatenated state
+__global__ void offset_ids_kernel(uint32_t *__restrict__ out, const uint32_t *__restrict__ local, uint32_t n,
+                                  uint32_t base)
+{
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) out[v] = base + (local ? local[v] : v);
+}
+
+cudaError_t launch_offset_ids(uint32_t *out, const uint32_t *local, uint32_t n, uint32_t base, cudaStream_t stream)
+{
+    offset_ids_kernel<<<(n + 255u) / 256u, 256, 0, stream>>>(out, local, n, base);
     return cudaGetLastError();
 }
 

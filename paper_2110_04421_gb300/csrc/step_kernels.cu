@@ -67,11 +67,18 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     // exposure notification every agent takes the full path: the app holders
     // record their contacts anyway, and one path for all measured faster than the
     // divergent pair there.
+    // Block 0 of the random network is drawn once, before the two paths part,
+    // so that a warp holding both kinds of agent runs its Philox rounds once.
+    const bool full = !DEABM_SUSCEPTIBLE_ONLY || DEN || a.st == DEABM_S || lam_out != nullptr;
+    RowBounds rb = {};
+    if (full) rb = row_bounds(P, j);
+    RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
+    if (P.rand_on) r0 = random_block0(P, jo, day);
     float lam = 0.0f;
-    if (!DEABM_SUSCEPTIBLE_ONLY || DEN || a.st == DEABM_S || lam_out != nullptr)
-        lam = lambda_of<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, k_out, rec);
+    if (full)
+        lam = lambda_at<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
     else
-        *k_out = contact_count(P, j, jo, day);
+        *k_out = contact_count(P, j, r0.k);
     a.tm = S.timer[i];
     a.ti = S.tinf[i];
     a.fl = S.flags[i];

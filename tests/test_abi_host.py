@@ -118,6 +118,52 @@ def test_create_rejects_invalid_input(lib, case):
     assert ctx.value is None and msg
 
 
+@pytest.mark.parametrize("case", ["self_loop_first", "decrease_wins", "age_before_stage", "second_network"])
+def test_create_reports_the_first_error_of_a_large_graph(lib, case):
+    """n = 200,000 rows are checked on several host threads: the error reported is
+    still the first one in the fixed order (network by network: row pointers,
+    then columns; then ages, stages), whichever thread found it, and rows whose
+    bounds leave col are never read."""
+    n = 200_000
+    rp = np.arange(n + 1, dtype=np.uint32)
+    col = ((np.arange(n) + 1) % n).astype(np.uint32)
+    age = np.zeros(n, np.uint8)
+    stage, occ, want = None, None, None
+    if case == "self_loop_first":
+        col[150_000] = n
+        col[10_000] = 10_000
+        want = "self-loop at row 10000 of network 0"
+    elif case == "decrease_wins":
+        col[5] = n
+        rp[100] = 4_000_000_000  # rows 99 and 100 point far past col: never read
+        want = "row_ptr[0] decreases at row 100"
+    elif case == "age_before_stage":
+        age[170_000] = 9
+        stage = np.zeros(n, np.int8)
+        stage[1_000] = 11
+        want = "age_bin[170000]"
+    elif case == "second_network":
+        rp2, col2 = rp.copy(), col.copy()
+        col2[199_999] = 199_999
+        age[3] = 9
+        from paper_2110_04421_gb300 import workloads as W
+        from paper_2110_04421_gb300.deabm import Agents, make_params
+        g = _graph(n, rp, col, 2.0)
+        g.n_nets = 2
+        g.row_ptr[1], g.col[1] = rp2.ctypes.data, col2.ctypes.data
+        a = Agents()
+        a.age_bin = age.ctypes.data
+        p = make_params(W.params_with())
+        ctx = C.c_void_p()
+        rc = lib.deabm_create(C.byref(g), C.byref(a), C.byref(p), None, C.byref(ctx))
+        msg = lib.deabm_last_error(None).decode()
+        assert rc == -1 and ctx.value is None and "self-loop at row 199999 of network 1" in msg, msg
+        return
+    rc, ctx, msg = _create(lib, n, rp, col, age, None, 2.0, stage, occ)
+    assert rc == -1 and ctx.value is None, (case, rc, msg)
+    assert want in msg, (case, msg)
+
+
 def test_null_arguments(lib):
     ctx = C.c_void_p()
     assert lib.deabm_create(None, None, None, None, C.byref(ctx)) == -1
