@@ -429,8 +429,8 @@ def run_ragged(args):
     _, _, msgs = r.counters(args.warmup + T)
     r.close()
     messages = int(msgs[args.warmup:].astype(np.int64).sum())
-    sims = [Simulation(p, par, p["age"], p["seed_ids"], max_steps=args.warmup + T, stream=stream.cuda_stream,
-                       locality_order=False) for p, par in zip(w["pops"], w["params"])]
+    sims = [Simulation(p, par, p["age"], p["seed_ids"], max_steps=args.warmup + T, stream=stream.cuda_stream)
+            for p, par in zip(w["pops"], w["params"])]
     for s in sims:
         s.step(args.warmup)
     torch.cuda.synchronize()
@@ -444,8 +444,17 @@ def run_ragged(args):
     ms_loop = e2.elapsed_time(e3)
     for s in sims:
         s.close()
+    # algorithmic bytes: each population's plain day (its arrays once)
+    alg = sum(step_bytes_plain(int(p["n"]), int(sum(int(rp[-1]) for rp in p["row_ptr"])), len(p["row_ptr"]),
+                               bool(par.get("vax_on", 0)))
+              for p, par in zip(w["pops"], w["params"]))
+    achieved = alg / (ms / T / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
     return {"workload": w["name"], "total_agents": int(sum(p["n"] for p in w["pops"])), "steps": T,
             "value": messages / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / T,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "kernel": "step_ragged_kernel", "alg_bytes_per_launch": alg,
+                         "traffic": None},
             "autotuned": {"rows_per_tile": rows, "blocks_per_sm": bps},
             "loop_of_plain_launches_ms_per_step": ms_loop / T, "multiple_of_plain_loop": ms_loop / ms}
 

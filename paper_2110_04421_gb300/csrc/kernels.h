@@ -37,12 +37,14 @@ cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, float *
 // notification pass that follows each day's update
 cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t stream);
 cudaError_t launch_den(const KParams &P, uint32_t day, const StateRef &S, const Counters &C, cudaStream_t stream);
-// internal numbering: min-label rounds over a CSR (rounds even; result in label,
-// tmp is scratch of n words); a CSR rebuilt in the new numbering (rp_new n+1
+// internal numbering: min-label rounds over a CSR (at most `rounds`, even,
+// fewer once the labels stop moving; result in label, tmp is scratch of n words,
+// changed one device word; synchronises the stream after each pair of rounds);
+// a CSR rebuilt in the new numbering (rp_new n+1
 // words, col_new as many as col, scratch of scan_scratch_words(n + 1) words);
 // internal-order arrays ([n][n_rep] of elem = 1, 2 or 4 bytes) back to caller order
 cudaError_t launch_locality_labels(const uint32_t *rp, const uint32_t *col, uint32_t n, uint32_t rounds,
-                                   uint32_t *label, uint32_t *tmp, cudaStream_t stream);
+                                   uint32_t *label, uint32_t *tmp, uint32_t *changed, cudaStream_t stream);
 cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const uint32_t *new2orig,
                                 const uint32_t *orig2new, uint32_t n, uint32_t *rp_new, uint32_t *col_new,
                                 uint32_t *scratch, cudaStream_t stream);

@@ -3,8 +3,9 @@
 // Agents are renumbered so that the members of a group (a workplace) sit next
 // to each other and a warp's in-edge gathers touch few cache lines.  The order
 // is: agents grouped by the smallest id that reaches them along the in-edges
-// of the network with the most edges (a min-label propagation, a fixed number
-// of rounds), groups in order of that label, ids ascending inside a group.
+// of the network with the most edges (a min-label propagation of at most a
+// fixed number of rounds, stopped once no label moves), groups in order of that
+// label, ids ascending inside a group.
 // Any permutation gives the same results (draws and outputs use the caller's
 // ids); this one only decides where data sits.  Also here: the CSR rebuilt in
 // the new numbering and the copy of internal-order arrays back to caller order.
@@ -21,25 +22,40 @@ __global__ void label_init_kernel(uint32_t *label, uint32_t n)
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) label[v] = v;
 }
 
-// one Jacobi round: out[v] = min(in[v], in[u] for every in-edge u -> v)
+// one Jacobi round: out[v] = min(in[v], in[u] for every in-edge u -> v); *changed
+// is set when some label moved
 __global__ void label_round_kernel(const uint32_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                                   const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n)
+                                   const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n,
+                                   uint32_t *changed)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    uint32_t m = in[v];
+    const uint32_t m0 = in[v];
+    uint32_t m = m0;
     const uint32_t e1 = rp[v + 1];
     for (uint32_t e = rp[v]; e < e1; ++e) m = min(m, __ldg(in + col[e]));
     out[v] = m;
+    if (m != m0) *changed = 1u;
 }
 
 cudaError_t launch_locality_labels(const uint32_t *rp, const uint32_t *col, uint32_t n, uint32_t rounds,
-                                   uint32_t *label, uint32_t *tmp, cudaStream_t stream)
+                                   uint32_t *label, uint32_t *tmp, uint32_t *changed, cudaStream_t stream)
 {
     const uint32_t blocks = (n + 255u) / 256u;
     label_init_kernel<<<blocks, 256, 0, stream>>>(label, n);
-    for (uint32_t r = 0; r < rounds; ++r) {  // rounds is even: the result ends in `label`
-        label_round_kernel<<<blocks, 256, 0, stream>>>(rp, col, (r & 1u) ? tmp : label, (r & 1u) ? label : tmp, n);
+    // rounds in pairs, so that the result ends in `label`; the labels have
+    // converged (and the rest would change nothing) once a pair's second round
+    // moved none of them
+    for (uint32_t r = 0; r + 1u < rounds; r += 2u) {
+        label_round_kernel<<<blocks, 256, 0, stream>>>(rp, col, label, tmp, n, changed);
+        cudaError_t e = cudaMemsetAsync(changed, 0, sizeof(uint32_t), stream);
+        if (e != cudaSuccess) return e;
+        label_round_kernel<<<blocks, 256, 0, stream>>>(rp, col, tmp, label, n, changed);
+        uint32_t moved = 1;
+        if ((e = cudaMemcpyAsync(&moved, changed, sizeof moved, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+            return e;
+        if (!moved) break;
     }
     return cudaGetLastError();
 }

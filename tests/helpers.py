@@ -36,9 +36,14 @@ def gpu_sim(pop, params, keep_lambda=True, state=None, seed_ids="pop", **kw):
 def compare_days(pop, params, T, state=None, seed_ids="pop", check_lambda=True):
     """Run T days on both sides, comparing after every day.  Returns a report dict.
     A draw whose |u - p| < 1e-6 on the oracle side is a tolerated flip: it ends
-    the comparison (the trajectories legitimately part there) and is counted."""
+    the comparison (the trajectories legitimately part there) and is counted.
+    With check_lambda a second GPU context that does not keep lambda (the
+    launch configuration of runs and of the benchmark) steps alongside and must
+    equal the first bit for bit every day."""
     osim = oracle_sim(pop, params, state, seed_ids)
     g = gpu_sim(pop, params, keep_lambda=check_lambda, state=state, seed_ids=seed_ids, max_steps=max(T, 1))
+    g2 = gpu_sim(pop, params, keep_lambda=False, state=state, seed_ids=seed_ids, max_steps=max(T, 1)) \
+        if check_lambda else None
     report = dict(days=0, flips=0, max_rel_lambda64=0.0, new_inf=[], messages=[])
     try:
         s0 = g.state()
@@ -48,6 +53,11 @@ def compare_days(pop, params, T, state=None, seed_ids="pop", check_lambda=True):
             d = osim.step(diag=True)
             g.step(1)
             s = g.state(with_lambda=check_lambda)
+            if g2 is not None:
+                g2.step(1)
+                s2 = g2.state()
+                for k in STATE_KEYS:
+                    assert np.array_equal(s2[k], s[k]), f"day {t}: {k} differs between the two launch configurations"
             if check_lambda:
                 lam_o = d["lambda32"]
                 bad = np.nonzero(s["lambda"].view(np.uint32) != lam_o.view(np.uint32))[0]
@@ -77,9 +87,14 @@ def compare_days(pop, params, T, state=None, seed_ids="pop", check_lambda=True):
         ni, h, m = g.counters(T)
         assert ni[:, 0].tolist() == report["new_inf"]
         assert m.astype(np.int64).tolist() == report["messages"]
+        if g2 is not None:
+            ni2, h2, m2 = g2.counters(T)
+            assert np.array_equal(ni2, ni) and np.array_equal(h2, h) and np.array_equal(m2, m)
         if params.get("den_on"):
             assert g.notified(T).tolist() == osim.den_notified[:T]
             report["notified"] = osim.den_notified[:T]
         return report
     finally:
         g.close()
+        if g2 is not None:
+            g2.close()
