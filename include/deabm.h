@@ -184,7 +184,8 @@ typedef struct {
     uint32_t locality_order; /* 1: number the agents internally so that the members of a group sit
                                 next to each other in device memory: agents grouped by the smallest
                                 id reaching them along the in-edges of the stored network with the
-                                most edges (8 rounds of min-label propagation on the device), groups
+                                most edges (up to 8 rounds of min-label propagation on the device,
+                                fewer once no label moves), groups
                                 in label order, ids ascending inside a group; results and every
                                 array the ABI returns are unchanged (random draws and outputs use
                                 the caller's agent ids) */
@@ -227,10 +228,13 @@ int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, con
 
 /* Create a ragged batch: n_pops independent populations of different sizes
  * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda, no
- * internal renumbering) simulated together, one kernel launch per day for all
- * of them: resident thread blocks take tiles of rows (never spanning two
- * populations) from a per-day work queue.  Population q's results equal those of
- * deabm_create on its own inputs with locality_order = 0.  State arrays are
+ * daily occupation networks, no exposure notification, no vaccination priority
+ * strategy: DEABM_EINVAL otherwise) simulated together, one
+ * kernel launch per day for all of them: resident thread blocks take tiles of
+ * rows (never spanning two populations) from a per-day work queue.  A population
+ * whose params ask for locality_order is numbered internally like a plain
+ * context (its random contacts reach rows through a caller id -> row map).
+ * Population q's results equal those of deabm_create on its own inputs.  State arrays are
  * concatenated in population order (sum of n_agents entries); per-day counters
  * are [day][population] (deabm_info's n_rep = n_pops).  deabm_run captures its T
  * days as one CUDA graph and replays it; a NULL stream here means a stream the
