@@ -323,7 +323,9 @@ def run_relaxed(args):
     cal_s = time.perf_counter() - t1
     loss1, _, _ = rx.grad(theta, y)
     rx.close()
+    cpu = None if args.no_cpu_baseline else cpu_baseline_relaxed(pop, w["params"], w["tau"], w["start"], y, w["T"])
     return {"workload": w["name"], "ms_per_gradient": ms_grad, "days": w["T"], "checkpoint_every": 10,
+            "cpu_baseline": cpu,
             "l2": "flushed before every timed gradient (write of twice its size)",
             "calibration": {"steps": args.calib_steps, "seconds": cal_s, "loss_start": float(trace[0]),
                             "loss_end": float(loss1), "theta_hidden": [float(x) for x in w["hidden"][:4]],
@@ -390,13 +392,21 @@ def run_surrogate(args):
         step_ms = timed(lambda: m.train_step(x, y, 1e-4))
         m.use_tcgen05(False)
         fwd_mma_ms = timed(lambda: m.forward(x, out))
+        params_now = m.get_params()
     m.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        with tempfile.TemporaryDirectory() as d:
+            pth = os.path.join(d, "params.npy")
+            np.save(pth, params_now.astype(np.float64))
+            cpu = cpu_baseline_mlp(sizes, pth, 16384)
     f = mlp_flops_per_sample(sizes)
     peak, kind = measured_peak_bf16()
     fwd_tf = f * B / (fwd_ms / 1e3) / 1e12
     train_tf = 3 * f * B / (step_ms / 1e3) / 1e12
     return {"workload": w["name"] + f", batch {B}", "forward_ms": fwd_ms, "train_step_ms": step_ms,
             "forward_ms_mma_sync_path": fwd_mma_ms, "samples_per_s": B / (fwd_ms / 1e3), "flops_per_sample_forward": f,
+            "cpu_baseline": cpu,
             "l2": "flushed before every timed call (write of twice its size)",
             "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
                          "peak_kind": kind,
@@ -450,7 +460,11 @@ def run_ragged(args):
               for p, par in zip(w["pops"], w["params"]))
     achieved = alg / (ms / T / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
+    cpu = None
+    if not args.no_cpu_baseline:  # the populations one after another, whole days, as the oracle stands
+        cpu = cpu_baseline(w["pops"], w["params"], args.cpu_seconds / 3, max_days=T + args.warmup)
     return {"workload": w["name"], "total_agents": int(sum(p["n"] for p in w["pops"])), "steps": T,
+            "cpu_baseline": cpu,
             "value": messages / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / T,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "kernel": "step_ragged_kernel", "alg_bytes_per_launch": alg,
@@ -491,12 +505,13 @@ def run_occupation(args):
 
     ms, msg = timed_days(pop)
     ms_ws, msg_ws = timed_days(dict(pop, occ_lattice=1, occ_rewire=0.1))
+    cpu = None if args.no_cpu_baseline else cpu_baseline(pop, w["params"], args.cpu_seconds / 3)
     alg = step_bytes_occ(n, static_edges, len(pop["row_ptr"]), int(pop["occ_k"].size), True)
     peak, _ = measured_peak_hbm()
     avg = ms / K
     achieved = alg / (avg / 1e3) / 1e9
     return {"workload": w["name"], "value": msg / (ms / 1e3), "unit": "interactions/s", "ms_per_step": avg,
-            "steps": K, "messages_per_day": msg / K,
+            "steps": K, "messages_per_day": msg / K, "cpu_baseline": cpu,
             "l2": f"inputs larger than L2: {alg / 1e6:.0f} MB algorithmic per day, no flush",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "kernel": "step_plain_kernel (daily occupation networks)", "alg_bytes_per_launch": alg,
@@ -535,7 +550,9 @@ def run_den(args):
     den = sim.notified()
     sim.close()
     msg = int(msgs[W0:W0 + K].astype(np.int64).sum())
+    cpu = None if args.no_cpu_baseline else cpu_baseline(pop, params, args.cpu_seconds / 3)
     return {"workload": "plain N=2e6 with exposure notification (adoption 0.3, compliance 0.8, 7-day look-back)",
+            "cpu_baseline": cpu,
             "value": msg / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / K, "steps": K,
             "days_timed": f"{W0}..{W0 + K - 1}", "notified_per_day": float(den[W0:W0 + K].mean()),
             "launches_per_day": 2}
@@ -603,23 +620,31 @@ def run_batched(args):
 
 
 # ---------------------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(pop, params, seconds: float):
-    """The oracle, as it stands (single-threaded C), on the same population: whole
-    days from day 0 until about `seconds` of CPU time."""
+def cpu_baseline(pops, params, seconds: float, max_days: int = 180):
+    """The oracle, as it stands (single-threaded C): whole days from day 0 of the
+    given population(s) -- one population, or a list taken in turn -- each run for
+    at most max_days (the workload's horizon), until about `seconds` of CPU time."""
     import oracle
-    sim = oracle.Sim(pop, params, pop["age"], pop["seed_ids"])
-    msgs, days = 0, 0
+    pops = pops if isinstance(pops, list) else [pops]
+    params = params if isinstance(params, list) else [params] * len(pops)
+    msgs, days, runs, el = 0, 0, 0, 0.0
     t0 = time.perf_counter()
-    while True:
-        d = sim.step(diag=False)
-        msgs += d["messages"]
-        days += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
+    while el < seconds:
+        q = runs % len(pops)
+        sim = oracle.Sim(pops[q], params[q], pops[q]["age"], pops[q]["seed_ids"])
+        runs += 1
+        for _ in range(max_days):
+            msgs += sim.step(diag=False)["messages"]
+            days += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    sizes = sorted({int(p["n"]) for p in pops[:runs]})
+    what = (f"the same N={pops[0]['n']} population" if len(pops) == 1
+            else f"{min(runs, len(pops))} of the {len(pops)} populations in turn (N {sizes[0]}..{sizes[-1]})")
     return {"value": msgs / el, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-            "sample": f"{days} whole days (days 0..{days - 1}) of the same N={pop['n']} population, "
-                      f"{el:.1f} s, single thread", "cpu": cpu_model()}
+            "sample": f"{days} whole days of {what}, from day 0, at most {max_days} days a run, {el:.1f} s, "
+                      "single thread", "cpu": cpu_model()}
 
 
 def cpu_baseline_columns(pop, base, rp, seeds, seconds: float):
@@ -647,6 +672,38 @@ def cpu_baseline_columns(pop, base, rp, seeds, seconds: float):
             "sample": f"{days} replicate-days over {cols} of the {len(seeds)} columns (from day 0), {el:.1f} s, "
                       "single thread; the columns are independent, so this per-column rate is the whole "
                       "batch's rate on one core (extrapolated, not run for all columns)", "cpu": cpu_model()}
+
+
+def cpu_baseline_relaxed(pop, params, tau, theta, target, T):
+    """The FP64 relaxed oracle (full history, reverse sweep) for one gradient of the
+    same workload, single thread."""
+    import oracle
+    rx = oracle.Relaxed(pop, params, pop["age"], pop["seed_ids"], tau=tau)
+    t0 = time.perf_counter()
+    rx.run(theta, T, target=np.asarray(target, np.float64), grad=True)
+    el = time.perf_counter() - t0
+    return {"value": el * 1e3, "unit": "ms per gradient", "cores": 1, "kind": "oracle",
+            "sample": f"one gradient (forward and reverse sweep in FP64, full history), N={pop['n']}, {T} days, "
+                      f"{el:.1f} s, single thread", "cpu": cpu_model()}
+
+
+def cpu_baseline_mlp(sizes, params, batch: int):
+    """The numpy MLP oracle (FP64 with the kernel's BF16 rounding points) on
+    `batch` samples, in a child process with single-threaded BLAS."""
+    code = ("import sys, time, json, numpy as np\n"
+            f"sys.path.insert(0, {ROOT!r})\n"
+            "from oracle import mlp\n"
+            f"sizes = {list(sizes)!r}\n"
+            f"params = np.load({params!r})\n"
+            f"x = np.random.default_rng(0).random(({batch}, sizes[0]))\n"
+            "t0 = time.perf_counter(); mlp.forward(params, sizes, x); el = time.perf_counter() - t0\n"
+            "print(json.dumps({'seconds': el}))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    el = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
+    return {"value": batch / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"forward of {batch} samples (FP64 with BF16 rounding points), {el:.2f} s, single-threaded BLAS",
+            "cpu": cpu_model()}
 
 
 def cpu_model():
