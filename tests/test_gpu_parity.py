@@ -128,6 +128,29 @@ def test_full_size_bench_configuration_60_days():
     assert h_o[-1, 0] < 0.8 * w["n"]  # the skip path carried most agents
 
 
+def test_more_than_2_pow_24_agents():
+    """N = 2^24 + 3 agents (households only): the internal numbering's radix sort
+    takes four 8-bit passes and row indices pass 2^24.  Three days' counters and
+    the final state equal the oracle's."""
+    n = (1 << 24) + 3
+    pop = W.population(n, 5, 200_000)
+    g = dict(pop, row_ptr=pop["row_ptr"][:1], col=pop["col"][:1])
+    p = W.params_with(B_net=[1.0], R=4.0, test_on=1, quar_on=1, seed=3, net_seed=4)
+    T = 3
+    sim = gpu_sim(g, p, keep_lambda=False, max_steps=T)
+    ni, h = sim.run(T)
+    _, _, m = sim.counters(T)
+    s = sim.state()
+    sim.close()
+    o = oracle_sim(g, p)
+    ni_o, h_o, m_o = o.run(T)
+    assert np.array_equal(ni[:, 0], ni_o) and np.array_equal(h[:, 0], h_o)
+    assert np.array_equal(m.astype(np.int64), m_o)
+    for k in ("stage", "timer", "tinf", "flags", "qt"):
+        assert np.array_equal(s[k], getattr(o.state, k)), k
+    assert ni_o.sum() > 1000
+
+
 @pytest.mark.parametrize("B", [37, 36, 132])
 def test_batched_columns_equal_plain_runs_and_oracle(B):
     """B = 37 runs the one-replicate-per-thread panel kernel; B = 36 and 132 (a
