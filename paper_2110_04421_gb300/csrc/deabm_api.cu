@@ -22,7 +22,11 @@ struct deabm_ctx {
     uint32_t n = 0, n_nets = 0, n_rep = 1, max_steps = 0, day = 0;
     uint64_t static_edges = 0;
     bool keep_lambda = false;
-    std::vector<void *> allocs;
+    std::vector<void *> allocs;               // device blocks owned by the context (freed at destroy)
+    // the context's arrays are carved out of a few large device blocks (one
+    // cudaMalloc and one cudaFree each instead of one per array)
+    char *arena = nullptr;
+    size_t arena_used = 0, arena_size = 0, arena_chunk = 0;
     uint32_t *row_ptr[DEABM_MAX_NETS] = {};
     uint32_t *col[DEABM_MAX_NETS] = {};
     uint8_t *age = nullptr;
@@ -99,16 +103,38 @@ static int fail(deabm_ctx *ctx, int code, const char *fmt, ...)
 template <class T>
 static int dalloc(deabm_ctx *ctx, T **out, size_t count)
 {
-    void *ptr = nullptr;
     const size_t bytes = count ? count * sizeof(T) : sizeof(T);
-    cudaError_t e = cudaMalloc(&ptr, bytes);
+    const size_t rounded = (bytes + 255u) & ~(size_t)255u;  // every array 256-byte aligned
+    const size_t chunk = ctx->arena_chunk ? ctx->arena_chunk : (size_t)1 << 20;
+    const bool own_block = rounded > chunk / 4;  // large arrays get a block of their own
+    if (!own_block && ctx->arena && ctx->arena_used + rounded <= ctx->arena_size) {
+        *out = (T *)(ctx->arena + ctx->arena_used);
+        ctx->arena_used += rounded;
+        return DEABM_OK;
+    }
+    void *ptr = nullptr;
+    const size_t block = own_block ? rounded : chunk;
+    cudaError_t e = cudaMalloc(&ptr, block);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", block, cudaGetErrorString(e));
     }
     ctx->allocs.push_back(ptr);
+    if (!own_block) {
+        ctx->arena = (char *)ptr;
+        ctx->arena_size = block;
+        ctx->arena_used = rounded;
+    }
     *out = (T *)ptr;
     return DEABM_OK;
+}
+
+// Block size for the context's small arrays: about what a context of n agents x
+// n_rep replicates keeps, between 1 MB and 256 MB.
+static void arena_plan(deabm_ctx *ctx, uint64_t n, uint64_t n_rep)
+{
+    const uint64_t want = n * n_rep * 32u + n * 16u;
+    ctx->arena_chunk = (size_t)std::min<uint64_t>(std::max<uint64_t>(want, 1u << 20), 256ull << 20);
 }
 
 static uint64_t threshold(double p)
@@ -426,6 +452,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             const uint32_t n = g->n_agents;
             const size_t nb = (size_t)n * n_rep;
             ctx->n = n;
+            arena_plan(ctx, n, n_rep);
             ctx->n_nets = g->n_nets;
             ctx->n_rep = n_rep;
             ctx->max_steps = p->max_steps ? p->max_steps : 1024u;
@@ -1033,6 +1060,7 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         if (total >= (1ull << 31)) return fail(ctx, DEABM_EINVAL, "too many agents in total");
         ctx->ragged = true;
         ctx->n = (uint32_t)total;
+        arena_plan(ctx, total, 1);
         ctx->n_rep = n_pops;  // counters are [day][population]
         ctx->max_steps = max_steps;
         ctx->base = params[0];
