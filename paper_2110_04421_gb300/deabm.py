@@ -323,7 +323,7 @@ class RaggedSimulation:
     parameters) stepped together by one persistent kernel per day; ``run`` replays
     a captured CUDA graph of the days."""
 
-    def __init__(self, pops: list, params: list, max_steps: int = 1024, stream=None):
+    def __init__(self, pops: list, params: list, max_steps: int = 1024, stream=None, locality_order: bool = True):
         L = lib()
         keep = []
         n = len(pops)
@@ -340,7 +340,7 @@ class RaggedSimulation:
             if ids.size:
                 ag[q].seed_ids = ids.ctypes.data
                 ag[q].n_seed = ids.size
-            ps[q] = make_params(par, max_steps=max_steps, locality_order=False)
+            ps[q] = make_params(par, max_steps=max_steps, locality_order=locality_order)
         self.sizes = [int(p["n"]) for p in pops]
         self.n_pops = n
         self.n = sum(self.sizes)

@@ -49,12 +49,15 @@ def check(ragged_out, singles):
             assert np.array_equal(states[q][k], st1[k]), (q, k)
 
 
-def test_each_population_matches_its_own_run():
+@pytest.mark.parametrize("locality", [True, False])
+def test_each_population_matches_its_own_run(locality):
+    """locality: each population numbered internally for locality (its random
+    contacts through a caller id -> row map) or kept in caller order."""
     from paper_2110_04421_gb300.deabm import RaggedSimulation
     pops, params = case()
     T = 35
     singles = single_runs(pops, params, T)
-    r = RaggedSimulation(pops, params, max_steps=T)
+    r = RaggedSimulation(pops, params, max_steps=T, locality_order=locality)
     ni, h = r.run(T)
     check((ni, h, r.state()), singles)
     r.reset()
