@@ -88,7 +88,10 @@ __device__ __forceinline__ bool den_ring_eval(const KParams &P, uint32_t a, uint
     return hit;
 }
 
-__global__ void __launch_bounds__(256) den_kernel(const KParams P, uint32_t day, StateRef S, Counters C)
+// 8 blocks per SM (32 registers, some spilled): the pass waits on dependent loads,
+// so more resident warps beat fewer spills (day with the pass, N = 2e6: 0.202 ms
+// at 48 registers, 0.193 at 6 blocks, 0.190 at 8)
+__global__ void __launch_bounds__(256, 8) den_kernel(const KParams P, uint32_t day, StateRef S, Counters C)
 {
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
