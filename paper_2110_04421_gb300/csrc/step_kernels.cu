@@ -269,7 +269,9 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
 // left, so populations of 10^4 and 10^6 agents share the GPU without one
 // launch each.  Every row runs the plain day on its population's local ids,
 // giving exactly the single-population result.
-__global__ void __launch_bounds__(256) step_ragged_kernel(const PopDesc *__restrict__ pops, const Tile *__restrict__ tiles,
+// 6 blocks per SM asked (swept at 64 populations, autotuned tiling: no minimum
+// 0.533 ms a day at 64 registers, 6 blocks 0.472, 8 blocks 0.480)
+__global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__restrict__ pops, const Tile *__restrict__ tiles,
                                                           uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                                           const float *inf_cur, float *inf_next, StateRef S,
                                                           Counters C, uint32_t n_pops)
@@ -358,8 +360,9 @@ __device__ __forceinline__ void add4(float4 &h, const float4 v)
 
 template <bool KEEP>
 #ifndef DEABM_B4_MINB
-#define DEABM_B4_MINB 4  // resident blocks per SM asked of the four-replicate kernel: 64 registers
-                         // (swept: 1 -> 105 registers, 38 % slower; 5, 6 -> spills, 8-12 % slower)
+#define DEABM_B4_MINB 6  // resident blocks per SM asked of the four-replicate kernel: 40 registers with
+                         // some spilled (swept at N = 1e5, B = 256: 1 block 105 registers, 38 % slower;
+                         // 3 0.634 ms, 4 0.544, 5 0.517, 6 0.512, 7 and 8 0.700 a day)
 #endif
 __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                           Counters C, float *lam_out, float *p_out)
