@@ -195,23 +195,21 @@ static uint32_t host_threads(uint32_t n)
     return n < (1u << 16) ? 1u : std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
 }
 
-static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a, const deabm_params *p,
-                    uint32_t n_rep, const float *rep_params)
+// Every per-row check of create's inputs runs in one pass over the rows on host
+// threads (each thread a contiguous range), recording per thread the first bad
+// row of each check; validate() then reports errors in a fixed order.  A row's
+// edges are read only when rp[q] <= rp[q+1] <= rp[n], i.e. inside col; NULL
+// arrays are skipped (validate reports them).  Needs g, a non-NULL and
+// 0 < n_agents < 2^31, n_nets <= DEABM_MAX_NETS.
+struct RowFirsts {
+    uint32_t dec[DEABM_MAX_NETS], col[DEABM_MAX_NETS], occ, age, stage, qt;
+};
+
+static std::vector<RowFirsts> scan_rows(const deabm_graph *g, const deabm_agents *a)
 {
-    if (!g || !a || !p) return fail(ctx, DEABM_EINVAL, "graph, agents and params are required");
     const uint32_t n = g->n_agents;
-    if (n == 0 || n >= (1u << 31)) return fail(ctx, DEABM_EINVAL, "n_agents must be in [1, 2^31)");
-    if (g->n_nets > DEABM_MAX_NETS) return fail(ctx, DEABM_EINVAL, "n_nets > %d", DEABM_MAX_NETS);
-    if (!(g->rand_mean >= 0.0f) || g->rand_mean > 1e3f) return fail(ctx, DEABM_EINVAL, "rand_mean out of range");
-    if (g->rand_mean > 0.0f && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
-    if ((uint64_t)n * n_rep >= (1ull << 40)) return fail(ctx, DEABM_EINVAL, "n_agents * n_rep too large");
-    // Every per-row check runs in one pass over the rows on host threads (each
-    // thread a contiguous range); errors are then reported in a fixed order.  A
-    // row's edges are read only when rp[q] <= rp[q+1] <= rp[n], i.e. inside col.
     const bool occ_arrays = g->n_occ && g->n_occ < (1u << 31) && g->occ_group && g->occ_k;
-    struct Firsts {
-        uint32_t dec[DEABM_MAX_NETS], col[DEABM_MAX_NETS], occ, age, stage, qt;
-    };
+    using Firsts = RowFirsts;
     const uint32_t T = host_threads(n);
     std::vector<Firsts> found(T);
     parallel_chunks(n, T, [&](uint32_t b, uint32_t e, uint32_t t) {
@@ -243,6 +241,24 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         }
         found[t] = f;
     });
+    return found;
+}
+
+// Host validation of create's inputs, before they are used: DEABM_OK or the
+// first error in a fixed order.  scanned: the rows already scanned by scan_rows
+// (create runs the scan on its own thread while the CSR goes up), else scanned here.
+static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a, const deabm_params *p,
+                    uint32_t n_rep, const float *rep_params, const std::vector<RowFirsts> *scanned = nullptr)
+{
+    if (!g || !a || !p) return fail(ctx, DEABM_EINVAL, "graph, agents and params are required");
+    const uint32_t n = g->n_agents;
+    if (n == 0 || n >= (1u << 31)) return fail(ctx, DEABM_EINVAL, "n_agents must be in [1, 2^31)");
+    if (g->n_nets > DEABM_MAX_NETS) return fail(ctx, DEABM_EINVAL, "n_nets > %d", DEABM_MAX_NETS);
+    if (!(g->rand_mean >= 0.0f) || g->rand_mean > 1e3f) return fail(ctx, DEABM_EINVAL, "rand_mean out of range");
+    if (g->rand_mean > 0.0f && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
+    if ((uint64_t)n * n_rep >= (1ull << 40)) return fail(ctx, DEABM_EINVAL, "n_agents * n_rep too large");
+    using Firsts = RowFirsts;
+    const std::vector<Firsts> found = scanned ? *scanned : scan_rows(g, a);
     auto first = [&](uint32_t Firsts::*m) {
         uint32_t v = n;
         for (const Firsts &f : found) v = std::min(v, f.*m);
@@ -445,7 +461,27 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
     *out = nullptr;
     deabm_ctx *ctx = new (std::nothrow) deabm_ctx();
     if (!ctx) return fail(nullptr, DEABM_ENOMEM, "host allocation failed");
-    int rc = validate(ctx, g, a, p, n_rep, rep_params);
+    // The row scan of the inputs (most of validation) runs on its own host thread
+    // while the stored networks go up to the device; the scan is reported before
+    // anything reads the inputs on the host or the device.  Inputs too broken to
+    // size the uploads are validated first, in full.
+    bool overlap = g && a && p && g->n_agents > 0 && g->n_agents < (1u << 31) && g->n_nets <= DEABM_MAX_NETS;
+    for (uint32_t k = 0; overlap && k < g->n_nets; ++k)
+        overlap = g->row_ptr[k] && (g->col[k] || g->row_ptr[k][g->n_agents] == 0);
+    std::vector<RowFirsts> scanned;
+    struct Joined {
+        std::thread t;
+        ~Joined()
+        {
+            if (t.joinable()) t.join();
+        }
+    } scan;
+    if (overlap) scan.t = std::thread([&] { scanned = scan_rows(g, a); });
+    auto validated = [&]() -> int {
+        if (scan.t.joinable()) scan.t.join();
+        return validate(ctx, g, a, p, n_rep, rep_params, &scanned);
+    };
+    int rc = overlap ? DEABM_OK : validate(ctx, g, a, p, n_rep, rep_params);
     if (rc == DEABM_OK) {
         rc = [&]() -> int {
             ctx->stream = (cudaStream_t)stream;
@@ -481,6 +517,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                                         cudaMemcpyHostToDevice, s));
                 if (E) CU(ctx, cudaMemcpyAsync(src_col[k], g->col[k], sizeof(uint32_t) * E, cudaMemcpyHostToDevice, s));
             }
+            if (overlap && (r = validated())) return r;  // the uploads above read nothing else
             std::vector<uint32_t> occ_start;
             uint32_t *d_o2n = nullptr;
             if (ctx->relabel) {
@@ -751,6 +788,12 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaStreamSynchronize(s));
             return DEABM_OK;
         }();
+        // a failure during the uploads, before the scan was reported: an invalid
+        // input is the error to report
+        if (rc != DEABM_OK && scan.t.joinable()) {
+            const int v = validated();
+            if (v != DEABM_OK) rc = v;
+        }
     }
     if (rc != DEABM_OK) {
         std::string msg = ctx->err;
