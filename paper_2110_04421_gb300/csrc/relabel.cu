@@ -136,15 +136,39 @@ size_t scan_scratch_words(size_t m)
     return words + 2;
 }
 
-// one warp per new row: its edges in the caller's order, sources renumbered
+// One warp per 32 consecutive new rows: their edges form one contiguous output
+// range, which the lanes fill 32 positions at a time (coalesced writes, no idle
+// lanes on short rows).  Position p belongs to the last of the 32 rows whose
+// output start is <= p (a binary search over the lanes' starts); each row keeps
+// its edges in the caller's order, sources renumbered.
 __global__ void csr_copy_kernel(const uint32_t *__restrict__ rp, const uint32_t *__restrict__ col,
                                 const uint32_t *__restrict__ new2orig, const uint32_t *__restrict__ orig2new,
                                 const uint32_t *__restrict__ rp_new, uint32_t n, uint32_t *__restrict__ col_new)
 {
-    const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31u;
-    if (q >= n) return;
-    const uint32_t o = new2orig[q], b0 = rp[o], len = rp[o + 1] - b0, d0 = rp_new[q];
-    for (uint32_t i = lane; i < len; i += 32u) col_new[d0 + i] = orig2new[col[b0 + i]];
+    const unsigned full = 0xFFFFFFFFu;
+    const uint32_t q0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u, lane = threadIdx.x & 31u;
+    if (q0 >= n) return;  // whole warps leave together
+    const uint32_t q = q0 + lane, last = min(31u, n - 1u - q0);
+    uint32_t d0 = 0, len = 0, b0 = 0;
+    if (q < n) {
+        const uint32_t o = new2orig[q];
+        b0 = rp[o];
+        len = rp[o + 1] - b0;
+        d0 = rp_new[q];
+    }
+    const uint32_t beg = __shfl_sync(full, d0, 0), end = __shfl_sync(full, d0 + len, last);
+    for (uint32_t base = beg; base < end; base += 32u) {
+        const uint32_t p = base + lane;
+        uint32_t r = 0;
+#pragma unroll
+        for (uint32_t s = 16; s >= 1u; s >>= 1) {
+            const uint32_t c = r + s;
+            const uint32_t dc = __shfl_sync(full, d0, c);
+            if (c <= last && dc <= p) r = c;
+        }
+        const uint32_t dr = __shfl_sync(full, d0, r), br = __shfl_sync(full, b0, r);
+        if (p < end) col_new[p] = orig2new[col[br + (p - dr)]];
+    }
 }
 
 cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const uint32_t *new2orig,
@@ -154,7 +178,7 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
     csr_degree_kernel<<<(n + 256u) / 256u, 256, 0, stream>>>(rp, new2orig, n, rp_new);
     cudaError_t e = scan_inplace(rp_new, (size_t)n + 1, scratch, stream);
     if (e != cudaSuccess) return e;
-    const uint64_t threads = (uint64_t)n * 32u;
+    const uint64_t threads = ((uint64_t)n + 31u) / 32u * 32u;  // one warp per 32 rows
     csr_copy_kernel<<<(unsigned)((threads + 255u) / 256u), 256, 0, stream>>>(rp, col, new2orig, orig2new, rp_new, n,
                                                                              col_new);
     return cudaGetLastError();
