@@ -317,18 +317,22 @@ int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t *timer, con
  * layout as deabm_graph but its row_ptr / col arrays are DEVICE pointers, and so
  * are age_bin, stage, tinf, qt (n_agents entries each, caller numbering, the
  * state at the start of `day`) and the output lambda (float[n_agents]).  The
- * CSR is not validated (the rules of deabm_create apply; invalid indices are
- * the caller's error); graph_dev->n_occ must be 0 (daily occupation networks
- * need a context, DEABM_EINVAL otherwise).  lambda_j equals what deabm_step computes for that day
+ * device arrays cannot be checked on the host: the CSR rules of deabm_create
+ * apply and invalid indices are the caller's error; a stage code outside 0..10
+ * emits nothing; an age_bin outside 0..8 gives lambda = NaN for that agent (no
+ * read outside the parameter block).  graph_dev->n_occ must be 0 (daily
+ * occupation networks need a context, DEABM_EINVAL otherwise).  lambda_j equals what deabm_step computes for that day
  * and state (Eq. 1 summed over the static networks and the day's random network,
  * with params' R, inv_Ibar, B_net, B_rand, S_age, A_class, infectiousness curve
  * and net_seed).
  * Working memory: a fixed array compiled into the library (4 MiB + 4 KiB on every
  * GPU that loads it, held until the process exits).  At most
  * DEABM_NOALLOC_MAX_AGENTS agents; larger populations get DEABM_EINVAL before
- * any GPU work.  No cudaMalloc, cudaFree or other allocating call is made.  The
- * first call on each device looks up the array's device address on that device
- * (with that device current); make that first call before any stream capture.
+ * any GPU work.  No cudaMalloc, cudaFree or other allocating call is made.  Every
+ * call looks up the array's device address on the current device (where the
+ * caller's buffers must live); the first lookup on a device may load the
+ * library's device code there, so make the first call on each device before any
+ * stream capture.
  * All calls share the array and it keeps the last call's contents; calls whose
  * GPU work overlaps (other streams or threads) race, so serialise them.  Work is
  * queued on cuda_stream and the call returns without waiting.  Errors:

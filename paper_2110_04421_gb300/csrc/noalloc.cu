@@ -18,16 +18,15 @@
 // start at zero.
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "day_common.cuh"
 #include "deabm.h"
 #include "deabm_device.cuh"
+#include "gamma_day.cuh"
 
 namespace deabm {
 
@@ -44,53 +43,12 @@ struct NoAllocTableArgs {
     uint64_t pois[DEABM_POIS_CAP];
 };
 
-// same integrals as the context path's table (FP64 incomplete gamma, rounded once)
-__device__ double na_gamma_p(double s, double x)
-{
-    if (x <= 0.0) return 0.0;
-    double ap = s, del = 1.0 / s, sum = del;
-    for (int n = 0; n < 2000; ++n) {
-        ap += 1.0;
-        del *= x / ap;
-        sum += del;
-        if (fabs(del) < fabs(sum) * 1e-17) break;
-    }
-    return sum * exp(-x + s * log(x) - lgamma(s));
-}
-
-__device__ double na_gamma_q(double s, double x)
-{
-    const double tiny = 1e-300;
-    double b = x + 1.0 - s, c = 1.0 / tiny, d = 1.0 / b, h = d;
-    for (int i = 1; i < 2000; ++i) {
-        const double an = -(double)i * ((double)i - s);
-        b += 2.0;
-        d = an * d + b;
-        if (fabs(d) < tiny) d = tiny;
-        c = b + an / c;
-        if (fabs(c) < tiny) c = tiny;
-        d = 1.0 / d;
-        const double del = d * c;
-        h *= del;
-        if (fabs(del - 1.0) < 1e-17) break;
-    }
-    return exp(-x + s * log(x) - lgamma(s)) * h;
-}
-
-__device__ double na_gamma_day(double shape, double scale, uint32_t t)
-{
-    const double a = ((double)t - 1.0) / scale, b = (double)t / scale, edge = shape + 1.0;
-    if (b <= edge) return na_gamma_p(shape, b) - na_gamma_p(shape, a);
-    if (a >= edge) return na_gamma_q(shape, a) - na_gamma_q(shape, b);
-    return (1.0 - na_gamma_q(shape, b)) - na_gamma_p(shape, a);
-}
-
 // one block: rebuild the tables in the fixed array
 __global__ void na_tables_kernel(Tables *tab, const NoAllocTableArgs a)
 {
     const uint32_t c = threadIdx.y, t = threadIdx.x;  // 64 x 3 threads
     float v = 0.0f;
-    if (t >= 1 && t < a.len) v = __fmul_rn(a.A[c], (float)na_gamma_day(a.shape[c], a.scale[c], t));
+    if (t >= 1 && t < a.len) v = __fmul_rn(a.A[c], (float)gamma_day(a.shape[c], a.scale[c], t));
     tab->infT[c][t] = v;
     if (c == 0 && t < DEABM_POIS_CAP) tab->pois[t] = a.pois[t];
 }
@@ -113,7 +71,10 @@ __global__ void __launch_bounds__(256) na_lambda_kernel(const KParams P, const R
     I.rand_next = nullptr;
     I.row_of = nullptr;
     uint32_t k;
-    lambda[j] = lambda_of<false>(P, rp, I, j, j, day, 1u, 0u, __ldg(P.age + j), &k);
+    // the caller's age codes are not checked on the host (device memory): an
+    // age bin outside 0..8 gives NaN instead of a read past S_age
+    const uint32_t age = __ldg(P.age + j);
+    lambda[j] = age < DEABM_N_AGE ? lambda_of<false>(P, rp, I, j, j, day, 1u, 0u, (int)age, &k) : __int_as_float(0x7FC00000);
 }
 
 }  // namespace deabm
@@ -121,9 +82,6 @@ __global__ void __launch_bounds__(256) na_lambda_kernel(const KParams P, const R
 using namespace deabm;
 
 static thread_local std::string g_na_err;
-static std::mutex g_na_mutex;
-static void *g_na_ptr[64];  // symbol address of the fixed array, per device
-
 static int na_fail(int code, const char *fmt, ...)
 {
     char buf[512];
@@ -167,23 +125,14 @@ extern "C" int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t 
     if (!(graph_dev->rand_mean >= 0.0f) || (graph_dev->rand_mean > 0.0f && n < 2))
         return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: bad rand_mean for %u agents", n);
 
-    // set-up, once per device: the device address of the fixed array
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return na_fail(DEABM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= 64) return na_fail(DEABM_ECUDA, "device ordinal %d out of range", dev);
+    // the device address of the fixed array on the current device, looked up on
+    // every call (no allocation; valid after a device reset too).  The first
+    // lookup on a device may load the library's device code there, so the first
+    // call on each device belongs before any stream capture.
     void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[dev]) {
-            e = cudaGetSymbolAddress(&g_na_ptr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_na_ptr[dev] = nullptr;
-                return na_fail(DEABM_ECUDA, "cudaGetSymbolAddress of the working array: %s", cudaGetErrorString(e));
-            }
-        }
-        base = g_na_ptr[dev];
-    }
+    cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess || !base)
+        return na_fail(DEABM_ECUDA, "cudaGetSymbolAddress of the working array: %s", cudaGetErrorString(e));
     Tables *tab = (Tables *)base;
     float *inf = (float *)((unsigned char *)base + kTablesBytes);
     cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -647,10 +647,55 @@ class MLP:
             pass
 
 
+def _check_noalloc_args(graph_dev: dict, arrays: dict, out):
+    """Everything deabm_lambda_noalloc cannot check itself (its arrays are device
+    memory): each tensor's dtype, that it is a contiguous CUDA tensor on one common
+    device, and that it holds the entries the call reads or writes.  Raises
+    ValueError; returns the common device."""
+    import torch
+    n = int(graph_dev["n"])
+    rps, cols = list(graph_dev["row_ptr"]), list(graph_dev["col"])
+    if len(rps) != len(cols) or len(rps) > 4:
+        raise ValueError("graph_dev needs as many row_ptr as col tensors, at most 4")
+    if n > NOALLOC_MAX_AGENTS:
+        return None  # the library rejects the size itself, before touching any array
+    idx = (torch.int32, torch.uint32) if hasattr(torch, "uint32") else (torch.int32,)
+    want = {"age": ((torch.uint8,), n), "stage": ((torch.int8,), n), "tinf": ((torch.int16,), n),
+            "qt": ((torch.uint8,), n), "out": ((torch.float32,), n)}
+    items = dict(arrays, out=out)
+    for k, (rp, cl) in enumerate(zip(rps, cols)):
+        items[f"row_ptr[{k}]"], want[f"row_ptr[{k}]"] = rp, (idx, n + 1)
+        items[f"col[{k}]"], want[f"col[{k}]"] = cl, (idx, 0)
+    device = None
+    for name, t in items.items():
+        dtypes, count = want[name]
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} has dtype {t.dtype}, expected {' or '.join(str(d) for d in dtypes)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < count:
+            raise ValueError(f"{name} has {t.numel()} entries, the call needs {count}")
+    for name, t in items.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if device is None:
+            device = t.device
+        elif t.device != device:
+            raise ValueError(f"{name} is on {t.device}, the other arrays on {device}")
+    return device
+
+
 def lambda_noalloc(graph_dev: dict, age, stage, tinf, qt, params: dict, day: int, out, stream=None):
     """Infection rates of one day through deabm_lambda_noalloc, which allocates
-    nothing: every argument is a caller-owned torch CUDA tensor (graph_dev holds
-    ``n``, ``row_ptr`` and ``col`` tensors of dtype int32/uint32 on the device)."""
+    nothing: every argument is a caller-owned torch CUDA tensor on one device
+    (graph_dev holds ``n``, ``row_ptr`` and ``col`` tensors of dtype int32/uint32;
+    age and qt uint8, stage int8, tinf int16, out float32, n entries each;
+    row_ptr n + 1; the column arrays as long as the row pointers say, which the
+    library does not check).  The tensors' device is made current for the call."""
+    import torch
+    device = _check_noalloc_args(graph_dev, {"age": age, "stage": stage, "tinf": tinf, "qt": qt}, out)
     g = Graph()
     g.n_agents = int(graph_dev["n"])
     g.n_nets = len(graph_dev["row_ptr"])
@@ -659,10 +704,11 @@ def lambda_noalloc(graph_dev: dict, age, stage, tinf, qt, params: dict, day: int
         g.col[i] = cl.data_ptr()
     g.rand_mean = params["rand_mean"]
     p = make_params(params)
-    st = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
-    rc = lib().deabm_lambda_noalloc(C.byref(g), C.c_void_p(age.data_ptr()), C.c_void_p(stage.data_ptr()),
-                                    C.c_void_p(tinf.data_ptr()), C.c_void_p(qt.data_ptr()), C.byref(p), day,
-                                    C.c_void_p(out.data_ptr()), st)
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        st = C.c_void_p(stream) if isinstance(stream, int) else (stream or _current_stream())
+        rc = lib().deabm_lambda_noalloc(C.byref(g), C.c_void_p(age.data_ptr()), C.c_void_p(stage.data_ptr()),
+                                        C.c_void_p(tinf.data_ptr()), C.c_void_p(qt.data_ptr()), C.byref(p), day,
+                                        C.c_void_p(out.data_ptr()), st)
     if rc != OK:
         raise DeabmError(rc, lib().deabm_lambda_noalloc_last_error().decode(errors="replace"))
     return out

@@ -196,3 +196,53 @@ def test_binding_passes_daily_occupations(lib):
     pop["occ_group"][7] = pop["occ_k"].size
     with pytest.raises(DeabmError, match="occ_group"):
         Simulation(pop, W.params_with(), pop["age"], pop["seed_ids"])
+
+
+def test_noalloc_wrapper_rejects_bad_tensors_before_the_call(lib):
+    """lambda_noalloc's arrays are device memory the library cannot inspect, so the
+    binding checks dtype, contiguity, length and device first: a wrong dtype or a
+    short output is a ValueError and the C entry point is never reached."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import lambda_noalloc
+    n = 50
+    g = dict(n=n, row_ptr=[torch.zeros(n + 1, dtype=torch.int32)], col=[torch.zeros(4, dtype=torch.int32)])
+    ok = dict(age=torch.zeros(n, dtype=torch.uint8), stage=torch.zeros(n, dtype=torch.int8),
+              tinf=torch.zeros(n, dtype=torch.int16), qt=torch.zeros(n, dtype=torch.uint8))
+    out = torch.zeros(n, dtype=torch.float32)
+    p = W.params_with()
+
+    def call(graph=g, out=out, **kw):
+        a = dict(ok, **kw)
+        return lambda_noalloc(graph, a["age"], a["stage"], a["tinf"], a["qt"], p, 0, out)
+
+    with pytest.raises(ValueError, match="age has dtype torch.int64"):
+        call(age=torch.zeros(n, dtype=torch.int64))
+    with pytest.raises(ValueError, match="tinf has dtype"):
+        call(tinf=torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(ValueError, match="out has 49 entries, the call needs 50"):
+        call(out=torch.zeros(n - 1, dtype=torch.float32))
+    with pytest.raises(ValueError, match=r"row_ptr\[0\] has 50 entries, the call needs 51"):
+        call(graph=dict(g, row_ptr=[torch.zeros(n, dtype=torch.int32)]))
+    with pytest.raises(ValueError, match="col.0. has dtype torch.int64"):
+        call(graph=dict(g, col=[torch.zeros(4, dtype=torch.int64)]))
+    with pytest.raises(ValueError, match="stage must be contiguous"):
+        call(stage=torch.zeros(2 * n, dtype=torch.int8)[::2])
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        call()  # every check but the device passes on host tensors
+
+
+def test_noalloc_rejects_oversized_population_before_any_gpu_work(lib):
+    """The C entry point refuses more agents than its fixed array holds during its
+    host checks, before it looks at the (here dummy) device pointers."""
+    from paper_2110_04421_gb300.deabm import NOALLOC_MAX_AGENTS, Graph, make_params
+    from paper_2110_04421_gb300 import workloads as W
+    g = Graph()
+    g.n_agents = NOALLOC_MAX_AGENTS + 1
+    g.n_nets = 0
+    g.rand_mean = 2.0
+    p = make_params(W.params_with())
+    dummy = C.c_void_p(16)
+    rc = lib.deabm_lambda_noalloc(C.byref(g), dummy, dummy, dummy, dummy, C.byref(p), 0, dummy, None)
+    assert rc == -1
+    assert b"exceed the fixed working array" in lib.deabm_lambda_noalloc_last_error()

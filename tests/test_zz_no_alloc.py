@@ -68,3 +68,32 @@ def test_no_alloc_rejects_populations_beyond_its_array():
     g = dict(n=n, row_ptr=[t], col=[t])
     with pytest.raises(DeabmError, match="exceed the fixed working array"):
         lambda_noalloc(g, t, t, t, t, W.params_with(), 0, t)
+
+
+def test_no_alloc_tables_follow_non_default_infectiousness_curves():
+    """Both table builders share one FP64 integral: with other gamma shapes and
+    scales per class and a shorter curve, the rates still equal the context
+    path's bit for bit; an age code outside 0..8 gives NaN for that agent only."""
+    import torch
+    from paper_2110_04421_gb300.deabm import lambda_noalloc
+    pop = W.population(9_001, 11, 40)
+    params = W.params_with(R=4.0, seed=8, net_seed=9, inf_shape=[2.5, 3.0, 6.2], inf_scale=[1.7, 0.9, 0.75],
+                           inf_len=17, A_class=[0.3, 1.0, 1.6])
+    ref = context_lambdas(pop, params, days=(5,))
+    dev = torch.device("cuda")
+    gdev = dict(n=pop["n"], row_ptr=[torch.tensor(r.astype(np.int32), device=dev) for r in pop["row_ptr"]],
+                col=[torch.tensor(c.astype(np.int32), device=dev) for c in pop["col"]])
+    st, lam_ref = ref[5]
+    age = pop["age"].copy()
+    bad = np.array([3, 4000, 9000])
+    age[bad] = np.array([9, 200, 255], np.uint8)
+    out = torch.full((pop["n"],), -1.0, device=dev)
+    lambda_noalloc(gdev, torch.tensor(age, device=dev), torch.tensor(st["stage"], device=dev),
+                   torch.tensor(st["tinf"], device=dev), torch.tensor(st["qt"], device=dev), params, 5, out)
+    torch.cuda.synchronize()
+    lam = out.cpu().numpy()
+    assert np.isnan(lam[bad]).all()
+    keep = np.ones(pop["n"], bool)
+    keep[bad] = False
+    assert lam_ref[keep].max() > 0
+    assert np.array_equal(lam[keep].view(np.uint32), lam_ref[keep].view(np.uint32))
