@@ -449,6 +449,15 @@ int deabm_mlp_grad(deabm_mlp *mlp, const float *x, const float *y, uint32_t batc
 /* deabm_mlp_grad, then one Adam step (beta 0.9 / 0.999, eps 1e-8) with rate lr.
  * loss (host, may be NULL: no synchronisation) is the loss before the step. */
 int deabm_mlp_train_step(deabm_mlp *mlp, const float *x, const float *y, uint32_t batch, float lr, float *loss);
+/* One Adam step (Kingma and Ba, Algorithm 1: beta 0.9 / 0.999, eps 1e-8, the
+ * context's own moments and step count) with rate lr on gradients the caller
+ * supplies, e.g. gradients summed over data-parallel ranks.  grads: FP32 in the
+ * deabm_mlp_get_params layout (per layer W [fan_in x fan_out] row-major, then b);
+ * a device pointer when on_device != 0 (queued, asynchronous), else a host
+ * pointer (copied, then the call waits for the step).  deabm_mlp_train_step is
+ * deabm_mlp_grad followed by this step.  Returns DEABM_OK, DEABM_EINVAL (NULL,
+ * lr not finite and > 0), DEABM_ECUDA. */
+int deabm_mlp_apply_grads(deabm_mlp *mlp, const float *grads, uint32_t on_device, float lr);
 /* Wait for the MLP's queued work; DEABM_ETIMEOUT if a bounded device wait gave up. */
 int deabm_mlp_sync(deabm_mlp *mlp);
 const char *deabm_mlp_last_error(void);

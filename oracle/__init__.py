@@ -52,9 +52,11 @@ def _build_locked(force: bool) -> str:
             and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, *_SRCS, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    # OpenMP over agents when the compiler has it (or_set_threads); one thread otherwise
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, *_SRCS, "-lm"], capture_output=True)
+    if r.returncode != 0:
+        subprocess.run(base + ["-o", tmp, *_SRCS, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -141,8 +143,17 @@ def lib():
             L.rx_classes.argtypes = [C.POINTER(_RxModel), vp, vp]
             L.rx_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
             L.rx_noise.restype = C.c_double
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_set_threads.restype = C.c_int
             _lib = L
     return _lib
+
+
+def set_threads(threads: int) -> int:
+    """Host threads for the oracle's per-agent loops (OpenMP over agents; results
+    are the same for every count).  Returns the count in effect (1 when the
+    library was built without OpenMP)."""
+    return int(lib().or_set_threads(int(threads)))
 
 
 def _ptr(a: np.ndarray | None):

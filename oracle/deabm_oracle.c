@@ -24,9 +24,18 @@
  * run left to right from +0.0f in the order the CSR lists the edges; products
  * are rounded one at a time (build with -ffp-contract=off).  A parallel FP64
  * path (same order, unrounded infectiousness) gives the accuracy reference.
+ *
+ * Threads: the per-agent loops may run on several host threads (OpenMP over
+ * agents, or_set_threads; one thread by default).  Each agent's sums, draw and
+ * update touch only that agent's outputs and read the state of the start of the
+ * step, and the counters are integer sums, so every thread count gives the same
+ * results bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -514,6 +523,20 @@ uint32_t or_occ_contacts(const or_model *m, uint32_t j, uint32_t step, uint32_t 
     return k;
 }
 
+static int g_threads = 1;
+
+/* Host threads for the per-agent loops (>= 1); returns the number in effect. */
+int or_set_threads(int threads)
+{
+#ifdef _OPENMP
+    g_threads = threads > 0 ? threads : 1;
+#else
+    (void)threads;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
 static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age, const int16_t *vday1,
                      uint32_t t, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags, uint8_t *qt,
                      int16_t *vd1, int16_t *vd2, or_diag *dg)
@@ -527,6 +550,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
     uint8_t *newinf = (uint8_t *)calloc(n ? n : 1, 1);
 
     /* a1: per-source infectiousness from the state at the start of step t */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (uint32_t i = 0; i < n; ++i) {
         int c = infectious_class(stage[i]);
         int ti = tinf[i];
@@ -540,10 +564,11 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
     const float c_R = m->R * m->inv_Ibar;
     int64_t messages = 0;
     int32_t n_new = 0;
-    uint32_t contacts[OR_POIS_CAP];
     or_occ occ = {NULL, NULL, NULL};
     if (m->n_occ) occ_build(m, &occ);
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : messages, n_new)
     for (uint32_t j = 0; j < n; ++j) {
+        uint32_t contacts[OR_POIS_CAP];
         float s32 = 0.0f;
         double s64 = 0.0;
         for (uint32_t net = 0; net < m->n_nets; ++net) {
@@ -608,6 +633,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
     }
 
     /* a6-a7: state machine and interventions, agent by agent */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (uint32_t j = 0; j < n; ++j) {
         int st = stage[j], a = age[j];
         int tm = timer[j], ti = tinf[j];
@@ -712,7 +738,9 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
      * den_compliance and is then tested on the next step. */
     int32_t n_notified = 0;
     if (den_src) {
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : n_notified)
         for (uint32_t j = 0; j < n; ++j) {
+            uint32_t contacts[OR_POIS_CAP];
             const int st = stage[j];
             if (!(flags[j] & FL_APP) || QT_QDAYS(qt[j]) > 0 || st == ST_HOSP || st == ST_ICU || st == ST_DEAD)
                 continue;

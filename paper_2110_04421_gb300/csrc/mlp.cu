@@ -659,10 +659,10 @@ extern "C" int deabm_mlp_grad(deabm_mlp *m, const float *x, const float *y, uint
     return mlp_backward_dev(m, y, (int)batch, loss);
 }
 
-extern "C" int deabm_mlp_train_step(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float lr, float *loss)
+// one Adam step (Kingma and Ba, Algorithm 1) on the FP32 master weights from the
+// gradients in gW / gb; refreshes the BF16 copies
+static int mlp_adam(deabm_mlp *m, float lr)
 {
-    int r;
-    if ((r = deabm_mlp_grad(m, x, y, batch, nullptr))) return r;
     m->step += 1;
     m->wt_dirty = true;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -675,10 +675,37 @@ extern "C" int deabm_mlp_train_step(deabm_mlp *m, const float *x, const float *y
                                                      1e-8f, c1, c2, nullptr, 0, 0, 0);
     }
     MCU(cudaGetLastError());
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_train_step(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float lr, float *loss)
+{
+    int r;
+    if ((r = deabm_mlp_grad(m, x, y, batch, nullptr))) return r;
+    if ((r = mlp_adam(m, lr))) return r;
     if (loss) {
         MCU(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
         MCU(cudaStreamSynchronize(m->stream));
     }
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_apply_grads(deabm_mlp *m, const float *grads, uint32_t on_device, float lr)
+{
+    if (!m || !grads) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    if (!(lr > 0.0f) || !std::isfinite(lr)) return mlp_fail(DEABM_EINVAL, "lr must be finite and > 0");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t off = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const size_t nw = (size_t)m->fin[l] * m->fout[l];
+        MCU(cudaMemcpyAsync(m->gW[l], grads + off, 4 * nw, kind, m->stream));
+        off += nw;
+        MCU(cudaMemcpyAsync(m->gb[l], grads + off, 4ull * m->fout[l], kind, m->stream));
+        off += m->fout[l];
+    }
+    int r;
+    if ((r = mlp_adam(m, lr))) return r;
+    if (!on_device) MCU(cudaStreamSynchronize(m->stream));  // the host buffer may be reused on return
     return DEABM_OK;
 }
 

@@ -25,7 +25,8 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
-           "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore")
+           "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore",
+           "deabm_mlp_apply_grads")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -130,6 +131,7 @@ def lib():
         L.deabm_mlp_grad.argtypes = [vp, vp, vp, u32, vp]
         L.deabm_mlp_train_step.argtypes = [vp, vp, vp, u32, C.c_float, vp]
         L.deabm_mlp_sync.argtypes = [vp]
+        L.deabm_mlp_apply_grads.argtypes = [vp, vp, u32, C.c_float]
         L.deabm_mlp_use_tcgen05.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.deabm_mlp_use_tcgen05.restype = C.c_int
         L.deabm_mlp_last_error.argtypes = []
@@ -140,7 +142,7 @@ def lib():
                      "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_relaxed_create",
                      "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate", "deabm_reset", "deabm_mlp_create",
                      "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
-                     "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync"):
+                     "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_apply_grads"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -631,6 +633,18 @@ class MLP:
         _mlp_check(lib().deabm_mlp_train_step(self.ctx, self._dev(x, self.n_in), self._dev(y, self.n_out), x.shape[0],
                                               lr, _p(loss)))
         return float(loss[0]) if sync else None
+
+    def apply_grads(self, grads, lr):
+        """One Adam step on caller-supplied gradients (numpy FP32 on the host, or a
+        contiguous CUDA FP32 tensor) in the get_params layout."""
+        if hasattr(grads, "is_cuda") and grads.is_cuda:
+            assert grads.dtype.is_floating_point and grads.element_size() == 4 and grads.is_contiguous()
+            assert grads.numel() == self.n_params
+            _mlp_check(lib().deabm_mlp_apply_grads(self.ctx, C.c_void_p(grads.data_ptr()), 1, lr))
+        else:
+            g = np.ascontiguousarray(grads, np.float32)
+            assert g.size == self.n_params
+            _mlp_check(lib().deabm_mlp_apply_grads(self.ctx, _p(g), 0, lr))
 
     def sync(self):
         _mlp_check(lib().deabm_mlp_sync(self.ctx))

@@ -61,6 +61,87 @@ def test_forward_matches_bf16_oracle(batch, tcgen05):
     assert np.max(np.abs(y - ref)) <= 1e-2 * np.max(np.abs(ref)), np.max(np.abs(y - ref))
 
 
+@pytest.mark.parametrize("tcgen05", [True, False])
+def test_forward_full_inference_batch_matches_oracle(tcgen05):
+    """The inference batch of 65,536 rows (512 CTAs of the fused kernel, two per
+    SM), every output element against the oracle at the bar above."""
+    import torch
+    from paper_2110_04421_gb300.deabm import MLP
+    B = W.surrogate_workload()["batch"]
+    p = M.init_params(SIZES, 21)
+    x, _ = make(B, 22)
+    m = MLP(max_batch=B)
+    assert m.use_tcgen05(tcgen05)
+    m.set_params(p)
+    y = m.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    m.sync()
+    m.close()
+    ref, _, _ = M.forward(p, SIZES, x)
+    err = np.abs(y - ref)
+    assert np.all(err <= 1e-2 * np.max(np.abs(ref))), (np.max(err), np.unravel_index(np.argmax(err), err.shape))
+
+
+def test_adam_steps_match_oracle_adam():
+    """Five Adam steps on seeded gradients (spanning twelve orders of magnitude,
+    down to the size of eps) through deabm_mlp_apply_grads, host and device
+    gradients alternating, against the oracle's FP64 Adam from the same start.
+    FP32 master weights and moments: each parameter within 1e-5 of the rate
+    plus 4e-7 of its size."""
+    import torch
+    from oracle.adam import Adam
+    from paper_2110_04421_gb300.deabm import MLP
+    p0 = M.init_params(SIZES, 12)
+    m = MLP(max_batch=64)
+    m.set_params(p0)
+    lr = 1e-3
+    opt = Adam(p0.size, lr)
+    ref = p0.astype(np.float64)
+    rng = np.random.default_rng(13)
+    for it in range(5):
+        g = (rng.normal(size=p0.size) * np.exp(rng.uniform(-20.0, 3.0, p0.size))).astype(np.float32)
+        if it % 2:
+            m.apply_grads(torch.tensor(g, device="cuda"), lr)
+        else:
+            m.apply_grads(g, lr)
+        ref = opt.step(ref, g.astype(np.float64))
+        got = m.get_params().astype(np.float64)
+        err = np.abs(got - ref)
+        tol = 1e-5 * lr + 4e-7 * np.abs(ref)
+        assert np.all(err <= tol), (it, np.max(err / tol))
+    m.close()
+
+
+def test_train_step_equals_gradient_then_oracle_adam():
+    """One deabm_mlp_train_step at batch 4,096 against the oracle's gradient
+    followed by the oracle's Adam.  The gradients agree at the bar above; the
+    first Adam step moves a weight by lr g / (|g| + eps), so where the oracle's
+    gradient is larger than twice that bar the GPU's step must equal the oracle's
+    (1e-4 of the rate plus FP32 rounding), and elsewhere it is at most lr."""
+    import torch
+    from oracle.adam import Adam
+    from paper_2110_04421_gb300.deabm import MLP
+    p0 = M.init_params(SIZES, 14)
+    x, y = make(4096, 15)
+    lr = 2e-3
+    m = MLP(max_batch=4096)
+    m.set_params(p0)
+    m.train_step(torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"), lr)
+    p1 = m.get_params().astype(np.float64)
+    g = m.get_grads()
+    m.close()
+    _, gref, _ = M.loss_and_grad(p0, SIZES, x, y)
+    ref = Adam(p0.size, lr).step(p0.astype(np.float64), gref)
+    d, dref = p1 - p0, ref - p0
+    for a, b in layer_slices(SIZES):
+        bar = 1e-2 * np.max(np.abs(gref[a:b])) + 1e-8
+        assert np.max(np.abs(g[a:b] - gref[a:b])) <= bar, (a, b)
+        sure = np.abs(gref[a:b]) > 2 * bar
+        assert sure.mean() > 0.4, (a, b, sure.mean())
+        tol = 1e-4 * lr + 2.4e-7 * np.abs(p0[a:b])
+        assert np.all(np.abs(d[a:b][sure] - dref[a:b][sure]) <= tol[sure]), (a, b)
+        assert np.all(np.abs(d[a:b]) <= lr * (1 + 1e-4) + tol), (a, b)
+
+
 def test_gradients_match_bf16_oracle():
     import torch
     from paper_2110_04421_gb300.deabm import MLP

@@ -104,6 +104,32 @@ def test_calibration_reduces_loss(case):
     assert np.all(out >= 0)
 
 
+def test_calibration_steps_match_oracle_adam_on_oracle_gradients(case):
+    """deabm_calibrate for 6 steps against the oracle's projected Adam driven by
+    the oracle's FP64 reverse sweep from the same start.  The GPU gradient is
+    within 1e-4 of the gradient's norm, and Adam normalises each coordinate, so
+    where the oracle's gradient coordinates stay well clear of 0 every step the
+    parameters agree within 2e-3 of the total step (lr per step); the loss trace
+    within 1e-4 relative."""
+    from oracle.adam import Adam
+    pop, p, T, rx, th, y = case
+    steps, lr = 6, 0.02
+    g = gpu(pop, p, max_days=T, ckpt_every=10)
+    out, trace = g.calibrate(th, y, steps=steps, lr=lr)
+    g.close()
+    opt = Adam(13, lr, nonneg=True)
+    ref = np.float32(th).astype(np.float64)
+    for it in range(steps):
+        o = rx.run(ref, T, target=y.astype(np.float64), grad=True)
+        assert abs(trace[it] - o["loss"]) <= 1e-4 * o["loss"], (it, trace[it], o["loss"])
+        gr = o["grad"]
+        assert np.min(np.abs(gr)) > 1e-2 * np.linalg.norm(gr), (it, gr)
+        ref = opt.step(ref, gr)
+        # the GPU keeps theta in FP32
+        ref = np.float32(ref).astype(np.float64)
+    assert np.max(np.abs(out - ref)) <= 2e-3 * lr * steps, (out, ref)
+
+
 def test_full_size_gradient():
     """N = 100,000, 90 days, tau = 0.5, checkpoint every 10 days; target simulated
     at hidden parameters R = 3.5, weights 2.0 / 1.0 / 0.7."""
