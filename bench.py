@@ -133,14 +133,20 @@ def sources_hash(names) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(sources, profile: str, units_per_launch: float):
+def traffic_from_profile(sources, profile: str, units_per_launch: float, days=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (their sha256 prefix is recorded there); else None."""
+    current kernel sources (their sha256 prefix is recorded there) and, when
+    `days` = (first, last) is given, on a day inside that timed range (the
+    summary's `captured_day` line); else None."""
     try:
         txt = open(os.path.join(ROOT, "profiles", profile)).read()
         src_hash = sources_hash(sources)
         if f"source_sha256_16: {src_hash}" not in txt:
             return None
+        if days is not None:
+            d = re.search(r"captured_day:\s*([0-9]+)", txt)
+            if not d or not (days[0] <= int(d.group(1)) <= days[1]):
+                return None
         m = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+-]+)", txt)
         return float(m.group(1)) * units_per_launch if m else None
     except Exception:
@@ -208,6 +214,7 @@ def run_ours(args, rank, world, local):
     per_day_ms = [total_ms / K] * K
     _, hist_days, msgs = sim.counters(Wm + K)
     messages = int(msgs[Wm:].astype(np.int64).sum())
+    gathered = int(sim.gathered(Wm + K)[Wm:].astype(np.int64).sum())
     # susceptible agents at the start of each timed day (end of the day before)
     sus_days = [float(hist_days[d - 1, 0, 0]) for d in range(Wm, Wm + K)]
     sim.close()
@@ -228,9 +235,9 @@ def run_ours(args, rank, world, local):
         d2h = ni.nbytes + hist.nbytes + sum(v.nbytes for v in st.values()) + msgs2.nbytes
 
     # ---- max over ranks
-    (total_ms, e2e_s), (messages, e2e_messages) = reduce_over_ranks(dist, [total_ms, e2e_s],
-                                                                    [messages, e2e_messages], "cuda")
-    messages, e2e_messages = int(messages), int(e2e_messages)
+    (total_ms, e2e_s), (messages, e2e_messages, gathered) = reduce_over_ranks(
+        dist, [total_ms, e2e_s], [messages, e2e_messages, gathered], "cuda")
+    messages, e2e_messages, gathered = int(messages), int(e2e_messages), int(gathered)
 
     # ---- batched ensemble vs plain per-replicate loop, relaxed gradient (rank 0)
     batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
@@ -248,7 +255,8 @@ def run_ours(args, rank, world, local):
             step_bytes_plain_needed(n, static_edges, len(pop["row_ptr"]), bool(params["vax_on"]), ns) for ns in sus_days)
         peak, peak_kind = measured_peak_hbm()
         achieved = alg / (avg_ms / 1e3) / 1e9
-        traffic = traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_n2e6.md", n)
+        achieved_needed = alg_needed / (avg_ms / 1e3) / 1e9
+        traffic = traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_n2e6.md", n, (Wm, Wm + K - 1))
         cpu = None if args.no_cpu_baseline else cpu_baseline(pop, params, args.cpu_seconds)
         line = {
             "metric": "agent interactions/s on 1 GB300 (plain day kernel; batched B=256 in 'batched')",
@@ -265,14 +273,20 @@ def run_ours(args, rank, world, local):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "step_plain_kernel", "alg_bytes_per_launch": alg,
                          "alg_bytes_needed_mean": alg_needed,
-                         "alg_note": "achieved counts every array once (163 MB a day); only susceptible agents "
-                                     "gather (Eq. 2 applies to them alone), so a day needs alg_bytes_needed_mean "
-                                     f"on average (mean susceptible share {statistics.mean(sus_days) / n:.3f} "
-                                     "over the timed days)",
+                         "achieved_needed": achieved_needed, "frac_needed": achieved_needed / peak,
+                         "alg_note": f"achieved counts every array once ({alg / 1e6:.0f} MB a day); only susceptible "
+                                     "agents gather (Eq. 2 applies to them alone), so a day needs "
+                                     "alg_bytes_needed_mean on average (mean susceptible share "
+                                     f"{statistics.mean(sus_days) / n:.3f} over the timed days): achieved_needed "
+                                     "and frac_needed divide those bytes by the same time",
                          "launch_ms_mean": avg_ms},
             "e2e": None if args.no_e2e else {
                 "value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K, "seconds": e2e_s},
+            "gathered": {"value": gathered / (total_ms / 1e3), "unit": "messages gathered/s",
+                         "share": gathered / max(messages, 1),
+                         "note": "in-contacts of the destinations that evaluated Eq. 1 (the agents susceptible at "
+                                 "the start of each day); value counts every message of the day, gathered or not"},
             "gpu_launches": K,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -515,7 +529,8 @@ def run_occupation(args):
             "l2": f"inputs larger than L2: {alg / 1e6:.0f} MB algorithmic per day, no flush",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "kernel": "step_plain_kernel (daily occupation networks)", "alg_bytes_per_launch": alg,
-                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_occ_n2e6.md", n)},
+                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_occ_n2e6.md", n,
+                                                         (args.warmup, args.warmup + K - 1))},
             "watts_strogatz": {"workload": "the same with Watts-Strogatz occupations (ring lattice, rewiring 0.1)",
                                "value": msg_ws / (ms_ws / 1e3), "unit": "interactions/s", "ms_per_step": ms_ws / K,
                                "roofline": {"bound": "hbm", "achieved": alg / (ms_ws / K / 1e3) / 1e9, "peak": peak,
@@ -591,7 +606,8 @@ def run_batched(args):
            "value": value, "unit": "interactions/s", "ms_per_step": ms / Kb, "steps": Kb,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "kernel": "step_batch4_kernel", "alg_bytes_per_launch": alg,
-                        "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_batch_n1e5_b256.md", n * B)}}
+                        "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_batch_n1e5_b256.md", n * B,
+                                                        (args.warmup, args.warmup + Kb - 1))}}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_columns(pop, w["params"], rp, seeds, args.cpu_seconds / 2)
     if args.no_loop:
@@ -620,58 +636,73 @@ def run_batched(args):
 
 
 # ---------------------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(pops, params, seconds: float, max_days: int = 180):
-    """The oracle, as it stands (single-threaded C): whole days from day 0 of the
-    given population(s) -- one population, or a list taken in turn -- each run for
-    at most max_days (the workload's horizon), until about `seconds` of CPU time."""
+def _oracle_days(pops, params, seconds: float, max_days: int, threads: int):
+    """Whole oracle days from day 0 of the population(s), in turn, each run for at
+    most max_days, until about `seconds`; the oracle's per-agent loops on `threads`
+    host threads.  Returns (messages, days, runs, seconds)."""
     import oracle
+    used = oracle.set_threads(threads)
+    msgs, days, runs, el = 0, 0, 0, 0.0
+    try:
+        t0 = time.perf_counter()
+        while el < seconds:
+            q = runs % len(pops)
+            sim = oracle.Sim(pops[q], params[q], pops[q]["age"], pops[q]["seed_ids"])
+            runs += 1
+            for _ in range(max_days):
+                msgs += sim.step(diag=False)["messages"]
+                days += 1
+                el = time.perf_counter() - t0
+                if el >= seconds:
+                    break
+    finally:
+        oracle.set_threads(1)
+    return msgs, days, runs, el, used
+
+
+def cpu_baseline(pops, params, seconds: float, max_days: int = 180):
+    """The oracle, as written (plain C; its per-agent loops on OpenMP threads, which
+    changes no result): whole days from day 0 of the given population(s) -- one
+    population, or a list taken in turn -- each run for at most max_days (the
+    workload's horizon).  Timed on every host core (the reported value) and on one
+    core, about seconds/2 each."""
     pops = pops if isinstance(pops, list) else [pops]
     params = params if isinstance(params, list) else [params] * len(pops)
-    msgs, days, runs, el = 0, 0, 0, 0.0
-    t0 = time.perf_counter()
-    while el < seconds:
-        q = runs % len(pops)
-        sim = oracle.Sim(pops[q], params[q], pops[q]["age"], pops[q]["seed_ids"])
-        runs += 1
-        for _ in range(max_days):
-            msgs += sim.step(diag=False)["messages"]
-            days += 1
-            el = time.perf_counter() - t0
-            if el >= seconds:
-                break
-    sizes = sorted({int(p["n"]) for p in pops[:runs]})
-    what = (f"the same N={pops[0]['n']} population" if len(pops) == 1
-            else f"{min(runs, len(pops))} of the {len(pops)} populations in turn (N {sizes[0]}..{sizes[-1]})")
-    return {"value": msgs / el, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-            "sample": f"{days} whole days of {what}, from day 0, at most {max_days} days a run, {el:.1f} s, "
-                      "single thread", "cpu": cpu_model()}
+
+    def what(runs):
+        sizes = sorted({int(p["n"]) for p in pops[:runs]})
+        return (f"the same N={pops[0]['n']} population" if len(pops) == 1
+                else f"{min(runs, len(pops))} of the {len(pops)} populations in turn (N {sizes[0]}..{sizes[-1]})")
+
+    m1, d1, r1, e1, _ = _oracle_days(pops, params, seconds / 2, max_days, 1)
+    ma, da, ra, ea, used = _oracle_days(pops, params, seconds / 2, max_days, host_cores())
+    return {"value": ma / ea, "unit": "interactions/s", "cores": used, "kind": "oracle",
+            "sample": f"{da} whole days of {what(ra)}, from day 0, at most {max_days} days a run, {ea:.1f} s, "
+                      f"{used} threads (OpenMP over agents)",
+            "cpu": cpu_model(),
+            "one_core": {"value": m1 / e1, "unit": "interactions/s", "cores": 1,
+                         "sample": f"{d1} whole days of {what(r1)}, {e1:.1f} s, single thread"}}
 
 
 def cpu_baseline_columns(pop, base, rp, seeds, seconds: float):
     """The oracle on replicate columns of the batched workload, one after another
-    (each column is an independent run on the shared graph), 8 columns of whole
-    days from day 0, stopping after about `seconds`."""
-    import oracle
-    msgs, days, cols = 0, 0, 0
-    t0 = time.perf_counter()
-    el = 0.0
+    (each column is an independent run on the shared graph), whole days from day
+    0 of up to 8 columns, about seconds/2 on every host core (the reported value)
+    and seconds/2 on one core."""
+    cols = []
     for r in range(min(8, len(seeds))):
-        pr = dict(base, R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
-                  S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r]))
-        sim = oracle.Sim(pop, pr, pop["age"], pop["seed_ids"])
-        cols += 1
-        for _ in range(180):
-            msgs += sim.step(diag=False)["messages"]
-            days += 1
-            el = time.perf_counter() - t0
-            if el >= seconds:
-                break
-        if el >= seconds:
-            break
-    return {"value": msgs / el, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-            "sample": f"{days} replicate-days over {cols} of the {len(seeds)} columns (from day 0), {el:.1f} s, "
-                      "single thread; the columns are independent, so this per-column rate is the whole "
-                      "batch's rate on one core (extrapolated, not run for all columns)", "cpu": cpu_model()}
+        cols.append(dict(base, R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])], B_rand=float(rp[r, 3]),
+                         S_age=[float(x) for x in rp[r, 4:13]], dose2_delay=int(rp[r, 13]), seed=int(seeds[r])))
+    pops = [pop] * len(cols)
+    m1, d1, r1, e1, _ = _oracle_days(pops, cols, seconds / 2, 180, 1)
+    ma, da, ra, ea, used = _oracle_days(pops, cols, seconds / 2, 180, host_cores())
+    note = ("the columns are independent, so this per-column rate is the whole batch's rate "
+            "(extrapolated, not run for all columns)")
+    return {"value": ma / ea, "unit": "interactions/s", "cores": used, "kind": "oracle",
+            "sample": f"{da} replicate-days over {min(ra, len(cols))} of the {len(seeds)} columns (from day 0), "
+                      f"{ea:.1f} s, {used} threads (OpenMP over agents); {note}", "cpu": cpu_model(),
+            "one_core": {"value": m1 / e1, "unit": "interactions/s", "cores": 1,
+                         "sample": f"{d1} replicate-days over {min(r1, len(cols))} columns, {e1:.1f} s, single thread"}}
 
 
 def cpu_baseline_relaxed(pop, params, tau, theta, target, T):
@@ -689,42 +720,76 @@ def cpu_baseline_relaxed(pop, params, tau, theta, target, T):
 
 def cpu_baseline_mlp(sizes, params, batch: int):
     """The numpy MLP oracle (FP64 with the kernel's BF16 rounding points) on
-    `batch` samples, in a child process with single-threaded BLAS."""
-    code = ("import sys, time, json, numpy as np\n"
-            f"sys.path.insert(0, {ROOT!r})\n"
-            "from oracle import mlp\n"
-            f"sizes = {list(sizes)!r}\n"
-            f"params = np.load({params!r})\n"
-            f"x = np.random.default_rng(0).random(({batch}, sizes[0]))\n"
-            "t0 = time.perf_counter(); mlp.forward(params, sizes, x); el = time.perf_counter() - t0\n"
-            "print(json.dumps({'seconds': el}))\n")
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
-    el = json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
-    return {"value": batch / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"forward of {batch} samples (FP64 with BF16 rounding points), {el:.2f} s, single-threaded BLAS",
-            "cpu": cpu_model()}
+    `batch` samples, in a child process: BLAS on every host core (the reported
+    value) and on one."""
+    def timed(threads):
+        code = ("import sys, time, json, numpy as np\n"
+                f"sys.path.insert(0, {ROOT!r})\n"
+                "from oracle import mlp\n"
+                f"sizes = {list(sizes)!r}\n"
+                f"params = np.load({params!r})\n"
+                f"x = np.random.default_rng(0).random(({batch}, sizes[0]))\n"
+                "t0 = time.perf_counter(); mlp.forward(params, sizes, x); el = time.perf_counter() - t0\n"
+                "print(json.dumps({'seconds': el}))\n")
+        n = str(threads)
+        env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n)
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+        return json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
+
+    el1 = timed(1)
+    cores = host_cores()
+    ela = timed(cores)
+    return {"value": batch / ela, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"forward of {batch} samples (FP64 with BF16 rounding points), {ela:.2f} s, BLAS on {cores} threads",
+            "cpu": cpu_model(),
+            "one_core": {"value": batch / el1, "unit": "samples/s", "cores": 1,
+                         "sample": f"the same forward, {el1:.2f} s, single-threaded BLAS"}}
 
 
-def cpu_model():
+def cpu_model() -> str:
+    """The host CPU as lscpu names it (vendor and model; aarch64 hosts have no
+    'model name' line in /proc/cpuinfo), with the online core count."""
+    name = None
     try:
-        for line in open("/proc/cpuinfo"):
-            if "model name" in line:
-                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        f = {}
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                f.setdefault(k.strip(), v.strip())
+        parts = [f.get("Vendor ID"), f.get("Model name")]
+        name = " ".join(x for x in parts if x and x != "-") or None
     except Exception:
         pass
+    if not name:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if "model name" in line:
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
     import platform
-    return platform.machine()
+    return f"{name or platform.processor() or 'unknown'} ({platform.machine()}, {host_cores()} cores)"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args, rank, world, local):
-    """The oracle arm: each step is one whole oracle day of the same workload."""
+    """The oracle arm: each step is one whole oracle day of the same workload, the
+    oracle's per-agent loops on every host core (OpenMP over agents)."""
     if rank != 0:
         return
     import oracle
     from paper_2110_04421_gb300 import workloads as W
     w = W.plain_large()
     pop = W.population(w["n"], 0, w["n_seed"])
+    cores = oracle.set_threads(host_cores())
     sim = oracle.Sim(pop, w["params"], pop["age"], pop["seed_ids"])
     for _ in range(args.warmup):
         sim.step(diag=False)
@@ -733,6 +798,7 @@ def run_reference(args, rank, world, local):
     for _ in range(args.steps):
         msgs += sim.step(diag=False)["messages"]
     el = time.perf_counter() - t0
+    oracle.set_threads(1)
     value = msgs / el
     line = {"impl": "reference", "metric": "agent interactions/s on 1 GB300 (plain day kernel; batched B=256 in "
             "'batched')", "value": value, "unit": "interactions/s", "n_gpus": 1, "steps": args.steps,
@@ -741,8 +807,9 @@ def run_reference(args, rank, world, local):
             "data": "synthetic (seeded generators shaped like the paper's population)",
             "config": {"workload": PLAIN_WORKLOAD, "n_agents": w["n"],
                        "days_timed": f"{args.warmup}..{args.warmup + args.steps - 1}"},
-            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} whole oracle days after {args.warmup} warm-up days",
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} whole oracle days after {args.warmup} warm-up days, "
+                                       f"{cores} threads (OpenMP over agents)",
                              "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

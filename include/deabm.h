@@ -274,6 +274,16 @@ int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day);
 int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *new_inf, int32_t *hist,
                        uint64_t *messages);
 
+/* Messages gathered per day, days [0, day_count) (host uint64 [day]): the
+ * in-contacts (stored, occupation, random) of the destinations that evaluated
+ * Eq. 1 -- the agents susceptible at the start of the day (Eq. 2 applies to them
+ * alone), or every agent when lambda is kept or exposure notification is on --
+ * summed over populations in ragged batches.  The batched kernels gather every
+ * agent's in-contacts for every replicate, so there this equals the messages of
+ * deabm_get_counters.  Returns DEABM_OK, DEABM_EINVAL (NULL, more days than
+ * run), DEABM_ECUDA.  Synchronises. */
+int deabm_get_gathered(deabm_ctx *ctx, uint32_t day_count, uint64_t *gathered);
+
 /* Tables the device built: infectiousness [3][inf_len] (FP32), Poisson CDF
  * thresholds [15], first-dose day per agent [n_agents] (0x7FFF = never).
  * Any output may be NULL.  Synchronises. */

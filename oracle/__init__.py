@@ -93,7 +93,7 @@ class _Diag(C.Structure):
         ("lambda32", C.c_void_p), ("lambda64", C.c_void_p), ("p32", C.c_void_p), ("u32", C.c_void_p),
         ("inf32", C.c_void_p), ("near", C.c_void_p), ("rand_k", C.c_void_p),
         ("new_inf", C.c_int32), ("messages", C.c_int64), ("hist", C.c_int32 * N_STAGE),
-        ("den_notified", C.c_int32),
+        ("den_notified", C.c_int32), ("messages_sus", C.c_int64),
     ]
 
 
@@ -340,6 +340,7 @@ class Sim:
             raise ValueError("oracle rejected the model parameters")
         out["new_inf"] = int(d.new_inf)
         out["messages"] = int(d.messages)
+        out["messages_sus"] = int(d.messages_sus)
         out["hist"] = np.array(list(d.hist), np.int32)
         out["den_notified"] = int(d.den_notified)
         self.den_notified.append(out["den_notified"])

@@ -348,6 +348,8 @@ typedef struct {
     int64_t messages;  /* household+occupation+random in-edges processed */
     int32_t hist[OR_N_STAGE];
     int32_t den_notified;  /* app holders notified at the end of this step */
+    int64_t messages_sus;  /* the in-edges counted in `messages` whose destination was
+                              susceptible at the start of the step (Eq. 2 applies to them) */
 } or_diag;
 
 /*
@@ -562,12 +564,13 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
 
     /* a2-a5: per destination sums, lambda, p, Bernoulli draw */
     const float c_R = m->R * m->inv_Ibar;
-    int64_t messages = 0;
+    int64_t messages = 0, messages_sus = 0;
     int32_t n_new = 0;
     or_occ occ = {NULL, NULL, NULL};
     if (m->n_occ) occ_build(m, &occ);
-#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : messages, n_new)
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : messages, messages_sus, n_new)
     for (uint32_t j = 0; j < n; ++j) {
+        const int64_t messages_before = messages;
         uint32_t contacts[OR_POIS_CAP];
         float s32 = 0.0f;
         double s64 = 0.0;
@@ -605,6 +608,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             s64 += (double)m->B_rand * r64;
             messages += k;
         }
+        if (stage[j] == ST_S) messages_sus += messages - messages_before;
         float sus = m->S_age[age[j]];
         float lam = (c_R * sus) * s32;
         double lam64 = (double)m->R * (double)m->inv_Ibar * (double)sus * s64;
@@ -773,6 +777,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         dg->den_notified = n_notified;
         dg->new_inf = n_new;
         dg->messages = messages;
+        dg->messages_sus = messages_sus;
         for (int s = 0; s < OR_N_STAGE; ++s) dg->hist[s] = 0;
         for (uint32_t j = 0; j < n; ++j) dg->hist[(int)stage[j]]++;
     }

@@ -78,8 +78,7 @@ __device__ __forceinline__ RandBlock0 random_block0(const KParams &P, uint32_t j
 {
     RandBlock0 r;
     r.w = draw(seed_key(P.net_seed), j, day, kStreamRnet, 0u);
-    r.k = 0;
-    while (r.k < DEABM_POIS_CAP && (uint64_t)r.w.x >= __ldg(&P.tab->pois[r.k])) ++r.k;
+    r.k = poisson_count(P, r.w.x);
     return r;
 }
 

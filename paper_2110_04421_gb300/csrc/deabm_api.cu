@@ -144,6 +144,26 @@ static uint64_t threshold(double p)
     return (uint64_t)std::floor(p * 4294967296.0);
 }
 
+// Before a state is installed (create, reset, restore): the infectiousness
+// buffers the next day writes start at 0, since the day kernels leave a quiet
+// susceptible agent's entry untouched (it emits nothing).
+static cudaError_t clear_next_buffers(deabm_ctx *ctx, size_t count)
+{
+    cudaError_t e = cudaMemsetAsync(ctx->inf[1], 0, sizeof(float) * count, ctx->stream);
+    if (e == cudaSuccess && ctx->inf_rand[1]) e = cudaMemsetAsync(ctx->inf_rand[1], 0, sizeof(float) * count, ctx->stream);
+    return e;
+}
+
+// the Poisson thresholds as the day kernels' 32-bit words (KParams::pois32)
+static void set_pois32(KParams &K, const uint64_t *pois)
+{
+    K.pois_fin = 0;
+    for (int k = 0; k < DEABM_POIS_CAP; ++k) {
+        K.pois32[k] = pois[k] < ((uint64_t)1 << 32) ? (uint32_t)pois[k] : 0xFFFFFFFFu;
+        if (pois[k] < ((uint64_t)1 << 32)) K.pois_fin = (uint32_t)k + 1u;
+    }
+}
+
 static bool prob_ok(double p) { return p >= 0.0 && p <= 1.0; }
 
 // ---------------------------------------------------------------- validation
@@ -590,6 +610,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->C.new_inf, days * n_rep))) return r;
             if ((r = dalloc(ctx, &ctx->C.hist, days * n_rep * DEABM_N_STAGE))) return r;
             if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
+        if ((r = dalloc(ctx, &ctx->C.gath, days))) return r;
             if ((r = dalloc(ctx, &ctx->C.den, days))) return r;
             CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
             if (p->den_on) {
@@ -605,6 +626,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * n_rep, s));
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
             CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+        CU(ctx, cudaMemsetAsync(ctx->C.gath, 0, sizeof(unsigned long long) * days, s));
 
             // agents: [N] -> [N][n_rep] in internal order, each agent's initial state
             // repeated per replicate.  Caller arrays go up as given and are put in
@@ -746,6 +768,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.thr_eff2 = threshold(p->vax_eff2);
             K.tab = ctx->tab;
             K.rep = ctx->rep;
+            set_pois32(K, T.pois);
+            K.rep0 = reps[0];
             K.age = ctx->age;
             K.dose1_day = ctx->dose1;
             K.orig_id = ctx->relabel ? ctx->orig_id : nullptr;
@@ -784,6 +808,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 ctx->seed_ids = d_ids;
                 ctx->n_seed = a->n_seed;
             }
+            CU(ctx, clear_next_buffers(ctx, nb));
             CU(ctx, launch_emit(K, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
             CU(ctx, cudaStreamSynchronize(s));
             return DEABM_OK;
@@ -878,6 +903,20 @@ extern "C" int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *n
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     if (messages)
         for (uint32_t d = 0; d < day_count; ++d) messages[d] += ctx->static_edges;
+    return DEABM_OK;
+}
+
+extern "C" int deabm_get_gathered(deabm_ctx *ctx, uint32_t day_count, uint64_t *gathered)
+{
+    if (!ctx || !gathered) return fail(ctx, DEABM_EINVAL, "ctx and gathered are required");
+    if (day_count > ctx->day) return fail(ctx, DEABM_EINVAL, "only %u days have run", ctx->day);
+    if (day_count == 0) return DEABM_OK;
+    if (!ctx->ragged && ctx->n_rep > 1) {
+        // the batched kernels gather every agent's in-contacts for every replicate
+        return deabm_get_counters(ctx, day_count, nullptr, nullptr, gathered);
+    }
+    CU(ctx, cudaMemcpyAsync(gathered, ctx->C.gath, sizeof(uint64_t) * day_count, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
     return DEABM_OK;
 }
 
@@ -1138,6 +1177,7 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         if ((r = dalloc(ctx, &ctx->C.new_inf, days * n_pops))) return r;
         if ((r = dalloc(ctx, &ctx->C.hist, days * n_pops * DEABM_N_STAGE))) return r;
         if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
+        if ((r = dalloc(ctx, &ctx->C.gath, days))) return r;
         if ((r = dalloc(ctx, &ctx->queue, days))) return r;
         uint32_t max_n = 0;
         for (uint32_t q = 0; q < n_pops; ++q) max_n = std::max(max_n, graphs[q].n_agents);
@@ -1251,6 +1291,8 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             std::memcpy(T.dur_lo, p.dur_lo, sizeof T.dur_lo);
             std::memcpy(T.dur_hi, p.dur_hi, sizeof T.dur_hi);
             CU(ctx, cudaMemcpyAsync(ctx->tab + q, &T, sizeof T, cudaMemcpyHostToDevice, s));
+            set_pois32(K, T.pois);
+            K.rep0 = pd.rep;
             const double gs[6] = {p.inf_shape[0], p.inf_shape[1], p.inf_shape[2], p.inf_scale[0], p.inf_scale[1],
                                   p.inf_scale[2]};
             CU(ctx, cudaMemcpyAsync(d_gamma + 6 * q, gs, sizeof gs, cudaMemcpyHostToDevice, s));
@@ -1390,6 +1432,7 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
         std::vector<Rep> reps;
         build_reps(&ctx->base, ctx->n_rep, rep_params, rep_seeds, reps);
         CU(ctx, cudaMemcpyAsync(ctx->rep, reps.data(), sizeof(Rep) * ctx->n_rep, cudaMemcpyHostToDevice, s));
+        if (!ctx->ragged) ctx->kp.rep0 = reps[0];
         CU(ctx, cudaStreamSynchronize(s));  // the staging vector goes out of scope
     }
     if (ctx->ragged && rep_params)
@@ -1400,6 +1443,7 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     CU(ctx, cudaMemcpyAsync(ctx->S.flags, ctx->S0.flags, nb, cudaMemcpyDeviceToDevice, s));
     CU(ctx, cudaMemcpyAsync(ctx->S.qt, ctx->S0.qt, nb, cudaMemcpyDeviceToDevice, s));
     if (ctx->ragged) {
+        CU(ctx, clear_next_buffers(ctx, nb));
         for (size_t q = 0; q < ctx->pops.size(); ++q) {
             const PopDesc &pd = ctx->pops[q];
             StateRef Sp{ctx->S.stage + pd.base, ctx->S.timer + pd.base, ctx->S.tinf + pd.base, ctx->S.flags + pd.base,
@@ -1414,6 +1458,7 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
         CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * ctx->n_rep, s));
         CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
         CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+        CU(ctx, cudaMemsetAsync(ctx->C.gath, 0, sizeof(unsigned long long) * days, s));
         ctx->day = 0;
         return DEABM_OK;
     }
@@ -1429,11 +1474,13 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     }
     if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
     ctx->cur = 0;
+    CU(ctx, clear_next_buffers(ctx, nb));
     CU(ctx, launch_emit(ctx->kp, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
     const size_t days = ctx->max_steps;
     CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * ctx->n_rep, s));
     CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
     CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.gath, 0, sizeof(unsigned long long) * days, s));
     CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
     ctx->day = 0;
     return DEABM_OK;
@@ -1511,6 +1558,7 @@ extern "C" int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t 
     }
     ctx->day = day;
     ctx->cur = 0;
+    CU(ctx, clear_next_buffers(ctx, nb));
     CU(ctx, launch_emit(ctx->kp, ctx->S, ctx->inf[0], ctx->inf_rand[0], s));
     // counters of the days to come start from zero again
     const size_t rest = ctx->max_steps - day;
@@ -1518,6 +1566,7 @@ extern "C" int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t 
     CU(ctx, cudaMemsetAsync(ctx->C.hist + (size_t)day * B * DEABM_N_STAGE, 0,
                             sizeof(int32_t) * rest * B * DEABM_N_STAGE, s));
     CU(ctx, cudaMemsetAsync(ctx->C.msgs + day, 0, sizeof(unsigned long long) * rest, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.gath + day, 0, sizeof(unsigned long long) * rest, s));
     CU(ctx, cudaMemsetAsync(ctx->C.den + day, 0, sizeof(int32_t) * rest, s));
     if (ctx->kp.den_on) {
         CU(ctx, cudaMemsetAsync(ctx->den_pos + day, 0, sizeof(int32_t) * rest, s));

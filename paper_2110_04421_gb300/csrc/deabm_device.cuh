@@ -116,7 +116,29 @@ struct KParams {
     const uint32_t *app_rows, *app_rank;
     uint32_t *den_ring;
     uint32_t den_slots;
+    // The random network's Poisson CDF thresholds (Tables::pois) as 32-bit words:
+    // thresholds from index pois_fin on are 2^32, which no word reaches.
+    uint32_t pois32[DEABM_POIS_CAP];
+    uint32_t pois_fin;
+    // replicate 0's parameters by value: plain contexts read them from the
+    // kernel's parameter space (uniform across the grid) instead of through `rep`
+    Rep rep0;
 };
+
+// K_j of the random network from word 0 of its block 0: the number of Poisson
+// thresholds at or below w, which (the thresholds being non-decreasing) is the
+// first index whose threshold exceeds w.  The first eight compares are unrolled
+// against the parameter-space thresholds; beyond them (P(K >= 8) < 0.2 % at the
+// mean of 2) a loop finishes the count.
+__device__ __forceinline__ uint32_t poisson_count(const KParams &P, uint32_t w)
+{
+    uint32_t k = 0;
+#pragma unroll
+    for (uint32_t t = 0; t < 8u; ++t) k += (t < P.pois_fin && w >= P.pois32[t]) ? 1u : 0u;
+    if (k == 8u)
+        for (uint32_t t = 8u; t < P.pois_fin && w >= P.pois32[t]; ++t) ++k;
+    return k;
+}
 
 // Infectiousness buffers of a day.  Static-network gathers read `cur` (internal
 // ids); random-network gathers read `rand_cur`, indexed by the caller's agent ids
@@ -158,6 +180,7 @@ struct Counters {
     int32_t *new_inf;          // [day][n_rep]
     int32_t *hist;             // [day][n_rep][11]
     unsigned long long *msgs;  // [day] random in-contacts (static edges added on the host)
+    unsigned long long *gath;  // [day] in-contacts (stored, occupation, random) of the destinations that gathered
     int32_t *den;              // [day] agents notified (exposure notification)
 };
 

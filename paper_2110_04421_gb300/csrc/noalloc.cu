@@ -170,6 +170,11 @@ extern "C" int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t 
     }
     K.net_seed = params->net_seed;
     K.tab = tab;
+    K.pois_fin = 0;
+    for (int k = 0; k < DEABM_POIS_CAP; ++k) {
+        K.pois32[k] = ta.pois[k] < ((uint64_t)1 << 32) ? (uint32_t)ta.pois[k] : 0xFFFFFFFFu;
+        if (ta.pois[k] < ((uint64_t)1 << 32)) K.pois_fin = (uint32_t)k + 1u;
+    }
     K.age = age_bin;
     Rep rp{};
     volatile float rv = params->R, ib = params->inv_Ibar;  // one FP32 product, as in deabm_create

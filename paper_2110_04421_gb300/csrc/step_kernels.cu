@@ -39,6 +39,9 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
     return u < pe;
 }
 
+#ifndef DEABM_QUIET_S
+#define DEABM_QUIET_S 1  // 1: a susceptible agent with nothing happening today writes nothing
+#endif
 #ifndef DEABM_SUSCEPTIBLE_ONLY
 #define DEABM_SUSCEPTIBLE_ONLY 1  // 0: lambda (all gathers) for every agent, as the method is written
 #endif
@@ -52,7 +55,7 @@ template <bool OCC = true, bool DEN = false, bool ROWMAP = false>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
                                           float *p_out, int *new_stage, bool *infected, uint32_t *k_out,
-                                          bool *notify = nullptr)
+                                          uint32_t *kg_out, bool *notify = nullptr)
 {
     const size_t i = (size_t)j * stride + b;
     const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
@@ -75,10 +78,16 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
     if (P.rand_on) r0 = random_block0(P, jo, day);
     float lam = 0.0f;
-    if (full)
+    if (full) {
         lam = lambda_at<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
-    else
+        uint32_t deg = 0;
+#pragma unroll
+        for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) deg += rb.end[net] - rb.beg[net];
+        *kg_out = *k_out + deg;
+    } else {
         *k_out = contact_count(P, j, r0.k);
+        *kg_out = 0;
+    }
     a.tm = S.timer[i];
     a.ti = S.tinf[i];
     a.fl = S.flags[i];
@@ -104,6 +113,32 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
         inf_now = (a.st == DEABM_S) && hit;
     }
     const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
+#if DEABM_QUIET_S
+    // A susceptible agent that is not infected today and has nothing pending (no
+    // quarantine, no test result, no notification, no dose or vaccine onset of the
+    // static schedule today) keeps its state word for word and emits nothing, so
+    // neither its state nor its infectiousness is written: the buffer being
+    // written already holds its 0 of two days ago (S is only ever left, and both
+    // buffers are cleared whenever a state is installed).
+    bool quiet = !DEN && a.st == DEABM_S && !inf_now && a.qd == 0u && a.cd == 0u && !(a.fl & DEABM_FL_DEN);
+    if (quiet && P.vax_on) {
+        if (P.vax_strategy != 0) {
+            quiet = false;
+        } else if (d1 != kNever) {
+            const int32_t t = (int32_t)day, D1 = d1, D2 = D1 + (int32_t)rp.dose2_delay, on = (int32_t)P.vax_onset;
+            quiet = t != D1 && t != D2 && t != D1 + on && t != D2 + on;
+        }
+    }
+    if (quiet) {
+        if (lam_out) {
+            lam_out[i] = lam;
+            p_out[i] = p;
+        }
+        *new_stage = DEABM_S;
+        *infected = false;
+        return;
+    }
+#endif
     advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
     if (DEN) {  // a positive app holder notifies its contacts after the day
         const bool v = a.pos_result && (a.fl & DEABM_FL_APP);
@@ -135,8 +170,8 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
 #define DEABM_HIST_MATCH 0  // 1: warp-aggregated (match.any) stage counts; 2: warp-reduced packed counts;
                             // 0: one shared atomic per agent
 #endif
-__device__ __forceinline__ void count_day(bool active, int st, bool infected, uint32_t k, int *s_hist, int *s_new,
-                                          unsigned long long *s_msgs)
+__device__ __forceinline__ void count_day(bool active, int st, bool infected, uint32_t k, uint32_t kg, int *s_hist,
+                                          int *s_new, unsigned long long *s_msgs, unsigned long long *s_gath)
 {
     const unsigned full = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
@@ -165,6 +200,8 @@ __device__ __forceinline__ void count_day(bool active, int st, bool infected, ui
     if (lane == 0 && nb) atomicAdd(s_new, __popc(nb));
     const unsigned ks = __reduce_add_sync(full, active ? k : 0u);
     if (lane == 0 && ks) atomicAdd(s_msgs, (unsigned long long)ks);
+    const unsigned kgs = __reduce_add_sync(full, active ? kg : 0u);
+    if (lane == 0 && kgs) atomicAdd(s_gath, (unsigned long long)kgs);
 }
 
 #ifndef DEABM_PLAIN_BLOCK
@@ -179,7 +216,7 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
 {
     __shared__ int s_hist[DEABM_N_STAGE];
     __shared__ int s_new;
-    __shared__ unsigned long long s_msgs;
+    __shared__ unsigned long long s_msgs, s_gath;
 #ifndef DEABM_REP_SMEM
 #define DEABM_REP_SMEM 0  // 1: stage the replicate parameters in shared memory once per block
 #endif
@@ -189,20 +226,20 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
         ((uint32_t *)&s_rep)[q] = ((const uint32_t *)P.rep)[q];
 #endif
     if (threadIdx.x < DEABM_N_STAGE) s_hist[threadIdx.x] = 0;
-    if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; }
+    if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; s_gath = 0ull; }
     __syncthreads();
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = j < P.n;
     int st = 0;
     bool infected = false, notify = false;
-    uint32_t k = 0;
+    uint32_t k = 0, kg = 0;
     if (active) {
 #if DEABM_REP_SMEM
         const Rep &rp = s_rep;
 #else
-        const Rep &rp = P.rep[0];
+        const Rep &rp = P.rep0;
 #endif
-        agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k,
+        agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k, &kg,
                             &notify);
     }
     if (DEN) {  // the day's positive app holders as a bit map over rows: one word per warp
@@ -212,13 +249,14 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
             if (bits) atomicAdd(P.den_pos + day, __popc(bits));
         }
     }
-    count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
+    count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
     __syncthreads();
     if (threadIdx.x < DEABM_N_STAGE && s_hist[threadIdx.x])
         atomicAdd(&C.hist[(size_t)day * DEABM_N_STAGE + threadIdx.x], s_hist[threadIdx.x]);
     if (threadIdx.x == 0) {
         if (s_new) atomicAdd(&C.new_inf[day], s_new);
         if (s_msgs) atomicAdd(&C.msgs[day], s_msgs);
+        if (s_gath) atomicAdd(&C.gath[day], s_gath);
     }
 }
 
@@ -244,8 +282,9 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     uint32_t k = 0;
     if (active) {
         const Rep &rp = P.rep[b];
+        uint32_t kg;
         agent_day<true, false, true>(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st,
-                                     &infected, &k);
+                                     &infected, &k, &kg);
         atomicAdd(&s_cnt[st][lane], 1);
         if (infected) atomicAdd(&s_cnt[DEABM_N_STAGE][lane], 1);
     }
@@ -280,7 +319,7 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
     __shared__ uint32_t s_tile;
     __shared__ int s_hist[DEABM_N_STAGE];
     __shared__ int s_new;
-    __shared__ unsigned long long s_msgs;
+    __shared__ unsigned long long s_msgs, s_gath;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(queue + day, 1u);
         __syncthreads();
@@ -293,7 +332,7 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             for (uint32_t q = threadIdx.x; q < sizeof(PopDesc) / 4; q += blockDim.x) dst[q] = src[q];
         }
         if (threadIdx.x < DEABM_N_STAGE) s_hist[threadIdx.x] = 0;
-        if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; }
+        if (threadIdx.x == 0) { s_new = 0; s_msgs = 0ull; s_gath = 0ull; }
         __syncthreads();
         InfBuffers I;
         I.cur = inf_cur + sp.base;
@@ -314,10 +353,11 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             const bool active = j < tl.end;
             int st = 0;
             bool infected = false;
-            uint32_t k = 0;
+            uint32_t k = 0, kg = 0;
             if (active)
-                agent_day<false, false, true>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k);
-            count_day(active, st, infected, k, s_hist, &s_new, &s_msgs);
+                agent_day<false, false, true>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k,
+                                              &kg);
+            count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
         }
         __syncthreads();
         if (threadIdx.x < DEABM_N_STAGE && s_hist[threadIdx.x])
@@ -325,6 +365,7 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
         if (threadIdx.x == 0) {
             if (s_new) atomicAdd(&C.new_inf[(size_t)day * n_pops + tl.pop], s_new);
             if (s_msgs) atomicAdd(&C.msgs[day], s_msgs);
+            if (s_gath) atomicAdd(&C.gath[day], s_gath);
         }
         __syncthreads();
     }
@@ -452,8 +493,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
         if (P.rand_on) {
             const uint2 nk = seed_key(P.net_seed);
             uint4 w = draw(nk, jo, day, kStreamRnet, 0u);
-            uint32_t kr = 0;
-            while (kr < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kr])) ++kr;
+            const uint32_t kr = poisson_count(P, w.x);
             float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const uint64_t nm1 = (uint64_t)(P.n - 1u);
             const float *panel = I.row_of ? I.cur : I.rand_cur;

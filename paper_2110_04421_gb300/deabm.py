@@ -26,7 +26,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
            "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore",
-           "deabm_mlp_apply_grads")
+           "deabm_mlp_apply_grads", "deabm_get_gathered")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -132,6 +132,7 @@ def lib():
         L.deabm_mlp_train_step.argtypes = [vp, vp, vp, u32, C.c_float, vp]
         L.deabm_mlp_sync.argtypes = [vp]
         L.deabm_mlp_apply_grads.argtypes = [vp, vp, u32, C.c_float]
+        L.deabm_get_gathered.argtypes = [vp, u32, vp]
         L.deabm_mlp_use_tcgen05.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.deabm_mlp_use_tcgen05.restype = C.c_int
         L.deabm_mlp_last_error.argtypes = []
@@ -142,7 +143,8 @@ def lib():
                      "deabm_get_counters", "deabm_get_tables", "deabm_info", "deabm_sync", "deabm_relaxed_create",
                      "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate", "deabm_reset", "deabm_mlp_create",
                      "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
-                     "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_apply_grads"):
+                     "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_apply_grads",
+                     "deabm_get_gathered"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -378,6 +380,12 @@ class RaggedSimulation:
         _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
         return ni, h, m
 
+    def gathered(self, days: int):
+        """Messages gathered per day, summed over the populations (deabm_get_gathered)."""
+        g = np.zeros(days, np.uint64)
+        _check(lib().deabm_get_gathered(self.ctx, days, _p(g)), self.ctx)
+        return g
+
     def state(self) -> list:
         """Per-population state dicts (caller ids)."""
         out = dict(stage=np.zeros(self.n, np.int8), timer=np.zeros(self.n, np.int16), tinf=np.zeros(self.n, np.int16),
@@ -509,6 +517,14 @@ class Simulation:
         m = np.zeros(days, np.uint64)
         _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
         return ni, h, m
+
+    def gathered(self, days: int | None = None):
+        """Messages gathered per day (deabm_get_gathered): the in-contacts of the
+        destinations that evaluated Eq. 1 that day."""
+        days = self.day if days is None else days
+        g = np.zeros(days, np.uint64)
+        _check(lib().deabm_get_gathered(self.ctx, days, _p(g)), self.ctx)
+        return g
 
     def save(self) -> dict:
         """A checkpoint: the state at the start of the next day to run ([N, B] or

@@ -44,7 +44,7 @@ def compare_days(pop, params, T, state=None, seed_ids="pop", check_lambda=True):
     g = gpu_sim(pop, params, keep_lambda=check_lambda, state=state, seed_ids=seed_ids, max_steps=max(T, 1))
     g2 = gpu_sim(pop, params, keep_lambda=False, state=state, seed_ids=seed_ids, max_steps=max(T, 1)) \
         if check_lambda else None
-    report = dict(days=0, flips=0, max_rel_lambda64=0.0, new_inf=[], messages=[])
+    report = dict(days=0, flips=0, max_rel_lambda64=0.0, new_inf=[], messages=[], messages_sus=[])
     try:
         s0 = g.state()
         for k in STATE_KEYS:
@@ -84,12 +84,19 @@ def compare_days(pop, params, T, state=None, seed_ids="pop", check_lambda=True):
             report["days"] = t + 1
             report["new_inf"].append(d["new_inf"])
             report["messages"].append(d["messages"])
+            report["messages_sus"].append(d["messages_sus"])
         ni, h, m = g.counters(T)
         assert ni[:, 0].tolist() == report["new_inf"]
         assert m.astype(np.int64).tolist() == report["messages"]
+        # messages gathered: every destination when lambda is kept (or with exposure
+        # notification), else only the destinations susceptible at the start of the day
+        gath = g.gathered(T).astype(np.int64).tolist()
+        assert gath == report["messages"], "gathered messages with lambda kept"
         if g2 is not None:
             ni2, h2, m2 = g2.counters(T)
             assert np.array_equal(ni2, ni) and np.array_equal(h2, h) and np.array_equal(m2, m)
+            want = report["messages"] if params.get("den_on") else report["messages_sus"]
+            assert g2.gathered(T).astype(np.int64).tolist() == want, "gathered messages"
         if params.get("den_on"):
             assert g.notified(T).tolist() == osim.den_notified[:T]
             report["notified"] = osim.den_notified[:T]

@@ -109,8 +109,10 @@ def test_calibration_steps_match_oracle_adam_on_oracle_gradients(case):
     the oracle's FP64 reverse sweep from the same start.  The GPU gradient is
     within 1e-4 of the gradient's norm, and Adam normalises each coordinate, so
     where the oracle's gradient coordinates stay well clear of 0 every step the
-    parameters agree within 2e-3 of the total step (lr per step); the loss trace
-    within 1e-4 relative."""
+    parameters agree within 2e-3 of the total step (lr per step).  The loss trace
+    agrees within 1e-4 of the starting loss: as the fit improves the loss shrinks
+    towards the FP32 rounding of the incidence it is made of, so its error is
+    bounded in absolute terms, not relative to itself."""
     from oracle.adam import Adam
     pop, p, T, rx, th, y = case
     steps, lr = 6, 0.02
@@ -119,9 +121,11 @@ def test_calibration_steps_match_oracle_adam_on_oracle_gradients(case):
     g.close()
     opt = Adam(13, lr, nonneg=True)
     ref = np.float32(th).astype(np.float64)
+    loss0 = None
     for it in range(steps):
         o = rx.run(ref, T, target=y.astype(np.float64), grad=True)
-        assert abs(trace[it] - o["loss"]) <= 1e-4 * o["loss"], (it, trace[it], o["loss"])
+        loss0 = o["loss"] if loss0 is None else loss0
+        assert abs(trace[it] - o["loss"]) <= 1e-4 * loss0, (it, trace[it], o["loss"])
         gr = o["grad"]
         assert np.min(np.abs(gr)) > 1e-2 * np.linalg.norm(gr), (it, gr)
         ref = opt.step(ref, gr)

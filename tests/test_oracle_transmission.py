@@ -165,3 +165,23 @@ def test_random_network_term_uses_the_days_contacts():
     # messages = static in-edges + random in-contacts
     assert d["messages"] == int(pop["row_ptr"][0][-1]) + int(pop["row_ptr"][1][-1]) + int(d["rand_k"].sum())
     del st0
+
+
+def test_messages_of_susceptible_destinations(oracle_lib):
+    """The oracle's messages_sus counts exactly the in-edges (stored rows, the day's
+    random contacts) of the agents susceptible at the start of the day."""
+    import oracle
+    from paper_2110_04421_gb300 import workloads as W
+    pop = W.population(3000, 4, 40)
+    p = W.params_with(R=5.0, seed=3, net_seed=4)
+    sim = oracle.Sim(pop, p, pop["age"], pop["seed_ids"])
+    deg = sum(np.diff(rp.astype(np.int64)) for rp in pop["row_ptr"])
+    seen_partial = False
+    for _ in range(15):
+        sus = sim.state.stage == 0
+        d = sim.step(diag=True)
+        want = int((deg[sus] + d["rand_k"][sus].astype(np.int64)).sum())
+        assert d["messages_sus"] == want
+        assert d["messages"] == int((deg + d["rand_k"].astype(np.int64)).sum())
+        seen_partial |= 0 < d["messages_sus"] < d["messages"]
+    assert seen_partial
