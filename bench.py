@@ -406,6 +406,7 @@ def run_surrogate(args):
         step_ms = timed(lambda: m.train_step(x, y, 1e-4))
         m.use_tcgen05(False)
         fwd_mma_ms = timed(lambda: m.forward(x, out))
+        step_mma_ms = timed(lambda: m.train_step(x, y, 1e-4))
         params_now = m.get_params()
     m.close()
     cpu = None
@@ -419,7 +420,10 @@ def run_surrogate(args):
     fwd_tf = f * B / (fwd_ms / 1e3) / 1e12
     train_tf = 3 * f * B / (step_ms / 1e3) / 1e12
     return {"workload": w["name"] + f", batch {B}", "forward_ms": fwd_ms, "train_step_ms": step_ms,
-            "forward_ms_mma_sync_path": fwd_mma_ms, "samples_per_s": B / (fwd_ms / 1e3), "flops_per_sample_forward": f,
+            "forward_ms_mma_sync_path": fwd_mma_ms, "train_step_ms_mma_sync_path": step_mma_ms,
+            "train_step_note": "forward keeping activations + input and weight gradients on tcgen05 GEMMs, "
+                               "bias gradients, Adam; 3 x forward FLOPs counted",
+            "samples_per_s": B / (fwd_ms / 1e3), "flops_per_sample_forward": f,
             "cpu_baseline": cpu,
             "l2": "flushed before every timed call (write of twice its size)",
             "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,

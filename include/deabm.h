@@ -103,7 +103,23 @@ typedef struct deabm_ctx deabm_ctx;
  * stored networks and before the random network, so n_nets must be <= 3.
  * Only plain and batched contexts take them (deabm_create, deabm_create_batch);
  * the other constructors reject n_occ > 0.  n_occ = 0: occ_group and occ_k are
- * ignored. */
+ * ignored. *
+ * rand_ws = 1 replaces the Poisson contacts by the paper's form of the global
+ * random network (Sec. 3 "Interaction Networks": one small-world Watts-Strogatz
+ * graph, re-initialised every step; rand_mean is then ignored).  The ring
+ * lattice runs over all agents in caller-id order; agent i owns the undirected
+ * edges to (i + m) mod n_agents, m = 1..rand_ws_k/2.  Every day each owned edge
+ * is rewired when word 2((m-1)%2) of block (m-1)/2 of Philox stream 10, keyed by
+ * (net_seed, day, i), is below floor(rand_ws_beta 2^32), or when i + m wraps
+ * onto i: its far end becomes agent floor(w (n-1) / 2^32), skipping i, w = word
+ * 2((m-1)%2)+1 of that block.  A rewired edge leaves its lattice end and reaches
+ * the new one, and both ends receive each other's messages.  Agent j's messages
+ * are summed in this order: its own edges m = 1..k/2, the unrewired lattice
+ * edges of agents j - m, m = 1..k/2, then the rewired edges that landed on j by
+ * owner ascending and m ascending.  Plain contexts only (one replicate, no
+ * exposure notification, not in ragged batches); the day's graph is built on the
+ * device before each day kernel (three small kernels and a prefix sum).
+ */
 typedef struct {
     uint32_t n_agents;
     uint32_t n_nets;
@@ -115,6 +131,9 @@ typedef struct {
     const uint8_t *occ_k;
     uint32_t occ_lattice; /* 0: as above; 1: Watts-Strogatz (see below) */
     float occ_rewire;     /* occ_lattice = 1: rewiring probability, 0..1 */
+    uint32_t rand_ws;     /* 1: the random network is a daily Watts-Strogatz graph (see below) */
+    uint32_t rand_ws_k;   /* rand_ws = 1: lattice neighbours, even, 2..16 */
+    float rand_ws_beta;   /* rand_ws = 1: daily rewiring probability, 0..1 */
 } deabm_graph;
 
 /* Agents (Sec. 3 "Agent State Definition"); all host arrays of n_agents entries.
@@ -454,7 +473,13 @@ int deabm_mlp_forward(deabm_mlp *mlp, const float *x, uint32_t batch, float *y);
  * *available (may be NULL) tells whether the fused path applies to this shape. */
 int deabm_mlp_use_tcgen05(deabm_mlp *mlp, int enable, int *available);
 /* Loss (1/(batch n_out)) sum (MLP(x) - y)^2 and its gradients (kept in the
- * context, read with deabm_mlp_get_params); loss -> host float, may be NULL. */
+ * context, read with deabm_mlp_get_params); loss -> host float, may be NULL.
+ * On the fused-forward shapes (see deabm_mlp_forward) and with tcgen05 enabled,
+ * the forward pass that keeps its activations, the input gradients and the
+ * weight gradients are GEMMs on the tcgen05 tensor cores (TMA operand tiles,
+ * TMEM accumulators; weight gradients split over the batch and summed in a fixed
+ * order); otherwise the per-layer mma.sync GEMMs.  A bounded wait that gave up
+ * is reported by the next deabm_mlp_sync as DEABM_ETIMEOUT. */
 int deabm_mlp_grad(deabm_mlp *mlp, const float *x, const float *y, uint32_t batch, float *loss);
 /* deabm_mlp_grad, then one Adam step (beta 0.9 / 0.999, eps 1e-8) with rate lr.
  * loss (host, may be NULL: no synchronisation) is the loss before the step. */
@@ -468,6 +493,14 @@ int deabm_mlp_train_step(deabm_mlp *mlp, const float *x, const float *y, uint32_
  * deabm_mlp_grad followed by this step.  Returns DEABM_OK, DEABM_EINVAL (NULL,
  * lr not finite and > 0), DEABM_ECUDA. */
 int deabm_mlp_apply_grads(deabm_mlp *mlp, const float *grads, uint32_t on_device, float lr);
+/* Bound of every wait inside the tcgen05 kernels (on a copy or an MMA landing):
+ * `polls` potentially blocking tries, 2^26 by default (0 restores it); 1 = one
+ * non-blocking test, so a wait that is not already satisfied gives up at once.  A
+ * kernel whose wait gave up records it, waits (with the default bound) for the
+ * copies and MMAs it had started, frees its Tensor Memory and returns; the next
+ * deabm_mlp_sync reports DEABM_ETIMEOUT and the context stays usable.  Returns
+ * DEABM_OK, DEABM_EINVAL (NULL). */
+int deabm_mlp_set_wait_limit(deabm_mlp *mlp, uint32_t polls);
 /* Wait for the MLP's queued work; DEABM_ETIMEOUT if a bounded device wait gave up. */
 int deabm_mlp_sync(deabm_mlp *mlp);
 const char *deabm_mlp_last_error(void);

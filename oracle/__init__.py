@@ -85,6 +85,7 @@ class _Model(C.Structure):
         ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_float),
         ("den_on", C.c_uint32), ("den_adoption", C.c_double), ("den_compliance", C.c_double),
         ("den_window", C.c_uint32),
+        ("rand_ws", C.c_uint32), ("rand_ws_k", C.c_uint32), ("rand_ws_beta", C.c_double),
     ]
 
 
@@ -143,6 +144,8 @@ def lib():
             L.rx_classes.argtypes = [C.POINTER(_RxModel), vp, vp]
             L.rx_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
             L.rx_noise.restype = C.c_double
+            L.or_wsg_neighbours.argtypes = [C.POINTER(_Model), C.c_uint32, vp, vp, C.c_uint32]
+            L.or_wsg_neighbours.restype = C.c_int
             L.or_set_threads.argtypes = [C.c_int]
             L.or_set_threads.restype = C.c_int
             _lib = L
@@ -259,8 +262,23 @@ class Model:
             m.occ_k = ok.ctypes.data
             m.occ_lattice = int(graph.get("occ_lattice", 0))
             m.occ_rewire = float(graph.get("occ_rewire", 0.0))
+        if graph.get("rand_ws"):  # the global random network as a daily Watts-Strogatz graph
+            m.rand_ws = 1
+            m.rand_ws_k = int(graph.get("rand_ws_k", 2))
+            m.rand_ws_beta = float(graph.get("rand_ws_beta", 0.5))
         self.m = m
         self.params = P
+
+    def ws_neighbours(self, step: int):
+        """The Watts-Strogatz random network of `step`: (start[n+1], neighbours) with
+        agent j's neighbours, in summation order, at neighbours[start[j]:start[j+1]]."""
+        n, k = self.n, int(self.m.rand_ws_k)
+        start = np.zeros(n + 1, np.uint32)
+        cap = 2 * k * n + 64
+        nb = np.zeros(cap, np.uint32)
+        if lib().or_wsg_neighbours(C.byref(self.m), step, _ptr(start), _ptr(nb), cap) != 0:
+            raise ValueError("no Watts-Strogatz random network in this model")
+        return start, nb[:start[-1]].copy()
 
     def occ_contacts(self, j: int, step: int) -> np.ndarray:
         """The daily occupation network's in-contacts of agent j on `step`."""

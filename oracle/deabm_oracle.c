@@ -73,6 +73,8 @@ enum {
 #define SM_VAX 7u     /* x: vaccine response (step word fixed at 0) */
 #define SM_GUMBEL 8u  /* relaxed draw noise */
 #define SM_WS 9u      /* Watts-Strogatz occupation contacts: block e/2, lanes 2(e%2), 2(e%2)+1 = rewire coin, place */
+#define SM_WSG 10u    /* Watts-Strogatz global random network: edge m of agent i in block (m-1)/2, lanes
+                         2((m-1)%2), 2((m-1)%2)+1 = rewire coin, new far end */
 
 typedef struct {
     uint32_t n, n_nets;
@@ -107,6 +109,11 @@ typedef struct {
     uint32_t den_on;
     double den_adoption, den_compliance;
     uint32_t den_window;       /* steps of contacts looked back over, >= 1 */
+    /* the global random network as a Watts-Strogatz graph re-initialised every
+     * step (Sec. 3, Interaction Networks) instead of the Poisson contacts:
+     * rand_ws_k lattice neighbours (even, 2..16), rewiring probability rand_ws_beta */
+    uint32_t rand_ws, rand_ws_k;
+    double rand_ws_beta;
 } or_model;
 
 /* ------------------------------------------------------------------------- */
@@ -292,6 +299,135 @@ uint32_t or_random_contacts(uint64_t net_seed, uint32_t n, uint32_t j, uint32_t 
 }
 
 /* ------------------------------------------------------------------------- */
+/* The global random network as a Watts-Strogatz graph (Watts and Strogatz 1998),
+ * re-initialised every step (Sec. 3, Interaction Networks).  The ring lattice
+ * runs over all agents in id order; agent i owns the edges to the next h = k/2
+ * agents, edge m joining i and (i + m) mod n (m = 1..h).  Every step each owned
+ * edge is rewired with probability beta (always when i + m wraps onto i): its far
+ * end moves to an agent drawn uniformly from the other n - 1.  Edges are
+ * undirected, so a rewired edge leaves the old far end and reaches the new one,
+ * and both ends of every edge receive each other's messages.  Agent j's
+ * neighbours, in the order their messages are summed: its own edges m = 1..h
+ * (the far end, new or lattice); the lattice edges m = 1..h of agent j - m that
+ * were not rewired; the rewired edges that landed on j, by owner ascending, then m. */
+typedef struct {
+    uint32_t h;
+    uint8_t *rew;      /* [n*h] edge (i, m) rewired this step */
+    uint32_t *far;     /* [n*h] far end of edge (i, m) */
+    uint32_t *start;   /* [n+1] first landing edge of each agent */
+    uint32_t *land;    /* owners of the landing edges, grouped by the agent they landed on */
+} or_wsg;
+
+static void wsg_build(const or_model *m, uint32_t t, or_wsg *g)
+{
+    const uint32_t n = m->n, h = m->rand_ws_k / 2u;
+    g->h = h;
+    g->rew = (uint8_t *)calloc((size_t)n * h + 1u, 1);
+    g->far = (uint32_t *)calloc((size_t)n * h + 1u, sizeof(uint32_t));
+    g->start = (uint32_t *)calloc((size_t)n + 1u, sizeof(uint32_t));
+    for (uint32_t i = 0; i < n; ++i) {
+        for (uint32_t e = 1; e <= h; ++e) {
+            uint32_t w[4];
+            draw4(m->net_seed, i, t, SM_WSG, (e - 1u) / 2u, w);
+            const uint32_t coin = w[2u * ((e - 1u) % 2u)], word = w[2u * ((e - 1u) % 2u) + 1u];
+            const size_t q = (size_t)i * h + (e - 1u);
+            if (e % n == 0u || happens(coin, m->rand_ws_beta)) {
+                uint32_t v = (uint32_t)(((uint64_t)word * (uint64_t)(n - 1u)) >> 32);
+                if (v >= i) v += 1u;
+                g->rew[q] = 1;
+                g->far[q] = v;
+                g->start[v + 1u]++;
+            } else {
+                g->far[q] = (uint32_t)(((uint64_t)i + e) % n);
+            }
+        }
+    }
+    for (uint32_t j = 0; j < n; ++j) g->start[j + 1u] += g->start[j];
+    g->land = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)g->start[n] + 1u));
+    uint32_t *fill = (uint32_t *)calloc((size_t)n + 1u, sizeof(uint32_t));
+    for (uint32_t i = 0; i < n; ++i) /* owners ascending, then m: each group comes out sorted */
+        for (uint32_t e = 1; e <= h; ++e) {
+            const size_t q = (size_t)i * h + (e - 1u);
+            if (g->rew[q]) {
+                const uint32_t v = g->far[q];
+                g->land[g->start[v] + fill[v]++] = i;
+            }
+        }
+    free(fill);
+}
+
+static void wsg_free(or_wsg *g) { free(g->rew); free(g->far); free(g->start); free(g->land); }
+
+/* agent j's neighbours this step, in summation order; returns their number */
+static uint32_t wsg_neighbours(const or_model *m, const or_wsg *g, uint32_t j, uint32_t *out)
+{
+    const uint32_t n = m->n, h = g->h;
+    uint32_t k = 0;
+    for (uint32_t e = 1; e <= h; ++e) out[k++] = g->far[(size_t)j * h + (e - 1u)];
+    for (uint32_t e = 1; e <= h; ++e) {
+        const uint32_t i = (uint32_t)(((uint64_t)j + (uint64_t)n - (e % n)) % n);
+        if (!g->rew[(size_t)i * h + (e - 1u)]) out[k++] = i;
+    }
+    for (uint32_t q = g->start[j]; q < g->start[j + 1u]; ++q) out[k++] = g->land[q];
+    return k;
+}
+
+/* the sums of inf over agent j's neighbours in summation order (FP32 left to
+ * right from +0, FP64 alongside); returns their number */
+static uint32_t wsg_sum(const or_model *m, const or_wsg *g, uint32_t j, const float *inf32, const double *inf64,
+                        float *r32, double *r64)
+{
+    const uint32_t n = m->n, h = g->h;
+    uint32_t k = 0;
+    float s32 = 0.0f;
+    double s64 = 0.0;
+    for (uint32_t e = 1; e <= h; ++e) {
+        const uint32_t v = g->far[(size_t)j * h + (e - 1u)];
+        s32 = s32 + inf32[v];
+        s64 = s64 + inf64[v];
+        ++k;
+    }
+    for (uint32_t e = 1; e <= h; ++e) {
+        const uint32_t i = (uint32_t)(((uint64_t)j + (uint64_t)n - (e % n)) % n);
+        if (!g->rew[(size_t)i * h + (e - 1u)]) {
+            s32 = s32 + inf32[i];
+            s64 = s64 + inf64[i];
+            ++k;
+        }
+    }
+    for (uint32_t q = g->start[j]; q < g->start[j + 1u]; ++q) {
+        s32 = s32 + inf32[g->land[q]];
+        s64 = s64 + inf64[g->land[q]];
+        ++k;
+    }
+    *r32 = s32;
+    *r64 = s64;
+    return k;
+}
+
+/* the neighbour lists of one step for the tests: start[n+1], nb[start[n]] */
+int or_wsg_neighbours(const or_model *m, uint32_t t, uint32_t *start, uint32_t *nb, uint32_t cap)
+{
+    if (!m->rand_ws || m->rand_ws_k < 2u || m->rand_ws_k > 16u || m->rand_ws_k % 2u || m->n < 2u) return -1;
+    or_wsg g;
+    wsg_build(m, t, &g);
+    uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)m->rand_ws_k + g.start[m->n] + 1u));
+    uint32_t off = 0;
+    int rc = 0;
+    start[0] = 0;
+    for (uint32_t j = 0; j < m->n; ++j) {
+        const uint32_t k = wsg_neighbours(m, &g, j, tmp);
+        if (off + k > cap) { rc = -1; break; }
+        memcpy(nb + off, tmp, sizeof(uint32_t) * k);
+        off += k;
+        start[j + 1] = off;
+    }
+    free(tmp);
+    wsg_free(&g);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* static vaccination schedule: priority = age bin descending, then id ascending;
  * Q = floor(rate * N) first doses a day from vax_start; day1 = start + rank / Q.
  * Agents that the campaign never reaches get 0x7FFF. */
@@ -367,6 +503,9 @@ static int check_model(const or_model *m)
     if (m->inf_len == 0 || m->inf_len > OR_MAX_INF_LEN || m->n_nets > OR_MAX_NETS) return -1;
     if (m->quar_days > 15 || m->test_hi > 7 || m->test_lo < 1 || m->test_lo > m->test_hi) return -1;
     if (m->rand_mean > 0.0f && m->n < 2) return -1;
+    if (m->rand_ws && (m->rand_ws_k < 2u || m->rand_ws_k > 16u || m->rand_ws_k % 2u || m->n < 2u || m->den_on ||
+                       !(m->rand_ws_beta >= 0.0 && m->rand_ws_beta <= 1.0)))
+        return -1;
     if (m->vax_strategy > 3 || m->elderly_bin > 9) return -1;
     if (m->den_on && (!m->test_on || m->den_window < 1 || m->den_window > 64)) return -1;
     if (m->n_occ) {
@@ -568,6 +707,8 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
     int32_t n_new = 0;
     or_occ occ = {NULL, NULL, NULL};
     if (m->n_occ) occ_build(m, &occ);
+    or_wsg wsg = {0, NULL, NULL, NULL, NULL};
+    if (m->rand_ws) wsg_build(m, t, &wsg);
 #pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : messages, messages_sus, n_new)
     for (uint32_t j = 0; j < n; ++j) {
         const int64_t messages_before = messages;
@@ -598,7 +739,15 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             messages += ko;
         }
         uint32_t k = 0;
-        if (m->rand_mean > 0.0f) {
+        if (m->rand_ws) {
+            float r32;
+            double r64;
+            k = wsg_sum(m, &wsg, j, inf32, inf64, &r32, &r64);
+            float term = m->B_rand * r32;
+            s32 = (m->n_nets == 0 && m->n_occ == 0) ? term : s32 + term;
+            s64 += (double)m->B_rand * r64;
+            messages += k;
+        } else if (m->rand_mean > 0.0f) {
             k = random_contacts(m->net_seed, n, j, t, tb->pois, contacts);
             float r32 = 0.0f;
             double r64 = 0.0;
@@ -782,6 +931,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
         for (uint32_t j = 0; j < n; ++j) dg->hist[(int)stage[j]]++;
     }
     if (m->n_occ) occ_free(&occ);
+    if (m->rand_ws) wsg_free(&wsg);
     free(inf32); free(inf64); free(newinf); free(dose_today);
     return 0;
 }

@@ -49,6 +49,8 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
                                 const uint32_t *orig2new, uint32_t n, uint32_t *rp_new, uint32_t *col_new,
                                 uint32_t *scratch, cudaStream_t stream);
 size_t scan_scratch_words(size_t m);
+// in-place inclusive prefix sum of m words (scratch of scan_scratch_words(m) words)
+cudaError_t launch_scan_inclusive(uint32_t *a, size_t m, uint32_t *scratch, cudaStream_t stream);
 // new2orig[q] = the agent at internal row q: agents by ascending label (labels
 // < n), ids ascending among equal labels.  label is overwritten; scratch of
 // order_scratch_words(n) words.

@@ -277,6 +277,64 @@ __global__ void weights_to_bf16_kernel(const float *w, int rows, int cols, int r
     }
 }
 
+// tensor-core training path: x -> a_0 (BF16 [rows x ld], zero-padded) and its
+// transpose a_0^T [ld x ldt]
+__global__ void to_bf16_pad_t_kernel(const float *x, int rows, int cols, int ld, __nv_bfloat16 *out,
+                                     __nv_bfloat16 *outt, int ldt)
+{
+    const long n = (long)rows * ld;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / ld), c = (int)(q % ld);
+        const __nv_bfloat16 v = __float2bfloat16(c < cols ? x[(long)r * cols + c] : 0.0f);
+        out[q] = v;
+        outt[(long)c * ldt + r] = v;
+    }
+}
+
+// dz_L = 2 (y_hat - y) / (B n_out) in FP32 [rows x cols], its BF16 copy with row
+// stride ldb and its BF16 transpose [cols x ldt], and the loss (block partials)
+__global__ void mse_grad_t_kernel(const float *yhat, const float *y, int rows, int cols, float scale, float *dz,
+                                  __nv_bfloat16 *dzb, int ldb, __nv_bfloat16 *dzt, int ldt, double *loss_part)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    const long n = (long)rows * cols;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / cols), c = (int)(q % cols);
+        const float d = yhat[q] - y[q];
+        acc += (double)d * d;
+        const float gq = 2.0f * d * scale;
+        dz[q] = gq;
+        const __nv_bfloat16 b = __float2bfloat16(gq);
+        dzb[(long)r * ldb + c] = b;
+        dzt[(long)c * ldt + r] = b;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// BF16 weight copies of the tensor-core training path: W [fi x ldf] (the input
+// gradients' operand, K = fan-out) and W^T [fo x ldt] (the forward operand,
+// K = fan-in), zero in the padding
+__global__ void weights_tc_kernel(const float *w, int fi, int fo, __nv_bfloat16 *wf, int ldf, __nv_bfloat16 *wt, int ldt)
+{
+    const long n = (long)fi * ldf;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / ldf), c = (int)(q % ldf);
+        wf[q] = __float2bfloat16(c < fo ? w[(long)r * fo + c] : 0.0f);
+    }
+    const long nt = (long)fo * ldt;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nt; q += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / ldt), c = (int)(q % ldt);
+        wt[q] = __float2bfloat16(c < fi ? w[(long)c * fo + r] : 0.0f);
+    }
+}
+
 }  // namespace mlpk
 
 using namespace mlpk;
@@ -301,7 +359,17 @@ struct deabm_mlp {
     std::vector<__nv_bfloat16 *> Wt;
     std::vector<int> tcK, tcN;
     int *tc_err = nullptr;
+    // tensor-core training path: transposed activations a_l^T [kpad_l x bpad],
+    // BF16 output gradients row-major [B x ld8] and transposed [width x bpad],
+    // BF16 weights W_l [fi x ld8(fo)] and W_l^T [fo x ld8(fi)]
+    bool tr_ok = false, tr_dirty = true;
+    int bpad = 0, ldg = 0;
+    std::vector<__nv_bfloat16 *> actT, Wf, WT;
+    __nv_bfloat16 *gb16[2] = {nullptr, nullptr}, *gT[2] = {nullptr, nullptr};
+    uint32_t polls = 1u << 26;
 };
+
+static int ld8(int v) { return (v + 7) / 8 * 8; }
 
 static thread_local std::string g_mlp_err;
 
@@ -443,6 +511,23 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
             }
             if ((r = m_alloc(m, &m->tc_err, 1))) return r;
             MCU(cudaMemsetAsync(m->tc_err, 0, sizeof(int), m->stream));
+            // the training path on the same tensor cores
+            m->tr_ok = true;
+            m->bpad = ld8((int)max_batch);
+            m->ldg = ld8(std::max(m->H, m->n_out));
+            for (int l = 0; l < m->L; ++l) {
+                __nv_bfloat16 *at, *wf, *wt;
+                if ((r = m_alloc(m, &at, (size_t)m->kpad[l] * m->bpad))) return r;
+                if ((r = m_alloc(m, &wf, (size_t)m->fin[l] * ld8(m->fout[l])))) return r;
+                if ((r = m_alloc(m, &wt, (size_t)m->fout[l] * ld8(m->kpad[l])))) return r;
+                m->actT.push_back(at);
+                m->Wf.push_back(wf);
+                m->WT.push_back(wt);
+            }
+            for (int q = 0; q < 2; ++q) {
+                if ((r = m_alloc(m, &m->gb16[q], B * m->ldg))) return r;
+                if ((r = m_alloc(m, &m->gT[q], (size_t)m->ldg * m->bpad))) return r;
+            }
         }
         MCU(cudaStreamSynchronize(m->stream));
         return DEABM_OK;
@@ -487,6 +572,7 @@ extern "C" int deabm_mlp_set_params(deabm_mlp *m, const float *params)
     }
     m->step = 0;
     m->wt_dirty = true;
+    m->tr_dirty = true;
     MCU(cudaGetLastError());
     MCU(cudaStreamSynchronize(m->stream));
     return DEABM_OK;
@@ -638,6 +724,7 @@ extern "C" int deabm_mlp_forward(deabm_mlp *m, const float *x, uint32_t batch, f
         g.N[l] = m->tcN[l];
     }
     g.err = m->tc_err;
+    g.polls = m->polls;
     MCU(mlptc_forward(g, m->stream));
     return DEABM_OK;
 }
@@ -650,10 +737,124 @@ extern "C" int deabm_mlp_use_tcgen05(deabm_mlp *m, int enable, int *available)
     return DEABM_OK;
 }
 
+// forward (keeping z_l, a_l and a_l^T) and backward of one batch on the tcgen05
+// GEMMs (mlp_tc_gemm.cu); same quantities and rounding points as the mma.sync path
+static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, float *loss_host)
+{
+    cudaStream_t s = m->stream;
+    if (m->tr_dirty) {
+        for (int l = 0; l < m->L; ++l)
+            weights_tc_kernel<<<256, 256, 0, s>>>(m->W[l], m->fin[l], m->fout[l], m->Wf[l], ld8(m->fout[l]), m->WT[l],
+                                                   ld8(m->kpad[l]));
+        MCU(cudaGetLastError());
+        m->tr_dirty = false;
+    }
+    to_bf16_pad_t_kernel<<<512, 256, 0, s>>>(x, batch, m->n_in, m->k_in, m->act[0], m->actT[0], m->bpad);
+    MCU(cudaGetLastError());
+    for (int l = 0; l < m->L; ++l) {
+        TcGemm g{};
+        g.A = m->act[l];
+        g.lda = m->kpad[l];
+        g.B = m->WT[l];
+        g.ldb = ld8(m->kpad[l]);
+        g.M = batch;
+        g.N = m->fout[l];
+        g.K = m->kpad[l];
+        g.kps = (g.K + 63) / 64 * 64;
+        g.bias = m->b[l];
+        g.polls = m->polls;
+        g.err = m->tc_err;
+        if (l < m->L - 1) {
+            g.epi = TC_EPI_HIDDEN;
+            g.outf = m->z[l];
+            g.ldf = m->H;
+            g.outb = m->act[l + 1];
+            g.ldo = m->kpad[l + 1];
+            g.outt = m->actT[l + 1];
+            g.ldt = m->bpad;
+        } else {
+            g.epi = TC_EPI_OUTPUT;
+            g.outf = m->yhat;
+            g.ldf = m->n_out;
+        }
+        MCU(mlptc_gemm(g, s));
+    }
+    const long n = (long)batch * m->n_out;
+    const int nparts = 256;
+    int cur = 0;
+    mse_grad_t_kernel<<<nparts, 256, 0, s>>>(m->yhat, y, batch, m->n_out, 1.0f / (float)n, m->dz, m->gb16[cur], m->ldg,
+                                             m->gT[cur], m->bpad, m->loss_part);
+    loss_reduce_kernel<<<1, 32, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
+    MCU(cudaGetLastError());
+    float *dz = m->dz, *dzo = m->dz2;
+    for (int l = m->L - 1; l >= 0; --l) {
+        const int fo = m->fout[l], fi = m->fin[l];
+        // dW_l = a_l^T dz_l, split over the batch, partials summed in split order
+        TcGemm gw{};
+        gw.A = m->actT[l];
+        gw.lda = m->bpad;
+        gw.B = m->gT[cur];
+        gw.ldb = m->bpad;
+        gw.M = fi;
+        gw.N = fo;
+        gw.K = batch;
+        const int tiles = ((fi + 127) / 128) * ((fo + 255) / 256);
+        int splits = std::max(1, std::min(m->max_splits, 2 * 152 / tiles));
+        splits = std::min(splits, (batch + 63) / 64);
+        gw.kps = ((batch + splits - 1) / splits + 63) / 64 * 64;
+        splits = (batch + gw.kps - 1) / gw.kps;
+        gw.epi = TC_EPI_WGRAD;
+        gw.outf = splits > 1 ? m->wpart : m->gW[l];
+        gw.ldf = fo;
+        gw.polls = m->polls;
+        gw.err = m->tc_err;
+        MCU(mlptc_gemm(gw, s));
+        if (splits > 1) {
+            splitk_reduce_kernel<<<256, 256, 0, s>>>(m->wpart, splits, (long)fi * fo, m->gW[l]);
+            MCU(cudaGetLastError());
+        }
+        colsum_partial_kernel<<<dim3((fo + 31) / 32, kColChunks), 256, 0, s>>>(dz, batch, fo, m->wpart);
+        colsum_final_kernel<<<(fo + 127) / 128, 128, 0, s>>>(m->wpart, fo, m->gb[l]);
+        MCU(cudaGetLastError());
+        if (l > 0) {
+            // dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})
+            TcGemm gd{};
+            gd.A = m->gb16[cur];
+            gd.lda = m->ldg;
+            gd.B = m->Wf[l];
+            gd.ldb = ld8(fo);
+            gd.M = batch;
+            gd.N = m->H;
+            gd.K = fo;
+            gd.kps = (fo + 63) / 64 * 64;
+            gd.epi = TC_EPI_DGRAD;
+            gd.zin = m->z[l - 1];
+            gd.ldz = m->H;
+            gd.outf = dzo;
+            gd.ldf = m->H;
+            gd.outb = m->gb16[cur ^ 1];
+            gd.ldo = m->ldg;
+            gd.outt = m->gT[cur ^ 1];
+            gd.ldt = m->bpad;
+            gd.polls = m->polls;
+            gd.err = m->tc_err;
+            MCU(mlptc_gemm(gd, s));
+            std::swap(dz, dzo);
+            cur ^= 1;
+        }
+    }
+    if (loss_host) {
+        MCU(cudaMemcpyAsync(loss_host, m->loss, 4, cudaMemcpyDeviceToHost, s));
+        MCU(cudaStreamSynchronize(s));
+    }
+    return DEABM_OK;
+}
+
 extern "C" int deabm_mlp_grad(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float *loss)
 {
     if (!m || !x || !y) return mlp_fail(DEABM_EINVAL, "NULL argument");
     if (batch == 0 || (int)batch > m->max_batch) return mlp_fail(DEABM_EINVAL, "batch must be in 1..max_batch");
+    if (m->tr_ok && m->tc_on) return mlp_grad_tc(m, x, y, (int)batch, loss);
     int r;
     if ((r = mlp_forward_dev(m, x, (int)batch, m->yhat, true))) return r;
     return mlp_backward_dev(m, y, (int)batch, loss);
@@ -665,6 +866,7 @@ static int mlp_adam(deabm_mlp *m, float lr)
 {
     m->step += 1;
     m->wt_dirty = true;
+    m->tr_dirty = true;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     for (int l = 0; l < m->L; ++l) {
@@ -706,6 +908,13 @@ extern "C" int deabm_mlp_apply_grads(deabm_mlp *m, const float *grads, uint32_t 
     int r;
     if ((r = mlp_adam(m, lr))) return r;
     if (!on_device) MCU(cudaStreamSynchronize(m->stream));  // the host buffer may be reused on return
+    return DEABM_OK;
+}
+
+extern "C" int deabm_mlp_set_wait_limit(deabm_mlp *m, uint32_t polls)
+{
+    if (!m) return mlp_fail(DEABM_EINVAL, "NULL argument");
+    m->polls = polls ? polls : (1u << 26);
     return DEABM_OK;
 }
 

@@ -66,9 +66,20 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+// polls <= 1: one non-blocking test (mbarrier.test_wait)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t polls)
 {
-    for (uint32_t it = 0; it < kMaxWaitPolls; ++it) {
+    if (polls <= 1u) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        return done != 0;
+    }
+    for (uint32_t it = 0; it < polls; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -174,14 +185,14 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_forward_tc_kernel(const Fused
             const uint32_t idesc = idesc_bf16(kRows, N);
             const uint32_t a_base0 = smem_u32(sA);
             for (uint32_t c = 0; c < nch; ++c, ++gchunk) {
-                if (!mbar_wait(mw, gchunk & 1u)) { s_abort = 1; break; }  // chunk in shared memory
+                if (!mbar_wait(mw, gchunk & 1u, g.polls)) { s_abort = 1; break; }  // chunk in shared memory
                 tc_fence_after();
 #pragma unroll
                 for (uint32_t kk = 0; kk < 4; ++kk)
                     mma_bf16(tmem, sw128_desc(a_base0 + c * kAChunkBytes + kk * 32u), sw128_desc(sB_addr + kk * 32u),
                              idesc, (c > 0 || kk > 0) ? 1u : 0u);
                 mma_commit(mm);
-                if (!mbar_wait(mm, gchunk & 1u)) { s_abort = 1; break; }  // buffer free again
+                if (!mbar_wait(mm, gchunk & 1u, g.polls)) { s_abort = 2; break; }  // buffer free again
                 woff += (size_t)N * 128u;
                 // next chunk: this layer's, or the first of the next layer (overlaps the epilogue)
                 if (c + 1 < nch) bulk_load(sB_addr, (const unsigned char *)g.wimg + woff, N * 128u, mw);
@@ -229,7 +240,10 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_forward_tc_kernel(const Fused
     }
     if (!ok && tid == 0) {
         atomicExch(g.err, 1);
-        (void)mbar_wait(mw, gchunk & 1u);  // a copy may still be in flight: give it a bounded chance to land
+        // what the gave-up wait was waiting for is still in flight: the chunk's copy,
+        // or its MMAs; let it land (long fixed bound) before TMEM and the buffers go
+        if (s_abort == 1) (void)mbar_wait(mw, gchunk & 1u, kMaxWaitPolls);
+        else (void)mbar_wait(mm, gchunk & 1u, kMaxWaitPolls);
     }
     tc_fence_before();
     __syncthreads();

@@ -1,0 +1,290 @@
+// mlp_tc_gemm.cu -- the surrogate MLP's training GEMMs on the 5th-generation
+// tensor cores (tcgen05, sm_103a): the forward pass that keeps what the backward
+// pass needs, the input gradients (dgrad) and the weight gradients (wgrad).
+//
+// C[M x N] = A[M x K] . B[N x K]^T, BF16 operands with K contiguous in memory,
+// FP32 accumulation.  One CTA (192 threads) computes a 128 x BN tile of C over
+// its K range (a split of K for the weight gradients):
+//   * warp 0, one thread: TMA (cp.async.bulk.tensor, 128-byte swizzle) brings
+//     64-column K chunks of A (128 rows) and B (BN rows) into a two-stage ring of
+//     shared-memory buffers; each stage completes on its "full" mbarrier;
+//   * warp 1, one thread: four tcgen05.mma (M = 128, N = BN, K = 16) per chunk
+//     into the TMEM accumulator (128 lanes x BN columns), then tcgen05.commit to
+//     the stage's "empty" mbarrier (the buffer may be refilled) and, after the
+//     last chunk, to the accumulator's mbarrier;
+//   * warps 2-5: the epilogue, each reading its 32 TMEM lanes (rows) with
+//     tcgen05.ld, 32 columns at a time, and writing what the MLP needs (bias,
+//     erf-GELU or its derivative, FP32 / BF16 / transposed BF16 stores).
+// Two CTAs share an SM (97 KB of shared memory and 256 TMEM columns each), so one
+// CTA's epilogue overlaps the other's copies and MMAs.  Operand tiles are read
+// only from this GPU's global memory (no cluster multicast).
+// Every mbarrier wait is bounded: a wait that gives up records an error, the
+// kernel waits (with a long fixed bound) for the copies and MMAs it started,
+// frees its TMEM and returns.
+#include <cuda.h>  // CUtensorMap and its enums; the encoder comes from the runtime's driver entry point
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "mlp_tc.h"
+#include "tc_ptx.cuh"
+
+namespace mlpgemm {
+
+using namespace tcx;
+
+constexpr uint32_t kBM = 128;
+constexpr uint32_t kStages = 2;
+constexpr uint32_t kThreads = 192;
+constexpr uint32_t kATile = kBM * 128;     // 128 rows x 64 BF16
+constexpr uint32_t kBTileMax = 256 * 128;  // up to 256 rows x 64 BF16
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kDrainPolls = 1u << 26;  // bound of the waits for work already started
+constexpr size_t kSmemBytes = kStages * (kATile + kBTileMax) + 1024;
+
+__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_erf_grad(float z)
+{
+    // d/dz [z Phi(z)] = Phi(z) + z phi(z)
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *(const uint32_t *)&h;
+}
+
+struct KArgs {
+    TcGemm g;
+    uint32_t bn;  // N tile (multiple of 16, <= 256)
+};
+
+__global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_constant__ CUtensorMap ta,
+                                                              const __grid_constant__ CUtensorMap tb, const KArgs ka)
+{
+    const TcGemm &g = ka.g;
+    const uint32_t BN = ka.bn;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t full[kStages], empty[kStages], accb;
+    __shared__ uint32_t s_tmem, s_issued, s_consumed;
+    __shared__ int s_abort;
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023u) & ~(uintptr_t)1023u);
+    const uint32_t stage_bytes = kATile + BN * 128u;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const uint32_t k0 = blockIdx.z * (uint32_t)g.kps;
+    const uint32_t k1 = min((uint32_t)g.K, k0 + (uint32_t)g.kps);
+    const uint32_t nch = k1 > k0 ? (k1 - k0 + 63u) / 64u : 0u;
+
+    if (warp == 1) tmem_alloc(smem_u32(&s_tmem), kTmemCols);
+    if (tid == 0) {
+        for (uint32_t s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(&accb), 1);
+        fence_mbar_init();
+        s_abort = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int *abort = &s_abort;
+
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            for (uint32_t c = 0; c < nch; ++c) {
+                const uint32_t s = c % kStages;
+                if (c >= kStages && !mbar_wait_or_abort(smem_u32(&empty[s]), ((c / kStages) - 1u) & 1u, g.polls, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                if (*abort) break;
+                unsigned char *sa = smem + s * stage_bytes;
+                const uint32_t fb = smem_u32(&full[s]);
+                expect_tx(fb, stage_bytes);
+                tma_load_2d(smem_u32(sa), &ta, (int32_t)(k0 + c * 64u), (int32_t)m0, fb);
+                tma_load_2d(smem_u32(sa + kATile), &tb, (int32_t)(k0 + c * 64u), (int32_t)n0, fb);
+                *(volatile uint32_t *)&s_issued = c + 1u;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            const uint32_t idesc = idesc_bf16(kBM, BN);
+            bool done = true;
+            for (uint32_t c = 0; c < nch; ++c) {
+                const uint32_t s = c % kStages;
+                if (!mbar_wait_or_abort(smem_u32(&full[s]), (c / kStages) & 1u, g.polls, abort)) {
+                    *abort = 1;
+                    done = false;
+                    break;
+                }
+                *(volatile uint32_t *)&s_consumed = c + 1u;
+                tc_fence_after();
+                const uint32_t a_base = smem_u32(smem + s * stage_bytes), b_base = a_base + kATile;
+#pragma unroll
+                for (uint32_t kk = 0; kk < 4; ++kk)
+                    mma_bf16(tmem, sw128_desc(a_base + kk * 32u), sw128_desc(b_base + kk * 32u), idesc,
+                             (c > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(smem_u32(&empty[s]));
+            }
+            if (done) mma_commit(smem_u32(&accb));
+        }
+    } else {  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+        const uint32_t q = warp & 3u, row = q * 32u + lane, gm = m0 + row;
+        const bool ok = nch > 0 ? mbar_wait_or_abort(smem_u32(&accb), 0u, g.polls, abort) : true;
+        if (!ok) *abort = 1;
+        tc_fence_after();
+        if (ok) {
+            const bool rv = gm < (uint32_t)g.M;
+            for (uint32_t cb = 0; cb < BN; cb += 32u) {
+                float v[32];
+                if (nch > 0) {
+                    tmem_ld32(tmem + ((q * 32u) << 16) + cb, v);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = 0.0f;
+                }
+                const uint32_t n = n0 + cb;
+                if (n >= (uint32_t)g.N) break;  // warp-uniform
+                const bool full32 = n + 32u <= (uint32_t)g.N;
+                if (g.epi == TC_EPI_WGRAD) {
+                    if (rv) {
+                        float *o = g.outf + (size_t)blockIdx.z * g.M * g.ldf + (size_t)gm * g.ldf + n;
+                        for (int e = 0; e < 32; ++e)
+                            if (n + e < (uint32_t)g.N) o[e] = v[e];
+                    }
+                    continue;
+                }
+                if (g.epi == TC_EPI_OUTPUT) {
+                    if (rv) {
+                        float *o = g.outf + (size_t)gm * g.ldf + n;
+                        for (int e = 0; e < 32; ++e)
+                            if (n + e < (uint32_t)g.N) o[e] = v[e] + __ldg(g.bias + n + e);
+                    }
+                    continue;
+                }
+                // HIDDEN and DGRAD: the FP32 value, then its BF16 copies
+                if (g.epi == TC_EPI_HIDDEN) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const float z = v[e] + (n + e < (uint32_t)g.N ? __ldg(g.bias + n + e) : 0.0f);
+                        if (rv && n + e < (uint32_t)g.N) g.outf[(size_t)gm * g.ldf + n + e] = z;
+                        v[e] = gelu_erf(z);
+                    }
+                } else {  // DGRAD
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const float z = (rv && n + e < (uint32_t)g.N) ? __ldg(g.zin + (size_t)gm * g.ldz + n + e) : 0.0f;
+                        v[e] = v[e] * gelu_erf_grad(z);
+                        if (rv && n + e < (uint32_t)g.N) g.outf[(size_t)gm * g.ldf + n + e] = v[e];
+                    }
+                }
+                if (rv) {
+                    if (full32) {
+                        uint4 *o = (uint4 *)(g.outb + (size_t)gm * g.ldo + n);
+#pragma unroll
+                        for (int c8 = 0; c8 < 4; ++c8)
+                            o[c8] = make_uint4(pack_bf16x2(v[c8 * 8 + 0], v[c8 * 8 + 1]), pack_bf16x2(v[c8 * 8 + 2], v[c8 * 8 + 3]),
+                                               pack_bf16x2(v[c8 * 8 + 4], v[c8 * 8 + 5]), pack_bf16x2(v[c8 * 8 + 6], v[c8 * 8 + 7]));
+                    } else {
+                        for (int e = 0; e < 32; ++e)
+                            if (n + e < (uint32_t)g.N) g.outb[(size_t)gm * g.ldo + n + e] = __float2bfloat16(v[e]);
+                    }
+                    // transposed copy: for each column, the warp's 32 rows are 64 contiguous bytes
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (n + e < (uint32_t)g.N) g.outt[(size_t)(n + e) * g.ldt + gm] = __float2bfloat16(v[e]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) {
+        atomicExch(g.err, 1);
+        // copies issued but never consumed, then the MMAs already issued, land
+        // before the buffers and the accumulator are given up
+        for (uint32_t c = s_consumed; c < s_issued; ++c)
+            (void)mbar_wait(smem_u32(&full[c % kStages]), (c / kStages) & 1u, kDrainPolls);
+        if (s_consumed > 0) {
+            const uint32_t c = s_consumed - 1u;
+            (void)mbar_wait(smem_u32(&empty[c % kStages]), (c / kStages) & 1u, kDrainPolls);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder()
+{
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    });
+    return fn;
+}
+
+// a 2-D BF16 tensor [rows x cols] with row stride ld elements, read in boxes of
+// 64 columns x box_rows rows with the 128-byte swizzle; zeros outside
+static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc || ((uintptr_t)base & 15u) || (ld * 2u) % 16u || rows == 0 || cols == 0) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * 2u};
+    const cuuint32_t box[2] = {64u, box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace mlpgemm
+
+cudaError_t mlptc_gemm(const TcGemm &g, cudaStream_t s)
+{
+    using namespace mlpgemm;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.kps <= 0 || g.kps % 64 || !g.err) return cudaErrorInvalidValue;
+    if ((g.epi == TC_EPI_HIDDEN || g.epi == TC_EPI_DGRAD) && (g.ldo % 8 || !g.outb || !g.outt || !g.outf))
+        return cudaErrorInvalidValue;
+    KArgs ka{};
+    ka.g = g;
+    const uint32_t n16 = ((uint32_t)g.N + 15u) / 16u * 16u;
+    ka.bn = n16 < 256u ? n16 : 256u;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, g.A, (uint64_t)g.M, (uint64_t)g.K, (uint64_t)g.lda, kBM) ||
+        !make_map(&tb, g.B, (uint64_t)g.N, (uint64_t)g.K, (uint64_t)g.ldb, ka.bn))
+        return cudaErrorInvalidValue;
+    const uint32_t splits = (uint32_t)((g.K + g.kps - 1) / g.kps);
+    const dim3 grid((g.M + kBM - 1) / kBM, (g.N + ka.bn - 1) / ka.bn, splits);
+    if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidValue;
+    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(ta, tb, ka);
+    return cudaGetLastError();
+}

@@ -126,6 +126,11 @@ static cudaError_t scan_inplace(uint32_t *a, size_t m, uint32_t *scratch, cudaSt
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan_inclusive(uint32_t *a, size_t m, uint32_t *scratch, cudaStream_t stream)
+{
+    return scan_inplace(a, m, scratch, stream);
+}
+
 size_t scan_scratch_words(size_t m)
 {
     size_t words = 0;

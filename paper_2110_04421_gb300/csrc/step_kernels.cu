@@ -40,7 +40,9 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 }
 
 #ifndef DEABM_QUIET_S
-#define DEABM_QUIET_S 1  // 1: a susceptible agent with nothing happening today writes nothing
+#define DEABM_QUIET_S 0  // 1: a susceptible agent with nothing happening today writes nothing (measured at
+                         // N = 2e6, days 5..24: 12 MB less DRAM written a day but 1 % slower, 90.2 against
+                         // 89.1 us a day)
 #endif
 #ifndef DEABM_SUSCEPTIBLE_ONLY
 #define DEABM_SUSCEPTIBLE_ONLY 1  // 0: lambda (all gathers) for every agent, as the method is written

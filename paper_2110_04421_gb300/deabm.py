@@ -26,7 +26,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
            "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore",
-           "deabm_mlp_apply_grads", "deabm_get_gathered")
+           "deabm_mlp_apply_grads", "deabm_get_gathered", "deabm_mlp_set_wait_limit")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -133,6 +133,7 @@ def lib():
         L.deabm_mlp_sync.argtypes = [vp]
         L.deabm_mlp_apply_grads.argtypes = [vp, vp, u32, C.c_float]
         L.deabm_get_gathered.argtypes = [vp, u32, vp]
+        L.deabm_mlp_set_wait_limit.argtypes = [vp, u32]
         L.deabm_mlp_use_tcgen05.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.deabm_mlp_use_tcgen05.restype = C.c_int
         L.deabm_mlp_last_error.argtypes = []
@@ -144,7 +145,7 @@ def lib():
                      "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate", "deabm_reset", "deabm_mlp_create",
                      "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
                      "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_apply_grads",
-                     "deabm_get_gathered"):
+                     "deabm_get_gathered", "deabm_mlp_set_wait_limit"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -661,6 +662,10 @@ class MLP:
             g = np.ascontiguousarray(grads, np.float32)
             assert g.size == self.n_params
             _mlp_check(lib().deabm_mlp_apply_grads(self.ctx, _p(g), 0, lr))
+
+    def set_wait_limit(self, polls: int):
+        """Bound of the tcgen05 kernels' waits (deabm_mlp_set_wait_limit)."""
+        _mlp_check(lib().deabm_mlp_set_wait_limit(self.ctx, int(polls)))
 
     def sync(self):
         _mlp_check(lib().deabm_mlp_sync(self.ctx))

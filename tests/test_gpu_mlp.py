@@ -142,12 +142,17 @@ def test_train_step_equals_gradient_then_oracle_adam():
         assert np.all(np.abs(d[a:b]) <= lr * (1 + 1e-4) + tol), (a, b)
 
 
-def test_gradients_match_bf16_oracle():
+@pytest.mark.parametrize("tcgen05", [True, False])
+@pytest.mark.parametrize("batch", [257, 4096])
+def test_gradients_match_bf16_oracle(tcgen05, batch):
+    """Both training paths: the tcgen05 GEMMs (forward keeping activations, input
+    and weight gradients, the latter split over the batch) and the mma.sync ones."""
     import torch
     from paper_2110_04421_gb300.deabm import MLP
     p = M.init_params(SIZES, 8)
-    x, y = make(257, 2)
-    m = MLP(max_batch=512)
+    x, y = make(batch, 2)
+    m = MLP(max_batch=4096)
+    assert m.use_tcgen05(tcgen05)
     m.set_params(p)
     loss = m.grad(torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"))
     g = m.get_grads()
@@ -225,3 +230,34 @@ def test_surrogate_beats_the_mean_curve_and_falls_back_outside_its_box():
     m.close()
     assert not inside.any()
     assert np.array_equal(out, S.simulate(pop, w["params"], outside, seeds[2048:2050], w["T"]))
+
+
+def test_tensor_core_waits_that_run_out_are_reported_and_the_context_recovers():
+    """With the wait bound at one non-blocking test, the fused forward and the
+    training GEMMs give up on their first copy or MMA that has not landed yet: the
+    kernels return on their own (after letting what they started land), the next
+    sync reports DEABM_ETIMEOUT, and with the bound restored the same context
+    computes the oracle's output again."""
+    import torch
+    from paper_2110_04421_gb300.deabm import MLP, DeabmError, ETIMEOUT
+    p = M.init_params(SIZES, 31)
+    x, y = make(2048, 32)
+    X, Y = torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda")
+    m = MLP(max_batch=2048)
+    m.set_params(p)
+    for run in (lambda: m.forward(X), lambda: m.grad(X, Y)):
+        m.set_wait_limit(1)
+        try:
+            run()
+        except DeabmError:
+            pass  # the gradient call reads the loss back and may already see the error
+        with pytest.raises(DeabmError) as e:
+            m.sync()
+        assert e.value.code == ETIMEOUT
+        m.set_wait_limit(0)
+        m.sync()
+    out = m.forward(X).cpu().numpy()
+    m.sync()
+    m.close()
+    ref, _, _ = M.forward(p, SIZES, x)
+    assert np.max(np.abs(out - ref)) <= 1e-2 * np.max(np.abs(ref))
