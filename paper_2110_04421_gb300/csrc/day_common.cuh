@@ -145,6 +145,58 @@ __device__ __forceinline__ float random_sum(const KParams &P, const float *__res
     return random_tail<REC, ROWMAP>(P, inf, j, day, stride, b, h, rec, row_of);
 }
 
+// Far end of edge m (1-based) of agent i in the day's Watts-Strogatz random
+// network, from its block of stream 10: the lattice neighbour (i + m) mod n, or,
+// when rewired (coin below the threshold, or i + m wrapping onto i), the agent
+// the word picks among the other n - 1.
+__device__ __forceinline__ uint32_t wsg_far(const KParams &P, uint32_t i, uint32_t m, uint32_t coin, uint32_t word)
+{
+    const uint32_t n = P.n;
+    if (m % n == 0u || (uint64_t)coin < P.thr_wsg) {
+        uint32_t v = (uint32_t)(((uint64_t)word * (uint64_t)(n - 1u)) >> 32);
+        return v + ((v >= i) ? 1u : 0u);
+    }
+    return (uint32_t)(((uint64_t)i + m) % n);
+}
+
+// Agent jo's (caller id) messages in the day's Watts-Strogatz random network,
+// summed left to right from +0.0f: its own edges m = 1..h, the unrewired lattice
+// edges of agents jo - m, m = 1..h, then the rewired edges that landed on jo, by
+// owner ascending.  *k_out = their number.  NEED_SUM = false: the count only.
+template <bool NEED_SUM = true>
+__device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restrict__ inf, uint32_t jo, uint32_t day,
+                                         uint32_t *k_out)
+{
+    const uint32_t n = P.n, h = P.wsg_h;
+    const uint2 nk = seed_key(P.net_seed);
+    float r = 0.0f;
+    uint32_t k = h;
+    if (NEED_SUM) {
+        for (uint32_t m = 1; m <= h; m += 2u) {
+            const uint4 w = draw(nk, jo, day, kStreamWsg, (m - 1u) >> 1);
+            const uint32_t f0 = wsg_far(P, jo, m, w.x, w.y);
+            const float v0 = __ldg(inf + f0);
+            float v1 = 0.0f;
+            if (m + 1u <= h) v1 = __ldg(inf + wsg_far(P, jo, m + 1u, w.z, w.w));
+            r = __fadd_rn(r, v0);
+            if (m + 1u <= h) r = __fadd_rn(r, v1);
+        }
+    }
+    for (uint32_t m = 1; m <= h; ++m) {
+        const uint32_t i = (uint32_t)(((uint64_t)jo + (uint64_t)n - (uint64_t)(m % n)) % n);
+        if (!((__ldg(P.wsg_rew + i) >> (m - 1u)) & 1u)) {
+            ++k;
+            if (NEED_SUM) r = __fadd_rn(r, __ldg(inf + i));
+        }
+    }
+    const uint32_t s0 = __ldg(P.wsg_start + jo), s1 = __ldg(P.wsg_start + jo + 1u);
+    k += s1 - s0;
+    if (NEED_SUM)
+        for (uint32_t q = s0; q < s1; ++q) r = __fadd_rn(r, __ldg(inf + __ldg(P.wsg_land + q)));
+    *k_out = k;
+    return r;
+}
+
 // Place of the member an occupation contact lands on: word x mapped to
 // [0, size-1), the agent's own place skipped.
 __device__ __forceinline__ uint32_t occ_place(uint32_t x, uint32_t size_m1, uint32_t own)
@@ -228,9 +280,15 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 // The number of the day's in-contacts of an agent whose lambda is not needed
 // (not susceptible): the random network's count (k_rand, from block 0) and the
 // occupation's daily count.  No gathers.
-__device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t k_rand)
+__device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t k_rand, uint32_t jo,
+                                                  uint32_t day)
 {
     uint32_t k = k_rand;
+    if (P.wsg_on) {
+        uint32_t kw;
+        (void)wsg_sum<false>(P, nullptr, jo, day, &kw);
+        k += kw;
+    }
     if (P.n_occ) {
         const uint32_t g = __ldg(P.occ_gid + j);
         if (__ldg(P.occ_start + g + 1u) - __ldg(P.occ_start + g) > 1u) k += __ldg(P.occ_k + g);
@@ -300,6 +358,12 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
         *k_out += k_occ;
     }
     if (REC && rec) rec[0] = k_rand | (k_occ << 8);
+    if (P.wsg_on) {  // the Watts-Strogatz random network in the random network's place
+        uint32_t kw;
+        const float term = __fmul_rn(rp.B_rand, wsg_sum<true>(P, I.rand_cur, jo, day, &kw));
+        s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
+        *k_out += kw;
+    }
     if (P.rand_on) {
 #if DEABM_RAND_DEFER
         const float r = rmap ? random_tail<REC, true>(P, rinf, jo, day, stride, b, head, rec, I.row_of)

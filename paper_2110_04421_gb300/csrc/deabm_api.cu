@@ -29,6 +29,7 @@ struct deabm_ctx {
     size_t arena_used = 0, arena_size = 0, arena_chunk = 0;
     uint32_t *row_ptr[DEABM_MAX_NETS] = {};
     uint32_t *col[DEABM_MAX_NETS] = {};
+    WsgBuffers wsg{};                         // the day's Watts-Strogatz random network (rand_ws)
     uint8_t *age = nullptr;
     int16_t *dose1 = nullptr;
     StateRef S{};
@@ -277,6 +278,18 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
     if (!(g->rand_mean >= 0.0f) || g->rand_mean > 1e3f) return fail(ctx, DEABM_EINVAL, "rand_mean out of range");
     if (g->rand_mean > 0.0f && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
     if ((uint64_t)n * n_rep >= (1ull << 40)) return fail(ctx, DEABM_EINVAL, "n_agents * n_rep too large");
+    if (g->rand_ws) {
+        if (g->rand_ws != 1) return fail(ctx, DEABM_EINVAL, "rand_ws must be 0 or 1");
+        if (g->rand_ws_k < 2 || g->rand_ws_k > 16 || g->rand_ws_k % 2)
+            return fail(ctx, DEABM_EINVAL, "rand_ws_k must be even, 2..16");
+        if (!(g->rand_ws_beta >= 0.0f && g->rand_ws_beta <= 1.0f))
+            return fail(ctx, DEABM_EINVAL, "rand_ws_beta must be in [0,1]");
+        if (n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
+        if ((uint64_t)n * (g->rand_ws_k / 2) >= (1ull << 31))
+            return fail(ctx, DEABM_EINVAL, "n_agents * rand_ws_k / 2 must be < 2^31");
+        if (n_rep != 1) return fail(ctx, DEABM_EINVAL, "the Watts-Strogatz random network runs in plain contexts only");
+        if (p->den_on) return fail(ctx, DEABM_EINVAL, "the Watts-Strogatz random network excludes exposure notification");
+    }
     using Firsts = RowFirsts;
     const std::vector<Firsts> found = scanned ? *scanned : scan_rows(g, a);
     auto first = [&](uint32_t Firsts::*m) {
@@ -594,7 +607,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->S.qt, nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
-            if (ctx->relabel && g->rand_mean > 0.0f && n_rep == 1) {
+            if (ctx->relabel && (g->rand_mean > 0.0f || g->rand_ws) && n_rep == 1) {
                 if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
                 if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
             }
@@ -749,7 +762,24 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.n_rep = n_rep;
             K.inf_len = p->inf_len;
             K.dt = p->dt;
-            K.rand_on = g->rand_mean > 0.0f ? 1u : 0u;
+            K.rand_on = (g->rand_mean > 0.0f && !g->rand_ws) ? 1u : 0u;
+            if (g->rand_ws) {  // the day's Watts-Strogatz random network, rebuilt before each day kernel
+                K.wsg_on = 1;
+                K.wsg_h = g->rand_ws_k / 2u;
+                K.thr_wsg = threshold((double)g->rand_ws_beta);
+                WsgBuffers &W = ctx->wsg;
+                const size_t edges = (size_t)n * K.wsg_h;
+                if ((r = dalloc(ctx, &W.rew, n))) return r;
+                if ((r = dalloc(ctx, &W.cnt1, (size_t)n + 1))) return r;
+                if ((r = dalloc(ctx, &W.fill, n))) return r;
+                if ((r = dalloc(ctx, &W.list, 2 * edges))) return r;
+                if ((r = dalloc(ctx, &W.list_n, 1))) return r;
+                if ((r = dalloc(ctx, &W.land, edges))) return r;
+                if ((r = dalloc(ctx, &W.scratch, wsg_scratch_words(n)))) return r;
+                K.wsg_rew = W.rew;
+                K.wsg_start = W.cnt1;
+                K.wsg_land = W.land;
+            }
             for (uint32_t k = 0; k < DEABM_MAX_NETS; ++k) {
                 K.row_ptr[k] = ctx->row_ptr[k];
                 K.col[k] = ctx->col[k];
@@ -876,6 +906,7 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         I.row_of = ctx->row_of;
         if (kp.den_bits_orig)
             CU(ctx, cudaMemsetAsync(kp.den_bits_orig, 0, sizeof(uint32_t) * (((size_t)ctx->n + 31) / 32), ctx->stream));
+        if (kp.wsg_on) CU(ctx, launch_wsg_build(kp, ctx->day, ctx->wsg, ctx->stream));
         CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
                             ctx->stream));
         if (kp.den_on) CU(ctx, launch_den(kp, ctx->day, ctx->S, ctx->C, ctx->stream));
@@ -1132,6 +1163,8 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
+            if (graphs[q].rand_ws)
+                return fail(ctx, DEABM_EINVAL, "population %u: the Watts-Strogatz random network runs in plain contexts only", q);
             if (graphs[q].n_occ)
                 return fail(ctx, DEABM_EINVAL, "daily occupation networks are not available for ragged batches");
             if (params[q].den_on)

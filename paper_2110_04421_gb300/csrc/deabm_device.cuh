@@ -21,6 +21,8 @@ enum : uint32_t {
     kStreamVax = 7,    // x: vaccine response (day word fixed at 0)
     kStreamGumbel = 8, // relaxed draw noise
     kStreamWs = 9,     // Watts-Strogatz occupation contacts: block e/2, lanes 2(e%2), 2(e%2)+1 = coin, place
+    kStreamWsg = 10,   // Watts-Strogatz global random network: edge m of an agent in block (m-1)/2, lanes
+                       // 2((m-1)%2), 2((m-1)%2)+1 = rewire coin, new far end
 };
 constexpr uint32_t kSeedDay = 0xFFFFFFFFu;  // day word of the infections before day 0
 constexpr int16_t kNever = 0x7FFF;
@@ -123,6 +125,16 @@ struct KParams {
     // replicate 0's parameters by value: plain contexts read them from the
     // kernel's parameter space (uniform across the grid) instead of through `rep`
     Rep rep0;
+    // the global random network as a daily Watts-Strogatz graph (wsg_on; then
+    // rand_on = 0): h = k/2 owned edges per agent, rewiring threshold; the day's
+    // graph built before the day kernel, by caller id: bit m-1 of wsg_rew[i] = edge
+    // m of agent i rewired; the owners of the rewired edges that landed on agent v
+    // at wsg_land[wsg_start[v] .. wsg_start[v+1]), ascending
+    uint32_t wsg_on, wsg_h;
+    uint64_t thr_wsg;
+    const uint8_t *wsg_rew;
+    const uint32_t *wsg_start;
+    const uint32_t *wsg_land;
 };
 
 // K_j of the random network from word 0 of its block 0: the number of Poisson

@@ -49,6 +49,15 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
                                 const uint32_t *orig2new, uint32_t n, uint32_t *rp_new, uint32_t *col_new,
                                 uint32_t *scratch, cudaStream_t stream);
 size_t scan_scratch_words(size_t m);
+// the day's Watts-Strogatz random network (wsg.cu): device buffers over n agents
+// with h owned edges each -- rew [n], cnt1 [n+1] (landing slots after the build),
+// fill [n], list [2 n h], list_n [1], land [n h], scratch [wsg_scratch_words(n)]
+struct WsgBuffers {
+    uint8_t *rew;
+    uint32_t *cnt1, *fill, *list, *list_n, *land, *scratch;
+};
+size_t wsg_scratch_words(uint32_t n);
+cudaError_t launch_wsg_build(const KParams &P, uint32_t day, const WsgBuffers &B, cudaStream_t stream);
 // in-place inclusive prefix sum of m words (scratch of scan_scratch_words(m) words)
 cudaError_t launch_scan_inclusive(uint32_t *a, size_t m, uint32_t *scratch, cudaStream_t stream);
 // new2orig[q] = the agent at internal row q: agents by ascending label (labels

@@ -87,7 +87,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
         for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) deg += rb.end[net] - rb.beg[net];
         *kg_out = *k_out + deg;
     } else {
-        *k_out = contact_count(P, j, r0.k);
+        *k_out = contact_count(P, j, r0.k, jo, day);
         *kg_out = 0;
     }
     a.tm = S.timer[i];

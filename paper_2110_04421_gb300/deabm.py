@@ -42,7 +42,8 @@ class Graph(C.Structure):
                 ("row_ptr", C.c_void_p * MAX_NETS), ("col", C.c_void_p * MAX_NETS),
                 ("rand_mean", C.c_float),
                 ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
-                ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_float)]
+                ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_float),
+                ("rand_ws", C.c_uint32), ("rand_ws_k", C.c_uint32), ("rand_ws_beta", C.c_float)]
 
 
 class Agents(C.Structure):
@@ -228,6 +229,10 @@ def _graph_struct(graph: dict, rand_mean: float, keep: list) -> Graph:
         g.occ_k = ok.ctypes.data
         g.occ_lattice = int(graph.get("occ_lattice", 0))
         g.occ_rewire = float(graph.get("occ_rewire", 0.0))
+    if graph.get("rand_ws"):  # the random network as a daily Watts-Strogatz graph
+        g.rand_ws = 1
+        g.rand_ws_k = int(graph.get("rand_ws_k", 2))
+        g.rand_ws_beta = float(graph.get("rand_ws_beta", 0.5))
     return g
 
 
