@@ -163,6 +163,37 @@ def rank_inputs(w: dict, rank: int):
     return params, pop
 
 
+def column_range(B: int, rank: int, world: int):
+    """The replicate columns [lo, hi) of a B-column ensemble that rank `rank` of
+    `world` runs: contiguous shares, the first B % world ranks one column more.
+    Columns are independent runs on the shared graph (own parameters and seed;
+    the day's random network is keyed by the graph's seed), so a split changes no
+    column's trajectory and needs no exchange until the results are gathered."""
+    base, extra = divmod(B, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def gather_columns(dist, local, B: int, world: int, device):
+    """The [T, B] per-column results from every rank's [T, hi - lo] share, in
+    column order (all_gather of equal-sized, zero-padded blocks)."""
+    import torch
+    T = local.shape[0]
+    width = -(-B // world)
+    buf = torch.zeros((T, width), dtype=torch.int64, device=device)
+    buf[:, :local.shape[1]] = torch.as_tensor(np.asarray(local, np.int64), device=device)
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    if dist is not None:
+        dist.all_gather(parts, buf)
+    else:
+        parts = [buf]
+    out = np.zeros((T, B), np.int64)
+    for q in range(world):
+        lo, hi = column_range(B, q, world)
+        out[:, lo:hi] = parts[q][:, :hi - lo].cpu().numpy()
+    return out
+
+
 def reduce_over_ranks(dist, maxed, summed, device):
     """Whole-job figures: the slowest rank's times (max) and the work of all ranks
     (sum).  dist is torch.distributed (None on one rank)."""
@@ -240,7 +271,7 @@ def run_ours(args, rank, world, local):
     messages, e2e_messages, gathered = int(messages), int(e2e_messages), int(gathered)
 
     # ---- batched ensemble vs plain per-replicate loop, relaxed gradient (rank 0)
-    batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
+    batched = run_batched(args, rank, world, dist) if not args.no_batched else None  # columns split over ranks
     relaxed = run_relaxed(args) if (rank == 0 and not args.no_relaxed) else None
     surrogate = run_surrogate(args) if (rank == 0 and not args.no_surrogate) else None
     ragged = run_ragged(args) if (rank == 0 and not args.no_ragged) else None
@@ -577,7 +608,11 @@ def run_den(args):
             "launches_per_day": 2}
 
 
-def run_batched(args):
+def run_batched(args, rank: int = 0, world: int = 1, dist=None):
+    """The batched ensemble: one N = 1e5 graph shared by B = 256 replicate columns.
+    With several ranks the columns are split between them (column_range), each
+    rank runs its own batch context over its columns, and the per-day new
+    infections [T, B] are gathered at the end: no exchange on the simulation path."""
     import torch
     from paper_2110_04421_gb300 import workloads as W
     from paper_2110_04421_gb300.deabm import Simulation
@@ -587,34 +622,49 @@ def run_batched(args):
     Kb = max(3, min(args.batched_steps, args.steps))
     pop = W.population(n, 0, w["n_seed"])
     rp, seeds = W.batch_params(B, 0)
+    lo, hi = column_range(B, rank, world)
     static_edges = int(sum(int(r[-1]) for r in pop["row_ptr"]))
     stream = torch.cuda.Stream()
-    sim = Simulation(pop, w["params"], pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds,
-                     max_steps=args.warmup + Kb, stream=stream.cuda_stream)
+    sim = Simulation(pop, w["params"], pop["age"], pop["seed_ids"], n_rep=hi - lo, rep_params=rp[lo:hi],
+                     rep_seeds=seeds[lo:hi], max_steps=args.warmup + Kb, stream=stream.cuda_stream)
     sim.step(args.warmup)
     sim.sync()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     sim.step(Kb)
     e1.record(stream)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     ms = e0.elapsed_time(e1)
-    _, _, msgs = sim.counters()
+    ni, _, msgs = sim.counters()
     sim.close()
-    msg_b = int(msgs[args.warmup:].astype(np.int64).sum()) * B
+    msg_local = int(msgs[args.warmup:].astype(np.int64).sum()) * (hi - lo)
+    (ms,), (msg_b,) = reduce_over_ranks(dist, [ms], [msg_local], "cuda")
+    msg_b = int(msg_b)
+    incidence = gather_columns(dist, ni[args.warmup:], B, world, "cuda")
+    if rank != 0:
+        return None
     alg = step_bytes_batch(n, B, static_edges, len(pop["row_ptr"]), True)
     peak, _ = measured_peak_hbm()
     achieved = alg / (ms / Kb / 1e3) / 1e9
     value = msg_b / (ms / 1e3)
     out = {"workload": "batched N=1e5 B=256 (R~U[2,6], weights~U[0.5,2], dose-2 delay~U{21..84}, own seeds)",
            "value": value, "unit": "interactions/s", "ms_per_step": ms / Kb, "steps": Kb,
+           "columns_per_rank": [column_range(B, q, world) for q in range(world)],
+           "new_infections_timed": int(incidence.sum()),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "kernel": "step_batch4_kernel", "alg_bytes_per_launch": alg,
                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_batch_n1e5_b256.md", n * B,
-                                                        (args.warmup, args.warmup + Kb - 1))}}
+                                                        (args.warmup, args.warmup + Kb - 1)) if world == 1 else None}}
+    if world > 1:
+        out["roofline"]["note"] = "whole-job bytes over the slowest rank's time, B/world columns per rank"
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_columns(pop, w["params"], rp, seeds, args.cpu_seconds / 2)
-    if args.no_loop:
+    if args.no_loop or world > 1:
         return out
     # plain loop: the same B replicates one after another, same days
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -337,6 +337,14 @@ int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t *timer, con
                   const uint8_t *flags, const uint8_t *qt, const int16_t *dose1_day, const int16_t *dose2_day,
                   uint32_t day);
 
+/* Failure injection for tests (the paper has no counterpart; off by default): the
+ * `after`-th device allocation made from now on by a simulation context (create,
+ * batch, ragged; arrays and set-up scratch) fails as if cudaMalloc had run out of
+ * memory -- the call reports DEABM_ENOMEM and releases everything it had
+ * allocated -- and the injection switches itself off.  after = 0 switches it
+ * off.  Process-wide; meant for single-threaded tests. */
+void deabm_inject_alloc_failure(uint32_t after);
+
 /* ---- Infection rates of one day without allocating memory ------------------------------
  * The paper has no counterpart: this is a library convenience.  It exists for
  * callers that may not allocate device memory where they call us (code living

@@ -24,9 +24,8 @@ namespace deabm {
 #endif
 template <uint32_t kRound = DEABM_ROUND>
 __device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const float *__restrict__ inf, uint32_t e,
-                                         uint32_t end, uint32_t stride, uint32_t b)
+                                         uint32_t end, uint32_t stride, uint32_t b, float h = 0.0f)
 {
-    float h = 0.0f;
     while (e < end) {
         uint32_t c[kRound];
         float v[kRound];
@@ -40,6 +39,42 @@ __device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const
         e += kRound;
     }
     return h;
+}
+
+// The first two stored networks' sums of one row at once: the first round of
+// each (R0 and R1 edges) loads its columns together, then gathers together, so
+// the two rows cost two dependent memory round trips instead of four; longer
+// rows finish with csr_sum.  Same left-to-right order per network.
+#ifndef DEABM_MERGED_ROUNDS
+#define DEABM_MERGED_ROUNDS 0
+#endif
+template <uint32_t R0, uint32_t R1>
+__device__ __forceinline__ void csr_sum_pair(const uint32_t *__restrict__ col0, const uint32_t *__restrict__ col1,
+                                             const float *__restrict__ inf, uint32_t e0, uint32_t end0, uint32_t e1,
+                                             uint32_t end1, float *h0_out, float *h1_out)
+{
+    uint32_t c0[R0], c1[R1];
+    float v0[R0], v1[R1];
+#pragma unroll
+    for (uint32_t u = 0; u < R0; ++u) c0[u] = (e0 + u < end0) ? __ldg(col0 + e0 + u) : 0u;
+#pragma unroll
+    for (uint32_t u = 0; u < R1; ++u) c1[u] = (e1 + u < end1) ? __ldg(col1 + e1 + u) : 0u;
+#pragma unroll
+    for (uint32_t u = 0; u < R0; ++u) v0[u] = (e0 + u < end0) ? __ldg(inf + c0[u]) : 0.0f;
+#pragma unroll
+    for (uint32_t u = 0; u < R1; ++u) v1[u] = (e1 + u < end1) ? __ldg(inf + c1[u]) : 0.0f;
+    float h0 = 0.0f, h1 = 0.0f;
+#pragma unroll
+    for (uint32_t u = 0; u < R0; ++u)
+        if (e0 + u < end0) h0 = __fadd_rn(h0, v0[u]);
+#pragma unroll
+    for (uint32_t u = 0; u < R1; ++u)
+        if (e1 + u < end1) h1 = __fadd_rn(h1, v1[u]);
+    // rows longer than a round: the rest, still left to right after the first round
+    if (e0 + R0 < end0) h0 = csr_sum<R0>(col0, inf, e0 + R0, end0, 1u, 0u, h0);
+    if (e1 + R1 < end1) h1 = csr_sum<R1>(col1, inf, e1 + R1, end1, 1u, 0u, h1);
+    *h0_out = h0;
+    *h1_out = h1;
 }
 
 // Exposure-notification record of one (day, app holder), kept for the last
@@ -343,6 +378,20 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
     *k_out = k_rand;
     uint32_t k_occ = 0;
     float s = 0.0f;
+#if DEABM_MERGED_ROUNDS
+    if (stride == 1u && P.n_nets >= 2) {  // plain contexts: the first two networks' rows together
+        float h0, h1;
+        csr_sum_pair<DEABM_ROUND0, DEABM_ROUND>(P.col[0], P.col[1], I.cur, rb.beg[0], rb.end[0], rb.beg[1], rb.end[1],
+                                                &h0, &h1);
+        s = __fadd_rn(__fmul_rn(rp.B_net[0], h0), __fmul_rn(rp.B_net[1], h1));
+#pragma unroll
+        for (uint32_t net = 2; net < DEABM_MAX_NETS; ++net)
+            if (net < P.n_nets) {
+                const float h = csr_sum<DEABM_ROUND>(P.col[net], I.cur, rb.beg[net], rb.end[net], stride, b);
+                s = __fadd_rn(s, __fmul_rn(rp.B_net[net], h));
+            }
+    } else
+#endif
 #pragma unroll
     for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
         if (net < P.n_nets) {

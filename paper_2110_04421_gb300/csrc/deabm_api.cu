@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <thread>
 #include <vector>
@@ -101,6 +102,21 @@ static int fail(deabm_ctx *ctx, int code, const char *fmt, ...)
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                             \
     } while (0)
 
+// Allocation-failure injection for the tests (deabm_inject_alloc_failure): the
+// number of device allocations of simulation contexts still to succeed before
+// one fails; 0 = off.
+static std::atomic<uint32_t> g_alloc_fault{0};
+
+static bool injected_alloc_failure()
+{
+    uint32_t c = g_alloc_fault.load();
+    while (c != 0u)
+        if (g_alloc_fault.compare_exchange_weak(c, c - 1u)) return c == 1u;
+    return false;
+}
+
+extern "C" void deabm_inject_alloc_failure(uint32_t after) { g_alloc_fault.store(after); }
+
 template <class T>
 static int dalloc(deabm_ctx *ctx, T **out, size_t count)
 {
@@ -115,7 +131,7 @@ static int dalloc(deabm_ctx *ctx, T **out, size_t count)
     }
     void *ptr = nullptr;
     const size_t block = own_block ? rounded : chunk;
-    cudaError_t e = cudaMalloc(&ptr, block);
+    cudaError_t e = injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&ptr, block);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", block, cudaGetErrorString(e));
@@ -393,7 +409,8 @@ template <class T>
 static int scratch_alloc(deabm_ctx *ctx, DevScratch &sc, T **out, size_t count)
 {
     void *ptr = nullptr;
-    const cudaError_t e = cudaMalloc(&ptr, (count ? count : 1) * sizeof(T));
+    const cudaError_t e =
+        injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&ptr, (count ? count : 1) * sizeof(T));
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu scratch bytes failed: %s", count * sizeof(T),

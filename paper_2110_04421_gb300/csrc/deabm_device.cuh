@@ -142,8 +142,16 @@ struct KParams {
 // first index whose threshold exceeds w.  The first eight compares are unrolled
 // against the parameter-space thresholds; beyond them (P(K >= 8) < 0.2 % at the
 // mean of 2) a loop finishes the count.
+#ifndef DEABM_POIS32
+#define DEABM_POIS32 1
+#endif
 __device__ __forceinline__ uint32_t poisson_count(const KParams &P, uint32_t w)
 {
+#if !DEABM_POIS32
+    uint32_t c = 0;
+    while (c < DEABM_POIS_CAP && (uint64_t)w >= __ldg(&P.tab->pois[c])) ++c;
+    return c;
+#endif
     uint32_t k = 0;
 #pragma unroll
     for (uint32_t t = 0; t < 8u; ++t) k += (t < P.pois_fin && w >= P.pois32[t]) ? 1u : 0u;

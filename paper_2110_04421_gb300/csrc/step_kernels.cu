@@ -236,10 +236,15 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
     bool infected = false, notify = false;
     uint32_t k = 0, kg = 0;
     if (active) {
+#ifndef DEABM_REP_PARAM
+#define DEABM_REP_PARAM 1  // 1: replicate 0 from the kernel's parameter space; 0: through the rep pointer
+#endif
 #if DEABM_REP_SMEM
         const Rep &rp = s_rep;
-#else
+#elif DEABM_REP_PARAM
         const Rep &rp = P.rep0;
+#else
+        const Rep &rp = P.rep[0];
 #endif
         agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k, &kg,
                             &notify);

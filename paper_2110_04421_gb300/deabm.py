@@ -26,7 +26,8 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_last_error", "deabm_mlp_destroy",
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
            "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore",
-           "deabm_mlp_apply_grads", "deabm_get_gathered", "deabm_mlp_set_wait_limit")
+           "deabm_mlp_apply_grads", "deabm_get_gathered", "deabm_mlp_set_wait_limit",
+           "deabm_inject_alloc_failure")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -135,6 +136,8 @@ def lib():
         L.deabm_mlp_apply_grads.argtypes = [vp, vp, u32, C.c_float]
         L.deabm_get_gathered.argtypes = [vp, u32, vp]
         L.deabm_mlp_set_wait_limit.argtypes = [vp, u32]
+        L.deabm_inject_alloc_failure.argtypes = [u32]
+        L.deabm_inject_alloc_failure.restype = None
         L.deabm_mlp_use_tcgen05.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.deabm_mlp_use_tcgen05.restype = C.c_int
         L.deabm_mlp_last_error.argtypes = []

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2110_04421_gb300 import workloads as W
-from tests.helpers import STATE_KEYS, gpu_available
+from tests.helpers import STATE_KEYS, compare_days, gpu_available
 
 pytestmark = pytest.mark.gpu
 
@@ -106,3 +106,37 @@ def test_restore_rejects_bad_input():
         if rc != 0:
             raise DeabmError(rc, "ragged")
     r.close()
+
+
+def test_allocation_failure_in_create_reports_enomem_and_frees_everything():
+    """The library's allocation-failure injection makes the k-th device allocation
+    of deabm_create fail, for every k a create makes: each attempt returns
+    DEABM_ENOMEM with no context, the device's free memory is back where it was,
+    and a create without injection then runs and matches the oracle."""
+    import torch
+    from paper_2110_04421_gb300.deabm import ENOMEM, DeabmError, Simulation, lib
+    pop = W.population(30_000, 2, 20)
+    p = W.params_with(test_on=1, quar_on=1, vax_on=1, vax_start=2, vax_rate=0.02, R=3.0)
+    Simulation(pop, p, pop["age"], pop["seed_ids"], max_steps=5).close()  # device code of create loaded once
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    k = 1
+    try:
+        while True:
+            lib().deabm_inject_alloc_failure(k)
+            try:
+                s = Simulation(pop, p, pop["age"], pop["seed_ids"], max_steps=5)
+            except DeabmError as e:
+                assert e.code == ENOMEM, e
+                torch.cuda.synchronize()
+                assert torch.cuda.mem_get_info()[0] == free0, (k, free0 - torch.cuda.mem_get_info()[0])
+                k += 1
+                assert k < 200
+                continue
+            s.close()
+            break
+    finally:
+        lib().deabm_inject_alloc_failure(0)
+    assert k > 3  # create makes several device allocations, each one was made to fail
+    rep = compare_days(pop, p, 5)
+    assert rep["days"] == 5

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_2110_04421_gb300 import workloads as W
-from tests.helpers import compare_days, gpu_available, gpu_sim, oracle_sim
+from tests.helpers import STATE_KEYS, compare_days, gpu_available, gpu_sim, oracle_sim
 
 pytestmark = pytest.mark.gpu
 
@@ -234,3 +234,28 @@ def test_batched_without_internal_numbering():
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     for k in ("stage", "timer", "tinf", "flags", "qt"):
         assert np.array_equal(out[0][2][k], out[1][2][k])
+
+
+def test_column_split_equals_full_batch():
+    """The split the multi-GPU bench makes (bench.column_range): contexts over
+    columns [0, 16) and [16, 40) of a 40-column ensemble give exactly the full
+    batch's columns -- counters every day and the final state."""
+    import bench
+    pop = W.population(20_000, 9, 30)
+    base = W.params_with(vax_on=1, vax_start=5, vax_rate=0.01)
+    rp, seeds = W.batch_params(40, 3)
+    T = 25
+    full = gpu_sim(pop, base, keep_lambda=False, n_rep=40, rep_params=rp, rep_seeds=seeds, max_steps=T)
+    ni, h = full.run(T)
+    st = full.state()
+    full.close()
+    assert ni.sum() > 0
+    for lo, hi in [bench.column_range(40, q, 2) for q in range(2)] + [(0, 16), (16, 40)]:
+        part = gpu_sim(pop, base, keep_lambda=False, n_rep=hi - lo, rep_params=rp[lo:hi], rep_seeds=seeds[lo:hi],
+                       max_steps=T)
+        ni_p, h_p = part.run(T)
+        st_p = part.state()
+        part.close()
+        assert np.array_equal(ni_p, ni[:, lo:hi]) and np.array_equal(h_p, h[:, lo:hi])
+        for k in STATE_KEYS:
+            assert np.array_equal(st_p[k].reshape(pop["n"], hi - lo), st[k][:, lo:hi]), k

@@ -61,3 +61,54 @@ def test_two_gloo_ranks(tmp_path):
     for q in range(world):
         assert r[q][0] == 20.0                                      # max of the ranks' times
         assert r[q][1] == sum(a[0] for a in alone) and r[q][2] == sum(a[1] for a in alone)
+
+
+def _columns(B):
+    from paper_2110_04421_gb300 import workloads as W
+    w = W.batched()
+    pop = W.population(1200, 3, 12)
+    rp, seeds = W.batch_params(B, 4)
+    params = []
+    for r in range(B):
+        params.append(dict(w["params"], R=float(rp[r, 0]), B_net=[float(rp[r, 1]), float(rp[r, 2])],
+                           B_rand=float(rp[r, 3]), S_age=[float(x) for x in rp[r, 4:13]],
+                           dose2_delay=int(rp[r, 13]), seed=int(seeds[r]), vax_start=2, vax_rate=0.05))
+    return pop, params
+
+
+def _column_rank_main(rank, world, port, out_dir, B, T):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    pop, params = _columns(B)
+    lo, hi = bench.column_range(B, rank, world)
+    local = np.zeros((T, hi - lo), np.int64)
+    for c in range(lo, hi):   # this rank's columns only
+        ni, _, _ = oracle.Sim(pop, params[c], pop["age"], pop["seed_ids"]).run(T)
+        local[:, c - lo] = ni
+    full = bench.gather_columns(dist, local, B, world, "cpu")
+    np.save(os.path.join(out_dir, f"cols{rank}.npy"), full)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("B", [7, 8])
+def test_ensemble_columns_split_over_two_gloo_ranks(tmp_path, B):
+    """The batched ensemble's columns split over two ranks (uneven for B = 7):
+    each rank runs its own columns, the gathered [T, B] incidence equals the
+    unsplit run on every rank."""
+    import torch.multiprocessing as mp
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    T, world, port = 8, 2, _free_port()
+    assert [bench.column_range(B, q, world) for q in range(world)] == ([(0, 4), (4, 7)] if B == 7 else [(0, 4), (4, 8)])
+    mp.start_processes(_column_rank_main, args=(world, port, str(tmp_path), B, T), nprocs=world, start_method="spawn")
+    pop, params = _columns(B)
+    want = np.stack([oracle.Sim(pop, params[c], pop["age"], pop["seed_ids"]).run(T)[0] for c in range(B)], axis=1)
+    assert want.sum() > 0 and len({tuple(want[:, c]) for c in range(B)}) > 1
+    for q in range(world):
+        assert np.array_equal(np.load(tmp_path / f"cols{q}.npy"), want)
