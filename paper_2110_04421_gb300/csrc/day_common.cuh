@@ -41,42 +41,6 @@ __device__ __forceinline__ float csr_sum(const uint32_t *__restrict__ col, const
     return h;
 }
 
-// The first two stored networks' sums of one row at once: the first round of
-// each (R0 and R1 edges) loads its columns together, then gathers together, so
-// the two rows cost two dependent memory round trips instead of four; longer
-// rows finish with csr_sum.  Same left-to-right order per network.
-#ifndef DEABM_MERGED_ROUNDS
-#define DEABM_MERGED_ROUNDS 0
-#endif
-template <uint32_t R0, uint32_t R1>
-__device__ __forceinline__ void csr_sum_pair(const uint32_t *__restrict__ col0, const uint32_t *__restrict__ col1,
-                                             const float *__restrict__ inf, uint32_t e0, uint32_t end0, uint32_t e1,
-                                             uint32_t end1, float *h0_out, float *h1_out)
-{
-    uint32_t c0[R0], c1[R1];
-    float v0[R0], v1[R1];
-#pragma unroll
-    for (uint32_t u = 0; u < R0; ++u) c0[u] = (e0 + u < end0) ? __ldg(col0 + e0 + u) : 0u;
-#pragma unroll
-    for (uint32_t u = 0; u < R1; ++u) c1[u] = (e1 + u < end1) ? __ldg(col1 + e1 + u) : 0u;
-#pragma unroll
-    for (uint32_t u = 0; u < R0; ++u) v0[u] = (e0 + u < end0) ? __ldg(inf + c0[u]) : 0.0f;
-#pragma unroll
-    for (uint32_t u = 0; u < R1; ++u) v1[u] = (e1 + u < end1) ? __ldg(inf + c1[u]) : 0.0f;
-    float h0 = 0.0f, h1 = 0.0f;
-#pragma unroll
-    for (uint32_t u = 0; u < R0; ++u)
-        if (e0 + u < end0) h0 = __fadd_rn(h0, v0[u]);
-#pragma unroll
-    for (uint32_t u = 0; u < R1; ++u)
-        if (e1 + u < end1) h1 = __fadd_rn(h1, v1[u]);
-    // rows longer than a round: the rest, still left to right after the first round
-    if (e0 + R0 < end0) h0 = csr_sum<R0>(col0, inf, e0 + R0, end0, 1u, 0u, h0);
-    if (e1 + R1 < end1) h1 = csr_sum<R1>(col1, inf, e1 + R1, end1, 1u, 0u, h1);
-    *h0_out = h0;
-    *h1_out = h1;
-}
-
 // Exposure-notification record of one (day, app holder), kept for the last
 // den_window days: word 0 = random count | occupation count << 8, the random
 // contacts (caller ids) from word 1, the occupation contacts (internal rows)
@@ -112,7 +76,7 @@ struct RandBlock0 {
 __device__ __forceinline__ RandBlock0 random_block0(const KParams &P, uint32_t j, uint32_t day)
 {
     RandBlock0 r;
-    r.w = draw(seed_key(P.net_seed), j, day, kStreamRnet, 0u);
+    r.w = draw_rk(P.nrk, j, day, kStreamRnet, 0u);
     r.k = poisson_count(P, r.w.x);
     return r;
 }
@@ -148,10 +112,9 @@ __device__ __forceinline__ float random_tail(const KParams &P, const float *__re
 #pragma unroll
     for (uint32_t u = 0; u < 3u; ++u)
         if (u < h.k) r = __fadd_rn(r, h.v[u]);
-    const uint2 nk = seed_key(P.net_seed);
     const uint64_t nm1 = (uint64_t)(P.n - 1u);
     for (uint32_t e = 3u; e < h.k; e += 4u) {
-        const uint4 w = draw(nk, j, day, kStreamRnet, (e + 1u) >> 2);
+        const uint4 w = draw_rk(P.nrk, j, day, kStreamRnet, (e + 1u) >> 2);
         const uint32_t x[4] = {w.x, w.y, w.z, w.w};
         float v[4];
 #pragma unroll
@@ -203,12 +166,11 @@ __device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restri
                                          uint32_t *k_out)
 {
     const uint32_t n = P.n, h = P.wsg_h;
-    const uint2 nk = seed_key(P.net_seed);
     float r = 0.0f;
     uint32_t k = h;
     if (NEED_SUM) {
         for (uint32_t m = 1; m <= h; m += 2u) {
-            const uint4 w = draw(nk, jo, day, kStreamWsg, (m - 1u) >> 1);
+            const uint4 w = draw_rk(P.nrk, jo, day, kStreamWsg, (m - 1u) >> 1);
             const uint32_t f0 = wsg_far(P, jo, m, w.x, w.y);
             const float v0 = __ldg(inf + f0);
             float v1 = 0.0f;
@@ -254,10 +216,9 @@ __device__ __forceinline__ float occ_ws_sum(const KParams &P, const float *__res
                                             uint32_t stride, uint32_t b, uint32_t beg, uint32_t size, uint32_t own,
                                             uint32_t k, uint32_t *rec)
 {
-    const uint2 nk = seed_key(P.net_seed);
     float h = 0.0f;
     for (uint32_t e = 0; e < k; e += 2u) {
-        const uint4 w = draw(nk, jo, day, kStreamWs, e >> 1);
+        const uint4 w = draw_rk(P.nrk, jo, day, kStreamWs, e >> 1);
         const uint32_t m = (e >> 1) + 1u;
         const uint32_t hop = m < size ? m : m % size;
         const uint32_t coin[2] = {w.x, w.z}, word[2] = {w.y, w.w};
@@ -292,10 +253,9 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
     const uint32_t own = j - beg;
     *k_out = k;
     if (P.occ_lattice) return occ_ws_sum<REC>(P, inf, jo, day, stride, b, beg, size, own, k, rec);
-    const uint2 nk = seed_key(P.net_seed);
     float h = 0.0f;
     for (uint32_t e = 0; e < k; e += 4u) {
-        const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
+        const uint4 w = draw_rk(P.nrk, jo, day, kStreamOcc, e >> 2);
         const uint32_t x[4] = {w.x, w.y, w.z, w.w};
         float v[4];
 #pragma unroll
@@ -315,11 +275,12 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 // The number of the day's in-contacts of an agent whose lambda is not needed
 // (not susceptible): the random network's count (k_rand, from block 0) and the
 // occupation's daily count.  No gathers.
+template <bool WSG = false>
 __device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t k_rand, uint32_t jo,
                                                   uint32_t day)
 {
     uint32_t k = k_rand;
-    if (P.wsg_on) {
+    if (WSG && P.wsg_on) {
         uint32_t kw;
         (void)wsg_sum<false>(P, nullptr, jo, day, &kw);
         k += kw;
@@ -354,7 +315,7 @@ __device__ __forceinline__ RowBounds row_bounds(const KParams &P, uint32_t j)
 // Callers load the row bounds and draw block 0 first, so that the bounds are in
 // flight while the Philox rounds run.  REC: the agent's exposure-notification
 // record of the day goes to rec (when not null).
-template <bool OCC = true, bool REC = false, bool ROWMAP = false>
+template <bool OCC = true, bool REC = false, bool ROWMAP = false, bool WSG = false>
 __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, const RowBounds &rb,
                                            const RandBlock0 &r0, uint32_t *k_out, uint32_t *rec = nullptr)
@@ -378,20 +339,6 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
     *k_out = k_rand;
     uint32_t k_occ = 0;
     float s = 0.0f;
-#if DEABM_MERGED_ROUNDS
-    if (stride == 1u && P.n_nets >= 2) {  // plain contexts: the first two networks' rows together
-        float h0, h1;
-        csr_sum_pair<DEABM_ROUND0, DEABM_ROUND>(P.col[0], P.col[1], I.cur, rb.beg[0], rb.end[0], rb.beg[1], rb.end[1],
-                                                &h0, &h1);
-        s = __fadd_rn(__fmul_rn(rp.B_net[0], h0), __fmul_rn(rp.B_net[1], h1));
-#pragma unroll
-        for (uint32_t net = 2; net < DEABM_MAX_NETS; ++net)
-            if (net < P.n_nets) {
-                const float h = csr_sum<DEABM_ROUND>(P.col[net], I.cur, rb.beg[net], rb.end[net], stride, b);
-                s = __fadd_rn(s, __fmul_rn(rp.B_net[net], h));
-            }
-    } else
-#endif
 #pragma unroll
     for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) {
         if (net < P.n_nets) {
@@ -407,7 +354,7 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
         *k_out += k_occ;
     }
     if (REC && rec) rec[0] = k_rand | (k_occ << 8);
-    if (P.wsg_on) {  // the Watts-Strogatz random network in the random network's place
+    if (WSG && P.wsg_on) {  // the Watts-Strogatz random network in the random network's place
         uint32_t kw;
         const float term = __fmul_rn(rp.B_rand, wsg_sum<true>(P, I.rand_cur, jo, day, &kw));
         s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
@@ -427,7 +374,7 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
 }
 
 // lambda_j with its own bounds and block 0 (see lambda_at).
-template <bool OCC = true, bool REC = false, bool ROWMAP = false>
+template <bool OCC = true, bool REC = false, bool ROWMAP = false, bool WSG = false>
 __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out,
                                            uint32_t *rec = nullptr)
@@ -435,7 +382,7 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
     const RowBounds rb = row_bounds(P, j);
     RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
     if (P.rand_on) r0 = random_block0(P, jo, day);
-    return lambda_at<OCC, REC, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
+    return lambda_at<OCC, REC, ROWMAP, WSG>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
 }
 
 }  // namespace deabm

@@ -171,6 +171,19 @@ static cudaError_t clear_next_buffers(deabm_ctx *ctx, size_t count)
     return e;
 }
 
+// Philox4x32-10 round keys of a 64-bit seed: the key (low, high word) after r
+// bumps by the Weyl constants 0x9E3779B9, 0xBB67AE85, r = 0..9 (philox_rk)
+static void round_keys(uint64_t seed, uint32_t *rk)
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0;
+        rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
 // the Poisson thresholds as the day kernels' 32-bit words (KParams::pois32)
 static void set_pois32(KParams &K, const uint64_t *pois)
 {
@@ -475,6 +488,7 @@ static void build_reps(const deabm_params *p, uint32_t n_rep, const float *rep_p
         for (int q = 0; q < DEABM_N_AGE; ++q) R.S_age[q] = Sa[q];
         R.dose2_delay = delay;
         R.seed = rep_seeds ? rep_seeds[b] : p->seed;
+        round_keys(R.seed, R.rk);
     }
 }
 
@@ -802,6 +816,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 K.col[k] = ctx->col[k];
             }
             K.net_seed = p->net_seed;
+            round_keys(p->net_seed, K.nrk);
             K.test_on = p->test_on;
             K.test_lo = p->test_lo;
             K.test_hi = p->test_hi;
@@ -1297,6 +1312,7 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
                 pd.row_of = ctx->row_local + base;
             }
             K.net_seed = p.net_seed;
+            round_keys(p.net_seed, K.nrk);
             K.test_on = p.test_on;
             K.test_lo = p.test_lo;
             K.test_hi = p.test_hi;

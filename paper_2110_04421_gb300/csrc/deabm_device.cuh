@@ -42,6 +42,26 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
     return c;
 }
 __device__ __forceinline__ uint2 seed_key(uint64_t s) { return make_uint2((uint32_t)s, (uint32_t)(s >> 32)); }
+
+// The same generator with its ten round keys given: rk[2r], rk[2r+1] = the key
+// after r bumps (k + r (0x9E3779B9, 0xBB67AE85)), computed once on the host.  When
+// rk lives in the kernel's parameter space the round keys are operands of the
+// XORs, and the two adds of each round disappear.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ uint4 draw_rk(const uint32_t *rk, uint32_t agent, uint32_t day, uint32_t stream,
+                                         uint32_t blk = 0)
+{
+    return philox_rk(make_uint4(agent, day, stream, blk), rk);
+}
 __device__ __forceinline__ uint4 draw(uint2 key, uint32_t agent, uint32_t day, uint32_t stream, uint32_t blk = 0)
 {
     return philox(make_uint4(agent, day, stream, blk), key);
@@ -71,6 +91,7 @@ struct Rep {
     float S_age[DEABM_N_AGE];
     uint32_t dose2_delay;
     uint64_t seed;
+    uint32_t rk[20];             // Philox round keys of seed (philox_rk)
 };
 
 // by-value kernel argument
@@ -122,6 +143,7 @@ struct KParams {
     // thresholds from index pois_fin on are 2^32, which no word reaches.
     uint32_t pois32[DEABM_POIS_CAP];
     uint32_t pois_fin;
+    uint32_t nrk[20];  // Philox round keys of net_seed (philox_rk)
     // replicate 0's parameters by value: plain contexts read them from the
     // kernel's parameter space (uniform across the grid) instead of through `rep`
     Rep rep0;
@@ -240,9 +262,15 @@ __device__ __forceinline__ void new_infection(const Tables *tab, int age, uint4 
 
 // One day's update of one agent (everything after the infection draw).
 // `infected` = the draw succeeded this day; `day` is the day index.
+template <bool RK = false>
 __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 key, uint32_t j, uint32_t day,
                                         int age, int16_t d1, bool infected, AgentState &a, uint32_t inf_y)
 {
+    // the replicate's draws: from its round keys (RK: rp in parameter or shared
+    // space) or from the seed's key schedule
+    auto draw_rep = [&](uint32_t dday, uint32_t stream) {
+        return RK ? draw_rk(rp.rk, j, dday, stream) : draw(key, j, dday, stream);
+    };
     bool onset = false;
     // one draw site for a new infection and for the end of a stage, so that a
     // warp holding both runs the Philox rounds once
@@ -253,7 +281,7 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
     }
     const bool stage_ends = in_course && a.tm <= 0;
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    if (infected || stage_ends) w = draw(key, j, day, kStreamProg);
+    if (infected || stage_ends) w = draw_rep(day, kStreamProg);
     if (infected) {
         new_infection(P.tab, age, w, a);
     } else if (stage_ends) {
@@ -289,7 +317,7 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
             a.fl &= ~DEABM_FL_POS;
         }
     } else if ((onset || (a.fl & DEABM_FL_DEN)) && P.test_on && a.qd == 0u) {
-        const uint4 w = draw(key, j, day, kStreamTest);
+        const uint4 w = draw_rep(day, kStreamTest);
         if (a.st >= DEABM_ASYM && a.st <= DEABM_SEV && (uint64_t)w.x < P.thr_sens) a.fl |= DEABM_FL_POS;
         else a.fl &= ~DEABM_FL_POS;
         a.cd = uniform_int(w.y, P.test_lo, P.test_hi);
@@ -306,7 +334,7 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
             const bool on1 = (a.fl & DEABM_FL_DOSE1) && (int64_t)day == (int64_t)a.vd1 + (int64_t)P.vax_onset;
             const bool on2 = (a.fl & DEABM_FL_DOSE2) && (int64_t)day == (int64_t)a.vd2 + (int64_t)P.vax_onset;
             if (on1 || on2) {
-                const uint32_t v = draw(key, j, 0u, kStreamVax).x;
+                const uint32_t v = draw_rep(0u, kStreamVax).x;
                 if ((on1 && (uint64_t)v < P.thr_eff1) || (on2 && (uint64_t)v < P.thr_eff2)) {
                     if (P.vax_nonsterile) a.fl |= DEABM_FL_IMMUNE;
                     else a.st = DEABM_VAX;
@@ -322,7 +350,7 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
             const bool on1 = (a.fl & DEABM_FL_DOSE1) && t == D1 + (int64_t)P.vax_onset;
             const bool on2 = (a.fl & DEABM_FL_DOSE2) && t == D2 + (int64_t)P.vax_onset;
             if (on1 || on2) {
-                const uint32_t v = draw(key, j, 0u, kStreamVax).x;
+                const uint32_t v = draw_rep(0u, kStreamVax).x;
                 if ((on1 && (uint64_t)v < P.thr_eff1) || (on2 && (uint64_t)v < P.thr_eff2)) {
                     if (P.vax_nonsterile) a.fl |= DEABM_FL_IMMUNE;
                     else a.st = DEABM_VAX;

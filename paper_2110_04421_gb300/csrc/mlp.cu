@@ -291,33 +291,6 @@ __global__ void to_bf16_pad_t_kernel(const float *x, int rows, int cols, int ld,
     }
 }
 
-// dz_L = 2 (y_hat - y) / (B n_out) in FP32 [rows x cols], its BF16 copy with row
-// stride ldb and its BF16 transpose [cols x ldt], and the loss (block partials)
-__global__ void mse_grad_t_kernel(const float *yhat, const float *y, int rows, int cols, float scale, float *dz,
-                                  __nv_bfloat16 *dzb, int ldb, __nv_bfloat16 *dzt, int ldt, double *loss_part)
-{
-    __shared__ double red[256];
-    double acc = 0.0;
-    const long n = (long)rows * cols;
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x) {
-        const int r = (int)(q / cols), c = (int)(q % cols);
-        const float d = yhat[q] - y[q];
-        acc += (double)d * d;
-        const float gq = 2.0f * d * scale;
-        dz[q] = gq;
-        const __nv_bfloat16 b = __float2bfloat16(gq);
-        dzb[(long)r * ldb + c] = b;
-        dzt[(long)c * ldt + r] = b;
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
-}
-
 // BF16 weight copies of the tensor-core training path: W [fi x ldf] (the input
 // gradients' operand, K = fan-out) and W^T [fo x ldt] (the forward operand,
 // K = fan-in), zero in the padding
@@ -492,7 +465,7 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
         // also holds the bias-gradient partials [kColChunks][fan_out]
         const size_t wp = std::max(wmax_params * m->max_splits, (size_t)kColChunks * (size_t)std::max(m->H, m->n_out));
         if ((r = m_alloc(m, &m->wpart, wp))) return r;
-        if ((r = m_alloc(m, &m->loss_part, 1024))) return r;
+        if ((r = m_alloc(m, &m->loss_part, std::max<size_t>(1024, (B + 127) / 128)))) return r;
         m->tc_ok = m->n_in <= 64 && m->H % 64 == 0 && m->H <= 256 && m->n_out <= 256 && m->L <= kMaxTcLayers;
         if (m->tc_ok) {
             size_t total = 0;
@@ -773,17 +746,24 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             g.outt = m->actT[l + 1];
             g.ldt = m->bpad;
         } else {
-            g.epi = TC_EPI_OUTPUT;
-            g.outf = m->yhat;
+            // the output layer's epilogue is the loss gradient itself: dz_L, its BF16
+            // copies and the loss partials (y_hat is not stored)
+            g.epi = TC_EPI_MSE;
+            g.y = y;
+            g.scale = 1.0f / (float)((long)batch * m->n_out);
+            g.outf = m->dz;
             g.ldf = m->n_out;
+            g.outb = m->gb16[0];
+            g.ldo = m->ldg;
+            g.outt = m->gT[0];
+            g.ldt = m->bpad;
+            g.loss_part = m->loss_part;
         }
         MCU(mlptc_gemm(g, s));
     }
     const long n = (long)batch * m->n_out;
-    const int nparts = 256;
+    const int nparts = (batch + 127) / 128;
     int cur = 0;
-    mse_grad_t_kernel<<<nparts, 256, 0, s>>>(m->yhat, y, batch, m->n_out, 1.0f / (float)n, m->dz, m->gb16[cur], m->ldg,
-                                             m->gT[cur], m->bpad, m->loss_part);
     loss_reduce_kernel<<<1, 32, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
     MCU(cudaGetLastError());
     float *dz = m->dz, *dzo = m->dz2;

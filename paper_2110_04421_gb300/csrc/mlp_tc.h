@@ -33,6 +33,8 @@ enum TcEpi : int {
     TC_EPI_OUTPUT = 1,  // y = acc + bias -> outf [M x ldf]
     TC_EPI_DGRAD = 2,   // d = acc * gelu'(zin) -> outf (FP32), outb (BF16) and outt (BF16, transposed)
     TC_EPI_WGRAD = 3,   // acc -> outf + split * M * ldf (split-K partials over blockIdx.z)
+    TC_EPI_MSE = 4,     // y_hat = acc + bias; d = 2 (y_hat - y) scale -> outf (FP32), outb, outt;
+                        // sum of (y_hat - y)^2 over the CTA's rows -> loss_part[blockIdx.x] (FP64)
 };
 
 struct TcGemm {
@@ -52,6 +54,9 @@ struct TcGemm {
     int ldt;
     uint32_t polls;          // tries of each bounded wait before the kernel gives up
     int *err;                // set to 1 when a bounded wait gave up
+    const float *y;          // MSE: targets [M x N] (row stride N)
+    float scale;             // MSE: 1 / (M N)
+    double *loss_part;       // MSE: one partial per CTA row block (grid.x entries)
 };
 
 // one launch (asynchronous); cudaErrorInvalidValue for shapes it does not take

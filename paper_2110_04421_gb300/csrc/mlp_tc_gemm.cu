@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         const bool ok = nch > 0 ? mbar_wait_or_abort(smem_u32(&accb), 0u, g.polls, abort) : true;
         if (!ok) *abort = 1;
         tc_fence_after();
+        double sq = 0.0;  // MSE: this row's squared errors
         if (ok) {
             const bool rv = gm < (uint32_t)g.M;
             for (uint32_t cb = 0; cb < BN; cb += 32u) {
@@ -153,39 +154,100 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                 }
                 const uint32_t n = n0 + cb;
                 if (n >= (uint32_t)g.N) break;  // warp-uniform
+                // 32 whole columns: 16-byte vector loads and stores along the row
+                // (row strides and n are multiples of 4 elements); else one by one
                 const bool full32 = n + 32u <= (uint32_t)g.N;
                 if (g.epi == TC_EPI_WGRAD) {
                     if (rv) {
                         float *o = g.outf + (size_t)blockIdx.z * g.M * g.ldf + (size_t)gm * g.ldf + n;
-                        for (int e = 0; e < 32; ++e)
-                            if (n + e < (uint32_t)g.N) o[e] = v[e];
+                        if (full32) {
+#pragma unroll
+                            for (int c4 = 0; c4 < 8; ++c4)
+                                *(float4 *)(o + 4 * c4) = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+                        } else {
+                            for (int e = 0; e < 32; ++e)
+                                if (n + e < (uint32_t)g.N) o[e] = v[e];
+                        }
                     }
                     continue;
+                }
+                // bias (OUTPUT, HIDDEN, MSE)
+                if (g.epi != TC_EPI_DGRAD) {
+                    if (full32) {
+#pragma unroll
+                        for (int c4 = 0; c4 < 8; ++c4) {
+                            const float4 bb = __ldg((const float4 *)(g.bias + n) + c4);
+                            v[4 * c4] += bb.x;
+                            v[4 * c4 + 1] += bb.y;
+                            v[4 * c4 + 2] += bb.z;
+                            v[4 * c4 + 3] += bb.w;
+                        }
+                    } else {
+                        for (int e = 0; e < 32; ++e) v[e] += (n + e < (uint32_t)g.N) ? __ldg(g.bias + n + e) : 0.0f;
+                    }
                 }
                 if (g.epi == TC_EPI_OUTPUT) {
                     if (rv) {
                         float *o = g.outf + (size_t)gm * g.ldf + n;
-                        for (int e = 0; e < 32; ++e)
-                            if (n + e < (uint32_t)g.N) o[e] = v[e] + __ldg(g.bias + n + e);
+                        if (full32) {
+#pragma unroll
+                            for (int c4 = 0; c4 < 8; ++c4)
+                                *(float4 *)(o + 4 * c4) = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+                        } else {
+                            for (int e = 0; e < 32; ++e)
+                                if (n + e < (uint32_t)g.N) o[e] = v[e];
+                        }
                     }
                     continue;
                 }
-                // HIDDEN and DGRAD: the FP32 value, then its BF16 copies
-                if (g.epi == TC_EPI_HIDDEN) {
+                // the FP32 value this epilogue keeps: z (HIDDEN), dz (DGRAD, MSE)
+                float other[32];
+                if (rv && g.epi != TC_EPI_HIDDEN) {  // DGRAD: the pre-activation; MSE: the target
+                    const float *src = g.epi == TC_EPI_DGRAD ? g.zin + (size_t)gm * g.ldz + n : g.y + (size_t)gm * g.N + n;
+                    if (full32) {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const float z = v[e] + (n + e < (uint32_t)g.N ? __ldg(g.bias + n + e) : 0.0f);
-                        if (rv && n + e < (uint32_t)g.N) g.outf[(size_t)gm * g.ldf + n + e] = z;
-                        v[e] = gelu_erf(z);
+                        for (int c4 = 0; c4 < 8; ++c4) {
+                            const float4 t = __ldg((const float4 *)src + c4);
+                            other[4 * c4] = t.x;
+                            other[4 * c4 + 1] = t.y;
+                            other[4 * c4 + 2] = t.z;
+                            other[4 * c4 + 3] = t.w;
+                        }
+                    } else {
+                        for (int e = 0; e < 32; ++e) other[e] = (n + e < (uint32_t)g.N) ? __ldg(src + e) : 0.0f;
                     }
-                } else {  // DGRAD
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) other[e] = 0.0f;
+                }
+                if (g.epi == TC_EPI_DGRAD) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = v[e] * gelu_erf_grad(other[e]);
+                } else if (g.epi == TC_EPI_MSE) {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
-                        const float z = (rv && n + e < (uint32_t)g.N) ? __ldg(g.zin + (size_t)gm * g.ldz + n + e) : 0.0f;
-                        v[e] = v[e] * gelu_erf_grad(z);
-                        if (rv && n + e < (uint32_t)g.N) g.outf[(size_t)gm * g.ldf + n + e] = v[e];
+                        const float d = v[e] - other[e];
+                        if (rv && n + e < (uint32_t)g.N) sq += (double)d * d;
+                        v[e] = 2.0f * d * g.scale;
                     }
                 }
+                if (rv) {
+                    float *o = g.outf + (size_t)gm * g.ldf + n;
+                    if (full32) {
+#pragma unroll
+                        for (int c4 = 0; c4 < 8; ++c4)
+                            *(float4 *)(o + 4 * c4) = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+                    } else {
+                        for (int e = 0; e < 32; ++e)
+                            if (n + e < (uint32_t)g.N) o[e] = v[e];
+                    }
+                }
+                if (g.epi == TC_EPI_HIDDEN) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = gelu_erf(v[e]);
+                }
+                // the BF16 copies: row-major, then transposed (for each column the
+                // warp's 32 rows are 64 contiguous bytes)
                 if (rv) {
                     if (full32) {
                         uint4 *o = (uint4 *)(g.outb + (size_t)gm * g.ldo + n);
@@ -197,11 +259,20 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                         for (int e = 0; e < 32; ++e)
                             if (n + e < (uint32_t)g.N) g.outb[(size_t)gm * g.ldo + n + e] = __float2bfloat16(v[e]);
                     }
-                    // transposed copy: for each column, the warp's 32 rows are 64 contiguous bytes
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (n + e < (uint32_t)g.N) g.outt[(size_t)(n + e) * g.ldt + gm] = __float2bfloat16(v[e]);
                 }
+            }
+        }
+        if (g.epi == TC_EPI_MSE) {  // the CTA's squared errors, rows in a fixed order
+            __shared__ double s_sq[kBM];
+            s_sq[row] = sq;
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the four epilogue warps
+            if (row == 0) {
+                double t = 0.0;
+                for (uint32_t r = 0; r < kBM; ++r) t += s_sq[r];
+                g.loss_part[blockIdx.x] = t;
             }
         }
     }
@@ -272,8 +343,12 @@ cudaError_t mlptc_gemm(const TcGemm &g, cudaStream_t s)
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.kps <= 0 || g.kps % 64 || !g.err) return cudaErrorInvalidValue;
-    if ((g.epi == TC_EPI_HIDDEN || g.epi == TC_EPI_DGRAD) && (g.ldo % 8 || !g.outb || !g.outt || !g.outf))
+    if ((g.epi == TC_EPI_HIDDEN || g.epi == TC_EPI_DGRAD || g.epi == TC_EPI_MSE) &&
+        (g.ldo % 8 || !g.outb || !g.outt || !g.outf))
         return cudaErrorInvalidValue;
+    if (g.ldf % 4 || (g.epi == TC_EPI_DGRAD && g.ldz % 4) || (g.epi == TC_EPI_MSE && (!g.y || !g.loss_part || g.N % 4)))
+        return cudaErrorInvalidValue;
+    if (g.epi == TC_EPI_MSE && g.N > 256) return cudaErrorInvalidValue;  // one column tile per CTA row block
     KArgs ka{};
     ka.g = g;
     const uint32_t n16 = ((uint32_t)g.N + 15u) / 16u * 16u;

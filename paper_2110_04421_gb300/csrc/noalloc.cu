@@ -171,6 +171,15 @@ extern "C" int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t 
         K.col[k] = graph_dev->col[k];
     }
     K.net_seed = params->net_seed;
+    {
+        uint32_t k0 = (uint32_t)params->net_seed, k1 = (uint32_t)(params->net_seed >> 32);
+        for (int r = 0; r < 10; ++r) {  // the round keys of net_seed (philox_rk)
+            K.nrk[2 * r] = k0;
+            K.nrk[2 * r + 1] = k1;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
     K.tab = tab;
     K.pois_fin = 0;
     for (int k = 0; k < DEABM_POIS_CAP; ++k) {

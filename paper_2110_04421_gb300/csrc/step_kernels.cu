@@ -53,7 +53,7 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 // inside the library changes no result.
 // DEN: exposure notification on (plain contexts): an app holder records the day's
 // contacts, a positive app holder is marked for the notification pass.
-template <bool OCC = true, bool DEN = false, bool ROWMAP = false>
+template <bool OCC = true, bool DEN = false, bool ROWMAP = false, bool WSG = false, bool RK = false>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
                                           float *p_out, int *new_stage, bool *infected, uint32_t *k_out,
@@ -81,13 +81,13 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     if (P.rand_on) r0 = random_block0(P, jo, day);
     float lam = 0.0f;
     if (full) {
-        lam = lambda_at<OCC, DEN, ROWMAP>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
+        lam = lambda_at<OCC, DEN, ROWMAP, WSG>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
         uint32_t deg = 0;
 #pragma unroll
         for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) deg += rb.end[net] - rb.beg[net];
         *kg_out = *k_out + deg;
     } else {
-        *k_out = contact_count(P, j, r0.k, jo, day);
+        *k_out = contact_count<WSG>(P, j, r0.k, jo, day);
         *kg_out = 0;
     }
     a.tm = S.timer[i];
@@ -109,7 +109,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     // whole warps skip the Philox rounds
     const float lam_dt = __fmul_rn(lam, P.dt);
     if ((a.st == DEABM_S && lam_dt > 0.0f) || a.qd > 0u || lam_out != nullptr) {
-        const uint4 w = draw(key, jo, day, kStreamInf);
+        const uint4 w = RK ? draw_rk(rp.rk, jo, day, kStreamInf) : draw(key, jo, day, kStreamInf);
         inf_y = w.y;
         const bool hit = infection_decision(lam_dt, unit_float(w.x), &p);
         inf_now = (a.st == DEABM_S) && hit;
@@ -141,7 +141,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
         return;
     }
 #endif
-    advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
+    advance<RK>(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
     if (DEN) {  // a positive app holder notifies its contacts after the day
         const bool v = a.pos_result && (a.fl & DEABM_FL_APP);
         *notify = v;
@@ -212,7 +212,7 @@ __device__ __forceinline__ void count_day(bool active, int st, bool infected, ui
 #ifndef DEABM_OCC_MINB
 #define DEABM_OCC_MINB 10  // resident blocks per SM asked of the daily-occupation variant (swept: 8, 10, 12)
 #endif
-template <bool KEEP, bool OCC, bool DEN>
+template <bool KEEP, bool OCC, bool DEN, bool WSG>
 __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEABM_PLAIN_MINB) step_plain_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                          Counters C, float *lam_out, float *p_out)
 {
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
 #else
         const Rep &rp = P.rep[0];
 #endif
-        agent_day<OCC, DEN>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr, p_out, &st, &infected, &k, &kg,
-                            &notify);
+        agent_day<OCC, DEN, false, WSG, DEABM_REP_PARAM != 0>(P, rp, day, I, S, j, 1u, 0u, KEEP ? lam_out : nullptr,
+                                                             p_out, &st, &infected, &k, &kg, &notify);
     }
     if (DEN) {  // the day's positive app holders as a bit map over rows: one word per warp
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, notify);
@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             bool infected = false;
             uint32_t k = 0, kg = 0;
             if (active)
-                agent_day<false, false, true>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st, &infected, &k,
-                                              &kg);
+                agent_day<false, false, true, false, true>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
+                                                           &infected, &k, &kg);
             count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
         }
         __syncthreads();
@@ -449,12 +449,11 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
             const uint32_t g = __ldg(P.occ_gid + j);
             const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
             const uint32_t ko = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
-            const uint2 nk = seed_key(P.net_seed);
             float4 h = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (P.occ_lattice) {  // Watts-Strogatz contacts, two per Philox block (as occ_ws_sum)
                 const uint32_t own = j - beg;
                 for (uint32_t e = 0; e < ko; e += 2u) {
-                    const uint4 w = draw(nk, jo, day, kStreamWs, e >> 1);
+                    const uint4 w = draw_rk(P.nrk, jo, day, kStreamWs, e >> 1);
                     const uint32_t m = (e >> 1) + 1u;
                     const uint32_t hop = m < size ? m : m % size;
                     const uint32_t coin[2] = {w.x, w.z}, word[2] = {w.y, w.w};
@@ -477,7 +476,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
                 }
             } else {
                 for (uint32_t e = 0; e < ko; e += 4u) {
-                    const uint4 w = draw(nk, jo, day, kStreamOcc, e >> 2);
+                    const uint4 w = draw_rk(P.nrk, jo, day, kStreamOcc, e >> 2);
                     const uint32_t x[4] = {w.x, w.y, w.z, w.w};
                     float4 v[4];
 #pragma unroll
@@ -498,8 +497,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
             k = ko;
         }
         if (P.rand_on) {
-            const uint2 nk = seed_key(P.net_seed);
-            uint4 w = draw(nk, jo, day, kStreamRnet, 0u);
+            uint4 w = draw_rk(P.nrk, jo, day, kStreamRnet, 0u);
             const uint32_t kr = poisson_count(P, w.x);
             float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const uint64_t nm1 = (uint64_t)(P.n - 1u);
@@ -507,7 +505,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
             // as random_sum: contacts 0..2 from block 0, then four per block,
             // each block's gathers issued together and added in draw order
             for (uint32_t e = 0; e < kr; e += (e == 0u ? 3u : 4u)) {
-                if (e) w = draw(nk, jo, day, kStreamRnet, (e + 1u) >> 2);
+                if (e) w = draw_rk(P.nrk, jo, day, kStreamRnet, (e + 1u) >> 2);
                 const uint32_t x[4] = {w.x, w.y, w.z, w.w};
                 const uint32_t u0 = e == 0u ? 1u : 0u;  // block 0 starts at word 1
                 float4 v[4];
@@ -611,18 +609,23 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
 {
     if (P.n_rep == 1) {
         const dim3 grid((P.n + DEABM_PLAIN_BLOCK - 1u) / DEABM_PLAIN_BLOCK);
-        const int v = (lam_out ? 4 : 0) | (P.n_occ ? 2 : 0) | (P.den_on ? 1 : 0);
+        // the Watts-Strogatz random network excludes exposure notification (checked at create)
+        const int v = (P.wsg_on ? 8 : 0) | (lam_out ? 4 : 0) | (P.n_occ ? 2 : 0) | (P.den_on && !P.wsg_on ? 1 : 0);
         switch (v) {
-#define DEABM_PLAIN_CASE(c, K, O, D)                                                                      \
-    case c: step_plain_kernel<K, O, D><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out); break;
-            DEABM_PLAIN_CASE(0, false, false, false)
-            DEABM_PLAIN_CASE(1, false, false, true)
-            DEABM_PLAIN_CASE(2, false, true, false)
-            DEABM_PLAIN_CASE(3, false, true, true)
-            DEABM_PLAIN_CASE(4, true, false, false)
-            DEABM_PLAIN_CASE(5, true, false, true)
-            DEABM_PLAIN_CASE(6, true, true, false)
-            DEABM_PLAIN_CASE(7, true, true, true)
+#define DEABM_PLAIN_CASE(c, K, O, D, W)                                                                      \
+    case c: step_plain_kernel<K, O, D, W><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out); break;
+            DEABM_PLAIN_CASE(0, false, false, false, false)
+            DEABM_PLAIN_CASE(1, false, false, true, false)
+            DEABM_PLAIN_CASE(2, false, true, false, false)
+            DEABM_PLAIN_CASE(3, false, true, true, false)
+            DEABM_PLAIN_CASE(4, true, false, false, false)
+            DEABM_PLAIN_CASE(5, true, false, true, false)
+            DEABM_PLAIN_CASE(6, true, true, false, false)
+            DEABM_PLAIN_CASE(7, true, true, true, false)
+            DEABM_PLAIN_CASE(8, false, false, false, true)
+            DEABM_PLAIN_CASE(10, false, true, false, true)
+            DEABM_PLAIN_CASE(12, true, false, false, true)
+            DEABM_PLAIN_CASE(14, true, true, false, true)
 #undef DEABM_PLAIN_CASE
         }
     } else if (P.n_rep % kRepPerThread == 0) {

@@ -35,11 +35,10 @@ __global__ void wsg_mark_kernel(const KParams P, uint32_t day, uint8_t *rew, uin
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < P.n;
     const uint32_t h = P.wsg_h, lane = threadIdx.x & 31u;
-    const uint2 nk = seed_key(P.net_seed);
     uint32_t bits = 0;
     for (uint32_t m = 1; m <= h; m += 2u) {  // every lane runs every block (warp-wide appends)
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (active) w = draw(nk, i, day, kStreamWsg, (m - 1u) >> 1);
+        if (active) w = draw_rk(P.nrk, i, day, kStreamWsg, (m - 1u) >> 1);
 #pragma unroll
         for (uint32_t u = 0; u < 2u; ++u) {
             const uint32_t e = m + u;
