@@ -47,12 +47,20 @@ __device__ __forceinline__ uint2 seed_key(uint64_t s) { return make_uint2((uint3
 // after r bumps (k + r (0x9E3779B9, 0xBB67AE85)), computed once on the host.  When
 // rk lives in the kernel's parameter space the round keys are operands of the
 // XORs, and the two adds of each round disappear.
+#ifndef DEABM_PHILOX_WIDE
+#define DEABM_PHILOX_WIDE 0  // 1: each round's products as one 64-bit product per word
+#endif
 __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
+#if DEABM_PHILOX_WIDE
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#else
         const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
         const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#endif
         c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
     }
     return c;

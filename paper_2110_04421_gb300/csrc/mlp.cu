@@ -213,13 +213,30 @@ __global__ void mse_grad_kernel(const float *yhat, const float *y, long n, float
     if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
 }
 
+// the loss from its partials: one block of 256 threads, each summing a strided
+// share, then a fixed tree (deterministic)
 __global__ void loss_reduce_kernel(const double *part, int nparts, float scale, float *loss)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < nparts; ++q) s += part[q];
-        *loss = (float)(s * scale);
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += blockDim.x) s += part[q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *loss = (float)(red[0] * scale);
+}
+
+// db[j] = the sum of the per-CTA column partials [parts][cols], in part order
+__global__ void colsum_parts_kernel(const float *part, int parts, int cols, float *db)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    float s = 0.0f;
+    for (int c = 0; c < parts; ++c) s += part[(long)c * cols + j];
+    db[j] = s;
 }
 
 // db[j] = sum_i dz[i][j]: row chunks summed in parallel (partials [chunk][col]),
@@ -340,6 +357,7 @@ struct deabm_mlp {
     std::vector<__nv_bfloat16 *> actT, Wf, WT;
     __nv_bfloat16 *gb16[2] = {nullptr, nullptr}, *gT[2] = {nullptr, nullptr};
     uint32_t polls = 1u << 26;
+    float *bpart = nullptr;  // bias-gradient partials of the tcgen05 path [max_batch / 128][width]
 };
 
 static int ld8(int v) { return (v + 7) / 8 * 8; }
@@ -501,6 +519,7 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
                 if ((r = m_alloc(m, &m->gb16[q], B * m->ldg))) return r;
                 if ((r = m_alloc(m, &m->gT[q], (size_t)m->ldg * m->bpad))) return r;
             }
+            if ((r = m_alloc(m, &m->bpart, ((B + 127) / 128) * (size_t)m->ldg))) return r;
         }
         MCU(cudaStreamSynchronize(m->stream));
         return DEABM_OK;
@@ -609,7 +628,7 @@ static int mlp_backward_dev(deabm_mlp *m, const float *y, int batch, float *loss
     const long n = (long)batch * m->n_out;
     const int nparts = 256;
     mse_grad_kernel<<<nparts, 256, 0, s>>>(m->yhat, y, n, 1.0f / (float)n, m->dz, m->dzb, m->loss_part);
-    loss_reduce_kernel<<<1, 32, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
+    loss_reduce_kernel<<<1, 256, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
     MCU(cudaGetLastError());
     float *dz = m->dz, *dzo = m->dz2;
     __nv_bfloat16 *dzb = m->dzb, *dzbo = m->dzb2;
@@ -751,8 +770,9 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             g.epi = TC_EPI_MSE;
             g.y = y;
             g.scale = 1.0f / (float)((long)batch * m->n_out);
-            g.outf = m->dz;
+            g.outf = nullptr;  // dz_L stays in BF16; its column sums (the bias gradient) come as partials
             g.ldf = m->n_out;
+            g.bpart = m->bpart;
             g.outb = m->gb16[0];
             g.ldo = m->ldg;
             g.outt = m->gT[0];
@@ -764,9 +784,8 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
     const long n = (long)batch * m->n_out;
     const int nparts = (batch + 127) / 128;
     int cur = 0;
-    loss_reduce_kernel<<<1, 32, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
+    loss_reduce_kernel<<<1, 256, 0, s>>>(m->loss_part, nparts, 1.0f / (float)n, m->loss);
     MCU(cudaGetLastError());
-    float *dz = m->dz, *dzo = m->dz2;
     for (int l = m->L - 1; l >= 0; --l) {
         const int fo = m->fout[l], fi = m->fin[l];
         // dW_l = a_l^T dz_l, split over the batch, partials summed in split order
@@ -793,8 +812,8 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             splitk_reduce_kernel<<<256, 256, 0, s>>>(m->wpart, splits, (long)fi * fo, m->gW[l]);
             MCU(cudaGetLastError());
         }
-        colsum_partial_kernel<<<dim3((fo + 31) / 32, kColChunks), 256, 0, s>>>(dz, batch, fo, m->wpart);
-        colsum_final_kernel<<<(fo + 127) / 128, 128, 0, s>>>(m->wpart, fo, m->gb[l]);
+        // db_l from the partials the epilogue that produced dz_l left (one per 128 rows)
+        colsum_parts_kernel<<<(fo + 127) / 128, 128, 0, s>>>(m->bpart, nparts, fo, m->gb[l]);
         MCU(cudaGetLastError());
         if (l > 0) {
             // dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})
@@ -810,8 +829,9 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             gd.epi = TC_EPI_DGRAD;
             gd.zin = m->z[l - 1];
             gd.ldz = m->H;
-            gd.outf = dzo;
+            gd.outf = nullptr;
             gd.ldf = m->H;
+            gd.bpart = m->bpart;
             gd.outb = m->gb16[cur ^ 1];
             gd.ldo = m->ldg;
             gd.outt = m->gT[cur ^ 1];
@@ -819,7 +839,6 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             gd.polls = m->polls;
             gd.err = m->tc_err;
             MCU(mlptc_gemm(gd, s));
-            std::swap(dz, dzo);
             cur ^= 1;
         }
     }

@@ -57,6 +57,8 @@ struct TcGemm {
     const float *y;          // MSE: targets [M x N] (row stride N)
     float scale;             // MSE: 1 / (M N)
     double *loss_part;       // MSE: one partial per CTA row block (grid.x entries)
+    float *bpart;            // DGRAD, MSE: if set, the column sums of the CTA's rows of d
+                             // [grid.x x N] (the bias gradient's partials); outf may then be null
 };
 
 // one launch (asynchronous); cudaErrorInvalidValue for shapes it does not take

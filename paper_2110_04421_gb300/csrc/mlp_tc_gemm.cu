@@ -142,6 +142,11 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         if (!ok) *abort = 1;
         tc_fence_after();
         double sq = 0.0;  // MSE: this row's squared errors
+        // bias-gradient partials: each epilogue warp's column sums over its 32 rows,
+        // through a transposed tile in the (no longer read) operand buffers
+        const bool colsums = g.bpart && (g.epi == TC_EPI_DGRAD || g.epi == TC_EPI_MSE);
+        float *tile = (float *)smem + q * (32u * 33u);            // [32 columns][33]
+        float *wsum = (float *)smem + 4u * 32u * 33u + q * 256u;  // this warp's sums of BN <= 256 columns
         if (ok) {
             const bool rv = gm < (uint32_t)g.M;
             for (uint32_t cb = 0; cb < BN; cb += 32u) {
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                         v[e] = 2.0f * d * g.scale;
                     }
                 }
-                if (rv) {
+                if (rv && g.outf) {
                     float *o = g.outf + (size_t)gm * g.ldf + n;
                     if (full32) {
 #pragma unroll
@@ -241,6 +246,16 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                         for (int e = 0; e < 32; ++e)
                             if (n + e < (uint32_t)g.N) o[e] = v[e];
                     }
+                }
+                if (colsums) {  // lane e's column: its 32 rows in order
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) tile[e * 33 + lane] = rv ? v[e] : 0.0f;
+                    __syncwarp();
+                    float cs = 0.0f;
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r) cs += tile[lane * 33 + r];
+                    wsum[cb + lane] = cs;
+                    __syncwarp();
                 }
                 if (g.epi == TC_EPI_HIDDEN) {
 #pragma unroll
@@ -273,6 +288,14 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                 double t = 0.0;
                 for (uint32_t r = 0; r < kBM; ++r) t += s_sq[r];
                 g.loss_part[blockIdx.x] = t;
+            }
+        }
+        if (colsums) {  // the CTA's column sums: the four warps' sums in warp order
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");
+            const float *ws = (const float *)smem + 4u * 32u * 33u;
+            for (uint32_t c = row; c < BN && n0 + c < (uint32_t)g.N; c += kBM) {
+                const float t = ok ? (ws[c] + ws[256u + c]) + (ws[512u + c] + ws[768u + c]) : 0.0f;
+                g.bpart[(size_t)blockIdx.x * g.N + n0 + c] = t;
             }
         }
     }
@@ -344,8 +367,9 @@ cudaError_t mlptc_gemm(const TcGemm &g, cudaStream_t s)
     if (attr_err != cudaSuccess) return attr_err;
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.kps <= 0 || g.kps % 64 || !g.err) return cudaErrorInvalidValue;
     if ((g.epi == TC_EPI_HIDDEN || g.epi == TC_EPI_DGRAD || g.epi == TC_EPI_MSE) &&
-        (g.ldo % 8 || !g.outb || !g.outt || !g.outf))
+        (g.ldo % 8 || !g.outb || !g.outt || (!g.outf && !g.bpart) || (g.epi == TC_EPI_HIDDEN && !g.outf)))
         return cudaErrorInvalidValue;
+    if (g.bpart && g.N > 256) return cudaErrorInvalidValue;  // one column tile per CTA row block
     if (g.ldf % 4 || (g.epi == TC_EPI_DGRAD && g.ldz % 4) || (g.epi == TC_EPI_MSE && (!g.y || !g.loss_part || g.N % 4)))
         return cudaErrorInvalidValue;
     if (g.epi == TC_EPI_MSE && g.N > 256) return cudaErrorInvalidValue;  // one column tile per CTA row block
