@@ -439,6 +439,21 @@ int deabm_relaxed_forward(deabm_relaxed *ctx, uint32_t T, const float *theta, fl
 int deabm_grad(deabm_relaxed *ctx, uint32_t T, const float *theta, const float *target, float *loss, float *grad,
                float *incidence);
 
+/* The loss and gradient of B parameter columns at once (the Abstract's and
+ * Sec. 1's gradient-based calibration over many candidate parameter sets): theta
+ * host float[B][13] (each >= 0, finite), target host float[T][B] (column b =
+ * log(I*_b(t) + 1)); loss float[B], grad float[B][13] (d loss_b / d theta_b) and
+ * incidence float[T][B] are host outputs, any may be NULL (target is required for
+ * loss and grad).  The columns share the graph, the initial cases and the
+ * relaxed draw's noise; each column's per-agent sums run as in deabm_grad, with
+ * agent state laid out [agent][column], so every day reads each edge list once
+ * for all columns.  Device arrays for B columns are allocated on the first call
+ * that needs them (about (L + 1) (T / ckpt_every + 2) + 7 ckpt_every floats per
+ * agent and column; DEABM_ENOMEM if they do not fit) and kept for later calls.
+ * 1 <= B <= 4096.  Synchronises.  Errors: DEABM_EINVAL, DEABM_ENOMEM, DEABM_ECUDA. */
+int deabm_grad_batch(deabm_relaxed *ctx, uint32_t T, uint32_t B, const float *theta, const float *target,
+                     float *loss, float *grad, float *incidence);
+
 /* `steps` Adam steps (lr; beta 0.9 / 0.999; eps 1e-8; parameters kept >= 0)
  * from theta0 against target, entirely on the device.  theta_out (float[13])
  * and loss_trace (float[steps], the loss before each step) may be NULL. */

@@ -229,14 +229,22 @@ __global__ void loss_reduce_kernel(const double *part, int nparts, float scale, 
     if (threadIdx.x == 0) *loss = (float)(red[0] * scale);
 }
 
-// db[j] = the sum of the per-CTA column partials [parts][cols], in part order
+// db[j] = the sum of the per-CTA column partials part[parts][cols]: one block of
+// 128 threads per column, each summing a strided share of the parts, then a fixed
+// tree (deterministic)
 __global__ void colsum_parts_kernel(const float *part, int parts, int cols, float *db)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+    __shared__ float red[128];
+    const int j = blockIdx.x;
     float s = 0.0f;
-    for (int c = 0; c < parts; ++c) s += part[(long)c * cols + j];
-    db[j] = s;
+    for (int c = threadIdx.x; c < parts; c += blockDim.x) s += part[(long)c * cols + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[j] = red[0];
 }
 
 // db[j] = sum_i dz[i][j]: row chunks summed in parallel (partials [chunk][col]),
@@ -813,7 +821,7 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             MCU(cudaGetLastError());
         }
         // db_l from the partials the epilogue that produced dz_l left (one per 128 rows)
-        colsum_parts_kernel<<<(fo + 127) / 128, 128, 0, s>>>(m->bpart, nparts, fo, m->gb[l]);
+        colsum_parts_kernel<<<fo, 128, 0, s>>>(m->bpart, nparts, fo, m->gb[l]);
         MCU(cudaGetLastError());
         if (l > 0) {
             // dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})

@@ -315,6 +315,246 @@ __global__ void rx_seed_kernel(const RxParams P, const uint32_t *seeds, uint32_t
     xring[seeds[q]] = 1.0f;  // slot 0 = day -1
 }
 
+
+// ------------------------------------------------------------------ B parameter columns
+// The same relaxed model for B parameter vectors theta_b at once (deabm_grad_batch):
+// every per-agent array becomes [agent][column] with the column fastest.  A block
+// is 8 agents x 32 columns, a warp one agent's 32 columns, so each CSR entry is
+// one broadcast load for 32 columns and each gather a contiguous 128-byte run:
+// the edge lists are read once a day for all columns.  The columns share the
+// graph, the initial cases and the noise (common random numbers); only theta
+// differs.  Every per-column sum runs in the single-column order, so a column
+// equals a single run up to FMA contraction and the scatter atomics' order.
+struct RxbArrays {
+    uint32_t B, nbx;        // columns; blocks along the agents (8 agents each)
+    const float *theta;     // [B][13]
+    float *s, *xring, *inf, *Ipart, *ibring, *sbar, *coef;
+    float *x, *g, *sr, *lam, *H;  // segment records [K][N][B]; H [K][n_nets + 1][N][B]
+    double *gpart;          // [nbx][B][13]
+};
+
+__device__ __forceinline__ float rxb_weight(const RxParams &P, const float *th, uint32_t net)
+{
+    return net < 2 ? th[1 + net] : P.B_extra[net];
+}
+
+__global__ void rxb_init_kernel(const RxParams P, RxbArrays A, const uint32_t *seeds, uint32_t n_seeds)
+{
+    const size_t nb = (size_t)P.n * A.B, stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < (size_t)P.L * nb; q += stride) {
+        if (q < nb) A.s[q] = 1.0f;
+        A.xring[q] = 0.0f;
+    }
+}
+
+__global__ void rxb_seed_kernel(const RxParams P, RxbArrays A, const uint32_t *seeds, uint32_t n_seeds)
+{
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)n_seeds * A.B) return;
+    const size_t i = (size_t)seeds[q / A.B] * A.B + q % A.B;
+    A.s[i] = 0.0f;
+    A.xring[i] = 1.0f;  // slot 0 = day -1
+}
+
+__global__ void rxb_inf_kernel(const RxParams P, RxbArrays A, int t)
+{
+    const uint32_t i = blockIdx.x * 8u + threadIdx.y, b = blockIdx.y * 32u + threadIdx.x;
+    if (i >= P.n || b >= A.B) return;
+    const int c = P.cls[i];
+    float v = 0.0f;
+    for (uint32_t d = 1; d < P.L; ++d)
+        v += __ldg(&P.tab->infT[c][d]) * A.xring[((size_t)ring_slot(t - (int)d, P.L) * P.n + i) * A.B + b];
+    A.inf[(size_t)i * A.B + b] = v;
+}
+
+template <bool REC>
+__global__ void __launch_bounds__(256) rxb_day_kernel(const RxParams P, RxbArrays A, int t, int k)
+{
+    __shared__ float sI[8][32];
+    const uint32_t lane = threadIdx.x, ay = threadIdx.y;
+    const uint32_t j = blockIdx.x * 8u + ay, b = blockIdx.y * 32u + lane;
+    const uint32_t B = A.B;
+    float x = 0.0f;
+    if (j < P.n && b < B) {
+        const float *th = A.theta + (size_t)b * kTheta;
+        const float *inf = A.inf;
+        const size_t nn = (size_t)P.n_nets + 1;
+        float ssum = 0.0f;
+        for (uint32_t net = 0; net < P.n_nets; ++net) {
+            float h = 0.0f;
+            for (uint32_t e = __ldg(P.row_ptr[net] + j); e < __ldg(P.row_ptr[net] + j + 1); ++e)
+                h = __fadd_rn(h, __ldg(inf + (size_t)__ldg(P.col[net] + e) * B + b));
+            ssum = __fadd_rn(ssum, __fmul_rn(rxb_weight(P, th, net), h));
+            if (REC) A.H[(((size_t)k * nn + net) * P.n + j) * B + b] = h;
+        }
+        float r = 0.0f;
+        if (P.rand_on) {
+            const uint2 nk = seed_key(P.net_seed);
+            uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+            uint32_t kk = 0;
+            while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+            for (uint32_t e = 0; e < kk; ++e) {
+                const uint32_t idx = e + 1u;
+                if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
+                const uint32_t xw = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+                uint32_t v = (uint32_t)(((uint64_t)xw * (uint64_t)(P.n - 1u)) >> 32);
+                v += (v >= j) ? 1u : 0u;
+                r = __fadd_rn(r, __ldg(inf + (size_t)v * B + b));
+            }
+            ssum = __fadd_rn(ssum, __fmul_rn(th[3], r));
+        }
+        if (REC) A.H[(((size_t)k * nn + P.n_nets) * P.n + j) * B + b] = r;
+        const float lam = th[0] * P.inv_Ibar * th[4 + P.age[j]] * ssum;
+        const float g = lam > 0.0f ? sigmoidf_((logit_p(lam) + logistic_noise(P.seed, j, (uint32_t)t)) / P.tau) : 0.0f;
+        const size_t q = (size_t)j * B + b;
+        const float sj = A.s[q];
+        x = sj * g;
+        A.s[q] = sj - x;
+        A.xring[(size_t)ring_slot(t, P.L) * P.n * B + q] = x;
+        if (REC) {
+            const size_t qk = (size_t)k * P.n * B + q;
+            A.x[qk] = x;
+            A.g[qk] = g;
+            A.sr[qk] = sj;
+            A.lam[qk] = lam;
+        }
+    }
+    // block partial of I(t) per column over the block's 8 agents, in a fixed order
+    sI[ay][lane] = x;
+    __syncthreads();
+    if (ay == 0 && b < B) {
+        float v = 0.0f;
+        for (uint32_t q = 0; q < 8u; ++q) v += sI[q][lane];
+        A.Ipart[((size_t)t * A.nbx + blockIdx.x) * B + b] = v;
+    }
+}
+
+// I(t), the loss and d loss / d I(t) of column blockIdx.x (256 threads, fixed tree)
+__global__ void rxb_loss_kernel(const RxParams P, RxbArrays A, uint32_t T, const float *y, float *I, float *Ibar,
+                                float *loss)
+{
+    __shared__ double red[256];
+    const uint32_t b = blockIdx.x, B = A.B;
+    double acc = 0.0;
+    for (uint32_t t = 0; t < T; ++t) {
+        double s = 0.0;
+        for (uint32_t q = threadIdx.x; q < A.nbx; q += blockDim.x) s += A.Ipart[((size_t)t * A.nbx + q) * B + b];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (uint32_t w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double tot = red[0];
+            I[(size_t)t * B + b] = (float)tot;
+            if (y) {
+                const double d = log(tot + 1.0) - (double)y[(size_t)t * B + b];
+                acc += d * d;
+                Ibar[(size_t)t * B + b] = (float)(2.0 / T * d / (tot + 1.0));
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && y) loss[b] = (float)(acc / T);
+}
+
+__global__ void __launch_bounds__(256) rxb_adj_kernel(const RxParams P, RxbArrays A, int t, int k, const float *Ibar)
+{
+    __shared__ float red[kTheta][8][32];
+    const uint32_t lane = threadIdx.x, ay = threadIdx.y;
+    const uint32_t j = blockIdx.x * 8u + ay, b = blockIdx.y * 32u + lane;
+    const uint32_t B = A.B;
+    float contrib[kTheta];
+#pragma unroll
+    for (int q = 0; q < kTheta; ++q) contrib[q] = 0.0f;
+    if (j < P.n && b < B) {
+        const float *th = A.theta + (size_t)b * kTheta;
+        const int c = P.cls[j], a = P.age[j];
+        const size_t qj = (size_t)j * B + b;
+        float xbar = Ibar[(size_t)t * B + b] - A.sbar[qj];
+        for (uint32_t d = 1; d < P.L && (uint32_t)t + d < P.T; ++d)
+            xbar += __ldg(&P.tab->infT[c][d]) * A.ibring[((size_t)(((uint32_t)t + d) % P.L) * P.n) * B + qj];
+        const size_t q = (size_t)k * P.n * B + qj;
+        const float g = A.g[q], lam = A.lam[q], sj = A.sr[q];
+        const float gbar = xbar * sj;
+        const float lbar = (lam > 0.0f && g > 0.0f) ? gbar * g * (1.0f - g) / (P.tau * (-expm1f(-lam))) : 0.0f;
+        A.sbar[qj] = xbar * g + A.sbar[qj];
+        const float R = th[0], Sa = th[4 + a], cR = R * P.inv_Ibar;
+        const float cf = lbar * cR * Sa;
+        A.coef[qj] = cf;
+        float ssum = 0.0f;
+        const size_t nn = (size_t)P.n_nets + 1;
+        for (uint32_t net = 0; net <= P.n_nets; ++net) {
+            const float h = A.H[(((size_t)k * nn + net) * P.n + j) * B + b];
+            const float w = net < P.n_nets ? rxb_weight(P, th, net) : th[3];
+            ssum += w * h;
+            if (net < 2 && net < P.n_nets) contrib[1 + net] = cf * h;
+            if (net == P.n_nets && P.rand_on) contrib[3] = cf * h;
+        }
+        contrib[0] = lbar * P.inv_Ibar * Sa * ssum;
+#pragma unroll
+        for (int q2 = 0; q2 < DEABM_N_AGE; ++q2) contrib[4 + q2] = (q2 == a) ? lbar * cR * ssum : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < kTheta; ++q) red[q][ay][lane] = contrib[q];
+    __syncthreads();
+    if (ay == 0 && b < B) {
+        double *gp = A.gpart + ((size_t)blockIdx.x * B + b) * kTheta;
+        for (int q = 0; q < kTheta; ++q) {
+            double v = 0.0;
+            for (uint32_t a2 = 0; a2 < 8u; ++a2) v += red[q][a2][lane];
+            gp[q] += v;
+        }
+    }
+}
+
+__global__ void rxb_scatter_static_kernel(const RxParams P, RxbArrays A, int t)
+{
+    const uint32_t i = blockIdx.x * 8u + threadIdx.y, b = blockIdx.y * 32u + threadIdx.x;
+    if (i >= P.n || b >= A.B) return;
+    const float *th = A.theta + (size_t)b * kTheta;
+    float v = 0.0f;
+    for (uint32_t net = 0; net < P.n_nets; ++net) {
+        float h = 0.0f;
+        for (uint32_t e = __ldg(P.tr_ptr[net] + i); e < __ldg(P.tr_ptr[net] + i + 1); ++e)
+            h += __ldg(A.coef + (size_t)__ldg(P.tr_col[net] + e) * A.B + b);
+        v += rxb_weight(P, th, net) * h;
+    }
+    A.ibring[((size_t)((uint32_t)t % P.L) * P.n + i) * A.B + b] = v;
+}
+
+__global__ void rxb_scatter_random_kernel(const RxParams P, RxbArrays A, int t)
+{
+    const uint32_t j = blockIdx.x * 8u + threadIdx.y, b = blockIdx.y * 32u + threadIdx.x;
+    if (j >= P.n || b >= A.B) return;
+    const float cf = A.coef[(size_t)j * A.B + b] * A.theta[(size_t)b * kTheta + 3];
+    if (cf == 0.0f) return;
+    const uint2 nk = seed_key(P.net_seed);
+    uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+    uint32_t kk = 0;
+    while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+    float *dst = A.ibring + (size_t)((uint32_t)t % P.L) * P.n * A.B;
+    for (uint32_t e = 0; e < kk; ++e) {
+        const uint32_t idx = e + 1u;
+        if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
+        const uint32_t xw = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+        uint32_t v = (uint32_t)(((uint64_t)xw * (uint64_t)(P.n - 1u)) >> 32);
+        v += (v >= j) ? 1u : 0u;
+        atomicAdd(dst + (size_t)v * A.B + b, cf);
+    }
+}
+
+__global__ void rxb_grad_reduce_kernel(const RxbArrays A, float *grad)
+{
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;  // (column, parameter)
+    if (q >= A.B * (uint32_t)kTheta) return;
+    const uint32_t b = q / kTheta, p = q % kTheta;
+    double s = 0.0;
+    for (uint32_t blk = 0; blk < A.nbx; ++blk) s += A.gpart[((size_t)blk * A.B + b) * kTheta + p];
+    grad[q] = (float)s;
+}
+
 }  // namespace deabm
 
 using namespace deabm;
@@ -330,6 +570,13 @@ struct deabm_relaxed {
     RxSeg seg{};
     float *Ipart = nullptr, *I = nullptr, *y = nullptr, *Ibar = nullptr, *loss = nullptr, *loss_trace = nullptr;
     float *ibring = nullptr, *sbar = nullptr, *coef = nullptr;
+    // B parameter columns (deabm_grad_batch): arrays for bat_cap columns, allocated
+    // on the first call that needs them
+    uint32_t bat_cap = 0;
+    std::vector<void *> bat_allocs;
+    RxbArrays bat{};
+    float *b_ckpt = nullptr, *b_I = nullptr, *b_y = nullptr, *b_Ibar = nullptr, *b_loss = nullptr, *b_grad = nullptr;
+    float *b_theta = nullptr;
     double *gpart = nullptr;
     uint32_t *seeds = nullptr;
     uint32_t trace_cap = 0;
@@ -390,6 +637,7 @@ extern "C" void deabm_relaxed_destroy(deabm_relaxed *c)
     if (c->grad_graph) (void)cudaGraphExecDestroy(c->grad_graph);
     if (c->cap_stream) (void)cudaStreamDestroy(c->cap_stream);
     for (void *p : c->allocs) (void)cudaFree(p);
+    for (void *p : c->bat_allocs) (void)cudaFree(p);
     delete c;
 }
 
@@ -699,3 +947,134 @@ extern "C" int deabm_calibrate(deabm_relaxed *c, uint32_t T, const float *theta0
 }
 
 extern "C" const char *deabm_relaxed_last_error(void) { return g_rx_err.c_str(); }
+
+// ------------------------------------------------------------------ B parameter columns
+template <class T>
+static int rxb_alloc(deabm_relaxed *c, T **out, size_t count)
+{
+    void *p = nullptr;
+    const size_t bytes = count ? count * sizeof(T) : sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return rx_fail(DEABM_ENOMEM, "cudaMalloc of %zu bytes for %u columns failed", bytes, c->bat_cap);
+    }
+    c->bat_allocs.push_back(p);
+    *out = (T *)p;
+    return DEABM_OK;
+}
+
+// arrays for B columns (kept, grown when a call needs more)
+static int rxb_reserve(deabm_relaxed *c, uint32_t B)
+{
+    if (B <= c->bat_cap) return DEABM_OK;
+    RCU(cudaStreamSynchronize(c->stream));
+    for (void *p : c->bat_allocs) (void)cudaFree(p);
+    c->bat_allocs.clear();
+    c->bat_cap = B;
+    const size_t n = c->n, L = c->L, K = c->K, NN = (size_t)c->n_nets + 1, nb = n * B;
+    const uint32_t nbx = (uint32_t)((n + 7) / 8);
+    RxbArrays &A = c->bat;
+    A.nbx = nbx;
+    int r;
+    if ((r = rxb_alloc(c, &c->b_theta, (size_t)B * kTheta))) return r;
+    if ((r = rxb_alloc(c, &A.s, nb))) return r;
+    if ((r = rxb_alloc(c, &A.xring, L * nb))) return r;
+    if ((r = rxb_alloc(c, &A.inf, nb))) return r;
+    if ((r = rxb_alloc(c, &c->b_ckpt, (size_t)c->nseg * (L + 1) * nb))) return r;
+    if ((r = rxb_alloc(c, &A.x, K * nb))) return r;
+    if ((r = rxb_alloc(c, &A.g, K * nb))) return r;
+    if ((r = rxb_alloc(c, &A.sr, K * nb))) return r;
+    if ((r = rxb_alloc(c, &A.lam, K * nb))) return r;
+    if ((r = rxb_alloc(c, &A.H, K * NN * nb))) return r;
+    if ((r = rxb_alloc(c, &A.Ipart, (size_t)c->max_days * nbx * B))) return r;
+    if ((r = rxb_alloc(c, &A.ibring, L * nb))) return r;
+    if ((r = rxb_alloc(c, &A.sbar, nb))) return r;
+    if ((r = rxb_alloc(c, &A.coef, nb))) return r;
+    if ((r = rxb_alloc(c, &A.gpart, (size_t)nbx * B * kTheta))) return r;
+    if ((r = rxb_alloc(c, &c->b_I, (size_t)c->max_days * B))) return r;
+    if ((r = rxb_alloc(c, &c->b_y, (size_t)c->max_days * B))) return r;
+    if ((r = rxb_alloc(c, &c->b_Ibar, (size_t)c->max_days * B))) return r;
+    if ((r = rxb_alloc(c, &c->b_loss, B))) return r;
+    if ((r = rxb_alloc(c, &c->b_grad, (size_t)B * kTheta))) return r;
+    return DEABM_OK;
+}
+
+// forward with checkpoints and the reverse sweep for B columns
+static int rxb_gradient(deabm_relaxed *c, uint32_t T, uint32_t B, bool want_grad)
+{
+    cudaStream_t s = c->stream;
+    RxParams P = c->P;
+    P.T = T;
+    RxbArrays A = c->bat;
+    A.B = B;
+    A.theta = c->b_theta;
+    const size_t n = c->n, L = c->L, nb = n * B;
+    const dim3 blk(32, 8), grid((unsigned)((n + 7) / 8), (B + 31) / 32);
+    rxb_init_kernel<<<1024, 256, 0, s>>>(P, A, c->seeds, c->n_seeds);
+    if (c->n_seeds)
+        rxb_seed_kernel<<<(unsigned)(((size_t)c->n_seeds * B + 255) / 256), 256, 0, s>>>(P, A, c->seeds, c->n_seeds);
+    RCU(cudaGetLastError());
+    for (uint32_t t = 0; t < T; ++t) {
+        if (t % c->K == 0) {
+            float *ck = c->b_ckpt + (size_t)(t / c->K) * (L + 1) * nb;
+            RCU(cudaMemcpyAsync(ck, A.s, 4 * nb, cudaMemcpyDeviceToDevice, s));
+            RCU(cudaMemcpyAsync(ck + nb, A.xring, 4 * L * nb, cudaMemcpyDeviceToDevice, s));
+        }
+        rxb_inf_kernel<<<grid, blk, 0, s>>>(P, A, (int)t);
+        rxb_day_kernel<false><<<grid, blk, 0, s>>>(P, A, (int)t, 0);
+    }
+    rxb_loss_kernel<<<B, 256, 0, s>>>(P, A, T, c->b_y, c->b_I, c->b_Ibar, c->b_loss);
+    RCU(cudaGetLastError());
+    if (!want_grad) return DEABM_OK;
+    RCU(cudaMemsetAsync(A.sbar, 0, 4 * nb, s));
+    RCU(cudaMemsetAsync(A.ibring, 0, 4 * L * nb, s));
+    RCU(cudaMemsetAsync(A.gpart, 0, sizeof(double) * A.nbx * B * kTheta, s));
+    const uint32_t nseg = (T + c->K - 1) / c->K;
+    for (int sg = (int)nseg - 1; sg >= 0; --sg) {
+        const uint32_t t0 = (uint32_t)sg * c->K, t1 = t0 + c->K < T ? t0 + c->K : T;
+        const float *ck = c->b_ckpt + (size_t)sg * (L + 1) * nb;
+        RCU(cudaMemcpyAsync(A.s, ck, 4 * nb, cudaMemcpyDeviceToDevice, s));
+        RCU(cudaMemcpyAsync(A.xring, ck + nb, 4 * L * nb, cudaMemcpyDeviceToDevice, s));
+        for (uint32_t t = t0; t < t1; ++t) {
+            rxb_inf_kernel<<<grid, blk, 0, s>>>(P, A, (int)t);
+            rxb_day_kernel<true><<<grid, blk, 0, s>>>(P, A, (int)t, (int)(t - t0));
+        }
+        for (int t = (int)t1 - 1; t >= (int)t0; --t) {
+            rxb_adj_kernel<<<grid, blk, 0, s>>>(P, A, t, t - (int)t0, c->b_Ibar);
+            rxb_scatter_static_kernel<<<grid, blk, 0, s>>>(P, A, t);
+            if (P.rand_on) rxb_scatter_random_kernel<<<grid, blk, 0, s>>>(P, A, t);
+        }
+    }
+    rxb_grad_reduce_kernel<<<(B * kTheta + 255) / 256, 256, 0, s>>>(A, c->b_grad);
+    RCU(cudaGetLastError());
+    return DEABM_OK;
+}
+
+extern "C" int deabm_grad_batch(deabm_relaxed *c, uint32_t T, uint32_t B, const float *theta, const float *target,
+                                float *loss, float *grad, float *incidence)
+{
+    int r;
+    if ((r = rx_check(c, T))) return r;
+    if (B == 0 || B > 4096) return rx_fail(DEABM_EINVAL, "B must be in 1..4096");
+    if (!theta || (!target && (loss || grad))) return rx_fail(DEABM_EINVAL, "theta is required, and target for loss or grad");
+    for (size_t q = 0; q < (size_t)B * kTheta; ++q)
+        if (!(theta[q] >= 0.0f) || !std::isfinite(theta[q]))
+            return rx_fail(DEABM_EINVAL, "theta[%zu][%zu] must be finite and >= 0", q / kTheta, q % kTheta);
+    if ((r = rxb_reserve(c, B))) return r;
+    cudaStream_t s = c->stream;
+    RCU(cudaMemcpyAsync(c->b_theta, theta, 4ull * B * kTheta, cudaMemcpyHostToDevice, s));
+    if (target) RCU(cudaMemcpyAsync(c->b_y, target, 4ull * T * B, cudaMemcpyHostToDevice, s));
+    c->bat.B = B;
+    // without a target only the forward pass runs (the loss kernel then skips the loss)
+    float *ysave = c->b_y;
+    if (!target) c->b_y = nullptr;
+    r = rxb_gradient(c, T, B, grad != nullptr);
+    c->b_y = ysave;
+    if (r) return r;
+    if (loss) RCU(cudaMemcpyAsync(loss, c->b_loss, 4ull * B, cudaMemcpyDeviceToHost, s));
+    if (grad) RCU(cudaMemcpyAsync(grad, c->b_grad, 4ull * B * kTheta, cudaMemcpyDeviceToHost, s));
+    if (incidence) RCU(cudaMemcpyAsync(incidence, c->b_I, 4ull * T * B, cudaMemcpyDeviceToHost, s));
+    RCU(cudaStreamSynchronize(s));
+    return DEABM_OK;
+}

@@ -27,7 +27,7 @@ EXPORTS = ("deabm_create", "deabm_create_batch", "deabm_step", "deabm_run", "dea
            "deabm_lambda_noalloc", "deabm_lambda_noalloc_last_error", "deabm_create_ragged", "deabm_autotune",
            "deabm_mlp_use_tcgen05", "deabm_get_dose_days", "deabm_get_notified", "deabm_save", "deabm_restore",
            "deabm_mlp_apply_grads", "deabm_get_gathered", "deabm_mlp_set_wait_limit",
-           "deabm_inject_alloc_failure")
+           "deabm_inject_alloc_failure", "deabm_grad_batch")
 N_THETA = 13
 NOALLOC_MAX_AGENTS = 1 << 20  # agents the library's fixed working array holds (deabm_lambda_noalloc)
 
@@ -137,6 +137,7 @@ def lib():
         L.deabm_get_gathered.argtypes = [vp, u32, vp]
         L.deabm_mlp_set_wait_limit.argtypes = [vp, u32]
         L.deabm_inject_alloc_failure.argtypes = [u32]
+        L.deabm_grad_batch.argtypes = [vp, u32, u32, vp, vp, vp, vp, vp]
         L.deabm_inject_alloc_failure.restype = None
         L.deabm_mlp_use_tcgen05.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.deabm_mlp_use_tcgen05.restype = C.c_int
@@ -149,7 +150,7 @@ def lib():
                      "deabm_relaxed_forward", "deabm_grad", "deabm_calibrate", "deabm_reset", "deabm_mlp_create",
                      "deabm_mlp_param_count", "deabm_mlp_set_params", "deabm_mlp_get_params", "deabm_mlp_forward",
                      "deabm_mlp_grad", "deabm_mlp_train_step", "deabm_mlp_sync", "deabm_mlp_apply_grads",
-                     "deabm_get_gathered", "deabm_mlp_set_wait_limit"):
+                     "deabm_get_gathered", "deabm_mlp_set_wait_limit", "deabm_grad_batch"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -291,6 +292,20 @@ class Relaxed:
         inc = np.zeros(T, np.float32)
         _rx_check(lib().deabm_grad(self.ctx, T, _p(th), _p(y), _p(loss), _p(g), _p(inc)))
         return float(loss[0]), g, inc
+
+    def grad_batch(self, theta, target):
+        """Loss and gradient of B parameter columns at once (deabm_grad_batch):
+        theta [B, 13], target [T, B] -> loss [B], grad [B, 13], incidence [T, B]."""
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        y = np.ascontiguousarray(target, dtype=np.float32)
+        B = th.shape[0]
+        assert th.shape == (B, N_THETA) and y.ndim == 2 and y.shape[1] == B
+        T = y.shape[0]
+        loss = np.zeros(B, np.float32)
+        g = np.zeros((B, N_THETA), np.float32)
+        inc = np.zeros((T, B), np.float32)
+        _rx_check(lib().deabm_grad_batch(self.ctx, T, B, _p(th), _p(y), _p(loss), _p(g), _p(inc)))
+        return loss, g, inc
 
     def calibrate(self, theta0, target, steps: int, lr: float):
         th0 = np.ascontiguousarray(theta0, dtype=np.float32)

@@ -157,3 +157,66 @@ def test_full_size_gradient():
         tm[i] -= 1e-3
         fd = (rx.run(tp, T, target=y, fp32_theta=False)["loss"] - rx.run(tm, T, target=y, fp32_theta=False)["loss"]) / 2e-3
         assert abs(grad[i] - fd) <= 1e-3 * max(abs(fd), 1e-2 * scale), (i, grad[i], fd)
+
+
+def test_batched_gradient_columns_match_oracle_and_single_runs(case):
+    """deabm_grad_batch over 5 parameter columns (R, the network weights and the
+    age susceptibilities varied per column; B = 5 leaves a partial 32-column warp):
+    each column's loss, gradient and incidence equal a single deabm_grad at that
+    theta (within FP32 rounding: the reverse sweep's random-network atomics add in
+    a different order) and the oracle's reverse sweep within the single path's bar."""
+    pop, p, T, rx, th, y = case
+    rng = np.random.default_rng(3)
+    B = 5
+    thetas = np.repeat(np.float32(th)[None, :], B, axis=0)
+    thetas[:, 0] *= rng.uniform(0.8, 1.25, B).astype(np.float32)
+    thetas[:, 1:4] *= rng.uniform(0.7, 1.3, (B, 3)).astype(np.float32)
+    thetas[:, 4:] *= rng.uniform(0.9, 1.1, (B, 9)).astype(np.float32)
+    targets = np.stack([y + np.float32(0.05 * b) for b in range(B)], axis=1)
+    g = gpu(pop, p, max_days=T, ckpt_every=10)
+    loss_b, grad_b, inc_b = g.grad_batch(thetas, targets)
+    singles = [g.grad(thetas[b], targets[:, b]) for b in range(B)]
+    g.close()
+    for b in range(B):
+        ls, gs, inc = singles[b]
+        scale = np.linalg.norm(gs)
+        assert abs(loss_b[b] - ls) <= 1e-5 * ls, (b, loss_b[b], ls)
+        assert np.max(np.abs(grad_b[b] - gs)) <= 1e-5 * scale, (b, grad_b[b], gs)
+        assert np.allclose(inc_b[:, b], inc, rtol=1e-5, atol=1e-3)
+    for b in (0, B - 1):
+        o = rx.run(thetas[b], T, target=targets[:, b].astype(np.float64), grad=True)
+        scale = np.linalg.norm(o["grad"])
+        assert abs(loss_b[b] - o["loss"]) <= 1e-4 * o["loss"]
+        assert np.max(np.abs(grad_b[b] - o["grad"])) <= 1e-4 * scale, (b, grad_b[b], o["grad"])
+    assert len({round(float(v), 6) for v in loss_b}) == B  # the columns ran different problems
+    from paper_2110_04421_gb300.deabm import DeabmError
+    g = gpu(pop, p, max_days=T)
+    bad = thetas.copy()
+    bad[2, 5] = -1.0
+    with pytest.raises(DeabmError, match="must be finite and >= 0"):
+        g.grad_batch(bad, targets)
+    g.close()
+
+
+def test_batched_gradient_full_workload_sample_columns():
+    """N = 100,000, 90 days, checkpoint every 10, B = 64 columns of the calibration
+    box (R in [2, 6], weights in [0.5, 2]); columns 0, 31, 63 against the oracle's
+    reverse sweep at the single path's bar."""
+    w = W.relaxed_workload()
+    pop = W.population(w["n"], 0, w["n_seed"])
+    p, T = w["params"], w["T"]
+    rx = oracle.Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=w["tau"])
+    y = np.log(rx.run(w["hidden"], T)["incidence"] + 1.0).astype(np.float32)
+    B = 64
+    rng = np.random.default_rng(9)
+    thetas = np.repeat(w["start"][None, :], B, axis=0).astype(np.float32)
+    thetas[:, 0] = rng.uniform(2.0, 6.0, B)
+    thetas[:, 1:4] = rng.uniform(0.5, 2.0, (B, 3))
+    g = gpu(pop, p, max_days=T, ckpt_every=10, tau=w["tau"])
+    loss_b, grad_b, _ = g.grad_batch(thetas, np.repeat(y[:, None], B, axis=1))
+    g.close()
+    for b in (0, 31, 63):
+        o = rx.run(thetas[b], T, target=y, grad=True)
+        scale = np.linalg.norm(o["grad"])
+        assert abs(loss_b[b] - o["loss"]) <= 1e-4 * o["loss"], b
+        assert np.max(np.abs(grad_b[b] - o["grad"])) <= 1e-4 * scale, (b, grad_b[b], o["grad"])
