@@ -62,10 +62,9 @@ def step_bytes_plain_needed(n: int, static_edges: int, n_nets: int, vax: bool, n
 
 
 def step_bytes_batch(n: int, B: int, static_edges: int, n_nets: int, vax: bool) -> int:
-    """Same for the [N][B] panel of a four-replicate batch: per (agent, replicate)
-    state 7 + 7 B and its 1-byte emission code read and written (1 + 1 B); per
-    agent age and first-dose day; the CSR once for all replicates."""
-    return 4 * (n + 1) * n_nets + 4 * static_edges + n * (1 + (2 if vax else 0)) + n * B * (7 + 7 + 1 + 1)
+    """Same for the [N][B] panel: per (agent, replicate) 7 + 7 + 4 + 4 B; per agent
+    age and first-dose day; the CSR once for all replicates."""
+    return 4 * (n + 1) * n_nets + 4 * static_edges + n * (1 + (2 if vax else 0)) + n * B * (7 + 7 + 4 + 4)
 
 
 def step_bytes_occ(n: int, static_edges: int, n_nets: int, n_occ: int, vax: bool) -> int:

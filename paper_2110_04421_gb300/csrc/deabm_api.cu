@@ -31,7 +31,6 @@ struct deabm_ctx {
     uint32_t *row_ptr[DEABM_MAX_NETS] = {};
     uint32_t *col[DEABM_MAX_NETS] = {};
     WsgBuffers wsg{};                         // the day's Watts-Strogatz random network (rand_ws)
-    bool inf_codes = false;                   // inf[] hold 1-byte emission codes (four-replicate batches)
     uint8_t *age = nullptr;
     int16_t *dose1 = nullptr;
     StateRef S{};
@@ -167,7 +166,7 @@ static uint64_t threshold(double p)
 // susceptible agent's entry untouched (it emits nothing).
 static cudaError_t clear_next_buffers(deabm_ctx *ctx, size_t count)
 {
-    cudaError_t e = cudaMemsetAsync(ctx->inf[1], 0, (ctx->inf_codes ? 1u : sizeof(float)) * count, ctx->stream);
+    cudaError_t e = cudaMemsetAsync(ctx->inf[1], 0, sizeof(float) * count, ctx->stream);
     if (e == cudaSuccess && ctx->inf_rand[1]) e = cudaMemsetAsync(ctx->inf_rand[1], 0, sizeof(float) * count, ctx->stream);
     return e;
 }
@@ -637,19 +636,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->S.tinf, nb))) return r;
             if ((r = dalloc(ctx, &ctx->S.flags, nb))) return r;
             if ((r = dalloc(ctx, &ctx->S.qt, nb))) return r;
-            // batches of four-replicate groups keep 1-byte emission codes instead of
-            // FP32 infectiousness in their [N][B] panels (step_batch4_kernel)
-            ctx->inf_codes = n_rep > 1 && n_rep % 4 == 0;
-            if (ctx->inf_codes) {
-                uint8_t *c0, *c1;
-                if ((r = dalloc(ctx, &c0, nb))) return r;
-                if ((r = dalloc(ctx, &c1, nb))) return r;
-                ctx->inf[0] = (float *)c0;  // byte panels; only the batched kernels and the emit kernel touch them
-                ctx->inf[1] = (float *)c1;
-            } else {
-                if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
-                if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
-            }
+            if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
+            if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
             if (ctx->relabel && (g->rand_mean > 0.0f || g->rand_ws) && n_rep == 1) {
                 if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
                 if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
@@ -844,7 +832,6 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.rep = ctx->rep;
             set_pois32(K, T.pois);
             K.rep0 = reps[0];
-            K.inf_codes = ctx->inf_codes ? 1u : 0u;
             K.age = ctx->age;
             K.dose1_day = ctx->dose1;
             K.orig_id = ctx->relabel ? ctx->orig_id : nullptr;

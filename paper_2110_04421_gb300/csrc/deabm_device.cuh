@@ -152,7 +152,6 @@ struct KParams {
     uint32_t pois32[DEABM_POIS_CAP];
     uint32_t pois_fin;
     uint32_t nrk[20];  // Philox round keys of net_seed (philox_rk)
-    uint32_t inf_codes;  // 1: the [N][B] infectiousness panels hold emission codes (emit_code)
     // replicate 0's parameters by value: plain contexts read them from the
     // kernel's parameter space (uniform across the grid) instead of through `rep`
     Rep rep0;
@@ -257,16 +256,6 @@ __device__ __forceinline__ float emitted(const Tables *tab, uint32_t L, int st, 
     const int c = infector_class(st);
     if (c < 0 || qd != 0u || ti < 0 || (uint32_t)ti >= L) return 0.0f;
     return __ldg(&tab->infT[c][ti]);
-}
-
-// The same as a 1-byte code: 0 = emits nothing, else 1 + 64 c + tinf, so that
-// entry code of the day's 256-entry lookup table (entry 0 = 0, entry 1 + 64 c + t
-// = A_c infT_c[t]) is exactly emitted()'s value.
-__device__ __forceinline__ uint8_t emit_code(uint32_t L, int st, int ti, uint32_t qd)
-{
-    const int c = infector_class(st);
-    if (c < 0 || qd != 0u || ti < 0 || (uint32_t)ti >= L) return 0;
-    return (uint8_t)(1 + 64 * c + ti);
 }
 
 __device__ __forceinline__ void new_infection(const Tables *tab, int age, uint4 w, AgentState &a)

@@ -138,10 +138,6 @@ __global__ void emit_kernel(const KParams P, StateRef S, float *inf, float *inf_
 {
     const size_t total = (size_t)P.n * P.n_rep;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        if (P.inf_codes) {  // four-replicate batches: the panel holds emission codes
-            ((uint8_t *)inf)[i] = emit_code(P.inf_len, S.stage[i], S.tinf[i], S.qt[i] & 0x0Fu);
-            continue;
-        }
         const float v = emitted(P.tab, P.inf_len, S.stage[i], S.tinf[i], S.qt[i] & 0x0Fu);
         inf[i] = v;
         if (inf_rand) {

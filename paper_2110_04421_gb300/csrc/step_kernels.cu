@@ -398,14 +398,6 @@ constexpr uint32_t kRepPerThread = 4;
 #endif
 constexpr int kB4Unroll = DEABM_B4_UNROLL;
 
-// four replicates' infectiousness from their 1-byte emission codes (one 4-byte
-// load, four table lookups in shared memory)
-__device__ __forceinline__ float4 code_gather4(const uint8_t *panel, size_t off, const float *tab)
-{
-    const uchar4 c = __ldg((const uchar4 *)(panel + off));
-    return make_float4(tab[c.x], tab[c.y], tab[c.z], tab[c.w]);
-}
-
 __device__ __forceinline__ void add4(float4 &h, const float4 v)
 {
     h.x = __fadd_rn(h.x, v.x);
@@ -425,20 +417,13 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
 {
     __shared__ int s_cnt[DEABM_N_STAGE + 1][32 * kRepPerThread];
     __shared__ unsigned long long s_msgs;
-    // the day's emission-code table: entry 0 = 0, entry 1 + 64 c + t = A_c infT_c[t]
-    __shared__ float s_tab[256];
     const uint32_t lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32u + lane;
     const uint32_t j = blockIdx.x * 8u + wy;
     const uint32_t B = P.n_rep;
     const uint32_t b0 = blockIdx.y * (32u * kRepPerThread) + lane * kRepPerThread;
     for (uint32_t q = tid; q < (DEABM_N_STAGE + 1) * 32u * kRepPerThread; q += 256u) (&s_cnt[0][0])[q] = 0;
     if (tid == 0) s_msgs = 0ull;
-    s_tab[tid] = (tid >= 1u && tid <= 3u * DEABM_MAX_INF_LEN) ? __ldg(&P.tab->infT[(tid - 1u) / DEABM_MAX_INF_LEN][(tid - 1u) % DEABM_MAX_INF_LEN])
-                                                           : 0.0f;
     __syncthreads();
-    // the [N][B] panels hold 1-byte emission codes (KParams::inf_codes)
-    const uint8_t *cur8 = (const uint8_t *)I.cur;
-    uint8_t *next8 = (uint8_t *)I.next;
     uint32_t k = 0;
     if (j < P.n && b0 < B) {
         const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
@@ -450,7 +435,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
             const uint32_t e1 = __ldg(P.row_ptr[net] + j + 1);
             for (uint32_t e = __ldg(P.row_ptr[net] + j); e < e1; ++e) {
                 const uint32_t c = __ldg(P.col[net] + e);
-                add4(h, code_gather4(cur8, (size_t)c * B + b0, s_tab));
+                add4(h, __ldg((const float4 *)(I.cur + (size_t)c * B + b0)));
             }
             const float hv[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
@@ -483,7 +468,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
                             r = own + off;
                             r = r >= size ? r - size : r;
                         }
-                        v[u] = (e + u < ko) ? code_gather4(cur8, (size_t)(beg + r) * B + b0, s_tab)
+                        v[u] = (e + u < ko) ? __ldg((const float4 *)(I.cur + (size_t)(beg + r) * B + b0))
                                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     }
                     add4(h, v[0]);
@@ -496,7 +481,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
                     float4 v[4];
 #pragma unroll
                     for (uint32_t u = 0; u < 4u; ++u)
-                        v[u] = (e + u < ko) ? code_gather4(cur8, (size_t)(beg + occ_place(x[u], size - 1u, j - beg)) * B + b0, s_tab)
+                        v[u] = (e + u < ko) ? __ldg((const float4 *)(I.cur + (size_t)(beg + occ_place(x[u], size - 1u, j - beg)) * B + b0))
                                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
                     for (uint32_t u = 0; u < 4u; ++u)
@@ -516,7 +501,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
             const uint32_t kr = poisson_count(P, w.x);
             float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const uint64_t nm1 = (uint64_t)(P.n - 1u);
-
+            const float *panel = I.row_of ? I.cur : I.rand_cur;
             // as random_sum: contacts 0..2 from block 0, then four per block,
             // each block's gathers issued together and added in draw order
             for (uint32_t e = 0; e < kr; e += (e == 0u ? 3u : 4u)) {
@@ -530,7 +515,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
                     uint32_t src = (uint32_t)(((uint64_t)x[u] * nm1) >> 32);
                     src += (src >= jo) ? 1u : 0u;
                     const bool ok = u >= u0 && c < kr;
-                    v[u] = ok ? code_gather4(cur8, (size_t)(I.row_of ? __ldg(I.row_of + src) : src) * B + b0, s_tab)
+                    v[u] = ok ? __ldg((const float4 *)(panel + (size_t)(I.row_of ? __ldg(I.row_of + src) : src) * B + b0))
                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 }
 #pragma unroll
@@ -558,7 +543,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
         int8_t st_out[4];
         int16_t tm_out[4], ti_out[4];
         uint8_t fl_out[4], qt_out[4];
-        uint8_t code_out[4];
+        float inf_out[4];
         const int16_t d1 = P.vax_on ? __ldg(P.dose1_day + j) : kNever;
 #pragma unroll kB4Unroll
         for (uint32_t v = 0; v < kRepPerThread; ++v) {
@@ -588,7 +573,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
             ti_out[v] = (int16_t)a.ti;
             fl_out[v] = (uint8_t)a.fl;
             qt_out[v] = (uint8_t)((a.qd & 0x0Fu) | ((a.cd & 0x07u) << 4));
-            code_out[v] = emit_code(P.inf_len, a.st, a.ti, a.qd);
+            inf_out[v] = emitted(P.tab, P.inf_len, a.st, a.ti, a.qd);
             if (KEEP) {
                 lam_out[i0 + v] = lam;
                 p_out[i0 + v] = p;
@@ -601,7 +586,9 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
         *(short4 *)(S.tinf + i0) = make_short4(ti_out[0], ti_out[1], ti_out[2], ti_out[3]);
         *(uchar4 *)(S.flags + i0) = make_uchar4(fl_out[0], fl_out[1], fl_out[2], fl_out[3]);
         *(uchar4 *)(S.qt + i0) = make_uchar4(qt_out[0], qt_out[1], qt_out[2], qt_out[3]);
-        *(uchar4 *)(next8 + i0) = make_uchar4(code_out[0], code_out[1], code_out[2], code_out[3]);
+        const float4 iv = make_float4(inf_out[0], inf_out[1], inf_out[2], inf_out[3]);
+        *(float4 *)(I.next + i0) = iv;
+        if (I.rand_next) *(float4 *)(I.rand_next + (size_t)jo * B + b0) = iv;
     }
     if (lane == 0 && blockIdx.y == 0 && j < P.n && k) atomicAdd(&s_msgs, (unsigned long long)k);
     __syncthreads();
