@@ -225,12 +225,16 @@ typedef struct {
     uint32_t den_window;
 } deabm_params;
 
-/* Create a plain (one replicate) simulation.  Validates the graph (monotone
- * row_ptr, col < n_agents, no self-loops, < 2^32 edges), the agents (age bins,
- * stage codes) and the parameters, copies everything to the device on `stream`,
- * builds the infectiousness table and the vaccination schedule there, and
- * infects seed_ids.  On success *out owns all device memory it allocated.
- * Errors: DEABM_EINVAL, DEABM_ENOMEM, DEABM_ECUDA. */
+/* Create a plain (one replicate) simulation: the population of Sec. 3 "Agent
+ * State Definition" on the interaction networks of Sec. 3 "Interaction Networks",
+ * with the infectiousness curve of Eq. 1 (its daily integrals, built on the
+ * device) and the vaccination schedule of Sec. 4.4 / Sec. 5.  Validates the graph
+ * (monotone row_ptr, col < n_agents, no self-loops, < 2^32 edges), the agents
+ * (age bins, stage codes) and the parameters, copies everything to the device on
+ * `stream` and infects seed_ids.  The network weights B_n travel in params, not
+ * in the graph: they are per-replicate parameters of Eq. 1 (varied across the
+ * columns of a batch), while the graph is shared.  On success *out owns all
+ * device memory it allocated.  Errors: DEABM_EINVAL, DEABM_ENOMEM, DEABM_ECUDA. */
 int deabm_create(const deabm_graph *graph, const deabm_agents *agents, const deabm_params *params,
                  void *cuda_stream, deabm_ctx **out);
 
@@ -267,18 +271,24 @@ int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, const deabm_
  * keep the fastest and restart at day 0.  Either output may be NULL.  Synchronises. */
 int deabm_autotune(deabm_ctx *ctx, uint32_t days_per_trial, uint32_t *rows_per_tile, uint32_t *blocks_per_sm);
 
-/* Queue n_steps days on the context's stream and return without waiting.
- * DEABM_ESTATE if the day counter would pass max_steps. */
+/* Queue n_steps days on the context's stream and return without waiting.  One
+ * day is one step of the simulation (Sec. 2.1 message passing; Sec. 3
+ * "Infection Transmission", Eq. 1-2, the draw; Sec. 3 "Disease Progression" and
+ * Sec. 4 interventions, the state update), all agents updated from the state at
+ * the start of the day.  DEABM_ESTATE if the day counter would pass max_steps. */
 int deabm_step(deabm_ctx *ctx, uint32_t n_steps);
 
 /* Run T days, then copy the per-day counters of those days to the host and
  * synchronise.  new_inf: host int32 [T][n_rep] new infections per day;
- * hist: host int32 [T][n_rep][11] stage counts after each day, or NULL. */
+ * hist: host int32 [T][n_rep][11] stage counts after each day, or NULL (the
+ * daily incidence and stage curves the paper reports, Sec. 4.5 and Sec. 5). */
 int deabm_run(deabm_ctx *ctx, uint32_t T, int32_t *new_inf, int32_t *hist);
 
 /* Copy the current state (host arrays of n_agents * n_rep entries; any may be
- * NULL) and, if params.keep_lambda was set, lambda and p of the last day.
- * Synchronises the stream. */
+ * NULL): the stage of Sec. 3 "Agent State Definition" and the timers of "Disease
+ * Progression"; and, if params.keep_lambda was set, lambda (Eq. 1 summed over the
+ * agent's interactions) and p = 1 - exp(-lambda dt) (Eq. 2) of the last day.
+ * Caller's agent order.  Synchronises the stream. */
 int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf, uint8_t *flags,
                     uint8_t *qt, float *lambda, float *p);
 
@@ -287,8 +297,9 @@ int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf
 int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day);
 
 /* Per-day counters already run: days [0, day_count) of new infections
- * [day][n_rep], stage histogram [day][n_rep][11] and messages processed
- * [day] (static in-edges + that day's random in-contacts, per replicate).
+ * [day][n_rep], stage histogram [day][n_rep][11] (Sec. 4.5 outcomes) and
+ * messages processed [day] (static in-edges + that day's random in-contacts, per
+ * replicate: the paper's interactions, Abstract and Sec. 1).
  * Any output may be NULL.  Synchronises. */
 int deabm_get_counters(deabm_ctx *ctx, uint32_t day_count, int32_t *new_inf, int32_t *hist,
                        uint64_t *messages);
@@ -395,7 +406,8 @@ int deabm_sync(deabm_ctx *ctx);
  * The string stays valid until the next call on the same ctx / thread. */
 const char *deabm_last_error(const deabm_ctx *ctx);
 
-/* Free all device memory of ctx.  NULL-safe. */
+/* Free all device memory of ctx (the library-side lifetime of the simulated
+ * population; the paper has no counterpart).  NULL-safe. */
 void deabm_destroy(deabm_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------------

@@ -9,6 +9,16 @@
 
 namespace deabm {
 
+// A block of the day's network words (net_seed): from the precomputed round keys
+// when the parameters live in the kernel's parameter space (RK), else from the
+// seed's key schedule (parameters in shared memory, where the keys would cost
+// a load each).
+template <bool RK = true>
+__device__ __forceinline__ uint4 net_draw(const KParams &P, uint32_t agent, uint32_t day, uint32_t stream, uint32_t blk)
+{
+    return RK ? draw_rk(P.nrk, agent, day, stream, blk) : draw(seed_key(P.net_seed), agent, day, stream, blk);
+}
+
 // Sum of inf over one CSR row, left to right from +0.0f.  The row is taken in
 // rounds of kRound edges: all column loads of a round are issued, then all
 // gathers, then the adds in order, so a row of up to kRound in-edges costs two
@@ -73,10 +83,11 @@ struct RandBlock0 {
     uint32_t k;
 };
 
+template <bool RK = true>
 __device__ __forceinline__ RandBlock0 random_block0(const KParams &P, uint32_t j, uint32_t day)
 {
     RandBlock0 r;
-    r.w = draw_rk(P.nrk, j, day, kStreamRnet, 0u);
+    r.w = net_draw<RK>(P, j, day, kStreamRnet, 0u);
     r.k = poisson_count(P, r.w.x);
     return r;
 }
@@ -103,7 +114,7 @@ __device__ __forceinline__ RandHead random_head(const KParams &P, const float *_
 
 // The sum over all k random contacts in draw order: block 0's values from the
 // head, then four contacts per further block, each block's gathers together.
-template <bool REC, bool ROWMAP>
+template <bool REC, bool ROWMAP, bool RK = true>
 __device__ __forceinline__ float random_tail(const KParams &P, const float *__restrict__ inf, uint32_t j,
                                              uint32_t day, uint32_t stride, uint32_t b, const RandHead &h,
                                              uint32_t *rec, const uint32_t *row_of)
@@ -114,7 +125,7 @@ __device__ __forceinline__ float random_tail(const KParams &P, const float *__re
         if (u < h.k) r = __fadd_rn(r, h.v[u]);
     const uint64_t nm1 = (uint64_t)(P.n - 1u);
     for (uint32_t e = 3u; e < h.k; e += 4u) {
-        const uint4 w = draw_rk(P.nrk, j, day, kStreamRnet, (e + 1u) >> 2);
+        const uint4 w = net_draw<RK>(P, j, day, kStreamRnet, (e + 1u) >> 2);
         const uint32_t x[4] = {w.x, w.y, w.z, w.w};
         float v[4];
 #pragma unroll
@@ -161,7 +172,7 @@ __device__ __forceinline__ uint32_t wsg_far(const KParams &P, uint32_t i, uint32
 // summed left to right from +0.0f: its own edges m = 1..h, the unrewired lattice
 // edges of agents jo - m, m = 1..h, then the rewired edges that landed on jo, by
 // owner ascending.  *k_out = their number.  NEED_SUM = false: the count only.
-template <bool NEED_SUM = true>
+template <bool NEED_SUM = true, bool RK = true>
 __device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restrict__ inf, uint32_t jo, uint32_t day,
                                          uint32_t *k_out)
 {
@@ -170,7 +181,7 @@ __device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restri
     uint32_t k = h;
     if (NEED_SUM) {
         for (uint32_t m = 1; m <= h; m += 2u) {
-            const uint4 w = draw_rk(P.nrk, jo, day, kStreamWsg, (m - 1u) >> 1);
+            const uint4 w = net_draw<RK>(P, jo, day, kStreamWsg, (m - 1u) >> 1);
             const uint32_t f0 = wsg_far(P, jo, m, w.x, w.y);
             const float v0 = __ldg(inf + f0);
             float v1 = 0.0f;
@@ -211,14 +222,14 @@ __device__ __forceinline__ uint32_t occ_place(uint32_t x, uint32_t size_m1, uint
 // own - (e/2+1) (e odd), unless the edge is rewired (coin below the threshold,
 // or a lattice offset that is a multiple of the size): then from a uniform
 // other member.  Two contacts per Philox block.
-template <bool REC = false>
+template <bool REC = false, bool RK = true>
 __device__ __forceinline__ float occ_ws_sum(const KParams &P, const float *__restrict__ inf, uint32_t jo, uint32_t day,
                                             uint32_t stride, uint32_t b, uint32_t beg, uint32_t size, uint32_t own,
                                             uint32_t k, uint32_t *rec)
 {
     float h = 0.0f;
     for (uint32_t e = 0; e < k; e += 2u) {
-        const uint4 w = draw_rk(P.nrk, jo, day, kStreamWs, e >> 1);
+        const uint4 w = net_draw<RK>(P, jo, day, kStreamWs, e >> 1);
         const uint32_t m = (e >> 1) + 1u;
         const uint32_t hop = m < size ? m : m % size;
         const uint32_t coin[2] = {w.x, w.z}, word[2] = {w.y, w.w};
@@ -242,7 +253,7 @@ __device__ __forceinline__ float occ_ws_sum(const KParams &P, const float *__res
     return h;
 }
 
-template <bool REC = false>
+template <bool REC = false, bool RK = true>
 __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restrict__ inf, uint32_t j, uint32_t jo,
                                          uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
                                          uint32_t *rec = nullptr)
@@ -252,10 +263,10 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
     const uint32_t k = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
     const uint32_t own = j - beg;
     *k_out = k;
-    if (P.occ_lattice) return occ_ws_sum<REC>(P, inf, jo, day, stride, b, beg, size, own, k, rec);
+    if (P.occ_lattice) return occ_ws_sum<REC, RK>(P, inf, jo, day, stride, b, beg, size, own, k, rec);
     float h = 0.0f;
     for (uint32_t e = 0; e < k; e += 4u) {
-        const uint4 w = draw_rk(P.nrk, jo, day, kStreamOcc, e >> 2);
+        const uint4 w = net_draw<RK>(P, jo, day, kStreamOcc, e >> 2);
         const uint32_t x[4] = {w.x, w.y, w.z, w.w};
         float v[4];
 #pragma unroll
@@ -275,14 +286,14 @@ __device__ __forceinline__ float occ_sum(const KParams &P, const float *__restri
 // The number of the day's in-contacts of an agent whose lambda is not needed
 // (not susceptible): the random network's count (k_rand, from block 0) and the
 // occupation's daily count.  No gathers.
-template <bool WSG = false>
+template <bool WSG = false, bool RK = true>
 __device__ __forceinline__ uint32_t contact_count(const KParams &P, uint32_t j, uint32_t k_rand, uint32_t jo,
                                                   uint32_t day)
 {
     uint32_t k = k_rand;
     if (WSG && P.wsg_on) {
         uint32_t kw;
-        (void)wsg_sum<false>(P, nullptr, jo, day, &kw);
+        (void)wsg_sum<false, RK>(P, nullptr, jo, day, &kw);
         k += kw;
     }
     if (P.n_occ) {
@@ -315,7 +326,7 @@ __device__ __forceinline__ RowBounds row_bounds(const KParams &P, uint32_t j)
 // Callers load the row bounds and draw block 0 first, so that the bounds are in
 // flight while the Philox rounds run.  REC: the agent's exposure-notification
 // record of the day goes to rec (when not null).
-template <bool OCC = true, bool REC = false, bool ROWMAP = false, bool WSG = false>
+template <bool OCC = true, bool REC = false, bool ROWMAP = false, bool WSG = false, bool RK = true>
 __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, const RowBounds &rb,
                                            const RandBlock0 &r0, uint32_t *k_out, uint32_t *rec = nullptr)
@@ -331,8 +342,8 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
         head = rmap ? random_head<REC, true>(P, rinf, jo, r0, stride, b, rec, I.row_of)
                     : random_head<REC, false>(P, rinf, jo, r0, stride, b, rec, nullptr);
 #if !DEABM_RAND_DEFER
-        r_now = rmap ? random_tail<REC, true>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
-                     : random_tail<REC, false>(P, rinf, jo, day, stride, b, head, rec, nullptr);
+        r_now = rmap ? random_tail<REC, true, RK>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
+                     : random_tail<REC, false, RK>(P, rinf, jo, day, stride, b, head, rec, nullptr);
 #endif
     }
     const uint32_t k_rand = head.k;
@@ -349,21 +360,21 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
         }
     }
     if (OCC && P.n_occ) {
-        const float term = __fmul_rn(rp.B_net[P.n_nets], occ_sum<REC>(P, I.cur, j, jo, day, stride, b, &k_occ, rec));
+        const float term = __fmul_rn(rp.B_net[P.n_nets], occ_sum<REC, RK>(P, I.cur, j, jo, day, stride, b, &k_occ, rec));
         s = P.n_nets == 0 ? term : __fadd_rn(s, term);
         *k_out += k_occ;
     }
     if (REC && rec) rec[0] = k_rand | (k_occ << 8);
     if (WSG && P.wsg_on) {  // the Watts-Strogatz random network in the random network's place
         uint32_t kw;
-        const float term = __fmul_rn(rp.B_rand, wsg_sum<true>(P, I.rand_cur, jo, day, &kw));
+        const float term = __fmul_rn(rp.B_rand, wsg_sum<true, RK>(P, I.rand_cur, jo, day, &kw));
         s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
         *k_out += kw;
     }
     if (P.rand_on) {
 #if DEABM_RAND_DEFER
-        const float r = rmap ? random_tail<REC, true>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
-                             : random_tail<REC, false>(P, rinf, jo, day, stride, b, head, rec, nullptr);
+        const float r = rmap ? random_tail<REC, true, RK>(P, rinf, jo, day, stride, b, head, rec, I.row_of)
+                             : random_tail<REC, false, RK>(P, rinf, jo, day, stride, b, head, rec, nullptr);
 #else
         const float r = r_now;
 #endif
@@ -374,15 +385,15 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
 }
 
 // lambda_j with its own bounds and block 0 (see lambda_at).
-template <bool OCC = true, bool REC = false, bool ROWMAP = false, bool WSG = false>
+template <bool OCC = true, bool REC = false, bool ROWMAP = false, bool WSG = false, bool RK = true>
 __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, const InfBuffers &I, uint32_t j, uint32_t jo,
                                            uint32_t day, uint32_t stride, uint32_t b, int age, uint32_t *k_out,
                                            uint32_t *rec = nullptr)
 {
     const RowBounds rb = row_bounds(P, j);
     RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
-    if (P.rand_on) r0 = random_block0(P, jo, day);
-    return lambda_at<OCC, REC, ROWMAP, WSG>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
+    if (P.rand_on) r0 = random_block0<RK>(P, jo, day);
+    return lambda_at<OCC, REC, ROWMAP, WSG, RK>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
 }
 
 }  // namespace deabm

@@ -78,16 +78,16 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     RowBounds rb = {};
     if (full) rb = row_bounds(P, j);
     RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
-    if (P.rand_on) r0 = random_block0(P, jo, day);
+    if (P.rand_on) r0 = random_block0<RK>(P, jo, day);
     float lam = 0.0f;
     if (full) {
-        lam = lambda_at<OCC, DEN, ROWMAP, WSG>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
+        lam = lambda_at<OCC, DEN, ROWMAP, WSG, RK>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
         uint32_t deg = 0;
 #pragma unroll
         for (uint32_t net = 0; net < DEABM_MAX_NETS; ++net) deg += rb.end[net] - rb.beg[net];
         *kg_out = *k_out + deg;
     } else {
-        *k_out = contact_count<WSG>(P, j, r0.k, jo, day);
+        *k_out = contact_count<WSG, RK>(P, j, r0.k, jo, day);
         *kg_out = 0;
     }
     a.tm = S.timer[i];
@@ -362,8 +362,9 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             bool infected = false;
             uint32_t k = 0, kg = 0;
             if (active)
-                agent_day<false, false, true, false, true>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
-                                                           &infected, &k, &kg);
+                // the population's parameters are in shared memory: keys from the seeds (RK = false)
+                agent_day<false, false, true, false, false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
+                                                            &infected, &k, &kg);
             count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
         }
         __syncthreads();
