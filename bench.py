@@ -277,6 +277,7 @@ def run_ours(args, rank, world, local):
     ragged = run_ragged(args) if (rank == 0 and not args.no_ragged) else None
     occupation = run_occupation(args) if (rank == 0 and not args.no_occupation) else None
     den = run_den(args) if (rank == 0 and not args.no_den) else None
+    wsr = run_ws_random(args) if (rank == 0 and not args.no_ws) else None
 
     if rank == 0:
         value = messages / (total_ms / 1e3)
@@ -334,6 +335,8 @@ def run_ours(args, rank, world, local):
             line["daily_occupation"] = occupation
         if den:
             line["exposure_notification"] = den
+        if wsr:
+            line["ws_random_network"] = wsr
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -601,6 +604,39 @@ def run_occupation(args):
                                "value": msg_ws / (ms_ws / 1e3), "unit": "interactions/s", "ms_per_step": ms_ws / K,
                                "roofline": {"bound": "hbm", "achieved": alg / (ms_ws / K / 1e3) / 1e9, "peak": peak,
                                             "unit": "GB/s", "frac": alg / (ms_ws / K / 1e3) / 1e9 / peak}}}
+
+
+def run_ws_random(args):
+    """The N=2e6 plain workload with its global random network as a daily
+    Watts-Strogatz graph (ring lattice over all agents, k = 2, rewiring 0.5, R24):
+    the day's graph built on the device, then the day kernel."""
+    import torch
+    from paper_2110_04421_gb300 import workloads as W
+    from paper_2110_04421_gb300.deabm import Simulation
+
+    w = W.plain_large()
+    n = w["n"]
+    K = max(3, min(args.occupation_steps, args.steps))
+    pop = dict(W.population(n, 0, w["n_seed"]), rand_ws=1, rand_ws_k=2, rand_ws_beta=0.5)
+    stream = torch.cuda.Stream()
+    sim = Simulation(pop, w["params"], pop["age"], pop["seed_ids"], max_steps=args.warmup + K, stream=stream.cuda_stream)
+    sim.step(args.warmup)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, _, msgs = sim.counters()
+    sim.close()
+    msg = int(msgs[args.warmup:args.warmup + K].astype(np.int64).sum())
+    cpu = None if args.no_cpu_baseline else cpu_baseline(pop, w["params"], args.cpu_seconds / 4)
+    return {"workload": "plain N=2e6 with the random network as a daily Watts-Strogatz graph (k = 2, beta = 0.5)",
+            "value": msg / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / K, "steps": K,
+            "days_timed": f"{args.warmup}..{args.warmup + K - 1}", "messages_per_day": msg / K,
+            "launches_per_day": "day kernel + the graph's build (3 kernels, a prefix sum, 3 memsets)",
+            "cpu_baseline": cpu}
 
 
 def run_den(args):
@@ -919,9 +955,10 @@ def main():
     ap.add_argument("--occupation-steps", type=int, default=20)
     ap.add_argument("--no-den", action="store_true")
     ap.add_argument("--den-steps", type=int, default=20)
+    ap.add_argument("--no-ws", action="store_true", help="skip the Watts-Strogatz random-network leg")
     ap.add_argument("--calib-steps", type=int, default=200)
     ap.add_argument("--only", default="all",
-                    choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged", "occupation", "den"],
+                    choices=["all", "plain", "batched", "relaxed", "surrogate", "ragged", "occupation", "den", "ws"],
                     help="profiling runs: time one workload only")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -934,13 +971,13 @@ def main():
         torch.cuda.set_device(local)
         print(json.dumps(run_batched(args)))
         return
-    if args.only in ("relaxed", "surrogate", "ragged", "occupation", "den"):
+    if args.only in ("relaxed", "surrogate", "ragged", "occupation", "den", "ws"):
         import __graft_entry__
         __graft_entry__.build()
         import torch
         torch.cuda.set_device(local)
         fn = {"relaxed": run_relaxed, "surrogate": run_surrogate, "ragged": run_ragged,
-              "occupation": run_occupation, "den": run_den}[args.only]
+              "occupation": run_occupation, "den": run_den, "ws": run_ws_random}[args.only]
         print(json.dumps(fn(args)))
         return
     if args.only == "plain":
@@ -950,6 +987,7 @@ def main():
         args.no_ragged = True
         args.no_occupation = True
         args.no_den = True
+        args.no_ws = True
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

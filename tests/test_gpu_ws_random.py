@@ -60,3 +60,15 @@ def test_watts_strogatz_rejected_where_not_built():
     rp, seeds = W.batch_params(8, 0)
     with pytest.raises(DeabmError, match="plain contexts"):
         gpu_sim(pop, W.params_with(), n_rep=8, rep_params=rp, rep_seeds=seeds)
+
+
+def test_watts_strogatz_full_size_first_days():
+    """The bench's N = 2,000,000 workload (testing, quarantine, vaccination) with
+    the random network as a daily Watts-Strogatz graph (k = 2, beta = 0.5), the
+    first 4 days against the oracle in full: lambda bit for bit, every state array
+    and counter."""
+    w = W.plain_large()
+    pop = dict(W.population(w["n"], 0, w["n_seed"]), rand_ws=1, rand_ws_k=2, rand_ws_beta=0.5)
+    rep = compare_days(pop, w["params"], 4)
+    assert rep["flips"] == 0 and rep["days"] == 4, rep
+    assert rep["max_rel_lambda64"] <= 1e-5
