@@ -401,8 +401,10 @@ def run_relaxed(args):
                             "products_found": [float(theta[0] * theta[k]) for k in (1, 2, 3)],
                             "note": "lambda depends on R, the network weights B_n and the age "
                                     "susceptibilities only through the products R S_a B_n (Eq. 1), so the "
-                                    "loss is flat along R -> c R, B_n -> B_n / c: R and the weights cannot "
-                                    "be recovered separately, only those products (R B_n with S_a = 1)"},
+                                    "loss is flat along R -> c R, B_n -> B_n / c; the networks' shares of the "
+                                    "daily incidence also trade off against each other, so one incidence "
+                                    "curve identifies neither R and the weights nor the products R B_n: "
+                                    "the fit matches the curve, not the hidden parameters"},
             "batched_gradient": {"columns": Bc, "ms": batch_ms, "ms_first_call": first_ms,
                                  "ms_per_column": batch_ms / Bc,
                                  "multiple_of_single_gradients": ms_grad * Bc / batch_ms,
@@ -480,6 +482,10 @@ def run_surrogate(args):
             pth = os.path.join(d, "params.npy")
             np.save(pth, params_now.astype(np.float64))
             cpu = cpu_baseline_mlp(sizes, pth, 16384)
+    acc = None
+    if args.surrogate_runs > 0:  # accuracy against the simulator: train on simulated runs, score held-out ones
+        from paper_2110_04421_gb300 import surrogate as S
+        acc = S.fit_and_score(runs=args.surrogate_runs, steps=args.surrogate_train_steps)
     f = mlp_flops_per_sample(sizes)
     peak, kind = measured_peak_bf16()
     fwd_tf = f * B / (fwd_ms / 1e3) / 1e12
@@ -490,6 +496,7 @@ def run_surrogate(args):
                                "bias gradients, Adam; 3 x forward FLOPs counted",
             "samples_per_s": B / (fwd_ms / 1e3), "flops_per_sample_forward": f,
             "cpu_baseline": cpu,
+            "accuracy": acc,
             "l2": "flushed before every timed call (write of twice its size)",
             "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": fwd_tf / peak,
                          "peak_kind": kind,
@@ -635,7 +642,7 @@ def run_ws_random(args):
     return {"workload": "plain N=2e6 with the random network as a daily Watts-Strogatz graph (k = 2, beta = 0.5)",
             "value": msg / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / K, "steps": K,
             "days_timed": f"{args.warmup}..{args.warmup + K - 1}", "messages_per_day": msg / K,
-            "launches_per_day": "day kernel + the graph's build (3 kernels, a prefix sum, 3 memsets)",
+            "launches_per_day": "day kernel + the graph's build (3 kernels, a prefix sum, 1 memset)",
             "cpu_baseline": cpu}
 
 
@@ -950,6 +957,9 @@ def main():
     ap.add_argument("--no-loop", action="store_true", help="skip the plain per-replicate loop of the batched leg")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-runs", type=int, default=20_000,
+                    help="simulated runs for the surrogate's accuracy (79/20/1 %% split); 0 skips it")
+    ap.add_argument("--surrogate-train-steps", type=int, default=3000)
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-occupation", action="store_true")
     ap.add_argument("--occupation-steps", type=int, default=20)

@@ -801,14 +801,12 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 WsgBuffers &W = ctx->wsg;
                 const size_t edges = (size_t)n * K.wsg_h;
                 if ((r = dalloc(ctx, &W.rew, n))) return r;
-                if ((r = dalloc(ctx, &W.cnt1, (size_t)n + 1))) return r;
-                if ((r = dalloc(ctx, &W.fill, n))) return r;
-                if ((r = dalloc(ctx, &W.list, 2 * edges))) return r;
-                if ((r = dalloc(ctx, &W.list_n, 1))) return r;
+                if ((r = dalloc(ctx, &W.far, edges))) return r;
+                if ((r = dalloc(ctx, &W.ends, (size_t)n + 3))) return r;
                 if ((r = dalloc(ctx, &W.land, edges))) return r;
                 if ((r = dalloc(ctx, &W.scratch, wsg_scratch_words(n)))) return r;
                 K.wsg_rew = W.rew;
-                K.wsg_start = W.cnt1;
+                K.wsg_start = W.ends + 2;
                 K.wsg_land = W.land;
             }
             for (uint32_t k = 0; k < DEABM_MAX_NETS; ++k) {

@@ -50,11 +50,12 @@ cudaError_t launch_csr_renumber(const uint32_t *rp, const uint32_t *col, const u
                                 uint32_t *scratch, cudaStream_t stream);
 size_t scan_scratch_words(size_t m);
 // the day's Watts-Strogatz random network (wsg.cu): device buffers over n agents
-// with h owned edges each -- rew [n], cnt1 [n+1] (landing slots after the build),
-// fill [n], list [2 n h], list_n [1], land [n h], scratch [wsg_scratch_words(n)]
+// with h owned edges each -- rew [n], far [n h], ends [n+3] (agent v's landing
+// slots are land[ends[v+2] .. ends[v+3]) after the build), land [n h],
+// scratch [wsg_scratch_words(n)]
 struct WsgBuffers {
     uint8_t *rew;
-    uint32_t *cnt1, *fill, *list, *list_n, *land, *scratch;
+    uint32_t *far, *ends, *land, *scratch;
 };
 size_t wsg_scratch_words(uint32_t n);
 cudaError_t launch_wsg_build(const KParams &P, uint32_t day, const WsgBuffers &B, cudaStream_t stream);
