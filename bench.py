@@ -250,15 +250,17 @@ def run_ours(args, rank, world, local):
     sus_days = [float(hist_days[d - 1, 0, 0]) for d in range(Wm, Wm + K)]
     sim.close()
 
-    # ---- end to end through the C-ABI with host buffers (create + run + readback)
+    # ---- end to end through the C-ABI with host buffers (create + run + readback),
+    # days 0 .. Wm+K-1: the device-timed days and the warm-up days before them
     e2e_s, e2e_messages, h2d, d2h = float("nan"), 0, 0, 0
+    KE = Wm + K
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim2 = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=K, stream=stream.cuda_stream)
-        ni, hist = sim2.run(K)
+        sim2 = Simulation(pop, params, pop["age"], pop["seed_ids"], max_steps=KE, stream=stream.cuda_stream)
+        ni, hist = sim2.run(KE)
         st = sim2.state()
-        _, _, msgs2 = sim2.counters(K)
+        _, _, msgs2 = sim2.counters(KE)
         sim2.close()
         e2e_s = time.perf_counter() - t0
         e2e_messages = int(msgs2.astype(np.int64).sum())
@@ -313,8 +315,11 @@ def run_ours(args, rank, world, local):
                                      "and frac_needed divide those bytes by the same time",
                          "launch_ms_mean": avg_ms},
             "e2e": None if args.no_e2e else {
-                "value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / K,
-                "d2h_bytes_per_step": d2h / K, "seconds": e2e_s},
+                "value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / KE,
+                "d2h_bytes_per_step": d2h / KE, "seconds": e2e_s, "days": f"0..{KE - 1}",
+                "note": "one call sequence from host buffers: create (graph, agents and parameters up), "
+                        "the days, state and counters back; the days are the timed days and the warm-up days "
+                        "before them"},
             "gathered": {"value": gathered / (total_ms / 1e3), "unit": "messages gathered/s",
                          "share": gathered / max(messages, 1),
                          "note": "in-contacts of the destinations that evaluated Eq. 1 (the agents susceptible at "
@@ -558,7 +563,9 @@ def run_ragged(args):
             "value": messages / (ms / 1e3), "unit": "interactions/s", "ms_per_step": ms / T,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "kernel": "step_ragged_kernel", "alg_bytes_per_launch": alg,
-                         "traffic": None},
+                         "traffic": traffic_from_profile(DAY_KERNEL_SOURCES, "step_ragged_64pops.md",
+                                                         int(sum(p["n"] for p in w["pops"])),
+                                                         (args.warmup, args.warmup + T - 1))},
             "autotuned": {"rows_per_tile": rows, "blocks_per_sm": bps},
             "loop_of_plain_launches_ms_per_step": ms_loop / T, "multiple_of_plain_loop": ms_loop / ms}
 

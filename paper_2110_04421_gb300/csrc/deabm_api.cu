@@ -50,7 +50,8 @@ struct deabm_ctx {
     // exposure notification: today's positive app holders (internal rows, caller ids), per-day counts
     uint32_t *den_bits = nullptr, *den_bits_orig = nullptr;
     int32_t *den_pos = nullptr;
-    uint32_t *den_ring = nullptr;  // [den_window][n_app][slots] contact records of the app holders
+    uint32_t *den_ring = nullptr;  // [den_window][slots][n_app] contact records of the app holders
+    size_t den_ring_cap = 0;       // app holders the ring has room for
     uint32_t *app_rows = nullptr, *app_rank = nullptr;
     float *lam = nullptr, *p = nullptr;
     Tables *tab = nullptr;
@@ -493,6 +494,39 @@ static void build_reps(const deabm_params *p, uint32_t n_rep, const float *rep_p
 }
 
 // ---------------------------------------------------------------- exposure notification
+// The contact ring (den_window days x den_slots words per app holder) is sized
+// to the app holders drawn: at creation, and again at a reset whose seed draws
+// more of them than it has room for.
+static int den_ring_reserve(deabm_ctx *ctx, KParams &K)
+{
+    if (ctx->den_ring && K.n_app <= ctx->den_ring_cap) {
+        K.den_ring = ctx->den_ring;
+        return DEABM_OK;
+    }
+    if (ctx->den_ring) {  // too small for this draw: replaced (nothing in flight reads it)
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), (void *)ctx->den_ring);
+        if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+        (void)cudaFree(ctx->den_ring);
+        ctx->den_ring = nullptr;
+        ctx->den_ring_cap = 0;
+        K.den_ring = nullptr;
+    }
+    const size_t cap = K.n_app;
+    const size_t bytes = std::max<size_t>(1, (size_t)K.den_window * K.den_slots * cap) * sizeof(uint32_t);
+    void *ptr = nullptr;
+    cudaError_t e = injected_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, DEABM_ENOMEM, "cudaMalloc of %zu bytes (contact ring) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(ptr);
+    ctx->den_ring = (uint32_t *)ptr;
+    ctx->den_ring_cap = cap;
+    K.den_ring = ctx->den_ring;
+    return DEABM_OK;
+}
+
 // The app holders drawn on the device, listed in row order with each row's rank
 // (for the notification pass and the contact ring); sets K.n_app.
 static int den_list_apps(deabm_ctx *ctx, KParams &K)
@@ -509,6 +543,7 @@ static int den_list_apps(deabm_ctx *ctx, KParams &K)
             rows.push_back(j);
         }
     K.n_app = (uint32_t)rows.size();
+    if (int r = den_ring_reserve(ctx, K)) return r;
     if (K.n_app)
         CU(ctx, cudaMemcpyAsync(ctx->app_rows, rows.data(), sizeof(uint32_t) * K.n_app, cudaMemcpyHostToDevice,
                                 ctx->stream));
@@ -662,8 +697,6 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 if (ctx->relabel && (r = dalloc(ctx, &ctx->den_bits_orig, ((size_t)n + 31) / 32))) return r;
                 if ((r = dalloc(ctx, &ctx->den_pos, days))) return r;
                 CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * days, s));
-                const size_t slots = g->n_occ ? 32 : 16;
-                if ((r = dalloc(ctx, &ctx->den_ring, (size_t)p->den_window * n * slots))) return r;
                 if ((r = dalloc(ctx, &ctx->app_rows, n))) return r;
                 if ((r = dalloc(ctx, &ctx->app_rank, n))) return r;
             }
@@ -849,7 +882,6 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.den_bits = ctx->den_bits;
             K.den_bits_orig = ctx->den_bits_orig;
             K.den_pos = ctx->den_pos;
-            K.den_ring = ctx->den_ring;
             K.den_slots = g->n_occ ? 32u : 16u;
             K.app_rows = ctx->app_rows;
             K.app_rank = ctx->app_rank;

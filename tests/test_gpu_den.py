@@ -83,6 +83,39 @@ def test_reset_redraws_app_holders():
     assert den.tolist() == o.den_notified
 
 
+def test_contact_ring_grows_when_a_reset_draws_more_app_holders():
+    """The contact ring is sized to the app holders drawn; resets whose seeds draw
+    more of them (seeds picked by the oracle's draw, each larger than the last)
+    must regrow it, and every run still matches the oracle."""
+    pop = W.population(4_000, 8, 20)
+    p = den_params(den_adoption=0.25)
+
+    def n_app(seed):
+        return int((oracle_sim(pop, dict(p, seed=seed)).state.flags & 0x20).astype(bool).sum())
+
+    seeds, best = [], n_app(p["seed"])
+    for cand in range(100, 160):
+        c = n_app(cand)
+        if c > best:
+            seeds.append(cand)
+            best = c
+        if len(seeds) == 2:
+            break
+    assert len(seeds) == 2
+    g = gpu_sim(pop, p, keep_lambda=False, max_steps=30)
+    g.run(30)
+    rp = np.array([[p["R"], 2.0, 1.0, 1.0, *p["S_age"], p["dose2_delay"]]], np.float32)
+    for sd in seeds:
+        g.reset(rp, np.array([sd], np.uint64))
+        g.run(30)
+        s, den = g.state(), g.notified()
+        o = oracle_sim(pop, dict(p, seed=sd))
+        o.run(30)
+        assert np.array_equal(s["flags"], o.state.flags) and np.array_equal(s["stage"], o.state.stage)
+        assert den.tolist() == o.den_notified and sum(den) > 0
+    g.close()
+
+
 def test_other_contexts_reject_notification():
     from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation, Relaxed, Simulation
     pop = W.population(500, 1, 5)
