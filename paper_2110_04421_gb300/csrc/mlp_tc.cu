@@ -15,7 +15,10 @@
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w: TMEM lanes
 //     32 (w % 4) .. +31, half w / 4 of the columns), adds the bias, applies the
 //     erf-GELU and writes the BF16 activations back to shared memory as the next
-//     layer's input, or the FP32 output to global memory after the last layer.
+//     layer's input; after the last layer each warp turns its 32 rows x 32
+//     columns around in shared memory so that every global store of the FP32
+//     output writes one row's 128 consecutive bytes (a thread per row storing
+//     its own columns would touch 32 rows, 32 cache lines, per instruction).
 // Every mbarrier wait is bounded: on time-out the kernel records an error,
 // frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -226,11 +229,30 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_forward_tc_kernel(const Fused
                                           pack_bf16x2(v[q * 8 + 4], v[q * 8 + 5]), pack_bf16x2(v[q * 8 + 6], v[q * 8 + 7]));
                     *(uint4 *)(sA + (n >> 6) * kAChunkBytes + sw128(row, (n & 63u) >> 3)) = pk;
                 }
-            } else if (row0 + row < (uint32_t)g.M) {
-                float *yrow = g.y + (size_t)(row0 + row) * g.n_out;
+            } else {
+                // output layer: the warp's 32 rows x 32 columns go through shared memory
+                // (the layer input is no longer read: the MMAs have completed) so that
+                // each global store writes one row's 32 consecutive columns
+                float *stg = (float *)sA + warp * 1024u;  // [32 rows][32], float4 q of row r at q ^ (r % 8)
 #pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    if (n0 + e < (uint32_t)g.n_out) yrow[n0 + e] = v[e] + __ldg(g.bias[l] + n0 + e);
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t n = n0 + 4u * q;
+                    float4 o;
+                    o.x = v[4 * q] + (n < (uint32_t)g.n_out ? __ldg(g.bias[l] + n) : 0.0f);
+                    o.y = v[4 * q + 1] + (n + 1u < (uint32_t)g.n_out ? __ldg(g.bias[l] + n + 1u) : 0.0f);
+                    o.z = v[4 * q + 2] + (n + 2u < (uint32_t)g.n_out ? __ldg(g.bias[l] + n + 2u) : 0.0f);
+                    o.w = v[4 * q + 3] + (n + 3u < (uint32_t)g.n_out ? __ldg(g.bias[l] + n + 3u) : 0.0f);
+                    *(float4 *)(stg + lane * 32u + (((uint32_t)q ^ (lane & 7u)) << 2)) = o;
+                }
+                __syncwarp();
+                const uint32_t col = n0 + lane;
+#pragma unroll 4
+                for (uint32_t r = 0; r < 32u; ++r) {
+                    const uint32_t grow = row0 + quad * 32u + r;
+                    const float val = stg[r * 32u + ((((lane >> 2) ^ r) & 7u) << 2) + (lane & 3u)];
+                    if (grow < (uint32_t)g.M && col < (uint32_t)g.n_out) g.y[(size_t)grow * g.n_out + col] = val;
+                }
+                __syncwarp();
             }
         }
         tc_fence_before();
