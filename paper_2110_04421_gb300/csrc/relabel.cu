@@ -113,9 +113,96 @@ __global__ void add_block_offsets_kernel(uint32_t *a, size_t m, const uint32_t *
     if (blockIdx.x > 0 && i < m) a[i] += sums[blockIdx.x - 1];
 }
 
+// Two-launch scan for up to kTileScanMaxTiles tiles of 4096 words: the tiles'
+// totals, then each tile scanned with the sum of the totals before it as its
+// offset (every block adds up that prefix itself; at most 4096 words).  Tiles
+// move through shared memory so that global loads and stores stay coalesced
+// while each thread scans 16 consecutive words.
+constexpr uint32_t kTileThreads = 256, kTilePer = 16, kTileWords = kTileThreads * kTilePer;
+constexpr size_t kTileScanMaxTiles = 4096;
+
+__device__ __forceinline__ uint32_t block_sum_256(uint32_t x, uint32_t *red)
+{
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    x = __reduce_add_sync(0xFFFFFFFFu, x);
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < kTileThreads / 32u; ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kTileThreads) tile_sum_kernel(const uint32_t *a, size_t m, uint32_t *sums)
+{
+    __shared__ uint32_t red[kTileThreads / 32u];
+    const size_t base = (size_t)blockIdx.x * kTileWords;
+    uint32_t x = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < kTilePer; ++i) {
+        const size_t q = base + i * kTileThreads + threadIdx.x;
+        if (q < m) x += a[q];
+    }
+    const uint32_t t = block_sum_256(x, red);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+__device__ __forceinline__ uint32_t tile_slot(uint32_t p) { return p + (p >> 5); }  // one pad word per 32
+
+__global__ void __launch_bounds__(kTileThreads) tile_scan_kernel(uint32_t *a, size_t m, const uint32_t *sums)
+{
+    __shared__ uint32_t red[kTileThreads / 32u];
+    __shared__ uint32_t tile[kTileWords + kTileWords / 32u];
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+    const size_t base = (size_t)blockIdx.x * kTileWords;
+    uint32_t pre = 0;  // this tile's offset: the totals of the tiles before it
+    for (uint32_t b = tid; b < blockIdx.x; b += kTileThreads) pre += sums[b];
+    const uint32_t off = block_sum_256(pre, red);
+#pragma unroll
+    for (uint32_t i = 0; i < kTilePer; ++i) {
+        const uint32_t p = i * kTileThreads + tid;
+        tile[tile_slot(p)] = base + p < m ? a[base + p] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kTilePer], run = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < kTilePer; ++i) {
+        run += tile[tile_slot(tid * kTilePer + i)];
+        v[i] = run;
+    }
+    // exclusive scan of the threads' runs
+    uint32_t x = run;
+#pragma unroll
+    for (uint32_t d = 1; d < 32u; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
+    }
+    __syncthreads();  // red is reused
+    if (lane == 31u) red[wid] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (uint32_t w = 0; w < wid; ++w) wpre += red[w];
+    const uint32_t excl = off + wpre + x - run;
+#pragma unroll
+    for (uint32_t i = 0; i < kTilePer; ++i) tile[tile_slot(tid * kTilePer + i)] = v[i] + excl;
+    __syncthreads();
+#pragma unroll
+    for (uint32_t i = 0; i < kTilePer; ++i) {
+        const uint32_t p = i * kTileThreads + tid;
+        if (base + p < m) a[base + p] = tile[tile_slot(p)];
+    }
+}
+
 // scratch: 2 * ceil(m / 1024) + 2 words (recursive block sums)
 static cudaError_t scan_inplace(uint32_t *a, size_t m, uint32_t *scratch, cudaStream_t stream)
 {
+    if (m == 0) return cudaSuccess;
+    const size_t nt = (m + kTileWords - 1) / kTileWords;
+    if (nt >= 1 && nt <= kTileScanMaxTiles) {
+        tile_sum_kernel<<<(unsigned)nt, kTileThreads, 0, stream>>>(a, m, scratch);
+        tile_scan_kernel<<<(unsigned)nt, kTileThreads, 0, stream>>>(a, m, scratch);
+        return cudaGetLastError();
+    }
     const size_t nb = (m + kScanBlock - 1) / kScanBlock;
     scan_blocks_kernel<<<(unsigned)nb, kScanBlock, 0, stream>>>(a, m, scratch);
     if (nb > 1) {

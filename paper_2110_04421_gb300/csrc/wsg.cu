@@ -20,7 +20,8 @@
 //      afterwards agent v's landings are land[ends[v + 2] .. ends[v + 3]);
 //   4. order: each agent's landing owners are sorted ascending (a few per agent),
 //      so the day kernel sums them in a fixed order and the result does not
-//      depend on the order the atomics ran in.
+//      depend on the order the atomics ran in (the prefix sum is the two-launch
+//      tiled scan of relabel.cu).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -56,7 +57,9 @@ __global__ void wsg_mark_kernel(const KParams P, uint32_t day, uint8_t *rew, uin
     rew[i] = (uint8_t)bits;
 }
 
-// key owner h + (m - 1) per rewired edge: ascending key order is ascending (owner, m)
+// each rewired edge's owner into a slot of its far end.  Only owners are kept:
+// two edges of one owner that land on the same agent carry the same message, so
+// the order between them does not change the sum.
 __global__ void wsg_fill_kernel(uint32_t n, uint32_t h, const uint8_t *rew, const uint32_t *far, uint32_t *ends,
                                 uint32_t *land)
 {
@@ -66,18 +69,38 @@ __global__ void wsg_fill_kernel(uint32_t n, uint32_t h, const uint8_t *rew, cons
     while (bits) {
         const uint32_t e = (uint32_t)__ffs(bits) - 1u;
         bits &= bits - 1u;
-        const uint32_t key = i * h + e;
-        land[atomicSub(ends + far[key] + 2u, 1u) - 1u] = key;
+        land[atomicSub(ends + far[i * h + e] + 2u, 1u) - 1u] = i;
     }
 }
 
-// each agent's landing edges in ascending key order, then as owners
-__global__ void wsg_order_kernel(uint32_t n, uint32_t h, const uint32_t *start, uint32_t *land)
+// each agent's landing owners in ascending order: up to kSortCap of them loaded
+// at once and sorted in registers (odd-even transposition network), more than
+// that by insertion in place (rare: the counts are about Poisson(h beta))
+constexpr uint32_t kSortCap = 8;
+__global__ void wsg_order_kernel(uint32_t n, const uint32_t *start, uint32_t *land)
 {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    const uint32_t s0 = start[v], s1 = start[v + 1u];
-    for (uint32_t a = s0 + 1u; a < s1; ++a) {
+    const uint32_t s0 = start[v], c = start[v + 1u] - s0;
+    if (c < 2u) return;
+    if (c <= kSortCap) {
+        uint32_t k[kSortCap];
+#pragma unroll
+        for (uint32_t u = 0; u < kSortCap; ++u) k[u] = u < c ? land[s0 + u] : 0xFFFFFFFFu;
+#pragma unroll
+        for (uint32_t r = 0; r < kSortCap; ++r)
+#pragma unroll
+            for (uint32_t u = r & 1u; u + 1u < kSortCap; u += 2u) {
+                const uint32_t lo = min(k[u], k[u + 1u]), hi = max(k[u], k[u + 1u]);
+                k[u] = lo;
+                k[u + 1u] = hi;
+            }
+#pragma unroll
+        for (uint32_t u = 0; u < kSortCap; ++u)
+            if (u < c) land[s0 + u] = k[u];
+        return;
+    }
+    for (uint32_t a = s0 + 1u; a < s0 + c; ++a) {
         const uint32_t key = land[a];
         uint32_t b = a;
         while (b > s0 && land[b - 1u] > key) {
@@ -86,7 +109,6 @@ __global__ void wsg_order_kernel(uint32_t n, uint32_t h, const uint32_t *start, 
         }
         land[b] = key;
     }
-    for (uint32_t a = s0; a < s1; ++a) land[a] /= h;
 }
 
 size_t wsg_scratch_words(uint32_t n) { return scan_scratch_words((size_t)n + 3u); }
@@ -102,7 +124,7 @@ cudaError_t launch_wsg_build(const KParams &P, uint32_t day, const WsgBuffers &B
     if ((e = launch_scan_inclusive(B.ends, (size_t)n + 3u, B.scratch, s)) != cudaSuccess) return e;
     wsg_fill_kernel<<<blocks, 256, 0, s>>>(n, h, B.rew, B.far, B.ends, B.land);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    wsg_order_kernel<<<blocks, 256, 0, s>>>(n, h, B.ends + 2, B.land);
+    wsg_order_kernel<<<blocks, 256, 0, s>>>(n, B.ends + 2, B.land);
     return cudaGetLastError();
 }
 
