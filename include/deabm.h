@@ -480,7 +480,8 @@ void deabm_relaxed_destroy(deabm_relaxed *ctx);
 /* ------------------------------------------------------------------------------------------
  * Learned surrogate: an MLP from the 14 simulation parameters to the daily
  * log incidence (not in the paper, which only hopes to bring agent-based models
- * and learning closer, Sec. 6).  n_in -> hidden x depth (erf-GELU) -> n_out,
+ * and learning closer, Sec. 6).  n_in -> hidden x depth (GELU, tanh form:
+ * z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))) -> n_out,
  * BF16 operands with FP32 accumulation on the tensor cores, FP32 master weights.
  * Parameter layout (FP32, host): for each layer l, W_l [fan_in x fan_out]
  * row-major, then b_l [fan_out].  Data pointers x / y are DEVICE FP32 arrays

@@ -6,10 +6,14 @@ BF16: the inputs, the weights, every hidden activation a_l = gelu(z_l), and the
 output-side gradients dz_l before they enter the weight- and input-gradient
 products.  Pre-activations, the output, the loss, the bias gradients and the
 accumulation of every product stay in high precision.
-    z_l = a_{l-1} W_l + b_l,  a_l = gelu(z_l) = z Phi(z)   (hidden layers)
+    z_l = a_{l-1} W_l + b_l,  a_l = gelu(z_l)   (hidden layers)
     y_hat = z_L,  loss = mean((y_hat - y)^2)
     dz_L = 2 (y_hat - y) / numel,  dW_l = a_{l-1}^T dz_l,  db_l = sum_rows dz_l
-    dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1}),  gelu'(z) = Phi(z) + z phi(z)
+    dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})
+The activation is GELU in its tanh form (Hendrycks and Gimpel, 2016, Sec. 2):
+    gelu(z) = z/2 (1 + tanh(u)),  u = sqrt(2/pi) (z + 0.044715 z^3)
+    gelu'(z) = (1 + tanh(u))/2 + z/2 (1 - tanh(u)^2) sqrt(2/pi) (1 + 3 * 0.044715 z^2)
+(the surrogate is not in the paper; its activation is this design's choice).
 """
 from __future__ import annotations
 
@@ -17,10 +21,8 @@ import math
 
 import numpy as np
 
-try:
-    from scipy.special import erf as _erf
-except ImportError:  # pragma: no cover
-    _erf = np.vectorize(math.erf)
+_C1 = math.sqrt(2.0 / math.pi)
+_A = 0.044715
 
 
 def bf16(x) -> np.ndarray:
@@ -32,11 +34,12 @@ def bf16(x) -> np.ndarray:
 
 
 def gelu(z):
-    return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(_C1 * (z + _A * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    t = np.tanh(_C1 * (z + _A * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * _C1 * (1.0 + 3.0 * _A * z * z)
 
 
 def unpack(params: np.ndarray, sizes):

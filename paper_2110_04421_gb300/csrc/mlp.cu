@@ -1,7 +1,8 @@
 // mlp.cu -- surrogate MLP (simulation parameters -> daily log incidence) trained
 // and evaluated on the GPU: BF16 operands, FP32 accumulation on the tensor cores.
 //
-// Layers: n_in -> H -> ... -> H (depth hidden layers, erf-GELU) -> n_out (linear).
+// Layers: n_in -> H -> ... -> H (depth hidden layers, GELU in its tanh form,
+// gelu.cuh) -> n_out (linear).
 // Forward of layer l:  z_l = a_{l-1} W_l + b_l  (FP32 accumulate of BF16 products),
 // a_l = bf16(gelu(z_l)) for hidden layers, the output z_L in FP32.
 // Backward (MSE loss (1/(B n_out)) sum (y_hat - y)^2):
@@ -21,6 +22,7 @@
 #include <vector>
 
 #include "deabm.h"
+#include "gelu.cuh"
 #include "mlp_tc.h"
 
 namespace mlpk {
@@ -50,12 +52,6 @@ struct GemmArgs {
     int epi;
 };
 
-__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_erf_grad(float z)
-{
-    // d/dz [z Phi(z)] = Phi(z) + z phi(z)
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
-}
 
 __device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p)
 {
@@ -158,11 +154,11 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g)
                     if (g.epi == EPI_HIDDEN) {
                         const float z = v + g.bias[j];
                         if (g.outf) g.outf[o] = z;
-                        g.outb[o] = __float2bfloat16(gelu_erf(z));
+                        g.outb[o] = __float2bfloat16(gelu_act(z));
                     } else if (g.epi == EPI_OUTPUT) {
                         g.outf[o] = v + g.bias[j];
                     } else if (g.epi == EPI_DGRAD) {
-                        const float d = v * gelu_erf_grad(g.zin[o]);
+                        const float d = v * gelu_act_grad(g.zin[o]);
                         g.outf[o] = d;
                         g.outb[o] = __float2bfloat16(d);
                     } else {

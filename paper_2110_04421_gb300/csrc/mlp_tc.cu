@@ -14,7 +14,7 @@
 //     overlaps the other's MMAs;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w: TMEM lanes
 //     32 (w % 4) .. +31, half w / 4 of the columns), adds the bias, applies the
-//     erf-GELU and writes the BF16 activations back to shared memory as the next
+//     GELU (tanh form) and writes the BF16 activations back to shared memory as the next
 //     layer's input; after the last layer each warp turns its 32 rows x 32
 //     columns around in shared memory so that every global store of the FP32
 //     output writes one row's 128 consecutive bytes (a thread per row storing
@@ -26,6 +26,7 @@
 
 #include <cstdint>
 
+#include "gelu.cuh"
 #include "mlp_tc.h"
 
 namespace mlptc {
@@ -115,7 +116,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
@@ -217,10 +217,10 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_forward_tc_kernel(const Fused
 #pragma unroll
                 for (int e = 0; e < 32; e += 4) {  // the bias four columns at a time (16-byte loads)
                     const float4 bb = __ldg((const float4 *)(g.bias[l] + n0 + e));
-                    v[e] = gelu_erf(v[e] + bb.x);
-                    v[e + 1] = gelu_erf(v[e + 1] + bb.y);
-                    v[e + 2] = gelu_erf(v[e + 2] + bb.z);
-                    v[e + 3] = gelu_erf(v[e + 3] + bb.w);
+                    v[e] = gelu_act(v[e] + bb.x);
+                    v[e + 1] = gelu_act(v[e + 1] + bb.y);
+                    v[e + 2] = gelu_act(v[e + 2] + bb.z);
+                    v[e + 3] = gelu_act(v[e + 3] + bb.w);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {

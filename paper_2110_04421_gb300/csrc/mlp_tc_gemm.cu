@@ -14,7 +14,7 @@
 //     last chunk, to the accumulator's mbarrier;
 //   * warps 2-5: the epilogue, each reading its 32 TMEM lanes (rows) with
 //     tcgen05.ld, 32 columns at a time, and writing what the MLP needs (bias,
-//     erf-GELU or its derivative, FP32 / BF16 / transposed BF16 stores).
+//     GELU (tanh form) or its derivative, FP32 / BF16 / transposed BF16 stores).
 // Two CTAs share an SM (97 KB of shared memory and 256 TMEM columns each), so one
 // CTA's epilogue overlaps the other's copies and MMAs.  Operand tiles are read
 // only from this GPU's global memory (no cluster multicast).
@@ -28,6 +28,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "gelu.cuh"
 #include "mlp_tc.h"
 #include "tc_ptx.cuh"
 
@@ -44,12 +45,6 @@ constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kDrainPolls = 1u << 26;  // bound of the waits for work already started
 constexpr size_t kSmemBytes = kStages * (kATile + kBTileMax) + 1024;
 
-__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_erf_grad(float z)
-{
-    // d/dz [z Phi(z)] = Phi(z) + z phi(z)
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
-}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
@@ -227,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                 }
                 if (g.epi == TC_EPI_DGRAD) {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) v[e] = v[e] * gelu_erf_grad(other[e]);
+                    for (int e = 0; e < 32; ++e) v[e] = v[e] * gelu_act_grad(other[e]);
                 } else if (g.epi == TC_EPI_MSE) {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
@@ -259,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                 }
                 if (g.epi == TC_EPI_HIDDEN) {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) v[e] = gelu_erf(v[e]);
+                    for (int e = 0; e < 32; ++e) v[e] = gelu_act(v[e]);
                 }
                 // the BF16 copies: row-major, then transposed (for each column the
                 // warp's 32 rows are 64 contiguous bytes)

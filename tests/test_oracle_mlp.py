@@ -17,6 +17,22 @@ def test_bf16_rounding_matches_torch():
     assert np.array_equal(mlp.bf16(x), want)
 
 
+def test_gelu_against_its_closed_forms():
+    """The tanh form against values that fix it independently: gelu(0) = 0;
+    gelu(z) - gelu(-z) = z (tanh is odd); as z -> +inf gelu(z) -> z and
+    gelu(-z) -> 0; and gelu(1) = (1 + tanh(1.044715 sqrt(2/pi))) / 2 written
+    out with the exponential form of tanh."""
+    z = np.linspace(-6.0, 6.0, 241)
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert np.allclose(mlp.gelu(z) - mlp.gelu(-z), z, rtol=0, atol=1e-13)
+    assert abs(mlp.gelu(np.array([30.0]))[0] - 30.0) < 1e-12 and abs(mlp.gelu(np.array([-30.0]))[0]) < 1e-12
+    u = 1.044715 * np.sqrt(2.0 / np.pi)
+    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.5 * (1.0 + (np.exp(2 * u) - 1) / (np.exp(2 * u) + 1))) < 1e-15
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(z), fd, rtol=0, atol=1e-8)
+
+
 def test_backward_matches_finite_differences():
     rng = np.random.default_rng(2)
     p = mlp.init_params(SIZES, 3).astype(np.float64)
@@ -49,7 +65,7 @@ def test_backward_matches_torch_autograd():
         off += fo
         a = a @ W + b
         if l < len(SIZES) - 2:
-            a = torch.nn.functional.gelu(a)  # exact (erf) form
+            a = torch.nn.functional.gelu(a, approximate="tanh")
     tl = ((a - torch.tensor(y)) ** 2).mean()
     tl.backward()
     assert abs(tl.item() - loss) < 1e-12
