@@ -122,7 +122,7 @@ def measured_peak_hbm():
 
 
 DAY_KERNEL_SOURCES = ("step_kernels.cu", "day_common.cuh", "deabm_device.cuh")
-MLP_KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc.h")
+MLP_KERNEL_SOURCES = ("mlp_tc.cu", "mlp_tc.h", "gelu.cuh")
 
 
 def sources_hash(names) -> str:

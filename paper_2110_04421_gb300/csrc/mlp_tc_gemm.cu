@@ -3,7 +3,7 @@
 // pass needs, the input gradients (dgrad) and the weight gradients (wgrad).
 //
 // C[M x N] = A[M x K] . B[N x K]^T, BF16 operands with K contiguous in memory,
-// FP32 accumulation.  One CTA (192 threads) computes a 128 x BN tile of C over
+// FP32 accumulation.  One CTA (320 threads) computes a 128 x BN tile of C over
 // its K range (a split of K for the weight gradients):
 //   * warp 0, one thread: TMA (cp.async.bulk.tensor, 128-byte swizzle) brings
 //     64-column K chunks of A (128 rows) and B (BN rows) into a two-stage ring of
@@ -12,9 +12,10 @@
 //     into the TMEM accumulator (128 lanes x BN columns), then tcgen05.commit to
 //     the stage's "empty" mbarrier (the buffer may be refilled) and, after the
 //     last chunk, to the accumulator's mbarrier;
-//   * warps 2-5: the epilogue, each reading its 32 TMEM lanes (rows) with
-//     tcgen05.ld, 32 columns at a time, and writing what the MLP needs (bias,
-//     GELU (tanh form) or its derivative, FP32 / BF16 / transposed BF16 stores).
+//   * warps 2-9: the epilogue, two warps per 32 TMEM lanes (rows), each reading
+//     every other block of 32 columns with tcgen05.ld and writing what the MLP
+//     needs (bias, GELU (tanh form) or its derivative, FP32 / BF16 / transposed
+//     BF16 stores).
 // Two CTAs share an SM (97 KB of shared memory and 256 TMEM columns each), so one
 // CTA's epilogue overlaps the other's copies and MMAs.  Operand tiles are read
 // only from this GPU's global memory (no cluster multicast).
@@ -38,7 +39,7 @@ using namespace tcx;
 
 constexpr uint32_t kBM = 128;
 constexpr uint32_t kStages = 2;
-constexpr uint32_t kThreads = 192;
+constexpr uint32_t kThreads = 320;
 constexpr uint32_t kATile = kBM * 128;     // 128 rows x 64 BF16
 constexpr uint32_t kBTileMax = 256 * 128;  // up to 256 rows x 64 BF16
 constexpr uint32_t kTmemCols = 256;
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
             }
             if (done) mma_commit(smem_u32(&accb));
         }
-    } else {  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+    } else {  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, every other 32 columns
+        const uint32_t ew = warp - 2u, half = ew >> 2;
         const uint32_t q = warp & 3u, row = q * 32u + lane, gm = m0 + row;
         const bool ok = nch > 0 ? mbar_wait_or_abort(smem_u32(&accb), 0u, g.polls, abort) : true;
         if (!ok) *abort = 1;
@@ -140,11 +142,11 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         // bias-gradient partials: each epilogue warp's column sums over its 32 rows,
         // through a transposed tile in the (no longer read) operand buffers
         const bool colsums = g.bpart && (g.epi == TC_EPI_DGRAD || g.epi == TC_EPI_MSE);
-        float *tile = (float *)smem + q * (32u * 33u);            // [32 columns][33]
-        float *wsum = (float *)smem + 4u * 32u * 33u + q * 256u;  // this warp's sums of BN <= 256 columns
+        float *tile = (float *)smem + ew * (32u * 33u);           // [32 columns][33]
+        float *wsum = (float *)smem + 8u * 32u * 33u + q * 256u;  // the quarter's sums of BN <= 256 columns
         if (ok) {
             const bool rv = gm < (uint32_t)g.M;
-            for (uint32_t cb = 0; cb < BN; cb += 32u) {
+            for (uint32_t cb = half * 32u; cb < BN; cb += 64u) {
                 float v[32];
                 if (nch > 0) {
                     tmem_ld32(tmem + ((q * 32u) << 16) + cb, v);
@@ -276,19 +278,19 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
             }
         }
         if (g.epi == TC_EPI_MSE) {  // the CTA's squared errors, rows in a fixed order
-            __shared__ double s_sq[kBM];
-            s_sq[row] = sq;
-            asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the four epilogue warps
-            if (row == 0) {
+            __shared__ double s_sq[2][kBM];
+            s_sq[half][row] = sq;
+            asm volatile("bar.sync 1, 256;\n" ::: "memory");  // the eight epilogue warps
+            if (row == 0 && half == 0) {
                 double t = 0.0;
-                for (uint32_t r = 0; r < kBM; ++r) t += s_sq[r];
+                for (uint32_t r = 0; r < kBM; ++r) t += s_sq[0][r] + s_sq[1][r];
                 g.loss_part[blockIdx.x] = t;
             }
         }
         if (colsums) {  // the CTA's column sums: the four warps' sums in warp order
-            asm volatile("bar.sync 1, 128;\n" ::: "memory");
-            const float *ws = (const float *)smem + 4u * 32u * 33u;
-            for (uint32_t c = row; c < BN && n0 + c < (uint32_t)g.N; c += kBM) {
+            asm volatile("bar.sync 1, 256;\n" ::: "memory");
+            const float *ws = (const float *)smem + 8u * 32u * 33u;
+            for (uint32_t c = half * kBM + row; c < BN && n0 + c < (uint32_t)g.N; c += 2u * kBM) {
                 const float t = ok ? (ws[c] + ws[256u + c]) + (ws[512u + c] + ws[768u + c]) : 0.0f;
                 g.bpart[(size_t)blockIdx.x * g.N + n0 + c] = t;
             }
