@@ -58,6 +58,51 @@ struct KArgs {
     uint32_t bn;  // N tile (multiple of 16, <= 256)
 };
 
+// A warp's 32 rows x 32 FP32 columns between registers (a thread per row) and
+// global memory, through a [32][36] shared tile: each global access instruction
+// then covers 4 rows x 128 contiguous bytes instead of 32 rows x 16 bytes (the
+// padding keeps both shared-memory access patterns free of bank conflicts).
+// base = the block's first row at its first column; rows at or past nrows are
+// neither read nor written.
+constexpr uint32_t kStgPitch = 36;
+
+__device__ __forceinline__ void rows_store_f32(float *stg, const float (&v)[32], float *base, size_t ld, uint32_t nrows,
+                                               uint32_t lane)
+{
+#pragma unroll
+    for (uint32_t q = 0; q < 8u; ++q)
+        *(float4 *)(stg + lane * kStgPitch + 4u * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    __syncwarp();
+#pragma unroll
+    for (uint32_t i = 0; i < 8u; ++i) {
+        const uint32_t r = 4u * i + (lane >> 3), c = 4u * (lane & 7u);
+        const float4 x = *(const float4 *)(stg + r * kStgPitch + c);
+        if (r < nrows) *(float4 *)(base + (size_t)r * ld + c) = x;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void rows_load_f32(float *stg, float (&v)[32], const float *base, size_t ld, uint32_t nrows,
+                                              uint32_t lane)
+{
+#pragma unroll
+    for (uint32_t i = 0; i < 8u; ++i) {
+        const uint32_t r = 4u * i + (lane >> 3), c = 4u * (lane & 7u);
+        const float4 x = r < nrows ? __ldg((const float4 *)(base + (size_t)r * ld + c)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        *(float4 *)(stg + r * kStgPitch + c) = x;
+    }
+    __syncwarp();
+#pragma unroll
+    for (uint32_t q = 0; q < 8u; ++q) {
+        const float4 x = *(const float4 *)(stg + lane * kStgPitch + 4u * q);
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_constant__ CUtensorMap ta,
                                                               const __grid_constant__ CUtensorMap tb, const KArgs ka)
 {
@@ -144,6 +189,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         const bool colsums = g.bpart && (g.epi == TC_EPI_DGRAD || g.epi == TC_EPI_MSE);
         float *tile = (float *)smem + ew * (32u * 33u);           // [32 columns][33]
         float *wsum = (float *)smem + 8u * 32u * 33u + q * 256u;  // the quarter's sums of BN <= 256 columns
+        float *stg = (float *)smem + 8u * 32u * 33u + 4u * 256u + ew * (32u * kStgPitch);  // this warp's row tile
+        const uint32_t r0 = m0 + q * 32u;  // the warp's first row
+        const uint32_t nrows = r0 < (uint32_t)g.M ? min(32u, (uint32_t)g.M - r0) : 0u;
         if (ok) {
             const bool rv = gm < (uint32_t)g.M;
             for (uint32_t cb = half * 32u; cb < BN; cb += 64u) {
@@ -160,16 +208,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                 // (row strides and n are multiples of 4 elements); else one by one
                 const bool full32 = n + 32u <= (uint32_t)g.N;
                 if (g.epi == TC_EPI_WGRAD) {
-                    if (rv) {
-                        float *o = g.outf + (size_t)blockIdx.z * g.M * g.ldf + (size_t)gm * g.ldf + n;
-                        if (full32) {
-#pragma unroll
-                            for (int c4 = 0; c4 < 8; ++c4)
-                                *(float4 *)(o + 4 * c4) = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
-                        } else {
-                            for (int e = 0; e < 32; ++e)
-                                if (n + e < (uint32_t)g.N) o[e] = v[e];
-                        }
+                    float *part = g.outf + (size_t)blockIdx.z * g.M * g.ldf;
+                    if (full32) {
+                        rows_store_f32(stg, v, part + (size_t)r0 * g.ldf + n, g.ldf, nrows, lane);
+                    } else if (rv) {
+                        float *o = part + (size_t)gm * g.ldf + n;
+                        for (int e = 0; e < 32; ++e)
+                            if (n + e < (uint32_t)g.N) o[e] = v[e];
                     }
                     continue;
                 }
@@ -189,35 +234,23 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
                     }
                 }
                 if (g.epi == TC_EPI_OUTPUT) {
-                    if (rv) {
+                    if (full32) {
+                        rows_store_f32(stg, v, g.outf + (size_t)r0 * g.ldf + n, g.ldf, nrows, lane);
+                    } else if (rv) {
                         float *o = g.outf + (size_t)gm * g.ldf + n;
-                        if (full32) {
-#pragma unroll
-                            for (int c4 = 0; c4 < 8; ++c4)
-                                *(float4 *)(o + 4 * c4) = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
-                        } else {
-                            for (int e = 0; e < 32; ++e)
-                                if (n + e < (uint32_t)g.N) o[e] = v[e];
-                        }
+                        for (int e = 0; e < 32; ++e)
+                            if (n + e < (uint32_t)g.N) o[e] = v[e];
                     }
                     continue;
                 }
                 // the FP32 value this epilogue keeps: z (HIDDEN), dz (DGRAD, MSE)
                 float other[32];
-                if (rv && g.epi != TC_EPI_HIDDEN) {  // DGRAD: the pre-activation; MSE: the target
+                if (g.epi != TC_EPI_HIDDEN && full32) {  // DGRAD: the pre-activation; MSE: the target
+                    if (g.epi == TC_EPI_DGRAD) rows_load_f32(stg, other, g.zin + (size_t)r0 * g.ldz + n, g.ldz, nrows, lane);
+                    else rows_load_f32(stg, other, g.y + (size_t)r0 * g.N + n, (size_t)g.N, nrows, lane);
+                } else if (rv && g.epi != TC_EPI_HIDDEN) {
                     const float *src = g.epi == TC_EPI_DGRAD ? g.zin + (size_t)gm * g.ldz + n : g.y + (size_t)gm * g.N + n;
-                    if (full32) {
-#pragma unroll
-                        for (int c4 = 0; c4 < 8; ++c4) {
-                            const float4 t = __ldg((const float4 *)src + c4);
-                            other[4 * c4] = t.x;
-                            other[4 * c4 + 1] = t.y;
-                            other[4 * c4 + 2] = t.z;
-                            other[4 * c4 + 3] = t.w;
-                        }
-                    } else {
-                        for (int e = 0; e < 32; ++e) other[e] = (n + e < (uint32_t)g.N) ? __ldg(src + e) : 0.0f;
-                    }
+                    for (int e = 0; e < 32; ++e) other[e] = (n + e < (uint32_t)g.N) ? __ldg(src + e) : 0.0f;
                 } else {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) other[e] = 0.0f;
@@ -226,20 +259,20 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = v[e] * gelu_act_grad(other[e]);
                 } else if (g.epi == TC_EPI_MSE) {
+                    float sq32 = 0.0f;  // this block's 32 squares in FP32, then one FP64 add
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const float d = v[e] - other[e];
-                        if (rv && n + e < (uint32_t)g.N) sq += (double)d * d;
+                        if (rv && n + e < (uint32_t)g.N) sq32 += d * d;
                         v[e] = 2.0f * d * g.scale;
                     }
+                    sq += (double)sq32;
                 }
-                if (rv && g.outf) {
-                    float *o = g.outf + (size_t)gm * g.ldf + n;
+                if (g.outf) {
                     if (full32) {
-#pragma unroll
-                        for (int c4 = 0; c4 < 8; ++c4)
-                            *(float4 *)(o + 4 * c4) = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
-                    } else {
+                        rows_store_f32(stg, v, g.outf + (size_t)r0 * g.ldf + n, g.ldf, nrows, lane);
+                    } else if (rv) {
+                        float *o = g.outf + (size_t)gm * g.ldf + n;
                         for (int e = 0; e < 32; ++e)
                             if (n + e < (uint32_t)g.N) o[e] = v[e];
                     }
