@@ -6,8 +6,9 @@
 // FP32 accumulation.  One CTA (320 threads) computes a 128 x BN tile of C over
 // its K range (a split of K for the weight gradients):
 //   * warp 0, one thread: TMA (cp.async.bulk.tensor, 128-byte swizzle) brings
-//     64-column K chunks of A (128 rows) and B (BN rows) into a two-stage ring of
-//     shared-memory buffers; each stage completes on its "full" mbarrier;
+//     64-column K chunks of A (128 rows) and B (BN rows) into a ring of two
+//     shared-memory stages (four for the weight gradients); each stage completes
+//     on its "full" mbarrier;
 //   * warp 1, one thread: four tcgen05.mma (M = 128, N = BN, K = 16) per chunk
 //     into the TMEM accumulator (128 lanes x BN columns), then tcgen05.commit to
 //     the stage's "empty" mbarrier (the buffer may be refilled) and, after the
@@ -16,9 +17,10 @@
 //     every other block of 32 columns with tcgen05.ld and writing what the MLP
 //     needs (bias, GELU (tanh form) or its derivative, FP32 / BF16 / transposed
 //     BF16 stores).
-// Two CTAs share an SM (97 KB of shared memory and 256 TMEM columns each), so one
-// CTA's epilogue overlaps the other's copies and MMAs.  Operand tiles are read
-// only from this GPU's global memory (no cluster multicast).
+// Two CTAs of the two-stage kernel share an SM (97 KB of shared memory and 256
+// TMEM columns each), so one CTA's epilogue overlaps the other's copies and
+// MMAs.  Operand tiles are read only from this GPU's global memory (no cluster
+// multicast).
 // Every mbarrier wait is bounded: a wait that gives up records an error, the
 // kernel waits (with a long fixed bound) for the copies and MMAs it started,
 // frees its TMEM and returns.
@@ -38,13 +40,14 @@ namespace mlpgemm {
 using namespace tcx;
 
 constexpr uint32_t kBM = 128;
-constexpr uint32_t kStages = 2;
 constexpr uint32_t kThreads = 320;
 constexpr uint32_t kATile = kBM * 128;     // 128 rows x 64 BF16
 constexpr uint32_t kBTileMax = 256 * 128;  // up to 256 rows x 64 BF16
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kDrainPolls = 1u << 26;  // bound of the waits for work already started
-constexpr size_t kSmemBytes = kStages * (kATile + kBTileMax) + 1024;
+// dynamic shared memory of a kernel with S stages (S = 2: two CTAs per SM; the
+// weight gradients, 128 CTAs or fewer, take 4 stages and one CTA per SM)
+constexpr size_t smem_bytes(uint32_t S) { return S * (kATile + kBTileMax) + 1024; }
 
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
@@ -103,6 +106,7 @@ __device__ __forceinline__ void rows_load_f32(float *stg, float (&v)[32], const 
     __syncwarp();
 }
 
+template <uint32_t kStages>
 __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_constant__ CUtensorMap ta,
                                                               const __grid_constant__ CUtensorMap tb, const KArgs ka)
 {
@@ -291,19 +295,29 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = gelu_act(v[e]);
                 }
-                // the BF16 copies: row-major, then transposed (for each column the
-                // warp's 32 rows are 64 contiguous bytes)
-                if (rv) {
-                    if (full32) {
-                        uint4 *o = (uint4 *)(g.outb + (size_t)gm * g.ldo + n);
+                // the BF16 copies: row-major (whole 64-byte row segments through the
+                // row tile), then transposed (for each column the warp's 32 rows are 64
+                // contiguous bytes)
+                if (full32) {  // row-major through the row tile: 4 lanes per row's 64 bytes
+                    uint32_t *st32 = (uint32_t *)stg;  // [32 rows][20 words]
 #pragma unroll
-                        for (int c8 = 0; c8 < 4; ++c8)
-                            o[c8] = make_uint4(pack_bf16x2(v[c8 * 8 + 0], v[c8 * 8 + 1]), pack_bf16x2(v[c8 * 8 + 2], v[c8 * 8 + 3]),
-                                               pack_bf16x2(v[c8 * 8 + 4], v[c8 * 8 + 5]), pack_bf16x2(v[c8 * 8 + 6], v[c8 * 8 + 7]));
-                    } else {
-                        for (int e = 0; e < 32; ++e)
-                            if (n + e < (uint32_t)g.N) g.outb[(size_t)gm * g.ldo + n + e] = __float2bfloat16(v[e]);
+                    for (int c8 = 0; c8 < 4; ++c8)
+                        *(uint4 *)(st32 + lane * 20u + 4u * c8) =
+                            make_uint4(pack_bf16x2(v[c8 * 8 + 0], v[c8 * 8 + 1]), pack_bf16x2(v[c8 * 8 + 2], v[c8 * 8 + 3]),
+                                       pack_bf16x2(v[c8 * 8 + 4], v[c8 * 8 + 5]), pack_bf16x2(v[c8 * 8 + 6], v[c8 * 8 + 7]));
+                    __syncwarp();
+#pragma unroll
+                    for (uint32_t i = 0; i < 4u; ++i) {
+                        const uint32_t r = 8u * i + (lane >> 2), c = lane & 3u;
+                        const uint4 x = *(const uint4 *)(st32 + r * 20u + 4u * c);
+                        if (r < nrows) *(uint4 *)(g.outb + (size_t)(r0 + r) * g.ldo + n + 8u * c) = x;
                     }
+                    __syncwarp();
+                } else if (rv) {
+                    for (int e = 0; e < 32; ++e)
+                        if (n + e < (uint32_t)g.N) g.outb[(size_t)gm * g.ldo + n + e] = __float2bfloat16(v[e]);
+                }
+                if (rv) {
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (n + e < (uint32_t)g.N) g.outt[(size_t)(n + e) * g.ldt + gm] = __float2bfloat16(v[e]);
@@ -392,7 +406,9 @@ cudaError_t mlptc_gemm(const TcGemm &g, cudaStream_t s)
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        attr_err = cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(2));
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(4));
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.kps <= 0 || g.kps % 64 || !g.err) return cudaErrorInvalidValue;
@@ -414,6 +430,9 @@ cudaError_t mlptc_gemm(const TcGemm &g, cudaStream_t s)
     const uint32_t splits = (uint32_t)((g.K + g.kps - 1) / g.kps);
     const dim3 grid((g.M + kBM - 1) / kBM, (g.N + ka.bn - 1) / ka.bn, splits);
     if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidValue;
-    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(ta, tb, ka);
+    if (g.epi == TC_EPI_WGRAD)  // long K, few CTAs: deeper copy pipeline
+        tc_gemm_kernel<4><<<grid, kThreads, smem_bytes(4), s>>>(ta, tb, ka);
+    else
+        tc_gemm_kernel<2><<<grid, kThreads, smem_bytes(2), s>>>(ta, tb, ka);
     return cudaGetLastError();
 }
