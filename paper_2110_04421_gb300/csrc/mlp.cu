@@ -225,24 +225,6 @@ __global__ void loss_reduce_kernel(const double *part, int nparts, float scale, 
     if (threadIdx.x == 0) *loss = (float)(red[0] * scale);
 }
 
-// db[j] = the sum of the per-CTA column partials part[parts][cols]: one block of
-// 128 threads per column, each summing a strided share of the parts, then a fixed
-// tree (deterministic)
-__global__ void colsum_parts_kernel(const float *part, int parts, int cols, float *db)
-{
-    __shared__ float red[128];
-    const int j = blockIdx.x;
-    float s = 0.0f;
-    for (int c = threadIdx.x; c < parts; c += blockDim.x) s += part[(long)c * cols + j];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) db[j] = red[0];
-}
-
 // db[j] = sum_i dz[i][j]: row chunks summed in parallel (partials [chunk][col]),
 // then the chunks in order (deterministic)
 constexpr int kColChunks = 64;
@@ -329,6 +311,87 @@ __global__ void weights_tc_kernel(const float *w, int fi, int fo, __nv_bfloat16 
     }
 }
 
+// After the tensor-core training GEMMs, one launch finishes every layer: the
+// weight gradient from its split partials (summed in split order) and the bias
+// gradient from the per-CTA column partials (a block per column, a fixed tree),
+// the same sums as the per-layer reductions; with `adam`, the Adam step (Kingma
+// and Ba, Algorithm 1) on each element right after its gradient, and the BF16
+// copies both GEMM paths read written in place.
+struct FinishLayer {
+    const float *wpart;  // [splits][fi * fo]; splits == 0: gW already holds the gradient
+    const float *bpart;  // [nparts][fo]
+    float *gW, *gb, *W, *mW, *vW, *b, *mb, *vb;
+    __nv_bfloat16 *Wb, *Wf, *WT;
+    int splits, nparts, fi, fo, ldf, ldt;  // Wf [fi][ldf], WT [fo][ldt], Wb [kpad][fo]
+};
+struct FinishSet {
+    int L, adam, wblocks;
+    float lr, b1, b2, eps, c1, c2;
+    long wstart[kMaxTcLayers + 1];  // prefix sums of fi * fo
+    int bstart[kMaxTcLayers + 1];   // prefix sums of fo (one block per bias column)
+    FinishLayer ly[kMaxTcLayers];
+};
+constexpr int kFinishThreads = 128;
+
+__device__ __forceinline__ float adam_elem(float *w, float *m, float *v, float gq, const FinishSet &F)
+{
+    const float mq = F.b1 * *m + (1.0f - F.b1) * gq, vq = F.b2 * *v + (1.0f - F.b2) * gq * gq;
+    *m = mq;
+    *v = vq;
+    const float wq = *w - F.lr * (mq / F.c1) / (sqrtf(vq / F.c2) + F.eps);
+    *w = wq;
+    return wq;
+}
+
+__global__ void __launch_bounds__(kFinishThreads) grad_finish_kernel(const FinishSet F)
+{
+    if ((int)blockIdx.x < F.wblocks) {
+        const long total = F.wstart[F.L];
+        for (long q = (long)blockIdx.x * kFinishThreads + threadIdx.x; q < total;
+             q += (long)F.wblocks * kFinishThreads) {
+            int l = 0;
+            while (q >= F.wstart[l + 1]) ++l;
+            const FinishLayer &Y = F.ly[l];
+            const long n = F.wstart[l + 1] - F.wstart[l], i = q - F.wstart[l];
+            float gq;
+            if (Y.splits > 0) {
+                gq = 0.0f;
+                for (int z = 0; z < Y.splits; ++z) gq += Y.wpart[(long)z * n + i];
+                Y.gW[i] = gq;
+            } else {
+                gq = Y.gW[i];
+            }
+            if (F.adam) {
+                const float wq = adam_elem(Y.W + i, Y.mW + i, Y.vW + i, gq, F);
+                const int r = (int)(i / Y.fo), c = (int)(i % Y.fo);
+                const __nv_bfloat16 h = __float2bfloat16(wq);
+                Y.Wb[(long)r * Y.fo + c] = h;
+                Y.Wf[(long)r * Y.ldf + c] = h;
+                Y.WT[(long)c * Y.ldt + r] = h;
+            }
+        }
+        return;
+    }
+    const int col = (int)blockIdx.x - F.wblocks;
+    int l = 0;
+    while (col >= F.bstart[l + 1]) ++l;
+    const FinishLayer &Y = F.ly[l];
+    const int j = col - F.bstart[l];
+    __shared__ float red[kFinishThreads];
+    float s = 0.0f;
+    for (int c = threadIdx.x; c < Y.nparts; c += kFinishThreads) s += Y.bpart[(long)c * Y.fo + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kFinishThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        Y.gb[j] = red[0];
+        if (F.adam) (void)adam_elem(Y.b + j, Y.mb + j, Y.vb + j, red[0], F);
+    }
+}
+
 }  // namespace mlpk
 
 using namespace mlpk;
@@ -361,7 +424,10 @@ struct deabm_mlp {
     std::vector<__nv_bfloat16 *> actT, Wf, WT;
     __nv_bfloat16 *gb16[2] = {nullptr, nullptr}, *gT[2] = {nullptr, nullptr};
     uint32_t polls = 1u << 26;
-    float *bpart = nullptr;  // bias-gradient partials of the tcgen05 path [max_batch / 128][width]
+    // per layer, kept until the step's one finishing launch: weight-gradient split
+    // partials [max_splits][fi x fo] and bias-gradient column partials [parts][fo]
+    std::vector<float *> wpartL, bpartL;
+    std::vector<int> splitsL;
 };
 
 static int ld8(int v) { return (v + 7) / 8 * 8; }
@@ -523,7 +589,14 @@ extern "C" int deabm_mlp_create(uint32_t n_in, uint32_t hidden, uint32_t depth, 
                 if ((r = m_alloc(m, &m->gb16[q], B * m->ldg))) return r;
                 if ((r = m_alloc(m, &m->gT[q], (size_t)m->ldg * m->bpad))) return r;
             }
-            if ((r = m_alloc(m, &m->bpart, ((B + 127) / 128) * (size_t)m->ldg))) return r;
+            for (int l = 0; l < m->L; ++l) {
+                float *wp, *bp;
+                if ((r = m_alloc(m, &wp, (size_t)m->max_splits * m->fin[l] * m->fout[l]))) return r;
+                if ((r = m_alloc(m, &bp, ((B + 127) / 128) * (size_t)m->fout[l]))) return r;
+                m->wpartL.push_back(wp);
+                m->bpartL.push_back(bp);
+            }
+            m->splitsL.assign(m->L, 0);
         }
         MCU(cudaStreamSynchronize(m->stream));
         return DEABM_OK;
@@ -735,7 +808,8 @@ extern "C" int deabm_mlp_use_tcgen05(deabm_mlp *m, int enable, int *available)
 
 // forward (keeping z_l, a_l and a_l^T) and backward of one batch on the tcgen05
 // GEMMs (mlp_tc_gemm.cu); same quantities and rounding points as the mma.sync path
-static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, float *loss_host)
+static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, float *loss_host, bool adam = false,
+                       float lr = 0.0f)
 {
     cudaStream_t s = m->stream;
     if (m->tr_dirty) {
@@ -776,7 +850,7 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             g.scale = 1.0f / (float)((long)batch * m->n_out);
             g.outf = nullptr;  // dz_L stays in BF16; its column sums (the bias gradient) come as partials
             g.ldf = m->n_out;
-            g.bpart = m->bpart;
+            g.bpart = m->bpartL[m->L - 1];
             g.outb = m->gb16[0];
             g.ldo = m->ldg;
             g.outt = m->gT[0];
@@ -807,18 +881,12 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
         gw.kps = ((batch + splits - 1) / splits + 63) / 64 * 64;
         splits = (batch + gw.kps - 1) / gw.kps;
         gw.epi = TC_EPI_WGRAD;
-        gw.outf = splits > 1 ? m->wpart : m->gW[l];
+        gw.outf = splits > 1 ? m->wpartL[l] : m->gW[l];
         gw.ldf = fo;
         gw.polls = m->polls;
         gw.err = m->tc_err;
         MCU(mlptc_gemm(gw, s));
-        if (splits > 1) {
-            splitk_reduce_kernel<<<256, 256, 0, s>>>(m->wpart, splits, (long)fi * fo, m->gW[l]);
-            MCU(cudaGetLastError());
-        }
-        // db_l from the partials the epilogue that produced dz_l left (one per 128 rows)
-        colsum_parts_kernel<<<fo, 128, 0, s>>>(m->bpart, nparts, fo, m->gb[l]);
-        MCU(cudaGetLastError());
+        m->splitsL[l] = splits > 1 ? splits : 0;  // summed, with db_l, in the finishing launch
         if (l > 0) {
             // dz_{l-1} = (dz_l W_l^T) * gelu'(z_{l-1})
             TcGemm gd{};
@@ -835,7 +903,7 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             gd.ldz = m->H;
             gd.outf = nullptr;
             gd.ldf = m->H;
-            gd.bpart = m->bpart;
+            gd.bpart = m->bpartL[l - 1];
             gd.outb = m->gb16[cur ^ 1];
             gd.ldo = m->ldg;
             gd.outt = m->gT[cur ^ 1];
@@ -845,6 +913,51 @@ static int mlp_grad_tc(deabm_mlp *m, const float *x, const float *y, int batch, 
             MCU(mlptc_gemm(gd, s));
             cur ^= 1;
         }
+    }
+    FinishSet F{};
+    F.L = m->L;
+    F.adam = adam ? 1 : 0;
+    F.wblocks = 2 * 152;
+    if (adam) {
+        m->step += 1;
+        F.lr = lr;
+        F.b1 = 0.9f;
+        F.b2 = 0.999f;
+        F.eps = 1e-8f;
+        F.c1 = 1.0f - powf(F.b1, (float)m->step);
+        F.c2 = 1.0f - powf(F.b2, (float)m->step);
+    }
+    F.wstart[0] = 0;
+    F.bstart[0] = 0;
+    for (int l = 0; l < m->L; ++l) {
+        FinishLayer &Y = F.ly[l];
+        Y.wpart = m->wpartL[l];
+        Y.splits = m->splitsL[l];
+        Y.bpart = m->bpartL[l];
+        Y.nparts = nparts;
+        Y.gW = m->gW[l];
+        Y.gb = m->gb[l];
+        Y.W = m->W[l];
+        Y.mW = m->mW[l];
+        Y.vW = m->vW[l];
+        Y.b = m->b[l];
+        Y.mb = m->mb[l];
+        Y.vb = m->vb[l];
+        Y.Wb = m->Wb[l];
+        Y.Wf = m->Wf[l];
+        Y.WT = m->WT[l];
+        Y.fi = m->fin[l];
+        Y.fo = m->fout[l];
+        Y.ldf = ld8(m->fout[l]);
+        Y.ldt = ld8(m->kpad[l]);
+        F.wstart[l + 1] = F.wstart[l] + (long)m->fin[l] * m->fout[l];
+        F.bstart[l + 1] = F.bstart[l] + m->fout[l];
+    }
+    grad_finish_kernel<<<F.wblocks + F.bstart[m->L], kFinishThreads, 0, s>>>(F);
+    MCU(cudaGetLastError());
+    if (adam) {  // the BF16 copies are current; the fused forward's weight images are not
+        m->wt_dirty = true;
+        m->tr_dirty = false;
     }
     if (loss_host) {
         MCU(cudaMemcpyAsync(loss_host, m->loss, 4, cudaMemcpyDeviceToHost, s));
@@ -886,8 +999,13 @@ static int mlp_adam(deabm_mlp *m, float lr)
 extern "C" int deabm_mlp_train_step(deabm_mlp *m, const float *x, const float *y, uint32_t batch, float lr, float *loss)
 {
     int r;
-    if ((r = deabm_mlp_grad(m, x, y, batch, nullptr))) return r;
-    if ((r = mlp_adam(m, lr))) return r;
+    if (m && x && y && batch > 0 && (int)batch <= m->max_batch && m->tr_ok && m->tc_on) {
+        // tensor-core path: the gradients' reductions and the Adam step in one launch
+        if ((r = mlp_grad_tc(m, x, y, (int)batch, nullptr, true, lr))) return r;
+    } else {
+        if ((r = deabm_mlp_grad(m, x, y, batch, nullptr))) return r;
+        if ((r = mlp_adam(m, lr))) return r;
+    }
     if (loss) {
         MCU(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream));
         MCU(cudaStreamSynchronize(m->stream));
