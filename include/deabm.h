@@ -195,7 +195,10 @@ typedef struct {
                                 1 standard (second doses first), 2 delayed second dose (first doses first),
                                 3 delayed except the elderly (bins >= elderly_bin interleaved by age with a
                                 first dose before a second, then the others' first doses, then their second
-                                doses); ties by agent id.  Plain contexts only. */
+                                doses); ties by agent id.  Plain and batched contexts (in a batched
+                                context every replicate column selects from its own state with its own
+                                dose2_delay and the same supply; the general panel kernel then runs
+                                the day instead of the four-replicate one); not ragged batches. */
     uint32_t elderly_bin;    /* first age bin counted as "65+" by strategy 3 */
     uint32_t vax_nonsterile; /* 0: immunity is sterilising (stage VAX); 1: non-sterilising (Sec. 5, second
                                 version): the agent stays susceptible with flag DEABM_FL_IMMUNE and any
@@ -293,7 +296,8 @@ int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf
                     uint8_t *qt, float *lambda, float *p);
 
 /* Days of each agent's first and second dose under a priority strategy
- * (host int16 [N], 0x7FFF = none; either may be NULL).  Synchronises. */
+ * (host int16 [n_agents][n_rep] in caller order, 0x7FFF = none; either may be
+ * NULL).  Synchronises. */
 int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day);
 
 /* Per-day counters already run: days [0, day_count) of new infections
@@ -331,7 +335,7 @@ int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64_t *rep_see
  * exactly.  deabm_save writes the state at the start of the next day to run
  * (stage, timer, tinf, flags, qt: host arrays [n_agents][n_rep] in caller order,
  * as deabm_get_state) and, under a priority strategy, the dose days (host
- * [n_agents], 0x7FFF = none; NULL otherwise); *day receives the day index.
+ * [n_agents][n_rep], 0x7FFF = none; NULL otherwise); *day receives the day index.
  * deabm_restore puts such a state back into a context created with the same
  * graph and parameters (this one or another) and sets its day: the next
  * deabm_step runs that day.  The day's emitted infectiousness is rebuilt from

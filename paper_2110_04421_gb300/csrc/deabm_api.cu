@@ -390,8 +390,6 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         return fail(ctx, DEABM_EINVAL, "vax_onset and dose2_delay must be >= 1");
     if (p->vax_strategy > 3 || p->elderly_bin > 9)
         return fail(ctx, DEABM_EINVAL, "vax_strategy must be 0..3 and elderly_bin 0..9");
-    if (p->vax_strategy != 0 && n_rep != 1)
-        return fail(ctx, DEABM_EINVAL, "vaccination priority strategies need a plain (one replicate) context");
     if (p->den_on) {
         if (n_rep != 1) return fail(ctx, DEABM_EINVAL, "exposure notification needs a plain (one replicate) context");
         if (!p->test_on) return fail(ctx, DEABM_EINVAL, "exposure notification needs test_on");
@@ -744,17 +742,20 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 std::vector<int16_t> d1(nb, kNever), d2(nb, kNever);
                 if ((a->dose1_day || a->dose2_day) && (r = host_order(ctx))) return r;
                 auto orig_of = [&](uint32_t q) { return ctx->relabel ? ctx->new2orig[q] : q; };
-                for (uint32_t q = 0; q < n; ++q) {
-                    if (a->dose1_day) d1[q] = a->dose1_day[orig_of(q)];
-                    if (a->dose2_day) d2[q] = a->dose2_day[orig_of(q)];
-                }
+                for (uint32_t q = 0; q < n; ++q)  // the caller's dose days, the same in every replicate
+                    for (uint32_t b = 0; b < n_rep; ++b) {
+                        if (a->dose1_day) d1[(size_t)q * n_rep + b] = a->dose1_day[orig_of(q)];
+                        if (a->dose2_day) d2[(size_t)q * n_rep + b] = a->dose2_day[orig_of(q)];
+                    }
                 if ((r = dalloc(ctx, &ctx->S.vd1, nb))) return r;
                 if ((r = dalloc(ctx, &ctx->S.vd2, nb))) return r;
                 if ((r = dalloc(ctx, &ctx->S0.vd1, nb))) return r;
                 if ((r = dalloc(ctx, &ctx->S0.vd2, nb))) return r;
-                if ((r = dalloc(ctx, &ctx->vax_cls, n))) return r;
-                if ((r = dalloc(ctx, &ctx->vax_dose, n))) return r;
-                if ((r = dalloc(ctx, &ctx->vax_scratch, vax_select_scratch_words(n)))) return r;
+                if ((r = dalloc(ctx, &ctx->vax_cls, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->vax_dose, nb))) return r;
+                if ((r = dalloc(ctx, &ctx->vax_scratch, n_rep > 1 ? vax_select_batch_scratch_words(n, n_rep)
+                                                                    : vax_select_scratch_words(n))))
+                    return r;
                 CU(ctx, cudaMemcpyAsync(ctx->S0.vd1, d1.data(), nb * 2, cudaMemcpyHostToDevice, s));
                 CU(ctx, cudaMemcpyAsync(ctx->S0.vd2, d2.data(), nb * 2, cudaMemcpyHostToDevice, s));
                 CU(ctx, cudaMemcpyAsync(ctx->S.vd1, d1.data(), nb * 2, cudaMemcpyHostToDevice, s));
@@ -956,8 +957,12 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         const int c = ctx->cur;
         KParams kp = ctx->kp;
         if (kp.vax_strategy != 0 && kp.vax_on && ctx->day >= ctx->base.vax_start) {
-            CU(ctx, launch_vax_select(kp, ctx->day, ctx->base.dose2_delay, ctx->base.elderly_bin, ctx->vax_supply,
-                                      ctx->S, ctx->vax_cls, ctx->vax_dose, ctx->vax_scratch, ctx->stream));
+            if (ctx->n_rep > 1)
+                CU(ctx, launch_vax_select_batch(kp, ctx->day, ctx->base.elderly_bin, ctx->vax_supply, ctx->S,
+                                                ctx->vax_cls, ctx->vax_dose, ctx->vax_scratch, ctx->stream));
+            else
+                CU(ctx, launch_vax_select(kp, ctx->day, ctx->base.dose2_delay, ctx->base.elderly_bin, ctx->vax_supply,
+                                          ctx->S, ctx->vax_cls, ctx->vax_dose, ctx->vax_scratch, ctx->stream));
             kp.dose_today = ctx->vax_dose;
         }
         InfBuffers I;
@@ -1145,7 +1150,8 @@ extern "C" int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if (!ctx->S.vd1) return fail(ctx, DEABM_ESTATE, "no vaccination priority strategy in this context");
-    const size_t nb = (size_t)ctx->n;
+    const uint32_t B = ctx->n_rep;
+    const size_t nb = (size_t)ctx->n * B;
     std::vector<int16_t> t1(nb), t2(nb);
     CU(ctx, cudaMemcpyAsync(t1.data(), ctx->S.vd1, nb * 2, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaMemcpyAsync(t2.data(), ctx->S.vd2, nb * 2, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1153,9 +1159,11 @@ extern "C" int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *
     int r = host_order(ctx);
     if (r) return r;
     for (uint32_t q = 0; q < ctx->n; ++q) {
-        const uint32_t o = ctx->relabel ? ctx->new2orig[q] : q;
-        if (dose1_day) dose1_day[o] = t1[q];
-        if (dose2_day) dose2_day[o] = t2[q];
+        const size_t o = (size_t)(ctx->relabel ? ctx->new2orig[q] : q) * B;
+        for (uint32_t b = 0; b < B; ++b) {
+            if (dose1_day) dose1_day[o + b] = t1[(size_t)q * B + b];
+            if (dose2_day) dose2_day[o + b] = t2[(size_t)q * B + b];
+        }
     }
     return DEABM_OK;
 }
@@ -1649,8 +1657,8 @@ extern "C" int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t 
     if ((r = put(ctx->S.flags, flags, 1, B))) return r;
     if ((r = put(ctx->S.qt, qt, 1, B))) return r;
     if (ctx->S.vd1) {
-        if ((r = put(ctx->S.vd1, dose1_day, 2, 1))) return r;
-        if ((r = put(ctx->S.vd2, dose2_day, 2, 1))) return r;
+        if ((r = put(ctx->S.vd1, dose1_day, 2, B))) return r;
+        if ((r = put(ctx->S.vd2, dose2_day, 2, B))) return r;
     }
     ctx->day = day;
     ctx->cur = 0;

@@ -121,7 +121,7 @@ struct KParams {
     const uint32_t *orig_id;   // internal id -> caller's agent id (nullptr: the same)
     uint32_t vax_strategy;     // 0 static schedule; 1..3 priority strategies with a shared supply
     uint32_t vax_nonsterile;   // 1: immunity leaves the agent susceptible (flag), infections asymptomatic
-    const uint8_t *dose_today; // priority strategies: 1 = dosed today, by caller id (nullptr: none)
+    const uint8_t *dose_today; // priority strategies: 1 = dosed today, [caller id][replicate] (nullptr: none)
     // daily occupation networks (n_occ = 0: none).  Internal rows are in
     // occupation order, members of one occupation consecutive and in ascending
     // caller id, so the member in place r of occupation g is row occ_start[g] + r.
@@ -272,7 +272,8 @@ __device__ __forceinline__ void new_infection(const Tables *tab, int age, uint4 
 // `infected` = the draw succeeded this day; `day` is the day index.
 template <bool RK = false>
 __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 key, uint32_t j, uint32_t day,
-                                        int age, int16_t d1, bool infected, AgentState &a, uint32_t inf_y)
+                                        int age, int16_t d1, bool infected, AgentState &a, uint32_t inf_y,
+                                        size_t dsel)
 {
     // the replicate's draws: from its round keys (RK: rp in parameter or shared
     // space) or from the seed's key schedule
@@ -334,7 +335,7 @@ __device__ __forceinline__ void advance(const KParams &P, const Rep &rp, uint2 k
     // two-dose vaccination (Sec. 4.4, Sec. 5)
     if (P.vax_on && P.vax_strategy != 0) {
         // priority strategies: today's doses were selected before the day from its starting state
-        if (P.dose_today && P.dose_today[j]) {
+        if (P.dose_today && P.dose_today[dsel]) {  // dsel: the agent's (caller id, replicate) slot
             if (!(a.fl & DEABM_FL_DOSE1)) { a.fl |= DEABM_FL_DOSE1; a.vd1 = (int)day; }
             else { a.fl |= DEABM_FL_DOSE2; a.vd2 = (int)day; }
         }

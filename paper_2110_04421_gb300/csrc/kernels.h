@@ -21,6 +21,13 @@ cudaError_t launch_vax_select(const KParams &P, uint32_t day, uint32_t dose2_del
                               uint32_t supply, const StateRef &S, uint8_t *cls_caller, uint8_t *dose_caller,
                               uint32_t *scratch, cudaStream_t stream);
 size_t vax_select_scratch_words(uint32_t n);
+// the same in every replicate column of a batched context (state [N][B], each
+// column's dose-2 delay, the same supply): dose [caller id][B]; scratch of
+// vax_select_batch_scratch_words(n, B)
+cudaError_t launch_vax_select_batch(const KParams &P, uint32_t day, uint32_t elderly_bin, uint32_t supply,
+                                    const StateRef &S, uint8_t *cls, uint8_t *dose, uint32_t *scratch,
+                                    cudaStream_t stream);
+size_t vax_select_batch_scratch_words(uint32_t n, uint32_t B);
 
 // set-up: infectiousness table (FP64 gamma integrals, rounded once, times A_class)
 cudaError_t launch_inf_table(Tables *tab, const double *shape_scale /*device [6]*/, const float *A_class /*device [3]*/,

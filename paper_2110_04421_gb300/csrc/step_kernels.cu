@@ -141,7 +141,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
         return;
     }
 #endif
-    advance<RK>(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
+    advance<RK>(P, rp, key, jo, day, age, d1, inf_now, a, inf_y, (size_t)jo * stride + b);
     if (DEN) {  // a positive app holder notifies its contacts after the day
         const bool v = a.pos_result && (a.fl & DEABM_FL_APP);
         *notify = v;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
                 const bool hit = infection_decision(lam_dt, unit_float(w.x), &p);
                 inf_now = (a.st == DEABM_S) && hit;
             }
-            advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y);
+            advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y, (size_t)jo * B + b0 + v);
             st_out[v] = (int8_t)a.st;
             tm_out[v] = (int16_t)a.tm;
             ti_out[v] = (int16_t)a.ti;
@@ -629,7 +629,7 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
             DEABM_PLAIN_CASE(14, true, true, false, true)
 #undef DEABM_PLAIN_CASE
         }
-    } else if (P.n_rep % kRepPerThread == 0) {
+    } else if (P.n_rep % kRepPerThread == 0 && P.vax_strategy == 0) {  // priority strategies: the general panel
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 32u * kRepPerThread - 1u) / (32u * kRepPerThread));
         const dim3 block(32, 8);
         if (lam_out) step_batch4_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);

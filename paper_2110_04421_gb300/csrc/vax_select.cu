@@ -138,4 +138,130 @@ cudaError_t launch_vax_select(const KParams &P, uint32_t day, uint32_t dose2_del
     return cudaGetLastError();
 }
 
+// ---- batched contexts: the same selection in every replicate column, each
+// from its own state and dose-2 delay, with the same supply.  The class array is
+// [caller id][replicate] like the state; the per-column ranking inside the
+// threshold class walks caller ids in chunks of kSelChunk (a thread per (chunk,
+// column), the columns of a warp side by side so every read is coalesced).
+constexpr uint32_t kSelChunk = 256;
+
+__global__ void vax_class_batch_kernel(const KParams P, uint32_t day, uint32_t elderly_bin, StateRef S, uint8_t *cls,
+                                       uint32_t *counts)
+{
+    __shared__ uint32_t h[kVaxClasses][32];
+    const uint32_t lane = threadIdx.x, wy = threadIdx.y, B = P.n_rep;
+    for (uint32_t q = wy * 32u + lane; q < kVaxClasses * 32u; q += 256u) (&h[0][0])[q] = 0;
+    __syncthreads();
+    const uint32_t b = blockIdx.y * 32u + lane;
+    if (b < B) {
+        const uint32_t delay = P.rep[b].dose2_delay;
+        for (uint32_t t = 0; t < 8u; ++t) {
+            const uint32_t j = blockIdx.x * 64u + t * 8u + wy;
+            if (j >= P.n) break;
+            const size_t i = (size_t)j * B + b;
+            const int st = S.stage[i];
+            const uint32_t fl = S.flags[i];
+            uint32_t type = 0;
+            if (!(st == DEABM_HOSP || st == DEABM_ICU || st == DEABM_DEAD)) {
+                if (!(fl & DEABM_FL_DOSE1)) type = 1;
+                else if (!(fl & DEABM_FL_DOSE2) && (int64_t)day - (int64_t)S.vd1[i] >= (int64_t)delay) type = 2;
+            }
+            uint8_t c = 255;
+            if (type) {
+                c = (uint8_t)vax_key(P.vax_strategy, elderly_bin, P.age[j], type);
+                atomicAdd(&h[c][lane], 1u);
+            }
+            cls[(size_t)(P.orig_id ? P.orig_id[j] : j) * B + b] = c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = wy * 32u + lane; q < kVaxClasses * 32u; q += 256u) {
+        const uint32_t c = q / 32u, l = q % 32u, bb = blockIdx.y * 32u + l;
+        if (bb < B && h[c][l]) atomicAdd(&counts[(size_t)bb * kVaxClasses + c], h[c][l]);
+    }
+}
+
+// a thread per column: threshold class and how many of it are dosed (sel[2b], sel[2b+1])
+__global__ void vax_threshold_batch_kernel(const uint32_t *counts, uint32_t B, uint32_t supply, uint32_t *sel)
+{
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint32_t *cb = counts + (size_t)b * kVaxClasses;
+    uint32_t cum = 0, c = 0;
+    for (; c < kVaxClasses; ++c) {
+        if (cum + cb[c] >= supply) break;
+        cum += cb[c];
+    }
+    sel[2u * b] = c;
+    sel[2u * b + 1u] = c < kVaxClasses ? supply - cum : 0u;
+}
+
+// per (chunk, column): members of the column's threshold class in the chunk
+__global__ void vax_chunk_count_kernel(const uint8_t *cls, uint32_t n, uint32_t B, const uint32_t *sel, uint32_t *ccnt)
+{
+    const uint32_t b = blockIdx.y * 32u + threadIdx.x, chunk = blockIdx.x * blockDim.y + threadIdx.y;
+    const uint32_t chunks = (n + kSelChunk - 1u) / kSelChunk;
+    if (b >= B || chunk >= chunks) return;
+    const uint32_t cstar = sel[2u * b], o1 = min(n, (chunk + 1u) * kSelChunk);
+    uint32_t cnt = 0;
+    for (uint32_t o = chunk * kSelChunk; o < o1; ++o) cnt += cls[(size_t)o * B + b] == cstar ? 1u : 0u;
+    ccnt[(size_t)chunk * B + b] = cnt;
+}
+
+// a thread per column: exclusive scan of its chunk counts, in chunk order (in place)
+__global__ void vax_chunk_scan_kernel(uint32_t *ccnt, uint32_t chunks, uint32_t B)
+{
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    uint32_t run = 0;
+    for (uint32_t c = 0; c < chunks; ++c) {
+        const uint32_t v = ccnt[(size_t)c * B + b];
+        ccnt[(size_t)c * B + b] = run;
+        run += v;
+    }
+}
+
+// per (chunk, column): the chunk's agents in caller-id order, ranked inside the
+// threshold class from the chunk's offset
+__global__ void vax_chunk_decide_kernel(const uint8_t *cls, uint32_t n, uint32_t B, const uint32_t *sel,
+                                        const uint32_t *coff, uint8_t *dose)
+{
+    const uint32_t b = blockIdx.y * 32u + threadIdx.x, chunk = blockIdx.x * blockDim.y + threadIdx.y;
+    const uint32_t chunks = (n + kSelChunk - 1u) / kSelChunk;
+    if (b >= B || chunk >= chunks) return;
+    const uint32_t cstar = sel[2u * b], r = sel[2u * b + 1u], o1 = min(n, (chunk + 1u) * kSelChunk);
+    uint32_t rank = coff[(size_t)chunk * B + b];
+    for (uint32_t o = chunk * kSelChunk; o < o1; ++o) {
+        const size_t i = (size_t)o * B + b;
+        const uint32_t c = cls[i];
+        const bool m = c == cstar;
+        dose[i] = (c != 255u && (c < cstar || (m && rank < r))) ? 1 : 0;
+        if (m) ++rank;
+    }
+}
+
+size_t vax_select_batch_scratch_words(uint32_t n, uint32_t B)
+{
+    return (size_t)B * (kVaxClasses + 2u) + (size_t)((n + kSelChunk - 1u) / kSelChunk) * B;
+}
+
+cudaError_t launch_vax_select_batch(const KParams &P, uint32_t day, uint32_t elderly_bin, uint32_t supply,
+                                    const StateRef &S, uint8_t *cls, uint8_t *dose, uint32_t *scratch,
+                                    cudaStream_t stream)
+{
+    const uint32_t n = P.n, B = P.n_rep, chunks = (n + kSelChunk - 1u) / kSelChunk;
+    uint32_t *counts = scratch, *sel = scratch + (size_t)B * kVaxClasses, *ccnt = sel + 2u * (size_t)B;
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * kVaxClasses * (size_t)B, stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t cgroups = (B + 31u) / 32u;
+    vax_class_batch_kernel<<<dim3((n + 63u) / 64u, cgroups), dim3(32, 8), 0, stream>>>(P, day, elderly_bin, S, cls,
+                                                                                      counts);
+    vax_threshold_batch_kernel<<<(B + 127u) / 128u, 128, 0, stream>>>(counts, B, supply, sel);
+    const dim3 cgrid((chunks + 7u) / 8u, cgroups), cblock(32, 8);
+    vax_chunk_count_kernel<<<cgrid, cblock, 0, stream>>>(cls, n, B, sel, ccnt);
+    vax_chunk_scan_kernel<<<(B + 127u) / 128u, 128, 0, stream>>>(ccnt, chunks, B);
+    vax_chunk_decide_kernel<<<cgrid, cblock, 0, stream>>>(cls, n, B, sel, ccnt, dose);
+    return cudaGetLastError();
+}
+
 }  // namespace deabm

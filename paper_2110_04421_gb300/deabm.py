@@ -528,9 +528,13 @@ class Simulation:
         return out
 
     def dose_days(self):
+        """Each agent's first and second dose day under a priority strategy
+        (0x7FFF = none): [N] arrays, or [N, B] in a batched context."""
         d1 = np.zeros(self.n * self.n_rep, np.int16)
         d2 = np.zeros(self.n * self.n_rep, np.int16)
         _check(lib().deabm_get_dose_days(self.ctx, _p(d1), _p(d2)), self.ctx)
+        if self.n_rep > 1:
+            return d1.reshape(self.n, self.n_rep), d2.reshape(self.n, self.n_rep)
         return d1, d2
 
     def counters(self, days: int | None = None):
@@ -556,7 +560,7 @@ class Simulation:
         shape = (self.n,) if self.n_rep == 1 else (self.n, self.n_rep)
         out = dict(stage=np.zeros(shape, np.int8), timer=np.zeros(shape, np.int16), tinf=np.zeros(shape, np.int16),
                    flags=np.zeros(shape, np.uint8), qt=np.zeros(shape, np.uint8),
-                   dose1_day=np.zeros(self.n, np.int16), dose2_day=np.zeros(self.n, np.int16))
+                   dose1_day=np.zeros(shape, np.int16), dose2_day=np.zeros(shape, np.int16))
         day = C.c_uint32()
         _check(lib().deabm_save(self.ctx, *(_p(out[k]) for k in ("stage", "timer", "tinf", "flags", "qt",
                                                                  "dose1_day", "dose2_day")), C.byref(day)), self.ctx)

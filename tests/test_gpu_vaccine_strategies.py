@@ -71,3 +71,36 @@ def test_nonsterilising_immunity_matches_oracle(strategy):
                       vax_nonsterile=1, R=4.5, seed=91, net_seed=92)
     rep = compare_days(pop, p, 60)
     assert rep["flips"] == 0 and rep["days"] == 60
+
+
+@pytest.mark.parametrize("strategy,B", [(1, 8), (3, 5)])
+def test_strategies_in_batched_contexts_match_oracle_columns(strategy, B):
+    """A batched context under a priority strategy: every replicate column
+    selects its doses from its own state with its own dose-2 delay (and the same
+    supply); each column equals the oracle's plain run with that column's
+    parameters and seed — incidence, stages and dose days."""
+    from paper_2110_04421_gb300.deabm import Simulation
+    T = 45
+    pop = W.population(4001, 14, 30)
+    base = W.params_with(vax_on=1, vax_start=3, vax_rate=0.03, vax_strategy=strategy, R=4.0, test_on=1, quar_on=1,
+                         net_seed=85)
+    rp, seeds = W.batch_params(B, 7)
+    g = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds, max_steps=T)
+    ni, _ = g.run(T)
+    st = g.state()
+    d1, d2 = g.dose_days()
+    g.close()
+    assert d1.shape == (pop["n"], B)
+    delays = set()
+    for c in range(B):
+        pc = dict(base, R=float(rp[c, 0]), B_net=[float(rp[c, 1]), float(rp[c, 2])], B_rand=float(rp[c, 3]),
+                  S_age=[float(x) for x in rp[c, 4:13]], dose2_delay=int(rp[c, 13]), seed=int(seeds[c]))
+        delays.add(int(rp[c, 13]))
+        o = oracle.Sim(pop, pc, pop["age"], pop["seed_ids"])
+        o_ni, _, _ = o.run(T)
+        assert np.array_equal(ni[:, c], o_ni), c
+        assert np.array_equal(st["stage"][:, c], o.state.stage), c
+        assert np.array_equal(d1[:, c], o.state.vd1) and np.array_equal(d2[:, c], o.state.vd2), c
+        if int(rp[c, 13]) < T - 4:
+            assert (d2[:, c] != 0x7FFF).sum() > 0, c  # second doses were given
+    assert len(delays) > 1  # the columns' delays differ
