@@ -116,9 +116,11 @@ typedef struct deabm_ctx deabm_ctx;
  * the new one, and both ends receive each other's messages.  Agent j's messages
  * are summed in this order: its own edges m = 1..k/2, the unrewired lattice
  * edges of agents j - m, m = 1..k/2, then the rewired edges that landed on j by
- * owner ascending and m ascending.  Plain contexts only (one replicate, no
- * exposure notification, not in ragged batches); the day's graph is built on the
- * device before each day kernel (three small kernels and a prefix sum).
+ * owner ascending and m ascending.  Plain and batched contexts (the graph,
+ * keyed by net_seed, is shared by every replicate column; a batched context
+ * then runs the general panel kernel), without exposure notification, not in
+ * ragged batches; the day's graph is built on the device before each day kernel
+ * (three small kernels and a prefix sum).
  */
 typedef struct {
     uint32_t n_agents;

@@ -172,10 +172,14 @@ __device__ __forceinline__ uint32_t wsg_far(const KParams &P, uint32_t i, uint32
 // summed left to right from +0.0f: its own edges m = 1..h, the unrewired lattice
 // edges of agents jo - m, m = 1..h, then the rewired edges that landed on jo, by
 // owner ascending.  *k_out = their number.  NEED_SUM = false: the count only.
-template <bool NEED_SUM = true, bool RK = true>
+// Agent c's infectiousness is inf[c * stride + b], or (ROWMAP) inf[row_of[c] *
+// stride + b] when the panel is in internal row order.
+template <bool NEED_SUM = true, bool RK = true, bool ROWMAP = false>
 __device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restrict__ inf, uint32_t jo, uint32_t day,
-                                         uint32_t *k_out)
+                                         uint32_t *k_out, uint32_t stride = 1u, uint32_t b = 0u,
+                                         const uint32_t *row_of = nullptr)
 {
+    auto val = [&](uint32_t c) { return __ldg(inf + (size_t)(ROWMAP ? __ldg(row_of + c) : c) * stride + b); };
     const uint32_t n = P.n, h = P.wsg_h;
     float r = 0.0f;
     uint32_t k = h;
@@ -183,9 +187,9 @@ __device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restri
         for (uint32_t m = 1; m <= h; m += 2u) {
             const uint4 w = net_draw<RK>(P, jo, day, kStreamWsg, (m - 1u) >> 1);
             const uint32_t f0 = wsg_far(P, jo, m, w.x, w.y);
-            const float v0 = __ldg(inf + f0);
+            const float v0 = val(f0);
             float v1 = 0.0f;
-            if (m + 1u <= h) v1 = __ldg(inf + wsg_far(P, jo, m + 1u, w.z, w.w));
+            if (m + 1u <= h) v1 = val(wsg_far(P, jo, m + 1u, w.z, w.w));
             r = __fadd_rn(r, v0);
             if (m + 1u <= h) r = __fadd_rn(r, v1);
         }
@@ -194,13 +198,13 @@ __device__ __forceinline__ float wsg_sum(const KParams &P, const float *__restri
         const uint32_t i = (uint32_t)(((uint64_t)jo + (uint64_t)n - (uint64_t)(m % n)) % n);
         if (!((__ldg(P.wsg_rew + i) >> (m - 1u)) & 1u)) {
             ++k;
-            if (NEED_SUM) r = __fadd_rn(r, __ldg(inf + i));
+            if (NEED_SUM) r = __fadd_rn(r, val(i));
         }
     }
     const uint32_t s0 = __ldg(P.wsg_start + jo), s1 = __ldg(P.wsg_start + jo + 1u);
     k += s1 - s0;
     if (NEED_SUM)
-        for (uint32_t q = s0; q < s1; ++q) r = __fadd_rn(r, __ldg(inf + __ldg(P.wsg_land + q)));
+        for (uint32_t q = s0; q < s1; ++q) r = __fadd_rn(r, val(__ldg(P.wsg_land + q)));
     *k_out = k;
     return r;
 }
@@ -367,7 +371,9 @@ __device__ __forceinline__ float lambda_at(const KParams &P, const Rep &rp, cons
     if (REC && rec) rec[0] = k_rand | (k_occ << 8);
     if (WSG && P.wsg_on) {  // the Watts-Strogatz random network in the random network's place
         uint32_t kw;
-        const float term = __fmul_rn(rp.B_rand, wsg_sum<true, RK>(P, I.rand_cur, jo, day, &kw));
+        const float w = rmap ? wsg_sum<true, RK, true>(P, rinf, jo, day, &kw, stride, b, I.row_of)
+                             : wsg_sum<true, RK, false>(P, rinf, jo, day, &kw, stride, b, nullptr);
+        const float term = __fmul_rn(rp.B_rand, w);
         s = (P.n_nets == 0 && (!OCC || P.n_occ == 0)) ? term : __fadd_rn(s, term);
         *k_out += kw;
     }

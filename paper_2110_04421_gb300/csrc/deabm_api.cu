@@ -317,7 +317,6 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         if (n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
         if ((uint64_t)n * (g->rand_ws_k / 2) >= (1ull << 31))
             return fail(ctx, DEABM_EINVAL, "n_agents * rand_ws_k / 2 must be < 2^31");
-        if (n_rep != 1) return fail(ctx, DEABM_EINVAL, "the Watts-Strogatz random network runs in plain contexts only");
         if (p->den_on) return fail(ctx, DEABM_EINVAL, "the Watts-Strogatz random network excludes exposure notification");
     }
     using Firsts = RowFirsts;

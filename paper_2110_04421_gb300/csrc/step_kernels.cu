@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
 // Batched panel: block (32 x 8) covers 8 agents x 32 replicates; lane = replicate.
 // The 32 lanes of a warp read the same CSR entries (one broadcast load) and
 // gather one contiguous 128 B run of the [N][B] infectiousness panel per edge.
-template <bool KEEP>
+template <bool KEEP, bool WSG>
 __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                          Counters C, float *lam_out, float *p_out)
 {
@@ -290,8 +290,8 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     if (active) {
         const Rep &rp = P.rep[b];
         uint32_t kg;
-        agent_day<true, false, true>(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st,
-                                     &infected, &k, &kg);
+        agent_day<true, false, true, WSG>(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st,
+                                          &infected, &k, &kg);
         atomicAdd(&s_cnt[st][lane], 1);
         if (infected) atomicAdd(&s_cnt[DEABM_N_STAGE][lane], 1);
     }
@@ -629,7 +629,8 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
             DEABM_PLAIN_CASE(14, true, true, false, true)
 #undef DEABM_PLAIN_CASE
         }
-    } else if (P.n_rep % kRepPerThread == 0 && P.vax_strategy == 0) {  // priority strategies: the general panel
+    } else if (P.n_rep % kRepPerThread == 0 && P.vax_strategy == 0 && !P.wsg_on) {
+        // (priority strategies and the Watts-Strogatz random network: the general panel)
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 32u * kRepPerThread - 1u) / (32u * kRepPerThread));
         const dim3 block(32, 8);
         if (lam_out) step_batch4_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
@@ -637,8 +638,13 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
     } else {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
         const dim3 block(32, 8);
-        if (lam_out) step_batch_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
-        else step_batch_kernel<false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        if (P.wsg_on) {
+            if (lam_out) step_batch_kernel<true, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_batch_kernel<false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        } else {
+            if (lam_out) step_batch_kernel<true, false><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_batch_kernel<false, false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        }
     }
     return cudaGetLastError();
 }

@@ -57,9 +57,39 @@ def test_watts_strogatz_rejected_where_not_built():
     pop["rand_ws_k"] = 2
     with pytest.raises(DeabmError, match="exposure notification"):
         gpu_sim(pop, W.params_with(den_on=1, test_on=1))
-    rp, seeds = W.batch_params(8, 0)
+    from paper_2110_04421_gb300.deabm import RaggedSimulation
     with pytest.raises(DeabmError, match="plain contexts"):
-        gpu_sim(pop, W.params_with(), n_rep=8, rep_params=rp, rep_seeds=seeds)
+        RaggedSimulation([pop, W.population(1_500, 2, 5)], [W.params_with(), W.params_with()], max_steps=4)
+
+
+@pytest.mark.parametrize("B,locality", [(8, True), (5, False)])
+def test_watts_strogatz_in_batched_contexts_match_oracle_columns(B, locality):
+    """A batched context: the day's graph (keyed by the network seed) built once
+    and shared by every replicate column; each column equals the oracle's plain
+    run with its own parameters and seed (incidence and stages), and the day's
+    message count is the shared graph's."""
+    import oracle
+    from paper_2110_04421_gb300.deabm import Simulation
+    T = 30
+    pop = dict(W.population(6_007, 4, 30), rand_ws=1, rand_ws_k=4, rand_ws_beta=0.3)
+    base = W.params_with(test_on=1, quar_on=1, net_seed=17)
+    rp, seeds = W.batch_params(B, 3)
+    g = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds, max_steps=T,
+                   locality_order=locality)
+    ni, _ = g.run(T)
+    st = g.state()
+    _, _, msgs = g.counters(T)
+    g.close()
+    for c in range(B):
+        pc = dict(base, R=float(rp[c, 0]), B_net=[float(rp[c, 1]), float(rp[c, 2])], B_rand=float(rp[c, 3]),
+                  S_age=[float(x) for x in rp[c, 4:13]], dose2_delay=int(rp[c, 13]), seed=int(seeds[c]))
+        o = oracle.Sim(pop, pc, pop["age"], pop["seed_ids"])
+        o_ni, _, o_msgs = o.run(T)
+        assert np.array_equal(ni[:, c], o_ni), c
+        assert np.array_equal(st["stage"][:, c], o.state.stage), c
+        if c == 0:
+            assert np.array_equal(np.asarray(msgs[:T], np.int64), np.asarray(o_msgs, np.int64))
+    assert ni.sum() > 100
 
 
 def test_watts_strogatz_full_size_first_days():
