@@ -101,9 +101,10 @@ typedef struct deabm_ctx deabm_ctx;
  * 2^32), skipping the agent itself, word' = word 2(e%2)+1 of that block.
  * Their sum enters Eq. 1 with weight B_net[n_nets], after the
  * stored networks and before the random network, so n_nets must be <= 3.
- * Only plain and batched contexts take them (deabm_create, deabm_create_batch);
- * the other constructors reject n_occ > 0.  n_occ = 0: occ_group and occ_k are
- * ignored. *
+ * Plain, batched and ragged contexts take them (deabm_create,
+ * deabm_create_batch, deabm_create_ragged: a population with n_occ > 0 is
+ * numbered in occupation order); the relaxed model rejects n_occ > 0.  n_occ =
+ * 0: occ_group and occ_k are ignored. *
  * rand_ws = 1 replaces the Poisson contacts by the paper's form of the global
  * random network (Sec. 3 "Interaction Networks": one small-world Watts-Strogatz
  * graph, re-initialised every step; rand_mean is then ignored).  The ring

@@ -64,6 +64,7 @@ struct deabm_ctx {
     deabm_params base{};
     // ragged batch of populations (n_rep counts the populations for the counters)
     bool ragged = false;
+    bool ragged_occ = false;  // some population of the ragged batch draws daily occupation contacts
     std::vector<PopDesc> pops;         // host copies, KParams pointers already offset
     PopDesc *d_pops = nullptr;
     Tile *d_tiles = nullptr;
@@ -946,7 +947,8 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         for (uint32_t q = 0; q < n_steps; ++q) {
             const int c = ctx->cur;
             CU(ctx, launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, ctx->day, ctx->inf[c],
-                                       ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->stream));
+                                       ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ,
+                                       ctx->stream));
             ctx->cur ^= 1;
             ctx->day += 1;
         }
@@ -1034,7 +1036,8 @@ static int run_ragged_graph(deabm_ctx *ctx, uint32_t T)
         int c = cur0;
         for (uint32_t q = 0; q < T; ++q) {
             cudaError_t e = launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, d0 + q, ctx->inf[c],
-                                               ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->stream);
+                                               ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ,
+                                               ctx->stream);
             if (e != cudaSuccess) {
                 cudaStreamEndCapture(ctx->stream, &g);
                 return fail(ctx, DEABM_ECUDA, "capture: %s", cudaGetErrorString(e));
@@ -1234,8 +1237,6 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
             if (graphs[q].rand_ws)
                 return fail(ctx, DEABM_EINVAL, "population %u: the Watts-Strogatz random network runs in plain contexts only", q);
-            if (graphs[q].n_occ)
-                return fail(ctx, DEABM_EINVAL, "daily occupation networks are not available for ragged batches");
             if (params[q].den_on)
                 return fail(ctx, DEABM_EINVAL, "exposure notification is not available for ragged batches");
             if (params[q].vax_strategy)
@@ -1311,8 +1312,12 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.dt = p.dt;
             K.rand_on = g.rand_mean > 0.0f ? 1u : 0u;
             // the population's stored networks; renumbered on the device like a
-            // plain context's when locality_order asks for it
-            const bool relabel_q = p.locality_order != 0 && g.n_nets > 0;
+            // plain context's when locality_order asks for it, or in occupation
+            // order (members of an occupation adjacent) when it draws daily
+            // occupation contacts
+            const bool occ_q = g.n_occ > 0;
+            const bool relabel_q = (p.locality_order != 0 && g.n_nets > 0) || occ_q;
+            std::vector<uint32_t> occ_order, occ_start;  // host staging, kept to the population's sync
             DevScratch sc;
             uint32_t *src_rp[DEABM_MAX_NETS] = {}, *src_col[DEABM_MAX_NETS] = {};
             uint32_t best = 0;
@@ -1334,19 +1339,46 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
                 K.col[k] = cl;
                 ctx->static_edges += E;
             }
-            if (relabel_q) {  // this population's numbering (local ids), built on the device
-                uint32_t *label, *tmp, *d_scan, *changed;
-                if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
-                if ((r = scratch_alloc(ctx, sc, &tmp, std::max<size_t>(n, order_scratch_words(n))))) return r;
+            if (relabel_q) {  // this population's numbering (local ids)
+                uint32_t *d_scan;
                 if ((r = scratch_alloc(ctx, sc, &d_scan, scan_scratch_words((size_t)n + 1)))) return r;
-                if ((r = scratch_alloc(ctx, sc, &changed, 1))) return r;
-                CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, changed, s));
-                CU(ctx, launch_order_by_label(label, n, ctx->orig_local + base, tmp, s));
+                if (occ_q) {
+                    occupation_order(&g, occ_order, occ_start);
+                    CU(ctx, cudaMemcpyAsync(ctx->orig_local + base, occ_order.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+                } else {  // by label propagation on the device
+                    uint32_t *label, *tmp, *changed;
+                    if ((r = scratch_alloc(ctx, sc, &label, n))) return r;
+                    if ((r = scratch_alloc(ctx, sc, &tmp, std::max<size_t>(n, order_scratch_words(n))))) return r;
+                    if ((r = scratch_alloc(ctx, sc, &changed, 1))) return r;
+                    CU(ctx, launch_locality_labels(src_rp[best], src_col[best], n, kLocalityRounds, label, tmp, changed,
+                                                   s));
+                    CU(ctx, launch_order_by_label(label, n, ctx->orig_local + base, tmp, s));
+                }
                 CU(ctx, launch_invert(ctx->orig_local + base, n, ctx->row_local + base, s));
                 for (uint32_t k = 0; k < g.n_nets; ++k)
                     CU(ctx, launch_csr_renumber(src_rp[k], src_col[k], ctx->orig_local + base, ctx->row_local + base, n,
                                                 (uint32_t *)K.row_ptr[k], (uint32_t *)K.col[k], d_scan, s));
                 pd.row_of = ctx->row_local + base;
+            }
+            std::vector<uint32_t> occ_gid;
+            if (occ_q) {  // occupation of each row, each occupation's first row and daily count
+                occ_gid.resize(n);
+                for (uint32_t q2 = 0; q2 < n; ++q2) occ_gid[q2] = g.occ_group[occ_order[q2]];
+                uint32_t *d_gid, *d_start;
+                uint8_t *d_k;
+                if ((r = dalloc(ctx, &d_gid, n))) return r;
+                if ((r = dalloc(ctx, &d_start, (size_t)g.n_occ + 1))) return r;
+                if ((r = dalloc(ctx, &d_k, g.n_occ))) return r;
+                CU(ctx, cudaMemcpyAsync(d_gid, occ_gid.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(d_start, occ_start.data(), 4ull * ((size_t)g.n_occ + 1), cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(d_k, g.occ_k, g.n_occ, cudaMemcpyHostToDevice, s));
+                K.n_occ = g.n_occ;
+                K.occ_gid = d_gid;
+                K.occ_start = d_start;
+                K.occ_k = d_k;
+                K.occ_lattice = g.occ_lattice;
+                K.thr_rewire = threshold((double)g.occ_rewire);
+                ctx->ragged_occ = true;
             }
             K.net_seed = p.net_seed;
             round_keys(p.net_seed, K.nrk);

@@ -309,14 +309,15 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     if (tid == 0 && s_msgs) atomicAdd(&C.msgs[day], s_msgs);
 }
 
-// Ragged batch of independent populations in one launch (no daily occupation
-// networks): CTAs stay resident and
+// Ragged batch of independent populations in one launch (OCC: some population
+// draws its occupation contacts daily): CTAs stay resident and
 // pull tiles (rows of one population) from the day's atomic queue until none is
 // left, so populations of 10^4 and 10^6 agents share the GPU without one
 // launch each.  Every row runs the plain day on its population's local ids,
 // giving exactly the single-population result.
 // 6 blocks per SM asked (swept at 64 populations, autotuned tiling: no minimum
 // 0.533 ms a day at 64 registers, 6 blocks 0.472, 8 blocks 0.480)
+template <bool OCC>
 __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__restrict__ pops, const Tile *__restrict__ tiles,
                                                           uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                                           const float *inf_cur, float *inf_next, StateRef S,
@@ -363,8 +364,8 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             uint32_t k = 0, kg = 0;
             if (active)
                 // the population's parameters are in shared memory: keys from the seeds (RK = false)
-                agent_day<false, false, true, false, false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
-                                                            &infected, &k, &kg);
+                agent_day<OCC, false, true, false, false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
+                                                          &infected, &k, &kg);
             count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
         }
         __syncthreads();
@@ -381,9 +382,10 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
 
 cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
-                               uint32_t n_pops, uint32_t grid, cudaStream_t stream)
+                               uint32_t n_pops, uint32_t grid, bool occ, cudaStream_t stream)
 {
-    step_ragged_kernel<<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops);
+    if (occ) step_ragged_kernel<true><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops);
+    else step_ragged_kernel<false><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops);
     return cudaGetLastError();
 }
 

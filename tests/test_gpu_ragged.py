@@ -83,3 +83,29 @@ def test_autotuned_tiling_changes_nothing():
     ni, h, _ = r.counters(T)
     check((ni, h, r.state()), singles)
     r.close()
+
+
+@pytest.mark.parametrize("locality", [True, False])
+def test_daily_occupations_in_ragged_batches(locality):
+    """Populations that draw their occupation contacts daily (one of them as
+    rewired ring lattices) mixed with ones that store them: each population of
+    the ragged batch equals its own single-population run, and the small one
+    the oracle."""
+    from paper_2110_04421_gb300.deabm import RaggedSimulation
+    pops, params = case()
+    for q, lattice in ((0, 0), (2, 1), (3, 0)):
+        p = pops[q]
+        p["row_ptr"], p["col"] = p["row_ptr"][:1], p["col"][:1]  # households stay stored
+        p["occ_group"], p["occ_k"] = W.occupations(p["n"], 60 + q, n_occ=4 if p["n"] < 100 else 23)
+        if lattice:
+            p["occ_lattice"], p["occ_rewire"] = 1, 0.2
+    T = 30
+    singles = single_runs(pops, params, T)
+    r = RaggedSimulation(pops, params, max_steps=T, locality_order=locality)
+    ni, h = r.run(T)
+    check((ni, h, r.state()), singles)
+    r.close()
+    assert ni[:, 0].sum() > 0 and ni[:, 2].sum() > 0
+    o = oracle_sim(pops[3], params[3])  # the 33-agent population with daily occupations
+    ni_o, h_o, _ = o.run(T)
+    assert np.array_equal(ni_o, ni[:, 3]) and np.array_equal(h_o, h[:, 3])
