@@ -214,10 +214,13 @@ typedef struct {
                                 in label order, ids ascending inside a group; results and every
                                 array the ABI returns are unchanged (random draws and outputs use
                                 the caller's agent ids) */
-    /* Digital exposure notification (Sec. 4.2); plain contexts with test_on only.
+    /* Digital exposure notification (Sec. 4.2); plain and batched contexts with
+     * test_on (not ragged batches, not with the Watts-Strogatz random network).
      * At create (and reset) agent j gets DEABM_FL_APP when word x of Philox
      * stream 6 keyed (seed, j, day word 0xFFFFFFFD) is below floor(den_adoption
-     * 2^32).  An app holder whose positive test result lands on day t notifies,
+     * 2^32); in a batched context each replicate column draws its own app holders
+     * (and compliance words) with its own seed, so column b reproduces the plain
+     * run with that seed.  An app holder whose positive test result lands on day t notifies,
      * after every agent's update of day t, each app holder that is out of
      * quarantine, not in hospital, ICU or dead, and had it as an in-contact on one
      * of the days max(0, t-den_window+1) .. t (stored networks, daily occupation
@@ -398,9 +401,11 @@ int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t *age_bin, c
                          float *lambda, void *cuda_stream);
 const char *deabm_lambda_noalloc_last_error(void);
 
-/* Exposure notification (den_on): notified[d] = agents notified at the end of
- * day d, for d < day_count (day_count <= days run; host array).  Zeros when
- * den_on = 0.  Returns DEABM_OK, DEABM_EINVAL, DEABM_ECUDA. */
+/* Exposure notification (Sec. 4.2, den_on): notified[d][b] = agents of replicate
+ * column b notified at the end of day d, for d < day_count (day_count <= days
+ * run; host array of day_count x n_rep int32, n_rep = 1 in plain contexts).
+ * Zeros when den_on = 0 (ragged batches: day_count entries, all zero).  Returns
+ * DEABM_OK, DEABM_EINVAL, DEABM_ECUDA. */
 int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *notified);
 
 /* Days run so far, agents, replicates. */

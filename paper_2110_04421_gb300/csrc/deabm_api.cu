@@ -47,7 +47,8 @@ struct deabm_ctx {
     uint32_t n_occ = 0;
     uint32_t *occ_gid = nullptr, *occ_start = nullptr;
     uint8_t *occ_k = nullptr;
-    // exposure notification: today's positive app holders (internal rows, caller ids), per-day counts
+    // exposure notification: today's positive app holders (internal rows, caller ids;
+    // batched: [n][ceil(B/32)] words by rows), per-day counts
     uint32_t *den_bits = nullptr, *den_bits_orig = nullptr;
     int32_t *den_pos = nullptr;
     uint32_t *den_ring = nullptr;  // [den_window][slots][n_app] contact records of the app holders
@@ -391,7 +392,6 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
     if (p->vax_strategy > 3 || p->elderly_bin > 9)
         return fail(ctx, DEABM_EINVAL, "vax_strategy must be 0..3 and elderly_bin 0..9");
     if (p->den_on) {
-        if (n_rep != 1) return fail(ctx, DEABM_EINVAL, "exposure notification needs a plain (one replicate) context");
         if (!p->test_on) return fail(ctx, DEABM_EINVAL, "exposure notification needs test_on");
         if (p->den_window < 1 || p->den_window > 64) return fail(ctx, DEABM_EINVAL, "den_window must be 1..64");
         if (!prob_ok(p->den_adoption) || !prob_ok(p->den_compliance))
@@ -688,15 +688,19 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->C.hist, days * n_rep * DEABM_N_STAGE))) return r;
             if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
         if ((r = dalloc(ctx, &ctx->C.gath, days))) return r;
-            if ((r = dalloc(ctx, &ctx->C.den, days))) return r;
-            CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
+            if ((r = dalloc(ctx, &ctx->C.den, days * n_rep))) return r;
+            CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days * n_rep, s));
             if (p->den_on) {
-                if ((r = dalloc(ctx, &ctx->den_bits, ((size_t)n + 31) / 32))) return r;
-                if (ctx->relabel && (r = dalloc(ctx, &ctx->den_bits_orig, ((size_t)n + 31) / 32))) return r;
                 if ((r = dalloc(ctx, &ctx->den_pos, days))) return r;
                 CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * days, s));
-                if ((r = dalloc(ctx, &ctx->app_rows, n))) return r;
-                if ((r = dalloc(ctx, &ctx->app_rank, n))) return r;
+                if (n_rep == 1) {
+                    if ((r = dalloc(ctx, &ctx->den_bits, ((size_t)n + 31) / 32))) return r;
+                    if (ctx->relabel && (r = dalloc(ctx, &ctx->den_bits_orig, ((size_t)n + 31) / 32))) return r;
+                    if ((r = dalloc(ctx, &ctx->app_rows, n))) return r;
+                    if ((r = dalloc(ctx, &ctx->app_rank, n))) return r;
+                } else {  // positives of the day: one word per (row, 32 columns)
+                    if ((r = dalloc(ctx, &ctx->den_bits, (size_t)n * ((n_rep + 31) / 32)))) return r;
+                }
             }
             CU(ctx, cudaMemsetAsync(ctx->C.new_inf, 0, sizeof(int32_t) * days * n_rep, s));
             CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * n_rep * DEABM_N_STAGE, s));
@@ -889,7 +893,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if (K.den_on) {  // app holders, part of the initial state kept for deabm_reset
                 CU(ctx, launch_den_apps(K, ctx->S, s));
                 CU(ctx, cudaMemcpyAsync(ctx->S0.flags, ctx->S.flags, nb, cudaMemcpyDeviceToDevice, s));
-                if ((r = den_list_apps(ctx, K))) return r;
+                if (n_rep == 1 && (r = den_list_apps(ctx, K))) return r;
             }
 
             if (a->n_seed) {
@@ -977,7 +981,10 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         if (kp.wsg_on) CU(ctx, launch_wsg_build(kp, ctx->day, ctx->wsg, ctx->stream));
         CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
                             ctx->stream));
-        if (kp.den_on) CU(ctx, launch_den(kp, ctx->day, ctx->S, ctx->C, ctx->stream));
+        if (kp.den_on) {
+            if (ctx->n_rep == 1) CU(ctx, launch_den(kp, ctx->day, ctx->S, ctx->C, ctx->stream));
+            else CU(ctx, launch_den_batch(kp, ctx->day, ctx->row_of, ctx->S, ctx->C, ctx->stream));
+        }
         ctx->cur ^= 1;
         ctx->day += 1;
     }
@@ -1604,8 +1611,10 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     if (ctx->kp.den_on) {  // the app draw follows the (possibly new) seed
         CU(ctx, launch_den_apps(ctx->kp, ctx->S, s));
         CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * ctx->max_steps, s));
-        int r = den_list_apps(ctx, ctx->kp);
-        if (r) return r;
+        if (ctx->n_rep == 1) {
+            int r = den_list_apps(ctx, ctx->kp);
+            if (r) return r;
+        }
     }
     if (ctx->n_seed) CU(ctx, launch_seed(ctx->kp, ctx->seed_ids, ctx->n_seed, ctx->S, s));
     ctx->cur = 0;
@@ -1616,7 +1625,7 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
     CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
     CU(ctx, cudaMemsetAsync(ctx->C.gath, 0, sizeof(unsigned long long) * days, s));
-    CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days * ctx->n_rep, s));
     ctx->day = 0;
     return DEABM_OK;
 }
@@ -1630,7 +1639,8 @@ extern "C" int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *n
         std::memset(notified, 0, sizeof(int32_t) * day_count);
         return DEABM_OK;
     }
-    CU(ctx, cudaMemcpyAsync(notified, ctx->C.den, sizeof(int32_t) * day_count, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(notified, ctx->C.den, sizeof(int32_t) * day_count * ctx->n_rep, cudaMemcpyDeviceToHost,
+                            ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     return DEABM_OK;
 }
@@ -1702,11 +1712,12 @@ extern "C" int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t 
                             sizeof(int32_t) * rest * B * DEABM_N_STAGE, s));
     CU(ctx, cudaMemsetAsync(ctx->C.msgs + day, 0, sizeof(unsigned long long) * rest, s));
     CU(ctx, cudaMemsetAsync(ctx->C.gath + day, 0, sizeof(unsigned long long) * rest, s));
-    CU(ctx, cudaMemsetAsync(ctx->C.den + day, 0, sizeof(int32_t) * rest, s));
+    CU(ctx, cudaMemsetAsync(ctx->C.den + (size_t)day * B, 0, sizeof(int32_t) * rest * B, s));
     if (ctx->kp.den_on) {
         CU(ctx, cudaMemsetAsync(ctx->den_pos + day, 0, sizeof(int32_t) * rest, s));
         const uint32_t W = ctx->kp.den_window;
-        CU(ctx, launch_den_records(ctx->kp, day + 1u > W ? day + 1u - W : 0u, day, s));
+        // (batched contexts keep no records: their pass redraws the contacts)
+        if (ctx->n_rep == 1) CU(ctx, launch_den_records(ctx->kp, day + 1u > W ? day + 1u - W : 0u, day, s));
     }
     CU(ctx, cudaStreamSynchronize(s));  // host arrays and device scratch end here
     return DEABM_OK;

@@ -8,7 +8,8 @@
 // drawing them (a ring of den_window records per app holder, stored as word
 // planes) -- and looks each
 // source up in the day's bit map of positive app holders.  One thread per app
-// holder, app holders listed in row order.
+// holder, app holders listed in row order.  Batched contexts run the same
+// notification in every replicate column at once (den_batch_* below).
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -125,15 +126,68 @@ __global__ void __launch_bounds__(256, 8) den_kernel(const KParams P, uint32_t d
     if (threadIdx.x == 0 && s_cnt) atomicAdd(C.den + day, s_cnt);
 }
 
-// app holders, drawn once: word x of (seed, caller id, day word 0xFFFFFFFD, stream 6)
+// app holders, drawn once per replicate column: word x of (the column's seed,
+// caller id, day word 0xFFFFFFFD, stream 6); one thread per (agent, column)
 __global__ void den_apps_kernel(const KParams P, StateRef S)
 {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.n) return;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)P.n * P.n_rep) return;
+    const uint32_t j = (uint32_t)(i / P.n_rep), b = (uint32_t)(i % P.n_rep);
     const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
-    const uint32_t w = draw(seed_key(P.rep[0].seed), jo, 0xFFFFFFFDu, kStreamDen).x;
-    const uint32_t fl = S.flags[j];
-    S.flags[j] = (uint8_t)((uint64_t)w < P.thr_adopt ? (fl | DEABM_FL_APP) : (fl & ~DEABM_FL_APP));
+    const uint32_t w = draw(seed_key(P.rep[b].seed), jo, 0xFFFFFFFDu, kStreamDen).x;
+    const uint32_t fl = S.flags[i];
+    S.flags[i] = (uint8_t)((uint64_t)w < P.thr_adopt ? (fl | DEABM_FL_APP) : (fl & ~DEABM_FL_APP));
+}
+
+// The in-contacts agent j (internal row; jo its caller id) received on day d
+// through the day's generated networks, redrawn from Philox exactly as the day
+// kernel drew them: f(0, e, caller id) for random contact e, then f(1, e, row) for
+// daily occupation contact e.  Returns the counts, k_rand | k_occ << 8.
+template <class F>
+__device__ uint32_t den_day_contacts(const KParams &P, uint32_t j, uint32_t jo, uint32_t d, F f)
+{
+    const uint2 nk = seed_key(P.net_seed);
+    uint32_t k_rand = 0, k_occ = 0;
+    if (P.rand_on) {
+        uint4 w = draw(nk, jo, d, kStreamRnet, 0u);
+        while (k_rand < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k_rand])) ++k_rand;
+        const uint64_t nm1 = (uint64_t)(P.n - 1u);
+        for (uint32_t e = 0; e < k_rand; ++e) {
+            const uint32_t idx = e + 1u;
+            if ((idx & 3u) == 0u) w = draw(nk, jo, d, kStreamRnet, idx >> 2);
+            const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+            uint32_t c = (uint32_t)(((uint64_t)x * nm1) >> 32);
+            c += (c >= jo) ? 1u : 0u;
+            f(0u, e, c);
+        }
+    }
+    if (P.n_occ) {
+        const uint32_t g = __ldg(P.occ_gid + j);
+        const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
+        k_occ = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
+        const uint32_t own = j - beg;
+        for (uint32_t e = 0; e < k_occ; ++e) {
+            uint32_t r;
+            if (P.occ_lattice) {  // as occ_ws_sum
+                const uint4 w = draw(nk, jo, d, kStreamWs, e >> 1);
+                const uint32_t m = (e >> 1) + 1u, hop = m < size ? m : m % size;
+                const uint32_t coin = (e & 1u) ? w.z : w.x, word = (e & 1u) ? w.w : w.y;
+                const uint32_t off = (e & 1u) == 0u ? hop : (hop == 0u ? 0u : size - hop);
+                if (off == 0u || (uint64_t)coin < P.thr_rewire) {
+                    r = occ_place(word, size - 1u, own);
+                } else {
+                    r = own + off;
+                    r = r >= size ? r - size : r;
+                }
+            } else {  // as occ_sum
+                const uint4 w = draw(nk, jo, d, kStreamOcc, e >> 2);
+                const uint32_t x = (e & 3u) == 0u ? w.x : (e & 3u) == 1u ? w.y : (e & 3u) == 2u ? w.z : w.w;
+                r = occ_place(x, size - 1u, own);
+            }
+            f(1u, e, beg + r);
+        }
+    }
+    return k_rand | (k_occ << 8);
 }
 
 // One app holder's contact record of day d redrawn from Philox: the random and
@@ -146,51 +200,103 @@ __global__ void den_record_kernel(const KParams P, uint32_t d0, uint32_t d1)
     const uint32_t j = __ldg(P.app_rows + a);
     const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
     const size_t plane = P.n_app;
-    const uint2 nk = seed_key(P.net_seed);
     for (uint32_t d = d0; d < d1; ++d) {
         uint32_t *rec = P.den_ring + (size_t)(d % P.den_window) * P.den_slots * plane + a;
-        uint32_t k_rand = 0, k_occ = 0;
-        if (P.rand_on) {
-            uint4 w = draw(nk, jo, d, kStreamRnet, 0u);
-            while (k_rand < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k_rand])) ++k_rand;
-            const uint64_t nm1 = (uint64_t)(P.n - 1u);
-            for (uint32_t e = 0; e < k_rand; ++e) {
-                const uint32_t idx = e + 1u;
-                if ((idx & 3u) == 0u) w = draw(nk, jo, d, kStreamRnet, idx >> 2);
-                const uint32_t x = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
-                uint32_t c = (uint32_t)(((uint64_t)x * nm1) >> 32);
-                c += (c >= jo) ? 1u : 0u;
-                rec[(size_t)(1u + e) * plane] = c;
-            }
-        }
-        if (P.n_occ) {
-            const uint32_t g = __ldg(P.occ_gid + j);
-            const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
-            k_occ = size > 1u ? (uint32_t)__ldg(P.occ_k + g) : 0u;
-            const uint32_t own = j - beg;
-            for (uint32_t e = 0; e < k_occ; ++e) {
-                uint32_t r;
-                if (P.occ_lattice) {  // as occ_ws_sum
-                    const uint4 w = draw(nk, jo, d, kStreamWs, e >> 1);
-                    const uint32_t m = (e >> 1) + 1u, hop = m < size ? m : m % size;
-                    const uint32_t coin = (e & 1u) ? w.z : w.x, word = (e & 1u) ? w.w : w.y;
-                    const uint32_t off = (e & 1u) == 0u ? hop : (hop == 0u ? 0u : size - hop);
-                    if (off == 0u || (uint64_t)coin < P.thr_rewire) {
-                        r = occ_place(word, size - 1u, own);
-                    } else {
-                        r = own + off;
-                        r = r >= size ? r - size : r;
-                    }
-                } else {  // as occ_sum
-                    const uint4 w = draw(nk, jo, d, kStreamOcc, e >> 2);
-                    const uint32_t x = (e & 3u) == 0u ? w.x : (e & 3u) == 1u ? w.y : (e & 3u) == 2u ? w.z : w.w;
-                    r = occ_place(x, size - 1u, own);
-                }
-                rec[(size_t)(kDenOccAt + e) * plane] = beg + r;
-            }
-        }
-        rec[0] = k_rand | (k_occ << 8);
+        rec[0] = den_day_contacts(P, j, jo, d, [&](uint32_t kind, uint32_t e, uint32_t v) {
+            rec[(size_t)((kind ? kDenOccAt : 1u) + e) * plane] = v;
+        });
     }
+}
+
+// ---- batched contexts (state [N][B], column b = replicate b)
+// The day kernel leaves bit b % 32 of den_bits[row * W + b / 32] set (W = ceil(B /
+// 32)) when the row's agent is a positive app holder of column b today.  The
+// notification pass is one launch per 256 columns: eight lanes per row OR, word
+// by word, the bits of all the row's in-contacts of the last den_window days --
+// its stored rows (the same every day) and the random and daily occupation
+// contacts of each day, redrawn from Philox (the contacts are the same in every
+// column, so no record is kept) -- and then, for each column whose bit is set,
+// check that column's own state (app holder, out of quarantine, not in hospital,
+// ICU or dead), count the notification and draw the compliance word of the
+// column's seed.  Each column reproduces the plain pass of its own run.  Bit
+// lookups are whole words (32 columns at once), so a contact costs the same for
+// any B <= 256.
+constexpr uint32_t kDenHitWords = 8;  // words of columns one launch covers (256 columns)
+
+// Lane g of a row's eight takes the stored in-edges g, g + 8, ... of each row and
+// the days d0 + g, d0 + g + 8, ... of the window; the partial ORs are combined by
+// shuffles and lane g then works through the columns of word w0 + g.
+__global__ void __launch_bounds__(128) den_batch_kernel(const KParams P, uint32_t day, const uint32_t *row_of,
+                                                         uint32_t W, uint32_t w0, StateRef S, Counters C)
+{
+    __shared__ int s_cnt[kDenHitWords * 32];
+    for (uint32_t q = threadIdx.x; q < kDenHitWords * 32u; q += blockDim.x) s_cnt[q] = 0;
+    __syncthreads();
+    if (__ldg(P.den_pos + day) == 0) return;  // uniform: nobody tested positive today
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, j = t >> 3, g = t & 7u;
+    const uint32_t nw = W - w0 < kDenHitWords ? W - w0 : kDenHitWords;
+    uint32_t acc[kDenHitWords];
+#pragma unroll
+    for (uint32_t u = 0; u < kDenHitWords; ++u) acc[u] = 0u;
+    auto add = [&](uint32_t row) {
+        const uint32_t *src = P.den_bits + (size_t)row * W + w0;
+#pragma unroll
+        for (uint32_t u = 0; u < kDenHitWords; ++u)
+            if (u < nw) acc[u] |= __ldg(src + u);
+    };
+    const uint32_t jo = j < P.n ? (P.orig_id ? __ldg(P.orig_id + j) : j) : 0u;
+    if (j < P.n) {
+        for (uint32_t net = 0; net < P.n_nets; ++net) {
+            const uint32_t e1 = __ldg(P.row_ptr[net] + j + 1);
+            for (uint32_t e = __ldg(P.row_ptr[net] + j) + g; e < e1; e += 8u) add(__ldg(P.col[net] + e));
+        }
+        const uint32_t d0 = day + 1u > P.den_window ? day + 1u - P.den_window : 0u;
+        for (uint32_t d = d0 + g; d <= day; d += 8u)
+            (void)den_day_contacts(P, j, jo, d, [&](uint32_t kind, uint32_t, uint32_t v) {
+                add(kind || !row_of ? v : __ldg(row_of + v));
+            });
+    }
+    // (a row's eight lanes are an aligned eighth of one warp; rows past n add nothing)
+#pragma unroll
+    for (uint32_t u = 0; u < kDenHitWords; ++u) {
+        acc[u] |= __shfl_xor_sync(0xFFFFFFFFu, acc[u], 1);
+        acc[u] |= __shfl_xor_sync(0xFFFFFFFFu, acc[u], 2);
+        acc[u] |= __shfl_xor_sync(0xFFFFFFFFu, acc[u], 4);
+    }
+    uint32_t hit = 0;
+#pragma unroll
+    for (uint32_t u = 0; u < kDenHitWords; ++u)
+        if (u == g) hit = acc[u];
+    if (j < P.n && g < nw) {
+        while (hit) {
+            const uint32_t bit = __ffs(hit) - 1u;
+            hit &= hit - 1u;
+            const uint32_t b = (w0 + g) * 32u + bit;
+            if (b >= P.n_rep) break;
+            const size_t i = (size_t)j * P.n_rep + b;
+            const uint32_t fl = S.flags[i];
+            const int st = S.stage[i];
+            if ((fl & DEABM_FL_APP) && (S.qt[i] & 0x0Fu) == 0u && st != DEABM_HOSP && st != DEABM_ICU &&
+                st != DEABM_DEAD) {
+                atomicAdd(&s_cnt[g * 32u + bit], 1);
+                const uint32_t w = draw(seed_key(P.rep[b].seed), jo, day, kStreamDen).x;
+                if ((uint64_t)w < P.thr_comp) S.flags[i] = (uint8_t)(fl | DEABM_FL_DEN);
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < kDenHitWords * 32u; q += blockDim.x)
+        if (s_cnt[q]) atomicAdd(C.den + (size_t)day * P.n_rep + w0 * 32u + q, s_cnt[q]);
+}
+
+cudaError_t launch_den_batch(const KParams &P, uint32_t day, const uint32_t *row_of, const StateRef &S,
+                             const Counters &C, cudaStream_t stream)
+{
+    const uint32_t W = (P.n_rep + 31u) / 32u;
+    const unsigned blocks = (unsigned)(((size_t)P.n * 8u + 127u) / 128u);
+    for (uint32_t w0 = 0; w0 < W; w0 += kDenHitWords)
+        den_batch_kernel<<<blocks, 128, 0, stream>>>(P, day, row_of, W, w0, S, C);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_den_records(const KParams &P, uint32_t d0, uint32_t d1, cudaStream_t stream)
@@ -202,7 +308,8 @@ cudaError_t launch_den_records(const KParams &P, uint32_t d0, uint32_t d1, cudaS
 
 cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t stream)
 {
-    den_apps_kernel<<<(P.n + 255u) / 256u, 256, 0, stream>>>(P, S);
+    const size_t m = (size_t)P.n * P.n_rep;
+    den_apps_kernel<<<(unsigned)((m + 255u) / 256u), 256, 0, stream>>>(P, S);
     return cudaGetLastError();
 }
 

@@ -40,10 +40,15 @@ size_t dose1_scratch_words(uint32_t n);
 cudaError_t launch_seed(const KParams &P, const uint32_t *ids, uint32_t n_ids, const StateRef &S, cudaStream_t stream);
 // set-up: emitted infectiousness of the current state (inf_rand: copy by caller id, or nullptr)
 cudaError_t launch_emit(const KParams &P, const StateRef &S, float *inf, float *inf_rand, cudaStream_t stream);
-// exposure notification (plain contexts): app holders drawn at set-up, and the
-// notification pass that follows each day's update
+// exposure notification: app holders drawn at set-up (per replicate column), and
+// the notification pass of a plain context that follows each day's update
 cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t stream);
 cudaError_t launch_den(const KParams &P, uint32_t day, const StateRef &S, const Counters &C, cudaStream_t stream);
+// the notification pass of a batched context ([N][B] state; positives in P.den_bits
+// as [N][ceil(B/32)] words; row_of: caller id -> row, or nullptr when not
+// relabelled; notified counts in C.den [day][B])
+cudaError_t launch_den_batch(const KParams &P, uint32_t day, const uint32_t *row_of, const StateRef &S,
+                             const Counters &C, cudaStream_t stream);
 // internal numbering: min-label rounds over a CSR (at most `rounds`, even,
 // fewer once the labels stop moving; result in label, tmp is scratch of n words,
 // changed one device word; synchronises the stream after each pair of rounds);

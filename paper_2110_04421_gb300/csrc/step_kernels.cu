@@ -52,8 +52,9 @@ __device__ __forceinline__ bool infection_decision(float lam_dt, float u, float 
 // random draw is keyed by the caller's agent id jo, so relabelling the agents
 // inside the library changes no result.
 // DEN: exposure notification on (plain contexts): an app holder records the day's
-// contacts, a positive app holder is marked for the notification pass.
-template <bool OCC = true, bool DEN = false, bool ROWMAP = false, bool WSG = false, bool RK = false>
+// contacts, a positive app holder is marked for the notification pass.  POS:
+// only the mark (*notify), for the batched notification pass.
+template <bool OCC = true, bool DEN = false, bool ROWMAP = false, bool WSG = false, bool RK = false, bool POS = false>
 __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint32_t day, const InfBuffers &I,
                                           const StateRef &S, uint32_t j, uint32_t stride, uint32_t b, float *lam_out,
                                           float *p_out, int *new_stage, bool *infected, uint32_t *k_out,
@@ -142,10 +143,10 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     }
 #endif
     advance<RK>(P, rp, key, jo, day, age, d1, inf_now, a, inf_y, (size_t)jo * stride + b);
-    if (DEN) {  // a positive app holder notifies its contacts after the day
+    if (DEN || POS) {  // a positive app holder notifies its contacts after the day
         const bool v = a.pos_result && (a.fl & DEABM_FL_APP);
         *notify = v;
-        if (v && P.den_bits_orig) atomicOr(P.den_bits_orig + (jo >> 5), 1u << (jo & 31u));
+        if (DEN && v && P.den_bits_orig) atomicOr(P.den_bits_orig + (jo >> 5), 1u << (jo & 31u));
     }
     S.stage[i] = (int8_t)a.st;
     S.timer[i] = (int16_t)a.tm;
@@ -270,7 +271,9 @@ __global__ void __launch_bounds__(DEABM_PLAIN_BLOCK, OCC ? DEABM_OCC_MINB : DEAB
 // Batched panel: block (32 x 8) covers 8 agents x 32 replicates; lane = replicate.
 // The 32 lanes of a warp read the same CSR entries (one broadcast load) and
 // gather one contiguous 128 B run of the [N][B] infectiousness panel per edge.
-template <bool KEEP, bool WSG>
+// DEN: the warp's positive app holders go to word blockIdx.y of the row's
+// ceil(B/32) words in den_bits (one ballot; every word is written every day).
+template <bool KEEP, bool WSG, bool DEN = false>
 __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32_t day, const InfBuffers I, StateRef S,
                                                          Counters C, float *lam_out, float *p_out)
 {
@@ -285,15 +288,22 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
     __syncthreads();
     const bool active = (j < P.n) && (b < P.n_rep);
     int st = 0;
-    bool infected = false;
+    bool infected = false, notify = false;
     uint32_t k = 0;
     if (active) {
         const Rep &rp = P.rep[b];
         uint32_t kg;
-        agent_day<true, false, true, WSG>(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out, &st,
-                                          &infected, &k, &kg);
+        agent_day<true, false, true, WSG, false, DEN>(P, rp, day, I, S, j, P.n_rep, b, KEEP ? lam_out : nullptr, p_out,
+                                                      &st, &infected, &k, &kg, &notify);
         atomicAdd(&s_cnt[st][lane], 1);
         if (infected) atomicAdd(&s_cnt[DEABM_N_STAGE][lane], 1);
+    }
+    if (DEN) {
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, notify);
+        if (lane == 0 && j < P.n) {
+            P.den_bits[(size_t)j * gridDim.y + blockIdx.y] = bits;
+            if (bits) atomicAdd(P.den_pos + day, __popc(bits));
+        }
     }
     // messages are counted once per agent row (lane 0 of the first replicate panel)
     if (lane == 0 && blockIdx.y == 0 && j < P.n && k) atomicAdd(&s_msgs, (unsigned long long)k);
@@ -409,7 +419,9 @@ __device__ __forceinline__ void add4(float4 &h, const float4 v)
     h.w = __fadd_rn(h.w, v.w);
 }
 
-template <bool KEEP>
+// DEN: the positive app holders of the warp's 128 replicates go to four words of
+// the row's ceil(B/32) in den_bits (every word is written every day).
+template <bool KEEP, bool DEN = false>
 #ifndef DEABM_B4_MINB
 #define DEABM_B4_MINB 6  // resident blocks per SM asked of the four-replicate kernel: 40 registers with
                          // some spilled (swept at N = 1e5, B = 256: 1 block 105 registers, 38 % slower;
@@ -427,7 +439,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
     for (uint32_t q = tid; q < (DEABM_N_STAGE + 1) * 32u * kRepPerThread; q += 256u) (&s_cnt[0][0])[q] = 0;
     if (tid == 0) s_msgs = 0ull;
     __syncthreads();
-    uint32_t k = 0;
+    uint32_t k = 0, pos4 = 0;  // pos4 bit v: replicate b0 + v is a positive app holder today (DEN)
     if (j < P.n && b0 < B) {
         const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
         const int age = __ldg(P.age + j);
@@ -571,6 +583,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
                 inf_now = (a.st == DEABM_S) && hit;
             }
             advance(P, rp, key, jo, day, age, d1, inf_now, a, inf_y, (size_t)jo * B + b0 + v);
+            if (DEN && a.pos_result && (a.fl & DEABM_FL_APP)) pos4 |= 1u << v;
             st_out[v] = (int8_t)a.st;
             tm_out[v] = (int16_t)a.tm;
             ti_out[v] = (int16_t)a.ti;
@@ -592,6 +605,17 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
         const float4 iv = make_float4(inf_out[0], inf_out[1], inf_out[2], inf_out[3]);
         *(float4 *)(I.next + i0) = iv;
         if (I.rand_next) *(float4 *)(I.rand_next + (size_t)jo * B + b0) = iv;
+    }
+    if (DEN) {  // lanes 8q .. 8q + 7 hold the 32 replicates of word 4 blockIdx.y + q
+        uint32_t v = pos4 << ((lane & 7u) * 4u);
+        v |= __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+        v |= __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+        v |= __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+        const uint32_t W = (B + 31u) / 32u, w = blockIdx.y * 4u + (lane >> 3);
+        if ((lane & 7u) == 0u && j < P.n && w < W) {
+            P.den_bits[(size_t)j * W + w] = v;
+            if (v) atomicAdd(P.den_pos + day, __popc(v));
+        }
     }
     if (lane == 0 && blockIdx.y == 0 && j < P.n && k) atomicAdd(&s_msgs, (unsigned long long)k);
     __syncthreads();
@@ -635,14 +659,22 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
         // (priority strategies and the Watts-Strogatz random network: the general panel)
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 32u * kRepPerThread - 1u) / (32u * kRepPerThread));
         const dim3 block(32, 8);
-        if (lam_out) step_batch4_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
-        else step_batch4_kernel<false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        if (P.den_on) {
+            if (lam_out) step_batch4_kernel<true, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_batch4_kernel<false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        } else {
+            if (lam_out) step_batch4_kernel<true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_batch4_kernel<false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        }
     } else {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
         const dim3 block(32, 8);
         if (P.wsg_on) {
             if (lam_out) step_batch_kernel<true, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
             else step_batch_kernel<false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        } else if (P.den_on) {  // (the Watts-Strogatz random network excludes exposure notification)
+            if (lam_out) step_batch_kernel<true, false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_batch_kernel<false, false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
         } else {
             if (lam_out) step_batch_kernel<true, false><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
             else step_batch_kernel<false, false><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);

@@ -580,9 +580,10 @@ class Simulation:
         _check(lib().deabm_restore(self.ctx, *(_p(a) for a in arrs), _p(d1), _p(d2), int(ckpt["day"])), self.ctx)
 
     def notified(self, days: int | None = None) -> np.ndarray:
-        """Agents notified by exposure notification at the end of each day."""
+        """Agents notified by exposure notification at the end of each day: [days]
+        in a plain context, [days, n_rep] in a batched one."""
         days = self.day if days is None else days
-        out = np.zeros(days, np.int32)
+        out = np.zeros((days, self.n_rep) if self.n_rep > 1 else days, np.int32)
         _check(lib().deabm_get_notified(self.ctx, days, _p(out)), self.ctx)
         return out
 

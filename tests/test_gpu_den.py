@@ -116,13 +116,54 @@ def test_contact_ring_grows_when_a_reset_draws_more_app_holders():
     g.close()
 
 
+def column_params(base, rp, seeds, c):
+    return dict(base, R=float(rp[c, 0]), B_net=[float(rp[c, 1]), float(rp[c, 2])], B_rand=float(rp[c, 3]),
+                S_age=[float(x) for x in rp[c, 4:13]], dose2_delay=int(rp[c, 13]), seed=int(seeds[c]))
+
+
+@pytest.mark.parametrize("B,daily_occ,locality_order",
+                         [(4, False, True), (37, False, False), (6, True, True), (8, True, False)])
+def test_batched_columns_match_oracle_runs(B, daily_occ, locality_order):
+    """Exposure notification in a batched context: each replicate column draws its
+    own app holders and compliance words with its own seed, the columns share the
+    day's contacts, and the notification pass runs for all columns at once.  Every
+    column equals the oracle's plain run with that column's parameters and seed:
+    incidence, stage histogram, final state (app, notification and test flags
+    included) and the per-day notified counts.  B = 4 and 8 run the four-replicate
+    kernel, B = 6 and 37 the general panel; B = 37 spans two words of columns with a
+    ragged last word."""
+    import oracle
+    from paper_2110_04421_gb300.deabm import Simulation
+    T = 45
+    pop = W.population_daily_occupation(4_000, 23, 30) if daily_occ else W.population(4_001, 21, 30)
+    base = den_params(R=4.5, q_dropout=0.05)
+    if daily_occ:
+        base = den_params(R=4.5, den_adoption=0.6, vax_on=1, vax_start=15, vax_rate=0.01)
+    rp, seeds = W.batch_params(B, 9)
+    g = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds, max_steps=T,
+                   locality_order=locality_order)
+    ni, h = g.run(T)
+    st = g.state()
+    den = g.notified()
+    g.close()
+    assert den.shape == (T, B)
+    total = 0
+    for c in range(B):
+        o = oracle.Sim(pop, column_params(base, rp, seeds, c), pop["age"], pop["seed_ids"])
+        o_ni, o_h, _ = o.run(T)
+        assert np.array_equal(ni[:, c], o_ni), c
+        assert np.array_equal(h[:, c], o_h), c
+        for k in ("stage", "timer", "flags", "qt"):
+            assert np.array_equal(st[k][:, c], getattr(o.state, k)), (c, k)
+        assert den[:, c].tolist() == o.den_notified, c
+        total += sum(o.den_notified)
+    assert total > 50 * B  # notifications happened in every column on average
+
+
 def test_other_contexts_reject_notification():
-    from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation, Relaxed, Simulation
+    from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation, Relaxed
     pop = W.population(500, 1, 5)
     p = den_params()
-    rp, seeds = W.batch_params(4, 0)
-    with pytest.raises(DeabmError):
-        Simulation(pop, p, pop["age"], pop["seed_ids"], n_rep=4, rep_params=rp, rep_seeds=seeds)
     with pytest.raises(DeabmError):
         RaggedSimulation([pop], [p], max_steps=5)
     with pytest.raises(DeabmError):
