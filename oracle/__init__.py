@@ -108,6 +108,8 @@ class _RxModel(C.Structure):
         ("inf_shape", C.c_double * N_CLASS), ("inf_scale", C.c_double * N_CLASS), ("inf_len", C.c_uint32),
         ("p_asym", C.c_double * N_AGE), ("p_sev", C.c_double * N_AGE),
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
+        ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
+        ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_double),
     ]
 
 
@@ -422,6 +424,15 @@ class Relaxed:
             m.p_asym[a] = params["p_asym"][a]
             m.p_sev[a] = params["p_sev"][a]
         m.seed, m.net_seed = params["seed"], params["net_seed"]
+        if graph.get("occ_group") is not None:  # daily occupation networks
+            og = np.ascontiguousarray(graph["occ_group"], dtype=np.uint32)
+            ok = np.ascontiguousarray(graph["occ_k"], dtype=np.uint8)
+            self._keep += [og, ok]
+            m.n_occ = ok.size
+            m.occ_group = og.ctypes.data
+            m.occ_k = ok.ctypes.data
+            m.occ_lattice = int(graph.get("occ_lattice", 0))
+            m.occ_rewire = float(np.float32(graph.get("occ_rewire", 0.0)))
         self.m = m
         self.age = np.ascontiguousarray(age, dtype=np.uint8)
         self.seeds = np.ascontiguousarray(seed_ids if seed_ids is not None else [], dtype=np.uint32)

@@ -9,7 +9,11 @@
  *   - x_j(t) in [0,1] is the infected mass of agent j on day t and s_j(t) its
  *     susceptible mass; the initial cases have x(-1) = 1, s(0) = 0;
  *   - inf_i(t) = A_{c_i} * sum_{d=1}^{L-1} infT_{c_i}[d] * x_i(t-d)     (Eq. 1 by age of infection)
- *   - lambda_j(t) = R/I * S_{a_j} * (sum_n B_n sum_{i->j} inf_i(t) + B_r sum_{rand} inf_i(t))
+ *   - lambda_j(t) = R/I * S_{a_j} * (sum_n B_n sum_{i->j} inf_i(t) + B_o sum_{occ} inf_i(t)
+ *                                    + B_r sum_{rand} inf_i(t)),
+ *     the occupation term present with daily occupation networks (Sec. 3,
+ *     Interaction Networks: fixed membership, in-contacts drawn anew every day,
+ *     as in the plain model), B_o the weight of network n_nets;
  *   - the Bernoulli(p) draw with p = 1 - exp(-lambda) (Eq. 2) is relaxed with a
  *     logistic (binary Gumbel-softmax) sample:
  *       g_j(t) = sigmoid((logit p_j(t) + l_j(t)) / tau),  logit p = log(expm1(lambda)),
@@ -45,6 +49,13 @@ typedef struct {
     uint32_t inf_len;
     double p_asym[RX_N_AGE], p_sev[RX_N_AGE];
     uint64_t seed, net_seed;
+    /* daily occupation networks (n_occ = 0: none): occupation of each agent, daily
+     * in-contacts per member, Watts-Strogatz ring lattice and its rewiring */
+    uint32_t n_occ;
+    const uint32_t *occ_group;
+    const uint8_t *occ_k;
+    uint32_t occ_lattice;
+    double occ_rewire;
 } rx_model;
 
 static void draw4(uint64_t seed, uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t out[4])
@@ -82,6 +93,65 @@ static uint32_t contacts_of(const rx_model *m, const uint64_t *thr, uint32_t j, 
     return k;
 }
 
+/* Members of every occupation in ascending agent id (start[g] .. start[g+1]) and
+ * each agent's place among them. */
+typedef struct {
+    uint32_t *start, *members, *pos;
+} rx_occ;
+
+static void rx_occ_build(const rx_model *m, rx_occ *o)
+{
+    const uint32_t n = m->n, G = m->n_occ;
+    o->start = (uint32_t *)calloc(G + 1u, sizeof(uint32_t));
+    o->members = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    o->pos = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *fill = (uint32_t *)calloc(G + 1u, sizeof(uint32_t));
+    for (uint32_t j = 0; j < n; ++j) o->start[m->occ_group[j] + 1u]++;
+    for (uint32_t g = 0; g < G; ++g) o->start[g + 1u] += o->start[g];
+    for (uint32_t j = 0; j < n; ++j) {
+        const uint32_t g = m->occ_group[j];
+        o->pos[j] = fill[g];
+        o->members[o->start[g] + fill[g]++] = j;
+    }
+    free(fill);
+}
+
+/* The day's occupation in-contacts of agent j on day t (as the plain model draws
+ * them): occ_k[g] of them, none for a lone member.  Uniform: contact e is the
+ * member at place floor(w (size-1) / 2^32) among the others, w = word e % 4 of
+ * block e / 4 of stream 4.  Ring lattice: in-edge e comes from place q + (e/2+1)
+ * (e even) or q - (e/2+1) (e odd) mod size, unless its coin (word 2(e%2) of block
+ * e/2 of stream 9) is below the rewiring threshold or the offset is a multiple of
+ * the size, when word 2(e%2)+1 picks a uniform other member. */
+static uint32_t rx_occ_contacts(const rx_model *m, const rx_occ *o, uint32_t j, uint32_t t, uint32_t *out)
+{
+    const uint32_t g = m->occ_group[j];
+    const uint32_t beg = o->start[g], size = o->start[g + 1u] - beg;
+    if (size < 2u) return 0;
+    const uint32_t k = m->occ_k[g], q = o->pos[j];
+    for (uint32_t e = 0; e < k; ++e) {
+        uint32_t blk[4], r;
+        if (m->occ_lattice) {
+            draw4(m->net_seed, j, t, 9u, e / 2u, blk);
+            const uint32_t coin = blk[2u * (e % 2u)], word = blk[2u * (e % 2u) + 1u];
+            const uint32_t hop = (e / 2u + 1u) % size;
+            const uint32_t off = (e % 2u == 0u) ? hop : (size - hop) % size;
+            if (off == 0u || (uint64_t)coin < or_threshold(m->occ_rewire)) {
+                r = (uint32_t)(((uint64_t)word * (uint64_t)(size - 1u)) >> 32);
+                if (r >= q) r += 1u;
+            } else {
+                r = (q + off) % size;
+            }
+        } else {
+            draw4(m->net_seed, j, t, 4u, e / 4u, blk);
+            r = (uint32_t)(((uint64_t)blk[e % 4u] * (uint64_t)(size - 1u)) >> 32);
+            if (r >= q) r += 1u;
+        }
+        out[e] = o->members[beg + r];
+    }
+    return k;
+}
+
 double rx_noise(uint64_t seed, uint32_t j, uint32_t t)
 {
     uint32_t w[4];
@@ -107,6 +177,13 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
 {
     const uint32_t n = m->n, L = m->inf_len;
     if (L < 2 || L > RX_MAX_L || m->n_nets > RX_MAX_NETS || m->tau <= 0.0) return -1;
+    if (m->n_occ) {
+        if (m->n_nets >= RX_MAX_NETS || !m->occ_group || !m->occ_k || m->occ_lattice > 1) return -1;
+        for (uint32_t g = 0; g < m->n_occ; ++g)
+            if (m->occ_k[g] > RX_POIS_CAP) return -1;
+        for (uint32_t j = 0; j < m->n; ++j)
+            if (m->occ_group[j] >= m->n_occ) return -1;
+    }
     const double R = theta[0], B[RX_MAX_NETS] = {theta[1], theta[2], m->B_extra[2], m->B_extra[3]};
     const double Br = theta[3];
     const double *S = theta + 4;
@@ -130,7 +207,9 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
     double *Ssum = (double *)malloc(sizeof(double) * ((size_t)T * n + 1));
     double *inf = (double *)malloc(sizeof(double) * (n ? n : 1));
     double *I = (double *)calloc(T ? T : 1, sizeof(double));
-    uint32_t cts[RX_POIS_CAP];
+    uint32_t cts[RX_POIS_CAP], octs[RX_POIS_CAP];
+    rx_occ oc = {NULL, NULL, NULL};
+    if (m->n_occ) rx_occ_build(m, &oc);
     for (uint32_t j = 0; j < n; ++j) s[j] = 1.0;
     for (uint32_t q = 0; q < n_seeds; ++q) {
         x[seeds[q]] = 1.0;        /* day -1 */
@@ -149,6 +228,13 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
                 for (uint32_t e = m->row_ptr[net][j]; e < m->row_ptr[net][j + 1]; ++e) h += inf[m->col[net][e]];
                 Hs[((size_t)t * (RX_MAX_NETS + 1) + net) * n + j] = h;
                 ssum += B[net] * h;
+            }
+            if (m->n_occ) {  /* the occupation term, in the slot of network n_nets */
+                double h = 0.0;
+                const uint32_t k = rx_occ_contacts(m, &oc, j, t, octs);
+                for (uint32_t e = 0; e < k; ++e) h += inf[octs[e]];
+                Hs[((size_t)t * (RX_MAX_NETS + 1) + m->n_nets) * n + j] = h;
+                ssum += B[m->n_nets] * h;
             }
             double r = 0.0;
             if (m->rand_mean > 0.0) {
@@ -205,6 +291,11 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
                     for (uint32_t e = m->row_ptr[net][j]; e < m->row_ptr[net][j + 1]; ++e)
                         ibar[(size_t)t * n + m->col[net][e]] += B[net] * coef;
                 }
+                if (m->n_occ) {
+                    gB[m->n_nets] += coef * Hs[((size_t)t * (RX_MAX_NETS + 1) + m->n_nets) * n + j];
+                    const uint32_t k = rx_occ_contacts(m, &oc, j, (uint32_t)t, octs);
+                    for (uint32_t e = 0; e < k; ++e) ibar[(size_t)t * n + octs[e]] += B[m->n_nets] * coef;
+                }
                 if (m->rand_mean > 0.0) {
                     gBr += coef * Hs[((size_t)t * (RX_MAX_NETS + 1) + RX_MAX_NETS) * n + j];
                     uint32_t k = contacts_of(m, thr, j, (uint32_t)t, cts);
@@ -221,5 +312,6 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
         free(sbar);
     }
     free(cls); free(x); free(s); free(g); free(lam); free(Hs); free(Ssum); free(inf); free(I);
+    free(oc.start); free(oc.members); free(oc.pos);
     return 0;
 }
