@@ -103,8 +103,9 @@ typedef struct deabm_ctx deabm_ctx;
  * stored networks and before the random network, so n_nets must be <= 3.
  * Plain, batched and ragged contexts take them (deabm_create,
  * deabm_create_batch, deabm_create_ragged: a population with n_occ > 0 is
- * numbered in occupation order); the relaxed model rejects n_occ > 0.  n_occ =
- * 0: occ_group and occ_k are ignored. *
+ * numbered in occupation order), and so does the relaxed model
+ * (deabm_relaxed_create: the same daily contacts in its forward and reverse
+ * sweep).  n_occ = 0: occ_group and occ_k are ignored. *
  * rand_ws = 1 replaces the Poisson contacts by the paper's form of the global
  * random network (Sec. 3 "Interaction Networks": one small-world Watts-Strogatz
  * graph, re-initialised every step; rand_mean is then ignored).  The ring
@@ -431,7 +432,8 @@ void deabm_destroy(deabm_ctx *ctx);
  *   p_asym[age], else severe with p_sev[age], else mild);  x_j(t), s_j(t) are the
  *   infected / susceptible mass of agent j (initial cases: x(-1) = 1, s(0) = 0);
  *   inf_i(t) = sum_{d=1}^{inf_len-1} A_c infT_c[d] x_i(t-d);  lambda_j(t) as in Eq. 1
- *   over the static networks and the day's random network;
+ *   over the static networks, the day's occupation contacts (graph->n_occ > 0, weight
+ *   B_net[n_nets]) and the day's random network;
  *   g_j(t) = sigmoid((log(expm1(lambda_j)) + l_j(t)) / tau) with logistic noise
  *   l = log(u) - log(1-u), u = ((w >> 8) + 0.5) 2^-24, w = Philox(seed; j, t, 8, 0).x
  *   (a binary Gumbel-softmax relaxation of the Eq. 2 draw);

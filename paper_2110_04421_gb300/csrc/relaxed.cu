@@ -7,13 +7,15 @@
 //   x_j(t) = s_j(t) * g_j(t),  s_j(t+1) = s_j(t) - x_j(t),  I(t) = sum_j x_j(t)
 //   g_j(t) = sigmoid((log expm1(lambda_j(t)) + l_j(t)) / tau)   (binary Gumbel-softmax
 //            relaxation of the Eq. 2 draw; l = logistic noise from Philox stream 8)
-//   lambda_j(t) = R/I * S_{a_j} * (sum_n B_n sum_{i->j} inf_i(t) + B_r sum_rand inf_i(t))   (Eq. 1)
+//   lambda_j(t) = R/I * S_{a_j} * (sum_n B_n sum_{i->j} inf_i(t) + B_o sum_occ inf_i(t)
+//                                  + B_r sum_rand inf_i(t))   (Eq. 1; the occupation term with
+//                 daily occupation networks, B_o the weight of network n_nets)
 //   inf_i(t) = sum_{d=1}^{L-1} A_{c_i} infT_{c_i}[d] * x_i(t-d)
 //   loss = (1/T) sum_t (log(I(t)+1) - y_t)^2
 // The reverse sweep carries d loss / d x back through the susceptible mass and,
 // along the transpose of every network, to the infectiousness of the sources;
-// the days are recomputed segment by segment from checkpoints (Philox noise and
-// random contacts are regenerated, never stored).
+// the days are recomputed segment by segment from checkpoints (Philox noise,
+// random and occupation contacts are regenerated, never stored).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,6 +36,14 @@ constexpr int kTheta = DEABM_N_THETA;
 
 struct RxParams {
     uint32_t n, n_nets, L, rand_on, T, nblk;
+    uint32_t nh;  // per-day H slots: the stored networks, the occupation term (n_occ > 0), the random network
+    // daily occupation networks (n_occ = 0: none), by agent id: occupation, place
+    // among its members; members of occupation g in ascending id at
+    // occ_members[occ_start[g] ..]; daily in-contacts per member; lattice rewiring
+    uint32_t n_occ, occ_lattice;
+    uint64_t thr_rewire;
+    const uint32_t *occ_gid, *occ_pos, *occ_start, *occ_members;
+    const uint8_t *occ_k;
     float tau, inv_Ibar;
     float B_extra[DEABM_MAX_NETS];
     uint64_t seed, net_seed;
@@ -47,6 +57,42 @@ struct RxParams {
 __device__ __forceinline__ float rx_weight(const RxParams &P, uint32_t net)
 {
     return net < 2 ? P.theta[1 + net] : P.B_extra[net];
+}
+
+// The day's occupation in-contacts of agent j on day t, drawn as in the plain
+// model (uniform over the other members from stream 4, or the Watts-Strogatz
+// lattice with rewiring from stream 9); f(agent id) for each, in draw order.
+template <class F>
+__device__ __forceinline__ void rx_occ_for(const RxParams &P, uint32_t j, uint32_t t, F f)
+{
+    const uint32_t g = __ldg(P.occ_gid + j);
+    const uint32_t beg = __ldg(P.occ_start + g), size = __ldg(P.occ_start + g + 1u) - beg;
+    if (size < 2u) return;
+    const uint32_t k = __ldg(P.occ_k + g), q = __ldg(P.occ_pos + j);
+    const uint2 nk = seed_key(P.net_seed);
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t e = 0; e < k; ++e) {
+        uint32_t r;
+        if (P.occ_lattice) {
+            if ((e & 1u) == 0u) w = draw(nk, j, t, kStreamWs, e >> 1);
+            const uint32_t coin = (e & 1u) ? w.z : w.x, word = (e & 1u) ? w.w : w.y;
+            const uint32_t m = (e >> 1) + 1u, hop = m < size ? m : m % size;
+            const uint32_t off = (e & 1u) == 0u ? hop : (hop == 0u ? 0u : size - hop);
+            if (off == 0u || (uint64_t)coin < P.thr_rewire) {
+                r = (uint32_t)(((uint64_t)word * (uint64_t)(size - 1u)) >> 32);
+                r += (r >= q) ? 1u : 0u;
+            } else {
+                r = q + off;
+                r = r >= size ? r - size : r;
+            }
+        } else {
+            if ((e & 3u) == 0u) w = draw(nk, j, t, kStreamOcc, e >> 2);
+            const uint32_t x = (e & 3u) == 0u ? w.x : (e & 3u) == 1u ? w.y : (e & 3u) == 2u ? w.z : w.w;
+            r = (uint32_t)(((uint64_t)x * (uint64_t)(size - 1u)) >> 32);
+            r += (r >= q) ? 1u : 0u;
+        }
+        f(__ldg(P.occ_members + beg + r));
+    }
 }
 
 __device__ __forceinline__ float sigmoidf_(float z)
@@ -99,7 +145,7 @@ __global__ void rx_inf_kernel(const RxParams P, int t, const float *__restrict__
 }
 
 struct RxSeg {  // per-day records of one checkpoint segment (k = t - t0)
-    float *x, *g, *s, *lam, *H;  // H: [K][n_nets + 1][N]
+    float *x, *g, *s, *lam, *H;  // H: [K][nh][N]
 };
 
 template <bool REC>
@@ -118,7 +164,13 @@ __global__ void __launch_bounds__(kRxBlock) rx_day_kernel(const RxParams P, int 
             for (uint32_t e = __ldg(P.row_ptr[net] + j); e < __ldg(P.row_ptr[net] + j + 1); ++e)
                 h = __fadd_rn(h, __ldg(inf + __ldg(P.col[net] + e)));
             ssum = __fadd_rn(ssum, __fmul_rn(rx_weight(P, net), h));
-            if (REC) seg.H[((size_t)k * (P.n_nets + 1) + net) * P.n + j] = h;
+            if (REC) seg.H[((size_t)k * P.nh + net) * P.n + j] = h;
+        }
+        if (P.n_occ) {
+            float h = 0.0f;
+            rx_occ_for(P, j, (uint32_t)t, [&](uint32_t v) { h = __fadd_rn(h, __ldg(inf + v)); });
+            ssum = __fadd_rn(ssum, __fmul_rn(rx_weight(P, P.n_nets), h));
+            if (REC) seg.H[((size_t)k * P.nh + P.n_nets) * P.n + j] = h;
         }
         float r = 0.0f;
         if (P.rand_on) {
@@ -136,7 +188,7 @@ __global__ void __launch_bounds__(kRxBlock) rx_day_kernel(const RxParams P, int 
             }
             ssum = __fadd_rn(ssum, __fmul_rn(P.theta[3], r));
         }
-        if (REC) seg.H[((size_t)k * (P.n_nets + 1) + P.n_nets) * P.n + j] = r;
+        if (REC) seg.H[((size_t)k * P.nh + P.nh - 1u) * P.n + j] = r;
         const float lam = R * P.inv_Ibar * P.theta[4 + P.age[j]] * ssum;
         const float g = lam > 0.0f ? sigmoidf_((logit_p(lam) + logistic_noise(P.seed, j, (uint32_t)t)) / P.tau) : 0.0f;
         const float sj = s[j];
@@ -215,12 +267,13 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
         const float cf = lbar * cR * Sa;
         coef[j] = cf;
         float ssum = 0.0f;
-        for (uint32_t net = 0; net <= P.n_nets; ++net) {
-            const float h = seg.H[((size_t)k * (P.n_nets + 1) + net) * P.n + j];
-            const float w = net < P.n_nets ? rx_weight(P, net) : P.theta[3];
+        const uint32_t nw = P.nh - 1u;  // weighted network slots (stored, occupation); the random one last
+        for (uint32_t net = 0; net < P.nh; ++net) {
+            const float h = seg.H[((size_t)k * P.nh + net) * P.n + j];
+            const float w = net < nw ? rx_weight(P, net) : P.theta[3];
             ssum += w * h;
-            if (net < 2 && net < P.n_nets) contrib[1 + net] = cf * h;
-            if (net == P.n_nets && P.rand_on) contrib[3] = cf * h;
+            if (net < 2 && net < nw) contrib[1 + net] = cf * h;
+            if (net == nw && P.rand_on) contrib[3] = cf * h;
         }
         contrib[0] = lbar * P.inv_Ibar * Sa * ssum;
 #pragma unroll
@@ -278,6 +331,17 @@ __global__ void rx_scatter_random_kernel(const RxParams P, int t, const float *_
     }
 }
 
+// ... and over the day's occupation contacts (regenerated as in the forward day)
+__global__ void rx_scatter_occ_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n) return;
+    const float cf = coef[j] * rx_weight(P, P.n_nets);
+    if (cf == 0.0f) return;
+    float *dst = ibring + (size_t)((uint32_t)t % P.L) * P.n;
+    rx_occ_for(P, j, (uint32_t)t, [&](uint32_t v) { atomicAdd(dst + v, cf); });
+}
+
 __global__ void rx_grad_reduce_kernel(const RxParams P, const double *gpart, float *grad)
 {
     const int q = threadIdx.x;
@@ -329,7 +393,7 @@ struct RxbArrays {
     uint32_t B, nbx;        // columns; blocks along the agents (8 agents each)
     const float *theta;     // [B][13]
     float *s, *xring, *inf, *Ipart, *ibring, *sbar, *coef;
-    float *x, *g, *sr, *lam, *H;  // segment records [K][N][B]; H [K][n_nets + 1][N][B]
+    float *x, *g, *sr, *lam, *H;  // segment records [K][N][B]; H [K][nh][N][B]
     double *gpart;          // [nbx][B][13]
 };
 
@@ -378,7 +442,7 @@ __global__ void __launch_bounds__(256) rxb_day_kernel(const RxParams P, RxbArray
     if (j < P.n && b < B) {
         const float *th = A.theta + (size_t)b * kTheta;
         const float *inf = A.inf;
-        const size_t nn = (size_t)P.n_nets + 1;
+        const size_t nn = P.nh;
         float ssum = 0.0f;
         for (uint32_t net = 0; net < P.n_nets; ++net) {
             float h = 0.0f;
@@ -386,6 +450,12 @@ __global__ void __launch_bounds__(256) rxb_day_kernel(const RxParams P, RxbArray
                 h = __fadd_rn(h, __ldg(inf + (size_t)__ldg(P.col[net] + e) * B + b));
             ssum = __fadd_rn(ssum, __fmul_rn(rxb_weight(P, th, net), h));
             if (REC) A.H[(((size_t)k * nn + net) * P.n + j) * B + b] = h;
+        }
+        if (P.n_occ) {
+            float h = 0.0f;
+            rx_occ_for(P, j, (uint32_t)t, [&](uint32_t v) { h = __fadd_rn(h, __ldg(inf + (size_t)v * B + b)); });
+            ssum = __fadd_rn(ssum, __fmul_rn(rxb_weight(P, th, P.n_nets), h));
+            if (REC) A.H[(((size_t)k * nn + P.n_nets) * P.n + j) * B + b] = h;
         }
         float r = 0.0f;
         if (P.rand_on) {
@@ -403,7 +473,7 @@ __global__ void __launch_bounds__(256) rxb_day_kernel(const RxParams P, RxbArray
             }
             ssum = __fadd_rn(ssum, __fmul_rn(th[3], r));
         }
-        if (REC) A.H[(((size_t)k * nn + P.n_nets) * P.n + j) * B + b] = r;
+        if (REC) A.H[(((size_t)k * nn + nn - 1u) * P.n + j) * B + b] = r;
         const float lam = th[0] * P.inv_Ibar * th[4 + P.age[j]] * ssum;
         const float g = lam > 0.0f ? sigmoidf_((logit_p(lam) + logistic_noise(P.seed, j, (uint32_t)t)) / P.tau) : 0.0f;
         const size_t q = (size_t)j * B + b;
@@ -484,13 +554,14 @@ __global__ void __launch_bounds__(256) rxb_adj_kernel(const RxParams P, RxbArray
         const float cf = lbar * cR * Sa;
         A.coef[qj] = cf;
         float ssum = 0.0f;
-        const size_t nn = (size_t)P.n_nets + 1;
-        for (uint32_t net = 0; net <= P.n_nets; ++net) {
+        const size_t nn = P.nh;
+        const uint32_t nw = P.nh - 1u;  // weighted network slots (stored, occupation); the random one last
+        for (uint32_t net = 0; net < P.nh; ++net) {
             const float h = A.H[(((size_t)k * nn + net) * P.n + j) * B + b];
-            const float w = net < P.n_nets ? rxb_weight(P, th, net) : th[3];
+            const float w = net < nw ? rxb_weight(P, th, net) : th[3];
             ssum += w * h;
-            if (net < 2 && net < P.n_nets) contrib[1 + net] = cf * h;
-            if (net == P.n_nets && P.rand_on) contrib[3] = cf * h;
+            if (net < 2 && net < nw) contrib[1 + net] = cf * h;
+            if (net == nw && P.rand_on) contrib[3] = cf * h;
         }
         contrib[0] = lbar * P.inv_Ibar * Sa * ssum;
 #pragma unroll
@@ -543,6 +614,16 @@ __global__ void rxb_scatter_random_kernel(const RxParams P, RxbArrays A, int t)
         v += (v >= j) ? 1u : 0u;
         atomicAdd(dst + (size_t)v * A.B + b, cf);
     }
+}
+
+__global__ void rxb_scatter_occ_kernel(const RxParams P, RxbArrays A, int t)
+{
+    const uint32_t j = blockIdx.x * 8u + threadIdx.y, b = blockIdx.y * 32u + threadIdx.x;
+    if (j >= P.n || b >= A.B) return;
+    const float cf = A.coef[(size_t)j * A.B + b] * rxb_weight(P, A.theta + (size_t)b * kTheta, P.n_nets);
+    if (cf == 0.0f) return;
+    float *dst = A.ibring + (size_t)((uint32_t)t % P.L) * P.n * A.B;
+    rx_occ_for(P, j, (uint32_t)t, [&](uint32_t v) { atomicAdd(dst + (size_t)v * A.B + b, cf); });
 }
 
 __global__ void rxb_grad_reduce_kernel(const RxbArrays A, float *grad)
@@ -650,7 +731,16 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
     const uint32_t n = g->n_agents;
     if (n == 0 || n >= (1u << 31) || g->n_nets > DEABM_MAX_NETS) return rx_fail(DEABM_EINVAL, "bad graph size");
     if (!(tau > 0.0f)) return rx_fail(DEABM_EINVAL, "tau must be > 0");
-    if (g->n_occ) return rx_fail(DEABM_EINVAL, "daily occupation networks are not available in the relaxed model");
+    if (g->n_occ) {
+        if (g->n_nets >= DEABM_MAX_NETS) return rx_fail(DEABM_EINVAL, "daily occupations need n_nets < %d", DEABM_MAX_NETS);
+        if (!g->occ_group || !g->occ_k) return rx_fail(DEABM_EINVAL, "occ_group and occ_k are required");
+        if (g->occ_lattice > 1 || !(g->occ_rewire >= 0.0f && g->occ_rewire <= 1.0f))
+            return rx_fail(DEABM_EINVAL, "occ_lattice must be 0 or 1 and occ_rewire in [0,1]");
+        for (uint32_t q = 0; q < g->n_occ; ++q)
+            if (g->occ_k[q] > DEABM_POIS_CAP) return rx_fail(DEABM_EINVAL, "occ_k must be <= %d", DEABM_POIS_CAP);
+        for (uint32_t j = 0; j < n; ++j)
+            if (g->occ_group[j] >= g->n_occ) return rx_fail(DEABM_EINVAL, "occ_group out of range");
+    }
     if (p->den_on) return rx_fail(DEABM_EINVAL, "exposure notification is not available in the relaxed model");
     if (max_days == 0 || ckpt_every == 0) return rx_fail(DEABM_EINVAL, "max_days and ckpt_every must be >= 1");
     if (p->inf_len < 2 || p->inf_len > DEABM_MAX_INF_LEN) return rx_fail(DEABM_EINVAL, "inf_len must be 2..64");
@@ -692,7 +782,41 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
         for (int k = 0; k < DEABM_MAX_NETS; ++k) P.B_extra[k] = p->B_net[k];
         P.seed = p->seed;
         P.net_seed = p->net_seed;
+        P.n_occ = g->n_occ;
+        P.nh = g->n_nets + (g->n_occ ? 1u : 0u) + 1u;
         int r;
+        if (g->n_occ) {  // members of each occupation in ascending id, each agent's place
+            const uint32_t G = g->n_occ;
+            std::vector<uint32_t> start((size_t)G + 1, 0), members(n), pos(n), fill;
+            for (uint32_t j = 0; j < n; ++j) start[g->occ_group[j] + 1]++;
+            for (uint32_t q = 0; q < G; ++q) start[q + 1] += start[q];
+            fill.assign(start.begin(), start.end() - 1);
+            for (uint32_t j = 0; j < n; ++j) {
+                const uint32_t q = g->occ_group[j];
+                pos[j] = fill[q] - start[q];
+                members[fill[q]++] = j;
+            }
+            uint32_t *d_gid, *d_pos, *d_start, *d_mem;
+            uint8_t *d_k;
+            if ((r = rx_alloc(c, &d_gid, n))) return r;
+            if ((r = rx_alloc(c, &d_pos, n))) return r;
+            if ((r = rx_alloc(c, &d_start, (size_t)G + 1))) return r;
+            if ((r = rx_alloc(c, &d_mem, n))) return r;
+            if ((r = rx_alloc(c, &d_k, G))) return r;
+            RCU(cudaMemcpyAsync(d_gid, g->occ_group, 4ull * n, cudaMemcpyHostToDevice, s));
+            RCU(cudaMemcpyAsync(d_pos, pos.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+            RCU(cudaMemcpyAsync(d_start, start.data(), 4ull * (G + 1), cudaMemcpyHostToDevice, s));
+            RCU(cudaMemcpyAsync(d_mem, members.data(), 4ull * n, cudaMemcpyHostToDevice, s));
+            RCU(cudaMemcpyAsync(d_k, g->occ_k, G, cudaMemcpyHostToDevice, s));
+            RCU(cudaStreamSynchronize(s));  // the staging vectors go out of scope
+            P.occ_gid = d_gid;
+            P.occ_pos = d_pos;
+            P.occ_start = d_start;
+            P.occ_members = d_mem;
+            P.occ_k = d_k;
+            P.occ_lattice = g->occ_lattice;
+            P.thr_rewire = rx_threshold((double)g->occ_rewire);
+        }
         std::vector<uint32_t> tptr, tcol, fill;
         for (uint32_t k = 0; k < g->n_nets; ++k) {
             const uint32_t E = g->row_ptr[k][n];
@@ -761,7 +885,7 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
         P.theta = c->theta;
         rx_class_kernel<<<(n + 255) / 256, 256, 0, s>>>(P, cls);
         RCU(cudaGetLastError());
-        const size_t L = c->L, K = c->K, NN = (size_t)g->n_nets + 1;
+        const size_t L = c->L, K = c->K, NN = P.nh;
         if ((r = rx_alloc(c, &c->s, n))) return r;
         if ((r = rx_alloc(c, &c->xring, L * n))) return r;
         if ((r = rx_alloc(c, &c->inf, n))) return r;
@@ -841,6 +965,7 @@ static int rx_backward_device(deabm_relaxed *c, uint32_t T)
             rx_adj_kernel<<<nb, kRxBlock, 0, s>>>(P, t, t - (int)t0, c->Ibar, c->ibring, c->sbar, c->coef, c->seg, c->gpart);
             rx_scatter_static_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
             if (P.rand_on) rx_scatter_random_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
+            if (P.n_occ) rx_scatter_occ_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
         }
     }
     rx_grad_reduce_kernel<<<1, 32, 0, s>>>(P, c->gpart, c->grad);
@@ -972,7 +1097,7 @@ static int rxb_reserve(deabm_relaxed *c, uint32_t B)
     for (void *p : c->bat_allocs) (void)cudaFree(p);
     c->bat_allocs.clear();
     c->bat_cap = B;
-    const size_t n = c->n, L = c->L, K = c->K, NN = (size_t)c->n_nets + 1, nb = n * B;
+    const size_t n = c->n, L = c->L, K = c->K, NN = c->P.nh, nb = n * B;
     const uint32_t nbx = (uint32_t)((n + 7) / 8);
     RxbArrays &A = c->bat;
     A.nbx = nbx;
@@ -1044,6 +1169,7 @@ static int rxb_gradient(deabm_relaxed *c, uint32_t T, uint32_t B, bool want_grad
             rxb_adj_kernel<<<grid, blk, 0, s>>>(P, A, t, t - (int)t0, c->b_Ibar);
             rxb_scatter_static_kernel<<<grid, blk, 0, s>>>(P, A, t);
             if (P.rand_on) rxb_scatter_random_kernel<<<grid, blk, 0, s>>>(P, A, t);
+            if (P.n_occ) rxb_scatter_occ_kernel<<<grid, blk, 0, s>>>(P, A, t);
         }
     }
     rxb_grad_reduce_kernel<<<(B * kTheta + 255) / 256, 256, 0, s>>>(A, c->b_grad);

@@ -86,16 +86,6 @@ def test_batched_columns_equal_plain_and_oracle(B):
             assert np.array_equal(m_o, m_b.astype(np.int64))
 
 
-def test_relaxed_model_rejects_occupations():
-    """Daily occupations run in plain, batched and ragged contexts, not in the
-    relaxed model (its adjoint covers the stored and Poisson networks)."""
-    from paper_2110_04421_gb300.deabm import DeabmError, Relaxed
-    pop = W.population_daily_occupation(500, 1, 5)
-    p = W.params_with()
-    with pytest.raises(DeabmError):
-        Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=0.5, max_days=5, ckpt_every=5)
-
-
 @pytest.mark.parametrize("beta", [0.0, 0.1, 1.0])
 def test_watts_strogatz_occupations(beta):
     """Watts-Strogatz contacts rewired daily: 23 occupations, households stored."""

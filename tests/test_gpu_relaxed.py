@@ -220,3 +220,41 @@ def test_batched_gradient_full_workload_sample_columns():
         scale = np.linalg.norm(o["grad"])
         assert abs(loss_b[b] - o["loss"]) <= 1e-4 * o["loss"], b
         assert np.max(np.abs(grad_b[b] - o["grad"])) <= 1e-4 * scale, (b, grad_b[b], o["grad"])
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_daily_occupations_gradient_matches_oracle(lattice):
+    """The relaxed model with daily occupation networks (households stored, 23
+    occupations drawn every day; uniform or Watts-Strogatz lattice contacts): the
+    forward incidence, the loss and the gradient (its occupation weight theta[2]
+    included) against the oracle's FP64 run and reverse sweep at the bars above,
+    and the batched gradient's columns against single runs."""
+    pop = W.population_daily_occupation(6000, 17, 15)
+    if lattice:
+        pop = dict(pop, occ_lattice=1, occ_rewire=0.2)
+    p = W.params_with(R=3.1, seed=41, net_seed=42, S_age=[0.6, 0.8, 1.0, 1.1, 1.2, 0.9, 1.3, 1.0, 0.7])
+    T = 50
+    rx = oracle.Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=0.5)
+    th = oracle.theta_of(p)
+    hidden = th.copy()
+    hidden[0], hidden[2] = 3.6, 1.4
+    y = np.log(rx.run(hidden, T)["incidence"] + 1.0).astype(np.float32)
+    g = gpu(pop, p, max_days=T, ckpt_every=10)
+    inc = g.forward(th, T)
+    loss, grad, _ = g.grad(th, y)
+    B = 3
+    thetas = np.repeat(np.float32(th)[None, :], B, axis=0)
+    thetas[:, 2] *= np.array([0.8, 1.0, 1.3], np.float32)
+    loss_b, grad_b, _ = g.grad_batch(thetas, np.repeat(y[:, None], B, axis=1))
+    singles = [g.grad(thetas[b], y) for b in range(B)]
+    g.close()
+    o = rx.run(th, T, target=y.astype(np.float64), grad=True)
+    assert np.all(np.abs(inc - o["incidence"]) <= 1e-4 * np.maximum(o["incidence"], 1.0))
+    assert abs(loss - o["loss"]) <= 1e-4 * o["loss"]
+    scale = np.linalg.norm(o["grad"])
+    assert abs(o["grad"][2]) > 1e-3 * scale  # the occupation weight matters
+    assert np.max(np.abs(grad - o["grad"])) <= 1e-4 * scale, (grad, o["grad"])
+    for b in range(B):
+        ls, gs, _ = singles[b]
+        assert abs(loss_b[b] - ls) <= 1e-5 * ls, (b, loss_b[b], ls)
+        assert np.max(np.abs(grad_b[b] - gs)) <= 1e-5 * np.linalg.norm(gs), (b, grad_b[b], gs)
