@@ -132,26 +132,37 @@ __global__ void rx_class_kernel(const RxParams P, uint8_t *cls)
     cls[i] = (uint64_t)w.x < __ldg(&P.tab->thr_asym[a]) ? 0 : ((uint64_t)w.z < __ldg(&P.tab->thr_sev[a]) ? 2 : 1);
 }
 
-// inf_i(t) from the ring of the last L days of x
-__global__ void rx_inf_kernel(const RxParams P, int t, const float *__restrict__ xring, float *__restrict__ inf)
+// inf_i(t) from the ring of the last L days of x: the sum over d = 1 .. L-1 of
+// A_c infT_c[d] x_i(t-d), d ascending
+__device__ __forceinline__ float rx_inf_of(const RxParams &P, int t, const float *__restrict__ xring, uint32_t i)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
     const int c = P.cls[i];
     float v = 0.0f;
     for (uint32_t d = 1; d < P.L; ++d)
         v += __ldg(&P.tab->infT[c][d]) * xring[(size_t)ring_slot(t - (int)d, P.L) * P.n + i];
-    inf[i] = v;
+    return v;
+}
+
+// inf(t) of every agent (the first day of a run or of a recomputed segment; the
+// day kernel computes each later day's for its own agent)
+__global__ void rx_inf_kernel(const RxParams P, int t, const float *__restrict__ xring, float *__restrict__ inf)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    inf[i] = rx_inf_of(P, t, xring, i);
 }
 
 struct RxSeg {  // per-day records of one checkpoint segment (k = t - t0)
     float *x, *g, *s, *lam, *H;  // H: [K][nh][N]
 };
 
+// Day t: reads inf(t), writes x(t) into the ring and then the agent's own
+// inf(t+1) into inf_next (the ring then holds every x it needs), so no separate
+// launch computes the next day's infectiousness.
 template <bool REC>
 __global__ void __launch_bounds__(kRxBlock) rx_day_kernel(const RxParams P, int t, int k, const float *__restrict__ inf,
                                                           float *__restrict__ s, float *__restrict__ xring, RxSeg seg,
-                                                          float *__restrict__ Ipart)
+                                                          float *__restrict__ Ipart, float *__restrict__ inf_next)
 {
     __shared__ float warp_sum[kRxBlock / 32];
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,6 +206,7 @@ __global__ void __launch_bounds__(kRxBlock) rx_day_kernel(const RxParams P, int 
         x = sj * g;
         s[j] = sj - x;
         xring[(size_t)ring_slot(t, P.L) * P.n + j] = x;
+        inf_next[j] = rx_inf_of(P, t + 1, xring, j);  // this thread's own ring entries only
         if (REC) {
             seg.x[(size_t)k * P.n + j] = x;
             seg.g[(size_t)k * P.n + j] = g;
@@ -243,7 +255,7 @@ __global__ void rx_loss_kernel(const RxParams P, uint32_t T, const float *Ipart,
 // reverse of day t: d loss / d x, d loss / d lambda, the susceptible-mass adjoint,
 // each agent's coefficient for the transpose scatter and the parameter partials
 __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int t, int k, const float *__restrict__ Ibar,
-                                                          const float *__restrict__ ibring, float *__restrict__ sbar,
+                                                          float *__restrict__ ibring, float *__restrict__ sbar,
                                                           float *__restrict__ coef, RxSeg seg, double *gpart)
 {
     __shared__ float red[kTheta][kRxBlock / 32];
@@ -266,6 +278,32 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
         const float R = P.theta[0], Sa = P.theta[4 + a], cR = R * P.inv_Ibar;
         const float cf = lbar * cR * Sa;
         coef[j] = cf;
+        // d loss / d inf_i(t) along the day's generated networks: this destination
+        // regenerates its random and occupation contacts and adds to theirs
+        // (atomics; the slot was cleared after the day above it read it, and the
+        // stored networks' gathers add to it afterwards)
+        if (cf != 0.0f) {
+            float *dst = ibring + (size_t)((uint32_t)t % P.L) * P.n;
+            if (P.rand_on) {
+                const float cfr = cf * P.theta[3];
+                const uint2 nk = seed_key(P.net_seed);
+                uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+                uint32_t kk = 0;
+                while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+                for (uint32_t e = 0; e < kk; ++e) {
+                    const uint32_t idx = e + 1u;
+                    if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
+                    const uint32_t xw = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
+                    uint32_t v = (uint32_t)(((uint64_t)xw * (uint64_t)(P.n - 1u)) >> 32);
+                    v += (v >= j) ? 1u : 0u;
+                    atomicAdd(dst + v, cfr);
+                }
+            }
+            if (P.n_occ) {
+                const float cfo = cf * rx_weight(P, P.n_nets);
+                rx_occ_for(P, j, (uint32_t)t, [&](uint32_t v) { atomicAdd(dst + v, cfo); });
+            }
+        }
         float ssum = 0.0f;
         const uint32_t nw = P.nh - 1u;  // weighted network slots (stored, occupation); the random one last
         for (uint32_t net = 0; net < P.nh; ++net) {
@@ -293,7 +331,10 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
     }
 }
 
-// d loss / d inf_i(t) over the static networks: gather along the transpose CSR
+// d loss / d inf_i(t) over the static networks: gather along the transpose CSR,
+// added to what the day's generated networks scattered in; then the slot of
+// day t-1 (day t-1+L's, last read by the reverse day just run) is cleared for
+// the next reverse day's scatters
 __global__ void rx_scatter_static_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -305,41 +346,8 @@ __global__ void rx_scatter_static_kernel(const RxParams P, int t, const float *_
             h += __ldg(coef + __ldg(P.tr_col[net] + e));
         v += rx_weight(P, net) * h;
     }
-    ibring[(size_t)((uint32_t)t % P.L) * P.n + i] = v;
-}
-
-// ... and over the day's random network: each destination regenerates its contacts
-// and adds to theirs (atomics: the day's transpose is never stored)
-__global__ void rx_scatter_random_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
-{
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.n) return;
-    const float cf = coef[j] * P.theta[3];
-    if (cf == 0.0f) return;
-    const uint2 nk = seed_key(P.net_seed);
-    uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
-    uint32_t kk = 0;
-    while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
-    float *dst = ibring + (size_t)((uint32_t)t % P.L) * P.n;
-    for (uint32_t e = 0; e < kk; ++e) {
-        const uint32_t idx = e + 1u;
-        if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
-        const uint32_t xw = (idx & 3u) == 1u ? w.y : (idx & 3u) == 2u ? w.z : (idx & 3u) == 3u ? w.w : w.x;
-        uint32_t v = (uint32_t)(((uint64_t)xw * (uint64_t)(P.n - 1u)) >> 32);
-        v += (v >= j) ? 1u : 0u;
-        atomicAdd(dst + v, cf);
-    }
-}
-
-// ... and over the day's occupation contacts (regenerated as in the forward day)
-__global__ void rx_scatter_occ_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
-{
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.n) return;
-    const float cf = coef[j] * rx_weight(P, P.n_nets);
-    if (cf == 0.0f) return;
-    float *dst = ibring + (size_t)((uint32_t)t % P.L) * P.n;
-    rx_occ_for(P, j, (uint32_t)t, [&](uint32_t v) { atomicAdd(dst + v, cf); });
+    ibring[(size_t)((uint32_t)t % P.L) * P.n + i] += v;
+    ibring[(size_t)(((uint32_t)t + P.L - 1u) % P.L) * P.n + i] = 0.0f;
 }
 
 __global__ void rx_grad_reduce_kernel(const RxParams P, const double *gpart, float *grad)
@@ -888,7 +896,7 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
         const size_t L = c->L, K = c->K, NN = P.nh;
         if ((r = rx_alloc(c, &c->s, n))) return r;
         if ((r = rx_alloc(c, &c->xring, L * n))) return r;
-        if ((r = rx_alloc(c, &c->inf, n))) return r;
+        if ((r = rx_alloc(c, &c->inf, 2 * (size_t)n))) return r;  // inf(t), inf(t+1)
         if ((r = rx_alloc(c, &c->ckpt, (size_t)c->nseg * (L + 1) * n))) return r;
         if ((r = rx_alloc(c, &c->seg.x, K * n))) return r;
         if ((r = rx_alloc(c, &c->seg.g, K * n))) return r;
@@ -928,14 +936,15 @@ static int rx_forward_device(deabm_relaxed *c, uint32_t T, const float *y_dev, f
     rx_init_kernel<<<nb, kRxBlock, 0, s>>>(P, c->seeds, c->n_seeds, c->s, c->xring);
     if (c->n_seeds) rx_seed_kernel<<<(c->n_seeds + 255) / 256, 256, 0, s>>>(P, c->seeds, c->n_seeds, c->s, c->xring);
     RCU(cudaGetLastError());
+    if (T) rx_inf_kernel<<<nb, kRxBlock, 0, s>>>(P, 0, c->xring, c->inf);
     for (uint32_t t = 0; t < T; ++t) {
         if (t % c->K == 0) {
             float *ck = c->ckpt + (size_t)(t / c->K) * (L + 1) * n;
             RCU(cudaMemcpyAsync(ck, c->s, 4ull * n, cudaMemcpyDeviceToDevice, s));
             RCU(cudaMemcpyAsync(ck + n, c->xring, 4ull * L * n, cudaMemcpyDeviceToDevice, s));
         }
-        rx_inf_kernel<<<nb, kRxBlock, 0, s>>>(P, (int)t, c->xring, c->inf);
-        rx_day_kernel<false><<<nb, kRxBlock, 0, s>>>(P, (int)t, 0, c->inf, c->s, c->xring, c->seg, c->Ipart);
+        rx_day_kernel<false><<<nb, kRxBlock, 0, s>>>(P, (int)t, 0, c->inf + (size_t)(t & 1u) * n, c->s, c->xring,
+                                                    c->seg, c->Ipart, c->inf + (size_t)((t + 1u) & 1u) * n);
     }
     rx_loss_kernel<<<1, 256, 0, s>>>(P, T, c->Ipart, y_dev, c->I, c->Ibar, c->loss, loss_trace_slot);
     RCU(cudaGetLastError());
@@ -957,15 +966,15 @@ static int rx_backward_device(deabm_relaxed *c, uint32_t T)
         const float *ck = c->ckpt + (size_t)sg * (L + 1) * n;
         RCU(cudaMemcpyAsync(c->s, ck, 4ull * n, cudaMemcpyDeviceToDevice, s));
         RCU(cudaMemcpyAsync(c->xring, ck + n, 4ull * L * n, cudaMemcpyDeviceToDevice, s));
-        for (uint32_t t = t0; t < t1; ++t) {  // recompute the segment, recording it
-            rx_inf_kernel<<<nb, kRxBlock, 0, s>>>(P, (int)t, c->xring, c->inf);
-            rx_day_kernel<true><<<nb, kRxBlock, 0, s>>>(P, (int)t, (int)(t - t0), c->inf, c->s, c->xring, c->seg, c->Ipart);
-        }
+        rx_inf_kernel<<<nb, kRxBlock, 0, s>>>(P, (int)t0, c->xring, c->inf + (size_t)(t0 & 1u) * n);
+        for (uint32_t t = t0; t < t1; ++t)  // recompute the segment, recording it
+            rx_day_kernel<true><<<nb, kRxBlock, 0, s>>>(P, (int)t, (int)(t - t0), c->inf + (size_t)(t & 1u) * n, c->s,
+                                                       c->xring, c->seg, c->Ipart, c->inf + (size_t)((t + 1u) & 1u) * n);
+        // each reverse day: the adjoint with the generated networks' scatters, then
+        // the stored networks' gathers (two launches)
         for (int t = (int)t1 - 1; t >= (int)t0; --t) {
             rx_adj_kernel<<<nb, kRxBlock, 0, s>>>(P, t, t - (int)t0, c->Ibar, c->ibring, c->sbar, c->coef, c->seg, c->gpart);
             rx_scatter_static_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
-            if (P.rand_on) rx_scatter_random_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
-            if (P.n_occ) rx_scatter_occ_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
         }
     }
     rx_grad_reduce_kernel<<<1, 32, 0, s>>>(P, c->gpart, c->grad);
