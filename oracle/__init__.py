@@ -86,6 +86,7 @@ class _Model(C.Structure):
         ("den_on", C.c_uint32), ("den_adoption", C.c_double), ("den_compliance", C.c_double),
         ("den_window", C.c_uint32),
         ("rand_ws", C.c_uint32), ("rand_ws_k", C.c_uint32), ("rand_ws_beta", C.c_double),
+        ("rand_by_age", C.c_uint32), ("rand_mean_age", C.c_float * N_AGE),
     ]
 
 
@@ -110,6 +111,7 @@ class _RxModel(C.Structure):
         ("seed", C.c_uint64), ("net_seed", C.c_uint64),
         ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
         ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_double),
+        ("rand_by_age", C.c_uint32), ("rand_mean_age", C.c_double * N_AGE),
     ]
 
 
@@ -264,6 +266,10 @@ class Model:
             m.occ_k = ok.ctypes.data
             m.occ_lattice = int(graph.get("occ_lattice", 0))
             m.occ_rewire = float(graph.get("occ_rewire", 0.0))
+        if P.get("rand_mean_age") is not None:  # age-stratified Poisson means
+            m.rand_by_age = 1
+            for a in range(N_AGE):
+                m.rand_mean_age[a] = float(P["rand_mean_age"][a])
         if graph.get("rand_ws"):  # the global random network as a daily Watts-Strogatz graph
             m.rand_ws = 1
             m.rand_ws_k = int(graph.get("rand_ws_k", 2))
@@ -433,6 +439,10 @@ class Relaxed:
             m.occ_k = ok.ctypes.data
             m.occ_lattice = int(graph.get("occ_lattice", 0))
             m.occ_rewire = float(np.float32(graph.get("occ_rewire", 0.0)))
+        if params.get("rand_mean_age") is not None:  # age-stratified Poisson means (FP32 values)
+            m.rand_by_age = 1
+            for a in range(N_AGE):
+                m.rand_mean_age[a] = f32(params["rand_mean_age"][a])
         self.m = m
         self.age = np.ascontiguousarray(age, dtype=np.uint8)
         self.seeds = np.ascontiguousarray(seed_ids if seed_ids is not None else [], dtype=np.uint32)

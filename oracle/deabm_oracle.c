@@ -114,6 +114,12 @@ typedef struct {
      * rand_ws_k lattice neighbours (even, 2..16), rewiring probability rand_ws_beta */
     uint32_t rand_ws, rand_ws_k;
     double rand_ws_beta;
+    /* age-stratified random interactions (Sec. 3, Interaction Networks: each
+     * agent's age-stratified number of random interactions parameterises the
+     * random network): with rand_by_age set, agent j's daily in-contact count is
+     * Poisson(rand_mean_age[age_j]) instead of Poisson(rand_mean) */
+    uint32_t rand_by_age;
+    float rand_mean_age[OR_N_AGE];
 } or_model;
 
 /* ------------------------------------------------------------------------- */
@@ -496,13 +502,32 @@ typedef struct {
     double t64[OR_N_CLASS * OR_MAX_INF_LEN];
     float t32[OR_N_CLASS * OR_MAX_INF_LEN];
     uint64_t pois[OR_POIS_CAP];
+    uint64_t pois_age[OR_N_AGE][OR_POIS_CAP];  /* rand_by_age: thresholds of each age bin's mean */
 } or_tables;
+
+/* is the Poisson random network on (some agent has a positive mean)? */
+static int rand_poisson_on(const or_model *m)
+{
+    if (!m->rand_by_age) return m->rand_mean > 0.0f;
+    for (int a = 0; a < OR_N_AGE; ++a)
+        if (m->rand_mean_age[a] > 0.0f) return 1;
+    return 0;
+}
+
+/* the Poisson thresholds of an agent of age bin a */
+static const uint64_t *pois_of(const or_model *m, const or_tables *tb, int a)
+{
+    return m->rand_by_age ? tb->pois_age[a] : tb->pois;
+}
 
 static int check_model(const or_model *m)
 {
     if (m->inf_len == 0 || m->inf_len > OR_MAX_INF_LEN || m->n_nets > OR_MAX_NETS) return -1;
     if (m->quar_days > 15 || m->test_hi > 7 || m->test_lo < 1 || m->test_lo > m->test_hi) return -1;
-    if (m->rand_mean > 0.0f && m->n < 2) return -1;
+    if (rand_poisson_on(m) && m->n < 2) return -1;
+    if (m->rand_by_age)
+        for (int a = 0; a < OR_N_AGE; ++a)
+            if (!(m->rand_mean_age[a] >= 0.0f)) return -1;
     if (m->rand_ws && (m->rand_ws_k < 2u || m->rand_ws_k > 16u || m->rand_ws_k % 2u || m->n < 2u || m->den_on ||
                        !(m->rand_ws_beta >= 0.0 && m->rand_ws_beta <= 1.0)))
         return -1;
@@ -523,6 +548,7 @@ static void make_tables(const or_model *m, or_tables *tb)
 {
     or_inf_table(m, tb->t64, tb->t32);
     or_poisson_thresholds((double)m->rand_mean, tb->pois);
+    for (int a = 0; a < OR_N_AGE; ++a) or_poisson_thresholds((double)m->rand_mean_age[a], tb->pois_age[a]);
 }
 
 /* Daily dose selection of the priority strategies (Sec. 5, Table 1): a shared
@@ -747,8 +773,8 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             s32 = (m->n_nets == 0 && m->n_occ == 0) ? term : s32 + term;
             s64 += (double)m->B_rand * r64;
             messages += k;
-        } else if (m->rand_mean > 0.0f) {
-            k = random_contacts(m->net_seed, n, j, t, tb->pois, contacts);
+        } else if (rand_poisson_on(m)) {
+            k = random_contacts(m->net_seed, n, j, t, pois_of(m, tb, age[j]), contacts);
             float r32 = 0.0f;
             double r64 = 0.0;
             for (uint32_t e = 0; e < k; ++e) { r32 = r32 + inf32[contacts[e]]; r64 = r64 + inf64[contacts[e]]; }
@@ -908,8 +934,8 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
                     k = occ_contacts(m, &occ, j, d, contacts);
                     for (uint32_t e = 0; e < k && !hit; ++e) hit = den_src[contacts[e]];
                 }
-                if (m->rand_mean > 0.0f) {
-                    k = random_contacts(m->net_seed, n, j, d, tb->pois, contacts);
+                if (rand_poisson_on(m)) {
+                    k = random_contacts(m->net_seed, n, j, d, pois_of(m, tb, age[j]), contacts);
                     for (uint32_t e = 0; e < k && !hit; ++e) hit = den_src[contacts[e]];
                 }
             }

@@ -21,7 +21,8 @@
  *   - x_j(t) = s_j(t) g_j(t),  s_j(t+1) = s_j(t) - x_j(t),  I(t) = sum_j x_j(t);
  *   - loss = (1/T) sum_t (log(I(t)+1) - y_t)^2.
  * Parameters theta = (R, B_0, B_1, B_r, S_0..S_8).  The random network is the
- * day's Philox network of the plain model.
+ * day's Philox network of the plain model (with age-stratified means when
+ * rand_by_age is set).
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,6 +57,10 @@ typedef struct {
     const uint8_t *occ_k;
     uint32_t occ_lattice;
     double occ_rewire;
+    /* age-stratified random interactions: agent j's daily count is
+     * Poisson(rand_mean_age[age_j]) when rand_by_age is set */
+    uint32_t rand_by_age;
+    double rand_mean_age[RX_N_AGE];
 } rx_model;
 
 static void draw4(uint64_t seed, uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t out[4])
@@ -192,8 +197,13 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
     for (int c = 0; c < 3; ++c)
         for (uint32_t d = 0; d < L; ++d)
             infT[c][d] = d == 0 ? 0.0 : m->A_class[c] * or_gamma_integral(d - 1.0, (double)d, m->inf_shape[c], m->inf_scale[c]);
-    uint64_t thr[RX_POIS_CAP];
-    or_poisson_thresholds(m->rand_mean, thr);
+    /* Poisson thresholds of each age bin (all the same without rand_by_age) */
+    uint64_t thr_age[RX_N_AGE][RX_POIS_CAP];
+    int rand_on = m->rand_by_age ? 0 : m->rand_mean > 0.0;
+    for (int a = 0; a < RX_N_AGE; ++a) {
+        or_poisson_thresholds(m->rand_by_age ? m->rand_mean_age[a] : m->rand_mean, thr_age[a]);
+        if (m->rand_by_age && m->rand_mean_age[a] > 0.0) rand_on = 1;
+    }
     uint8_t *cls = (uint8_t *)malloc(n ? n : 1);
     rx_classes(m, age, cls);
 
@@ -237,8 +247,8 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
                 ssum += B[m->n_nets] * h;
             }
             double r = 0.0;
-            if (m->rand_mean > 0.0) {
-                uint32_t k = contacts_of(m, thr, j, t, cts);
+            if (rand_on) {
+                uint32_t k = contacts_of(m, thr_age[age[j]], j, t, cts);
                 for (uint32_t e = 0; e < k; ++e) r += inf[cts[e]];
             }
             Hs[((size_t)t * (RX_MAX_NETS + 1) + RX_MAX_NETS) * n + j] = r;
@@ -296,9 +306,9 @@ int rx_run(const rx_model *m, const uint8_t *age, const uint32_t *seeds, uint32_
                     const uint32_t k = rx_occ_contacts(m, &oc, j, (uint32_t)t, octs);
                     for (uint32_t e = 0; e < k; ++e) ibar[(size_t)t * n + octs[e]] += B[m->n_nets] * coef;
                 }
-                if (m->rand_mean > 0.0) {
+                if (rand_on) {
                     gBr += coef * Hs[((size_t)t * (RX_MAX_NETS + 1) + RX_MAX_NETS) * n + j];
-                    uint32_t k = contacts_of(m, thr, j, (uint32_t)t, cts);
+                    uint32_t k = contacts_of(m, thr_age[age[j]], j, (uint32_t)t, cts);
                     for (uint32_t e = 0; e < k; ++e) ibar[(size_t)t * n + cts[e]] += Br * coef;
                 }
             }

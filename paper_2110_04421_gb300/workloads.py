@@ -155,6 +155,7 @@ def default_params() -> dict:
     return dict(
         R=3.0, inv_Ibar=1.0 / 14.0, dt=1.0,   # 1/I: I = mean daily interactions (about 14 here)
         B_net=[2.0, 1.0], B_rand=1.0, rand_mean=2.0,
+        rand_mean_age=None,  # per-age-bin Poisson means of the random network (None: rand_mean for all)
         S_age=[1.0] * N_AGE,
         A_class=[0.5, 1.0, 1.0],
         inf_shape=[4.0, 4.0, 4.0], inf_scale=[1.25, 1.25, 1.25], inf_len=30,
