@@ -81,7 +81,12 @@ typedef struct deabm_ctx deabm_ctx;
  * e in [row_ptr[j], row_ptr[j+1]).  The in-edges of a row are summed in the
  * order listed.  rand_mean > 0 adds the daily random network: each agent j
  * receives K_j ~ Poisson(rand_mean) (capped at DEABM_POIS_CAP) in-contacts
- * drawn uniformly from the other agents, regenerated every day.
+ * drawn uniformly from the other agents, regenerated every day.  rand_by_age = 1
+ * makes the mean age-stratified (Sec. 3 "Interaction Networks": each agent's
+ * age-stratified number of random interactions parameterises the random
+ * network): K_j ~ Poisson(rand_mean_age[age_bin_j]) (each 0..1000; the network
+ * is on when one of them is > 0; rand_mean is then ignored).  Not with rand_ws
+ * (which ignores both) and not in deabm_lambda_noalloc.
  *
  * n_occ > 0 adds the daily occupation networks (Sec. 3 "Interaction Networks":
  * an agent's occupation is fixed, whom it meets there changes every day).
@@ -138,6 +143,8 @@ typedef struct {
     uint32_t rand_ws;     /* 1: the random network is a daily Watts-Strogatz graph (see below) */
     uint32_t rand_ws_k;   /* rand_ws = 1: lattice neighbours, even, 2..16 */
     float rand_ws_beta;   /* rand_ws = 1: daily rewiring probability, 0..1 */
+    uint32_t rand_by_age; /* 1: per-age-bin Poisson means rand_mean_age (see above) */
+    float rand_mean_age[DEABM_N_AGE];
 } deabm_graph;
 
 /* Agents (Sec. 3 "Agent State Definition"); all host arrays of n_agents entries.

@@ -76,19 +76,20 @@ struct RandHead {
 };
 
 // Block 0 of agent j's random network on `day` (caller id) and the day's
-// in-contact count it fixes: K_j = the number of Poisson thresholds at or
-// below word 0, at most DEABM_POIS_CAP.
+// in-contact count it fixes: K_j = the number of Poisson thresholds (of j's age
+// bin's mean when the means are age-stratified) at or below word 0, at most
+// DEABM_POIS_CAP.
 struct RandBlock0 {
     uint4 w;
     uint32_t k;
 };
 
 template <bool RK = true>
-__device__ __forceinline__ RandBlock0 random_block0(const KParams &P, uint32_t j, uint32_t day)
+__device__ __forceinline__ RandBlock0 random_block0(const KParams &P, uint32_t j, uint32_t day, int age)
 {
     RandBlock0 r;
     r.w = net_draw<RK>(P, j, day, kStreamRnet, 0u);
-    r.k = poisson_count(P, r.w.x);
+    r.k = poisson_count(P, r.w.x, age);
     return r;
 }
 
@@ -140,18 +141,6 @@ __device__ __forceinline__ float random_tail(const KParams &P, const float *__re
             if (e + u < h.k) r = __fadd_rn(r, v[u]);
     }
     return r;
-}
-
-// All random in-contacts at once (head and tail back to back).  REC: also write
-// the contacts to rec[1..] when rec is not null.
-template <bool REC = false, bool ROWMAP = false>
-__device__ __forceinline__ float random_sum(const KParams &P, const float *__restrict__ inf, uint32_t j,
-                                            uint32_t day, uint32_t stride, uint32_t b, uint32_t *k_out,
-                                            uint32_t *rec = nullptr, const uint32_t *row_of = nullptr)
-{
-    const RandHead h = random_head<REC, ROWMAP>(P, inf, j, random_block0(P, j, day), stride, b, rec, row_of);
-    *k_out = h.k;
-    return random_tail<REC, ROWMAP>(P, inf, j, day, stride, b, h, rec, row_of);
 }
 
 // Far end of edge m (1-based) of agent i in the day's Watts-Strogatz random
@@ -398,7 +387,7 @@ __device__ __forceinline__ float lambda_of(const KParams &P, const Rep &rp, cons
 {
     const RowBounds rb = row_bounds(P, j);
     RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
-    if (P.rand_on) r0 = random_block0<RK>(P, jo, day);
+    if (P.rand_on) r0 = random_block0<RK>(P, jo, day, age);
     return lambda_at<OCC, REC, ROWMAP, WSG, RK>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
 }
 

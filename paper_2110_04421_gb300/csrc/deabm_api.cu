@@ -164,6 +164,37 @@ static uint64_t threshold(double p)
     return (uint64_t)std::floor(p * 4294967296.0);
 }
 
+// Poisson(m) CDF thresholds: t_0 = exp(-m), t_k = (t_{k-1} * m) / k, c_k = c_{k-1} + t_k
+static void poisson_thresholds(double m, uint64_t *thr)
+{
+    volatile double t = std::exp(-m), c = t;
+    thr[0] = threshold(c);
+    for (int k = 1; k < DEABM_POIS_CAP; ++k) {
+        t = (t * m) / (double)k;
+        c = c + t;
+        thr[k] = threshold(c);
+    }
+}
+
+// the Poisson random network is on: a positive mean (of some age bin when the
+// means are age-stratified), and not replaced by the Watts-Strogatz graph
+static bool poisson_on(const deabm_graph *g)
+{
+    if (g->rand_ws) return false;
+    if (!g->rand_by_age) return g->rand_mean > 0.0f;
+    for (int a = 0; a < DEABM_N_AGE; ++a)
+        if (g->rand_mean_age[a] > 0.0f) return true;
+    return false;
+}
+
+// both Poisson tables of a context's graph (the single mean, and each age bin's)
+static void poisson_tables(const deabm_graph *g, Tables &T)
+{
+    poisson_thresholds((double)g->rand_mean, T.pois);
+    for (int a = 0; a < DEABM_N_AGE; ++a)
+        poisson_thresholds(g->rand_by_age ? (double)g->rand_mean_age[a] : (double)g->rand_mean, T.pois_age[a]);
+}
+
 // Before a state is installed (create, reset, restore): the infectiousness
 // buffers the next day writes start at 0, since the day kernels leave a quiet
 // susceptible agent's entry untouched (it emits nothing).
@@ -308,7 +339,12 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
     if (n == 0 || n >= (1u << 31)) return fail(ctx, DEABM_EINVAL, "n_agents must be in [1, 2^31)");
     if (g->n_nets > DEABM_MAX_NETS) return fail(ctx, DEABM_EINVAL, "n_nets > %d", DEABM_MAX_NETS);
     if (!(g->rand_mean >= 0.0f) || g->rand_mean > 1e3f) return fail(ctx, DEABM_EINVAL, "rand_mean out of range");
-    if (g->rand_mean > 0.0f && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
+    if (g->rand_by_age > 1) return fail(ctx, DEABM_EINVAL, "rand_by_age must be 0 or 1");
+    if (g->rand_by_age)
+        for (int q = 0; q < DEABM_N_AGE; ++q)
+            if (!(g->rand_mean_age[q] >= 0.0f) || g->rand_mean_age[q] > 1e3f)
+                return fail(ctx, DEABM_EINVAL, "rand_mean_age[%d] out of range", q);
+    if (poisson_on(g) && n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
     if ((uint64_t)n * n_rep >= (1ull << 40)) return fail(ctx, DEABM_EINVAL, "n_agents * n_rep too large");
     if (g->rand_ws) {
         if (g->rand_ws != 1) return fail(ctx, DEABM_EINVAL, "rand_ws must be 0 or 1");
@@ -644,7 +680,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                     CU(ctx, launch_csr_renumber(src_rp[k], src_col[k], ctx->orig_id, d_o2n, n, ctx->row_ptr[k],
                                                 ctx->col[k], d_scan, s));
             }
-            if (ctx->relabel && g->rand_mean > 0.0f && n_rep > 1) {  // batched: caller id -> row map
+            if (ctx->relabel && (poisson_on(g) || g->rand_ws) && n_rep > 1) {  // batched: caller id -> row map
                 if ((r = dalloc(ctx, &ctx->row_of, n))) return r;
                 CU(ctx, cudaMemcpyAsync(ctx->row_of, d_o2n, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
             }
@@ -671,7 +707,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             if ((r = dalloc(ctx, &ctx->S.qt, nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[0], nb))) return r;
             if ((r = dalloc(ctx, &ctx->inf[1], nb))) return r;
-            if (ctx->relabel && (g->rand_mean > 0.0f || g->rand_ws) && n_rep == 1) {
+            if (ctx->relabel && (poisson_on(g) || g->rand_ws) && n_rep == 1) {
                 if ((r = dalloc(ctx, &ctx->inf_rand[0], nb))) return r;
                 if ((r = dalloc(ctx, &ctx->inf_rand[1], nb))) return r;
             }
@@ -776,17 +812,7 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             // host-side integer tables (thresholds are exact: p * 2^32 then floor)
             Tables T;
             std::memset(&T, 0, sizeof T);
-            {
-                // Poisson CDF: t_0 = exp(-m), t_k = (t_{k-1} * m) / k, c_k = c_{k-1} + t_k
-                const double m = (double)g->rand_mean;
-                volatile double t = std::exp(-m), c = t;
-                T.pois[0] = threshold(c);
-                for (int k = 1; k < DEABM_POIS_CAP; ++k) {
-                    t = (t * m) / (double)k;
-                    c = c + t;
-                    T.pois[k] = threshold(c);
-                }
-            }
+            poisson_tables(g, T);
             for (int q = 0; q < DEABM_N_AGE; ++q) {
                 T.thr_asym[q] = threshold(p->p_asym[q]);
                 T.thr_sev[q] = threshold(p->p_sev[q]);
@@ -831,7 +857,8 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
             K.n_rep = n_rep;
             K.inf_len = p->inf_len;
             K.dt = p->dt;
-            K.rand_on = (g->rand_mean > 0.0f && !g->rand_ws) ? 1u : 0u;
+            K.rand_on = poisson_on(g) ? 1u : 0u;
+            K.rand_by_age = g->rand_by_age ? 1u : 0u;
             if (g->rand_ws) {  // the day's Watts-Strogatz random network, rebuilt before each day kernel
                 K.wsg_on = 1;
                 K.wsg_h = g->rand_ws_k / 2u;
@@ -1317,7 +1344,8 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.n_rep = 1;
             K.inf_len = p.inf_len;
             K.dt = p.dt;
-            K.rand_on = g.rand_mean > 0.0f ? 1u : 0u;
+            K.rand_on = poisson_on(&g) ? 1u : 0u;
+            K.rand_by_age = g.rand_by_age ? 1u : 0u;
             // the population's stored networks; renumbered on the device like a
             // plain context's when locality_order asks for it, or in occupation
             // order (members of an occupation adjacent) when it draws daily
@@ -1413,16 +1441,7 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             // tables of this population
             Tables T;
             std::memset(&T, 0, sizeof T);
-            {
-                const double m = (double)g.rand_mean;
-                volatile double t = std::exp(-m), c = t;
-                T.pois[0] = threshold(c);
-                for (int k = 1; k < DEABM_POIS_CAP; ++k) {
-                    t = (t * m) / (double)k;
-                    c = c + t;
-                    T.pois[k] = threshold(c);
-                }
-            }
+            poisson_tables(&g, T);
             for (int a2 = 0; a2 < DEABM_N_AGE; ++a2) {
                 T.thr_asym[a2] = threshold(p.p_asym[a2]);
                 T.thr_sev[a2] = threshold(p.p_sev[a2]);

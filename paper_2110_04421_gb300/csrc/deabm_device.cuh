@@ -86,6 +86,7 @@ __device__ __forceinline__ uint32_t uniform_int(uint32_t w, uint32_t lo, uint32_
 struct Tables {
     float infT[DEABM_N_CLASS][DEABM_MAX_INF_LEN];  // A_class folded in: A_c * infT_c[t]
     uint64_t pois[DEABM_POIS_CAP];
+    uint64_t pois_age[DEABM_N_AGE][DEABM_POIS_CAP];  // rand_by_age: the thresholds of each age bin's mean
     uint64_t thr_asym[DEABM_N_AGE], thr_sev[DEABM_N_AGE];
     uint64_t thr_branch[8][DEABM_N_AGE];   // by stage: SEV->HOSP, HOSP->ICU, ICU->DEAD
     uint8_t dur_lo[8][DEABM_N_AGE], dur_hi[8][DEABM_N_AGE];
@@ -151,6 +152,7 @@ struct KParams {
     // thresholds from index pois_fin on are 2^32, which no word reaches.
     uint32_t pois32[DEABM_POIS_CAP];
     uint32_t pois_fin;
+    uint32_t rand_by_age;  // 1: agent j's count from tab->pois_age[age_j] (age-stratified means)
     uint32_t nrk[20];  // Philox round keys of net_seed (philox_rk)
     // replicate 0's parameters by value: plain contexts read them from the
     // kernel's parameter space (uniform across the grid) instead of through `rep`
@@ -175,8 +177,14 @@ struct KParams {
 #ifndef DEABM_POIS32
 #define DEABM_POIS32 1
 #endif
-__device__ __forceinline__ uint32_t poisson_count(const KParams &P, uint32_t w)
+__device__ __forceinline__ uint32_t poisson_count(const KParams &P, uint32_t w, int age)
 {
+    if (P.rand_by_age) {  // age-stratified means: the bin's thresholds from the table (L1)
+        const uint64_t *thr = P.tab->pois_age[age];
+        uint32_t c = 0;
+        while (c < DEABM_POIS_CAP && (uint64_t)w >= __ldg(thr + c)) ++c;
+        return c;
+    }
 #if !DEABM_POIS32
     uint32_t c = 0;
     while (c < DEABM_POIS_CAP && (uint64_t)w >= __ldg(&P.tab->pois[c])) ++c;

@@ -150,7 +150,8 @@ __device__ uint32_t den_day_contacts(const KParams &P, uint32_t j, uint32_t jo, 
     uint32_t k_rand = 0, k_occ = 0;
     if (P.rand_on) {
         uint4 w = draw(nk, jo, d, kStreamRnet, 0u);
-        while (k_rand < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[k_rand])) ++k_rand;
+        const uint64_t *thr = P.rand_by_age ? P.tab->pois_age[__ldg(P.age + j)] : P.tab->pois;
+        while (k_rand < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(thr + k_rand)) ++k_rand;
         const uint64_t nm1 = (uint64_t)(P.n - 1u);
         for (uint32_t e = 0; e < k_rand; ++e) {
             const uint32_t idx = e + 1u;

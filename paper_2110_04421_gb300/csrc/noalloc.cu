@@ -116,6 +116,8 @@ extern "C" int deabm_lambda_noalloc(const deabm_graph *graph_dev, const uint8_t 
         return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: daily occupation networks need a context (n_occ must be 0)");
     if (graph_dev->rand_ws)
         return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: the Watts-Strogatz random network needs a context (rand_ws must be 0)");
+    if (graph_dev->rand_by_age)
+        return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: age-stratified random means need a context (rand_by_age must be 0)");
     for (uint32_t k = 0; k < graph_dev->n_nets; ++k)
         if (!graph_dev->row_ptr[k] || !graph_dev->col[k])
             return na_fail(DEABM_EINVAL, "deabm_lambda_noalloc: network %u has a NULL array", k);

@@ -36,6 +36,7 @@ constexpr int kTheta = DEABM_N_THETA;
 
 struct RxParams {
     uint32_t n, n_nets, L, rand_on, T, nblk;
+    uint32_t rand_by_age;  // 1: agent j's random-contact count from tab->pois_age[age_j]
     uint32_t nh;  // per-day H slots: the stored networks, the occupation term (n_occ > 0), the random network
     // daily occupation networks (n_occ = 0: none), by agent id: occupation, place
     // among its members; members of occupation g in ascending id at
@@ -93,6 +94,12 @@ __device__ __forceinline__ void rx_occ_for(const RxParams &P, uint32_t j, uint32
         }
         f(__ldg(P.occ_members + beg + r));
     }
+}
+
+// the Poisson thresholds of agent j's daily random-contact count
+__device__ __forceinline__ const uint64_t *rx_pois(const RxParams &P, uint32_t j)
+{
+    return P.rand_by_age ? P.tab->pois_age[P.age[j]] : P.tab->pois;
 }
 
 __device__ __forceinline__ float sigmoidf_(float z)
@@ -187,8 +194,9 @@ __global__ void __launch_bounds__(kRxBlock) rx_day_kernel(const RxParams P, int 
         if (P.rand_on) {
             const uint2 nk = seed_key(P.net_seed);
             uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+            const uint64_t *thr = rx_pois(P, j);
             uint32_t kk = 0;
-            while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+            while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(thr + kk)) ++kk;
             for (uint32_t e = 0; e < kk; ++e) {
                 const uint32_t idx = e + 1u;
                 if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
@@ -288,8 +296,9 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
                 const float cfr = cf * P.theta[3];
                 const uint2 nk = seed_key(P.net_seed);
                 uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+                const uint64_t *thr = rx_pois(P, j);
                 uint32_t kk = 0;
-                while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+                while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(thr + kk)) ++kk;
                 for (uint32_t e = 0; e < kk; ++e) {
                     const uint32_t idx = e + 1u;
                     if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
@@ -469,8 +478,9 @@ __global__ void __launch_bounds__(256) rxb_day_kernel(const RxParams P, RxbArray
         if (P.rand_on) {
             const uint2 nk = seed_key(P.net_seed);
             uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+            const uint64_t *thr = rx_pois(P, j);
             uint32_t kk = 0;
-            while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+            while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(thr + kk)) ++kk;
             for (uint32_t e = 0; e < kk; ++e) {
                 const uint32_t idx = e + 1u;
                 if ((idx & 3u) == 0u) w = draw(nk, j, (uint32_t)t, kStreamRnet, idx >> 2);
@@ -611,8 +621,9 @@ __global__ void rxb_scatter_random_kernel(const RxParams P, RxbArrays A, int t)
     if (cf == 0.0f) return;
     const uint2 nk = seed_key(P.net_seed);
     uint4 w = draw(nk, j, (uint32_t)t, kStreamRnet, 0u);
+    const uint64_t *thr = rx_pois(P, j);
     uint32_t kk = 0;
-    while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(&P.tab->pois[kk])) ++kk;
+    while (kk < DEABM_POIS_CAP && (uint64_t)w.x >= __ldg(thr + kk)) ++kk;
     float *dst = A.ibring + (size_t)((uint32_t)t % P.L) * P.n * A.B;
     for (uint32_t e = 0; e < kk; ++e) {
         const uint32_t idx = e + 1u;
@@ -752,7 +763,13 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
     if (p->den_on) return rx_fail(DEABM_EINVAL, "exposure notification is not available in the relaxed model");
     if (max_days == 0 || ckpt_every == 0) return rx_fail(DEABM_EINVAL, "max_days and ckpt_every must be >= 1");
     if (p->inf_len < 2 || p->inf_len > DEABM_MAX_INF_LEN) return rx_fail(DEABM_EINVAL, "inf_len must be 2..64");
-    if (g->rand_mean > 0.0f && n < 2) return rx_fail(DEABM_EINVAL, "the random network needs >= 2 agents");
+    if (g->rand_ws) return rx_fail(DEABM_EINVAL, "the relaxed model uses the Poisson random network (rand_ws must be 0)");
+    if (g->rand_by_age > 1) return rx_fail(DEABM_EINVAL, "rand_by_age must be 0 or 1");
+    if (g->rand_by_age)
+        for (int q = 0; q < DEABM_N_AGE; ++q)
+            if (!(g->rand_mean_age[q] >= 0.0f) || g->rand_mean_age[q] > 1e3f)
+                return rx_fail(DEABM_EINVAL, "rand_mean_age[%d] out of range", q);
+    if ((g->rand_mean > 0.0f || g->rand_by_age) && n < 2) return rx_fail(DEABM_EINVAL, "the random network needs >= 2 agents");
     for (uint32_t k = 0; k < g->n_nets; ++k) {
         const uint32_t *rp = g->row_ptr[k];
         if (!rp || rp[0] != 0 || (rp[n] && !g->col[k])) return rx_fail(DEABM_EINVAL, "bad CSR %u", k);
@@ -783,7 +800,12 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
         P.n = n;
         P.n_nets = g->n_nets;
         P.L = p->inf_len;
+        P.rand_by_age = g->rand_by_age ? 1u : 0u;
         P.rand_on = g->rand_mean > 0.0f;
+        if (g->rand_by_age) {
+            P.rand_on = 0;
+            for (int q = 0; q < DEABM_N_AGE; ++q) P.rand_on |= g->rand_mean_age[q] > 0.0f ? 1u : 0u;
+        }
         P.nblk = nblk;
         P.tau = tau;
         P.inv_Ibar = p->inv_Ibar;
@@ -859,14 +881,15 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
         P.cls = cls;
         Tables T;
         std::memset(&T, 0, sizeof T);
-        {
-            const double m = (double)g->rand_mean;
+        for (int a = -1; a < DEABM_N_AGE; ++a) {  // the single mean (a = -1), then each age bin's
+            const double m = a < 0 || !g->rand_by_age ? (double)g->rand_mean : (double)g->rand_mean_age[a];
+            uint64_t *thr = a < 0 ? T.pois : T.pois_age[a];
             volatile double t = std::exp(-m), cdf = t;
-            T.pois[0] = rx_threshold(cdf);
+            thr[0] = rx_threshold(cdf);
             for (int k = 1; k < DEABM_POIS_CAP; ++k) {
                 t = (t * m) / (double)k;
                 cdf = cdf + t;
-                T.pois[k] = rx_threshold(cdf);
+                thr[k] = rx_threshold(cdf);
             }
         }
         for (int q = 0; q < DEABM_N_AGE; ++q) {

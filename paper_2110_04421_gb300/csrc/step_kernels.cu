@@ -79,7 +79,7 @@ __device__ __forceinline__ void agent_day(const KParams &P, const Rep &rp, uint3
     RowBounds rb = {};
     if (full) rb = row_bounds(P, j);
     RandBlock0 r0{make_uint4(0u, 0u, 0u, 0u), 0u};
-    if (P.rand_on) r0 = random_block0<RK>(P, jo, day);
+    if (P.rand_on) r0 = random_block0<RK>(P, jo, day, age);
     float lam = 0.0f;
     if (full) {
         lam = lambda_at<OCC, DEN, ROWMAP, WSG, RK>(P, rp, I, j, jo, day, stride, b, age, rb, r0, k_out, rec);
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(256, DEABM_B4_MINB) step_batch4_kernel(const K
         }
         if (P.rand_on) {
             uint4 w = draw_rk(P.nrk, jo, day, kStreamRnet, 0u);
-            const uint32_t kr = poisson_count(P, w.x);
+            const uint32_t kr = poisson_count(P, w.x, age);
             float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const uint64_t nm1 = (uint64_t)(P.n - 1u);
             const float *panel = I.row_of ? I.cur : I.rand_cur;

@@ -44,7 +44,8 @@ class Graph(C.Structure):
                 ("rand_mean", C.c_float),
                 ("n_occ", C.c_uint32), ("occ_group", C.c_void_p), ("occ_k", C.c_void_p),
                 ("occ_lattice", C.c_uint32), ("occ_rewire", C.c_float),
-                ("rand_ws", C.c_uint32), ("rand_ws_k", C.c_uint32), ("rand_ws_beta", C.c_float)]
+                ("rand_ws", C.c_uint32), ("rand_ws_k", C.c_uint32), ("rand_ws_beta", C.c_float),
+                ("rand_by_age", C.c_uint32), ("rand_mean_age", C.c_float * N_AGE)]
 
 
 class Agents(C.Structure):
@@ -213,7 +214,7 @@ def make_params(P: dict, max_steps: int = 1024, keep_lambda: bool = False, local
     return p
 
 
-def _graph_struct(graph: dict, rand_mean: float, keep: list) -> Graph:
+def _graph_struct(graph: dict, rand_mean: float, keep: list, rand_mean_age=None) -> Graph:
     g = Graph()
     g.n_agents = int(graph["n"])
     g.n_nets = len(graph["row_ptr"])
@@ -224,6 +225,10 @@ def _graph_struct(graph: dict, rand_mean: float, keep: list) -> Graph:
         g.row_ptr[i] = rp.ctypes.data
         g.col[i] = cl.ctypes.data if cl.size else None
     g.rand_mean = rand_mean
+    if rand_mean_age is not None:  # age-stratified Poisson means of the random network
+        g.rand_by_age = 1
+        for a in range(N_AGE):
+            g.rand_mean_age[a] = float(rand_mean_age[a])
     if graph.get("occ_group") is not None:  # daily occupation networks
         og = np.ascontiguousarray(graph["occ_group"], dtype=np.uint32)
         ok = np.ascontiguousarray(graph["occ_k"], dtype=np.uint8)
@@ -259,7 +264,7 @@ class Relaxed:
                  ckpt_every: int = 10, stream=None):
         L = lib()
         keep = []
-        g = _graph_struct(graph, params["rand_mean"], keep)
+        g = _graph_struct(graph, params["rand_mean"], keep, params.get("rand_mean_age"))
         a = Agents()
         age = np.ascontiguousarray(age, dtype=np.uint8)
         keep.append(age)
@@ -359,7 +364,7 @@ class RaggedSimulation:
         ag = (Agents * n)()
         ps = (Params * n)()
         for q, (pop, par) in enumerate(zip(pops, params)):
-            gs[q] = _graph_struct(pop, par["rand_mean"], keep)
+            gs[q] = _graph_struct(pop, par["rand_mean"], keep, par.get("rand_mean_age"))
             age = np.ascontiguousarray(pop["age"], dtype=np.uint8)
             keep.append(age)
             ag[q].age_bin = age.ctypes.data
@@ -450,7 +455,7 @@ class Simulation:
         self.n = int(graph["n"])
         self.n_rep = int(n_rep)
         keep = []
-        g = _graph_struct(graph, params["rand_mean"], keep)
+        g = _graph_struct(graph, params["rand_mean"], keep, params.get("rand_mean_age"))
         a = Agents()
         age = np.ascontiguousarray(age, dtype=np.uint8)
         keep.append(age)
