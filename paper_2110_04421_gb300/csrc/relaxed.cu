@@ -262,9 +262,16 @@ __global__ void rx_loss_kernel(const RxParams P, uint32_t T, const float *Ipart,
 
 // reverse of day t: d loss / d x, d loss / d lambda, the susceptible-mass adjoint,
 // each agent's coefficient for the transpose scatter and the parameter partials
+// One launch per reverse day t.  First this agent's d loss / d inf(t+1) is
+// completed with the stored networks' part: a gather along the transpose CSR of
+// the coefficients of day t+1 (coef_next, all written by the previous launch),
+// added to what the generated networks scattered into that slot; then the
+// adjoint of day t reads the agent's own slots t+1 .. t+L-1, clears slot t-1
+// (slot t+L-1, just read) for the next launch's scatters, and writes coef(t).
 __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int t, int k, const float *__restrict__ Ibar,
                                                           float *__restrict__ ibring, float *__restrict__ sbar,
-                                                          float *__restrict__ coef, RxSeg seg, double *gpart)
+                                                          float *__restrict__ coef, const float *__restrict__ coef_next,
+                                                          RxSeg seg, double *gpart)
 {
     __shared__ float red[kTheta][kRxBlock / 32];
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,9 +280,20 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
     for (int q = 0; q < kTheta; ++q) contrib[q] = 0.0f;
     if (j < P.n) {
         const int c = P.cls[j], a = P.age[j];
+        if ((uint32_t)t + 1u < P.T) {
+            float v = 0.0f;
+            for (uint32_t net = 0; net < P.n_nets; ++net) {
+                float h = 0.0f;
+                for (uint32_t e = __ldg(P.tr_ptr[net] + j); e < __ldg(P.tr_ptr[net] + j + 1); ++e)
+                    h += __ldg(coef_next + __ldg(P.tr_col[net] + e));
+                v += rx_weight(P, net) * h;
+            }
+            ibring[(size_t)(((uint32_t)t + 1u) % P.L) * P.n + j] += v;
+        }
         float xbar = Ibar[t] - sbar[j];
         for (uint32_t d = 1; d < P.L && (uint32_t)t + d < P.T; ++d)
             xbar += __ldg(&P.tab->infT[c][d]) * ibring[(size_t)(((uint32_t)t + d) % P.L) * P.n + j];
+        ibring[(size_t)(((uint32_t)t + P.L - 1u) % P.L) * P.n + j] = 0.0f;
         const size_t q = (size_t)k * P.n + j;
         const float g = seg.g[q], lam = seg.lam[q], sj = seg.s[q];
         const float gbar = xbar * sj;
@@ -288,8 +306,8 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
         coef[j] = cf;
         // d loss / d inf_i(t) along the day's generated networks: this destination
         // regenerates its random and occupation contacts and adds to theirs
-        // (atomics; the slot was cleared after the day above it read it, and the
-        // stored networks' gathers add to it afterwards)
+        // (atomics; the slot was cleared by the launch of day t+1, and the stored
+        // networks' gathers are added to it by the launch of day t-1)
         if (cf != 0.0f) {
             float *dst = ibring + (size_t)((uint32_t)t % P.L) * P.n;
             if (P.rand_on) {
@@ -338,25 +356,6 @@ __global__ void __launch_bounds__(kRxBlock) rx_adj_kernel(const RxParams P, int 
         for (uint32_t w = 0; w < kRxBlock / 32; ++w) b += red[threadIdx.x][w];
         gpart[(size_t)blockIdx.x * kTheta + threadIdx.x] += b;
     }
-}
-
-// d loss / d inf_i(t) over the static networks: gather along the transpose CSR,
-// added to what the day's generated networks scattered in; then the slot of
-// day t-1 (day t-1+L's, last read by the reverse day just run) is cleared for
-// the next reverse day's scatters
-__global__ void rx_scatter_static_kernel(const RxParams P, int t, const float *__restrict__ coef, float *__restrict__ ibring)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    float v = 0.0f;
-    for (uint32_t net = 0; net < P.n_nets; ++net) {
-        float h = 0.0f;
-        for (uint32_t e = __ldg(P.tr_ptr[net] + i); e < __ldg(P.tr_ptr[net] + i + 1); ++e)
-            h += __ldg(coef + __ldg(P.tr_col[net] + e));
-        v += rx_weight(P, net) * h;
-    }
-    ibring[(size_t)((uint32_t)t % P.L) * P.n + i] += v;
-    ibring[(size_t)(((uint32_t)t + P.L - 1u) % P.L) * P.n + i] = 0.0f;
 }
 
 __global__ void rx_grad_reduce_kernel(const RxParams P, const double *gpart, float *grad)
@@ -933,7 +932,7 @@ extern "C" int deabm_relaxed_create(const deabm_graph *g, const deabm_agents *a,
         if ((r = rx_alloc(c, &c->loss, 1))) return r;
         if ((r = rx_alloc(c, &c->ibring, L * n))) return r;
         if ((r = rx_alloc(c, &c->sbar, n))) return r;
-        if ((r = rx_alloc(c, &c->coef, n))) return r;
+        if ((r = rx_alloc(c, &c->coef, 2 * (size_t)n))) return r;  // coef(t) and coef(t+1)
         if ((r = rx_alloc(c, &c->gpart, (size_t)nblk * kTheta))) return r;
         c->n_seeds = a->n_seed;
         if ((r = rx_alloc(c, &c->seeds, a->n_seed))) return r;
@@ -993,12 +992,12 @@ static int rx_backward_device(deabm_relaxed *c, uint32_t T)
         for (uint32_t t = t0; t < t1; ++t)  // recompute the segment, recording it
             rx_day_kernel<true><<<nb, kRxBlock, 0, s>>>(P, (int)t, (int)(t - t0), c->inf + (size_t)(t & 1u) * n, c->s,
                                                        c->xring, c->seg, c->Ipart, c->inf + (size_t)((t + 1u) & 1u) * n);
-        // each reverse day: the adjoint with the generated networks' scatters, then
-        // the stored networks' gathers (two launches)
-        for (int t = (int)t1 - 1; t >= (int)t0; --t) {
-            rx_adj_kernel<<<nb, kRxBlock, 0, s>>>(P, t, t - (int)t0, c->Ibar, c->ibring, c->sbar, c->coef, c->seg, c->gpart);
-            rx_scatter_static_kernel<<<nb, kRxBlock, 0, s>>>(P, t, c->coef, c->ibring);
-        }
+        // one launch per reverse day (the stored networks' part of day t+1, the
+        // adjoint of day t with the generated networks' scatters)
+        for (int t = (int)t1 - 1; t >= (int)t0; --t)
+            rx_adj_kernel<<<nb, kRxBlock, 0, s>>>(P, t, t - (int)t0, c->Ibar, c->ibring, c->sbar,
+                                                  c->coef + (size_t)(t & 1) * n, c->coef + (size_t)((t + 1) & 1) * n,
+                                                  c->seg, c->gpart);
     }
     rx_grad_reduce_kernel<<<1, 32, 0, s>>>(P, c->gpart, c->grad);
     RCU(cudaGetLastError());
