@@ -152,7 +152,6 @@ struct KParams {
     // thresholds from index pois_fin on are 2^32, which no word reaches.
     uint32_t pois32[DEABM_POIS_CAP];
     uint32_t pois_fin;
-    uint32_t rand_by_age;  // 1: agent j's count from tab->pois_age[age_j] (age-stratified means)
     uint32_t nrk[20];  // Philox round keys of net_seed (philox_rk)
     // replicate 0's parameters by value: plain contexts read them from the
     // kernel's parameter space (uniform across the grid) instead of through `rep`
@@ -167,6 +166,7 @@ struct KParams {
     const uint8_t *wsg_rew;
     const uint32_t *wsg_start;
     const uint32_t *wsg_land;
+    uint32_t rand_by_age;  // 1: agent j's random-contact count from tab->pois_age[age_j] (age-stratified means)
 };
 
 // K_j of the random network from word 0 of its block 0: the number of Poisson
