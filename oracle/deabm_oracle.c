@@ -378,6 +378,21 @@ static uint32_t wsg_neighbours(const or_model *m, const or_wsg *g, uint32_t j, u
     return k;
 }
 
+/* is one of agent j's neighbours marked in src? */
+static int wsg_any(const or_model *m, const or_wsg *g, uint32_t j, const uint8_t *src)
+{
+    const uint32_t n = m->n, h = g->h;
+    for (uint32_t e = 1; e <= h; ++e)
+        if (src[g->far[(size_t)j * h + (e - 1u)]]) return 1;
+    for (uint32_t e = 1; e <= h; ++e) {
+        const uint32_t i = (uint32_t)(((uint64_t)j + (uint64_t)n - (e % n)) % n);
+        if (!g->rew[(size_t)i * h + (e - 1u)] && src[i]) return 1;
+    }
+    for (uint32_t q = g->start[j]; q < g->start[j + 1u]; ++q)
+        if (src[g->land[q]]) return 1;
+    return 0;
+}
+
 /* the sums of inf over agent j's neighbours in summation order (FP32 left to
  * right from +0, FP64 alongside); returns their number */
 static uint32_t wsg_sum(const or_model *m, const or_wsg *g, uint32_t j, const float *inf32, const double *inf64,
@@ -528,7 +543,7 @@ static int check_model(const or_model *m)
     if (m->rand_by_age)
         for (int a = 0; a < OR_N_AGE; ++a)
             if (!(m->rand_mean_age[a] >= 0.0f)) return -1;
-    if (m->rand_ws && (m->rand_ws_k < 2u || m->rand_ws_k > 16u || m->rand_ws_k % 2u || m->n < 2u || m->den_on ||
+    if (m->rand_ws && (m->rand_ws_k < 2u || m->rand_ws_k > 16u || m->rand_ws_k % 2u || m->n < 2u ||
                        !(m->rand_ws_beta >= 0.0 && m->rand_ws_beta <= 1.0)))
         return -1;
     if (m->vax_strategy > 3 || m->elderly_bin > 9) return -1;
@@ -916,6 +931,14 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
      * result this step and holds the app; it complies with probability
      * den_compliance and is then tested on the next step. */
     int32_t n_notified = 0;
+    /* with the Watts-Strogatz random network, the graphs of the window's steps
+     * (an agent's in-contacts there are its neighbours, the edges being undirected) */
+    const uint32_t dw0 = t + 1u > m->den_window ? t + 1u - m->den_window : 0u;
+    or_wsg *dwsg = NULL;
+    if (den_src && m->rand_ws) {
+        dwsg = (or_wsg *)calloc(t - dw0 + 1u, sizeof(or_wsg));
+        for (uint32_t d = dw0; d <= t; ++d) wsg_build(m, d, &dwsg[d - dw0]);
+    }
     if (den_src) {
 #pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : n_notified)
         for (uint32_t j = 0; j < n; ++j) {
@@ -938,6 +961,7 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
                     k = random_contacts(m->net_seed, n, j, d, pois_of(m, tb, age[j]), contacts);
                     for (uint32_t e = 0; e < k && !hit; ++e) hit = den_src[contacts[e]];
                 }
+                if (m->rand_ws && !hit) hit = wsg_any(m, &dwsg[d - d0], j, den_src);
             }
             if (!hit) continue;
             ++n_notified;
@@ -946,6 +970,10 @@ static int step_impl(const or_model *m, const or_tables *tb, const uint8_t *age,
             if (happens(w[0], m->den_compliance)) flags[j] |= FL_DEN;
         }
         free(den_src);
+    }
+    if (dwsg) {
+        for (uint32_t d = dw0; d <= t; ++d) wsg_free(&dwsg[d - dw0]);
+        free(dwsg);
     }
 
     if (dg) {

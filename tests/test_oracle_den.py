@@ -130,6 +130,37 @@ def test_look_back_window_over_random_contacts(window):
     assert len(want) >= window  # about 2 * window on average
 
 
+@pytest.mark.parametrize("window", [7, 2])
+def test_look_back_window_over_the_watts_strogatz_graphs(window):
+    """With the global random network as a daily Watts-Strogatz graph (edges
+    undirected: an agent's in-contacts are its neighbours), the notified set is
+    exactly the app holders that were the positive agent's neighbour in the graph
+    of one of the last den_window steps (each step's graph listed by the oracle's
+    own neighbour lists)."""
+    n, t_pos = 500, 8
+    g = dict(n=n, row_ptr=[], col=[], rand_ws=1, rand_ws_k=4, rand_ws_beta=0.5)
+    p = den_params(den_window=window, net_seed=23, seed=6)
+    s = oracle.Sim(g, p, np.zeros(n, np.uint8))
+    for _ in range(t_pos):
+        s.step(diag=False)
+    st = s.state
+    src = 41
+    st.stage[src], st.timer[src], st.tinf[src] = MILD, 9, 4
+    st.flags[src] |= FL_POS
+    st.qt[src] = qt(0, 1)
+    st.qt[7] = qt(5, 0)                 # one agent in quarantine
+    d = s.step()
+    want = set()
+    for day in range(max(0, t_pos - window + 1), t_pos + 1):
+        start, nb = s.model.ws_neighbours(day)
+        for j in range(n):
+            if j not in (src, 7) and src in nb[start[j]:start[j + 1]].tolist():
+                want.add(j)
+    got = {j for j in range(n) if st.flags[j] & FL_DEN}
+    assert got == want and d["den_notified"] == len(want)
+    assert len(want) >= 4
+
+
 def test_compliance_share():
     L = 4000
     g = star_graph(L)
