@@ -520,9 +520,11 @@ typedef struct {
     uint64_t pois_age[OR_N_AGE][OR_POIS_CAP];  /* rand_by_age: thresholds of each age bin's mean */
 } or_tables;
 
-/* is the Poisson random network on (some agent has a positive mean)? */
+/* is the Poisson random network on (some agent has a positive mean, and the
+ * network is not the Watts-Strogatz graph, which replaces it)? */
 static int rand_poisson_on(const or_model *m)
 {
+    if (m->rand_ws) return 0;
     if (!m->rand_by_age) return m->rand_mean > 0.0f;
     for (int a = 0; a < OR_N_AGE; ++a)
         if (m->rand_mean_age[a] > 0.0f) return 1;
