@@ -125,9 +125,11 @@ typedef struct deabm_ctx deabm_ctx;
  * edges of agents j - m, m = 1..k/2, then the rewired edges that landed on j by
  * owner ascending and m ascending.  Plain and batched contexts (the graph,
  * keyed by net_seed, is shared by every replicate column; a batched context
- * then runs the general panel kernel), without exposure notification, not in
- * ragged batches; the day's graph is built on the device before each day kernel
- * (three small kernels and a prefix sum).
+ * then runs the general panel kernel), not in ragged batches; the day's graph is
+ * built on the device before each day kernel (three small kernels and a prefix
+ * sum).  With exposure notification an agent's in-contacts in this network are
+ * its neighbours (the edges are undirected), and the graphs of the last
+ * den_window days are kept for the look-back.
  */
 typedef struct {
     uint32_t n_agents;
@@ -223,7 +225,7 @@ typedef struct {
                                 array the ABI returns are unchanged (random draws and outputs use
                                 the caller's agent ids) */
     /* Digital exposure notification (Sec. 4.2); plain and batched contexts with
-     * test_on (not ragged batches, not with the Watts-Strogatz random network).
+     * test_on (not ragged batches).
      * At create (and reset) agent j gets DEABM_FL_APP when word x of Philox
      * stream 6 keyed (seed, j, day word 0xFFFFFFFD) is below floor(den_adoption
      * 2^32); in a batched context each replicate column draws its own app holders

@@ -355,7 +355,6 @@ static int validate(deabm_ctx *ctx, const deabm_graph *g, const deabm_agents *a,
         if (n < 2) return fail(ctx, DEABM_EINVAL, "the random network needs >= 2 agents");
         if ((uint64_t)n * (g->rand_ws_k / 2) >= (1ull << 31))
             return fail(ctx, DEABM_EINVAL, "n_agents * rand_ws_k / 2 must be < 2^31");
-        if (p->den_on) return fail(ctx, DEABM_EINVAL, "the Watts-Strogatz random network excludes exposure notification");
     }
     using Firsts = RowFirsts;
     const std::vector<Firsts> found = scanned ? *scanned : scan_rows(g, a);
@@ -865,14 +864,20 @@ static int create_impl(const deabm_graph *g, const deabm_agents *a, const deabm_
                 K.thr_wsg = threshold((double)g->rand_ws_beta);
                 WsgBuffers &W = ctx->wsg;
                 const size_t edges = (size_t)n * K.wsg_h;
+                // with exposure notification the graphs of the look-back window are
+                // kept (a ring of den_window days), one day's otherwise
+                const uint32_t days_kept = p->den_on ? p->den_window : 1u;
                 if ((r = dalloc(ctx, &W.rew, n))) return r;
                 if ((r = dalloc(ctx, &W.far, edges))) return r;
-                if ((r = dalloc(ctx, &W.ends, (size_t)n + 3))) return r;
-                if ((r = dalloc(ctx, &W.land, edges))) return r;
+                if ((r = dalloc(ctx, &W.ends, ((size_t)n + 3) * days_kept))) return r;
+                if ((r = dalloc(ctx, &W.land, edges * days_kept))) return r;
                 if ((r = dalloc(ctx, &W.scratch, wsg_scratch_words(n)))) return r;
                 K.wsg_rew = W.rew;
                 K.wsg_start = W.ends + 2;
                 K.wsg_land = W.land;
+                K.wsg_ends_ring = W.ends;
+                K.wsg_land_ring = W.land;
+                K.wsg_ring_days = days_kept;
             }
             for (uint32_t k = 0; k < DEABM_MAX_NETS; ++k) {
                 K.row_ptr[k] = ctx->row_ptr[k];
@@ -969,6 +974,19 @@ extern "C" int deabm_create_batch(const deabm_graph *graph, const deabm_agents *
 }
 
 // ---------------------------------------------------------------- the day loop
+// The Watts-Strogatz graph of `day` built into its slot of the ring, and the
+// day kernel's view of it (kp.wsg_start, kp.wsg_land) pointed there.
+static cudaError_t wsg_day(deabm_ctx *ctx, KParams &kp, uint32_t day)
+{
+    const uint32_t slot = day % kp.wsg_ring_days;
+    WsgBuffers W = ctx->wsg;
+    W.ends += (size_t)slot * ((size_t)kp.n + 3);
+    W.land += (size_t)slot * kp.n * kp.wsg_h;
+    kp.wsg_start = W.ends + 2;
+    kp.wsg_land = W.land;
+    return launch_wsg_build(kp, day, W, ctx->stream);
+}
+
 extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
@@ -1005,7 +1023,7 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         I.row_of = ctx->row_of;
         if (kp.den_bits_orig)
             CU(ctx, cudaMemsetAsync(kp.den_bits_orig, 0, sizeof(uint32_t) * (((size_t)ctx->n + 31) / 32), ctx->stream));
-        if (kp.wsg_on) CU(ctx, launch_wsg_build(kp, ctx->day, ctx->wsg, ctx->stream));
+        if (kp.wsg_on) CU(ctx, wsg_day(ctx, kp, ctx->day));
         CU(ctx, launch_step(kp, ctx->day, I, ctx->S, ctx->C, ctx->keep_lambda ? ctx->lam : nullptr, ctx->p,
                             ctx->stream));
         if (kp.den_on) {
@@ -1737,6 +1755,11 @@ extern "C" int deabm_restore(deabm_ctx *ctx, const int8_t *stage, const int16_t 
         const uint32_t W = ctx->kp.den_window;
         // (batched contexts keep no records: their pass redraws the contacts)
         if (ctx->n_rep == 1) CU(ctx, launch_den_records(ctx->kp, day + 1u > W ? day + 1u - W : 0u, day, s));
+        if (ctx->kp.wsg_on)  // the Watts-Strogatz graphs of the look-back window's earlier days
+            for (uint32_t d = day + 1u > W ? day + 1u - W : 0u; d < day; ++d) {
+                KParams kd = ctx->kp;
+                CU(ctx, wsg_day(ctx, kd, d));
+            }
     }
     CU(ctx, cudaStreamSynchronize(s));  // host arrays and device scratch end here
     return DEABM_OK;

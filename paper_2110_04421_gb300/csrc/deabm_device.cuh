@@ -167,6 +167,13 @@ struct KParams {
     const uint32_t *wsg_start;
     const uint32_t *wsg_land;
     uint32_t rand_by_age;  // 1: agent j's random-contact count from tab->pois_age[age_j] (age-stratified means)
+    // with exposure notification, the Watts-Strogatz graphs of the last
+    // wsg_ring_days days (day d in slot d % wsg_ring_days): landing slot ends
+    // [slot][n + 3] (agent v's landings at [ends[v + 2], ends[v + 3]) of the slot's
+    // owners [slot][n wsg_h])
+    const uint32_t *wsg_ends_ring;
+    const uint32_t *wsg_land_ring;
+    uint32_t wsg_ring_days;
 };
 
 // K_j of the random network from word 0 of its block 0: the number of Poisson

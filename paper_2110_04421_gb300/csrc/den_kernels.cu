@@ -21,6 +21,36 @@ namespace deabm {
 
 __device__ __forceinline__ bool bit_of(const uint32_t *map, uint32_t x) { return (__ldg(map + (x >> 5)) >> (x & 31u)) & 1u; }
 
+// Agent jo's (caller id) neighbours in the Watts-Strogatz random network of day d
+// (edges undirected: its in-contacts): f(caller id) for each, returning true to
+// stop.  Its own edges' far ends and the unrewired lattice edges of the agents
+// jo - m come from Philox (stream 10), the rewired edges that landed on jo from
+// day d's slot of the kept graphs.  Returns whether f stopped the walk.
+template <class F>
+__device__ bool den_wsg_for(const KParams &P, uint32_t jo, uint32_t d, F f)
+{
+    const uint32_t n = P.n, h = P.wsg_h;
+    for (uint32_t m = 1; m <= h; m += 2u) {
+        const uint4 w = draw_rk(P.nrk, jo, d, kStreamWsg, (m - 1u) >> 1);
+        if (f(wsg_far(P, jo, m, w.x, w.y))) return true;
+        if (m + 1u <= h && f(wsg_far(P, jo, m + 1u, w.z, w.w))) return true;
+    }
+    for (uint32_t m = 1; m <= h; ++m) {
+        const uint32_t i = (uint32_t)(((uint64_t)jo + (uint64_t)n - (uint64_t)(m % n)) % n);
+        const uint4 w = draw_rk(P.nrk, i, d, kStreamWsg, (m - 1u) >> 1);
+        const uint32_t coin = ((m - 1u) & 1u) ? w.z : w.x;
+        const bool rewired = m % n == 0u || (uint64_t)coin < P.thr_wsg;
+        if (!rewired && f(i)) return true;
+    }
+    const uint32_t slot = d % P.wsg_ring_days;
+    const uint32_t *ends = P.wsg_ends_ring + (size_t)slot * ((size_t)n + 3u);
+    const uint32_t *land = P.wsg_land_ring + (size_t)slot * n * h;
+    const uint32_t s1 = __ldg(ends + jo + 3u);
+    for (uint32_t q = __ldg(ends + jo + 2u); q < s1; ++q)
+        if (f(__ldg(land + q))) return true;
+    return false;
+}
+
 // was any stored in-neighbour of row j a positive app holder today?  Each row
 // is taken in rounds of four edges: four column loads, then four bit lookups.
 __device__ __forceinline__ bool den_static_hit(const KParams &P, uint32_t j)
@@ -112,6 +142,12 @@ __global__ void __launch_bounds__(256, 8) den_kernel(const KParams P, uint32_t d
             bool hit = den_static_hit(P, j) || den_ring_eval(P, a, d0, first);
             for (uint32_t c0 = d0 + 4u; c0 <= day && !hit; c0 += 4u)
                 hit = den_ring_eval(P, a, c0, den_ring_load(P, a, c0, day + 1u));
+            if (P.wsg_on && !hit) {  // the Watts-Strogatz neighbours of the window's days
+                const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
+                const uint32_t *src_rand = P.den_bits_orig ? P.den_bits_orig : P.den_bits;
+                for (uint32_t d = d0; d <= day && !hit; ++d)
+                    hit = den_wsg_for(P, jo, d, [&](uint32_t v) { return bit_of(src_rand, v); });
+            }
             if (hit) {
                 notified = true;
                 const uint32_t jo = P.orig_id ? __ldg(P.orig_id + j) : j;
@@ -252,10 +288,16 @@ __global__ void __launch_bounds__(128) den_batch_kernel(const KParams P, uint32_
             for (uint32_t e = __ldg(P.row_ptr[net] + j) + g; e < e1; e += 8u) add(__ldg(P.col[net] + e));
         }
         const uint32_t d0 = day + 1u > P.den_window ? day + 1u - P.den_window : 0u;
-        for (uint32_t d = d0 + g; d <= day; d += 8u)
+        for (uint32_t d = d0 + g; d <= day; d += 8u) {
             (void)den_day_contacts(P, j, jo, d, [&](uint32_t kind, uint32_t, uint32_t v) {
                 add(kind || !row_of ? v : __ldg(row_of + v));
             });
+            if (P.wsg_on)  // the Watts-Strogatz neighbours (caller ids)
+                (void)den_wsg_for(P, jo, d, [&](uint32_t v) {
+                    add(row_of ? __ldg(row_of + v) : v);
+                    return false;
+                });
+        }
     }
     // (a row's eight lanes are an aligned eighth of one warp; rows past n add nothing)
 #pragma unroll

@@ -636,8 +636,7 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
 {
     if (P.n_rep == 1) {
         const dim3 grid((P.n + DEABM_PLAIN_BLOCK - 1u) / DEABM_PLAIN_BLOCK);
-        // the Watts-Strogatz random network excludes exposure notification (checked at create)
-        const int v = (P.wsg_on ? 8 : 0) | (lam_out ? 4 : 0) | (P.n_occ ? 2 : 0) | (P.den_on && !P.wsg_on ? 1 : 0);
+        const int v = (P.wsg_on ? 8 : 0) | (lam_out ? 4 : 0) | (P.n_occ ? 2 : 0) | (P.den_on ? 1 : 0);
         switch (v) {
 #define DEABM_PLAIN_CASE(c, K, O, D, W)                                                                      \
     case c: step_plain_kernel<K, O, D, W><<<grid, DEABM_PLAIN_BLOCK, 0, stream>>>(P, day, I, S, C, lam_out, p_out); break;
@@ -650,9 +649,13 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
             DEABM_PLAIN_CASE(6, true, true, false, false)
             DEABM_PLAIN_CASE(7, true, true, true, false)
             DEABM_PLAIN_CASE(8, false, false, false, true)
+            DEABM_PLAIN_CASE(9, false, false, true, true)
             DEABM_PLAIN_CASE(10, false, true, false, true)
+            DEABM_PLAIN_CASE(11, false, true, true, true)
             DEABM_PLAIN_CASE(12, true, false, false, true)
+            DEABM_PLAIN_CASE(13, true, false, true, true)
             DEABM_PLAIN_CASE(14, true, true, false, true)
+            DEABM_PLAIN_CASE(15, true, true, true, true)
 #undef DEABM_PLAIN_CASE
         }
     } else if (P.n_rep % kRepPerThread == 0 && P.vax_strategy == 0 && !P.wsg_on) {
@@ -669,10 +672,13 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
     } else {
         const dim3 grid((P.n + 7u) / 8u, (P.n_rep + 31u) / 32u);
         const dim3 block(32, 8);
-        if (P.wsg_on) {
+        if (P.wsg_on && P.den_on) {
+            if (lam_out) step_batch_kernel<true, true, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
+            else step_batch_kernel<false, true, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
+        } else if (P.wsg_on) {
             if (lam_out) step_batch_kernel<true, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
             else step_batch_kernel<false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
-        } else if (P.den_on) {  // (the Watts-Strogatz random network excludes exposure notification)
+        } else if (P.den_on) {
             if (lam_out) step_batch_kernel<true, false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, lam_out, p_out);
             else step_batch_kernel<false, false, true><<<grid, block, 0, stream>>>(P, day, I, S, C, nullptr, nullptr);
         } else {

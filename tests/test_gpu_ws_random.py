@@ -55,8 +55,6 @@ def test_watts_strogatz_rejected_where_not_built():
     with pytest.raises(DeabmError, match="rand_ws_k"):
         gpu_sim(pop, W.params_with())
     pop["rand_ws_k"] = 2
-    with pytest.raises(DeabmError, match="exposure notification"):
-        gpu_sim(pop, W.params_with(den_on=1, test_on=1))
     from paper_2110_04421_gb300.deabm import RaggedSimulation
     with pytest.raises(DeabmError, match="plain contexts"):
         RaggedSimulation([pop, W.population(1_500, 2, 5)], [W.params_with(), W.params_with()], max_steps=4)
@@ -102,3 +100,60 @@ def test_watts_strogatz_full_size_first_days():
     rep = compare_days(pop, w["params"], 4)
     assert rep["flips"] == 0 and rep["days"] == 4, rep
     assert rep["max_rel_lambda64"] <= 1e-5
+
+
+@pytest.mark.parametrize("locality_order", [True, False])
+def test_watts_strogatz_with_exposure_notification_matches_oracle(locality_order):
+    """Exposure notification over the Watts-Strogatz random network: an agent's
+    in-contacts there are its neighbours in each day's graph, and the graphs of the
+    7-day look-back are kept on the device.  Bit-exact against the oracle every
+    day (notified counts included), with and without the internal numbering."""
+    from tests.helpers import STATE_KEYS, oracle_sim
+    pop = dict(W.population(9_001, 7, 30), rand_ws=1, rand_ws_k=4, rand_ws_beta=0.3)
+    p = W.params_with(test_on=1, quar_on=1, den_on=1, den_adoption=0.5, den_compliance=0.9, R=3.5, seed=9,
+                      net_seed=10)
+    if locality_order:
+        rep = compare_days(pop, p, 45)
+        assert rep["flips"] == 0 and rep["days"] == 45, rep
+        assert sum(rep["notified"]) > 200
+        return
+    o = oracle_sim(pop, p)
+    g = gpu_sim(pop, p, keep_lambda=False, max_steps=45, locality_order=False)
+    ni, h = g.run(45)
+    s = g.state()
+    den = g.notified()
+    g.close()
+    ni_o, h_o, _ = o.run(45)
+    assert np.array_equal(ni[:, 0], ni_o) and np.array_equal(h[:, 0], h_o)
+    for k in STATE_KEYS:
+        assert np.array_equal(s[k], getattr(o.state, k)), k
+    assert den.tolist() == o.den_notified and sum(den) > 200
+
+
+def test_watts_strogatz_with_notification_in_batched_contexts_and_resumed():
+    """Batched columns with notification over the shared Watts-Strogatz graphs
+    equal the oracle's per-column runs; a plain run resumed from a checkpoint
+    (whose look-back graphs are rebuilt) equals the uninterrupted run."""
+    import oracle
+    from paper_2110_04421_gb300.deabm import Simulation
+    from tests.test_gpu_checkpoint import straight_and_split
+    T, B = 35, 6
+    pop = dict(W.population(5_003, 8, 30), rand_ws=1, rand_ws_k=2, rand_ws_beta=0.5)
+    base = W.params_with(test_on=1, quar_on=1, den_on=1, den_adoption=0.6, R=4.0, net_seed=19)
+    rp, seeds = W.batch_params(B, 5)
+    g = Simulation(pop, base, pop["age"], pop["seed_ids"], n_rep=B, rep_params=rp, rep_seeds=seeds, max_steps=T)
+    ni, _ = g.run(T)
+    st = g.state()
+    dn = g.notified()
+    g.close()
+    for c in range(B):
+        pc = dict(base, R=float(rp[c, 0]), B_net=[float(rp[c, 1]), float(rp[c, 2])], B_rand=float(rp[c, 3]),
+                  S_age=[float(x) for x in rp[c, 4:13]], dose2_delay=int(rp[c, 13]), seed=int(seeds[c]))
+        o = oracle.Sim(pop, pc, pop["age"], pop["seed_ids"])
+        o_ni, _, _ = o.run(T)
+        assert np.array_equal(ni[:, c], o_ni), c
+        assert np.array_equal(st["flags"][:, c], o.state.flags), c
+        assert dn[:, c].tolist() == o.den_notified, c
+    assert dn.sum() > 100
+    p = dict(base, seed=21)
+    straight_and_split(pop, p, 17, 15)
