@@ -153,6 +153,27 @@ def traffic_from_profile(sources, profile: str, units_per_launch: float, days=No
         return None
 
 
+def profile_value(sources, profile: str, key: str, days=None):
+    """A machine-readable number of a committed ncu summary (`key: value`), under
+    the same conditions as traffic_from_profile (current sources, captured inside
+    `days`); else None."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+        if f"source_sha256_16: {sources_hash(sources)}" not in txt:
+            return None
+        if days is not None:
+            d = re.search(r"captured_day:\s*([0-9]+)", txt)
+            if not d or not (days[0] <= int(d.group(1)) <= days[1]):
+                return None
+        m = re.search(key + r":\s*([0-9.eE+-]+)", txt)
+        return float(m.group(1)) if m else None
+    except Exception:
+        return None
+
+
+SMS, SMSP_PER_SM = 152, 4  # GB300: streaming multiprocessors, warp schedulers (one issue a cycle) each
+
+
 # ---------------------------------------------------------------------------------------- ours
 def rank_inputs(w: dict, rank: int):
     """Rank r's own problem: an independent population (seeded by r) with its own
@@ -291,6 +312,19 @@ def run_ours(args, rank, world, local):
         achieved = alg / (avg_ms / 1e3) / 1e9
         achieved_needed = alg_needed / (avg_ms / 1e3) / 1e9
         traffic = traffic_from_profile(DAY_KERNEL_SOURCES, "step_plain_n2e6.md", n, (Wm, Wm + K - 1))
+        # the issue-rate view of the same launches: warp-instructions a launch (ncu,
+        # same sources, a timed day) over the event-timed launch, against one issue
+        # a cycle per warp scheduler at the SM clock seen during the timed region
+        winst = profile_value(DAY_KERNEL_SOURCES, "step_plain_n2e6.md", "warp_instructions_per_launch",
+                              (Wm, Wm + K - 1))
+        sm_hz = 1e6 * float(clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0) if isinstance(clk, dict) else 2.07e9
+        issue = None
+        if winst:
+            issue_peak = SMS * SMSP_PER_SM * sm_hz
+            issue = {"achieved": winst / (avg_ms / 1e3), "peak": issue_peak, "unit": "warp-instructions/s",
+                     "frac": winst / (avg_ms / 1e3) / issue_peak, "warp_instructions_per_launch": winst,
+                     "note": "context for the HBM fraction: issued instructions (predicated-off and divergent "
+                             "lanes included), not algorithmic work"}
         cpu = None if args.no_cpu_baseline else cpu_baseline(pop, params, args.cpu_seconds)
         line = {
             "metric": "agent interactions/s on 1 GB300 (plain day kernel; batched B=256 in 'batched')",
@@ -313,7 +347,7 @@ def run_ours(args, rank, world, local):
                                      "alg_bytes_needed_mean on average (mean susceptible share "
                                      f"{statistics.mean(sus_days) / n:.3f} over the timed days): achieved_needed "
                                      "and frac_needed divide those bytes by the same time",
-                         "launch_ms_mean": avg_ms},
+                         "launch_ms_mean": avg_ms, "issue": issue},
             "e2e": None if args.no_e2e else {
                 "value": e2e_messages / e2e_s, "unit": "interactions/s", "h2d_bytes_per_step": h2d / KE,
                 "d2h_bytes_per_step": d2h / KE, "seconds": e2e_s, "days": f"0..{KE - 1}",
