@@ -125,9 +125,9 @@ typedef struct deabm_ctx deabm_ctx;
  * edges of agents j - m, m = 1..k/2, then the rewired edges that landed on j by
  * owner ascending and m ascending.  Plain and batched contexts (the graph,
  * keyed by net_seed, is shared by every replicate column; a batched context
- * then runs the general panel kernel), not in ragged batches; the day's graph is
- * built on the device before each day kernel (three small kernels and a prefix
- * sum).  With exposure notification an agent's in-contacts in this network are
+ * then runs the general panel kernel) and ragged batches (each population its
+ * own graph); the day's graph is built on the device before each day kernel
+ * (three small kernels and a prefix sum).  With exposure notification an agent's in-contacts in this network are
  * its neighbours (the edges are undirected), and the graphs of the last
  * den_window days are kept for the look-back.
  */
@@ -270,9 +270,12 @@ int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, con
 
 /* Create a ragged batch: n_pops independent populations of different sizes
  * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda, no
- * daily occupation networks, no exposure notification, no vaccination priority
- * strategy: DEABM_EINVAL otherwise) simulated together, one
- * kernel launch per day for all of them: resident thread blocks take tiles of
+ * exposure notification, no initial dose days under a priority strategy:
+ * DEABM_EINVAL otherwise) simulated together, one kernel launch per day for all
+ * of them (after the day's dose selection of each population under a vaccination
+ * priority strategy, Sec. 5 Table 1, and the day's graph of each population with
+ * a Watts-Strogatz random network: a few small launches per such population):
+ * resident thread blocks take tiles of
  * rows (never spanning two populations) from a per-day work queue.  A population
  * whose params ask for locality_order is numbered internally like a plain
  * context (its random contacts reach rows through a caller id -> row map).
@@ -313,7 +316,7 @@ int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf
 
 /* Days of each agent's first and second dose under a priority strategy
  * (host int16 [n_agents][n_rep] in caller order, 0x7FFF = none; either may be
- * NULL).  Synchronises. */
+ * NULL).  Not for ragged batches (DEABM_ESTATE).  Synchronises. */
 int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day);
 
 /* Per-day counters already run: days [0, day_count) of new infections

@@ -66,6 +66,8 @@ struct deabm_ctx {
     // ragged batch of populations (n_rep counts the populations for the counters)
     bool ragged = false;
     bool ragged_occ = false;  // some population of the ragged batch draws daily occupation contacts
+    bool ragged_wsg = false;  // some population of the ragged batch has a Watts-Strogatz random network
+    std::vector<std::pair<uint32_t, WsgBuffers>> ragged_wsg_bufs;  // (population, its day's graph)
     std::vector<PopDesc> pops;         // host copies, KParams pointers already offset
     PopDesc *d_pops = nullptr;
     Tile *d_tiles = nullptr;
@@ -80,6 +82,12 @@ struct deabm_ctx {
     uint8_t *vax_cls = nullptr, *vax_dose = nullptr;
     uint32_t *vax_scratch = nullptr;
     uint32_t vax_supply = 0;
+    // ragged batches: the populations under a priority strategy (their index,
+    // daily supply, first day, dose-2 delay and first "65+" bin)
+    struct RaggedVax {
+        uint32_t q, supply, start, delay, elderly;
+    };
+    std::vector<RaggedVax> ragged_vax;
     std::string err;
 };
 
@@ -974,6 +982,27 @@ extern "C" int deabm_create_batch(const deabm_graph *graph, const deabm_agents *
 }
 
 // ---------------------------------------------------------------- the day loop
+// One day of a ragged batch (infectiousness buffer c read): the day's dose
+// selection of each population under a priority strategy, then the day kernel.
+static cudaError_t ragged_day(deabm_ctx *ctx, uint32_t day, int c)
+{
+    for (const auto &rv : ctx->ragged_vax) {
+        if (day < rv.start) continue;
+        const PopDesc &pd = ctx->pops[rv.q];
+        StateRef Sp{ctx->S.stage + pd.base, ctx->S.timer + pd.base, ctx->S.tinf + pd.base,
+                    ctx->S.flags + pd.base, ctx->S.qt + pd.base, ctx->S.vd1 + pd.base, ctx->S.vd2 + pd.base};
+        cudaError_t e = launch_vax_select(pd.kp, day, rv.delay, rv.elderly, rv.supply, Sp, ctx->vax_cls + pd.base,
+                                          ctx->vax_dose + pd.base, ctx->vax_scratch, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    for (const auto &qw : ctx->ragged_wsg_bufs) {  // the day's Watts-Strogatz graph of each population that has one
+        cudaError_t e = launch_wsg_build(ctx->pops[qw.first].kp, day, qw.second, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, day, ctx->inf[c], ctx->inf[c ^ 1],
+                              ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ, ctx->ragged_wsg, ctx->stream);
+}
+
 // The Watts-Strogatz graph of `day` built into its slot of the ring, and the
 // day kernel's view of it (kp.wsg_start, kp.wsg_land) pointed there.
 static cudaError_t wsg_day(deabm_ctx *ctx, KParams &kp, uint32_t day)
@@ -994,10 +1023,7 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
         return fail(ctx, DEABM_ESTATE, "day %u + %u steps exceeds max_steps %u", ctx->day, n_steps, ctx->max_steps);
     if (ctx->ragged) {
         for (uint32_t q = 0; q < n_steps; ++q) {
-            const int c = ctx->cur;
-            CU(ctx, launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, ctx->day, ctx->inf[c],
-                                       ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ,
-                                       ctx->stream));
+            CU(ctx, ragged_day(ctx, ctx->day, ctx->cur));
             ctx->cur ^= 1;
             ctx->day += 1;
         }
@@ -1087,9 +1113,7 @@ static int run_ragged_graph(deabm_ctx *ctx, uint32_t T)
         CU(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         int c = cur0;
         for (uint32_t q = 0; q < T; ++q) {
-            cudaError_t e = launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, d0 + q, ctx->inf[c],
-                                               ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ,
-                                               ctx->stream);
+            cudaError_t e = ragged_day(ctx, d0 + q, c);
             if (e != cudaSuccess) {
                 cudaStreamEndCapture(ctx->stream, &g);
                 return fail(ctx, DEABM_ECUDA, "capture: %s", cudaGetErrorString(e));
@@ -1204,6 +1228,7 @@ extern "C" int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if (!ctx->S.vd1) return fail(ctx, DEABM_ESTATE, "no vaccination priority strategy in this context");
+    if (ctx->ragged) return fail(ctx, DEABM_ESTATE, "dose days are not read back from ragged batches");
     const uint32_t B = ctx->n_rep;
     const size_t nb = (size_t)ctx->n * B;
     std::vector<int16_t> t1(nb), t2(nb);
@@ -1287,12 +1312,10 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
-            if (graphs[q].rand_ws)
-                return fail(ctx, DEABM_EINVAL, "population %u: the Watts-Strogatz random network runs in plain contexts only", q);
             if (params[q].den_on)
                 return fail(ctx, DEABM_EINVAL, "exposure notification is not available for ragged batches");
-            if (params[q].vax_strategy)
-                return fail(ctx, DEABM_EINVAL, "vaccination priority strategies are not available for ragged batches");
+            if (params[q].vax_strategy && (agents[q].dose1_day || agents[q].dose2_day))
+                return fail(ctx, DEABM_EINVAL, "population %u: initial dose days are not taken in ragged batches", q);
         }
         if (total >= (1ull << 31)) return fail(ctx, DEABM_EINVAL, "too many agents in total");
         ctx->ragged = true;
@@ -1336,6 +1359,22 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         if ((r = dalloc(ctx, &ctx->queue, days))) return r;
         uint32_t max_n = 0;
         for (uint32_t q = 0; q < n_pops; ++q) max_n = std::max(max_n, graphs[q].n_agents);
+        bool any_strategy = false;
+        for (uint32_t q = 0; q < n_pops; ++q) any_strategy |= params[q].vax_strategy && params[q].vax_on;
+        if (any_strategy) {  // dose days (none yet), the day's classes and doses by caller id, selection scratch
+            StateRef *vsets[2] = {&ctx->S, &ctx->S0};
+            for (StateRef *st : vsets) {
+                if ((r = dalloc(ctx, &st->vd1, N))) return r;
+                if ((r = dalloc(ctx, &st->vd2, N))) return r;
+            }
+            if ((r = dalloc(ctx, &ctx->vax_cls, N))) return r;
+            if ((r = dalloc(ctx, &ctx->vax_dose, N))) return r;
+            if ((r = dalloc(ctx, &ctx->vax_scratch, vax_select_scratch_words(max_n)))) return r;
+            const std::vector<int16_t> never(N, kNever);
+            CU(ctx, cudaMemcpyAsync(ctx->S0.vd1, never.data(), N * 2, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S0.vd2, never.data(), N * 2, cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaStreamSynchronize(s));
+        }
         uint32_t *d_scratch;
         double *d_gamma;
         float *d_A;
@@ -1435,6 +1474,26 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             }
             K.net_seed = p.net_seed;
             round_keys(p.net_seed, K.nrk);
+            if (g.rand_ws) {  // its Watts-Strogatz random network, rebuilt before each day (by caller id)
+                WsgBuffers W{};
+                K.wsg_on = 1;
+                K.wsg_h = g.rand_ws_k / 2u;
+                K.thr_wsg = threshold((double)g.rand_ws_beta);
+                const size_t edges = (size_t)n * K.wsg_h;
+                if ((r = dalloc(ctx, &W.rew, n))) return r;
+                if ((r = dalloc(ctx, &W.far, edges))) return r;
+                if ((r = dalloc(ctx, &W.ends, (size_t)n + 3))) return r;
+                if ((r = dalloc(ctx, &W.land, edges))) return r;
+                if ((r = dalloc(ctx, &W.scratch, wsg_scratch_words(n)))) return r;
+                K.wsg_rew = W.rew;
+                K.wsg_start = W.ends + 2;
+                K.wsg_land = W.land;
+                K.wsg_ends_ring = W.ends;
+                K.wsg_land_ring = W.land;
+                K.wsg_ring_days = 1;
+                ctx->ragged_wsg_bufs.push_back({q, W});
+                ctx->ragged_wsg = true;
+            }
             K.test_on = p.test_on;
             K.test_lo = p.test_lo;
             K.test_hi = p.test_hi;
@@ -1447,6 +1506,12 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.thr_eff1 = threshold(p.vax_eff1);
             K.thr_eff2 = threshold(p.vax_eff2);
             K.vax_nonsterile = p.vax_nonsterile ? 1u : 0u;
+            K.vax_strategy = p.vax_strategy;
+            if (p.vax_strategy && p.vax_on) {  // its doses are selected before each day from vax_start
+                K.dose_today = ctx->vax_dose + base;
+                ctx->ragged_vax.push_back({q, (uint32_t)std::floor(p.vax_rate * (double)n), p.vax_start,
+                                           p.dose2_delay, p.elderly_bin});
+            }
             K.tab = ctx->tab + q;
             K.rep = ctx->rep + q;
             K.age = ctx->age + base;
@@ -1622,6 +1687,11 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
     CU(ctx, cudaMemcpyAsync(ctx->S.flags, ctx->S0.flags, nb, cudaMemcpyDeviceToDevice, s));
     CU(ctx, cudaMemcpyAsync(ctx->S.qt, ctx->S0.qt, nb, cudaMemcpyDeviceToDevice, s));
     if (ctx->ragged) {
+        if (ctx->S.vd1) {  // priority strategies: no doses given yet, none selected
+            CU(ctx, cudaMemcpyAsync(ctx->S.vd1, ctx->S0.vd1, nb * 2, cudaMemcpyDeviceToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->S.vd2, ctx->S0.vd2, nb * 2, cudaMemcpyDeviceToDevice, s));
+            CU(ctx, cudaMemsetAsync(ctx->vax_dose, 0, nb, s));
+        }
         CU(ctx, clear_next_buffers(ctx, nb));
         for (size_t q = 0; q < ctx->pops.size(); ++q) {
             const PopDesc &pd = ctx->pops[q];

@@ -13,7 +13,7 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
 // one simulated day of a ragged batch of populations (persistent CTAs, tile queue)
 cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
-                               uint32_t n_pops, uint32_t grid, bool occ, cudaStream_t stream);
+                               uint32_t n_pops, uint32_t grid, bool occ, bool wsg, cudaStream_t stream);
 
 // daily dose selection of the vaccination priority strategies: dose_caller[o] = 1
 // for the agents (caller ids) dosed today; scratch of vax_select_scratch_words(n)

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
 // giving exactly the single-population result.
 // 6 blocks per SM asked (swept at 64 populations, autotuned tiling: no minimum
 // 0.533 ms a day at 64 registers, 6 blocks 0.472, 8 blocks 0.480)
-template <bool OCC>
+template <bool OCC, bool WSG, bool VAX>
 __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__restrict__ pops, const Tile *__restrict__ tiles,
                                                           uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                                           const float *inf_cur, float *inf_next, StateRef S,
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
         Sp.tinf = S.tinf + sp.base;
         Sp.flags = S.flags + sp.base;
         Sp.qt = S.qt + sp.base;
-        Sp.vd1 = nullptr;  // priority strategies are not available in ragged batches
-        Sp.vd2 = nullptr;
+        Sp.vd1 = VAX ? S.vd1 + sp.base : nullptr;  // dose days (some population under a priority strategy)
+        Sp.vd2 = VAX ? S.vd2 + sp.base : nullptr;
         for (uint32_t r0 = tl.begin; r0 < tl.end; r0 += blockDim.x) {
             const uint32_t j = r0 + threadIdx.x;
             const bool active = j < tl.end;
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             uint32_t k = 0, kg = 0;
             if (active)
                 // the population's parameters are in shared memory: keys from the seeds (RK = false)
-                agent_day<OCC, false, true, false, false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
+                agent_day<OCC, false, true, WSG, false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
                                                           &infected, &k, &kg);
             count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
         }
@@ -392,10 +392,24 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
 
 cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
-                               uint32_t n_pops, uint32_t grid, bool occ, cudaStream_t stream)
+                               uint32_t n_pops, uint32_t grid, bool occ, bool wsg, cudaStream_t stream)
 {
-    if (occ) step_ragged_kernel<true><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops);
-    else step_ragged_kernel<false><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops);
+    // compiled with the daily-occupation, the Watts-Strogatz and the dose-day paths
+    // only when some population needs them
+    const int v = (occ ? 4 : 0) | (wsg ? 2 : 0) | (S.vd1 ? 1 : 0);
+    switch (v) {
+#define DEABM_RAGGED_CASE(c, O, W, V)                                                                           \
+    case c: step_ragged_kernel<O, W, V><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops); break;
+        DEABM_RAGGED_CASE(0, false, false, false)
+        DEABM_RAGGED_CASE(1, false, false, true)
+        DEABM_RAGGED_CASE(2, false, true, false)
+        DEABM_RAGGED_CASE(3, false, true, true)
+        DEABM_RAGGED_CASE(4, true, false, false)
+        DEABM_RAGGED_CASE(5, true, false, true)
+        DEABM_RAGGED_CASE(6, true, true, false)
+        DEABM_RAGGED_CASE(7, true, true, true)
+#undef DEABM_RAGGED_CASE
+    }
     return cudaGetLastError();
 }
 

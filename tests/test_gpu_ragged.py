@@ -109,3 +109,54 @@ def test_daily_occupations_in_ragged_batches(locality):
     o = oracle_sim(pops[3], params[3])  # the 33-agent population with daily occupations
     ni_o, h_o, _ = o.run(T)
     assert np.array_equal(ni_o, ni[:, 3]) and np.array_equal(h_o, h[:, 3])
+
+
+@pytest.mark.parametrize("locality", [True, False])
+def test_priority_strategies_in_ragged_batches(locality):
+    """Populations under the three vaccination priority strategies (Sec. 5,
+    Table 1) mixed with ones on the static schedule and without vaccination: each
+    population selects its own doses from its own state before each day, and each
+    equals its own single-population run (states, dose bits included, and
+    counters), the 33-agent one also the oracle; a reset and rerun gives the same."""
+    from paper_2110_04421_gb300.deabm import RaggedSimulation
+    pops, params = case()
+    for q, strategy in ((0, 1), (2, 2), (3, 3), (5, 3)):
+        params[q] = dict(params[q], vax_on=1, vax_start=3, vax_rate=0.03, vax_strategy=strategy,
+                         dose2_delay=6 + q, elderly_bin=6)
+    T = 30
+    singles = single_runs(pops, params, T)
+    r = RaggedSimulation(pops, params, max_steps=T, locality_order=locality)
+    ni, h = r.run(T)
+    check((ni, h, r.state()), singles)
+    r.reset()
+    ni2, h2 = r.run(T)
+    assert np.array_equal(ni2, ni) and np.array_equal(h2, h)
+    states = r.state()
+    r.close()
+    for q in (0, 5):  # (strategy 2 puts every first dose before any second: none in 30 days there)
+        assert (states[q]["flags"] & 0x02).sum() > 0, q  # second doses were given
+    assert (states[2]["flags"] & 0x01).sum() > 3000
+    o = oracle_sim(pops[3], params[3])
+    ni_o, h_o, _ = o.run(T)
+    assert np.array_equal(ni_o, ni[:, 3]) and np.array_equal(h_o, h[:, 3])
+
+
+@pytest.mark.parametrize("locality", [True, False])
+def test_watts_strogatz_random_networks_in_ragged_batches(locality):
+    """Populations whose random network is a daily Watts-Strogatz graph (each its
+    own, built before each day) mixed with Poisson ones: each population equals
+    its own single-population run, the 33-agent one also the oracle."""
+    from paper_2110_04421_gb300.deabm import RaggedSimulation
+    pops, params = case()
+    for q, (k, beta) in ((1, (4, 0.2)), (2, (2, 0.5)), (3, (6, 0.1))):
+        pops[q] = dict(pops[q], rand_ws=1, rand_ws_k=k, rand_ws_beta=beta)
+    T = 30
+    singles = single_runs(pops, params, T)
+    r = RaggedSimulation(pops, params, max_steps=T, locality_order=locality)
+    ni, h = r.run(T)
+    check((ni, h, r.state()), singles)
+    r.close()
+    assert ni[:, 2].sum() > 0
+    o = oracle_sim(pops[3], params[3])
+    ni_o, h_o, _ = o.run(T)
+    assert np.array_equal(ni_o, ni[:, 3]) and np.array_equal(h_o, h[:, 3])

@@ -55,9 +55,6 @@ def test_watts_strogatz_rejected_where_not_built():
     with pytest.raises(DeabmError, match="rand_ws_k"):
         gpu_sim(pop, W.params_with())
     pop["rand_ws_k"] = 2
-    from paper_2110_04421_gb300.deabm import RaggedSimulation
-    with pytest.raises(DeabmError, match="plain contexts"):
-        RaggedSimulation([pop, W.population(1_500, 2, 5)], [W.params_with(), W.params_with()], max_steps=4)
 
 
 @pytest.mark.parametrize("B,locality", [(8, True), (5, False)])
