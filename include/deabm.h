@@ -211,7 +211,9 @@ typedef struct {
                                 doses); ties by agent id.  Plain and batched contexts (in a batched
                                 context every replicate column selects from its own state with its own
                                 dose2_delay and the same supply; the general panel kernel then runs
-                                the day instead of the four-replicate one); not ragged batches. */
+                                the day instead of the four-replicate one) and ragged batches (each
+                                population from its own state with its own supply; no initial dose
+                                days there). */
     uint32_t elderly_bin;    /* first age bin counted as "65+" by strategy 3 */
     uint32_t vax_nonsterile; /* 0: immunity is sterilising (stage VAX); 1: non-sterilising (Sec. 5, second
                                 version): the agent stays susceptible with flag DEABM_FL_IMMUNE and any
