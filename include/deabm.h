@@ -226,8 +226,8 @@ typedef struct {
                                 in label order, ids ascending inside a group; results and every
                                 array the ABI returns are unchanged (random draws and outputs use
                                 the caller's agent ids) */
-    /* Digital exposure notification (Sec. 4.2); plain and batched contexts with
-     * test_on (not ragged batches).
+    /* Digital exposure notification (Sec. 4.2); plain and batched contexts and
+     * ragged batches (not over a Watts-Strogatz random network there), with test_on.
      * At create (and reset) agent j gets DEABM_FL_APP when word x of Philox
      * stream 6 keyed (seed, j, day word 0xFFFFFFFD) is below floor(den_adoption
      * 2^32); in a batched context each replicate column draws its own app holders
@@ -272,11 +272,13 @@ int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, con
 
 /* Create a ragged batch: n_pops independent populations of different sizes
  * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda, no
- * exposure notification, no initial dose days under a priority strategy:
- * DEABM_EINVAL otherwise) simulated together, one kernel launch per day for all
- * of them (after the day's dose selection of each population under a vaccination
- * priority strategy, Sec. 5 Table 1, and the day's graph of each population with
- * a Watts-Strogatz random network: a few small launches per such population):
+ * initial dose days under a priority strategy, no exposure notification over a
+ * Watts-Strogatz random network: DEABM_EINVAL otherwise) simulated together, one
+ * kernel launch per day for all of them (after the day's dose selection of each
+ * population under a vaccination priority strategy, Sec. 5 Table 1, and the day's
+ * graph of each population with a Watts-Strogatz random network: a few small
+ * launches per such population; followed by the notification pass of each
+ * population with exposure notification, Sec. 4.2, one launch each):
  * resident thread blocks take tiles of
  * rows (never spanning two populations) from a per-day work queue.  A population
  * whose params ask for locality_order is numbered internally like a plain
@@ -419,7 +421,8 @@ const char *deabm_lambda_noalloc_last_error(void);
 /* Exposure notification (Sec. 4.2, den_on): notified[d][b] = agents of replicate
  * column b notified at the end of day d, for d < day_count (day_count <= days
  * run; host array of day_count x n_rep int32, n_rep = 1 in plain contexts).
- * Zeros when den_on = 0 (ragged batches: day_count entries, all zero).  Returns
+ * Zeros when den_on = 0 (ragged batches: [d][population], zeros in the columns
+ * of populations without exposure notification).  Returns
  * DEABM_OK, DEABM_EINVAL, DEABM_ECUDA. */
 int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *notified);
 

@@ -68,6 +68,7 @@ struct deabm_ctx {
     bool ragged_occ = false;  // some population of the ragged batch draws daily occupation contacts
     bool ragged_wsg = false;  // some population of the ragged batch has a Watts-Strogatz random network
     std::vector<std::pair<uint32_t, WsgBuffers>> ragged_wsg_bufs;  // (population, its day's graph)
+    std::vector<uint32_t> ragged_den;  // the populations with exposure notification
     std::vector<PopDesc> pops;         // host copies, KParams pointers already offset
     PopDesc *d_pops = nullptr;
     Tile *d_tiles = nullptr;
@@ -999,8 +1000,19 @@ static cudaError_t ragged_day(deabm_ctx *ctx, uint32_t day, int c)
         cudaError_t e = launch_wsg_build(ctx->pops[qw.first].kp, day, qw.second, ctx->stream);
         if (e != cudaSuccess) return e;
     }
-    return launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, day, ctx->inf[c], ctx->inf[c ^ 1],
-                              ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ, ctx->ragged_wsg, ctx->stream);
+    cudaError_t e = launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, day, ctx->inf[c],
+                                       ctx->inf[c ^ 1], ctx->S, ctx->C, ctx->n_rep, ctx->grid, ctx->ragged_occ,
+                                       ctx->ragged_wsg, !ctx->ragged_den.empty(), ctx->stream);
+    // the notification pass of each population that has one, on its own slice
+    // (one replicate column; its count goes to column q of [day][population])
+    for (uint32_t q : ctx->ragged_den) {
+        if (e != cudaSuccess) return e;
+        const PopDesc &pd = ctx->pops[q];
+        StateRef Sp{ctx->S.stage + pd.base, ctx->S.timer + pd.base, ctx->S.tinf + pd.base, ctx->S.flags + pd.base,
+                    ctx->S.qt + pd.base};
+        e = launch_den_batch(pd.kp, day, pd.row_of, Sp, ctx->C, ctx->n_rep, q, ctx->stream);
+    }
+    return e;
 }
 
 // The Watts-Strogatz graph of `day` built into its slot of the ring, and the
@@ -1054,7 +1066,7 @@ extern "C" int deabm_step(deabm_ctx *ctx, uint32_t n_steps)
                             ctx->stream));
         if (kp.den_on) {
             if (ctx->n_rep == 1) CU(ctx, launch_den(kp, ctx->day, ctx->S, ctx->C, ctx->stream));
-            else CU(ctx, launch_den_batch(kp, ctx->day, ctx->row_of, ctx->S, ctx->C, ctx->stream));
+            else CU(ctx, launch_den_batch(kp, ctx->day, ctx->row_of, ctx->S, ctx->C, ctx->n_rep, 0u, ctx->stream));
         }
         ctx->cur ^= 1;
         ctx->day += 1;
@@ -1312,8 +1324,10 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
-            if (params[q].den_on)
-                return fail(ctx, DEABM_EINVAL, "exposure notification is not available for ragged batches");
+            if (params[q].den_on && graphs[q].rand_ws)
+                return fail(ctx, DEABM_EINVAL,
+                            "population %u: exposure notification over a Watts-Strogatz random network is not "
+                            "available in ragged batches", q);
             if (params[q].vax_strategy && (agents[q].dose1_day || agents[q].dose2_day))
                 return fail(ctx, DEABM_EINVAL, "population %u: initial dose days are not taken in ragged batches", q);
         }
@@ -1357,6 +1371,13 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
         if ((r = dalloc(ctx, &ctx->C.msgs, days))) return r;
         if ((r = dalloc(ctx, &ctx->C.gath, days))) return r;
         if ((r = dalloc(ctx, &ctx->queue, days))) return r;
+        if ((r = dalloc(ctx, &ctx->C.den, days * n_pops))) return r;  // notified, [day][population]
+        bool any_den = false;
+        for (uint32_t q = 0; q < n_pops; ++q) any_den |= params[q].den_on != 0;
+        if (any_den) {  // positives of the day (one word per row) and their count, [population][day]
+            if ((r = dalloc(ctx, &ctx->den_bits, N))) return r;
+            if ((r = dalloc(ctx, &ctx->den_pos, days * n_pops))) return r;
+        }
         uint32_t max_n = 0;
         for (uint32_t q = 0; q < n_pops; ++q) max_n = std::max(max_n, graphs[q].n_agents);
         bool any_strategy = false;
@@ -1507,6 +1528,15 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             K.thr_eff2 = threshold(p.vax_eff2);
             K.vax_nonsterile = p.vax_nonsterile ? 1u : 0u;
             K.vax_strategy = p.vax_strategy;
+            if (p.den_on) {  // exposure notification: the positives of its rows and days
+                K.den_on = 1u;
+                K.den_window = p.den_window;
+                K.thr_comp = threshold(p.den_compliance);
+                K.thr_adopt = threshold(p.den_adoption);
+                K.den_bits = ctx->den_bits + base;
+                K.den_pos = ctx->den_pos + (size_t)q * days;
+                ctx->ragged_den.push_back(q);
+            }
             if (p.vax_strategy && p.vax_on) {  // its doses are selected before each day from vax_start
                 K.dose_today = ctx->vax_dose + base;
                 ctx->ragged_vax.push_back({q, (uint32_t)std::floor(p.vax_rate * (double)n), p.vax_start,
@@ -1576,6 +1606,11 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             if ((r = put(ctx->S0.tinf + base, a.tinf, 2))) return r;
             if ((r = put(ctx->S0.flags + base, a.flags, 1))) return r;
             if ((r = put(ctx->S0.qt + base, a.qt, 1))) return r;
+            if (K.den_on) {  // app holders, part of the initial state
+                StateRef S0p{ctx->S0.stage + base, ctx->S0.timer + base, ctx->S0.tinf + base, ctx->S0.flags + base,
+                             ctx->S0.qt + base};
+                CU(ctx, launch_den_apps(K, S0p, s));
+            }
             CU(ctx, cudaStreamSynchronize(s));  // scratch of this population ends here
             ctx->pop_seeds[q].assign(a.seed_ids, a.seed_ids + a.n_seed);  // caller ids
             if (a.n_seed) {  // on the device: local rows
@@ -1708,6 +1743,8 @@ extern "C" int deabm_reset(deabm_ctx *ctx, const float *rep_params, const uint64
         CU(ctx, cudaMemsetAsync(ctx->C.hist, 0, sizeof(int32_t) * days * ctx->n_rep * DEABM_N_STAGE, s));
         CU(ctx, cudaMemsetAsync(ctx->C.msgs, 0, sizeof(unsigned long long) * days, s));
         CU(ctx, cudaMemsetAsync(ctx->C.gath, 0, sizeof(unsigned long long) * days, s));
+        CU(ctx, cudaMemsetAsync(ctx->C.den, 0, sizeof(int32_t) * days * ctx->n_rep, s));
+        if (ctx->den_pos) CU(ctx, cudaMemsetAsync(ctx->den_pos, 0, sizeof(int32_t) * days * ctx->n_rep, s));
         ctx->day = 0;
         return DEABM_OK;
     }
@@ -1742,10 +1779,6 @@ extern "C" int deabm_get_notified(deabm_ctx *ctx, uint32_t day_count, int32_t *n
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if (day_count > ctx->day) return fail(ctx, DEABM_EINVAL, "only %u days have run", ctx->day);
     if (!notified || !day_count) return DEABM_OK;
-    if (ctx->ragged) {
-        std::memset(notified, 0, sizeof(int32_t) * day_count);
-        return DEABM_OK;
-    }
     CU(ctx, cudaMemcpyAsync(notified, ctx->C.den, sizeof(int32_t) * day_count * ctx->n_rep, cudaMemcpyDeviceToHost,
                             ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));

@@ -264,7 +264,8 @@ constexpr uint32_t kDenHitWords = 8;  // words of columns one launch covers (256
 // the days d0 + g, d0 + g + 8, ... of the window; the partial ORs are combined by
 // shuffles and lane g then works through the columns of word w0 + g.
 __global__ void __launch_bounds__(128) den_batch_kernel(const KParams P, uint32_t day, const uint32_t *row_of,
-                                                         uint32_t W, uint32_t w0, StateRef S, Counters C)
+                                                         uint32_t W, uint32_t w0, StateRef S, Counters C,
+                                                         uint32_t den_stride, uint32_t den_col0)
 {
     __shared__ int s_cnt[kDenHitWords * 32];
     for (uint32_t q = threadIdx.x; q < kDenHitWords * 32u; q += blockDim.x) s_cnt[q] = 0;
@@ -329,16 +330,16 @@ __global__ void __launch_bounds__(128) den_batch_kernel(const KParams P, uint32_
     }
     __syncthreads();
     for (uint32_t q = threadIdx.x; q < kDenHitWords * 32u; q += blockDim.x)
-        if (s_cnt[q]) atomicAdd(C.den + (size_t)day * P.n_rep + w0 * 32u + q, s_cnt[q]);
+        if (s_cnt[q]) atomicAdd(C.den + (size_t)day * den_stride + den_col0 + w0 * 32u + q, s_cnt[q]);
 }
 
 cudaError_t launch_den_batch(const KParams &P, uint32_t day, const uint32_t *row_of, const StateRef &S,
-                             const Counters &C, cudaStream_t stream)
+                             const Counters &C, uint32_t den_stride, uint32_t den_col0, cudaStream_t stream)
 {
     const uint32_t W = (P.n_rep + 31u) / 32u;
     const unsigned blocks = (unsigned)(((size_t)P.n * 8u + 127u) / 128u);
     for (uint32_t w0 = 0; w0 < W; w0 += kDenHitWords)
-        den_batch_kernel<<<blocks, 128, 0, stream>>>(P, day, row_of, W, w0, S, C);
+        den_batch_kernel<<<blocks, 128, 0, stream>>>(P, day, row_of, W, w0, S, C, den_stride, den_col0);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ cudaError_t launch_step(const KParams &P, uint32_t day, const InfBuffers &I, con
 // one simulated day of a ragged batch of populations (persistent CTAs, tile queue)
 cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
-                               uint32_t n_pops, uint32_t grid, bool occ, bool wsg, cudaStream_t stream);
+                               uint32_t n_pops, uint32_t grid, bool occ, bool wsg, bool den, cudaStream_t stream);
 
 // daily dose selection of the vaccination priority strategies: dose_caller[o] = 1
 // for the agents (caller ids) dosed today; scratch of vax_select_scratch_words(n)
@@ -46,9 +46,10 @@ cudaError_t launch_den_apps(const KParams &P, const StateRef &S, cudaStream_t st
 cudaError_t launch_den(const KParams &P, uint32_t day, const StateRef &S, const Counters &C, cudaStream_t stream);
 // the notification pass of a batched context ([N][B] state; positives in P.den_bits
 // as [N][ceil(B/32)] words; row_of: caller id -> row, or nullptr when not
-// relabelled; notified counts in C.den [day][B])
+// relabelled; notified count of column b at C.den[day * den_stride + den_col0 + b]);
+// also a ragged population's pass (one column, its counter column den_col0)
 cudaError_t launch_den_batch(const KParams &P, uint32_t day, const uint32_t *row_of, const StateRef &S,
-                             const Counters &C, cudaStream_t stream);
+                             const Counters &C, uint32_t den_stride, uint32_t den_col0, cudaStream_t stream);
 // internal numbering: min-label rounds over a CSR (at most `rounds`, even,
 // fewer once the labels stop moving; result in label, tmp is scratch of n words,
 // changed one device word; synchronises the stream after each pair of rounds);

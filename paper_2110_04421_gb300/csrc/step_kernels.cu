@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256) step_batch_kernel(const KParams P, uint32
 // giving exactly the single-population result.
 // 6 blocks per SM asked (swept at 64 populations, autotuned tiling: no minimum
 // 0.533 ms a day at 64 registers, 6 blocks 0.472, 8 blocks 0.480)
-template <bool OCC, bool WSG, bool VAX>
+template <bool OCC, bool WSG, bool VAX, bool DEN>
 __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__restrict__ pops, const Tile *__restrict__ tiles,
                                                           uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                                           const float *inf_cur, float *inf_next, StateRef S,
@@ -370,12 +370,16 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
             const uint32_t j = r0 + threadIdx.x;
             const bool active = j < tl.end;
             int st = 0;
-            bool infected = false;
+            bool infected = false, notify = false;
             uint32_t k = 0, kg = 0;
             if (active)
                 // the population's parameters are in shared memory: keys from the seeds (RK = false)
-                agent_day<OCC, false, true, WSG, false>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr, &st,
-                                                          &infected, &k, &kg);
+                agent_day<OCC, false, true, WSG, false, DEN>(sp.kp, sp.rep, day, I, Sp, j, 1u, 0u, nullptr, nullptr,
+                                                             &st, &infected, &k, &kg, &notify);
+            if (DEN && active && sp.kp.den_on) {  // the population's positive app holders: one word per row
+                sp.kp.den_bits[j] = notify ? 1u : 0u;
+                if (notify) atomicAdd(sp.kp.den_pos + day, 1);
+            }
             count_day(active, st, infected, k, kg, s_hist, &s_new, &s_msgs, &s_gath);
         }
         __syncthreads();
@@ -392,22 +396,30 @@ __global__ void __launch_bounds__(256, 6) step_ragged_kernel(const PopDesc *__re
 
 cudaError_t launch_step_ragged(const PopDesc *pops, const Tile *tiles, uint32_t n_tiles, uint32_t *queue, uint32_t day,
                                const float *inf_cur, float *inf_next, const StateRef &S, const Counters &C,
-                               uint32_t n_pops, uint32_t grid, bool occ, bool wsg, cudaStream_t stream)
+                               uint32_t n_pops, uint32_t grid, bool occ, bool wsg, bool den, cudaStream_t stream)
 {
-    // compiled with the daily-occupation, the Watts-Strogatz and the dose-day paths
-    // only when some population needs them
-    const int v = (occ ? 4 : 0) | (wsg ? 2 : 0) | (S.vd1 ? 1 : 0);
+    // compiled with the daily-occupation, the Watts-Strogatz, the dose-day and the
+    // notification paths only when some population needs them
+    const int v = (den ? 8 : 0) | (occ ? 4 : 0) | (wsg ? 2 : 0) | (S.vd1 ? 1 : 0);
     switch (v) {
-#define DEABM_RAGGED_CASE(c, O, W, V)                                                                           \
-    case c: step_ragged_kernel<O, W, V><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops); break;
-        DEABM_RAGGED_CASE(0, false, false, false)
-        DEABM_RAGGED_CASE(1, false, false, true)
-        DEABM_RAGGED_CASE(2, false, true, false)
-        DEABM_RAGGED_CASE(3, false, true, true)
-        DEABM_RAGGED_CASE(4, true, false, false)
-        DEABM_RAGGED_CASE(5, true, false, true)
-        DEABM_RAGGED_CASE(6, true, true, false)
-        DEABM_RAGGED_CASE(7, true, true, true)
+#define DEABM_RAGGED_CASE(c, O, W, V, D)                                                                        \
+    case c: step_ragged_kernel<O, W, V, D><<<grid, 256, 0, stream>>>(pops, tiles, n_tiles, queue, day, inf_cur, inf_next, S, C, n_pops); break;
+        DEABM_RAGGED_CASE(0, false, false, false, false)
+        DEABM_RAGGED_CASE(1, false, false, true, false)
+        DEABM_RAGGED_CASE(2, false, true, false, false)
+        DEABM_RAGGED_CASE(3, false, true, true, false)
+        DEABM_RAGGED_CASE(4, true, false, false, false)
+        DEABM_RAGGED_CASE(5, true, false, true, false)
+        DEABM_RAGGED_CASE(6, true, true, false, false)
+        DEABM_RAGGED_CASE(7, true, true, true, false)
+        DEABM_RAGGED_CASE(8, false, false, false, true)
+        DEABM_RAGGED_CASE(9, false, false, true, true)
+        DEABM_RAGGED_CASE(10, false, true, false, true)
+        DEABM_RAGGED_CASE(11, false, true, true, true)
+        DEABM_RAGGED_CASE(12, true, false, false, true)
+        DEABM_RAGGED_CASE(13, true, false, true, true)
+        DEABM_RAGGED_CASE(14, true, true, false, true)
+        DEABM_RAGGED_CASE(15, true, true, true, true)
 #undef DEABM_RAGGED_CASE
     }
     return cudaGetLastError();

@@ -409,6 +409,13 @@ class RaggedSimulation:
         _check(lib().deabm_get_counters(self.ctx, days, _p(ni), _p(h), _p(m)), self.ctx)
         return ni, h, m
 
+    def notified(self, days: int) -> np.ndarray:
+        """Agents notified by exposure notification at the end of each day, [days, n_pops]
+        (zeros in the columns of populations without it)."""
+        out = np.zeros((days, self.n_pops), np.int32)
+        _check(lib().deabm_get_notified(self.ctx, days, _p(out)), self.ctx)
+        return out
+
     def gathered(self, days: int):
         """Messages gathered per day, summed over the populations (deabm_get_gathered)."""
         g = np.zeros(days, np.uint64)

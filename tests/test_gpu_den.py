@@ -160,11 +160,9 @@ def test_batched_columns_match_oracle_runs(B, daily_occ, locality_order):
     assert total > 50 * B  # notifications happened in every column on average
 
 
-def test_other_contexts_reject_notification():
-    from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation, Relaxed
+def test_relaxed_model_rejects_notification():
+    from paper_2110_04421_gb300.deabm import DeabmError, Relaxed
     pop = W.population(500, 1, 5)
     p = den_params()
-    with pytest.raises(DeabmError):
-        RaggedSimulation([pop], [p], max_steps=5)
     with pytest.raises(DeabmError):
         Relaxed(pop, p, pop["age"], pop["seed_ids"], tau=0.5, max_days=5, ckpt_every=5)

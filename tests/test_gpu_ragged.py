@@ -160,3 +160,56 @@ def test_watts_strogatz_random_networks_in_ragged_batches(locality):
     o = oracle_sim(pops[3], params[3])
     ni_o, h_o, _ = o.run(T)
     assert np.array_equal(ni_o, ni[:, 3]) and np.array_equal(h_o, h[:, 3])
+
+
+@pytest.mark.parametrize("locality", [True, False])
+def test_exposure_notification_in_ragged_batches(locality):
+    """Populations with digital exposure notification (Sec. 4.2: each its own app
+    holders, look-back window and compliance draws; one with daily occupation
+    contacts, one under a priority strategy) mixed with ones without it: each
+    population equals its own single-population run (states, counters and the
+    daily notification counts, a column of [day][population]), the 157-agent one
+    also the oracle; a reset and rerun gives the same."""
+    from paper_2110_04421_gb300.deabm import RaggedSimulation, Simulation
+    pops, params = case()
+    den = dict(test_on=1, quar_on=1, den_on=1, den_compliance=0.8)
+    for q, (adopt, window) in ((1, (0.9, 7)), (2, (0.4, 7)), (3, (1.0, 3)), (5, (0.3, 12))):
+        params[q] = dict(params[q], den_adoption=adopt, den_window=window, R=3.5, **den)
+    p = pops[2]
+    p["row_ptr"], p["col"] = p["row_ptr"][:1], p["col"][:1]
+    p["occ_group"], p["occ_k"] = W.occupations(p["n"], 62, n_occ=23)
+    params[5] = dict(params[5], vax_on=1, vax_start=3, vax_rate=0.03, vax_strategy=1, dose2_delay=8, elderly_bin=6)
+    T = 40
+    singles, notified = [], []
+    for pop, par in zip(pops, params):
+        s = Simulation(pop, par, pop["age"], pop["seed_ids"], max_steps=T, locality_order=False)
+        ni1, h1 = s.run(T)
+        singles.append((ni1[:, 0], h1[:, 0], s.state()))
+        notified.append(s.notified(T))
+        s.close()
+    r = RaggedSimulation(pops, params, max_steps=T, locality_order=locality)
+    ni, h = r.run(T)
+    check((ni, h, r.state()), singles)
+    nt = r.notified(T)
+    for q in range(len(pops)):
+        assert np.array_equal(nt[:, q], notified[q]), q
+    assert not nt[:, [0, 4]].any()
+    for q in (1, 2, 5):
+        assert nt[:, q].sum() > 20, q
+    r.reset()
+    ni2, h2 = r.run(T)
+    assert np.array_equal(ni2, ni) and np.array_equal(h2, h) and np.array_equal(r.notified(T), nt)
+    r.close()
+    o = oracle_sim(pops[1], params[1])
+    ni_o, h_o, _ = o.run(T)
+    assert np.array_equal(ni_o, ni[:, 1]) and np.array_equal(h_o, h[:, 1])
+    assert list(nt[:, 1]) == o.den_notified
+
+
+def test_ragged_rejects_notification_over_watts_strogatz():
+    from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation
+    pops, params = case()
+    pops[1] = dict(pops[1], rand_ws=1, rand_ws_k=4, rand_ws_beta=0.2)
+    params[1] = dict(params[1], test_on=1, den_on=1, den_adoption=0.5, den_compliance=0.8)
+    with pytest.raises(DeabmError, match="Watts-Strogatz"):
+        RaggedSimulation(pops, params, max_steps=10)
