@@ -116,6 +116,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 16 columns of the warp's 32 TMEM lanes, issued without waiting: the registers
+// are read only after tmem_wait16 on the same array (which names them as
+// operands, so that no read of them is scheduled before the wait)
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
@@ -209,27 +230,48 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_forward_tc_kernel(const Fused
         const uint32_t quad = warp & 3u, half = warp >> 2, row = quad * 32u + lane;
         const uint32_t ncol = N / 2u, c0 = half * ncol;
         const bool last = (l == g.L - 1);
-        for (uint32_t cb = 0; cb < ncol; cb += 32u) {
-            float v[32];
-            tmem_ld32(tmem + ((quad * 32u) << 16) + c0 + cb, v);
-            const uint32_t n0 = c0 + cb;
-            if (!last) {
+        if (!last) {
+            // hidden layer: bias, GELU, BF16 into the next layer's input tile; the
+            // next 16 columns' TMEM load is in flight while these 16 are worked
+            // (ncol is a multiple of 32)
+            const float *bias = g.bias[l];
+            auto hidden16 = [&](const uint32_t (&r)[16], uint32_t n0) {
+                float v[16];
 #pragma unroll
-                for (int e = 0; e < 32; e += 4) {  // the bias four columns at a time (16-byte loads)
-                    const float4 bb = __ldg((const float4 *)(g.bias[l] + n0 + e));
-                    v[e] = gelu_act(v[e] + bb.x);
-                    v[e + 1] = gelu_act(v[e + 1] + bb.y);
-                    v[e + 2] = gelu_act(v[e + 2] + bb.z);
-                    v[e + 3] = gelu_act(v[e + 3] + bb.w);
+                for (int e = 0; e < 16; e += 4) {  // the bias four columns at a time (16-byte loads)
+                    const float4 bb = __ldg((const float4 *)(bias + n0 + e));
+                    v[e] = gelu_act(__uint_as_float(r[e]) + bb.x);
+                    v[e + 1] = gelu_act(__uint_as_float(r[e + 1]) + bb.y);
+                    v[e + 2] = gelu_act(__uint_as_float(r[e + 2]) + bb.z);
+                    v[e + 3] = gelu_act(__uint_as_float(r[e + 3]) + bb.w);
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 2; ++q) {
                     const uint32_t n = n0 + q * 8u;
                     uint4 pk = make_uint4(pack_bf16x2(v[q * 8 + 0], v[q * 8 + 1]), pack_bf16x2(v[q * 8 + 2], v[q * 8 + 3]),
                                           pack_bf16x2(v[q * 8 + 4], v[q * 8 + 5]), pack_bf16x2(v[q * 8 + 6], v[q * 8 + 7]));
                     *(uint4 *)(sA + (n >> 6) * kAChunkBytes + sw128(row, (n & 63u) >> 3)) = pk;
                 }
-            } else {
+            };
+            const uint32_t tb = tmem + ((quad * 32u) << 16) + c0;
+            uint32_t ra[16], rb[16];
+            tmem_ld16_issue(tb, ra);
+            tmem_wait16(ra);
+            for (uint32_t cb = 0; cb < ncol; cb += 32u) {
+                tmem_ld16_issue(tb + cb + 16u, rb);
+                hidden16(ra, c0 + cb);
+                tmem_wait16(rb);
+                const bool more = cb + 32u < ncol;
+                if (more) tmem_ld16_issue(tb + cb + 32u, ra);
+                hidden16(rb, c0 + cb + 16u);
+                if (more) tmem_wait16(ra);
+            }
+        }
+        for (uint32_t cb = 0; last && cb < ncol; cb += 32u) {
+            float v[32];
+            tmem_ld32(tmem + ((quad * 32u) << 16) + c0 + cb, v);
+            const uint32_t n0 = c0 + cb;
+            {
                 // output layer: the warp's 32 rows x 32 columns go through shared memory
                 // (the layer input is no longer read: the MMAs have completed) so that
                 // each global store writes one row's 32 consecutive columns
