@@ -227,7 +227,7 @@ typedef struct {
                                 array the ABI returns are unchanged (random draws and outputs use
                                 the caller's agent ids) */
     /* Digital exposure notification (Sec. 4.2); plain and batched contexts and
-     * ragged batches (not over a Watts-Strogatz random network there), with test_on.
+     * ragged batches, with test_on.
      * At create (and reset) agent j gets DEABM_FL_APP when word x of Philox
      * stream 6 keyed (seed, j, day word 0xFFFFFFFD) is below floor(den_adoption
      * 2^32); in a batched context each replicate column draws its own app holders
@@ -272,8 +272,7 @@ int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, con
 
 /* Create a ragged batch: n_pops independent populations of different sizes
  * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda, no
- * initial dose days under a priority strategy, no exposure notification over a
- * Watts-Strogatz random network: DEABM_EINVAL otherwise) simulated together, one
+ * initial dose days under a priority strategy: DEABM_EINVAL otherwise) simulated together, one
  * kernel launch per day for all of them (after the day's dose selection of each
  * population under a vaccination priority strategy, Sec. 5 Table 1, and the day's
  * graph of each population with a Watts-Strogatz random network: a few small

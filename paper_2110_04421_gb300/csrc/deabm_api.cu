@@ -997,7 +997,17 @@ static cudaError_t ragged_day(deabm_ctx *ctx, uint32_t day, int c)
         if (e != cudaSuccess) return e;
     }
     for (const auto &qw : ctx->ragged_wsg_bufs) {  // the day's Watts-Strogatz graph of each population that has one
-        cudaError_t e = launch_wsg_build(ctx->pops[qw.first].kp, day, qw.second, ctx->stream);
+        const KParams &kp = ctx->pops[qw.first].kp;
+        WsgBuffers W = qw.second;
+        cudaError_t e = cudaSuccess;
+        if (kp.wsg_ring_days > 1) {  // with exposure notification: a ring of the window's graphs
+            const uint32_t slot = day % kp.wsg_ring_days;
+            W.ends += (size_t)slot * ((size_t)kp.n + 3);
+            W.land += (size_t)slot * kp.n * kp.wsg_h;
+            e = launch_wsg_slot(&ctx->d_pops[qw.first].kp, day, ctx->stream);
+            if (e != cudaSuccess) return e;
+        }
+        e = launch_wsg_build(kp, day, W, ctx->stream);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = launch_step_ragged(ctx->d_pops, ctx->d_tiles, ctx->n_tiles, ctx->queue, day, ctx->inf[c],
@@ -1324,10 +1334,6 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
-            if (params[q].den_on && graphs[q].rand_ws)
-                return fail(ctx, DEABM_EINVAL,
-                            "population %u: exposure notification over a Watts-Strogatz random network is not "
-                            "available in ragged batches", q);
             if (params[q].vax_strategy && (agents[q].dose1_day || agents[q].dose2_day))
                 return fail(ctx, DEABM_EINVAL, "population %u: initial dose days are not taken in ragged batches", q);
         }
@@ -1501,17 +1507,19 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
                 K.wsg_h = g.rand_ws_k / 2u;
                 K.thr_wsg = threshold((double)g.rand_ws_beta);
                 const size_t edges = (size_t)n * K.wsg_h;
+                // with exposure notification the look-back window's graphs are kept
+                const uint32_t ring = p.den_on ? p.den_window : 1u;
                 if ((r = dalloc(ctx, &W.rew, n))) return r;
                 if ((r = dalloc(ctx, &W.far, edges))) return r;
-                if ((r = dalloc(ctx, &W.ends, (size_t)n + 3))) return r;
-                if ((r = dalloc(ctx, &W.land, edges))) return r;
+                if ((r = dalloc(ctx, &W.ends, ((size_t)n + 3) * ring))) return r;
+                if ((r = dalloc(ctx, &W.land, edges * ring))) return r;
                 if ((r = dalloc(ctx, &W.scratch, wsg_scratch_words(n)))) return r;
                 K.wsg_rew = W.rew;
                 K.wsg_start = W.ends + 2;
                 K.wsg_land = W.land;
                 K.wsg_ends_ring = W.ends;
                 K.wsg_land_ring = W.land;
-                K.wsg_ring_days = 1;
+                K.wsg_ring_days = ring;
                 ctx->ragged_wsg_bufs.push_back({q, W});
                 ctx->ragged_wsg = true;
             }

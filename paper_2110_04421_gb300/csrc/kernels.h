@@ -72,6 +72,9 @@ struct WsgBuffers {
 };
 size_t wsg_scratch_words(uint32_t n);
 cudaError_t launch_wsg_build(const KParams &P, uint32_t day, const WsgBuffers &B, cudaStream_t stream);
+// points the day view (wsg_start, wsg_land) of the parameters at kp_dev (device
+// memory) at slot day % wsg_ring_days of their ring of graphs
+cudaError_t launch_wsg_slot(KParams *kp_dev, uint32_t day, cudaStream_t stream);
 // in-place inclusive prefix sum of m words (scratch of scan_scratch_words(m) words)
 cudaError_t launch_scan_inclusive(uint32_t *a, size_t m, uint32_t *scratch, cudaStream_t stream);
 // new2orig[q] = the agent at internal row q: agents by ascending label (labels

@@ -113,6 +113,19 @@ __global__ void wsg_order_kernel(uint32_t n, const uint32_t *start, uint32_t *la
 
 size_t wsg_scratch_words(uint32_t n) { return scan_scratch_words((size_t)n + 3u); }
 
+__global__ void wsg_slot_kernel(KParams *kp, uint32_t day)
+{
+    const uint32_t slot = day % kp->wsg_ring_days;
+    kp->wsg_start = kp->wsg_ends_ring + (size_t)slot * ((size_t)kp->n + 3u) + 2u;
+    kp->wsg_land = kp->wsg_land_ring + (size_t)slot * kp->n * kp->wsg_h;
+}
+
+cudaError_t launch_wsg_slot(KParams *kp_dev, uint32_t day, cudaStream_t s)
+{
+    wsg_slot_kernel<<<1, 1, 0, s>>>(kp_dev, day);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wsg_build(const KParams &P, uint32_t day, const WsgBuffers &B, cudaStream_t s)
 {
     const uint32_t n = P.n, h = P.wsg_h;

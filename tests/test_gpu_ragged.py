@@ -206,10 +206,45 @@ def test_exposure_notification_in_ragged_batches(locality):
     assert list(nt[:, 1]) == o.den_notified
 
 
-def test_ragged_rejects_notification_over_watts_strogatz():
-    from paper_2110_04421_gb300.deabm import DeabmError, RaggedSimulation
+@pytest.mark.parametrize("locality", [True, False])
+def test_notification_over_watts_strogatz_networks_in_ragged_batches(locality):
+    """Populations with exposure notification whose random network is a daily
+    Watts-Strogatz graph (each keeps its look-back window's graphs in a ring of
+    its own, the day's slot chosen on the device inside the captured days),
+    beside Poisson and notification-free ones: each population equals its own
+    single-population run, notification counts included; the 157-agent one also
+    the oracle."""
+    from paper_2110_04421_gb300.deabm import RaggedSimulation, Simulation
     pops, params = case()
-    pops[1] = dict(pops[1], rand_ws=1, rand_ws_k=4, rand_ws_beta=0.2)
-    params[1] = dict(params[1], test_on=1, den_on=1, den_adoption=0.5, den_compliance=0.8)
-    with pytest.raises(DeabmError, match="Watts-Strogatz"):
-        RaggedSimulation(pops, params, max_steps=10)
+    den = dict(test_on=1, quar_on=1, den_on=1, den_compliance=0.8, R=4.0)
+    for q, (k, beta, adopt, window) in ((1, (4, 0.2, 0.9, 7)), (2, (6, 0.1, 0.5, 5)), (4, (2, 0.5, 0.7, 1))):
+        pops[q] = dict(pops[q], rand_ws=1, rand_ws_k=k, rand_ws_beta=beta)
+        params[q] = dict(params[q], den_adoption=adopt, den_window=window, **den)
+    pops[0] = dict(pops[0], rand_ws=1, rand_ws_k=4, rand_ws_beta=0.3)  # no notification
+    params[5] = dict(params[5], den_adoption=0.5, den_window=7, **den)  # Poisson network
+    T = 40
+    singles, notified = [], []
+    for pop, par in zip(pops, params):
+        s = Simulation(pop, par, pop["age"], pop["seed_ids"], max_steps=T, locality_order=False)
+        ni1, h1 = s.run(T)
+        singles.append((ni1[:, 0], h1[:, 0], s.state()))
+        notified.append(s.notified(T))
+        s.close()
+    r = RaggedSimulation(pops, params, max_steps=T, locality_order=locality)
+    ni, h = r.run(T)
+    check((ni, h, r.state()), singles)
+    nt = r.notified(T)
+    for q in range(len(pops)):
+        assert np.array_equal(nt[:, q], notified[q]), q
+    for q in (1, 2, 5):
+        assert nt[:, q].sum() > 20, q
+    r.reset()
+    r.step(T)  # the days one launch sequence at a time, outside the captured graph
+    r.sync()
+    ni2, h2, _ = r.counters(T)
+    assert np.array_equal(ni2, ni) and np.array_equal(h2, h) and np.array_equal(r.notified(T), nt)
+    r.close()
+    o = oracle_sim(pops[1], params[1])
+    ni_o, h_o, _ = o.run(T)
+    assert np.array_equal(ni_o, ni[:, 1]) and np.array_equal(h_o, h[:, 1])
+    assert list(nt[:, 1]) == o.den_notified
