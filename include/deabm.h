@@ -271,8 +271,8 @@ int deabm_create_batch(const deabm_graph *graph, const deabm_agents *agents, con
                        void *cuda_stream, deabm_ctx **out);
 
 /* Create a ragged batch: n_pops independent populations of different sizes
- * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda, no
- * initial dose days under a priority strategy: DEABM_EINVAL otherwise) simulated together, one
+ * (graphs[q], agents[q], params[q] each as for deabm_create; no keep_lambda:
+ * DEABM_EINVAL otherwise) simulated together, one
  * kernel launch per day for all of them (after the day's dose selection of each
  * population under a vaccination priority strategy, Sec. 5 Table 1, and the day's
  * graph of each population with a Watts-Strogatz random network: a few small
@@ -319,7 +319,8 @@ int deabm_get_state(deabm_ctx *ctx, int8_t *stage, int16_t *timer, int16_t *tinf
 
 /* Days of each agent's first and second dose under a priority strategy
  * (host int16 [n_agents][n_rep] in caller order, 0x7FFF = none; either may be
- * NULL).  Not for ragged batches (DEABM_ESTATE).  Synchronises. */
+ * NULL; ragged batches: the populations' agents concatenated, 0x7FFF throughout
+ * a population without a strategy).  Synchronises. */
 int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *dose2_day);
 
 /* Per-day counters already run: days [0, day_count) of new infections

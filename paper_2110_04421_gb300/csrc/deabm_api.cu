@@ -1250,7 +1250,25 @@ extern "C" int deabm_get_dose_days(deabm_ctx *ctx, int16_t *dose1_day, int16_t *
 {
     if (!ctx) return fail(nullptr, DEABM_EINVAL, "ctx is NULL");
     if (!ctx->S.vd1) return fail(ctx, DEABM_ESTATE, "no vaccination priority strategy in this context");
-    if (ctx->ragged) return fail(ctx, DEABM_ESTATE, "dose days are not read back from ragged batches");
+    if (ctx->ragged) {  // populations in order, each agent at its caller position (as deabm_get_state)
+        int r;
+        if ((r = perm_scratch_ready(ctx))) return r;
+        const HostBuf outs[] = {{dose1_day, 2ull * ctx->n}, {dose2_day, 2ull * ctx->n}};
+        prefault(outs, 2);
+        const int16_t *src[2] = {ctx->S.vd1, ctx->S.vd2};
+        int16_t *dst[2] = {dose1_day, dose2_day};
+        for (int q = 0; q < 2; ++q) {
+            if (!dst[q]) continue;
+            const void *from = src[q];
+            if (ctx->relabel) {
+                CU(ctx, launch_to_caller(ctx->perm_scratch, from, ctx->orig_id, ctx->n, 1u, 2u, ctx->stream));
+                from = ctx->perm_scratch;
+            }
+            CU(ctx, cudaMemcpyAsync(dst[q], from, 2ull * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return DEABM_OK;
+    }
     const uint32_t B = ctx->n_rep;
     const size_t nb = (size_t)ctx->n * B;
     std::vector<int16_t> t1(nb), t2(nb);
@@ -1334,8 +1352,6 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             total += graphs[q].n_agents;
             max_steps = std::max(max_steps, params[q].max_steps ? params[q].max_steps : 1024u);
             if (params[q].keep_lambda) return fail(ctx, DEABM_EINVAL, "keep_lambda is not available for ragged batches");
-            if (params[q].vax_strategy && (agents[q].dose1_day || agents[q].dose2_day))
-                return fail(ctx, DEABM_EINVAL, "population %u: initial dose days are not taken in ragged batches", q);
         }
         if (total >= (1ull << 31)) return fail(ctx, DEABM_EINVAL, "too many agents in total");
         ctx->ragged = true;
@@ -1614,6 +1630,10 @@ extern "C" int deabm_create_ragged(uint32_t n_pops, const deabm_graph *graphs, c
             if ((r = put(ctx->S0.tinf + base, a.tinf, 2))) return r;
             if ((r = put(ctx->S0.flags + base, a.flags, 1))) return r;
             if ((r = put(ctx->S0.qt + base, a.qt, 1))) return r;
+            if (p.vax_strategy && ctx->S0.vd1) {  // the caller's dose days so far (none where not given)
+                if (a.dose1_day && (r = put(ctx->S0.vd1 + base, a.dose1_day, 2))) return r;
+                if (a.dose2_day && (r = put(ctx->S0.vd2 + base, a.dose2_day, 2))) return r;
+            }
             if (K.den_on) {  // app holders, part of the initial state
                 StateRef S0p{ctx->S0.stage + base, ctx->S0.timer + base, ctx->S0.tinf + base, ctx->S0.flags + base,
                              ctx->S0.qt + base};

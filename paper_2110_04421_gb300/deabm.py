@@ -356,7 +356,10 @@ class RaggedSimulation:
     parameters) stepped together by one persistent kernel per day; ``run`` replays
     a captured CUDA graph of the days."""
 
-    def __init__(self, pops: list, params: list, max_steps: int = 1024, stream=None, locality_order: bool = True):
+    def __init__(self, pops: list, params: list, max_steps: int = 1024, stream=None, locality_order: bool = True,
+                 states: list | None = None):
+        """states: optional per-population initial state dicts (as Simulation's
+        `state`, dose days included), None entries for the default state."""
         L = lib()
         keep = []
         n = len(pops)
@@ -373,6 +376,14 @@ class RaggedSimulation:
             if ids.size:
                 ag[q].seed_ids = ids.ctypes.data
                 ag[q].n_seed = ids.size
+            st = states[q] if states is not None else None
+            if st is not None:
+                for k, dt in (("stage", np.int8), ("timer", np.int16), ("tinf", np.int16), ("flags", np.uint8),
+                              ("qt", np.uint8), ("dose1_day", np.int16), ("dose2_day", np.int16)):
+                    if k in st:
+                        arr = np.ascontiguousarray(st[k], dtype=dt)
+                        keep.append(arr)
+                        setattr(ag[q], k, arr.ctypes.data)
             ps[q] = make_params(par, max_steps=max_steps, locality_order=locality_order)
         self.sizes = [int(p["n"]) for p in pops]
         self.n_pops = n
@@ -421,6 +432,18 @@ class RaggedSimulation:
         g = np.zeros(days, np.uint64)
         _check(lib().deabm_get_gathered(self.ctx, days, _p(g)), self.ctx)
         return g
+
+    def dose_days(self) -> list:
+        """Per population, each agent's first and second dose day under a priority
+        strategy (0x7FFF = none), caller order."""
+        d1 = np.zeros(self.n, np.int16)
+        d2 = np.zeros(self.n, np.int16)
+        _check(lib().deabm_get_dose_days(self.ctx, _p(d1), _p(d2)), self.ctx)
+        res, b = [], 0
+        for n in self.sizes:
+            res.append((d1[b:b + n], d2[b:b + n]))
+            b += n
+        return res
 
     def state(self) -> list:
         """Per-population state dicts (caller ids)."""

@@ -248,3 +248,43 @@ def test_notification_over_watts_strogatz_networks_in_ragged_batches(locality):
     ni_o, h_o, _ = o.run(T)
     assert np.array_equal(ni_o, ni[:, 1]) and np.array_equal(h_o, h[:, 1])
     assert list(nt[:, 1]) == o.den_notified
+
+
+@pytest.mark.parametrize("locality", [True, False])
+def test_ragged_strategies_resume_from_given_dose_days(locality):
+    """A ragged batch started from saved states (dose days of a priority strategy
+    included) continues each population exactly as a plain context started from
+    the same state; the dose days read back per population equal the plain ones."""
+    from paper_2110_04421_gb300.deabm import RaggedSimulation, Simulation
+    pops, params = case()
+    for q, strategy in ((0, 1), (2, 3), (5, 2)):
+        params[q] = dict(params[q], vax_on=1, vax_start=2, vax_rate=0.03, vax_strategy=strategy,
+                         dose2_delay=5 + q, elderly_bin=6)
+    T0, T1 = 12, 20
+    saved, singles, doses = [], [], []
+    for pop, par in zip(pops, params):
+        s = Simulation(pop, par, pop["age"], pop["seed_ids"], max_steps=T0 + T1, locality_order=False)
+        s.run(T0)
+        st = s.state()
+        if par.get("vax_strategy", 0):
+            st["dose1_day"], st["dose2_day"] = s.dose_days()
+        s.close()
+        saved.append(st)
+        # the continuation: a plain context from the saved state (no initial cases again)
+        s2 = Simulation(pop, par, pop["age"], [], state=st, max_steps=T1, locality_order=False)
+        ni1, h1 = s2.run(T1)
+        singles.append((ni1[:, 0], h1[:, 0], s2.state()))
+        doses.append(s2.dose_days() if par.get("vax_strategy", 0) else None)
+        s2.close()
+    pops2 = [dict(p, seed_ids=[]) for p in pops]
+    r = RaggedSimulation(pops2, params, max_steps=T1, locality_order=locality, states=saved)
+    ni, h = r.run(T1)
+    check((ni, h, r.state()), singles)
+    dd = r.dose_days()
+    r.close()
+    for q, d in enumerate(doses):
+        if d is None:
+            assert (dd[q][0] == 0x7FFF).all() and (dd[q][1] == 0x7FFF).all(), q
+        else:
+            assert np.array_equal(dd[q][0], d[0]) and np.array_equal(dd[q][1], d[1]), q
+    assert (dd[2][1] != 0x7FFF).sum() > 0  # second doses given after the resume
